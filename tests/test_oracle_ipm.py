@@ -1,0 +1,267 @@
+"""Pins of the oracle's interior-point method (CPU only).
+
+* Newton step: the condensed Lifted-KKT solve plus recovery (eqs.
+  liftedkkt-pd, cholesky-lower/upper/delta, infiniteOCP-augmented) equals the
+  solution of the full primal-dual Newton system of the barrier KKT
+  conditions, assembled here densely and solved with numpy.
+* Sylvester relation (eq. infiniteOCP-inertia): Cholesky of K_c succeeds
+  exactly when K_aug has inertia (n + m_g, 0, m_g).
+* Converged solutions: linear-quadratic cases against the exact solution of
+  the equality-constrained QP; tiny box-constrained QPs against brute-force
+  active-set enumeration; nonlinear cases by finite-difference stationarity.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+GAMMA = 1e-9
+
+
+def _random_state(O, p, seed):
+    rng = np.random.default_rng(seed)
+    st = O.State(p.n, p.m)
+    yL, yU = p.bounds()
+    lo = np.where(np.isfinite(yL), yL, -1.0)
+    hi = np.where(np.isfinite(yU), yU, 2.0)
+    st.y[:] = lo + (hi - lo) * rng.uniform(0.2, 0.8, p.n)
+    st.zL[:] = np.where(np.isfinite(yL), rng.uniform(0.1, 2, p.n), 0.0)
+    st.zU[:] = np.where(np.isfinite(yU), rng.uniform(0.1, 2, p.n), 0.0)
+    for k in ("s_p", "s_m", "b_p", "b_m"):
+        getattr(st, k)[:] = rng.uniform(0.1, 2, p.m)
+    for k in ("w_p", "w_m"):
+        getattr(st, k)[:] = rng.uniform(-1, 2, p.m)
+    return st
+
+
+def _full_newton(O, p, st, mu, dw):
+    """Dense primal-dual Newton system of the lifted barrier KKT conditions
+    in (dy, ds+, ds-, dw+, dw-, db+, db-, dzL, dzU)."""
+    n, m = p.n, p.m
+    yL, yU = p.bounds()
+    L_idx = np.nonzero(np.isfinite(yL))[0]
+    U_idx = np.nonzero(np.isfinite(yU))[0]
+    _, g, h, _ = O.evaluate(p, st.y)
+    H = O.jacobian_dense(p, st.y)
+    W = O.hessian_dense(p, st.y, st.w_p - st.w_m) + dw * np.eye(n)
+    nL, nU = len(L_idx), len(U_idx)
+    sizes = [n, m, m, m, m, m, m, nL, nU]
+    off = np.cumsum([0] + sizes)
+    N = off[-1]
+    J = np.zeros((N, N))
+    F = np.zeros(N)
+    EL = np.zeros((n, nL)); EL[L_idx, np.arange(nL)] = 1
+    EU = np.zeros((n, nU)); EU[U_idx, np.arange(nU)] = 1
+    I = np.eye(m)
+    zL, zU = st.zL[L_idx], st.zU[U_idx]
+    B = lambda r, c, M: J.__setitem__((slice(off[r], off[r + 1]), slice(off[c], off[c + 1])), M)
+    # stationarity in y
+    B(0, 0, W); B(0, 3, H.T); B(0, 4, -H.T); B(0, 7, -EL); B(0, 8, EU)
+    F[off[0]:off[1]] = g + H.T @ (st.w_p - st.w_m) - EL @ zL + EU @ zU
+    # stationarity in s+, s-
+    B(1, 3, I); B(1, 5, -I); F[off[1]:off[2]] = st.w_p - st.b_p
+    B(2, 4, I); B(2, 6, -I); F[off[2]:off[3]] = st.w_m - st.b_m
+    # lifted constraints
+    B(3, 0, H); B(3, 1, I); F[off[3]:off[4]] = h - GAMMA + st.s_p
+    B(4, 0, -H); B(4, 2, I); F[off[4]:off[5]] = -h - GAMMA + st.s_m
+    # complementarity
+    B(5, 1, np.diag(st.b_p)); B(5, 5, np.diag(st.s_p)); F[off[5]:off[6]] = st.s_p * st.b_p - mu
+    B(6, 2, np.diag(st.b_m)); B(6, 6, np.diag(st.s_m)); F[off[6]:off[7]] = st.s_m * st.b_m - mu
+    gl = st.y[L_idx] - yL[L_idx]
+    gu = yU[U_idx] - st.y[U_idx]
+    B(7, 0, np.diag(zL) @ EL.T); B(7, 7, np.diag(gl)); F[off[7]:off[8]] = gl * zL - mu
+    B(8, 0, -np.diag(zU) @ EU.T); B(8, 8, np.diag(gu)); F[off[8]:off[9]] = gu * zU - mu
+    d = np.linalg.solve(J, -F)
+    parts = [d[off[i]:off[i + 1]] for i in range(9)]
+    dzL = np.zeros(n); dzL[L_idx] = parts[7]
+    dzU = np.zeros(n); dzU[U_idx] = parts[8]
+    return dict(y=parts[0], s_p=parts[1], s_m=parts[2], w_p=parts[3], w_m=parts[4],
+                b_p=parts[5], b_m=parts[6], zL=dzL, zU=dzU)
+
+
+@pytest.mark.parametrize("model", ["distill", "plate", "toy"])
+def test_newton_step_equals_uncondensed_solve(oracle, model):
+    O = oracle
+    if model == "distill":
+        p = O.distillation(5, 3, 3, np.full(5, 0.5), np.full(3, 0.6), 2.0, dt=0.5)
+    elif model == "plate":
+        p = O.plate(4, 8, 2, np.zeros(16), np.full(16, 0.3), dt=0.5)
+    else:
+        p = O.toy(4, 1.0, np.sin(np.arange(4)), dt=0.7)
+    for seed, mu, dw in [(1, 0.1, 0.0), (2, 1e-3, 0.5), (3, 1.0, 2.0)]:
+        st = _random_state(O, p, seed)
+        rc, d = O.newton_step(p, st, mu, dw, gamma=GAMMA)
+        if rc != 0:
+            continue  # K_c not PD at this point: covered by the Sylvester test
+        ref = _full_newton(O, p, st, mu, dw)
+        for k, v in ref.items():
+            np.testing.assert_allclose(getattr(d, k), v, rtol=1e-8, atol=1e-9 * (1 + np.abs(v).max()),
+                                       err_msg=f"{model} seed {seed} {k}")
+
+
+def test_sylvester_inertia_relation(oracle):
+    """eq. infiniteOCP-inertia for the lifted system (m_h = 0, m_g = 2m):
+    inertia(K_aug) = (n + 2m, 0, 2m)  <=>  K_c positive definite, where
+    K_aug = [[W + Sigma, 0, G^T], [0, Q, I], [G, I, 0]], G = [H; -H]."""
+    O = oracle
+    p = O.toy(5, 1.0, np.sin(np.arange(5)), dt=0.8)
+    agree = {True: 0, False: 0}
+    for seed in range(40):
+        st = _random_state(O, p, seed)
+        rng = np.random.default_rng(100 + seed)
+        st.w_p[:] = rng.uniform(-6, 6, p.m)  # large multipliers make W indefinite
+        dw = float(rng.choice([-3.0, -1.0, 0.0, 1.0, 5.0, 20.0]))
+        n, m = p.n, p.m
+        yL, yU = p.bounds()
+        H = O.jacobian_dense(p, st.y)
+        W = O.hessian_dense(p, st.y, st.w_p - st.w_m) + dw * np.eye(n)
+        sig = np.where(np.isfinite(yL), st.zL / (st.y - np.where(np.isfinite(yL), yL, 0)), 0.0)
+        sig += np.where(np.isfinite(yU), st.zU / (np.where(np.isfinite(yU), yU, 0) - st.y), 0.0)
+        Q = np.concatenate([st.b_p / st.s_p, st.b_m / st.s_m])
+        G = np.vstack([H, -H])
+        Kaug = np.block([[W + np.diag(sig), np.zeros((n, 2 * m)), G.T],
+                         [np.zeros((2 * m, n)), np.diag(Q), np.eye(2 * m)],
+                         [G, np.eye(2 * m), np.zeros((2 * m, 2 * m))]])
+        ev = np.linalg.eigvalsh(Kaug)
+        right_inertia = (np.sum(ev > 1e-10) == n + 2 * m) and (np.sum(ev < -1e-10) == 2 * m)
+        Kc = W + np.diag(sig) + G.T @ np.diag(Q) @ G
+        pd = bool(np.all(np.linalg.eigvalsh(Kc) > 0))
+        assert right_inertia == pd
+        rc, _ = O.newton_step(p, st, 0.1, dw, gamma=GAMMA)
+        assert (rc == 0) == pd
+        agree[pd] += 1
+    assert agree[True] > 3 and agree[False] > 3  # both branches exercised
+
+
+def _quadratic_model(O, p):
+    """f = 1/2 y'Qy + c'y + f0 and h = A y + h0 (exact for linear-quadratic
+    models), read off the oracle's gradient and constraint values."""
+    n = p.n
+    f0, c, h0, _ = O.evaluate(p, np.zeros(n))
+    Q = np.zeros((n, n))
+    A = O.jacobian_dense(p, np.zeros(n))
+    for j in range(n):
+        e = np.zeros(n); e[j] = 1.0
+        Q[:, j] = O.evaluate(p, e)[1] - c
+    return Q, c, A, h0
+
+
+def test_lq_plate_matches_equality_qp(oracle):
+    """With bounds far away the plate OCP is an equality-constrained QP whose
+    exact solution solves [[Q, A^T], [A, 0]] [y; lam] = [-c; -h0]."""
+    O = oracle
+    g, S, T = 3, 4, 4
+    rng = np.random.default_rng(4)
+    p = O.plate(g, S, T, rng.uniform(0, 0.5, g * g), rng.uniform(0, 1, g * g), dt=0.5,
+                xhi=1e3, ulo=-1e3, uhi=1e3, cq=0.5, rho_u=1e-2)
+    Q, c, A, h0 = _quadratic_model(O, p)
+    n, m = p.n, p.m
+    K = np.block([[Q, A.T], [A, np.zeros((m, m))]])
+    sol = np.linalg.solve(K, np.concatenate([-c, -h0]))
+    st, info, _ = O.solve(p)
+    assert info["status"] == 0
+    y_ref = sol[:n]
+    assert np.max(np.abs(st.y - y_ref)) / max(1.0, np.max(np.abs(y_ref))) < 1e-6
+    lam_ref = sol[n:]
+    np.testing.assert_allclose(st.w_p - st.w_m, lam_ref, rtol=1e-4, atol=1e-5)
+
+
+def test_box_qp_matches_bruteforce_active_set(oracle):
+    """Tiny plate QP (g=2, S=4, T=1) with state upper bounds and control
+    boxes: enumerate every active set (2^4 * 3^4), keep the one whose
+    equality-QP solution is primal feasible with correctly signed bound
+    multipliers; it is the unique optimum of the strictly convex QP."""
+    O = oracle
+    g, S, T = 2, 4, 1
+    tgt = np.array([1.0, 0.2, 1.0, 0.0])
+    p = O.plate(g, S, T, np.zeros(4), tgt, dt=1.0, xhi=0.6, cq=0.4, rho_u=0.05)
+    Q, c, A, h0 = _quadratic_model(O, p)
+    n, m = p.n, p.m
+    yL, yU = p.bounds()
+    xs = list(range(p.off_x(1), p.off_x(1) + 4))
+    us = list(range(p.off_u(1), p.off_u(1) + 4))
+    found = []
+    for xa in itertools.product([0, 1], repeat=4):
+        for ua in itertools.product([0, 1, 2], repeat=4):
+            act = [(i, yU[i], +1) for i, a in zip(xs, xa) if a] + \
+                  [(i, yL[i], -1) for i, a in zip(us, ua) if a == 1] + \
+                  [(i, yU[i], +1) for i, a in zip(us, ua) if a == 2]
+            E = np.zeros((len(act), n))
+            for r, (i, _, _) in enumerate(act):
+                E[r, i] = 1.0
+            Aall = np.vstack([A, E])
+            b = np.concatenate([-h0, [v for _, v, _ in act]])
+            k = Aall.shape[0]
+            K = np.block([[Q, Aall.T], [Aall, np.zeros((k, k))]])
+            try:
+                sol = np.linalg.solve(K, np.concatenate([-c, b]))
+            except np.linalg.LinAlgError:
+                continue
+            y, nu = sol[:n], sol[n + m:]
+            feas = np.all(y <= yU + 1e-12) and np.all(y >= yL - 1e-12)
+            signs = all(s * v >= -1e-12 for (_, _, s), v in zip(act, nu))
+            if feas and signs:
+                found.append((y, len(act)))
+    assert len(found) == 1
+    y_ref, nact = found[0]
+    assert 0 < nact < 8  # a genuine mix of active and inactive bounds
+    st, info, _ = O.solve(p)
+    assert info["status"] == 0
+    assert np.max(np.abs(st.y - y_ref)) < 1e-6
+
+
+def _fd_stationarity(O, p, st, step=1e-6):
+    """grad f + H^T lam - zL + zU with grad f and H from central differences
+    of the oracle's objective and constraint values only."""
+    n = p.n
+    lam = st.w_p - st.w_m
+    r = -st.zL + st.zU
+    for j in range(n):
+        e = np.zeros(n); e[j] = step
+        fp, _, hp, _ = O.evaluate(p, st.y + e)
+        fm, _, hm, _ = O.evaluate(p, st.y - e)
+        r[j] += (fp - fm) / (2 * step) + np.dot((hp - hm) / (2 * step), lam)
+    return r
+
+
+def test_toy_code_listing_problem_converges(oracle):
+    """The code listing's problem: dy/dt = 4 sin u - y^3, y(0) = 1, 1 <= u <= 3,
+    y >= 0, 15 supports on [0, 10] (14 intervals), setpoint sin(t + t_k)."""
+    O = oracle
+    T = 14
+    dt = 10.0 / T
+    t = dt * np.arange(1, T + 1)
+    p = O.toy(T, 1.0, np.sin(t), dt=dt)
+    st, info, _ = O.solve(p)
+    assert info["status"] == 0 and info["E0_scaled"] <= 1e-8
+    r = _fd_stationarity(O, p, st)
+    assert np.max(np.abs(r)) < 1e-6
+    _, _, h, _ = O.evaluate(p, st.y)
+    assert np.max(np.abs(h)) <= 2 * GAMMA + 1e-8
+    yL, yU = p.bounds()
+    assert np.all(st.y >= yL) and np.all(st.y <= yU)
+    # a second NMPC step from the measured state, warm-started
+    y1 = st.y[p.off_x(1)]
+    p.set_params(x0=[y1], sp=np.sin(t + 1.0))
+    st, info, _ = O.solve(p, state=st, warm=True)
+    assert info["status"] == 0
+
+
+def test_distillation_closed_loop_small(oracle):
+    """Config-1-sized column (N=12, feed tray 5, T=20): a cold solve and four
+    warm re-solves, each converged with FD-stationary primal-dual point."""
+    O = oracle
+    N, Nf, T = 12, 5, 20
+    xs = np.loadtxt(__import__("os").path.join(__import__("os").path.dirname(__file__),
+                                                "golden", "steady_state_N12_Nf5.txt"))
+    rng = np.random.default_rng(1)
+    x0 = np.clip(xs + rng.normal(0, 0.02, N), 0, 1)
+    p = O.distillation(N, Nf, T, x0, np.full(T, 0.8), 2.51459)
+    st, info, _ = O.solve(p)
+    assert info["status"] == 0
+    for k in range(4):
+        p.set_params(x0=st.y[p.off_x(1):p.off_x(1) + N].copy(), uprev=st.y[p.off_u(1)])
+        st, info, _ = O.solve(p, state=st, warm=True)
+        assert info["status"] == 0 and info["iters"] < 20
+    r = _fd_stationarity(O, p, st)
+    assert np.max(np.abs(r)) < 1e-5
