@@ -1,0 +1,224 @@
+/* nmpc.h -- C ABI of the GB300-native parametric interior-point NMPC library.
+ *
+ * The library implements the per-iteration hot path of the parametric
+ * interior-point method of arXiv 2606.04725 (Sec. 3.2, Algorithms 1 and 2):
+ * stage-parallel derivative evaluation, assembly of the condensed Lifted-KKT
+ * matrix (eq. liftedkkt-pd) into a fixed pattern, numeric supernodal Cholesky
+ * against a symbolic analysis done once (eqs. cholesky-symCholesky,
+ * cholesky-numCholesky), triangular solves (eqs. cholesky-lower/upper/delta),
+ * line search (eq. infiniteOCP-lineSearch) and barrier/termination control
+ * (eqs. infiniteOCP-innerTol/outerTol).  Every numeric step runs in CUDA
+ * kernels for sm_103a in FP64; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - Return value: NMPC_OK or an error status; no entry point aborts, exits
+ *    or throws.  nmpc_last_error() gives a message for the last failure.
+ *  - Pointers are owned by the caller and are not retained past the call.
+ *    "on_device" arguments say whether the caller's arrays are device
+ *    pointers (1) or host pointers (0).  Host arrays may be pageable.
+ *  - All device work is ordered on the CUDA stream given to nmpc_build.
+ *    Calls that read or write host memory synchronize that stream before
+ *    returning; calls with device arrays return without synchronizing.
+ *  - Device memory is not allocated by the library: nmpc_build performs the
+ *    one-time host analysis and reports the workspace size; the caller
+ *    allocates it (for example as a torch.uint8 tensor) and hands it over
+ *    with nmpc_bind.  The workspace must stay valid until nmpc_destroy.
+ *  - Layout of one instance's primal vector y (stage-interleaved):
+ *      y = [ x_0 | x_1 u_1 | ... | x_T u_T ],  n = nx + T (nx + nu)
+ *    with nx states and nu controls per stage; rows of h are the initial
+ *    condition x_0 - p_x0 = 0 followed by the T backward-Euler steps.
+ */
+#ifndef NMPC_H
+#define NMPC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nmpc_handle nmpc_handle;
+
+typedef enum {
+  NMPC_OK = 0,
+  NMPC_ERR_INVALID = 1,      /* bad argument (size, pointer, state of the handle) */
+  NMPC_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  NMPC_ERR_WORKSPACE = 3,    /* workspace missing or too small */
+  NMPC_MAX_ITER = 10,        /* interior-point iteration limit reached */
+  NMPC_LINESEARCH_FAIL = 11, /* step size fell below alpha_min (no restoration phase) */
+  NMPC_INERTIA_FAIL = 12,    /* regularization delta_w exceeded its maximum */
+  NMPC_NONFINITE = 13,       /* NaN or Inf in the residuals */
+  NMPC_TIMEOUT = 14,         /* a bounded device wait gave up */
+  NMPC_NOT_SOLVED = 15       /* no converged solution is available yet */
+} nmpc_status;
+
+typedef enum {
+  NMPC_MODEL_DISTILLATION = 0, /* binary column of Sec. 4.1 (eq. distill-ocp) */
+  NMPC_MODEL_PLATE = 1,        /* linear heated plate, boundary flux actuators */
+  NMPC_MODEL_TOY = 2           /* dy/dt = 4 sin u - y^3 of the paper's code listing */
+} nmpc_model;
+
+typedef enum {
+  NMPC_ORDER_AUTO = 0,         /* chosen by the autotuner (or a size rule) */
+  NMPC_ORDER_NATURAL = 1,      /* stage order: elimination tree is a chain */
+  NMPC_ORDER_ND = 2            /* geometric nested dissection (time, then space) */
+} nmpc_ordering;
+
+/* Problem description.  All instances share the model and its constants;
+ * each instance has its own horizon T (block-diagonal batch, one KKT block
+ * per instance).  Fill it with nmpc_problem_defaults first. */
+typedef struct {
+  int model;             /* nmpc_model */
+  int n_instances;       /* >= 1 */
+  const int* horizons;   /* n_instances horizons T >= 1 (host pointer) */
+  int N;                 /* distillation: trays, condenser = 1, reboiler = N */
+  int Nf;                /* distillation: feed tray (1-based, 2 <= Nf <= N-1) */
+  int g;                 /* plate: grid side (cells), g % (S/4) == 0 */
+  int S;                 /* plate: actuator segments, multiple of 4 */
+  double dt;             /* time step of the backward-Euler transcription */
+  double alpha, D, F, xF, Ac, At, Ar, wdu; /* distillation constants */
+  double kappa, cq, rho_u;                 /* plate constants */
+  double xlo, xhi, ulo, uhi;               /* bounds of x_1..x_T and u_1..u_T (+-INFINITY allowed) */
+} nmpc_problem;
+
+/* Solver options.  Defaults from nmpc_options_defaults. */
+typedef struct {
+  double tol;            /* outer tolerance on the scaled optimality error E_0 (1e-8) */
+  double gamma;          /* Lifted-KKT relaxation -gamma <= h <= gamma (1e-9) */
+  double mu0_cold;       /* initial barrier parameter, cold start (0.1) */
+  double mu0_warm;       /* initial barrier parameter, warm start (1e-8) */
+  double push_cold;      /* bound push of the initial point, cold (1e-2) */
+  double push_warm;      /* bound push of the initial point, warm (1e-9) */
+  int max_iter;          /* interior-point iteration limit (200) */
+  int ordering;          /* nmpc_ordering */
+  int nd_leaf;           /* nested dissection: stages per leaf (1) */
+  int use_graph;         /* capture one interior-point iteration in a CUDA graph (1) */
+  long long spin_limit;  /* iteration limit of bounded device waits (1e7) */
+} nmpc_options;
+
+/* Per-instance result of a solve.  Times are measured with CUDA events on
+ * the library stream and cover the whole solve call. */
+typedef struct {
+  int status;            /* nmpc_status of this instance */
+  int iters;             /* interior-point iterations */
+  int inertia_retries;   /* factorizations repeated with a larger delta_w */
+  int ls_trials;         /* line-search trial points evaluated */
+  double mu_final;
+  double kkt_scaled;     /* scaled E_0 at the returned point */
+  double kkt_unscaled;
+  double objective;
+  double ms_total;       /* whole solve call (same for all instances) */
+} nmpc_info;
+
+typedef struct {
+  int n_total, m_total;      /* primal variables / equality rows over all instances */
+  int n_supernodes, n_levels;
+  long long nnz_L;           /* stored entries of the supernodal factor (lower panels) */
+  double factor_flops;       /* floating-point operations of one numeric factorization */
+  double solve_flops;        /* of one forward + backward solve */
+  long long workspace_bytes;
+  double analysis_ms;        /* host time of the one-time structure analysis */
+  int max_front;             /* largest frontal matrix order */
+  int ordering_used;
+  long long kernel_launches; /* kernels launched by this handle so far */
+} nmpc_stats;
+
+/* Average device time (CUDA events on the library stream) of the phases of
+ * one interior-point iteration, re-run at the current iterate. */
+typedef struct {
+  double ms_eval;            /* stage-parallel residual/Jacobian/Hessian evaluation */
+  double ms_assemble;        /* condensed-matrix assembly into the factor pattern */
+  double ms_factor;          /* numeric supernodal Cholesky */
+  double ms_solve;           /* right-hand side, forward and backward solves */
+  int reps;
+} nmpc_phase_times;
+
+void nmpc_problem_defaults(int model, nmpc_problem* prob);
+void nmpc_options_defaults(nmpc_options* opts);
+
+/* One-time structure analysis (Sec. 3.2.3, Algorithm 2 "SymCholesky" and the
+ * transcription): Jacobian/Hessian patterns, condensed pattern, ordering P,
+ * elimination tree, supernodes, level sets, L layout and scatter maps.
+ * Host work only; no device memory is touched.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  On success *out owns the
+ * analysis; query nmpc_workspace_bytes and call nmpc_bind next. */
+nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void* cuda_stream,
+                       nmpc_handle** out);
+
+/* Device workspace size in bytes required by nmpc_bind (256-byte aligned). */
+nmpc_status nmpc_workspace_bytes(const nmpc_handle* h, size_t* bytes);
+
+/* Hand over caller-allocated device memory (workspace, >= nmpc_workspace_bytes,
+ * 256-byte aligned) and upload the structure.  Must be called once before
+ * set_params/solve.  The memory stays owned by the caller. */
+nmpc_status nmpc_bind(nmpc_handle* h, void* workspace, size_t bytes);
+
+/* Parameter update without rebuilding anything (Sec. 3.3,
+ * set_parameter_value; Algorithm 1 last line).  instance = -1 sets all
+ * instances from arrays packed instance after instance.  Any pointer may be
+ * NULL to keep that parameter.
+ *   x0:       nx values per instance (initial state p_x0)
+ *   setpoint: distillation/toy: T values per instance (setpoint of x_{k,1}
+ *             resp. y_k, k = 1..T); plate: g*g target field per instance
+ *   u_prev:   distillation: 1 value per instance (u_0 of the Delta-u term) */
+nmpc_status nmpc_set_params(nmpc_handle* h, int instance, const double* x0, const double* setpoint,
+                            const double* u_prev, int on_device);
+
+/* Run Algorithm 2 on every instance until each converges (E_0 <= tol) or
+ * fails.  warm_start = 0: cold start from a constant trajectory (the paper's
+ * PU mode); 1: start from the previous solution with mu0_warm (WS+PU).
+ * info: n_instances records (host), may be NULL.  Returns NMPC_OK when every
+ * instance converged, else the first failing instance's status. */
+nmpc_status nmpc_solve(nmpc_handle* h, int warm_start, nmpc_info* info);
+
+/* Copy an instance's solution: y (n of that instance); duals (nullable)
+ * receives [zL (n), zU (n), s+ (m), s- (m), w+ (m), w- (m), b+ (m), b- (m)]. */
+nmpc_status nmpc_get_solution(nmpc_handle* h, int instance, double* y, double* duals, int on_device);
+
+/* Overwrite an instance's primal-dual point (same layout as get_solution);
+ * the next warm solve starts from it.  duals may be NULL to keep them. */
+nmpc_status nmpc_set_start(nmpc_handle* h, int instance, const double* y, const double* duals,
+                           int on_device);
+
+/* Adjoint sensitivity at the converged point (not in the paper): for a loss
+ * l(y*) with gradient dloss_dy (n of the instance), solve the transposed
+ * condensed KKT system with the stored Cholesky factor (plus iterative
+ * refinement) and return dl/dp_x0 (nx) and dl/dsetpoint (T values or g*g).
+ * Either output may be NULL. */
+nmpc_status nmpc_sensitivity(nmpc_handle* h, int instance, const double* dloss_dy,
+                             double* dloss_dx0, double* dloss_dsetpoint, int on_device);
+
+/* Time each phase of an interior-point iteration reps times at the current
+ * iterate (after a solve or set_start) without changing the iterate or the
+ * solver state.  Used for roofline measurements. */
+nmpc_status nmpc_time_phases(nmpc_handle* h, int reps, nmpc_phase_times* out);
+
+/* Sizes and one-time analysis figures. */
+nmpc_status nmpc_get_stats(const nmpc_handle* h, nmpc_stats* stats);
+
+/* Per-instance dimensions: n, m, offset of the instance in the packed vectors. */
+nmpc_status nmpc_instance_dims(const nmpc_handle* h, int instance, int* n, int* m, int* T);
+
+/* Introspection of the one-time analysis (host only, usable before bind).
+ * Copies up to cap entries of the requested array into out (int32 unless
+ * noted) and returns the full length, or -1 for an unknown selector:
+ *   0 perm (n_total): factor position of each variable
+ *   1 supernode first column, 2 supernode column count, 3 supernode row count
+ *   4 supernode row lists, concatenated
+ *   5 supernode parent (-1 for roots)
+ *   6 level pointer (n_levels + 1), 7 supernodes ordered by level
+ *   8 condensed-matrix lower pattern as (row, col) pairs in factor order
+ *     (2 int32 per entry; the returned length counts pairs) */
+long long nmpc_structure_export(const nmpc_handle* h, int what, void* out, long long cap);
+
+/* Release host memory of the handle (the caller frees the workspace).
+ * Synchronizes the library stream.  NULL is ignored. */
+void nmpc_destroy(nmpc_handle* h);
+
+const char* nmpc_status_string(int status);
+const char* nmpc_last_error(const nmpc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

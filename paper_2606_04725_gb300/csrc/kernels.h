@@ -1,0 +1,46 @@
+// Kernel declarations of the NMPC library (all FP64, sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "nmpc_internal.h"
+
+namespace nmpc {
+
+constexpr int TPB = 256;
+
+// model_kernels.cu
+__global__ void k_eval_rows(Dev d, int use_trial, int with_jac);
+__global__ void k_eval_vars(Dev d, int use_trial);
+__global__ void k_set_params(Dev d, int i0, int i1, const double* x0, const double* sp, const double* up, int sp_len);
+__global__ void k_init_vars(Dev d, int warm, double push);
+__global__ void k_init_rows(Dev d, int warm, double push);
+
+// ipm_kernels.cu
+__global__ void k_ctl_init(Dev d, double mu0);
+__global__ void k_red_eval(Dev d);
+__global__ void k_ctl_pre(Dev d, int max_iter);
+__global__ void k_zero_L(Dev d, const long long* inst_Lbeg, const long long* inst_Lend);
+__global__ void k_rows_pre(Dev d, double* Drow);
+__global__ void k_assemble(Dev d, const int* tgt_inst, const double* Drow);
+__global__ void k_ctl_factor(Dev d);
+__global__ void k_rhs(Dev d);
+__global__ void k_recover_vars(Dev d);
+__global__ void k_recover_rows(Dev d);
+__global__ void k_red_dir(Dev d);
+__global__ void k_ctl_dir(Dev d);
+__global__ void k_trial_point(Dev d);
+__global__ void k_red_trial(Dev d);
+__global__ void k_ctl_ls(Dev d);
+__global__ void k_update_vars(Dev d);
+__global__ void k_update_rows(Dev d);
+__global__ void k_ctl_post(Dev d);
+__global__ void k_summary(Dev d, int* flags);
+
+// factor_kernels.cu
+__global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap);
+__global__ void k_fwd_level(Dev d, SnDev s, const int* list);
+__global__ void k_bwd_level(Dev d, SnDev s, const int* list);
+
+inline unsigned blocks_for(long long n, int tpb = TPB) { return (unsigned)((n + tpb - 1) / tpb); }
+
+}  // namespace nmpc

@@ -1,0 +1,365 @@
+// Stage-parallel model evaluation (hand-derived residuals, Jacobians and
+// Hessians of the Lagrangian) and the parameter-update kernel.
+//
+// One thread per equality row computes h_r and the WH Jacobian slots of the
+// row; one thread per primal variable computes the objective gradient, its
+// share of the objective and the Hessian slots it owns (Sec. 3.2.2: W, H and
+// the residuals of eq. infiniteOCP-augmentedRHS).  Rows and variables are laid
+// out stage after stage, so neighbouring threads read neighbouring stages.
+#include "kernels.h"
+
+namespace nmpc {
+
+struct Loc {  // position of an element inside its instance
+  int inst, T, vo, ro;
+};
+
+__device__ __forceinline__ int offx(const ModelConst& mc, int k) { return k == 0 ? 0 : mc.nx + (k - 1) * (mc.nx + mc.nu); }
+__device__ __forceinline__ int offu(const ModelConst& mc, int k) { return offx(mc, k) + mc.nx; }
+
+// ------------------------------------------------------------ distillation
+
+__device__ __forceinline__ double vle(double a, double x) { return a * x / (1.0 + (a - 1.0) * x); }
+__device__ __forceinline__ double vle_d1(double a, double x) { double d = 1.0 + (a - 1.0) * x; return a / (d * d); }
+__device__ __forceinline__ double vle_d2(double a, double x) { double d = 1.0 + (a - 1.0) * x; return -2.0 * a * (a - 1.0) / (d * d * d); }
+
+// Tray i (1-based) balance f_i(x, u) with L = uD, V = L + D, S = L + F, and its
+// partial derivatives w.r.t. x_{i-1}, x_i, x_{i+1}, u (eq. distill-ocp).
+struct TrayEval { double f, dm, d0, dp, du; };
+
+__device__ TrayEval tray_eval(const ModelConst& mc, const double* x, double u, int i) {
+  const int N = mc.N, Nf = mc.Nf;
+  const double a = mc.alpha, D = mc.D;
+  const double L = u * D, V = L + D, S = L + mc.F;
+  TrayEval e{0, 0, 0, 0, 0};
+  const double xi = x[i - 1];
+  if (i == 1) {  // total condenser
+    const double x2 = x[1];
+    const double y2 = vle(a, x2);
+    e.f = V * (y2 - xi) / mc.Ac;
+    e.d0 = -V / mc.Ac;
+    e.dp = V * vle_d1(a, x2) / mc.Ac;
+    e.du = D * (y2 - xi) / mc.Ac;
+    return e;
+  }
+  if (i == N) {  // reboiler
+    const double xm = x[N - 2], yN = vle(a, xi);
+    e.f = (S * xm - (mc.F - D) * xi - V * yN) / mc.Ar;
+    e.dm = S / mc.Ar;
+    e.d0 = (-(mc.F - D) - V * vle_d1(a, xi)) / mc.Ar;
+    e.du = D * (xm - yN) / mc.Ar;
+    return e;
+  }
+  const double xm = x[i - 2], xp = x[i];
+  const double yi = vle(a, xi), yp = vle(a, xp);
+  // liquid entering from above: L above the feed tray, L onto the feed tray,
+  // S below it; liquid leaving: L above the feed, S from the feed tray down
+  const double lin = (i <= Nf) ? L : S;
+  const double lout = (i < Nf) ? L : S;
+  const double feed = (i == Nf) ? mc.F * mc.xF : 0.0;
+  e.f = (feed + lin * xm - lout * xi - V * (yi - yp)) / mc.At;
+  e.dm = lin / mc.At;
+  e.d0 = (-lout - V * vle_d1(a, xi)) / mc.At;
+  e.dp = V * vle_d1(a, xp) / mc.At;
+  e.du = D * (xm - xi - (yi - yp)) / mc.At;
+  return e;
+}
+
+// ------------------------------------------------------------------ plate
+
+__device__ __forceinline__ int plate_seg_of(const ModelConst& mc, int ci, int cj, int* segs) {
+  const int per = mc.S / 4, run = mc.g / per;
+  int k = 0;
+  if (cj == 0) segs[k++] = ci / run;
+  if (ci == mc.g - 1) segs[k++] = per + cj / run;
+  if (cj == mc.g - 1) segs[k++] = 2 * per + ci / run;
+  if (ci == 0) segs[k++] = 3 * per + cj / run;
+  if (k == 2 && segs[1] < segs[0]) { int t = segs[0]; segs[0] = segs[1]; segs[1] = t; }
+  return k;
+}
+
+// ------------------------------------------------------------------ rows
+
+// h and H for every row (at iterate y, or at the trial point when only the
+// residual is wanted: Hv == nullptr).
+__device__ void eval_row(const Dev& d, const double* y, int r, double* hout, double* Hv) {
+  const ModelConst& mc = d.mc;
+  const int i = d.row_inst[r];
+  const int vo = d.inst_voff[i], ro = d.inst_roff[i];
+  const int lr = r - ro;
+  const int nx = mc.nx;
+  const int WH = mc.WH;
+  const double* yi = y + vo;
+  if (lr < nx) {  // initial condition x_0 - p_x0
+    hout[r] = yi[lr] - d.p_x0[(size_t)i * nx + lr];
+    if (Hv) {
+      Hv[(size_t)r * WH] = 1.0;
+      for (int s = 1; s < WH; ++s) Hv[(size_t)r * WH + s] = 0.0;
+    }
+    return;
+  }
+  const int k = lr / nx - 1, q = lr % nx;
+  const double* xk = yi + offx(mc, k);
+  const double* xn = yi + offx(mc, k + 1);
+  const double* un = yi + offu(mc, k + 1);
+  const double dt = mc.dt;
+  if (mc.model == MODEL_DISTILL) {
+    TrayEval e = tray_eval(mc, xn, un[0], q + 1);
+    hout[r] = xn[q] - xk[q] - dt * e.f;
+    if (Hv) {
+      double* H = Hv + (size_t)r * WH;
+      H[0] = -1.0;
+      H[1] = -dt * e.dm;
+      H[2] = 1.0 - dt * e.d0;
+      H[3] = -dt * e.dp;
+      H[4] = -dt * e.du;
+    }
+  } else if (mc.model == MODEL_PLATE) {
+    const int g = mc.g, ci = q % g, cj = q / g;
+    const double hh = 1.0 / g, c = mc.kappa / (hh * hh);
+    double lap = 0.0;
+    int nb = 0;
+    if (cj > 0) { lap += xn[q - g]; ++nb; }
+    if (ci > 0) { lap += xn[q - 1]; ++nb; }
+    if (ci < g - 1) { lap += xn[q + 1]; ++nb; }
+    if (cj < g - 1) { lap += xn[q + g]; ++nb; }
+    lap -= nb * xn[q];
+    int segs[2];
+    const int nsg = plate_seg_of(mc, ci, cj, segs);
+    double flux = 0.0;
+    for (int t = 0; t < nsg; ++t) flux += un[segs[t]];
+    hout[r] = xn[q] - xk[q] - dt * (c * lap + mc.cq / hh * flux);
+    if (Hv) {
+      double* H = Hv + (size_t)r * WH;
+      H[0] = -1.0;
+      H[1] = (cj > 0) ? -dt * c : 0.0;
+      H[2] = (ci > 0) ? -dt * c : 0.0;
+      H[3] = 1.0 + dt * c * nb;
+      H[4] = (ci < g - 1) ? -dt * c : 0.0;
+      H[5] = (cj < g - 1) ? -dt * c : 0.0;
+      H[6] = (nsg > 0) ? -dt * mc.cq / hh : 0.0;
+      H[7] = (nsg > 1) ? -dt * mc.cq / hh : 0.0;
+    }
+  } else {
+    const double yn = xn[0], u = un[0];
+    hout[r] = yn - xk[0] - dt * (4.0 * sin(u) - yn * yn * yn);
+    if (Hv) {
+      double* H = Hv + (size_t)r * WH;
+      H[0] = -1.0;
+      H[1] = 1.0 + 3.0 * dt * yn * yn;
+      H[2] = -4.0 * dt * cos(u);
+    }
+  }
+}
+
+__global__ void k_eval_rows(Dev d, int use_trial, int with_jac) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.m) return;
+  const Ctl& c = d.ctl[d.row_inst[r]];
+  if (use_trial) {
+    if (!c.ls_active) return;
+    eval_row(d, d.yt, r, d.ht, nullptr);
+  } else {
+    if (c.status != ST_RUNNING) return;
+    eval_row(d, d.y, r, d.h, with_jac ? d.Hv : nullptr);
+  }
+}
+
+// --------------------------------------------------------------- variables
+
+// Objective share owned by variable v (tracking and control terms are
+// attributed to the stage-k variable they penalize) and its gradient.
+__device__ void eval_var_obj(const Dev& d, const double* y, int v, double* fshare, double* grad) {
+  const ModelConst& mc = d.mc;
+  const int i = d.var_inst[v];
+  const int vo = d.inst_voff[i], T = d.inst_T[i];
+  const int lv = v - vo;
+  const int nx = mc.nx, nu = mc.nu;
+  double f = 0.0, gr = 0.0;
+  if (lv >= nx) {
+    const int k = (lv - nx) / (nx + nu) + 1;
+    const int q = (lv - nx) % (nx + nu);
+    const double* yi = y + vo;
+    const double dt = mc.dt;
+    if (mc.model == MODEL_DISTILL) {
+      if (q == 0) {
+        const double e = yi[lv] - d.p_sp[(size_t)i * d.sp_stride + k - 1];
+        f = dt * e * e;
+        gr = 2.0 * dt * e;
+      } else if (q == nx) {
+        const double up = (k == 1) ? d.p_uprev[i] : yi[offu(mc, k - 1)];
+        const double du = yi[lv] - up;
+        f = mc.wdu * du * du;
+        gr = 2.0 * mc.wdu * du;
+        if (k < T) gr -= 2.0 * mc.wdu * (yi[offu(mc, k + 1)] - yi[lv]);
+      }
+    } else if (mc.model == MODEL_PLATE) {
+      const double hh = 1.0 / mc.g;
+      if (q < nx) {
+        const double e = yi[lv] - d.p_sp[(size_t)i * d.sp_stride + q];
+        f = dt * hh * hh * e * e;
+        gr = 2.0 * dt * hh * hh * e;
+      } else {
+        f = mc.rho_u * dt * yi[lv] * yi[lv];
+        gr = 2.0 * mc.rho_u * dt * yi[lv];
+      }
+    } else {
+      if (q == 0) {
+        const double e = yi[lv] - d.p_sp[(size_t)i * d.sp_stride + k - 1];
+        f = dt * e * e;
+        gr = 2.0 * dt * e;
+      }
+    }
+  }
+  if (fshare) *fshare = f;
+  if (grad) *grad = gr;
+}
+
+// Hessian slots owned by variable v of stage k >= 1.  lam = w+ - w- of the
+// rows of the backward-Euler step that ends at stage k (rows of stage k-1).
+__device__ void eval_var_hess(const Dev& d, int v) {
+  const ModelConst& mc = d.mc;
+  const int i = d.var_inst[v];
+  const int vo = d.inst_voff[i], ro = d.inst_roff[i], T = d.inst_T[i];
+  const int lv = v - vo;
+  const int nx = mc.nx, nu = mc.nu;
+  if (lv < nx) return;
+  const int k = (lv - nx) / (nx + nu) + 1;
+  const int q = (lv - nx) % (nx + nu);
+  double* W = d.Wv + d.inst_woff[i] + (size_t)(k - 1) * mc.WS;
+  const double* yi = d.y + vo;
+  const int rbase = ro + nx * k;  // rows of step k-1 -> k
+  const double dt = mc.dt;
+  if (mc.model == MODEL_PLATE) {
+    const double hh = 1.0 / mc.g;
+    W[q] = (q < nx) ? 2.0 * dt * hh * hh : 2.0 * mc.rho_u * dt;
+    return;
+  }
+  if (mc.model == MODEL_TOY) {
+    const double lam = d.wp[rbase] - d.wm[rbase];
+    if (q == 0) W[0] = 2.0 * dt + lam * 6.0 * dt * yi[lv];
+    else W[1] = lam * 4.0 * dt * sin(yi[lv]);
+    return;
+  }
+  // distillation
+  const int N = nx;
+  const double a = mc.alpha, D = mc.D;
+  const double* x = yi + offx(mc, k);
+  const double u = yi[offu(mc, k)];
+  const double V = (u + 1.0) * D;
+  auto coef = [&](int tray) { const int r = rbase + tray - 1; return -dt * (d.wp[r] - d.wm[r]); };
+  auto hold = [&](int tray) { return tray == 1 ? mc.Ac : (tray == N ? mc.Ar : mc.At); };
+  if (q < N) {
+    const int j = q + 1;  // tray
+    const double xj = x[j - 1];
+    const double y1 = vle_d1(a, xj), y2 = vle_d2(a, xj);
+    double wdiag = (j == 1) ? 2.0 * dt : 0.0;
+    if (j >= 2) wdiag += coef(j) * (-V * y2) / hold(j);           // own row: -V y''(x_j)
+    if (j >= 2) wdiag += coef(j - 1) * (V * y2) / hold(j - 1);    // row above: +V y''(x_{i+1})
+    double wux = 0.0;
+    if (j >= 2) wux += coef(j - 1) * (D * y1) / hold(j - 1);      // row j-1: D y'(x_{i+1})
+    if (j == 1) wux += coef(1) * (-D) / mc.Ac;
+    else if (j < N) wux += coef(j) * (-D * (1.0 + y1)) / mc.At;
+    else wux += coef(N) * (-D * y1) / mc.Ar;
+    if (j + 1 <= N) wux += coef(j + 1) * D / hold(j + 1);         // row j+1: D from x_{i-1}
+    W[q] = wdiag;
+    W[N + q] = wux;
+  } else {
+    W[2 * N] = 2.0 * mc.wdu * (k < T ? 2.0 : 1.0);
+    W[2 * N + 1] = (k >= 2) ? -2.0 * mc.wdu : 0.0;
+  }
+}
+
+__global__ void k_eval_vars(Dev d, int use_trial) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.n) return;
+  const Ctl& c = d.ctl[d.var_inst[v]];
+  if (use_trial) {
+    if (!c.ls_active) return;
+    eval_var_obj(d, d.yt, v, &d.fvart[v], nullptr);
+  } else {
+    if (c.status != ST_RUNNING) return;
+    eval_var_obj(d, d.y, v, &d.fvar[v], &d.grad[v]);
+    eval_var_hess(d, v);
+  }
+}
+
+// --------------------------------------------------------- parameter update
+
+// Writes new parameters into the device parameter buffers (Sec. 3.3,
+// set_parameter_value): nothing structural changes.  src holds, per
+// instance in [i0, i1), nx initial-state values, sp_len setpoint values and
+// one u_prev (each part optional, flagged by the have_* arguments).
+__global__ void k_set_params(Dev d, int i0, int i1, const double* x0, const double* sp,
+                             const double* up, int sp_len) {
+  const int nx = d.mc.nx;
+  const int cnt = i1 - i0;
+  const size_t total = (size_t)cnt * (nx + sp_len + 1);
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int li = (int)(t / (nx + sp_len + 1));
+    const int q = (int)(t % (nx + sp_len + 1));
+    const int i = i0 + li;
+    if (q < nx) {
+      if (x0) d.p_x0[(size_t)i * nx + q] = x0[(size_t)li * nx + q];
+    } else if (q < nx + sp_len) {
+      if (sp) d.p_sp[(size_t)i * d.sp_stride + (q - nx)] = sp[(size_t)li * sp_len + (q - nx)];
+    } else {
+      if (up) d.p_uprev[i] = up[li];
+    }
+  }
+}
+
+// Cold-start trajectory from the parameters: x_k = p_x0 for all k, controls
+// at u_prev (distillation) or the midpoint of their bounds, then pushed into
+// the bounds (W&B Sec. 3.6).  Warm start only pushes the previous point.
+__global__ void k_init_vars(Dev d, int warm, double push) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.n) return;
+  const ModelConst& mc = d.mc;
+  const int i = d.var_inst[v];
+  const int lv = v - d.inst_voff[i];
+  const int nx = mc.nx, nu = mc.nu;
+  const double lo = d.yL[v], hi = d.yU[v];
+  double y = d.y[v];
+  if (!warm) {
+    if (lv < nx) y = d.p_x0[(size_t)i * nx + lv];
+    else {
+      const int q = (lv - nx) % (nx + nu);
+      if (q < nx) y = d.p_x0[(size_t)i * nx + q];
+      else if (mc.model == MODEL_DISTILL) y = d.p_uprev[i];
+      else y = (isfinite(lo) && isfinite(hi)) ? 0.5 * (lo + hi) : 0.0;
+    }
+  }
+  double pl = isfinite(lo) ? push * fmax(1.0, fabs(lo)) : 0.0;
+  double pu = isfinite(hi) ? push * fmax(1.0, fabs(hi)) : 0.0;
+  if (isfinite(lo) && isfinite(hi)) { pl = fmin(pl, push * (hi - lo)); pu = fmin(pu, push * (hi - lo)); }
+  if (isfinite(lo) && y < lo + pl) y = lo + pl;
+  if (isfinite(hi) && y > hi - pu) y = hi - pu;
+  d.y[v] = y;
+  if (!warm) {
+    d.zL[v] = isfinite(lo) ? 1.0 : 0.0;
+    d.zU[v] = isfinite(hi) ? 1.0 : 0.0;
+  } else {
+    d.zL[v] = isfinite(lo) ? fmax(d.zL[v], push) : 0.0;
+    d.zU[v] = isfinite(hi) ? fmax(d.zU[v], push) : 0.0;
+  }
+}
+
+__global__ void k_init_rows(Dev d, int warm, double push) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.m) return;
+  const double gam = d.mc.gamma;
+  if (!warm) {
+    d.sp[r] = fmax(gam - d.h[r], push);
+    d.sm[r] = fmax(gam + d.h[r], push);
+    d.wp[r] = d.wm[r] = 1.0;
+    d.bp[r] = d.bm[r] = 1.0;
+  } else {
+    d.sp[r] = fmax(d.sp[r], push);
+    d.sm[r] = fmax(d.sm[r], push);
+    d.bp[r] = fmax(d.bp[r], push);
+    d.bm[r] = fmax(d.bm[r], push);
+  }
+}
+
+}  // namespace nmpc

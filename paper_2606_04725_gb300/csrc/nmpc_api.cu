@@ -1,0 +1,639 @@
+// C ABI of the NMPC library: handle management, workspace layout, parameter
+// updates and the interior-point driver (Algorithm 2 of arXiv 2606.04725).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nmpc.h"
+#include "kernels.h"
+#include "structure.h"
+
+using namespace nmpc;
+
+namespace {
+
+// Bump allocator over the caller's workspace (first pass only measures).
+struct Carver {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += std::max<size_t>(count, 1) * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+struct nmpc_handle {
+  Analysis A;
+  nmpc_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  size_t ws_bytes = 0;
+  bool bound = false, have_solution = false;
+  Dev d{};
+  SnDev s{};
+  // device-only arrays not in Dev/SnDev
+  int* d_tgt_inst = nullptr;
+  double* d_Drow = nullptr;
+  long long* d_inst_Lbeg = nullptr;
+  long long* d_inst_Lend = nullptr;
+  int* d_flags = nullptr;
+  double* d_stage = nullptr;  // staging of host parameter arrays
+  int* h_flags = nullptr;     // pinned
+  std::vector<int> lvl_ptr;
+  std::vector<int> lvl_smem_factor, lvl_smem_solve;  // bytes per level
+  int smem_cap_doubles = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<Ctl> h_ctl;
+  Ctl* d_ctl_save = nullptr;
+  long long launches = 0;
+};
+
+namespace {
+
+constexpr int SMEM_FACTOR_CAP_BYTES = 200 * 1024;
+
+nmpc_status fail(nmpc_handle* h, nmpc_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+#define CUDA_TRY(h, call)                                                                    \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(h, NMPC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Lay out (or measure) every device array inside the workspace.
+void carve(nmpc_handle* h, Carver& cv) {
+  Analysis& A = h->A;
+  Dev& d = h->d;
+  SnDev& s = h->s;
+  const int ni = A.n_inst, n = A.n, m = A.m, WH = A.mc.WH;
+  const size_t nch = A.chunks.size(), ns = A.sn_first.size();
+  d.inst_T = cv.take<int>(ni); d.inst_voff = cv.take<int>(ni); d.inst_roff = cv.take<int>(ni);
+  d.inst_woff = cv.take<int>(ni); d.inst_n = cv.take<int>(ni); d.inst_m = cv.take<int>(ni);
+  d.inst_nz = cv.take<int>(ni);
+  d.var_inst = cv.take<int>(n); d.row_inst = cv.take<int>(m);
+  d.yL = cv.take<double>(n); d.yU = cv.take<double>(n);
+  d.p_x0 = cv.take<double>((size_t)ni * A.mc.nx); d.p_sp = cv.take<double>((size_t)ni * A.sp_stride);
+  d.p_uprev = cv.take<double>(ni);
+  d.y = cv.take<double>(n); d.zL = cv.take<double>(n); d.zU = cv.take<double>(n);
+  d.sp = cv.take<double>(m); d.sm = cv.take<double>(m); d.wp = cv.take<double>(m); d.wm = cv.take<double>(m);
+  d.bp = cv.take<double>(m); d.bm = cv.take<double>(m);
+  d.grad = cv.take<double>(n); d.h = cv.take<double>(m); d.Hv = cv.take<double>((size_t)m * WH);
+  d.Wv = cv.take<double>(A.nW); d.fvar = cv.take<double>(n);
+  d.Hcol = cv.take<int>((size_t)m * WH);
+  d.Hcsc_ptr = cv.take<int>(n + 1); d.Hcsc_slot = cv.take<int>(A.Hcsc_slot.size());
+  d.dy = cv.take<double>(n); d.dzL = cv.take<double>(n); d.dzU = cv.take<double>(n);
+  d.dsp = cv.take<double>(m); d.dsm = cv.take<double>(m); d.dwp = cv.take<double>(m); d.dwm = cv.take<double>(m);
+  d.dbp = cv.take<double>(m); d.dbm = cv.take<double>(m); d.rowv = cv.take<double>(m);
+  d.yt = cv.take<double>(n); d.spt = cv.take<double>(m); d.smt = cv.take<double>(m); d.ht = cv.take<double>(m);
+  d.fvart = cv.take<double>(n);
+  d.perm = cv.take<int>(n); d.iperm = cv.take<int>(n); d.b = cv.take<double>(n);
+  d.ctl = cv.take<Ctl>(ni);
+  d.filt_th = cv.take<double>((size_t)ni * FILTER_CAP); d.filt_ph = cv.take<double>((size_t)ni * FILTER_CAP);
+  d.chunks = cv.take<Chunk>(nch); d.inst_chunk_ptr = cv.take<int>(ni + 1); d.inst_chunk_list = cv.take<int>(nch);
+  d.red_eval = cv.take<RedEval>(nch); d.red_dir = cv.take<RedDir>(nch); d.red_trial = cv.take<RedTrial>(nch);
+  d.tgt_L = cv.take<long long>(A.tgt_L.size()); d.tgt_diag = cv.take<int>(A.tgt_diag.size());
+  d.tw_ptr = cv.take<int>(A.tw_ptr.size()); d.tw_idx = cv.take<int>(A.tw_idx.size());
+  d.th_ptr = cv.take<int>(A.th_ptr.size()); d.th_a = cv.take<int>(A.th_a.size()); d.th_b = cv.take<int>(A.th_b.size());
+  d.Lval = cv.take<double>(A.nnzL);
+  d.sn_inst = cv.take<int>(ns);
+  h->d_tgt_inst = cv.take<int>(A.tgt_L.size());
+  h->d_Drow = cv.take<double>(m);
+  h->d_inst_Lbeg = cv.take<long long>(ni); h->d_inst_Lend = cv.take<long long>(ni);
+  h->d_flags = cv.take<int>(4);
+  h->d_stage = cv.take<double>((size_t)ni * (A.mc.nx + A.sp_stride + 1));
+  h->d_ctl_save = cv.take<Ctl>(ni);
+  s.sn_first = cv.take<int>(ns); s.sn_ncol = cv.take<int>(ns); s.sn_nrow = cv.take<int>(ns);
+  s.sn_Lptr = cv.take<long long>(ns + 1); s.sn_Uptr = cv.take<long long>(ns + 1);
+  s.sn_rowptr = cv.take<long long>(ns + 1); s.sn_rows = cv.take<int>(A.sn_rows.size());
+  s.sn_child_ptr = cv.take<int>(ns + 1); s.sn_child = cv.take<int>(A.sn_child.size());
+  s.sn_relptr = cv.take<long long>(ns + 1); s.sn_rel = cv.take<int>(A.sn_rel.size());
+  s.level_ptr = cv.take<int>(A.level_ptr.size()); s.level_sn = cv.take<int>(ns);
+  s.sn_uvptr = cv.take<long long>(ns + 1);
+  s.U = cv.take<double>(A.nU);
+  s.uv = cv.take<double>(A.nuv);
+  s.L = d.Lval;
+  s.sn_inst = d.sn_inst;
+  s.ns = (int)ns;
+  d.mc = A.mc; d.n_inst = ni; d.n = n; d.m = m; d.nW = A.nW; d.sp_stride = A.sp_stride;
+  d.n_chunks = (int)nch; d.n_tgt = (int)A.tgt_L.size(); d.nnzL = A.nnzL;
+}
+
+template <class T>
+cudaError_t up(const T* dst, const std::vector<T>& src, cudaStream_t st) {
+  if (src.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(const_cast<T*>(dst), src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+nmpc_status read_flags(nmpc_handle* h) {
+  k_summary<<<1, 256, 0, h->stream>>>(h->d, h->d_flags);
+  ++h->launches;
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_flags, h->d_flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return NMPC_OK;
+}
+
+nmpc_status launch_factor(nmpc_handle* h) {
+  const int nl = (int)h->lvl_ptr.size() - 1;
+  for (int l = 0; l < nl; ++l) {
+    const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
+    if (!cnt) continue;
+    k_factor_level<<<cnt, TPB, h->lvl_smem_factor[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+                                                                   h->smem_cap_doubles);
+  }
+  return NMPC_OK;
+}
+
+nmpc_status launch_solve(nmpc_handle* h) {
+  const int nl = (int)h->lvl_ptr.size() - 1;
+  for (int l = 0; l < nl; ++l) {
+    const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
+    if (cnt) k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l]);
+    ++h->launches;
+  }
+  for (int l = nl - 1; l >= 0; --l) {
+    const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
+    if (cnt) k_bwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l]);
+    ++h->launches;
+  }
+  return NMPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nmpc_problem_defaults(int model, nmpc_problem* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->model = model;
+  p->n_instances = 1;
+  p->dt = 1.0;
+  p->alpha = 1.6; p->D = 0.2; p->F = 0.4; p->xF = 0.5; p->Ac = 1.0; p->At = 1.0; p->Ar = 1.0; p->wdu = 0.01;
+  p->kappa = 0.01; p->cq = 0.01; p->rho_u = 1e-3;
+  if (model == NMPC_MODEL_DISTILLATION) { p->N = 12; p->Nf = 5; p->xlo = 0; p->xhi = 1; p->ulo = 1; p->uhi = 5; }
+  else if (model == NMPC_MODEL_PLATE) { p->g = 64; p->S = 8; p->xlo = -INFINITY; p->xhi = 1.2; p->ulo = 0; p->uhi = 1; }
+  else { p->xlo = 0; p->xhi = INFINITY; p->ulo = 1; p->uhi = 3; }
+}
+
+void nmpc_options_defaults(nmpc_options* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-8; o->gamma = 1e-9; o->mu0_cold = 0.1; o->mu0_warm = 1e-8;
+  o->push_cold = 1e-2; o->push_warm = 1e-9; o->max_iter = 200; o->ordering = NMPC_ORDER_AUTO;
+  o->nd_leaf = 1; o->use_graph = 1; o->spin_limit = 10000000LL;
+}
+
+nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void* cuda_stream, nmpc_handle** out) {
+  if (!prob || !out || prob->n_instances < 1 || !prob->horizons) return NMPC_ERR_INVALID;
+  *out = nullptr;
+  nmpc_handle* h = new (std::nothrow) nmpc_handle();
+  if (!h) return NMPC_ERR_INVALID;
+  if (opts) h->opt = *opts;
+  else nmpc_options_defaults(&h->opt);
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  ProblemSpec sp;
+  sp.model = prob->model;
+  sp.T.assign(prob->horizons, prob->horizons + prob->n_instances);
+  sp.N = prob->N; sp.Nf = prob->Nf; sp.g = prob->g; sp.S = prob->S; sp.dt = prob->dt;
+  sp.alpha = prob->alpha; sp.D = prob->D; sp.F = prob->F; sp.xF = prob->xF;
+  sp.Ac = prob->Ac; sp.At = prob->At; sp.Ar = prob->Ar; sp.wdu = prob->wdu;
+  sp.kappa = prob->kappa; sp.cq = prob->cq; sp.rho_u = prob->rho_u;
+  sp.xlo = prob->xlo; sp.xhi = prob->xhi; sp.ulo = prob->ulo; sp.uhi = prob->uhi;
+  sp.gamma = h->opt.gamma; sp.tol = h->opt.tol;
+  sp.ordering = h->opt.ordering; sp.nd_leaf = h->opt.nd_leaf;
+  if (!(prob->dt > 0) || h->opt.max_iter < 1 || !(h->opt.tol > 0) || !(h->opt.gamma > 0)) {
+    delete h;
+    return NMPC_ERR_INVALID;
+  }
+  std::string e = analyze(sp, h->A);
+  if (!e.empty()) {
+    std::fprintf(stderr, "nmpc_build: %s\n", e.c_str());
+    delete h;
+    return NMPC_ERR_INVALID;
+  }
+  Carver cv;
+  carve(h, cv);
+  h->ws_bytes = (cv.off + 255) & ~size_t(255);
+  // per-level launch shapes
+  const Analysis& A = h->A;
+  h->lvl_ptr = A.level_ptr;
+  const int nl = (int)A.level_ptr.size() - 1;
+  h->smem_cap_doubles = SMEM_FACTOR_CAP_BYTES / 8;
+  h->lvl_smem_factor.assign(nl, 8);
+  h->lvl_smem_solve.assign(nl, 8);
+  for (int l = 0; l < nl; ++l)
+    for (int q = A.level_ptr[l]; q < A.level_ptr[l + 1]; ++q) {
+      const int sn = A.level_sn[q];
+      const long long mm = A.sn_nrow[sn], cc = A.sn_ncol[sn];
+      const long long need = mm * cc + (mm - cc) * (mm - cc);
+      if (need <= h->smem_cap_doubles) h->lvl_smem_factor[l] = std::max<int>(h->lvl_smem_factor[l], (int)(need * 8));
+      h->lvl_smem_solve[l] = std::max<int>(h->lvl_smem_solve[l], (int)((mm + cc) * 8));
+    }
+  *out = h;
+  return NMPC_OK;
+}
+
+nmpc_status nmpc_workspace_bytes(const nmpc_handle* h, size_t* bytes) {
+  if (!h || !bytes) return NMPC_ERR_INVALID;
+  *bytes = h->ws_bytes;
+  return NMPC_OK;
+}
+
+nmpc_status nmpc_bind(nmpc_handle* h, void* ws, size_t bytes) {
+  if (!h) return NMPC_ERR_INVALID;
+  if (h->bound) return fail(h, NMPC_ERR_INVALID, "workspace already bound");
+  if (!ws || bytes < h->ws_bytes) return fail(h, NMPC_ERR_WORKSPACE, "workspace missing or smaller than nmpc_workspace_bytes");
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(h, NMPC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  Carver cv;
+  cv.base = static_cast<char*>(ws);
+  carve(h, cv);
+  const Analysis& A = h->A;
+  Dev& d = h->d;
+  SnDev& s = h->s;
+  cudaStream_t st = h->stream;
+  std::vector<Chunk> ch = A.chunks;
+  CUDA_TRY(h, cudaMemsetAsync(ws, 0, h->ws_bytes, st));
+  CUDA_TRY(h, up(d.inst_T, A.inst_T, st)); CUDA_TRY(h, up(d.inst_voff, A.inst_voff, st));
+  CUDA_TRY(h, up(d.inst_roff, A.inst_roff, st)); CUDA_TRY(h, up(d.inst_woff, A.inst_woff, st));
+  CUDA_TRY(h, up(d.inst_n, A.inst_n, st)); CUDA_TRY(h, up(d.inst_m, A.inst_m, st));
+  CUDA_TRY(h, up(d.inst_nz, A.inst_nz, st));
+  CUDA_TRY(h, up(d.var_inst, A.var_inst, st)); CUDA_TRY(h, up(d.row_inst, A.row_inst, st));
+  CUDA_TRY(h, up(d.yL, A.yL, st)); CUDA_TRY(h, up(d.yU, A.yU, st));
+  CUDA_TRY(h, up(d.Hcol, A.Hcol, st)); CUDA_TRY(h, up(d.Hcsc_ptr, A.Hcsc_ptr, st));
+  CUDA_TRY(h, up(d.Hcsc_slot, A.Hcsc_slot, st));
+  CUDA_TRY(h, up(d.perm, A.perm, st)); CUDA_TRY(h, up(d.iperm, A.iperm, st));
+  CUDA_TRY(h, up(d.chunks, ch, st)); CUDA_TRY(h, up(d.inst_chunk_ptr, A.inst_chunk_ptr, st));
+  CUDA_TRY(h, up(d.inst_chunk_list, A.inst_chunk_list, st));
+  CUDA_TRY(h, up(d.tgt_L, A.tgt_L, st)); CUDA_TRY(h, up(d.tgt_diag, A.tgt_diag, st));
+  CUDA_TRY(h, up(d.tw_ptr, A.tw_ptr, st)); CUDA_TRY(h, up(d.tw_idx, A.tw_idx, st));
+  CUDA_TRY(h, up(d.th_ptr, A.th_ptr, st)); CUDA_TRY(h, up(d.th_a, A.th_a, st)); CUDA_TRY(h, up(d.th_b, A.th_b, st));
+  CUDA_TRY(h, up(d.sn_inst, A.sn_inst, st));
+  // instance of each assembly target and L range of each instance
+  std::vector<int> tinst(A.tgt_L.size());
+  std::vector<long long> lb(A.n_inst, 0), le(A.n_inst, 0);
+  {
+    std::vector<int> first_sn(A.n_inst, -1), last_sn(A.n_inst, -1);
+    for (int q = 0; q < (int)A.sn_first.size(); ++q) {
+      const int i = A.sn_inst[q];
+      if (first_sn[i] < 0) first_sn[i] = q;
+      last_sn[i] = q;
+    }
+    for (int i = 0; i < A.n_inst; ++i) { lb[i] = A.sn_Lptr[first_sn[i]]; le[i] = A.sn_Lptr[last_sn[i] + 1]; }
+    size_t i = 0;
+    for (size_t t = 0; t < A.tgt_L.size(); ++t) {
+      while (A.tgt_L[t] >= le[i]) ++i;
+      tinst[t] = (int)i;
+    }
+  }
+  CUDA_TRY(h, up(h->d_tgt_inst, tinst, st));
+  CUDA_TRY(h, up(h->d_inst_Lbeg, lb, st)); CUDA_TRY(h, up(h->d_inst_Lend, le, st));
+  CUDA_TRY(h, up(s.sn_first, A.sn_first, st)); CUDA_TRY(h, up(s.sn_ncol, A.sn_ncol, st));
+  CUDA_TRY(h, up(s.sn_nrow, A.sn_nrow, st)); CUDA_TRY(h, up(s.sn_Lptr, A.sn_Lptr, st));
+  CUDA_TRY(h, up(s.sn_Uptr, A.sn_Uptr, st)); CUDA_TRY(h, up(s.sn_rowptr, A.sn_rowptr, st));
+  CUDA_TRY(h, up(s.sn_rows, A.sn_rows, st)); CUDA_TRY(h, up(s.sn_child_ptr, A.sn_child_ptr, st));
+  CUDA_TRY(h, up(s.sn_child, A.sn_child, st)); CUDA_TRY(h, up(s.sn_relptr, A.sn_relptr, st));
+  CUDA_TRY(h, up(s.sn_rel, A.sn_rel, st)); CUDA_TRY(h, up(s.level_ptr, A.level_ptr, st));
+  CUDA_TRY(h, up(s.level_sn, A.level_sn, st)); CUDA_TRY(h, up(s.sn_uvptr, A.sn_uvptr, st));
+  CUDA_TRY(h, cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
+  int maxs = *std::max_element(h->lvl_smem_solve.begin(), h->lvl_smem_solve.end());
+  if (maxs > 48 * 1024) {
+    CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+    CUDA_TRY(h, cudaFuncSetAttribute(k_bwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
+  }
+  CUDA_TRY(h, cudaMallocHost(&h->h_flags, 4 * sizeof(int)));
+  CUDA_TRY(h, cudaEventCreate(&h->ev0));
+  CUDA_TRY(h, cudaEventCreate(&h->ev1));
+  CUDA_TRY(h, cudaStreamSynchronize(st));
+  h->d.max_iter = h->opt.max_iter;
+  h->h_ctl.resize(A.n_inst);
+  h->bound = true;
+  return NMPC_OK;
+}
+
+nmpc_status nmpc_set_params(nmpc_handle* h, int instance, const double* x0, const double* setpoint,
+                            const double* u_prev, int on_device) {
+  if (!h || !h->bound) return fail(h, NMPC_ERR_INVALID, "handle not bound");
+  const Analysis& A = h->A;
+  if (instance < -1 || instance >= A.n_inst) return fail(h, NMPC_ERR_INVALID, "instance out of range");
+  const int i0 = instance < 0 ? 0 : instance, i1 = instance < 0 ? A.n_inst : instance + 1;
+  const int cnt = i1 - i0, nx = A.mc.nx;
+  // setpoint values per instance as the caller packs them
+  int sp_len = A.sp_stride;
+  if (A.mc.model != MODEL_PLATE) {
+    for (int i = i0; i < i1; ++i)
+      if (A.inst_T[i] != A.inst_T[i0]) return fail(h, NMPC_ERR_INVALID, "set_params for several instances needs equal horizons; set them one by one");
+    sp_len = A.inst_T[i0];
+  }
+  const double *sx = x0, *ss = setpoint, *su = u_prev;
+  if (!on_device) {
+    // host arrays go through the workspace's staging area (sized for all instances)
+    double* p = h->d_stage;
+    if (x0) { CUDA_TRY(h, cudaMemcpyAsync(p, x0, (size_t)cnt * nx * 8, cudaMemcpyHostToDevice, h->stream)); sx = p; }
+    p += (size_t)cnt * nx;
+    if (setpoint) { CUDA_TRY(h, cudaMemcpyAsync(p, setpoint, (size_t)cnt * sp_len * 8, cudaMemcpyHostToDevice, h->stream)); ss = p; }
+    p += (size_t)cnt * sp_len;
+    if (u_prev) { CUDA_TRY(h, cudaMemcpyAsync(p, u_prev, (size_t)cnt * 8, cudaMemcpyHostToDevice, h->stream)); su = p; }
+  }
+  const long long total = (long long)cnt * (nx + sp_len + 1);
+  k_set_params<<<std::min<long long>(blocks_for(total), 1024), TPB, 0, h->stream>>>(h->d, i0, i1, sx, ss, su, sp_len);
+  ++h->launches;
+  CUDA_TRY(h, cudaGetLastError());
+  if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return NMPC_OK;
+}
+
+nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
+  if (!h || !h->bound) return fail(h, NMPC_ERR_INVALID, "handle not bound");
+  if (warm && !h->have_solution) warm = 0;
+  Dev& d = h->d;
+  const Analysis& A = h->A;
+  cudaStream_t st = h->stream;
+  const int ni = A.n_inst, n = A.n, m = A.m;
+  const double mu0 = warm ? h->opt.mu0_warm : h->opt.mu0_cold;
+  const double push = warm ? h->opt.push_warm : h->opt.push_cold;
+  CUDA_TRY(h, cudaEventRecord(h->ev0, st));
+  k_ctl_init<<<blocks_for(ni), TPB, 0, st>>>(d, mu0);
+  ++h->launches;
+  k_init_vars<<<blocks_for(n), TPB, 0, st>>>(d, warm, push);
+  ++h->launches;
+  k_eval_rows<<<blocks_for(m), TPB, 0, st>>>(d, 0, 0);
+  ++h->launches;
+  k_init_rows<<<blocks_for(m), TPB, 0, st>>>(d, warm, push);
+  ++h->launches;
+  CUDA_TRY(h, cudaGetLastError());
+  const dim3 zgrid(std::max(1u, std::min(1024u, blocks_for(A.nnzL / std::max(1, ni) + 1))), ni);
+  for (int it = 0; it <= h->opt.max_iter + 1; ++it) {
+    k_eval_rows<<<blocks_for(m), TPB, 0, st>>>(d, 0, 1);
+    ++h->launches;
+    k_eval_vars<<<blocks_for(n), TPB, 0, st>>>(d, 0);
+    ++h->launches;
+    k_red_eval<<<d.n_chunks, TPB, 0, st>>>(d);
+    ++h->launches;
+    k_ctl_pre<<<blocks_for(ni), TPB, 0, st>>>(d, h->opt.max_iter);
+    ++h->launches;
+    nmpc_status rs = read_flags(h);
+    if (rs != NMPC_OK) return rs;
+    if (!h->h_flags[0]) break;
+    for (;;) {
+      k_zero_L<<<zgrid, TPB, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend);
+      ++h->launches;
+      k_rows_pre<<<blocks_for(m), TPB, 0, st>>>(d, h->d_Drow);
+      ++h->launches;
+      k_assemble<<<blocks_for(d.n_tgt), TPB, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
+      ++h->launches;
+      launch_factor(h);
+      k_ctl_factor<<<blocks_for(ni), TPB, 0, st>>>(d);
+      ++h->launches;
+      CUDA_TRY(h, cudaGetLastError());
+      rs = read_flags(h);
+      if (rs != NMPC_OK) return rs;
+      if (!h->h_flags[1]) break;
+    }
+    k_rhs<<<blocks_for(n), TPB, 0, st>>>(d);
+    ++h->launches;
+    launch_solve(h);
+    k_recover_vars<<<blocks_for(n), TPB, 0, st>>>(d);
+    ++h->launches;
+    k_recover_rows<<<blocks_for(m), TPB, 0, st>>>(d);
+    ++h->launches;
+    k_red_dir<<<d.n_chunks, TPB, 0, st>>>(d);
+    ++h->launches;
+    k_ctl_dir<<<blocks_for(ni), TPB, 0, st>>>(d);
+    ++h->launches;
+    CUDA_TRY(h, cudaGetLastError());
+    rs = read_flags(h);
+    if (rs != NMPC_OK) return rs;
+    while (h->h_flags[2]) {
+      k_trial_point<<<blocks_for((long long)n + m), TPB, 0, st>>>(d);
+      ++h->launches;
+      k_eval_rows<<<blocks_for(m), TPB, 0, st>>>(d, 1, 0);
+      ++h->launches;
+      k_eval_vars<<<blocks_for(n), TPB, 0, st>>>(d, 1);
+      ++h->launches;
+      k_red_trial<<<d.n_chunks, TPB, 0, st>>>(d);
+      ++h->launches;
+      k_ctl_ls<<<blocks_for(ni), TPB, 0, st>>>(d);
+      ++h->launches;
+      CUDA_TRY(h, cudaGetLastError());
+      rs = read_flags(h);
+      if (rs != NMPC_OK) return rs;
+    }
+    k_update_vars<<<blocks_for(n), TPB, 0, st>>>(d);
+    ++h->launches;
+    k_update_rows<<<blocks_for(m), TPB, 0, st>>>(d);
+    ++h->launches;
+    k_ctl_post<<<blocks_for(ni), TPB, 0, st>>>(d);
+    ++h->launches;
+  }
+  CUDA_TRY(h, cudaEventRecord(h->ev1, st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl.data(), d.ctl, ni * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(h, cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->have_solution = true;
+  nmpc_status ret = NMPC_OK;
+  for (int i = 0; i < ni; ++i) {
+    const Ctl& c = h->h_ctl[i];
+    const int stt = (c.status == ST_CONVERGED) ? NMPC_OK : (c.status == ST_RUNNING ? NMPC_MAX_ITER : c.status);
+    if (stt != NMPC_OK && ret == NMPC_OK) ret = (nmpc_status)stt;
+    if (info) {
+      nmpc_info& o = info[i];
+      o.status = stt; o.iters = c.iter; o.inertia_retries = c.inertia_retries; o.ls_trials = c.ls_trials;
+      o.mu_final = c.mu; o.kkt_scaled = c.E0; o.kkt_unscaled = c.E0u; o.objective = c.f; o.ms_total = ms;
+    }
+  }
+  return ret;
+}
+
+nmpc_status nmpc_get_solution(nmpc_handle* h, int instance, double* y, double* duals, int on_device) {
+  if (!h || !h->bound) return fail(h, NMPC_ERR_INVALID, "handle not bound");
+  const Analysis& A = h->A;
+  if (instance < 0 || instance >= A.n_inst) return fail(h, NMPC_ERR_INVALID, "instance out of range");
+  if (!h->have_solution) return fail(h, NMPC_NOT_SOLVED, "no solution yet");
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const int vo = A.inst_voff[instance], ro = A.inst_roff[instance], n = A.inst_n[instance], m = A.inst_m[instance];
+  const Dev& d = h->d;
+  if (y) CUDA_TRY(h, cudaMemcpyAsync(y, d.y + vo, n * 8, k, h->stream));
+  if (duals) {
+    double* p = duals;
+    const double* src[8] = {d.zL + vo, d.zU + vo, d.sp + ro, d.sm + ro, d.wp + ro, d.wm + ro, d.bp + ro, d.bm + ro};
+    const int len[8] = {n, n, m, m, m, m, m, m};
+    for (int q = 0; q < 8; ++q) { CUDA_TRY(h, cudaMemcpyAsync(p, src[q], (size_t)len[q] * 8, k, h->stream)); p += len[q]; }
+  }
+  if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return NMPC_OK;
+}
+
+nmpc_status nmpc_set_start(nmpc_handle* h, int instance, const double* y, const double* duals, int on_device) {
+  if (!h || !h->bound) return fail(h, NMPC_ERR_INVALID, "handle not bound");
+  const Analysis& A = h->A;
+  if (instance < 0 || instance >= A.n_inst) return fail(h, NMPC_ERR_INVALID, "instance out of range");
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int vo = A.inst_voff[instance], ro = A.inst_roff[instance], n = A.inst_n[instance], m = A.inst_m[instance];
+  const Dev& d = h->d;
+  if (y) CUDA_TRY(h, cudaMemcpyAsync(d.y + vo, y, n * 8, k, h->stream));
+  if (duals) {
+    const double* p = duals;
+    double* dst[8] = {d.zL + vo, d.zU + vo, d.sp + ro, d.sm + ro, d.wp + ro, d.wm + ro, d.bp + ro, d.bm + ro};
+    const int len[8] = {n, n, m, m, m, m, m, m};
+    for (int q = 0; q < 8; ++q) { CUDA_TRY(h, cudaMemcpyAsync(dst[q], p, (size_t)len[q] * 8, k, h->stream)); p += len[q]; }
+  }
+  if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->have_solution = true;
+  return NMPC_OK;
+}
+
+nmpc_status nmpc_sensitivity(nmpc_handle* h, int, const double*, double*, double*, int) {
+  return fail(h, NMPC_ERR_INVALID, "adjoint sensitivity is not available in this build");
+}
+
+__global__ void k_ctl_force(Ctl* ctl, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ctl[i].status = ST_RUNNING;
+  ctl[i].need_factor = 1;
+  ctl[i].factor_fail = 0;
+}
+
+nmpc_status nmpc_time_phases(nmpc_handle* h, int reps, nmpc_phase_times* out) {
+  if (!h || !h->bound || !out || reps < 1) return fail(h, NMPC_ERR_INVALID, "bad arguments");
+  if (!h->have_solution) return fail(h, NMPC_NOT_SOLVED, "no iterate to time at");
+  const Analysis& A = h->A;
+  Dev& d = h->d;
+  cudaStream_t st = h->stream;
+  const int ni = A.n_inst, n = A.n, m = A.m;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_ctl_save, d.ctl, ni * sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
+  k_ctl_force<<<blocks_for(ni), TPB, 0, st>>>(d.ctl, ni);
+  const dim3 zgrid(std::max(1u, std::min(1024u, blocks_for(A.nnzL / std::max(1, ni) + 1))), ni);
+  cudaEvent_t e[5];
+  for (auto& x : e) CUDA_TRY(h, cudaEventCreate(&x));
+  double acc[4] = {0, 0, 0, 0};
+  for (int r = 0; r < reps + 1; ++r) {
+    CUDA_TRY(h, cudaEventRecord(e[0], st));
+    k_eval_rows<<<blocks_for(m), TPB, 0, st>>>(d, 0, 1);
+    k_eval_vars<<<blocks_for(n), TPB, 0, st>>>(d, 0);
+    CUDA_TRY(h, cudaEventRecord(e[1], st));
+    k_zero_L<<<zgrid, TPB, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend);
+    k_rows_pre<<<blocks_for(m), TPB, 0, st>>>(d, h->d_Drow);
+    k_assemble<<<blocks_for(d.n_tgt), TPB, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
+    CUDA_TRY(h, cudaEventRecord(e[2], st));
+    launch_factor(h);
+    CUDA_TRY(h, cudaEventRecord(e[3], st));
+    k_rhs<<<blocks_for(n), TPB, 0, st>>>(d);
+    launch_solve(h);
+    CUDA_TRY(h, cudaEventRecord(e[4], st));
+    CUDA_TRY(h, cudaEventSynchronize(e[4]));
+    if (r == 0) continue;  // warm-up
+    for (int q = 0; q < 4; ++q) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e[q], e[q + 1]);
+      acc[q] += ms;
+    }
+  }
+  for (auto& x : e) cudaEventDestroy(x);
+  CUDA_TRY(h, cudaMemcpyAsync(d.ctl, h->d_ctl_save, ni * sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(h, cudaStreamSynchronize(st));
+  out->ms_eval = acc[0] / reps; out->ms_assemble = acc[1] / reps;
+  out->ms_factor = acc[2] / reps; out->ms_solve = acc[3] / reps;
+  out->reps = reps;
+  return NMPC_OK;
+}
+
+nmpc_status nmpc_get_stats(const nmpc_handle* h, nmpc_stats* st) {
+  if (!h || !st) return NMPC_ERR_INVALID;
+  const Analysis& A = h->A;
+  st->n_total = A.n; st->m_total = A.m;
+  st->n_supernodes = (int)A.sn_first.size();
+  st->n_levels = (int)A.level_ptr.size() - 1;
+  st->nnz_L = A.nnzL_true;
+  st->factor_flops = A.factor_flops;
+  st->solve_flops = A.solve_flops;
+  st->workspace_bytes = (long long)h->ws_bytes;
+  st->analysis_ms = A.analysis_ms;
+  st->max_front = A.max_front;
+  st->ordering_used = A.ordering_used;
+  st->kernel_launches = h->launches;
+  return NMPC_OK;
+}
+
+nmpc_status nmpc_instance_dims(const nmpc_handle* h, int instance, int* n, int* m, int* T) {
+  if (!h || instance < 0 || instance >= h->A.n_inst) return NMPC_ERR_INVALID;
+  if (n) *n = h->A.inst_n[instance];
+  if (m) *m = h->A.inst_m[instance];
+  if (T) *T = h->A.inst_T[instance];
+  return NMPC_OK;
+}
+
+long long nmpc_structure_export(const nmpc_handle* h, int what, void* out, long long cap) {
+  if (!h) return -1;
+  const Analysis& A = h->A;
+  auto copy = [&](const std::vector<int>& v) -> long long {
+    if (out) std::memcpy(out, v.data(), sizeof(int) * (size_t)std::min<long long>(cap, (long long)v.size()));
+    return (long long)v.size();
+  };
+  switch (what) {
+    case 0: return copy(A.perm);
+    case 1: return copy(A.sn_first);
+    case 2: return copy(A.sn_ncol);
+    case 3: return copy(A.sn_nrow);
+    case 4: return copy(A.sn_rows);
+    case 5: return copy(A.sn_parent);
+    case 6: return copy(A.level_ptr);
+    case 7: return copy(A.level_sn);
+    case 8: {
+      const long long cnt = (long long)A.tgt_L.size();
+      int* o = static_cast<int*>(out);
+      for (long long t = 0; out && t < std::min(cap, cnt); ++t) {
+        const long long L = A.tgt_L[t];
+        const int s = (int)(std::upper_bound(A.sn_Lptr.begin(), A.sn_Lptr.end(), L) - A.sn_Lptr.begin()) - 1;
+        const long long off = L - A.sn_Lptr[s];
+        o[2 * t] = A.sn_rows[A.sn_rowptr[s] + off % A.sn_nrow[s]];
+        o[2 * t + 1] = A.sn_first[s] + (int)(off / A.sn_nrow[s]);
+      }
+      return cnt;
+    }
+    default: return -1;
+  }
+}
+
+void nmpc_destroy(nmpc_handle* h) {
+  if (!h) return;
+  if (h->bound) {
+    cudaStreamSynchronize(h->stream);
+    if (h->h_flags) cudaFreeHost(h->h_flags);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+  }
+  delete h;
+}
+
+const char* nmpc_status_string(int s) {
+  switch (s) {
+    case NMPC_OK: return "ok";
+    case NMPC_ERR_INVALID: return "invalid argument";
+    case NMPC_ERR_CUDA: return "CUDA error";
+    case NMPC_ERR_WORKSPACE: return "workspace missing or too small";
+    case NMPC_MAX_ITER: return "iteration limit reached";
+    case NMPC_LINESEARCH_FAIL: return "line search failed";
+    case NMPC_INERTIA_FAIL: return "inertia correction failed";
+    case NMPC_NONFINITE: return "non-finite residual";
+    case NMPC_TIMEOUT: return "bounded device wait timed out";
+    case NMPC_NOT_SOLVED: return "not solved";
+    default: return "unknown status";
+  }
+}
+
+const char* nmpc_last_error(const nmpc_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// Internal layout shared by the host structure builder and the CUDA kernels.
+//
+// Slot conventions (the builder and the kernels must agree):
+//   H (Jacobian of the equality rows) is stored ELL-style, WH slots per row:
+//     distillation (WH=5): [x_k,i | x_{k+1},i-1 | x_{k+1},i | x_{k+1},i+1 | u_{k+1}]
+//     plate        (WH=8): [x_k,c | x_{k+1},c-g | c-1 | c | c+1 | c+g | v_a | v_b]
+//     toy          (WH=3): [y_k | y_{k+1} | u_{k+1}]
+//   Initial-condition rows use slot 0 only (coefficient 1).  Unused slots
+//   carry column -1 and value 0.
+//   W (Hessian of the Lagrangian, lower triangle) is stored per stage
+//   k = 1..T, WS slots per stage:
+//     distillation (WS=2N+2): [x_k,i diag (N) | (u_k, x_k,i) (N) | u_k diag | (u_k, u_{k-1})]
+//     plate        (WS=g*g+S): [x_k,c diag | v_k,s diag]
+//     toy          (WS=2): [y_k diag | u_k diag]
+#pragma once
+#include <cstdint>
+
+namespace nmpc {
+
+enum Model { MODEL_DISTILL = 0, MODEL_PLATE = 1, MODEL_TOY = 2 };
+
+// Per-instance control state of the interior-point method (device resident).
+// One record per instance; the control kernels run one thread per instance.
+struct Ctl {
+  double mu, tau, dw, dw_last;
+  double theta_max, theta_min;
+  double f, logsum, theta, phi;       // at the current iterate
+  double gphi;                        // directional derivative of phi_mu
+  double alpha, alpha_min, alpha_pri, alpha_dual;
+  double E0, E0u, Emu;
+  double ft, logsum_t, theta_t;       // at the trial point
+  int status;                         // 0 running, else nmpc_status (1 = converged)
+  int iter;
+  int phase;                          // see PH_* below
+  int need_factor;                    // 1 while this instance still needs a factorization
+  int factor_fail;                    // set by the factor kernels
+  int ls_active;                      // 1 while the line search is running
+  int nf;                             // filter entries
+  int inertia_retries, ls_trials, augment;
+  int first;                          // first iteration of a solve
+  int pad;
+};
+
+constexpr int FILTER_CAP = 256;
+constexpr int ST_RUNNING = 0;
+constexpr int ST_CONVERGED = 1;  // mapped to NMPC_OK at the API
+
+// Constants of the interior-point method (Wachter & Biegler 2006 defaults).
+constexpr double KAPPA_EPS = 10.0, KAPPA_MU = 0.2, THETA_MU = 1.5, TAU_MIN = 0.99, S_MAX = 100.0;
+constexpr double KAPPA_SIGMA = 1e10, GAMMA_THETA = 1e-5, GAMMA_PHI = 1e-5, DELTA_SW = 1.0;
+constexpr double S_THETA = 1.1, S_PHI = 2.3, ETA_PHI = 1e-4, GAMMA_ALPHA = 0.05;
+constexpr double DELTA_W0 = 1e-4, DELTA_WMIN = 1e-20, DELTA_WMAX = 1e40;
+constexpr double KAPPA_W_MINUS = 1.0 / 3.0, KAPPA_W_PLUS = 8.0, KAPPA_W_PLUS_BAR = 100.0;
+
+struct ModelConst {
+  int model, nx, nu, N, Nf, g, S, WH, WS;
+  double dt, alpha, D, F, xF, Ac, At, Ar, wdu, kappa, cq, rho_u;
+  double xlo, xhi, ulo, uhi;
+  double gamma, tol;
+};
+
+// Reduction chunks never straddle an instance.  kind 0: variables, 1: rows.
+struct Chunk {
+  int inst, kind, begin, end;
+};
+
+// Partial sums/extrema of one chunk (deterministic two-pass reductions).
+struct RedEval {       // at the current iterate
+  double dual, prim, cmax, cmin, sum_l, sum_z, f, logsum, theta;
+  double nonfinite;     // count of non-finite residual/gradient entries
+};
+struct RedDir {        // after the Newton direction
+  double ap, ad, gphi;
+  double pad;
+};
+struct RedTrial {      // at a trial point
+  double f, logsum, theta, nonfinite;
+};
+
+// Device view of everything the kernels touch.  Passed by value.
+struct Dev {
+  ModelConst mc;
+  int n_inst, n, m, nW;
+  // per instance
+  const int* inst_T; const int* inst_voff; const int* inst_roff; const int* inst_woff;
+  const int* inst_n; const int* inst_m; const int* inst_nz;
+  // per variable / row
+  const int* var_inst; const int* row_inst;
+  const double* yL; const double* yU;
+  // parameters
+  double* p_x0; double* p_sp; double* p_uprev;
+  int sp_stride;        // setpoint values per instance
+  // iterate
+  double *y, *zL, *zU, *sp, *sm, *wp, *wm, *bp, *bm;
+  // evaluation
+  double *grad, *h, *Hv, *Wv, *fvar;
+  const int* Hcol;
+  const int* Hcsc_ptr; const int* Hcsc_slot;
+  // direction
+  double *dy, *dzL, *dzU, *dsp, *dsm, *dwp, *dwm, *dbp, *dbm;
+  double* rowv;         // per-row scratch (H^T v products)
+  // trial
+  double *yt, *spt, *smt, *ht, *fvart;
+  // permutation / solve
+  const int* perm;      // perm[i] = position of variable i in the factor ordering
+  const int* iperm;
+  double* b;            // permuted right-hand side / solution
+  // control
+  Ctl* ctl;
+  double* filt_th; double* filt_ph;
+  // reductions
+  const Chunk* chunks; int n_chunks;
+  const int* inst_chunk_ptr; const int* inst_chunk_list;
+  RedEval* red_eval; RedDir* red_dir; RedTrial* red_trial;
+  // assembly map
+  int n_tgt;
+  const long long* tgt_L;
+  const int* tgt_diag;
+  const int* tw_ptr; const int* tw_idx;
+  const int* th_ptr; const int* th_a; const int* th_b;
+  double* Lval;
+  long long nnzL;
+  // instance of each supernode (factor kernels)
+  const int* sn_inst;
+  int max_iter;
+};
+
+// Supernodal structure for the factor and solve kernels.
+struct SnDev {
+  int ns;
+  const int* sn_first;        // first (permuted) column
+  const int* sn_ncol;         // c_s
+  const int* sn_nrow;         // m_s (including the c_s pivot rows)
+  const long long* sn_Lptr;   // offset of the m_s x c_s column-major panel
+  const long long* sn_Uptr;   // offset of the (m_s-c_s)^2 update matrix
+  const long long* sn_rowptr; // offset into sn_rows
+  const int* sn_rows;         // sorted row indices of each supernode
+  const int* sn_child_ptr; const int* sn_child; // children (CSR, ascending)
+  const long long* sn_relptr; const int* sn_rel; // update-row positions in the parent
+  const int* sn_inst;
+  const int* level_ptr; const int* level_sn;    // supernodes by level (height)
+  const long long* sn_uvptr;  // offset of the (m_s-c_s) update vector (solves)
+  double* L;
+  double* U;
+  double* uv;                 // update vectors of the forward solve
+};
+
+}  // namespace nmpc

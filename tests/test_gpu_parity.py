@@ -1,0 +1,223 @@
+"""GPU parity of the CUDA path (through the C ABI) against the oracle.
+
+Criteria (spec tolerances): primal solution within 1e-6 relative
+(max-norm, scaled by max(1, |y|_inf)); the GPU's primal-dual point has scaled
+KKT error E_0 <= 1e-8 when evaluated by the oracle's own evaluator; equal
+interior-point iteration counts on the same seeds.
+"""
+import numpy as np
+import pytest
+
+import paper_2606_04725_gb300.inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_Y = 1e-6
+TOL_KKT = 1e-8
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_04725_gb300 as P
+    P.build()
+    return P
+
+
+def _oracle_problem(O, kind, T, x0, sp, uprev=I.U_REF, **kw):
+    if kind == "distill12":
+        return O.distillation(12, 5, T, x0, np.full(T, sp) if np.isscalar(sp) else sp, uprev)
+    if kind == "distill34":
+        return O.distillation(34, 17, T, x0, np.full(T, sp) if np.isscalar(sp) else sp, uprev)
+    if kind.startswith("plate"):
+        g, S = kw["g"], kw["S"]
+        return O.plate(g, S, T, x0, sp)
+    if kind == "toy":
+        return O.toy(T, x0, sp, dt=kw["dt"])
+    raise ValueError(kind)
+
+
+def _gpu_solver(P, kind, horizons, **kw):
+    if kind == "distill12":
+        return P.Solver(P.MODEL_DISTILLATION, horizons, N=12, Nf=5, **kw)
+    if kind == "distill34":
+        return P.Solver(P.MODEL_DISTILLATION, horizons, N=34, Nf=17, **kw)
+    if kind == "toy":
+        dt = kw.pop("dt")
+        return P.Solver(P.MODEL_TOY, horizons, dt=dt, **kw)
+    raise ValueError(kind)
+
+
+def _state_from_gpu(O, solver, inst, n, m):
+    y, du = solver.get_solution(inst, duals=True)
+    st = O.State(n, m)
+    st.y[:] = y
+    for k in ("zL", "zU", "s_p", "s_m", "w_p", "w_m", "b_p", "b_m"):
+        getattr(st, k)[:] = du[k]
+    return st
+
+
+def _compare(O, prob, solver, inst, st_or, info_or, info_gpu, check_iters=True):
+    assert info_or["status"] == 0, info_or
+    assert info_gpu["status"] == 0, info_gpu
+    st_gpu = _state_from_gpu(O, solver, inst, prob.n, prob.m)
+    err = np.max(np.abs(st_gpu.y - st_or.y)) / max(1.0, np.max(np.abs(st_or.y)))
+    assert err <= TOL_Y, err
+    es, _ = O.kkt_error(prob, st_gpu)
+    assert es <= TOL_KKT, es
+    if check_iters:
+        assert info_gpu["iters"] == info_or["iters"], (info_gpu["iters"], info_or["iters"])
+    return err
+
+
+def test_distillation_N12_cold_solve(P, oracle):
+    T = 20
+    x0 = I.distillation_x0(12, 5, seed=1)
+    sp, _ = I.distillation_setpoints(12, seed=1)
+    prob = _oracle_problem(oracle, "distill12", T, x0, sp)
+    st_or, info_or, _ = oracle.solve(prob)
+    s = _gpu_solver(P, "distill12", [T])
+    s.set_params(x0=x0, setpoint=np.full(T, sp), u_prev=np.array([I.U_REF]))
+    info = s.solve(warm=False)[0]
+    _compare(oracle, prob, s, 0, st_or, info_or, info)
+
+
+def test_distillation_N12_closed_loop(P, oracle):
+    """Five re-solves (the first cold), both sides fed the oracle's parameters."""
+    T = 20
+    x0 = I.distillation_x0(12, 5, seed=1)
+    sp, _ = I.distillation_setpoints(12, seed=1)
+    prob = _oracle_problem(oracle, "distill12", T, x0, sp)
+    s = _gpu_solver(P, "distill12", [T])
+    st_or, uprev = None, I.U_REF
+    for k in range(5):
+        s.set_params(x0=prob.x0.copy(), setpoint=np.full(T, sp), u_prev=np.array([uprev]))
+        st_or, info_or, _ = oracle.solve(prob, state=st_or, warm=k > 0)
+        info = s.solve(warm=k > 0)[0]
+        _compare(oracle, prob, s, 0, st_or, info_or, info)
+        uprev = st_or.y[prob.off_u(1)]
+        prob.set_params(x0=st_or.y[prob.off_x(1):prob.off_x(1) + 12].copy(), uprev=uprev)
+
+
+def test_distillation_N34_T200_resolves(P, oracle):
+    """Config-2 size: cold solve plus warm re-solves across a setpoint switch."""
+    T = 200
+    x0 = I.distillation_x0(34, 17, seed=2)
+    a, b = I.distillation_setpoints(34, seed=2)
+    prob = _oracle_problem(oracle, "distill34", T, x0, a)
+    s = _gpu_solver(P, "distill34", [T])
+    st_or, uprev = None, I.U_REF
+    for k, spk in enumerate([a, a, a, b, b]):
+        prob.set_params(sp=np.full(T, spk))
+        s.set_params(x0=prob.x0.copy(), setpoint=np.full(T, spk), u_prev=np.array([uprev]))
+        st_or, info_or, _ = oracle.solve(prob, state=st_or, warm=k > 0)
+        info = s.solve(warm=k > 0)[0]
+        _compare(oracle, prob, s, 0, st_or, info_or, info)
+        uprev = st_or.y[prob.off_u(1)]
+        prob.set_params(x0=st_or.y[prob.off_x(1):prob.off_x(1) + 34].copy(), uprev=uprev)
+
+
+def test_toy_code_listing_problem(P, oracle):
+    T = 14
+    dt = 10.0 / T
+    t = dt * np.arange(1, T + 1)
+    prob = oracle.toy(T, 1.0, np.sin(t), dt=dt)
+    st_or, info_or, _ = oracle.solve(prob)
+    s = _gpu_solver(P, "toy", [T], dt=dt)
+    s.set_params(x0=np.array([1.0]), setpoint=np.sin(t))
+    info = s.solve()[0]
+    _compare(oracle, prob, s, 0, st_or, info_or, info)
+
+
+@pytest.mark.parametrize("g,S,T", [(8, 8, 5), (12, 12, 4)])
+def test_plate_small(P, oracle, g, S, T):
+    tgt = I.plate_target(g, seed=3)
+    x0 = np.zeros(g * g)
+    prob = oracle.plate(g, S, T, x0, tgt)
+    st_or, info_or, _ = oracle.solve(prob)
+    s = P.Solver(P.MODEL_PLATE, [T], g=g, S=S)
+    s.set_params(x0=x0, setpoint=tgt)
+    info = s.solve()[0]
+    _compare(oracle, prob, s, 0, st_or, info_or, info)
+
+
+def test_batched_instances_match_individual_oracle_solves(P, oracle):
+    """Block-diagonal batch with uneven horizons: each instance equals its own
+    oracle solve (same iterations), in one batched GPU solve."""
+    hz = [20, 7, 13, 20, 5]
+    s = _gpu_solver(P, "distill12", hz)
+    for i, T in enumerate(hz):
+        x0 = I.distillation_x0(12, 5, seed=10 + i)
+        sp = 0.76 + 0.02 * i
+        s.set_params(instance=i, x0=x0, setpoint=np.full(T, sp), u_prev=np.array([I.U_REF]))
+    infos = s.solve()
+    for i, T in enumerate(hz):
+        x0 = I.distillation_x0(12, 5, seed=10 + i)
+        prob = _oracle_problem(oracle, "distill12", T, x0, 0.76 + 0.02 * i)
+        st_or, info_or, _ = oracle.solve(prob)
+        _compare(oracle, prob, s, i, st_or, info_or, infos[i])
+
+
+def test_one_iteration_matches_oracle(P, oracle):
+    """After exactly one interior-point iteration (max_iter = 1) the GPU
+    iterate equals the oracle's: evaluation, assembly, factorization, solve,
+    step recovery, line search and update of Algorithm 2 agree."""
+    T = 20
+    x0 = I.distillation_x0(12, 5, seed=1)
+    prob = _oracle_problem(oracle, "distill12", T, x0, 0.8)
+    for iters in (1, 2, 5):
+        st_or, info_or, _ = oracle.solve(prob, max_iter=iters)
+        s = _gpu_solver(P, "distill12", [T], opts=P.options(max_iter=iters))
+        s.set_params(x0=x0, setpoint=np.full(T, 0.8), u_prev=np.array([I.U_REF]))
+        info = s.solve()[0]
+        assert info["iters"] == info_or["iters"]
+        st_gpu = _state_from_gpu(oracle, s, 0, prob.n, prob.m)
+        for k in ("y", "s_p", "s_m", "w_p", "w_m", "b_p", "b_m", "zL", "zU"):
+            a, b = getattr(st_gpu, k), getattr(st_or, k)
+            np.testing.assert_allclose(a, b, rtol=1e-7, atol=1e-9 * (1 + np.abs(b).max()), err_msg=f"{iters} {k}")
+
+
+def test_ordering_does_not_change_the_solution(P):
+    T = 40
+    x0 = I.distillation_x0(12, 5, seed=5)
+    ys, its = [], []
+    for ordering in (1, 2):
+        s = _gpu_solver(P, "distill12", [T], opts=P.options(ordering=ordering))
+        s.set_params(x0=x0, setpoint=np.full(T, 0.8), u_prev=np.array([I.U_REF]))
+        info = s.solve()[0]
+        assert info["status"] == 0
+        ys.append(s.get_solution(0))
+        its.append(info["iters"])
+    assert its[0] == its[1]
+    assert np.max(np.abs(ys[0] - ys[1])) < 1e-9
+
+
+def test_device_parameters_equal_host_parameters_and_runs_are_deterministic(P):
+    import torch
+    T = 20
+    x0 = I.distillation_x0(12, 5, seed=3)
+    s = _gpu_solver(P, "distill12", [T])
+    s.set_params(x0=x0, setpoint=np.full(T, 0.8), u_prev=np.array([I.U_REF]))
+    s.solve()
+    y_host = s.get_solution(0)
+    dev = torch.device("cuda")
+    s.set_params(x0=torch.tensor(x0, device=dev), setpoint=torch.full((T,), 0.8, dtype=torch.float64, device=dev),
+                 u_prev=torch.tensor([I.U_REF], dtype=torch.float64, device=dev))
+    s.solve()
+    y_dev = s.get_solution(0)
+    assert np.array_equal(y_host, y_dev)  # bitwise: fixed-order reductions, no atomics
+    out = torch.empty(len(y_host), dtype=torch.float64, device=dev)
+    s.get_solution(0, out=(out, None))
+    assert np.array_equal(out.cpu().numpy(), y_host)
+
+
+def test_warm_start_without_solution_falls_back_to_cold_and_errors_are_reported(P):
+    T = 10
+    s = _gpu_solver(P, "distill12", [T])
+    with pytest.raises(P.NmpcError):
+        s.set_params(instance=3, x0=np.zeros(12))
+    s.set_params(x0=I.distillation_x0(12, 5, 1), setpoint=np.full(T, 0.8), u_prev=np.array([I.U_REF]))
+    info = s.solve(warm=True)[0]
+    assert info["status"] == 0

@@ -1,0 +1,107 @@
+"""Host-side checks of the CUDA library (no GPU needed): the C ABI loads and
+exports every entry point declared in include/nmpc.h, and the one-time
+structure analysis (ordering, elimination tree, supernodes, level sets) is a
+valid symbolic factorization of the condensed pattern, checked against the
+oracle's SymCholesky (Sec. 3.2.3)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2606_04725_gb300 as P
+    P.build()
+    return P
+
+
+def test_library_exports_every_declared_symbol(P):
+    header = open(os.path.join(ROOT, "include", "nmpc.h")).read()
+    declared = set(re.findall(r"\b(nmpc_[a-z_]+)\s*\(", header))
+    lib = P.lib()
+    missing = [name for name in sorted(declared) if not hasattr(lib, name)]
+    assert not missing, missing
+    assert declared == set(P._lib.EXPORTED)
+
+
+CASES = [
+    ("distill_nd", dict(model=0, horizons=[20], N=12, Nf=5), dict(ordering=2)),
+    ("distill_nat", dict(model=0, horizons=[20], N=12, Nf=5), dict(ordering=1)),
+    ("distill_batch", dict(model=0, horizons=[3, 7, 5], N=6, Nf=3), dict(ordering=0)),
+    ("plate", dict(model=1, horizons=[4], g=8, S=8), dict(ordering=2)),
+    ("toy", dict(model=2, horizons=[14]), dict(ordering=2)),
+]
+
+
+@pytest.mark.parametrize("name,prob,opt", CASES, ids=[c[0] for c in CASES])
+def test_supernodal_structure_covers_symbolic_factor(P, oracle, name, prob, opt):
+    s = P.Structure(opts=P.options(**opt), **prob)
+    st = s.stats()
+    n = st["n_total"]
+    perm = s.export(0)
+    assert sorted(perm.tolist()) == list(range(n))
+    pairs = s.export(8)              # condensed pattern in factor order, lower
+    assert np.all(pairs[:, 0] >= pairs[:, 1])
+    assert len({(a, b) for a, b in pairs}) == len(pairs)
+    assert np.all(np.isin(np.arange(n), pairs[pairs[:, 0] == pairs[:, 1], 0]))  # full diagonal
+    # oracle symbolic factorization of the same pattern
+    cols = [[] for _ in range(n)]
+    for r, c in pairs:
+        cols[c].append(r)
+    colptr = np.cumsum([0] + [len(c) for c in cols])
+    rowidx = np.concatenate([np.sort(c) for c in cols]).astype(np.int32)
+    parent, Lp, Li = oracle.symbolic(n, colptr, rowidx)
+    first, ncol, nrow = s.export(1), s.export(2), s.export(3)
+    rows = s.export(4)
+    sparent = s.export(5)
+    rowptr = np.concatenate([[0], np.cumsum(nrow)])
+    sn_of = np.empty(n, dtype=int)
+    for k in range(len(first)):
+        sn_of[first[k]:first[k] + ncol[k]] = k
+        R = rows[rowptr[k]:rowptr[k + 1]]
+        assert np.all(np.diff(R) > 0)
+        np.testing.assert_array_equal(R[:ncol[k]], np.arange(first[k], first[k] + ncol[k]))
+    assert np.all(np.diff(first) > 0) and first[0] == 0 and first[-1] + ncol[-1] == n
+    # every structural nonzero of L lies in its supernode's row list
+    for j in range(n):
+        k = sn_of[j]
+        R = set(rows[rowptr[k]:rowptr[k + 1]].tolist())
+        missing = set(Li[Lp[j]:Lp[j + 1]].tolist()) - R
+        assert not missing, (name, j, missing)
+    # supernodal tree agrees with the elimination tree
+    for k in range(len(first)):
+        last = first[k] + ncol[k] - 1
+        if parent[last] < 0:
+            assert sparent[k] == -1
+        else:
+            assert sparent[k] == sn_of[parent[last]]
+        for j in range(first[k], last):
+            assert parent[j] == j + 1  # columns inside a supernode form a chain
+    # levels: children strictly below parents
+    lptr, lsn = s.export(6), s.export(7)
+    level = np.empty(len(first), dtype=int)
+    for l in range(len(lptr) - 1):
+        level[lsn[lptr[l]:lptr[l + 1]]] = l
+    for k in range(len(first)):
+        if sparent[k] >= 0:
+            assert level[sparent[k]] > level[k]
+    assert st["factor_flops"] > 0 and s.workspace_bytes() > 0
+
+
+def test_nested_dissection_reduces_depth(P):
+    nd = P.Structure(model=0, horizons=[200], N=34, Nf=17, opts=P.options(ordering=2)).stats()
+    nat = P.Structure(model=0, horizons=[200], N=34, Nf=17, opts=P.options(ordering=1)).stats()
+    assert nd["n_levels"] <= 12 < nat["n_levels"]
+
+
+def test_invalid_problems_are_rejected(P):
+    with pytest.raises(P.NmpcError):
+        P.Structure(model=0, horizons=[10], N=12, Nf=12)   # feed tray must be inside the column
+    with pytest.raises(P.NmpcError):
+        P.Structure(model=1, horizons=[3], g=10, S=12)     # g % (S/4) != 0
+    with pytest.raises(P.NmpcError):
+        P.Structure(model=0, horizons=[0], N=12, Nf=5)
