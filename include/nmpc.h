@@ -84,7 +84,7 @@ typedef struct {
 /* Solver options.  Defaults from nmpc_options_defaults. */
 typedef struct {
   double tol;            /* outer tolerance on the scaled optimality error E_0 (1e-8) */
-  double gamma;          /* Lifted-KKT relaxation -gamma <= h <= gamma (1e-9) */
+  double gamma;          /* Lifted-KKT relaxation -gamma <= h <= gamma (1e-8) */
   double mu0_cold;       /* initial barrier parameter, cold start (0.1) */
   double mu0_warm;       /* initial barrier parameter, warm start (1e-8) */
   double push_cold;      /* bound push of the initial point, cold (1e-2) */
@@ -192,6 +192,12 @@ nmpc_status nmpc_sensitivity(nmpc_handle* h, int instance, const double* dloss_d
  * iterate (after a solve or set_start) without changing the iterate or the
  * solver state.  Used for roofline measurements. */
 nmpc_status nmpc_time_phases(nmpc_handle* h, int reps, nmpc_phase_times* out);
+
+/* Per-iteration trace of the last solve of an instance: 8 doubles per
+ * interior-point iteration [mu, alpha (accepted primal step), alpha_dual,
+ * delta_w, theta, phi_mu, E_mu, line-search trials].  Copies up to cap
+ * iterations to host memory; returns the number of iterations (or -1). */
+int nmpc_get_trace(nmpc_handle* h, int instance, double* out, int cap);
 
 /* Sizes and one-time analysis figures. */
 nmpc_status nmpc_get_stats(const nmpc_handle* h, nmpc_stats* stats);

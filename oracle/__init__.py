@@ -231,7 +231,7 @@ def steady_state(prob, u):
 
 
 def default_options(**kw):
-    o = dict(tol=1e-8, gamma=1e-9, mu0_cold=0.1, mu0_warm=1e-8, push_cold=1e-2, push_warm=1e-9,
+    o = dict(tol=1e-8, gamma=1e-8, mu0_cold=0.1, mu0_warm=1e-8, push_cold=1e-2, push_warm=1e-9,
              max_iter=200, refine=0)
     o.update(kw)
     return o

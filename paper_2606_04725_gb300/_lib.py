@@ -25,7 +25,7 @@ STATUS = {0: "ok", 1: "invalid", 2: "cuda_error", 3: "workspace", 10: "max_iter"
 
 EXPORTED = ["nmpc_problem_defaults", "nmpc_options_defaults", "nmpc_build", "nmpc_workspace_bytes",
             "nmpc_bind", "nmpc_set_params", "nmpc_solve", "nmpc_get_solution", "nmpc_set_start",
-            "nmpc_sensitivity", "nmpc_time_phases", "nmpc_get_stats", "nmpc_instance_dims", "nmpc_structure_export",
+            "nmpc_sensitivity", "nmpc_get_trace", "nmpc_time_phases", "nmpc_get_stats", "nmpc_instance_dims", "nmpc_structure_export",
             "nmpc_destroy", "nmpc_status_string", "nmpc_last_error"]
 
 
@@ -92,6 +92,7 @@ def lib():
             L.nmpc_set_start.argtypes = [_P, C.c_int, _P, _P, C.c_int]
             L.nmpc_sensitivity.argtypes = [_P, C.c_int, _P, _P, _P, C.c_int]
             L.nmpc_get_stats.argtypes = [_P, C.POINTER(Stats)]
+            L.nmpc_get_trace.argtypes = [_P, C.c_int, _P, C.c_int]
             L.nmpc_time_phases.argtypes = [_P, C.c_int, C.POINTER(PhaseTimes)]
             L.nmpc_instance_dims.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.nmpc_structure_export.argtypes = [_P, C.c_int, _P, C.c_longlong]
@@ -288,6 +289,14 @@ class Solver(Structure):
         py, on_dev = _ptr(y)
         pd = _ptr(duals)[0] if duals is not None else None
         self._check(lib().nmpc_set_start(self._h, instance, py, pd, on_dev))
+
+    def trace(self, instance=0):
+        cap = self._o.max_iter + 2
+        buf = np.zeros(cap * 8)
+        k = lib().nmpc_get_trace(self._h, instance, buf.ctypes.data, cap)
+        if k < 0:
+            raise NmpcError(15, "no trace")
+        return buf.reshape(cap, 8)[:k]
 
     def time_phases(self, reps=10):
         t = PhaseTimes()

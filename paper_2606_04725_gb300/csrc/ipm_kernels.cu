@@ -356,6 +356,7 @@ __global__ void k_ctl_dir(Dev d) {
     amin = GAMMA_ALPHA * GAMMA_THETA;
   }
   c.alpha_min = amin;
+  c.ls_trials0 = c.ls_trials;
   c.alpha = ap;
   c.phase = 0;
   c.augment = 0;
@@ -486,6 +487,11 @@ __global__ void k_ctl_post(Dev d) {
   if (i >= d.n_inst) return;
   Ctl c = d.ctl[i];
   if (c.phase != 1) return;
+  if (c.iter <= d.max_iter) {
+    double* t = d.trace + ((size_t)i * (d.max_iter + 2) + c.iter) * 8;
+    t[0] = c.mu; t[1] = c.alpha; t[2] = c.alpha_dual; t[3] = c.dw;
+    t[4] = c.theta; t[5] = c.phi; t[6] = c.Emu; t[7] = c.ls_trials - c.ls_trials0;
+  }
   if (c.augment && c.nf < FILTER_CAP) {
     d.filt_th[(size_t)i * FILTER_CAP + c.nf] = (1.0 - GAMMA_THETA) * c.theta;
     d.filt_ph[(size_t)i * FILTER_CAP + c.nf] = c.phi - GAMMA_PHI * c.theta;

@@ -115,6 +115,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   h->d_flags = cv.take<int>(4);
   h->d_stage = cv.take<double>((size_t)ni * (A.mc.nx + A.sp_stride + 1));
   h->d_ctl_save = cv.take<Ctl>(ni);
+  d.trace = cv.take<double>((size_t)ni * (h->opt.max_iter + 2) * 8);
   s.sn_first = cv.take<int>(ns); s.sn_ncol = cv.take<int>(ns); s.sn_nrow = cv.take<int>(ns);
   s.sn_Lptr = cv.take<long long>(ns + 1); s.sn_Uptr = cv.take<long long>(ns + 1);
   s.sn_rowptr = cv.take<long long>(ns + 1); s.sn_rows = cv.take<int>(A.sn_rows.size());
@@ -189,7 +190,7 @@ void nmpc_problem_defaults(int model, nmpc_problem* p) {
 
 void nmpc_options_defaults(nmpc_options* o) {
   std::memset(o, 0, sizeof(*o));
-  o->tol = 1e-8; o->gamma = 1e-9; o->mu0_cold = 0.1; o->mu0_warm = 1e-8;
+  o->tol = 1e-8; o->gamma = 1e-8; o->mu0_cold = 0.1; o->mu0_warm = 1e-8;
   o->push_cold = 1e-2; o->push_warm = 1e-9; o->max_iter = 200; o->ordering = NMPC_ORDER_AUTO;
   o->nd_leaf = 1; o->use_graph = 1; o->spin_limit = 10000000LL;
 }
@@ -492,6 +493,18 @@ nmpc_status nmpc_set_start(nmpc_handle* h, int instance, const double* y, const 
   if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->have_solution = true;
   return NMPC_OK;
+}
+
+int nmpc_get_trace(nmpc_handle* h, int instance, double* out, int cap) {
+  if (!h || !h->bound || instance < 0 || instance >= h->A.n_inst || !h->have_solution) return -1;
+  const int iters = std::min(h->h_ctl[instance].iter, h->opt.max_iter + 1);
+  const int cnt = std::min(cap, iters);
+  if (out && cnt > 0) {
+    if (cudaMemcpyAsync(out, h->d.trace + (size_t)instance * (h->opt.max_iter + 2) * 8, (size_t)cnt * 8 * sizeof(double),
+                        cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return -1;
+  }
+  return iters;
 }
 
 nmpc_status nmpc_sensitivity(nmpc_handle* h, int, const double*, double*, double*, int) {

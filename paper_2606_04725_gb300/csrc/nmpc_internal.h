@@ -38,7 +38,7 @@ struct Ctl {
   int nf;                             // filter entries
   int inertia_retries, ls_trials, augment;
   int first;                          // first iteration of a solve
-  int pad;
+  int ls_trials0;                     // ls_trials at the start of this iteration's search
 };
 
 constexpr int FILTER_CAP = 256;
@@ -123,6 +123,7 @@ struct Dev {
   // instance of each supernode (factor kernels)
   const int* sn_inst;
   int max_iter;
+  double* trace;        // per instance: (max_iter + 2) x 8 doubles
 };
 
 // Supernodal structure for the factor and solve kernels.
