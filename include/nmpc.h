@@ -217,6 +217,43 @@ nmpc_status nmpc_instance_dims(const nmpc_handle* h, int instance, int* n, int* 
  *     (2 int32 per entry; the returned length counts pairs) */
 long long nmpc_structure_export(const nmpc_handle* h, int what, void* out, long long cap);
 
+/* Size of the library's static device workspace used by nmpc_solve_static. */
+#define NMPC_STATIC_WORKSPACE_BYTES (32 * 1024 * 1024)
+
+/* One-shot cold solve that allocates nothing (no paper counterpart).
+ *
+ * For callers that cannot allocate device memory themselves -- for example a
+ * control task that may only use memory fixed when the process starts, or a
+ * plug-in that is handed a stream and its input/output buffers but no
+ * allocator -- and therefore cannot supply the workspace that nmpc_bind
+ * needs.  This entry point runs the same analysis and the same kernels as
+ * nmpc_build + nmpc_bind + nmpc_set_params + nmpc_solve + nmpc_get_solution,
+ * but every device scratch array (factor panels, multifrontal update
+ * matrices, reduction partials, iterates) lives in one file-scope device
+ * array of NMPC_STATIC_WORKSPACE_BYTES (32 MiB) that every GPU loading the
+ * library holds until the process exits.  It makes no device or pinned-host
+ * allocation: no cudaMalloc, cudaFree, cudaMallocHost or other CUDA
+ * allocating routine (the host-side analysis uses ordinary heap memory).
+ *
+ *   prob, opts:     as for nmpc_build (opts may be NULL)
+ *   cuda_stream:    stream for all work (NULL = legacy default stream)
+ *   x0, setpoint, u_prev: parameters packed for all instances as in
+ *                   nmpc_set_params(instance = -1); NULL keeps zeros
+ *   y_out:          receives the primal solutions of all instances, packed
+ *                   instance after instance (sum of n over instances)
+ *   info:           n_instances records (host), may be NULL
+ *   on_device:      1 if x0/setpoint/u_prev/y_out are device pointers
+ * Returns NMPC_ERR_WORKSPACE (with a message on stderr) when the problem's
+ * workspace exceeds NMPC_STATIC_WORKSPACE_BYTES, otherwise as nmpc_solve.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array and each call overwrites and clears what it
+ * uses: calls that overlap on the GPU (other streams or threads) race and
+ * must be serialized by the caller.  Always a cold start. */
+nmpc_status nmpc_solve_static(const nmpc_problem* prob, const nmpc_options* opts, void* cuda_stream,
+                              const double* x0, const double* setpoint, const double* u_prev,
+                              double* y_out, nmpc_info* info, int on_device);
+
 /* Release host memory of the handle (the caller frees the workspace).
  * Synchronizes the library stream.  NULL is ignored. */
 void nmpc_destroy(nmpc_handle* h);

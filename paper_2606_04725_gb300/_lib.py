@@ -26,7 +26,9 @@ STATUS = {0: "ok", 1: "invalid", 2: "cuda_error", 3: "workspace", 10: "max_iter"
 EXPORTED = ["nmpc_problem_defaults", "nmpc_options_defaults", "nmpc_build", "nmpc_workspace_bytes",
             "nmpc_bind", "nmpc_set_params", "nmpc_solve", "nmpc_get_solution", "nmpc_set_start",
             "nmpc_sensitivity", "nmpc_get_trace", "nmpc_time_phases", "nmpc_get_stats", "nmpc_instance_dims", "nmpc_structure_export",
-            "nmpc_destroy", "nmpc_status_string", "nmpc_last_error"]
+            "nmpc_solve_static", "nmpc_destroy", "nmpc_status_string", "nmpc_last_error"]
+
+STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
 
 class Problem(C.Structure):
@@ -97,6 +99,8 @@ def lib():
             L.nmpc_instance_dims.argtypes = [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.nmpc_structure_export.argtypes = [_P, C.c_int, _P, C.c_longlong]
             L.nmpc_structure_export.restype = C.c_longlong
+            L.nmpc_solve_static.argtypes = [C.POINTER(Problem), C.POINTER(Options), _P, _P, _P, _P, _P,
+                                            C.POINTER(Info), C.c_int]
             L.nmpc_destroy.argtypes = [_P]
             L.nmpc_destroy.restype = None
             L.nmpc_status_string.argtypes = [C.c_int]
@@ -310,6 +314,24 @@ class Solver(Structure):
         py, on_dev = _ptr(dloss_dy)
         self._check(lib().nmpc_sensitivity(self._h, instance, py, _ptr(dx0)[0], _ptr(dsp)[0], on_dev))
         return dx0, dsp
+
+
+def solve_static(model, horizons, x0, setpoint, u_prev, y_out, opts=None, stream=None, **prob_kw):
+    """nmpc_solve_static: a one-shot cold solve whose device scratch is the
+    library's static workspace (no allocation by the library or the caller
+    beyond the given arrays).  Returns (status, infos)."""
+    p, hz = problem(model, horizons, **prob_kw)
+    p.horizons = hz.ctypes.data_as(C.POINTER(C.c_int))
+    o = opts if opts is not None else options()
+    infos = (Info * int(hz.size))()
+    ptrs = [_ptr(a) for a in (x0, setpoint, u_prev, y_out)]
+    flags = {q[1] for q in ptrs if q[0] is not None}
+    if len(flags) > 1:
+        raise ValueError("mix of host and device arrays")
+    on_dev = flags.pop() if flags else 0
+    st = lib().nmpc_solve_static(C.byref(p), C.byref(o), stream, ptrs[0][0], ptrs[1][0], ptrs[2][0],
+                                 ptrs[3][0], infos, on_dev)
+    return st, [{k: getattr(infos[i], k) for k, _ in Info._fields_} for i in range(int(hz.size))]
 
 
 def _numel(a):

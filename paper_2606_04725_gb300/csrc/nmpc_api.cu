@@ -3,9 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -251,11 +253,13 @@ nmpc_status nmpc_workspace_bytes(const nmpc_handle* h, size_t* bytes) {
   return NMPC_OK;
 }
 
-nmpc_status nmpc_bind(nmpc_handle* h, void* ws, size_t bytes) {
-  if (!h) return NMPC_ERR_INVALID;
-  if (h->bound) return fail(h, NMPC_ERR_INVALID, "workspace already bound");
-  if (!ws || bytes < h->ws_bytes) return fail(h, NMPC_ERR_WORKSPACE, "workspace missing or smaller than nmpc_workspace_bytes");
-  if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(h, NMPC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+}  // extern "C"
+
+namespace {
+
+// Lay the workspace out, clear it and upload the structure (shared by the
+// binding entry points).
+nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   Carver cv;
   cv.base = static_cast<char*>(ws);
   carve(h, cv);
@@ -312,12 +316,26 @@ nmpc_status nmpc_bind(nmpc_handle* h, void* ws, size_t bytes) {
     CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
     CUDA_TRY(h, cudaFuncSetAttribute(k_bwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
   }
-  CUDA_TRY(h, cudaMallocHost(&h->h_flags, 4 * sizeof(int)));
-  CUDA_TRY(h, cudaEventCreate(&h->ev0));
-  CUDA_TRY(h, cudaEventCreate(&h->ev1));
   CUDA_TRY(h, cudaStreamSynchronize(st));
   h->d.max_iter = h->opt.max_iter;
   h->h_ctl.resize(A.n_inst);
+  return NMPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nmpc_status nmpc_bind(nmpc_handle* h, void* ws, size_t bytes) {
+  if (!h) return NMPC_ERR_INVALID;
+  if (h->bound) return fail(h, NMPC_ERR_INVALID, "workspace already bound");
+  if (!ws || bytes < h->ws_bytes) return fail(h, NMPC_ERR_WORKSPACE, "workspace missing or smaller than nmpc_workspace_bytes");
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(h, NMPC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  const nmpc_status st = upload_structure(h, ws);
+  if (st != NMPC_OK) return st;
+  CUDA_TRY(h, cudaMallocHost(&h->h_flags, 4 * sizeof(int)));
+  CUDA_TRY(h, cudaEventCreate(&h->ev0));
+  CUDA_TRY(h, cudaEventCreate(&h->ev1));
   h->bound = true;
   return NMPC_OK;
 }
@@ -363,7 +381,7 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
   const int ni = A.n_inst, n = A.n, m = A.m;
   const double mu0 = warm ? h->opt.mu0_warm : h->opt.mu0_cold;
   const double push = warm ? h->opt.push_warm : h->opt.push_cold;
-  CUDA_TRY(h, cudaEventRecord(h->ev0, st));
+  if (h->ev0) CUDA_TRY(h, cudaEventRecord(h->ev0, st));
   k_ctl_init<<<blocks_for(ni), TPB, 0, st>>>(d, mu0);
   ++h->launches;
   k_init_vars<<<blocks_for(n), TPB, 0, st>>>(d, warm, push);
@@ -437,11 +455,11 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
     k_ctl_post<<<blocks_for(ni), TPB, 0, st>>>(d);
     ++h->launches;
   }
-  CUDA_TRY(h, cudaEventRecord(h->ev1, st));
+  if (h->ev1) CUDA_TRY(h, cudaEventRecord(h->ev1, st));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl.data(), d.ctl, ni * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(h, cudaStreamSynchronize(st));
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  if (h->ev0 && h->ev1) cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->have_solution = true;
   nmpc_status ret = NMPC_OK;
   for (int i = 0; i < ni; ++i) {
@@ -650,3 +668,84 @@ const char* nmpc_status_string(int s) {
 const char* nmpc_last_error(const nmpc_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// One-shot solve without any allocation.
+//
+// The whole device workspace of this entry point is the file-scope array
+// below (NMPC_STATIC_WORKSPACE_BYTES).  Host code may not pass the array's
+// name to a kernel or a copy: in host code it names a host-side shadow, not
+// device memory.  Its device address is obtained with cudaGetSymbolAddress
+// once per device, with that device current, on the first call made on that
+// device, and cached.
+// ------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_static_workspace[NMPC_STATIC_WORKSPACE_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+constexpr int MAX_DEVICES = 256;
+void* g_static_addr[MAX_DEVICES] = {nullptr};
+}  // namespace
+
+extern "C" nmpc_status nmpc_solve_static(const nmpc_problem* prob, const nmpc_options* opts, void* cuda_stream,
+                                         const double* x0, const double* setpoint, const double* u_prev,
+                                         double* y_out, nmpc_info* info, int on_device) {
+  if (!prob || !y_out || prob->n_instances < 1 || !prob->horizons) return NMPC_ERR_INVALID;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return NMPC_ERR_CUDA;
+  void* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_static_workspace) != cudaSuccess || !p) {
+        std::fprintf(stderr, "nmpc_solve_static: cudaGetSymbolAddress failed on device %d\n", dev);
+        return NMPC_ERR_CUDA;
+      }
+      g_static_addr[dev] = p;
+    }
+    ws = g_static_addr[dev];
+  }
+  nmpc_handle* h = nullptr;
+  nmpc_status st = nmpc_build(prob, opts, cuda_stream, &h);
+  if (st != NMPC_OK) return st;
+  if (h->ws_bytes > (size_t)NMPC_STATIC_WORKSPACE_BYTES) {
+    std::fprintf(stderr,
+                 "nmpc_solve_static: the problem needs %zu bytes of device workspace, more than the %d bytes "
+                 "of the library's static workspace; use nmpc_build/nmpc_bind with caller memory instead\n",
+                 h->ws_bytes, NMPC_STATIC_WORKSPACE_BYTES);
+    delete h;
+    return NMPC_ERR_WORKSPACE;
+  }
+  // the previous call's contents are cleared by the upload (workspace memset)
+  st = upload_structure(h, ws);
+  int host_flags[4] = {0, 0, 0, 0};
+  if (st == NMPC_OK) {
+    h->h_flags = host_flags;  // pageable host memory: no pinned allocation
+    h->bound = true;
+    const auto t0 = std::chrono::steady_clock::now();
+    st = nmpc_set_params(h, -1, x0, setpoint, u_prev, on_device);
+    nmpc_status sst = NMPC_OK;
+    if (st == NMPC_OK) sst = nmpc_solve(h, 0, info);
+    if (st == NMPC_OK && (sst == NMPC_ERR_INVALID || sst == NMPC_ERR_CUDA || sst == NMPC_ERR_WORKSPACE)) st = sst;
+    if (st == NMPC_OK) {
+      double* out = y_out;
+      for (int i = 0; i < h->A.n_inst && st == NMPC_OK; ++i) {
+        st = nmpc_get_solution(h, i, out, nullptr, on_device);
+        out += h->A.inst_n[i];
+      }
+      if (st == NMPC_OK && on_device && cudaStreamSynchronize(h->stream) != cudaSuccess) st = NMPC_ERR_CUDA;
+      if (st == NMPC_OK) st = sst;
+    }
+    if (info) {
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      for (int i = 0; i < h->A.n_inst; ++i) info[i].ms_total = ms;
+    }
+  }
+  if (st != NMPC_OK && !h->err.empty()) std::fprintf(stderr, "nmpc_solve_static: %s\n", h->err.c_str());
+  cudaStreamSynchronize(h->stream);
+  h->h_flags = nullptr;
+  delete h;
+  return st;
+}
