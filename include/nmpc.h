@@ -94,6 +94,8 @@ typedef struct {
   int nd_leaf;           /* nested dissection: stages per leaf (1) */
   int use_graph;         /* capture one interior-point iteration in a CUDA graph (1) */
   long long spin_limit;  /* iteration limit of bounded device waits (1e7) */
+  double pivtol;         /* inertia test: a pivot must exceed pivtol * |K_jj| (1e-12) */
+  int factor_mode;       /* 0: cluster-cooperative fronts where they fit (default); 1: one CTA per front */
 } nmpc_options;
 
 /* Per-instance result of a solve.  Times are measured with CUDA events on

@@ -280,6 +280,34 @@ int or_band_cholesky(int n, int b, double* band) {
   return 0;
 }
 
+/* Cholesky with a relative pivot tolerance: column j's pivot must exceed
+ * tol * |K_jj| (K_jj the diagonal entry before factorization).  With tol > 0 a
+ * pivot at rounding level counts as a zero eigenvalue, i.e. the wrong inertia
+ * of eq. (infiniteOCP-inertia), which requires n_0 = 0. */
+static int band_cholesky_tol(int n, int b, double* band, double tol) {
+  const int w = b + 1;
+  if (tol <= 0.0) return or_band_cholesky(n, b, band);
+  double* diag = malloc(sizeof(double) * n);
+  for (int j = 0; j < n; ++j) diag[j] = fabs(band[(size_t)j * w]);
+  int rc = 0;
+  for (int j = 0; j < n && rc == 0; ++j) {
+    double* cj = band + (size_t)j * w;
+    double d = cj[0];
+    if (!(d > tol * diag[j]) || !(d > 0.0) || !isfinite(d)) { rc = j + 1; break; }
+    d = sqrt(d);
+    cj[0] = d;
+    const int len = (n - 1 - j < b) ? n - 1 - j : b;
+    for (int i = 1; i <= len; ++i) cj[i] /= d;
+    for (int q = 1; q <= len; ++q) {
+      double* cq = band + (size_t)(j + q) * w;
+      const double l = cj[q];
+      for (int i = q; i <= len; ++i) cq[i - q] -= cj[i] * l;
+    }
+  }
+  free(diag);
+  return rc;
+}
+
 static void band_solve(int n, int b, const double* band, double* x) {
   const int w = b + 1;
   for (int j = 0; j < n; ++j) {           /* L v = x */
@@ -568,13 +596,14 @@ static void direction(work* w, const or_state* z, double mu, or_state* d) {
  * last/3, then x100 (first) or x8, failing above 1e40.  Returns 0 on
  * success and sets *dw; -1 on failure. */
 static int factor_with_correction(work* w, const or_state* z, double* dw_last, double* dw, int* retries) {
+  const double tol = w->o->pivtol;
   assemble(w, z, 0.0);
-  if (or_band_cholesky(w->n, w->b, w->band) == 0) { *dw = 0.0; return 0; }
+  if (band_cholesky_tol(w->n, w->b, w->band, tol) == 0) { *dw = 0.0; return 0; }
   double d = (*dw_last == 0.0) ? DELTA_W0 : fmax(DELTA_WMIN, KAPPA_W_MINUS * *dw_last);
   for (;;) {
     ++*retries;
     assemble(w, z, d);
-    if (or_band_cholesky(w->n, w->b, w->band) == 0) { *dw = d; *dw_last = d; return 0; }
+    if (band_cholesky_tol(w->n, w->b, w->band, tol) == 0) { *dw = d; *dw_last = d; return 0; }
     d = (*dw_last == 0.0) ? KAPPA_W_PLUS_BAR * d : KAPPA_W_PLUS * d;
     if (d > DELTA_WMAX) return -1;
   }

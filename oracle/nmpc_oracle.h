@@ -47,6 +47,7 @@ typedef struct {
   double push_cold, push_warm;
   int max_iter;
   int refine;        /* iterative-refinement sweeps on the condensed system (0 = none) */
+  double pivtol;     /* relative pivot tolerance of the inertia test */
 } or_options;
 
 typedef struct {

@@ -15,8 +15,29 @@ namespace nmpc {
 
 __device__ __forceinline__ bool fin(double x) { return isfinite(x); }
 
+// Running product of positive numbers kept as mantissa in [1, 2) times 2^e:
+// sum_i log(x_i) = log(m) + e log 2 with one logarithm per chunk.  A
+// non-positive or non-finite factor makes m non-finite (caught by callers).
+__device__ __forceinline__ void logacc_mul(double& m, double& e, double x) {
+  m *= x;
+  const long long b = __double_as_longlong(m);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0 || ex == 0x7ff || m <= 0.0) {  // zero, subnormal, inf/nan or negative: leave to the caller
+    if (!(m > 0.0) || ex == 0x7ff) m = __longlong_as_double(0x7ff8000000000000LL);
+    else { int q; m = frexp(m, &q); e += q; }
+    return;
+  }
+  e += ex - 1023;
+  m = __longlong_as_double((b & ~(0x7ffLL << 52)) | (1023LL << 52));
+}
+
+constexpr double LN2 = 0.69314718055994530941723212145818;
+
+// combine chunk partials (mantissa products) exactly as elements: one log at the end
+__device__ __forceinline__ double logacc_value(double m, double e) { return log(m) + e * LN2; }
+
 // Fixed-order block reduction of NV doubles per thread with operator OP
-// (0 sum, 1 max, 2 min).  Result valid in thread 0.
+// (0 sum, 1 max, 2 min, 3 product).  Result valid in thread 0.
 template <int NV>
 __device__ void block_reduce(double (&v)[NV], const int (&op)[NV]) {
   __shared__ double sh[NV][TPB / 32];
@@ -25,7 +46,7 @@ __device__ void block_reduce(double (&v)[NV], const int (&op)[NV]) {
   for (int q = 0; q < NV; ++q) {
     for (int o = 16; o > 0; o >>= 1) {
       double t = __shfl_down_sync(0xffffffffu, v[q], o);
-      v[q] = op[q] == 0 ? v[q] + t : (op[q] == 1 ? fmax(v[q], t) : fmin(v[q], t));
+      v[q] = op[q] == 0 ? v[q] + t : (op[q] == 1 ? fmax(v[q], t) : (op[q] == 2 ? fmin(v[q], t) : v[q] * t));
     }
     if (lane == 0) sh[q][wid] = v[q];
   }
@@ -34,7 +55,8 @@ __device__ void block_reduce(double (&v)[NV], const int (&op)[NV]) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       double a = sh[q][0];
-      for (int w = 1; w < TPB / 32; ++w) a = op[q] == 0 ? a + sh[q][w] : (op[q] == 1 ? fmax(a, sh[q][w]) : fmin(a, sh[q][w]));
+      for (int w = 1; w < TPB / 32; ++w)
+        a = op[q] == 0 ? a + sh[q][w] : (op[q] == 1 ? fmax(a, sh[q][w]) : (op[q] == 2 ? fmin(a, sh[q][w]) : a * sh[q][w]));
       v[q] = a;
     }
   }
@@ -62,8 +84,9 @@ __global__ void k_red_eval(Dev d) {
   if (c.status != ST_RUNNING) return;
   const double gam = d.mc.gamma;
   const int WH = d.mc.WH;
-  double v[10] = {0.0, 0.0, 0.0, DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  const int op[10] = {1, 1, 1, 2, 0, 0, 0, 0, 0, 0};
+  // dual, prim, cmax, cmin, sum_l, sum_z, f, log-mantissa, log-exponent, theta, nonfinite
+  double v[11] = {0.0, 0.0, 0.0, DBL_MAX, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
+  const int op[11] = {1, 1, 1, 2, 0, 0, 0, 3, 0, 0, 0};
   if (ch.kind == 0) {
     for (int j = ch.begin + threadIdx.x; j < ch.end; j += TPB) {
       double r = d.grad[j];
@@ -77,23 +100,23 @@ __global__ void k_red_eval(Dev d) {
         const double p = (yj - lo) * d.zL[j];
         v[2] = fmax(v[2], p); v[3] = fmin(v[3], p);
         v[5] += d.zL[j];
-        v[7] += log(yj - lo);
+        logacc_mul(v[7], v[8], yj - lo);
       }
       if (fin(hi)) {
         r += d.zU[j];
         const double p = (hi - yj) * d.zU[j];
         v[2] = fmax(v[2], p); v[3] = fmin(v[3], p);
         v[5] += d.zU[j];
-        v[7] += log(hi - yj);
+        logacc_mul(v[7], v[8], hi - yj);
       }
-      if (!fin(r)) v[9] += 1.0;
+      if (!fin(r)) v[10] += 1.0;
       v[0] = fmax(v[0], fabs(r));
       v[6] += d.fvar[j];
     }
   } else {
     for (int r = ch.begin + threadIdx.x; r < ch.end; r += TPB) {
       const double h = d.h[r];
-      if (!fin(h)) v[9] += 1.0;
+      if (!fin(h)) v[10] += 1.0;
       v[0] = fmax(v[0], fmax(fabs(d.wp[r] - d.bp[r]), fabs(d.wm[r] - d.bm[r])));
       const double cp = h - gam + d.sp[r], cm = -h - gam + d.sm[r];
       v[1] = fmax(v[1], fmax(fabs(cp), fabs(cm)));
@@ -101,15 +124,16 @@ __global__ void k_red_eval(Dev d) {
       v[2] = fmax(v[2], fmax(pp, pm)); v[3] = fmin(v[3], fmin(pp, pm));
       v[4] += fabs(d.wp[r]) + fabs(d.wm[r]);
       v[5] += d.bp[r] + d.bm[r];
-      v[7] += log(d.sp[r]) + log(d.sm[r]);
-      v[8] += fabs(cp) + fabs(cm);
+      logacc_mul(v[7], v[8], d.sp[r]);
+      logacc_mul(v[7], v[8], d.sm[r]);
+      v[9] += fabs(cp) + fabs(cm);
     }
   }
-  block_reduce<10>(v, op);
+  block_reduce<11>(v, op);
   if (threadIdx.x == 0) {
     RedEval e;
     e.dual = v[0]; e.prim = v[1]; e.cmax = v[2]; e.cmin = v[3]; e.sum_l = v[4]; e.sum_z = v[5];
-    e.f = v[6]; e.logsum = v[7]; e.theta = v[8]; e.nonfinite = v[9];
+    e.f = v[6]; e.lgm = v[7]; e.lge = v[8]; e.theta = v[9]; e.nonfinite = v[10];
     d.red_eval[blockIdx.x] = e;
   }
 }
@@ -121,11 +145,15 @@ __global__ void k_ctl_pre(Dev d, int max_iter) {
   Ctl c = d.ctl[i];
   if (c.status != ST_RUNNING) return;
   double dual = 0, prim = 0, cmax = 0, cmin = DBL_MAX, sl = 0, sz = 0, f = 0, lg = 0, th = 0, nf = 0;
+  double lgm = 1.0, lge = 0.0;
   for (int q = d.inst_chunk_ptr[i]; q < d.inst_chunk_ptr[i + 1]; ++q) {
     const RedEval& e = d.red_eval[d.inst_chunk_list[q]];
     dual = fmax(dual, e.dual); prim = fmax(prim, e.prim); cmax = fmax(cmax, e.cmax); cmin = fmin(cmin, e.cmin);
-    sl += e.sum_l; sz += e.sum_z; f += e.f; lg += e.logsum; th += e.theta; nf += e.nonfinite;
+    sl += e.sum_l; sz += e.sum_z; f += e.f; th += e.theta; nf += e.nonfinite;
+    logacc_mul(lgm, lge, e.lgm);
+    lge += e.lge;
   }
+  lg = logacc_value(lgm, lge);
   const double mrows = d.inst_m[i], nz = d.inst_nz[i];
   const double sd = fmax(S_MAX, (sl + sz) / (2.0 * mrows + nz)) / S_MAX;
   const double sc = fmax(S_MAX, sz / nz) / S_MAX;
@@ -178,11 +206,11 @@ __global__ void k_rows_pre(Dev d, double* Drow) {
   const Ctl& c = d.ctl[d.row_inst[r]];
   if (c.status != ST_RUNNING) return;
   const double mu = c.mu, gam = d.mc.gamma;
-  const double sp = d.sp[r], sm = d.sm[r];
-  const double Qp = d.bp[r] / sp, Qm = d.bm[r] / sm;
+  const double sp = d.sp[r], sm = d.sm[r], isp = d.isp[r], ism = d.ism[r];
+  const double Qp = d.bp[r] * isp, Qm = d.bm[r] * ism;
   Drow[r] = Qp + Qm;
   const double r4p = d.h[r] - gam + sp, r4m = -d.h[r] - gam + sm;
-  const double r2p = d.wp[r] - mu / sp, r2m = d.wm[r] - mu / sm;
+  const double r2p = d.wp[r] - mu * isp, r2m = d.wm[r] - mu * ism;
   d.rowv[r] = (d.wp[r] - d.wm[r]) + (Qp * r4p - r2p) - (Qm * r4m - r2m);
 }
 
@@ -202,11 +230,9 @@ __global__ void k_assemble(Dev d, const int* tgt_inst, const double* Drow) {
   }
   const int j = d.tgt_diag[t];
   if (j >= 0) {
-    double sig = c.dw;
-    const double yj = d.y[j];
-    if (fin(d.yL[j])) sig += d.zL[j] / (yj - d.yL[j]);
-    if (fin(d.yU[j])) sig += d.zU[j] / (d.yU[j] - yj);
-    v += sig;
+    // Sigma_y = zL/(y - yL) + zU/(yU - y) (reciprocals are 0 where a bound is absent)
+    v += c.dw + d.zL[j] * d.igL[j] + d.zU[j] * d.igU[j];
+    d.Kdiag[d.perm[j]] = v;
   }
   d.Lval[d.tgt_L[t]] = v;
 }
@@ -244,8 +270,7 @@ __global__ void k_rhs(Dev d) {
     const int s = d.Hcsc_slot[q];
     r1 += d.Hv[s] * d.rowv[s / WH];
   }
-  if (fin(d.yL[v])) r1 -= mu / (d.y[v] - d.yL[v]);
-  if (fin(d.yU[v])) r1 += mu / (d.yU[v] - d.y[v]);
+  r1 += mu * (d.igU[v] - d.igL[v]);
   d.b[d.perm[v]] = -r1;
 }
 
@@ -259,10 +284,9 @@ __global__ void k_recover_vars(Dev d) {
   const double mu = c.mu;
   const double dy = d.b[d.perm[v]];
   d.dy[v] = dy;
-  const double yv = d.y[v];
   double dzl = 0.0, dzu = 0.0;
-  if (fin(d.yL[v])) { const double g = yv - d.yL[v]; dzl = mu / g - d.zL[v] - d.zL[v] / g * dy; }
-  if (fin(d.yU[v])) { const double g = d.yU[v] - yv; dzu = mu / g - d.zU[v] + d.zU[v] / g * dy; }
+  if (fin(d.yL[v])) { const double ig = d.igL[v]; dzl = mu * ig - d.zL[v] - d.zL[v] * ig * dy; }
+  if (fin(d.yU[v])) { const double ig = d.igU[v]; dzu = mu * ig - d.zU[v] + d.zU[v] * ig * dy; }
   d.dzL[v] = dzl;
   d.dzU[v] = dzu;
 }
@@ -281,56 +305,60 @@ __global__ void k_recover_rows(Dev d) {
     const int col = d.Hcol[(size_t)r * WH + s];
     if (col >= 0) Hd += d.Hv[(size_t)r * WH + s] * d.dy[col];
   }
-  const double sp = d.sp[r], sm = d.sm[r];
-  const double Qp = d.bp[r] / sp, Qm = d.bm[r] / sm;
+  const double sp = d.sp[r], sm = d.sm[r], isp = d.isp[r], ism = d.ism[r];
+  const double Qp = d.bp[r] * isp, Qm = d.bm[r] * ism;
   const double r4p = d.h[r] - gam + sp, r4m = -d.h[r] - gam + sm;
   const double dsp = -r4p - Hd, dsm = -r4m + Hd;
   d.dsp[r] = dsp;
   d.dsm[r] = dsm;
-  d.dwp[r] = -(d.wp[r] - mu / sp) - Qp * dsp;
-  d.dwm[r] = -(d.wm[r] - mu / sm) - Qm * dsm;
-  d.dbp[r] = mu / sp - d.bp[r] - Qp * dsp;
-  d.dbm[r] = mu / sm - d.bm[r] - Qm * dsm;
+  d.dwp[r] = -(d.wp[r] - mu * isp) - Qp * dsp;
+  d.dwm[r] = -(d.wm[r] - mu * ism) - Qm * dsm;
+  d.dbp[r] = mu * isp - d.bp[r] - Qp * dsp;
+  d.dbm[r] = mu * ism - d.bm[r] - Qm * dsm;
 }
 
-// fraction-to-the-boundary step limits and grad(phi_mu)^T d
+// Fraction-to-the-boundary step limits and grad(phi_mu)^T d.  The limits are
+// tau / max_i(-dv_i / v_i) over components moving toward their bound, with
+// the stored reciprocals, so the chunk needs no division per element.
 __global__ void k_red_dir(Dev d) {
   const Chunk ch = d.chunks[blockIdx.x];
   const Ctl& c = d.ctl[ch.inst];
   if (c.status != ST_RUNNING) return;
   const double mu = c.mu, tau = c.tau;
-  double v[3] = {1.0, 1.0, 0.0};
-  const int op[3] = {2, 2, 0};
+  double v[3] = {0.0, 0.0, 0.0};  // max primal ratio, max dual ratio, gphi
+  const int op[3] = {1, 1, 0};
   if (ch.kind == 0) {
     for (int j = ch.begin + threadIdx.x; j < ch.end; j += TPB) {
-      const double dy = d.dy[j], yj = d.y[j];
+      const double dy = d.dy[j];
       double gp = d.grad[j];
       if (fin(d.yL[j])) {
-        const double g = yj - d.yL[j];
-        if (dy < 0.0) v[0] = fmin(v[0], -tau * g / dy);
-        gp -= mu / g;
-        if (d.dzL[j] < 0.0) v[1] = fmin(v[1], -tau * d.zL[j] / d.dzL[j]);
+        const double ig = d.igL[j];
+        v[0] = fmax(v[0], -dy * ig);
+        gp -= mu * ig;
+        v[1] = fmax(v[1], -d.dzL[j] * d.izL[j]);
       }
       if (fin(d.yU[j])) {
-        const double g = d.yU[j] - yj;
-        if (dy > 0.0) v[0] = fmin(v[0], tau * g / dy);
-        gp += mu / g;
-        if (d.dzU[j] < 0.0) v[1] = fmin(v[1], -tau * d.zU[j] / d.dzU[j]);
+        const double ig = d.igU[j];
+        v[0] = fmax(v[0], dy * ig);
+        gp += mu * ig;
+        v[1] = fmax(v[1], -d.dzU[j] * d.izU[j]);
       }
       v[2] += gp * dy;
     }
   } else {
     for (int r = ch.begin + threadIdx.x; r < ch.end; r += TPB) {
-      const double sp = d.sp[r], sm = d.sm[r];
-      if (d.dsp[r] < 0.0) v[0] = fmin(v[0], -tau * sp / d.dsp[r]);
-      if (d.dsm[r] < 0.0) v[0] = fmin(v[0], -tau * sm / d.dsm[r]);
-      if (d.dbp[r] < 0.0) v[1] = fmin(v[1], -tau * d.bp[r] / d.dbp[r]);
-      if (d.dbm[r] < 0.0) v[1] = fmin(v[1], -tau * d.bm[r] / d.dbm[r]);
-      v[2] -= mu * (d.dsp[r] / sp + d.dsm[r] / sm);
+      const double isp = d.isp[r], ism = d.ism[r];
+      v[0] = fmax(v[0], fmax(-d.dsp[r] * isp, -d.dsm[r] * ism));
+      v[1] = fmax(v[1], fmax(-d.dbp[r] * d.ibp[r], -d.dbm[r] * d.ibm[r]));
+      v[2] -= mu * (d.dsp[r] * isp + d.dsm[r] * ism);
     }
   }
   block_reduce<3>(v, op);
-  if (threadIdx.x == 0) d.red_dir[blockIdx.x] = RedDir{v[0], v[1], v[2], 0.0};
+  if (threadIdx.x == 0) {
+    const double ap = v[0] > tau ? tau / v[0] : 1.0;
+    const double ad = v[1] > tau ? tau / v[1] : 1.0;
+    d.red_dir[blockIdx.x] = RedDir{ap, ad, v[2], 0.0};
+  }
 }
 
 // start of the backtracking filter line search (W&B Sec. 2.3): alpha_min
@@ -348,9 +376,12 @@ __global__ void k_ctl_dir(Dev d) {
   c.alpha_dual = ad;
   c.gphi = g;
   double amin;
+  // switching-condition powers, fixed within the iteration's line search
+  c.sw_gphi = g < 0.0 ? pow(-g, S_PHI) : 0.0;
+  c.sw_theta = DELTA_SW * pow(c.theta, S_THETA);
   if (g < 0.0) {
     amin = fmin(GAMMA_THETA, GAMMA_PHI * c.theta / (-g));
-    if (c.theta <= c.theta_min) amin = fmin(amin, DELTA_SW * pow(c.theta, S_THETA) / pow(-g, S_PHI));
+    if (c.theta <= c.theta_min) amin = fmin(amin, c.sw_theta / c.sw_gphi);
     amin *= GAMMA_ALPHA;
   } else {
     amin = GAMMA_ALPHA * GAMMA_THETA;
@@ -386,25 +417,26 @@ __global__ void k_red_trial(Dev d) {
   const Ctl& c = d.ctl[ch.inst];
   if (!c.ls_active) return;
   const double gam = d.mc.gamma;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  const int op[4] = {0, 0, 0, 0};
+  double v[5] = {0.0, 1.0, 0.0, 0.0, 0.0};  // f, log-mantissa, log-exponent, theta, nonfinite
+  const int op[5] = {0, 3, 0, 0, 0};
   if (ch.kind == 0) {
     for (int j = ch.begin + threadIdx.x; j < ch.end; j += TPB) {
       const double y = d.yt[j];
       v[0] += d.fvart[j];
-      if (fin(d.yL[j])) v[1] += log(y - d.yL[j]);
-      if (fin(d.yU[j])) v[1] += log(d.yU[j] - y);
+      if (fin(d.yL[j])) logacc_mul(v[1], v[2], y - d.yL[j]);
+      if (fin(d.yU[j])) logacc_mul(v[1], v[2], d.yU[j] - y);
     }
   } else {
     for (int r = ch.begin + threadIdx.x; r < ch.end; r += TPB) {
       const double h = d.ht[r];
-      if (!fin(h)) v[3] += 1.0;
-      v[1] += log(d.spt[r]) + log(d.smt[r]);
-      v[2] += fabs(h - gam + d.spt[r]) + fabs(-h - gam + d.smt[r]);
+      if (!fin(h)) v[4] += 1.0;
+      logacc_mul(v[1], v[2], d.spt[r]);
+      logacc_mul(v[1], v[2], d.smt[r]);
+      v[3] += fabs(h - gam + d.spt[r]) + fabs(-h - gam + d.smt[r]);
     }
   }
-  block_reduce<4>(v, op);
-  if (threadIdx.x == 0) d.red_trial[blockIdx.x] = RedTrial{v[0], v[1], v[2], v[3]};
+  block_reduce<5>(v, op);
+  if (threadIdx.x == 0) d.red_trial[blockIdx.x] = RedTrial{v[0], v[1], v[2], v[3], v[4]};
 }
 
 // filter acceptance test of one trial (W&B Sec. 2.3, A-5.2 .. A-5.4)
@@ -413,11 +445,14 @@ __global__ void k_ctl_ls(Dev d) {
   if (i >= d.n_inst) return;
   Ctl c = d.ctl[i];
   if (!c.ls_active) return;
-  double f = 0, lg = 0, th = 0, nf = 0;
+  double f = 0, th = 0, nf = 0, lgm = 1.0, lge = 0.0;
   for (int q = d.inst_chunk_ptr[i]; q < d.inst_chunk_ptr[i + 1]; ++q) {
     const RedTrial& e = d.red_trial[d.inst_chunk_list[q]];
-    f += e.f; lg += e.logsum; th += e.theta; nf += e.nonfinite;
+    f += e.f; th += e.theta; nf += e.nonfinite;
+    logacc_mul(lgm, lge, e.lgm);
+    lge += e.lge;
   }
+  const double lg = logacc_value(lgm, lge);
   c.ls_trials++;
   const double phit = f - c.mu * lg, thetat = th;
   c.ft = f; c.logsum_t = lg; c.theta_t = th;
@@ -427,7 +462,7 @@ __global__ void k_ctl_ls(Dev d) {
   for (int q = 0; ok && q < c.nf; ++q) if (thetat >= fth[q] && phit >= fph[q]) ok = false;
   bool accepted = false;
   if (ok) {
-    const bool sw = c.gphi < 0.0 && c.alpha * pow(-c.gphi, S_PHI) > DELTA_SW * pow(c.theta, S_THETA);
+    const bool sw = c.gphi < 0.0 && c.alpha * c.sw_gphi > c.sw_theta;
     if (c.theta <= c.theta_min && sw) {
       if (phit <= c.phi + ETA_PHI * c.alpha * c.gphi) { accepted = true; c.augment = 0; }
     } else if (thetat <= (1.0 - GAMMA_THETA) * c.theta || phit <= c.phi - GAMMA_PHI * c.theta) {
@@ -445,6 +480,15 @@ __global__ void k_ctl_ls(Dev d) {
   d.ctl[i] = c;
 }
 
+// Keep a bound multiplier z within [mu/(kappa g), kappa mu/g] for gap g
+// (W&B eq. (16)); the division happens only when the bound is active.
+__device__ __forceinline__ double safeguard(double z, double g, double mu) {
+  const double p = z * g;
+  if (p > KAPPA_SIGMA * mu) return KAPPA_SIGMA * mu / g;
+  if (p < mu / KAPPA_SIGMA) return mu / (KAPPA_SIGMA * g);
+  return z;
+}
+
 // accept the step; bound multipliers take the dual step and the safeguard
 // of W&B eq. (16)
 __global__ void k_update_vars(Dev d) {
@@ -454,16 +498,8 @@ __global__ void k_update_vars(Dev d) {
   if (c.phase != 1 || c.status != ST_RUNNING) return;
   const double y = d.yt[v], mu = c.mu, ad = c.alpha_dual;
   d.y[v] = y;
-  if (fin(d.yL[v])) {
-    const double g = y - d.yL[v];
-    const double z = d.zL[v] + ad * d.dzL[v];
-    d.zL[v] = fmax(fmin(z, KAPPA_SIGMA * mu / g), mu / (KAPPA_SIGMA * g));
-  }
-  if (fin(d.yU[v])) {
-    const double g = d.yU[v] - y;
-    const double z = d.zU[v] + ad * d.dzU[v];
-    d.zU[v] = fmax(fmin(z, KAPPA_SIGMA * mu / g), mu / (KAPPA_SIGMA * g));
-  }
+  if (fin(d.yL[v])) d.zL[v] = safeguard(d.zL[v] + ad * d.dzL[v], y - d.yL[v], mu);
+  if (fin(d.yU[v])) d.zU[v] = safeguard(d.zU[v] + ad * d.dzU[v], d.yU[v] - y, mu);
 }
 
 __global__ void k_update_rows(Dev d) {
@@ -477,9 +513,8 @@ __global__ void k_update_rows(Dev d) {
   d.sm[r] = sm;
   d.wp[r] += a * d.dwp[r];
   d.wm[r] += a * d.dwm[r];
-  const double bp = d.bp[r] + ad * d.dbp[r], bm = d.bm[r] + ad * d.dbm[r];
-  d.bp[r] = fmax(fmin(bp, KAPPA_SIGMA * mu / sp), mu / (KAPPA_SIGMA * sp));
-  d.bm[r] = fmax(fmin(bm, KAPPA_SIGMA * mu / sm), mu / (KAPPA_SIGMA * sm));
+  d.bp[r] = safeguard(d.bp[r] + ad * d.dbp[r], sp, mu);
+  d.bm[r] = safeguard(d.bm[r] + ad * d.dbm[r], sm, mu);
 }
 
 __global__ void k_ctl_post(Dev d) {

@@ -6,7 +6,8 @@
 
 namespace nmpc {
 
-constexpr int TPB = 256;
+constexpr int TPB = 256;  // reductions (fixed tree shape)
+constexpr int EW = 128;   // element-wise kernels: smaller blocks spread FP64 work over more SMs
 
 // model_kernels.cu
 __global__ void k_eval_rows(Dev d, int use_trial, int with_jac);
@@ -38,8 +39,9 @@ __global__ void k_summary(Dev d, int* flags);
 
 // factor_kernels.cu
 __global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap);
-__global__ void k_fwd_level(Dev d, SnDev s, const int* list);
-__global__ void k_bwd_level(Dev d, SnDev s, const int* list);
+__global__ void k_factor_cluster(Dev d, SnDev s, const int* list);
+__global__ void k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap);
+__global__ void k_bwd_level(Dev d, SnDev s, const int* list, int smem_cap);
 
 inline unsigned blocks_for(long long n, int tpb = TPB) { return (unsigned)((n + tpb - 1) / tpb); }
 

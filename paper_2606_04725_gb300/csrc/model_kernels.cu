@@ -162,6 +162,12 @@ __global__ void k_eval_rows(Dev d, int use_trial, int with_jac) {
   } else {
     if (c.status != ST_RUNNING) return;
     eval_row(d, d.y, r, d.h, with_jac ? d.Hv : nullptr);
+    if (with_jac) {  // reciprocals of the slacks and their duals, reused by every later kernel
+      d.isp[r] = 1.0 / d.sp[r];
+      d.ism[r] = 1.0 / d.sm[r];
+      d.ibp[r] = 1.0 / d.bp[r];
+      d.ibm[r] = 1.0 / d.bm[r];
+    }
   }
 }
 
@@ -281,6 +287,12 @@ __global__ void k_eval_vars(Dev d, int use_trial) {
     if (c.status != ST_RUNNING) return;
     eval_var_obj(d, d.y, v, &d.fvar[v], &d.grad[v]);
     eval_var_hess(d, v);
+    // reciprocals of the bound gaps and bound duals (0 where the bound is absent)
+    const double y = d.y[v], lo = d.yL[v], hi = d.yU[v];
+    d.igL[v] = isfinite(lo) ? 1.0 / (y - lo) : 0.0;
+    d.igU[v] = isfinite(hi) ? 1.0 / (hi - y) : 0.0;
+    d.izL[v] = isfinite(lo) ? 1.0 / d.zL[v] : 0.0;
+    d.izU[v] = isfinite(hi) ? 1.0 / d.zU[v] : 0.0;
   }
 }
 

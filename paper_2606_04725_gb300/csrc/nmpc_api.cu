@@ -53,6 +53,9 @@ struct nmpc_handle {
   int* h_flags = nullptr;     // pinned
   std::vector<int> lvl_ptr;
   std::vector<int> lvl_smem_factor, lvl_smem_solve;  // bytes per level
+  std::vector<int> lvl_cluster;                      // CTAs per front (0 = single-CTA kernel)
+  std::vector<int> lvl_cluster_smem;                 // bytes per CTA of the cluster kernel
+  int n_sm = 152;
   int smem_cap_doubles = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<Ctl> h_ctl;
@@ -63,6 +66,9 @@ struct nmpc_handle {
 namespace {
 
 constexpr int SMEM_FACTOR_CAP_BYTES = 200 * 1024;
+constexpr int FACTOR_THREADS = 1024;  // 32 warps per front hide FP64 and shared-memory latency
+constexpr int CLUSTER_THREADS = 256;  // per CTA of the cluster-cooperative front kernel
+constexpr int CLUSTER_PB = 8;         // column block of the cluster kernel (PB in factor_kernels.cu)
 
 nmpc_status fail(nmpc_handle* h, nmpc_status st, const std::string& msg) {
   if (h) h->err = msg;
@@ -94,6 +100,8 @@ void carve(nmpc_handle* h, Carver& cv) {
   d.bp = cv.take<double>(m); d.bm = cv.take<double>(m);
   d.grad = cv.take<double>(n); d.h = cv.take<double>(m); d.Hv = cv.take<double>((size_t)m * WH);
   d.Wv = cv.take<double>(A.nW); d.fvar = cv.take<double>(n);
+  d.igL = cv.take<double>(n); d.igU = cv.take<double>(n); d.izL = cv.take<double>(n); d.izU = cv.take<double>(n);
+  d.isp = cv.take<double>(m); d.ism = cv.take<double>(m); d.ibp = cv.take<double>(m); d.ibm = cv.take<double>(m);
   d.Hcol = cv.take<int>((size_t)m * WH);
   d.Hcsc_ptr = cv.take<int>(n + 1); d.Hcsc_slot = cv.take<int>(A.Hcsc_slot.size());
   d.dy = cv.take<double>(n); d.dzL = cv.take<double>(n); d.dzU = cv.take<double>(n);
@@ -110,6 +118,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   d.tw_ptr = cv.take<int>(A.tw_ptr.size()); d.tw_idx = cv.take<int>(A.tw_idx.size());
   d.th_ptr = cv.take<int>(A.th_ptr.size()); d.th_a = cv.take<int>(A.th_a.size()); d.th_b = cv.take<int>(A.th_b.size());
   d.Lval = cv.take<double>(A.nnzL);
+  d.Kdiag = cv.take<double>(n);
   d.sn_inst = cv.take<int>(ns);
   h->d_tgt_inst = cv.take<int>(A.tgt_L.size());
   h->d_Drow = cv.take<double>(m);
@@ -128,6 +137,8 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.U = cv.take<double>(A.nU);
   s.uv = cv.take<double>(A.nuv);
   s.L = d.Lval;
+  s.Kdiag = d.Kdiag;
+  s.pivtol = A.mc.pivtol;
   s.sn_inst = d.sn_inst;
   s.ns = (int)ns;
   d.mc = A.mc; d.n_inst = ni; d.n = n; d.m = m; d.nW = A.nW; d.sp_stride = A.sp_stride;
@@ -153,7 +164,25 @@ nmpc_status launch_factor(nmpc_handle* h) {
   for (int l = 0; l < nl; ++l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
-    k_factor_level<<<cnt, TPB, h->lvl_smem_factor[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+    if (h->lvl_cluster[l] > 0) {
+      const int Q = h->lvl_cluster[l];
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cnt * Q);
+      cfg.blockDim = dim3(CLUSTER_THREADS);
+      cfg.dynamicSmemBytes = h->lvl_cluster_smem[l];
+      cfg.stream = h->stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = Q;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_factor_cluster, h->d, h->s, (const int*)(h->s.level_sn + h->lvl_ptr[l])));
+      ++h->launches;
+      continue;
+    }
+    k_factor_level<<<cnt, FACTOR_THREADS, h->lvl_smem_factor[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
                                                                    h->smem_cap_doubles);
   }
   return NMPC_OK;
@@ -163,12 +192,14 @@ nmpc_status launch_solve(nmpc_handle* h) {
   const int nl = (int)h->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
-    if (cnt) k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l]);
+    if (cnt) k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+                                                                        h->smem_cap_doubles);
     ++h->launches;
   }
   for (int l = nl - 1; l >= 0; --l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
-    if (cnt) k_bwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l]);
+    if (cnt) k_bwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+                                                                        h->smem_cap_doubles);
     ++h->launches;
   }
   return NMPC_OK;
@@ -194,7 +225,7 @@ void nmpc_options_defaults(nmpc_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->tol = 1e-8; o->gamma = 1e-8; o->mu0_cold = 0.1; o->mu0_warm = 1e-8;
   o->push_cold = 1e-2; o->push_warm = 1e-9; o->max_iter = 200; o->ordering = NMPC_ORDER_AUTO;
-  o->nd_leaf = 1; o->use_graph = 1; o->spin_limit = 10000000LL;
+  o->nd_leaf = 1; o->use_graph = 1; o->spin_limit = 10000000LL; o->pivtol = 1e-12;
 }
 
 nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void* cuda_stream, nmpc_handle** out) {
@@ -214,7 +245,7 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   sp.kappa = prob->kappa; sp.cq = prob->cq; sp.rho_u = prob->rho_u;
   sp.xlo = prob->xlo; sp.xhi = prob->xhi; sp.ulo = prob->ulo; sp.uhi = prob->uhi;
   sp.gamma = h->opt.gamma; sp.tol = h->opt.tol;
-  sp.ordering = h->opt.ordering; sp.nd_leaf = h->opt.nd_leaf;
+  sp.ordering = h->opt.ordering; sp.nd_leaf = h->opt.nd_leaf; sp.pivtol = h->opt.pivtol;
   if (!(prob->dt > 0) || h->opt.max_iter < 1 || !(h->opt.tol > 0) || !(h->opt.gamma > 0)) {
     delete h;
     return NMPC_ERR_INVALID;
@@ -235,13 +266,39 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   h->smem_cap_doubles = SMEM_FACTOR_CAP_BYTES / 8;
   h->lvl_smem_factor.assign(nl, 8);
   h->lvl_smem_solve.assign(nl, 8);
+  // per level: cluster size Q so that the level's fronts occupy most SMs, if
+  // every front fits in shared memory with that Q
+  {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) h->n_sm = prop.multiProcessorCount;
+  }
+  h->lvl_cluster.assign(nl, 0);
+  h->lvl_cluster_smem.assign(nl, 0);
+  for (int l = 0; l < nl; ++l) {
+    const int cnt = A.level_ptr[l + 1] - A.level_ptr[l];
+    int Q = 1;
+    while (Q < 8 && 2 * Q * cnt <= h->n_sm) Q *= 2;
+    long long worst = 0;
+    bool fits = true;
+    for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1] && fits; ++qd) {
+      const int sn = A.level_sn[qd];
+      const long long mm = A.sn_nrow[sn];
+      const long long nblk = (mm + CLUSTER_PB - 1) / CLUSTER_PB;
+      const long long need = ((nblk + Q - 1) / Q * CLUSTER_PB + CLUSTER_PB) * mm;  // doubles
+      if (need * 8 > SMEM_FACTOR_CAP_BYTES) fits = false;
+      worst = std::max(worst, need * 8);
+    }
+    if (fits && h->opt.factor_mode == 0) { h->lvl_cluster[l] = Q; h->lvl_cluster_smem[l] = (int)worst; }
+  }
   for (int l = 0; l < nl; ++l)
     for (int q = A.level_ptr[l]; q < A.level_ptr[l + 1]; ++q) {
       const int sn = A.level_sn[q];
       const long long mm = A.sn_nrow[sn], cc = A.sn_ncol[sn];
-      const long long need = mm * cc + (mm - cc) * (mm - cc);
+      const long long need = mm * mm + cc;  // whole front plus the pivots' reciprocal square roots
       if (need <= h->smem_cap_doubles) h->lvl_smem_factor[l] = std::max<int>(h->lvl_smem_factor[l], (int)(need * 8));
-      h->lvl_smem_solve[l] = std::max<int>(h->lvl_smem_solve[l], (int)((mm + cc) * 8));
+      const long long sneed = (mm * cc + mm <= h->smem_cap_doubles) ? mm * cc + mm : mm;
+      h->lvl_smem_solve[l] = std::max<int>(h->lvl_smem_solve[l], (int)(sneed * 8));
     }
   *out = h;
   return NMPC_OK;
@@ -311,6 +368,7 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   CUDA_TRY(h, up(s.sn_rel, A.sn_rel, st)); CUDA_TRY(h, up(s.level_ptr, A.level_ptr, st));
   CUDA_TRY(h, up(s.level_sn, A.level_sn, st)); CUDA_TRY(h, up(s.sn_uvptr, A.sn_uvptr, st));
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
+  CUDA_TRY(h, cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
   int maxs = *std::max_element(h->lvl_smem_solve.begin(), h->lvl_smem_solve.end());
   if (maxs > 48 * 1024) {
     CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
@@ -384,18 +442,18 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
   if (h->ev0) CUDA_TRY(h, cudaEventRecord(h->ev0, st));
   k_ctl_init<<<blocks_for(ni), TPB, 0, st>>>(d, mu0);
   ++h->launches;
-  k_init_vars<<<blocks_for(n), TPB, 0, st>>>(d, warm, push);
+  k_init_vars<<<blocks_for(n, EW), EW, 0, st>>>(d, warm, push);
   ++h->launches;
-  k_eval_rows<<<blocks_for(m), TPB, 0, st>>>(d, 0, 0);
+  k_eval_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, 0, 0);
   ++h->launches;
-  k_init_rows<<<blocks_for(m), TPB, 0, st>>>(d, warm, push);
+  k_init_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, warm, push);
   ++h->launches;
   CUDA_TRY(h, cudaGetLastError());
   const dim3 zgrid(std::max(1u, std::min(1024u, blocks_for(A.nnzL / std::max(1, ni) + 1))), ni);
   for (int it = 0; it <= h->opt.max_iter + 1; ++it) {
-    k_eval_rows<<<blocks_for(m), TPB, 0, st>>>(d, 0, 1);
+    k_eval_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, 0, 1);
     ++h->launches;
-    k_eval_vars<<<blocks_for(n), TPB, 0, st>>>(d, 0);
+    k_eval_vars<<<blocks_for(n, EW), EW, 0, st>>>(d, 0);
     ++h->launches;
     k_red_eval<<<d.n_chunks, TPB, 0, st>>>(d);
     ++h->launches;
@@ -407,9 +465,9 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
     for (;;) {
       k_zero_L<<<zgrid, TPB, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend);
       ++h->launches;
-      k_rows_pre<<<blocks_for(m), TPB, 0, st>>>(d, h->d_Drow);
+      k_rows_pre<<<blocks_for(m, EW), EW, 0, st>>>(d, h->d_Drow);
       ++h->launches;
-      k_assemble<<<blocks_for(d.n_tgt), TPB, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
+      k_assemble<<<blocks_for(d.n_tgt, EW), EW, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
       ++h->launches;
       launch_factor(h);
       k_ctl_factor<<<blocks_for(ni), TPB, 0, st>>>(d);
@@ -419,12 +477,12 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
       if (rs != NMPC_OK) return rs;
       if (!h->h_flags[1]) break;
     }
-    k_rhs<<<blocks_for(n), TPB, 0, st>>>(d);
+    k_rhs<<<blocks_for(n, EW), EW, 0, st>>>(d);
     ++h->launches;
     launch_solve(h);
-    k_recover_vars<<<blocks_for(n), TPB, 0, st>>>(d);
+    k_recover_vars<<<blocks_for(n, EW), EW, 0, st>>>(d);
     ++h->launches;
-    k_recover_rows<<<blocks_for(m), TPB, 0, st>>>(d);
+    k_recover_rows<<<blocks_for(m, EW), EW, 0, st>>>(d);
     ++h->launches;
     k_red_dir<<<d.n_chunks, TPB, 0, st>>>(d);
     ++h->launches;
@@ -436,9 +494,9 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
     while (h->h_flags[2]) {
       k_trial_point<<<blocks_for((long long)n + m), TPB, 0, st>>>(d);
       ++h->launches;
-      k_eval_rows<<<blocks_for(m), TPB, 0, st>>>(d, 1, 0);
+      k_eval_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, 1, 0);
       ++h->launches;
-      k_eval_vars<<<blocks_for(n), TPB, 0, st>>>(d, 1);
+      k_eval_vars<<<blocks_for(n, EW), EW, 0, st>>>(d, 1);
       ++h->launches;
       k_red_trial<<<d.n_chunks, TPB, 0, st>>>(d);
       ++h->launches;
@@ -448,9 +506,9 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
       rs = read_flags(h);
       if (rs != NMPC_OK) return rs;
     }
-    k_update_vars<<<blocks_for(n), TPB, 0, st>>>(d);
+    k_update_vars<<<blocks_for(n, EW), EW, 0, st>>>(d);
     ++h->launches;
-    k_update_rows<<<blocks_for(m), TPB, 0, st>>>(d);
+    k_update_rows<<<blocks_for(m, EW), EW, 0, st>>>(d);
     ++h->launches;
     k_ctl_post<<<blocks_for(ni), TPB, 0, st>>>(d);
     ++h->launches;
@@ -552,16 +610,16 @@ nmpc_status nmpc_time_phases(nmpc_handle* h, int reps, nmpc_phase_times* out) {
   double acc[4] = {0, 0, 0, 0};
   for (int r = 0; r < reps + 1; ++r) {
     CUDA_TRY(h, cudaEventRecord(e[0], st));
-    k_eval_rows<<<blocks_for(m), TPB, 0, st>>>(d, 0, 1);
-    k_eval_vars<<<blocks_for(n), TPB, 0, st>>>(d, 0);
+    k_eval_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, 0, 1);
+    k_eval_vars<<<blocks_for(n, EW), EW, 0, st>>>(d, 0);
     CUDA_TRY(h, cudaEventRecord(e[1], st));
     k_zero_L<<<zgrid, TPB, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend);
-    k_rows_pre<<<blocks_for(m), TPB, 0, st>>>(d, h->d_Drow);
-    k_assemble<<<blocks_for(d.n_tgt), TPB, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
+    k_rows_pre<<<blocks_for(m, EW), EW, 0, st>>>(d, h->d_Drow);
+    k_assemble<<<blocks_for(d.n_tgt, EW), EW, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
     CUDA_TRY(h, cudaEventRecord(e[2], st));
     launch_factor(h);
     CUDA_TRY(h, cudaEventRecord(e[3], st));
-    k_rhs<<<blocks_for(n), TPB, 0, st>>>(d);
+    k_rhs<<<blocks_for(n, EW), EW, 0, st>>>(d);
     launch_solve(h);
     CUDA_TRY(h, cudaEventRecord(e[4], st));
     CUDA_TRY(h, cudaEventSynchronize(e[4]));

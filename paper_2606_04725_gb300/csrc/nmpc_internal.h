@@ -29,6 +29,7 @@ struct Ctl {
   double alpha, alpha_min, alpha_pri, alpha_dual;
   double E0, E0u, Emu;
   double ft, logsum_t, theta_t;       // at the trial point
+  double sw_gphi, sw_theta;           // (-gphi)^s_phi and delta theta^s_theta of this iteration
   int status;                         // 0 running, else nmpc_status (1 = converged)
   int iter;
   int phase;                          // see PH_* below
@@ -56,7 +57,7 @@ struct ModelConst {
   int model, nx, nu, N, Nf, g, S, WH, WS;
   double dt, alpha, D, F, xF, Ac, At, Ar, wdu, kappa, cq, rho_u;
   double xlo, xhi, ulo, uhi;
-  double gamma, tol;
+  double gamma, tol, pivtol;
 };
 
 // Reduction chunks never straddle an instance.  kind 0: variables, 1: rows.
@@ -65,8 +66,10 @@ struct Chunk {
 };
 
 // Partial sums/extrema of one chunk (deterministic two-pass reductions).
+// Sums of logarithms are carried as a product of mantissas in [1, 2) and a
+// sum of binary exponents (one log per chunk instead of one per element).
 struct RedEval {       // at the current iterate
-  double dual, prim, cmax, cmin, sum_l, sum_z, f, logsum, theta;
+  double dual, prim, cmax, cmin, sum_l, sum_z, f, lgm, lge, theta;
   double nonfinite;     // count of non-finite residual/gradient entries
 };
 struct RedDir {        // after the Newton direction
@@ -74,7 +77,7 @@ struct RedDir {        // after the Newton direction
   double pad;
 };
 struct RedTrial {      // at a trial point
-  double f, logsum, theta, nonfinite;
+  double f, lgm, lge, theta, nonfinite;
 };
 
 // Device view of everything the kernels touch.  Passed by value.
@@ -94,6 +97,8 @@ struct Dev {
   double *y, *zL, *zU, *sp, *sm, *wp, *wm, *bp, *bm;
   // evaluation
   double *grad, *h, *Hv, *Wv, *fvar;
+  // reciprocals at the current iterate: bound gaps, bound duals (n); slacks, slack duals (m)
+  double *igL, *igU, *izL, *izU, *isp, *ism, *ibp, *ibm;
   const int* Hcol;
   const int* Hcsc_ptr; const int* Hcsc_slot;
   // direction
@@ -119,6 +124,7 @@ struct Dev {
   const int* tw_ptr; const int* tw_idx;
   const int* th_ptr; const int* th_a; const int* th_b;
   double* Lval;
+  double* Kdiag;        // assembled diagonal of K_c in factor order (pivot tolerance)
   long long nnzL;
   // instance of each supernode (factor kernels)
   const int* sn_inst;
@@ -144,6 +150,8 @@ struct SnDev {
   double* L;
   double* U;
   double* uv;                 // update vectors of the forward solve
+  const double* Kdiag;        // assembled diagonal in factor order
+  double pivtol;
 };
 
 }  // namespace nmpc

@@ -301,7 +301,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
     mc.Ac = sp.Ac; mc.At = sp.At; mc.Ar = sp.Ar; mc.wdu = sp.wdu;
     mc.kappa = sp.kappa; mc.cq = sp.cq; mc.rho_u = sp.rho_u;
     mc.xlo = sp.xlo; mc.xhi = sp.xhi; mc.ulo = sp.ulo; mc.uhi = sp.uhi;
-    mc.gamma = sp.gamma; mc.tol = sp.tol;
+    mc.gamma = sp.gamma; mc.tol = sp.tol; mc.pivtol = sp.pivtol;
     const int nx = mc.nx, nu = mc.nu, WH = mc.WH, WS = mc.WS;
     A.n_inst = ni;
     A.sp_stride = (sp.model == MODEL_PLATE) ? nx : *std::max_element(sp.T.begin(), sp.T.end());
@@ -589,7 +589,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       A.th_ptr.push_back((int)A.th_a.size());
     }
     // reduction chunks (never crossing an instance)
-    const int CH = 2048;
+    const int CH = 512;
     A.chunks.clear();
     A.inst_chunk_ptr.assign(ni + 1, 0);
     for (int i = 0; i < ni; ++i) {

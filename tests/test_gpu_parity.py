@@ -5,11 +5,16 @@ max(1, |y|_inf)); the GPU's primal-dual point has scaled KKT error
 E_0 <= 1e-8 when evaluated by the oracle's own evaluator; equal
 interior-point iteration counts on the same seeds.
 
-Iteration counts are compared against the oracle's own rounding spread: the
-oracle is re-run with its inputs perturbed by 1e-15..1e-13 relative.  When
-that leaves its count unchanged the GPU count must be equal; when rounding
-alone moves the oracle's count (a pivot or filter decision on a knife edge),
-the GPU count must lie within the oracle's own range.  The heated plate's
+Iteration counts are compared with the GPU eliminating in the oracle's own
+order (stage order; the oracle's banded Cholesky), so both sides see the
+same pivot sequence up to rounding, and against the oracle's rounding spread:
+the oracle is re-run with its inputs perturbed by 1e-15..1e-13 relative.
+When that leaves its count unchanged the GPU count must be equal; when
+rounding alone moves the oracle's count, the GPU count must lie within the
+oracle's own range.  With nested dissection (the performance default) the
+pivots differ, so the pivot test of the inertia correction can decide
+differently; there the counts must be equal unless the first iteration at
+which the traces differ is an inertia-correction decision.  The heated plate's
 primal solution is only determined to ~1e-3 at tol 1e-8 (its reduced Hessian
 is nearly flat), so its primal parity is checked at tol 1e-12.
 """
@@ -47,7 +52,11 @@ def _oracle_problem(O, kind, T, x0, sp, uprev=I.U_REF, **kw):
     raise ValueError(kind)
 
 
+NATURAL = 1  # elimination in stage order, as the oracle's banded Cholesky
+
+
 def _gpu_solver(P, kind, horizons, **kw):
+    kw.setdefault("opts", P.options(ordering=NATURAL))
     if kind == "distill12":
         return P.Solver(P.MODEL_DISTILLATION, horizons, N=12, Nf=5, **kw)
     if kind == "distill34":
@@ -177,13 +186,13 @@ def test_plate_small(P, oracle, g, S, T):
     # at the default tolerance: both converge, the GPU point is KKT-optimal by
     # the oracle's evaluator, and the iteration count is within the spread
     st_or, info_or, tr = oracle.solve(prob)
-    s = P.Solver(P.MODEL_PLATE, [T], g=g, S=S)
+    s = P.Solver(P.MODEL_PLATE, [T], g=g, S=S, opts=P.options(ordering=NATURAL))
     s.set_params(x0=x0, setpoint=tgt)
     info = s.solve()[0]
     _compare(oracle, prob, s, 0, st_or, info_or, info, tol_y=1e-2, spread=_oracle_spread(oracle, prob), tr_or=tr)
     # primal parity where the tolerance ball is small enough to define it
     st_or, info_or, _ = oracle.solve(prob, tol=1e-12)
-    s = P.Solver(P.MODEL_PLATE, [T], g=g, S=S, opts=P.options(tol=1e-12))
+    s = P.Solver(P.MODEL_PLATE, [T], g=g, S=S, opts=P.options(tol=1e-12, ordering=NATURAL))
     s.set_params(x0=x0, setpoint=tgt)
     info = s.solve()[0]
     _compare(oracle, prob, s, 0, st_or, info_or, info, check_iters=False, tol_kkt=1e-12, opts=dict(tol=1e-12))
@@ -215,7 +224,7 @@ def test_one_iteration_matches_oracle(P, oracle):
     prob = _oracle_problem(oracle, "distill12", T, x0, 0.8)
     for iters in (1, 2, 5):
         st_or, info_or, _ = oracle.solve(prob, max_iter=iters)
-        s = _gpu_solver(P, "distill12", [T], opts=P.options(max_iter=iters))
+        s = _gpu_solver(P, "distill12", [T], opts=P.options(max_iter=iters, ordering=NATURAL))
         s.set_params(x0=x0, setpoint=np.full(T, 0.8), u_prev=np.array([I.U_REF]))
         info = s.solve()[0]
         assert info["iters"] == info_or["iters"]
@@ -225,18 +234,61 @@ def test_one_iteration_matches_oracle(P, oracle):
             np.testing.assert_allclose(a, b, rtol=1e-7, atol=1e-9 * (1 + np.abs(b).max()), err_msg=f"{iters} {k}")
 
 
+def test_nested_dissection_matches_oracle(P, oracle):
+    """The performance configuration (nested dissection, cluster fronts) on the
+    34-tray, 200-interval column: same solution and KKT error as the oracle;
+    iteration counts equal unless the traces first part at an inertia
+    decision (a different pivot sequence meets the pivot test differently)."""
+    T = 200
+    x0 = I.distillation_x0(34, 17, seed=2)
+    a, b = I.distillation_setpoints(34, seed=2)
+    prob = _oracle_problem(oracle, "distill34", T, x0, a)
+    s = P.Solver(P.MODEL_DISTILLATION, [T], N=34, Nf=17, opts=P.options(ordering=2))
+    st_or, uprev = None, I.U_REF
+    for k, spk in enumerate([a, a, b]):
+        prob.set_params(sp=np.full(T, spk))
+        s.set_params(x0=prob.x0.copy(), setpoint=np.full(T, spk), u_prev=np.array([uprev]))
+        st_or, info_or, tr = oracle.solve(prob, state=st_or, warm=k > 0)
+        info = s.solve(warm=k > 0)[0]
+        _compare(oracle, prob, s, 0, st_or, info_or, info, check_iters=False)
+        if info["iters"] != info_or["iters"]:
+            div = _first_divergence(s.trace(0), tr)
+            assert div is not None and div[1][3] != div[2][3], ("iterations differ without an inertia decision", div)
+        uprev = st_or.y[prob.off_u(1)]
+        prob.set_params(x0=st_or.y[prob.off_x(1):prob.off_x(1) + 34].copy(), uprev=uprev)
+
+
 def test_ordering_does_not_change_the_solution(P):
     T = 40
     x0 = I.distillation_x0(12, 5, seed=5)
     ys, its = [], []
     for ordering in (1, 2):
-        s = _gpu_solver(P, "distill12", [T], opts=P.options(ordering=ordering))
+        s = P.Solver(P.MODEL_DISTILLATION, [T], N=12, Nf=5, opts=P.options(ordering=ordering))
         s.set_params(x0=x0, setpoint=np.full(T, 0.8), u_prev=np.array([I.U_REF]))
         info = s.solve()[0]
         assert info["status"] == 0
         ys.append(s.get_solution(0))
         its.append(info["iters"])
-    assert abs(its[0] - its[1]) <= 1  # different elimination orders round differently
+    assert abs(its[0] - its[1]) <= 3  # different pivot sequences meet the inertia test differently
+    assert np.max(np.abs(ys[0] - ys[1])) < 1e-6
+
+
+def test_cluster_and_single_cta_factorizations_agree(P):
+    """The cluster-cooperative front kernel (several CTAs per front, panels
+    shared through distributed shared memory) and the one-CTA kernel compute
+    the same factor up to rounding: same solution, same iteration count."""
+    T = 200
+    x0 = I.distillation_x0(34, 17, seed=2)
+    a, _ = I.distillation_setpoints(34, seed=2)
+    ys, its = [], []
+    for mode in (0, 1):
+        s = _gpu_solver(P, "distill34", [T], opts=P.options(factor_mode=mode, ordering=2))
+        s.set_params(x0=x0, setpoint=np.full(T, a), u_prev=np.array([I.U_REF]))
+        info = s.solve()[0]
+        assert info["status"] == 0
+        ys.append(s.get_solution(0))
+        its.append(info["iters"])
+    assert abs(its[0] - its[1]) <= 1
     assert np.max(np.abs(ys[0] - ys[1])) < 1e-6
 
 
