@@ -43,6 +43,16 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list);
 __global__ void k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap);
 __global__ void k_bwd_level(Dev d, SnDev s, const int* list, int smem_cap);
 
+// adjoint_kernels.cu
+__global__ void k_kmat_rows(Dev d, const double* Drow, const double* x, double* t, double* ta, int inst);
+__global__ void k_kmat_vars_residual(Dev d, const double* x, const double* t, const double* ta, const double* g,
+                                     double* out, double* scale, int inst);
+__global__ void k_to_factor_order(Dev d, const double* src, int inst);
+__global__ void k_from_factor_order(Dev d, double* x, int accumulate, int inst);
+__global__ void k_sens_out(Dev d, const double* v, const double* Drow, int inst, double* dx0, double* dsp);
+__global__ void k_ctl_select(Ctl* ctl, int n, int inst, int refactor);
+__global__ void k_resid_norms(Dev d, const double* r, const double* scale, int inst, unsigned long long* out);
+
 inline unsigned blocks_for(long long n, int tpb = TPB) { return (unsigned)((n + tpb - 1) / tpb); }
 
 }  // namespace nmpc

@@ -61,6 +61,7 @@ struct nmpc_handle {
   std::vector<Ctl> h_ctl;
   Ctl* d_ctl_save = nullptr;
   long long launches = 0;
+  double sens_residual = 0.0;  // relative residual of the last adjoint solve
 };
 
 namespace {
@@ -69,6 +70,7 @@ constexpr int SMEM_FACTOR_CAP_BYTES = 200 * 1024;
 constexpr int FACTOR_THREADS = 1024;  // 32 warps per front hide FP64 and shared-memory latency
 constexpr int CLUSTER_THREADS = 256;  // per CTA of the cluster-cooperative front kernel
 constexpr int CLUSTER_PB = 8;         // column block of the cluster kernel (PB in factor_kernels.cu)
+constexpr int SENS_REFINE = 6;        // refinement sweeps of the adjoint solve
 
 nmpc_status fail(nmpc_handle* h, nmpc_status st, const std::string& msg) {
   if (h) h->err = msg;
@@ -104,6 +106,8 @@ void carve(nmpc_handle* h, Carver& cv) {
   d.isp = cv.take<double>(m); d.ism = cv.take<double>(m); d.ibp = cv.take<double>(m); d.ibm = cv.take<double>(m);
   d.Hcol = cv.take<int>((size_t)m * WH);
   d.Hcsc_ptr = cv.take<int>(n + 1); d.Hcsc_slot = cv.take<int>(A.Hcsc_slot.size());
+  d.Wadj_ptr = cv.take<int>(n + 1); d.Wadj_slot = cv.take<int>(A.Wadj_slot.size());
+  d.Wadj_other = cv.take<int>(A.Wadj_other.size());
   d.dy = cv.take<double>(n); d.dzL = cv.take<double>(n); d.dzU = cv.take<double>(n);
   d.dsp = cv.take<double>(m); d.dsm = cv.take<double>(m); d.dwp = cv.take<double>(m); d.dwm = cv.take<double>(m);
   d.dbp = cv.take<double>(m); d.dbm = cv.take<double>(m); d.rowv = cv.take<double>(m);
@@ -334,6 +338,8 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   CUDA_TRY(h, up(d.yL, A.yL, st)); CUDA_TRY(h, up(d.yU, A.yU, st));
   CUDA_TRY(h, up(d.Hcol, A.Hcol, st)); CUDA_TRY(h, up(d.Hcsc_ptr, A.Hcsc_ptr, st));
   CUDA_TRY(h, up(d.Hcsc_slot, A.Hcsc_slot, st));
+  CUDA_TRY(h, up(d.Wadj_ptr, A.Wadj_ptr, st)); CUDA_TRY(h, up(d.Wadj_slot, A.Wadj_slot, st));
+  CUDA_TRY(h, up(d.Wadj_other, A.Wadj_other, st));
   CUDA_TRY(h, up(d.perm, A.perm, st)); CUDA_TRY(h, up(d.iperm, A.iperm, st));
   CUDA_TRY(h, up(d.chunks, ch, st)); CUDA_TRY(h, up(d.inst_chunk_ptr, A.inst_chunk_ptr, st));
   CUDA_TRY(h, up(d.inst_chunk_list, A.inst_chunk_list, st));
@@ -583,8 +589,102 @@ int nmpc_get_trace(nmpc_handle* h, int instance, double* out, int cap) {
   return iters;
 }
 
-nmpc_status nmpc_sensitivity(nmpc_handle* h, int, const double*, double*, double*, int) {
-  return fail(h, NMPC_ERR_INVALID, "adjoint sensitivity is not available in this build");
+nmpc_status nmpc_sensitivity(nmpc_handle* h, int instance, const double* dloss_dy, double* dloss_dx0,
+                             double* dloss_dsp, int on_device) {
+  if (!h || !h->bound) return fail(h, NMPC_ERR_INVALID, "handle not bound");
+  const Analysis& A = h->A;
+  if (instance < 0 || instance >= A.n_inst || !dloss_dy) return fail(h, NMPC_ERR_INVALID, "bad instance or gradient");
+  if (!h->have_solution) return fail(h, NMPC_NOT_SOLVED, "no converged point");
+  Dev& d = h->d;
+  cudaStream_t st = h->stream;
+  const int ni = A.n_inst, n = A.n, m = A.m;
+  const int vo = A.inst_voff[instance], ni_n = A.inst_n[instance];
+  const int nx = A.mc.nx;
+  const int sp_len = (A.mc.model == MODEL_PLATE) ? nx : A.inst_T[instance];
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  double* g = d.fvart;   // natural-order right-hand side (free between solves)
+  double* x = d.dy;      // adjoint solution v
+  double* r = d.yt;      // refinement residual
+  double* t = d.rowv;    // per-row products
+  double* ta = d.dwp;    // their absolute values (backward error)
+  double* sc = d.dzL;    // (|K||x|)_v + |g_v|
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_ctl_save, d.ctl, ni * sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
+  k_ctl_select<<<blocks_for(ni), TPB, 0, st>>>(d.ctl, ni, instance, 0);
+  ++h->launches;
+  // residual data at the converged point
+  k_eval_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, 0, 1);
+  k_eval_vars<<<blocks_for(n, EW), EW, 0, st>>>(d, 0);
+  k_rows_pre<<<blocks_for(m, EW), EW, 0, st>>>(d, h->d_Drow);
+  h->launches += 3;
+  CUDA_TRY(h, cudaMemsetAsync(g, 0, (size_t)n * sizeof(double), st));
+  CUDA_TRY(h, cudaMemcpyAsync(g + vo, dloss_dy, (size_t)ni_n * sizeof(double), kin, st));
+  // v = K_f^{-1} g, then refinement sweeps v += K_f^{-1} (g - K(z*) v) with the
+  // stored factor K_f; if the componentwise backward error stays above 1e-12
+  // (the slack weights changed too much in the last step), K(z*) is
+  // refactored in place (same symbolic analysis, delta_w = 0) and the
+  // refinement repeated.
+  unsigned long long* d_norms = reinterpret_cast<unsigned long long*>(h->d_flags);  // 16 bytes, free here
+  auto refine = [&](int sweeps) -> nmpc_status {
+    k_to_factor_order<<<blocks_for(n, EW), EW, 0, st>>>(d, g, instance);
+    launch_solve(h);
+    k_from_factor_order<<<blocks_for(n, EW), EW, 0, st>>>(d, x, 0, instance);
+    h->launches += 2;
+    for (int sweep = 0; sweep < sweeps; ++sweep) {
+      k_kmat_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, h->d_Drow, x, t, ta, instance);
+      k_kmat_vars_residual<<<blocks_for(n, EW), EW, 0, st>>>(d, x, t, ta, g, r, sc, instance);
+      k_to_factor_order<<<blocks_for(n, EW), EW, 0, st>>>(d, r, instance);
+      launch_solve(h);
+      k_from_factor_order<<<blocks_for(n, EW), EW, 0, st>>>(d, x, 1, instance);
+      h->launches += 4;
+    }
+    k_kmat_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, h->d_Drow, x, t, ta, instance);
+    k_kmat_vars_residual<<<blocks_for(n, EW), EW, 0, st>>>(d, x, t, ta, g, r, sc, instance);
+    CUDA_TRY(h, cudaMemsetAsync(d_norms, 0, 2 * sizeof(unsigned long long), st));
+    k_resid_norms<<<blocks_for(n, EW), EW, 0, st>>>(d, r, sc, instance, d_norms);
+    h->launches += 3;
+    return NMPC_OK;
+  };
+  auto rel_residual = [&](double* out) -> nmpc_status {
+    unsigned long long nb[2];
+    CUDA_TRY(h, cudaMemcpyAsync(nb, d_norms, sizeof(nb), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    std::memcpy(out, &nb[0], 8);  // componentwise backward error
+    return NMPC_OK;
+  };
+  nmpc_status rs = refine(SENS_REFINE);
+  if (rs != NMPC_OK) return rs;
+  double rel = 0.0;
+  if ((rs = rel_residual(&rel)) != NMPC_OK) return rs;
+  if (!(rel <= 1e-12)) {
+    k_ctl_select<<<blocks_for(ni), TPB, 0, st>>>(d.ctl, ni, instance, 1);
+    const dim3 zgrid(std::max(1u, std::min(1024u, blocks_for(A.nnzL / std::max(1, ni) + 1))), ni);
+    k_zero_L<<<zgrid, TPB, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend);
+    k_assemble<<<blocks_for(d.n_tgt, EW), EW, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
+    h->launches += 3;
+    launch_factor(h);
+    if ((rs = refine(SENS_REFINE)) != NMPC_OK) return rs;
+    if ((rs = rel_residual(&rel)) != NMPC_OK) return rs;
+  }
+  h->sens_residual = rel;
+  // parameter gradients, through the staging area when the caller's arrays are on the host
+  double* ox = dloss_dx0;
+  double* os = dloss_dsp;
+  if (!on_device) {
+    ox = dloss_dx0 ? h->d_stage : nullptr;
+    os = dloss_dsp ? h->d_stage + nx : nullptr;
+  }
+  k_sens_out<<<std::max(1u, blocks_for(std::max(nx, sp_len))), TPB, 0, st>>>(d, x, h->d_Drow, instance, ox, os);
+  ++h->launches;
+  CUDA_TRY(h, cudaGetLastError());
+  if (!on_device) {
+    if (dloss_dx0) CUDA_TRY(h, cudaMemcpyAsync(dloss_dx0, ox, (size_t)nx * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (dloss_dsp) CUDA_TRY(h, cudaMemcpyAsync(dloss_dsp, os, (size_t)sp_len * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(d.ctl, h->d_ctl_save, ni * sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
+  if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (!(rel <= 1e-8))
+    return fail(h, NMPC_INERTIA_FAIL, "adjoint system not solved to a backward error of 1e-8 (K at the solution not positive definite?)");
+  return NMPC_OK;
 }
 
 __global__ void k_ctl_force(Ctl* ctl, int n) {

@@ -101,6 +101,7 @@ struct Dev {
   double *igL, *igU, *izL, *izU, *isp, *ism, *ibp, *ibm;
   const int* Hcol;
   const int* Hcsc_ptr; const int* Hcsc_slot;
+  const int* Wadj_ptr; const int* Wadj_slot; const int* Wadj_other;
   // direction
   double *dy, *dzL, *dzU, *dsp, *dsm, *dwp, *dwm, *dbp, *dbm;
   double* rowv;         // per-row scratch (H^T v products)

@@ -458,6 +458,22 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       for (size_t s = 0; s < A.Hcol.size(); ++s) if (A.Hcol[s] >= 0) A.Hcsc_slot[fill[A.Hcol[s]]++] = (int)s;
     }
 
+    // per-variable adjacency of the Hessian slots (both triangles), for K x
+    A.Wadj_ptr.assign(n + 1, 0);
+    for (long long q = 0; q < nW; ++q)
+      if (Wi[q] >= 0) { A.Wadj_ptr[Wi[q] + 1]++; if (Wj[q] != Wi[q]) A.Wadj_ptr[Wj[q] + 1]++; }
+    for (int v = 0; v < n; ++v) A.Wadj_ptr[v + 1] += A.Wadj_ptr[v];
+    A.Wadj_slot.resize(A.Wadj_ptr[n]);
+    A.Wadj_other.resize(A.Wadj_ptr[n]);
+    {
+      std::vector<int> fill(A.Wadj_ptr.begin(), A.Wadj_ptr.end() - 1);
+      for (long long q = 0; q < nW; ++q) {
+        if (Wi[q] < 0) continue;
+        A.Wadj_slot[fill[Wi[q]]] = (int)q; A.Wadj_other[fill[Wi[q]]++] = Wj[q];
+        if (Wj[q] != Wi[q]) { A.Wadj_slot[fill[Wj[q]]] = (int)q; A.Wadj_other[fill[Wj[q]]++] = Wi[q]; }
+      }
+    }
+
     // global supernodes
     A.sn_first.clear();
     std::vector<int> sn_base(ni);

@@ -31,6 +31,7 @@ struct Analysis {
   std::vector<double> yL, yU;
   std::vector<int> Hcol;                    // m * WH
   std::vector<int> Hcsc_ptr, Hcsc_slot;     // column lists of H slots
+  std::vector<int> Wadj_ptr, Wadj_slot, Wadj_other;  // per variable: W slots it takes part in, and the partner
   std::vector<int> perm, iperm;             // global: perm[var] = factor position
   // supernodes (global, instance after instance, each in postorder)
   std::vector<int> sn_first, sn_ncol, sn_nrow, sn_inst, sn_parent;
