@@ -404,7 +404,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
       // ordering
       int ord = sp.ordering;
-      if (ord == 0) ord = (ni > 1 || L.T < 8) ? 1 : 2;
+      if (ord == 0) ord = (L.T < 8) ? 1 : 2;  // short horizons: a chain; else nested dissection (also for batches)
       A.ordering_used = ord;
       std::vector<int> order(nl);
       if (ord == 1) {
