@@ -1,18 +1,24 @@
-// Numeric supernodal Cholesky (eq. cholesky-numeric, Sec. 3.2.3) and the
-// permuted triangular solves (eqs. cholesky-lower/upper), level by level
-// over the supernodal elimination tree computed once on the host.
+// Numeric supernodal factorization (eq. cholesky-numeric, Sec. 3.2.3) and the
+// permuted triangular solves (eqs. cholesky-lower/upper), level by level over
+// the supernodal elimination tree computed once on the host.
+//
+// The factor is computed in the square-root-free form K = L D L^T (L unit
+// lower triangular, D = diag(d_j)), which is the Cholesky factor L_c = L D^{1/2}
+// written differently: the pivots d_j equal L_c,jj^2, so the inertia test of
+// eq. infiniteOCP-inertia is unchanged, and the triangular solves need no
+// divisions.  On this GPU an FP64 square root or division costs hundreds of
+// cycles on the critical path of every column; a reciprocal costs three
+// dependent FMAs after a hardware seed.
 //
 // Storage: each supernode's panel is m x c column-major; its diagonal holds
-// the reciprocals 1/L_jj (the solves multiply by them), everything else is L.
+// 1/d_j, the entries below it hold L_ij.
 //
 // Multifrontal form: supernode J owns a frontal matrix whose first c_J
 // columns are its factor panel and whose trailing (m_J - c_J)^2 block is the
 // update matrix U_J passed to the parent.  A front is assembled from the
 // condensed-matrix values already scattered into the panel plus the
 // children's update matrices (extend-add in ascending child order, so the
-// result is deterministic), then partially factored: pivots, scaled
-// columns and the Schur complement.  One thread block handles one
-// supernode; blocks of the same level run concurrently.  A non-positive or
+// result is deterministic), then partially factored.  A non-positive or
 // non-finite pivot flags the instance for inertia correction.
 #include <cooperative_groups.h>
 
@@ -21,6 +27,8 @@
 namespace nmpc {
 
 extern __shared__ double dsm[];
+
+constexpr unsigned FULL = 0xffffffffu;
 
 // Column index kk of flat position t in the column-major lower triangle of
 // an nn x nn matrix (column kk holds nn - kk entries, starting at
@@ -35,49 +43,59 @@ __device__ __forceinline__ int tri_col(int t, int nn) {
   return kk;
 }
 
-// 1/sqrt(p) for a positive pivot: an FP32 seed (rsqrtf, about 23 bits) and
-// two Newton steps for f(y) = 1/y^2 - p, y <- y (3 - p y^2) / 2, which
-// converge quadratically to full double precision.  Seven FP64 operations
-// instead of a double division and square root: on this GPU the pivot
-// arithmetic sits on the critical path of every column.  Outside the FP32
-// range the exact expression is used.
-__device__ __forceinline__ double rsqrt_newton(double p) {
-  if (!(p >= 1e-36 && p <= 1e36)) return 1.0 / sqrt(p);
-  double y = (double)rsqrtf((float)p);
-  const double hp = 0.5 * p;
-  y = y * fma(-hp, y * y, 1.5);
-  y = y * fma(-hp, y * y, 1.5);
-  return y;
+// 1/d in double precision.  Seed: the PTX approximate reciprocal (relative
+// error below 2^-20).  Refinement: one third-order Newton-Raphson step for
+// f(y) = 1/y - d, i.e. with e = 1 - d*y the truncated series
+// 1/d = y/(1 - e) = y (1 + e + e^2 + ...), y <- y + y (e + e^2), which leaves
+// a relative error of order e^3 < 2^-60 plus the rounding of the last FMA.
+// Near the ends of the exponent range (and for zero, subnormal, infinite or
+// NaN input) the plain division is used.
+__device__ __forceinline__ double recip_nr(double d) {
+  const int ex = (__double2hiint(d) >> 20) & 0x7ff;
+  if (ex < 3 || ex > 2044) return 1.0 / d;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  const double e = fma(-d, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
-// Front held as one m x m column-major matrix in shared memory: columns
-// [0, c) become the factor panel, the trailing (m-c) block the update
-// matrix.  Two barriers per pivot column j: (A) column j is scaled by
-// 1/sqrt(p_j) into its final L values (the diagonal keeps 1/L_jj, which the
-// solves multiply by); (B) the rank-1 Schur update F_ik -= L_ij L_kj runs over
-// the flat-enumerated trailing lower triangle, one FMA per entry with all
-// lanes busy.  The thread that finalizes the next diagonal entry checks it
-// and computes its reciprocal square root for the next phase.
-// A pivot counts as positive only if it exceeds pivtol * |K_jj| (K_jj the
-// assembled diagonal): a pivot at rounding level is a zero eigenvalue, the
-// wrong inertia of eq. infiniteOCP-inertia (which requires n_0 = 0).
-__device__ __forceinline__ bool pivot_ok(double p, double kjj, double pivtol) {
-  return p > pivtol * fabs(kjj) && p > 0.0 && isfinite(p);
+// A pivot counts as positive only if it exceeds thr = pivtol * |K_jj| (K_jj
+// the assembled diagonal): a pivot at rounding level is a zero eigenvalue,
+// the wrong inertia of eq. infiniteOCP-inertia (which requires n_0 = 0).
+// Compared on the bit patterns (thr >= 0, and non-negative doubles order like
+// their bit patterns): p > thr, and p finite.  Integer work keeps the test off
+// the FP64 pipe, whose every instruction costs tens of cycles on this GPU.
+__device__ __forceinline__ bool pivot_ok(double p, double thr) {
+  const long long pb = __double_as_longlong(p), tb = __double_as_longlong(thr);
+  return pb > tb && pb < 0x7ff0000000000000LL;
 }
 
-__device__ void factor_front_smem(Ctl* ctl, double* F, int m, int c, double* rsq, const double* kd, double pivtol) {
+__device__ __forceinline__ void flag_fail(Ctl* ctl) { *(volatile int*)&ctl->factor_fail = 1; }
+
+// ---------------------------------------------------------------------------
+// Single-CTA front factorization (fallback when the cluster kernel's shared
+// memory does not fit, or when selected by option).  Right-looking, one
+// column at a time: pivot, reciprocal, scaled column, rank-1 update of the
+// trailing lower triangle with the unscaled column kept aside.
+// ---------------------------------------------------------------------------
+__device__ void factor_front_smem(Ctl* ctl, double* F, int m, int c, double* wcol, const double* kd, double pivtol) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    double p = F[0];
-    if (!pivot_ok(p, kd[0], pivtol)) { *(volatile int*)&ctl->factor_fail = 1; p = 1.0; }
-    rsq[0] = rsqrt_newton(p);
-  }
-  __syncthreads();
+  __shared__ double inv_s;
   for (int j = 0; j < c; ++j) {
     double* colj = F + (size_t)j * m;
-    const double sj = rsq[j];
-    for (int i = j + 1 + tid; i < m; i += nt) colj[i] *= sj;
-    if (tid == 0) colj[j] = sj;
+    if (tid == 0) {
+      double p = colj[j];
+      if (!pivot_ok(p, pivtol * fabs(kd[j]))) { flag_fail(ctl); p = 1.0; }
+      inv_s = recip_nr(p);
+      colj[j] = inv_s;
+    }
+    __syncthreads();
+    const double inv = inv_s;
+    for (int i = j + 1 + tid; i < m; i += nt) {
+      const double w = colj[i];
+      wcol[i] = w;
+      colj[i] = w * inv;
+    }
     __syncthreads();
     const int nn = m - j - 1;
     const int tot = nn * (nn + 1) / 2;
@@ -85,12 +103,7 @@ __device__ void factor_front_smem(Ctl* ctl, double* F, int m, int c, double* rsq
       const int kk = tri_col(t, nn);
       const int ii = kk + (t - (kk * nn - kk * (kk - 1) / 2));
       const int k = j + 1 + kk, i = j + 1 + ii;
-      double v = fma(-colj[i], colj[k], F[i + (size_t)k * m]);
-      if (t == 0 && j + 1 < c) {  // (j+1, j+1): the next pivot is final now
-        if (!pivot_ok(v, kd[j + 1], pivtol)) { *(volatile int*)&ctl->factor_fail = 1; v = 1.0; }
-        rsq[j + 1] = rsqrt_newton(v);
-      }
-      F[i + (size_t)k * m] = v;
+      F[i + (size_t)k * m] = fma(-colj[i], wcol[k], F[i + (size_t)k * m]);
     }
     __syncthreads();
   }
@@ -104,11 +117,12 @@ __global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap) {
   const int m = s.sn_nrow[J], c = s.sn_ncol[J], mu = m - c;
   double* Lp = s.L + s.sn_Lptr[J];
   double* Up = s.U + s.sn_Uptr[J];
+  const double* kd = s.Kdiag + s.sn_first[J];
   const int tid = threadIdx.x, nt = blockDim.x;
-  if ((long long)m * m + c <= smem_cap) {
+  if ((long long)m * m + m <= smem_cap) {
     // ---- whole front in shared memory
     double* F = dsm;
-    double* rsq = dsm + (size_t)m * m;  // c reciprocal square roots of the pivots
+    double* wcol = dsm + (size_t)m * m;
     for (int t = tid; t < m * c; t += nt) F[t] = Lp[t];
     for (int t = m * c + tid; t < m * m; t += nt) F[t] = 0.0;
     __syncthreads();
@@ -125,7 +139,7 @@ __global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap) {
       }
       __syncthreads();
     }
-    factor_front_smem(ctl, F, m, c, rsq, s.Kdiag + s.sn_first[J], s.pivtol);
+    factor_front_smem(ctl, F, m, c, wcol, kd, s.pivtol);
     for (int t = tid; t < m * c; t += nt) Lp[t] = F[t];
     for (int t = tid; t < mu * mu; t += nt) {
       const int a = t % mu, b = t / mu;
@@ -133,9 +147,11 @@ __global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap) {
     }
     return;
   }
-  // ---- large front: panel in the factor array, update matrix in scratch
+  // ---- large front: panel in the factor array, update matrix in scratch,
+  // unscaled pivot column in shared memory (m doubles)
   double* F = Lp;  // m x c, ld m
   double* G = Up;  // mu x mu, ld mu
+  double* wcol = dsm;
   for (int t = tid; t < mu * mu; t += nt) G[t] = 0.0;
   __syncthreads();
   for (int q = s.sn_child_ptr[J]; q < s.sn_child_ptr[J + 1]; ++q) {
@@ -154,50 +170,226 @@ __global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap) {
     }
     __syncthreads();
   }
-  __shared__ double pivg;
+  __shared__ double invg;
   for (int j = 0; j < c; ++j) {
+    double* colj = F + (size_t)j * m;
     if (tid == 0) {
-      double dj = F[j + (size_t)j * m];
-      if (!pivot_ok(dj, s.Kdiag[s.sn_first[J] + j], s.pivtol)) { *(volatile int*)&ctl->factor_fail = 1; dj = 1.0; }
-      pivg = 1.0 / sqrt(dj);
-      F[j + (size_t)j * m] = pivg;  // reciprocal of L_jj (see the solves)
+      double dj = colj[j];
+      if (!pivot_ok(dj, s.pivtol * fabs(kd[j]))) { flag_fail(ctl); dj = 1.0; }
+      invg = recip_nr(dj);
+      colj[j] = invg;
     }
     __syncthreads();
-    const double inv = pivg;
-    for (int i = j + 1 + tid; i < m; i += nt) F[i + (size_t)j * m] *= inv;
+    const double inv = invg;
+    for (int i = j + 1 + tid; i < m; i += nt) {
+      const double w = colj[i];
+      wcol[i] = w;
+      colj[i] = w * inv;
+    }
     __syncthreads();
     const int nn = m - j - 1;
     const int tot = nn * (nn + 1) / 2;
-    const double* colj = F + (size_t)j * m;
     for (int t = tid; t < tot; t += nt) {
       const int kk = tri_col(t, nn);
       const int ii = kk + (t - (kk * nn - kk * (kk - 1) / 2));
       const int i = j + 1 + ii, k = j + 1 + kk;
-      if (k < c) F[i + (size_t)k * m] = fma(-colj[i], colj[k], F[i + (size_t)k * m]);
-      else G[(i - c) + (size_t)(k - c) * mu] = fma(-colj[i], colj[k], G[(i - c) + (size_t)(k - c) * mu]);
+      if (k < c) F[i + (size_t)k * m] = fma(-colj[i], wcol[k], F[i + (size_t)k * m]);
+      else G[(i - c) + (size_t)(k - c) * mu] = fma(-colj[i], wcol[k], G[(i - c) + (size_t)(k - c) * mu]);
     }
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// Cluster-cooperative front factorization (blocked, right-looking).
+// Cluster-cooperative front factorization (blocked, right-looking, LDL^T).
+//
+// Cost model behind the layout: on this GPU an FP64 warp instruction keeps
+// its SM sub-partition's FP64 unit busy for about 64 cycles whether one lane
+// or all 32 are active, and a warp's FP64 instructions do not overlap.  So
+// the pivot chain must use as few FP64 instructions per column as possible,
+// run in a warp of its own sub-partition, and every other FP64 instruction
+// should keep all lanes busy on the other sub-partitions.
 //
 // One thread-block cluster of Q CTAs factors one front.  Columns are dealt to
-// the CTAs block-cyclically in blocks of PB columns (block b -> CTA b % Q), so
-// every CTA holds all m rows of its own columns in shared memory.  For each
-// pivot panel (block p < ceil(c / PB)):
-//   1. its owner factors the panel (pivot test, 1/sqrt(p) by Newton, column
-//      scaling, rank-1 updates inside the panel);
-//   2. one cluster barrier publishes it;
-//   3. every CTA copies the panel rows it needs from the owner's shared memory
-//      (distributed shared memory) and applies the rank-PB update to its own
-//      trailing columns, one FMA per panel column and entry.
-// Afterwards the owners write the factor panel (columns < c) and the update
-// matrix (columns >= c) back.  Q is chosen per level so that the fronts of a
-// level together occupy most SMs.  The panel diagonal keeps 1/L_jj.
+// the CTAs block-cyclically in blocks of PB = 8 columns (block b -> CTA b % Q);
+// every CTA holds all m rows of its own columns in shared memory.  Pivot
+// panel P (columns jb = P*PB .. jb + w - 1) is factored by its owner
+// (panel_factor):
+//   phase 1, in parallel on different sub-partitions:
+//     warp 0: applies the previous panel to the PB x PB diagonal block (one
+//       lane per lower-triangle entry: 28 entries of columns 1..7 in warp 0,
+//       the 8 entries of column 0 by warp 1), then runs the pivot chain: per
+//       column a shuffle of the pivot, its reciprocal (recip_nr: a seed and
+//       three FMAs), and one multiply and one FMA that update every remaining
+//       entry of the block at once -- five FP64 instructions per column;
+//     warps 1-3, 5-7: apply the previous panel to the rows below the block;
+//   phase 2: every row below the pivot block is solved against it (w-step
+//     forward substitution, one row per thread).
+// The scaled panel L (diagonal 1/d_j) and the unscaled panel W = L D go to
+// global memory (the factor and a scratch copy); a per-CTA counter, written
+// with release semantics at cluster scope after a block barrier, tells the
+// other CTAs that panel P is ready, and they read it from L2.  Every CTA
+// applies each published panel to its own columns (F_ik -= sum_j L_ij W_kj).
+// Lookahead: the owner of panel p+1 factors it right after reading panel p
+// and only then updates its other columns, so the pivot chain never waits for
+// the bulk update.  Waits are bounded (spin_limit polls); a wait that runs out
+// sets the instance's factor-failure flag and the workspace timeout flag, and
+// the kernel runs to completion on whatever data it has.
 // ---------------------------------------------------------------------------
 constexpr int PB = 8;
+
+__device__ __forceinline__ int ld_acquire_cluster(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cluster.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cluster(int* p, int v) {
+  asm volatile("st.release.cluster.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void bar_pair() { asm volatile("bar.sync 1, 64;" ::: "memory"); }  // warps 0 and 1
+
+// Fl[i + lc*m] -= sum_{jj<w} Pl[i + jj*m] * Pw[k + jj*m] for own columns
+// k in [kb, ke) (local column lc0 + k - kb) and rows i in [k, m).
+__device__ __forceinline__ void rank_update(double* Fl, const double* Pl, const double* Pw, int m, int w,
+                                            int kb, int ke, int lc0) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int rows = m - kb;
+  const int cols = ke - kb;
+  for (int t = tid; t < rows * cols; t += nt) {
+    const int kk = t / rows;
+    const int i = kb + (t - kk * rows);
+    const int k = kb + kk;
+    if (i < k) continue;
+    double* f = Fl + i + (size_t)(lc0 + kk) * m;
+    double acc = *f;
+#pragma unroll
+    for (int jj = 0; jj < PB; ++jj)
+      if (jj < w) acc = fma(-Pl[i + (size_t)jj * m], Pw[k + (size_t)jj * m], acc);
+    *f = acc;
+  }
+}
+
+// slot-A lane of diagonal-block entry (r, k), 1 <= k <= r <= 7
+__device__ __forceinline__ int tri_lane(int r, int k) { return r * (r - 1) / 2 + k - 1; }
+
+// Factor pivot panel of this CTA: block columns jb .. kend-1 (pivots
+// jb .. jb+w-1) at local columns lc0 ..; the previous panel (Pl, Pw, width
+// wprev; wprev = 0 for none) is applied to the block first.
+__device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* thr, double* Lg, double* Wg,
+                             const double* Pl, const double* Pw, int wprev, int m, int jb, int w, int lc0,
+                             double* sB) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double* Fp = Fl + (size_t)lc0 * m;  // block column kk at Fp + kk*m
+  const int kend = min(jb + PB, m), nb = kend - jb;
+  // ---- phase 1
+  if (warp == 1) {
+    // column 0 of the diagonal block: previous panel applied, handed to warp 0
+    if (lane < nb) {
+      double b = Fp[jb + lane];
+      for (int j = 0; j < wprev; ++j) b = fma(-Pl[(jb + lane) + (size_t)j * m], Pw[jb + (size_t)j * m], b);
+      sB[lane] = b;
+    }
+    bar_pair();
+  }
+  if (warp == 0) {
+    const int rA0 = 1 + (lane >= 1) + (lane >= 3) + (lane >= 6) + (lane >= 10) + (lane >= 15) + (lane >= 21);
+    const bool inA = lane < 28;
+    const int rA = inA ? rA0 : 7;
+    const int kA = inA ? 1 + lane - (rA0 - 1) * rA0 / 2 : 7;
+    const bool vA = inA && rA < nb;
+    double a = vA ? Fp[(jb + rA) + (size_t)kA * m] : 0.0;
+    for (int j = 0; j < wprev; ++j)
+      if (vA) a = fma(-Pl[(jb + rA) + (size_t)j * m], Pw[(jb + kA) + (size_t)j * m], a);
+    bar_pair();
+    const int rB = lane & 7;
+    double b = (lane < nb) ? sB[lane] : 0.0;
+    double inv[PB];
+    bool bad = false;
+#pragma unroll
+    for (int jj = 0; jj < PB; ++jj) {
+      inv[jj] = 0.0;
+      if (jj < w) {
+        // operands of this column's update, independent of the pivot
+        double x, y;
+        if (jj == 0) {
+          x = __shfl_sync(FULL, b, rA);
+          y = __shfl_sync(FULL, b, kA);
+        } else {
+          x = __shfl_sync(FULL, a, tri_lane(max(rA, jj), jj));
+          y = __shfl_sync(FULL, a, tri_lane(max(kA, jj), jj));
+        }
+        const double p = (jj == 0) ? __shfl_sync(FULL, b, 0) : __shfl_sync(FULL, a, tri_lane(jj, jj));
+        const double iv = recip_nr(p);
+        inv[jj] = iv;
+        if (lane == 0) bad = bad || !pivot_ok(p, thr[jj]);
+        if (vA && kA > jj && rA < w) a = fma(-(x * iv), y, a);
+      }
+    }
+    // outputs: W in place (phase 2 reads it), L and W to global memory
+    double ik = inv[1];
+#pragma unroll
+    for (int k = 2; k < PB; ++k)
+      if (kA == k) ik = inv[k];
+    if (vA) {
+      Fp[(jb + rA) + (size_t)kA * m] = a;
+      if (kA < w) {
+        const size_t g = (jb + rA) + (size_t)(jb + kA) * m;
+        Lg[g] = (rA == kA) ? ik : a * ik;
+        Wg[g] = a;
+      }
+    }
+    if (lane < nb) {
+      Fp[jb + rB] = b;
+      if (w > 0) {
+        const size_t g = jb + rB;
+        Lg[g + (size_t)jb * m] = (rB == 0) ? inv[0] : b * inv[0];
+        Wg[g + (size_t)jb * m] = b;
+      }
+    }
+    if (lane < w) {
+      double mine = inv[0];
+#pragma unroll
+      for (int k = 1; k < PB; ++k)
+        if (lane == k) mine = inv[k];
+      invd[lane] = mine;
+    }
+    if (lane == 0 && bad) flag_fail(ctl);
+  } else if (wprev > 0 && (warp & 3) != 0) {
+    // rows below the diagonal block: previous panel applied (warps off warp 0's sub-partition)
+    const int bw = (warp < 4) ? warp - 1 : warp - 2;  // 0..5
+    const int nbw = (blockDim.x / 32 >= 8) ? 6 : 3;
+    const int rows = m - kend;
+    for (int t = bw * 32 + lane; t < rows * nb; t += nbw * 32) {
+      const int kk = t / rows;
+      const int i = kend + (t - kk * rows);
+      double acc = Fp[i + (size_t)kk * m];
+#pragma unroll
+      for (int j = 0; j < PB; ++j)
+        if (j < wprev) acc = fma(-Pl[i + (size_t)j * m], Pw[(jb + kk) + (size_t)j * m], acc);
+      Fp[i + (size_t)kk * m] = acc;
+    }
+  }
+  __syncthreads();
+  // ---- phase 2: rows below the pivot block, l_ij = (F_ij - sum_{k<j} l_ik W_jk) / d_j
+  for (int i = jb + w + tid; i < m; i += blockDim.x) {
+    double f[PB];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) f[k] = (k < w) ? Fp[i + (size_t)k * m] : 0.0;
+#pragma unroll
+    for (int jj = 0; jj < PB; ++jj) {
+      if (jj < w) {
+        const double lj = f[jj] * invd[jj];
+        const size_t g = i + (size_t)(jb + jj) * m;
+        Lg[g] = lj;
+        Wg[g] = f[jj];
+#pragma unroll
+        for (int k = jj + 1; k < PB; ++k)
+          if (k < w) f[k] = fma(-lj, Fp[(jb + k) + (size_t)jj * m], f[k]);
+      }
+    }
+  }
+  __syncthreads();
+}
 
 __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
   namespace cg = cooperative_groups;
@@ -209,23 +401,33 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
   if (!ctl->need_factor) return;  // uniform over the cluster: same instance
   const int m = s.sn_nrow[J], c = s.sn_ncol[J], mu = m - c;
   double* Lp = s.L + s.sn_Lptr[J];
+  double* Wp = s.W + s.sn_Lptr[J];
   double* Up = s.U + s.sn_Uptr[J];
   const double* kd = s.Kdiag + s.sn_first[J];
-  const double pivtol = s.pivtol;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nblk = (m + PB - 1) / PB;
   const int my_blocks = (nblk - q + Q - 1) / Q;  // blocks q, q+Q, ...
-  double* Fl = dsm;                                // m x (my_blocks * PB), ld m
-  double* P = dsm + (size_t)m * my_blocks * PB;    // panel copy: m x PB, ld m
-  __shared__ double rsq_s;
-  // local column of global column k (owned by this CTA)
+  const int ncl = my_blocks * PB;
+  double* Pw = dsm;                          // m x PB: current panel, unscaled
+  double* Pl = Pw + (size_t)m * PB;          // m x PB: current panel, scaled
+  double* Fl = Pl + (size_t)m * PB;          // m x ncl, ld m: own columns
+  double* thr = Fl + (size_t)m * ncl;        // ncl: pivot thresholds of own columns
+  double* invd = thr + ncl;                  // ncl: 1/d of own pivot columns
+  __shared__ int s_pub;                      // panels of this CTA published so far
+  __shared__ int s_timeout;
+  __shared__ double sB[PB];
   auto lcol = [&](int k) { return ((k / PB) / Q) * PB + (k % PB); };
   // ---- assemble: own columns from the condensed values, then the children
-  for (int t = tid; t < m * my_blocks * PB; t += nt) {
+  for (int t = tid; t < m * ncl; t += nt) {
     const int i = t % m, lc = t / m;
     const int k = ((lc / PB) * Q + q) * PB + lc % PB;
     Fl[t] = (k < c) ? Lp[i + (size_t)k * m] : 0.0;
   }
+  for (int lc = tid; lc < ncl; lc += nt) {
+    const int k = ((lc / PB) * Q + q) * PB + lc % PB;
+    thr[lc] = (k < c) ? s.pivtol * fabs(kd[k]) : 0.0;
+  }
+  if (tid == 0) { s_pub = 0; s_timeout = 0; }
   __syncthreads();
   for (int qq = s.sn_child_ptr[J]; qq < s.sn_child_ptr[J + 1]; ++qq) {
     const int C = s.sn_child[qq];
@@ -242,89 +444,99 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
     }
     __syncthreads();
   }
-  // ---- panels
+  cluster.sync();  // every CTA assembled and initialized its counter
   const int npan = (c + PB - 1) / PB;
+  const long long limit = s.spin_limit;
+  if (q == 0 && npan > 0) {
+    panel_factor(ctl, Fl, invd, thr, Lp, Wp, Pl, Pw, 0, m, 0, min(PB, c), 0, sB);
+    if (tid == 0) st_release_cluster(&s_pub, 1);
+  }
   for (int p = 0; p < npan; ++p) {
     const int jb = p * PB, w = min(PB, c - jb);
     const int owner = p % Q;
-    if (q == owner) {
-      double* Fp = Fl + (size_t)lcol(jb) * m;  // panel columns are contiguous locally
-      for (int jj = 0; jj < w; ++jj) {
-        const int j = jb + jj;
-        double* colj = Fp + (size_t)jj * m;
-        if (tid == 0) {
-          double piv = colj[j];
-          if (!pivot_ok(piv, kd[j], pivtol)) { *(volatile int*)&ctl->factor_fail = 1; piv = 1.0; }
-          rsq_s = rsqrt_newton(piv);
-          colj[j] = rsq_s;
-        }
-        __syncthreads();
-        const double sj = rsq_s;
-        for (int i = j + 1 + tid; i < m; i += nt) colj[i] *= sj;
-        __syncthreads();
-        // rank-1 update of the remaining panel columns jj+1 .. w-1
-        const int rem = w - jj - 1;
-        if (rem > 0) {
-          const int rows = m - j - 1;
-          for (int t = tid; t < rows * rem; t += nt) {
-            const int i = j + 1 + t % rows, kk = jj + 1 + t / rows;
-            const int k = jb + kk;
-            if (i >= k) Fp[i + (size_t)kk * m] = fma(-colj[i], colj[k], Fp[i + (size_t)kk * m]);
-          }
-          __syncthreads();
+    // ---- wait for panel p, then read rows jb+w..m-1 of it from L2
+    if (owner != q) {
+      if (tid == 0) {
+        const int* rp = cluster.map_shared_rank(&s_pub, owner);
+        long long it = 0;
+        while (!s_timeout && ld_acquire_cluster(rp) <= p / Q) {
+          if (++it > limit) s_timeout = 1;
         }
       }
+      __syncthreads();
     }
-    cluster.sync();  // the panel is final and visible to the cluster
-    // copy rows jb..m-1 of the panel from the owner
     {
-      const double* src = cluster.map_shared_rank(Fl, owner) + (size_t)((jb / PB) / Q) * PB * m;
-      for (int t = tid; t < (m - jb) * w; t += nt) {
-        const int i = jb + t % (m - jb), jj = t / (m - jb);
-        P[i + (size_t)jj * m] = src[i + (size_t)jj * m];
+      const int r0 = jb + w, rows = m - r0;
+      for (int t = tid; t < rows * w; t += nt) {
+        const int jj = t / rows;
+        const int i = r0 + (t - jj * rows);
+        const size_t g = i + (size_t)(jb + jj) * m;
+        Pw[i + (size_t)jj * m] = __ldcg(Wp + g);
+        Pl[i + (size_t)jj * m] = __ldcg(Lp + g);
       }
     }
     __syncthreads();
-    // rank-w update of own columns k >= jb + w, rows i >= k (the panel's own
-    // block also holds update-matrix columns when c is not a multiple of PB)
+    // ---- lookahead: the owner of panel p+1 applies panel p to it and factors it
+    const int nx = p + 1;
+    const bool look = nx < npan && (nx % Q) == q;
+    if (look) {
+      const int k0 = nx * PB;
+      panel_factor(ctl, Fl, invd + (nx / Q) * PB, thr + (nx / Q) * PB, Lp, Wp, Pl, Pw, w, m, k0,
+                   min(PB, c - k0), (nx / Q) * PB, sB);
+      if (tid == 0) st_release_cluster(&s_pub, nx / Q + 1);
+    }
+    // ---- rank-w update of the remaining own columns
     for (int lb = 0; lb < my_blocks; ++lb) {
       const int b = lb * Q + q;
-      if (b < p) continue;
+      if (b < p || (look && b == nx)) continue;
       const int k0 = b * PB;
-      const int ks = (b == p) ? jb + w : k0;
-      const int kcnt = min(k0 + PB, m) - ks;
-      if (kcnt <= 0) continue;
-      const int rows = m - ks;
-      for (int t = tid; t < rows * kcnt; t += nt) {
-        const int i = ks + t % rows, kk = t / rows;
-        const int k = ks + kk;
-        if (i < k) continue;
-        const int lc = lb * PB + (k - k0);
-        double acc = Fl[i + (size_t)lc * m];
-#pragma unroll
-        for (int jj = 0; jj < PB; ++jj)
-          if (jj < w) acc = fma(-P[i + (size_t)jj * m], P[k + (size_t)jj * m], acc);
-        Fl[i + (size_t)lc * m] = acc;
-      }
+      const int ks = (b == p) ? jb + w : k0;  // the pivot block's own trailing columns
+      const int ke = min(k0 + PB, m);
+      if (ks >= ke) continue;
+      rank_update(Fl, Pl, Pw, m, w, ks, ke, lb * PB + (ks - k0));
     }
     __syncthreads();
   }
-  cluster.sync();  // no CTA may leave while others still read its panels
-  // ---- write back own columns
-  for (int t = tid; t < m * my_blocks * PB; t += nt) {
+  cluster.sync();  // no CTA may leave while others may still poll its counter
+  if (tid == 0 && s_timeout) {
+    flag_fail(ctl);
+    atomicExch(s.timeout, 1);
+  }
+  // ---- write back the update-matrix columns (the factor panel is written as it is factored)
+  for (int t = tid; t < m * ncl; t += nt) {
     const int i = t % m, lc = t / m;
     const int k = ((lc / PB) * Q + q) * PB + lc % PB;
-    if (k >= m) continue;
-    if (k < c) Lp[i + (size_t)k * m] = Fl[t];
-    else if (i >= c) Up[(i - c) + (size_t)(k - c) * mu] = Fl[t];
+    if (k < c || k >= m || i < c) continue;
+    Up[(i - c) + (size_t)(k - c) * mu] = Fl[t];
   }
 }
 
-// Forward substitution L v = P b for one level.  The front vector of J is
-// [b_J ; 0] plus the children's update vectors; after the pivot block is
-// solved the remaining rows become J's update vector.  The panel is staged
-// in shared memory (coalesced), the c x c triangular part runs in one warp
-// (warp barriers only), the update rows in all threads.
+// ---------------------------------------------------------------------------
+// Triangular solves with K = L D L^T, one thread block per supernode of a
+// level.  Forward: L y = P b over the tree (children first), then z = D^{-1} y;
+// backward: L^T x = z (parents first).  The c x c unit triangle runs in one
+// warp with the vector's pivot entries held in lanes' registers (row r in
+// lane r % 32, slot r / 32): one shuffle and one FMA per column on the
+// critical path.  The rectangular parts are dot products split over groups
+// of threads with shuffle reductions.
+// ---------------------------------------------------------------------------
+constexpr int SOLVE_SLOTS = 4;  // register path for c <= 128
+
+__device__ __forceinline__ double pick(const double (&v)[SOLVE_SLOTS], int sl) {
+  double r = v[0];
+#pragma unroll
+  for (int s = 1; s < SOLVE_SLOTS; ++s)
+    if (sl == s) r = v[s];
+  return r;
+}
+
+// threads per dot product so that `count` products fill the block
+__device__ __forceinline__ int group_width(int count, int nt) {
+  int g = 1;
+  while (g < 32 && g * 2 * count <= nt) g *= 2;
+  return g;
+}
+
 __global__ void k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
   const int J = list[blockIdx.x];
   if (d.ctl[s.sn_inst[J]].status != ST_RUNNING) return;
@@ -346,54 +558,115 @@ __global__ void k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
     for (int a = tid; a < mc; a += nt) fv[rel[a]] += uvC[a];
     __syncthreads();
   }
+  // unit lower triangle
   if (tid < 32) {
-    for (int j = 0; j < c; ++j) {
-      const double vj = fv[j] * Ls[j + (size_t)j * m];  // diagonal stores 1/L_jj
-      __syncwarp();
-      for (int i = j + 1 + tid; i < c; i += 32) fv[i] = fma(-Ls[i + (size_t)j * m], vj, fv[i]);
-      if (tid == 0) fv[j] = vj;
-      __syncwarp();
+    const int lane = tid;
+    if (c <= 32 * SOLVE_SLOTS) {
+      double v[SOLVE_SLOTS];
+#pragma unroll
+      for (int sl = 0; sl < SOLVE_SLOTS; ++sl) v[sl] = (lane + 32 * sl < c) ? fv[lane + 32 * sl] : 0.0;
+      for (int j = 0; j < c; ++j) {
+        const double yj = __shfl_sync(FULL, pick(v, j >> 5), j & 31);
+        const double* col = Ls + (size_t)j * m;
+#pragma unroll
+        for (int sl = 0; sl < SOLVE_SLOTS; ++sl) {
+          const int i = lane + 32 * sl;
+          if (i > j && i < c) v[sl] = fma(-col[i], yj, v[sl]);
+        }
+      }
+#pragma unroll
+      for (int sl = 0; sl < SOLVE_SLOTS; ++sl)
+        if (lane + 32 * sl < c) fv[lane + 32 * sl] = v[sl];
+    } else {
+      for (int j = 0; j < c; ++j) {
+        const double yj = fv[j];
+        __syncwarp();
+        for (int i = j + 1 + lane; i < c; i += 32) fv[i] = fma(-Ls[i + (size_t)j * m], yj, fv[i]);
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
+  // update vector u_i = f_i - sum_j L_ij y_j (rows c..m-1), and z = D^{-1} y
   double* uvJ = s.uv + s.sn_uvptr[J];
-  for (int i = c + tid; i < m; i += nt) {
-    double a = fv[i];
-    for (int j = 0; j < c; ++j) a = fma(-Ls[i + (size_t)j * m], fv[j], a);
-    uvJ[i - c] = a;
+  const int rows = m - c;
+  if (rows > 0) {
+    const int g = group_width(rows, nt);
+    for (int base = 0; base < rows * g; base += nt) {
+      const int t = base + tid;
+      const int r = t / g, part = t % g;
+      double a = 0.0;
+      if (r < rows)
+        for (int j = part; j < c; j += g) a = fma(-Ls[(c + r) + (size_t)j * m], fv[j], a);
+      for (int off = g >> 1; off > 0; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+      if (r < rows && part == 0) uvJ[r] = fv[c + r] + a;
+    }
   }
-  for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j];
+  for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
 }
 
-// Backward substitution L^T x = v for one level (parents before children).
 __global__ void k_bwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
   const int J = list[blockIdx.x];
   if (d.ctl[s.sn_inst[J]].status != ST_RUNNING) return;
   const int m = s.sn_nrow[J], c = s.sn_ncol[J], first = s.sn_first[J];
   const double* Lg = s.L + s.sn_Lptr[J];
-  const int* rows = s.sn_rows + s.sn_rowptr[J];
-  const bool stage = (long long)m * c + m <= smem_cap;
-  double* xv = dsm + (stage ? (size_t)m * c : 0);       // m
-  const double* Ls = stage ? dsm : Lg;                   // m x c
+  const int* rows_idx = s.sn_rows + s.sn_rowptr[J];
+  // staged: the panel (m x c) and the transposed pivot block T(i, j) = L(j, i) (c x c)
+  const bool stage = (long long)m * c + (long long)c * c + m <= smem_cap;
+  double* xv = dsm + (stage ? (size_t)m * c + (size_t)c * c : 0);  // m
+  const double* Ls = stage ? dsm : Lg;
+  double* T = dsm + (size_t)m * c;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (stage)
+  if (stage) {
     for (int t = tid; t < m * c; t += nt) dsm[t] = Lg[t];
-  for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : d.b[rows[i]];
+    for (int t = tid; t < c * c; t += nt) {
+      const int i = t % c, j = t / c;
+      T[t] = (i < j) ? Lg[j + (size_t)i * m] : 0.0;
+    }
+  }
+  for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : d.b[rows_idx[i]];
   __syncthreads();
-  // t_j = v_j - sum_{i >= c} L_ij x_i  (x_i of ancestors, already solved)
-  for (int j = tid; j < c; j += nt) {
-    double a = xv[j];
-    for (int i = c; i < m; ++i) a = fma(-Ls[i + (size_t)j * m], xv[i], a);
-    xv[j] = a;
+  // t_j = z_j - sum_{i >= c} L_ij x_i  (x_i of ancestors, already solved)
+  const int below = m - c;
+  if (below > 0) {
+    const int g = group_width(c, nt);
+    for (int base = 0; base < c * g; base += nt) {
+      const int t = base + tid;
+      const int j = t / g, part = t % g;
+      double a = 0.0;
+      if (j < c)
+        for (int i = c + part; i < m; i += g) a = fma(-Ls[i + (size_t)j * m], xv[i], a);
+      for (int off = g >> 1; off > 0; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+      if (j < c && part == 0) xv[j] += a;
+    }
   }
   __syncthreads();
+  // unit upper triangle L_cc^T x = t, last column first
   if (tid < 32) {
-    for (int j = c - 1; j >= 0; --j) {
-      const double xj = xv[j] * Ls[j + (size_t)j * m];  // diagonal stores 1/L_jj
-      __syncwarp();
-      for (int i = tid; i < j; i += 32) xv[i] = fma(-Ls[j + (size_t)i * m], xj, xv[i]);
-      if (tid == 0) xv[j] = xj;
-      __syncwarp();
+    const int lane = tid;
+    if (stage && c <= 32 * SOLVE_SLOTS) {
+      double v[SOLVE_SLOTS];
+#pragma unroll
+      for (int sl = 0; sl < SOLVE_SLOTS; ++sl) v[sl] = (lane + 32 * sl < c) ? xv[lane + 32 * sl] : 0.0;
+      for (int j = c - 1; j >= 0; --j) {
+        const double xj = __shfl_sync(FULL, pick(v, j >> 5), j & 31);
+        const double* col = T + (size_t)j * c;  // col[i] = L(j, i)
+#pragma unroll
+        for (int sl = 0; sl < SOLVE_SLOTS; ++sl) {
+          const int i = lane + 32 * sl;
+          if (i < j) v[sl] = fma(-col[i], xj, v[sl]);
+        }
+      }
+#pragma unroll
+      for (int sl = 0; sl < SOLVE_SLOTS; ++sl)
+        if (lane + 32 * sl < c) xv[lane + 32 * sl] = v[sl];
+    } else {
+      for (int j = c - 1; j >= 0; --j) {
+        const double xj = xv[j];
+        __syncwarp();
+        for (int i = lane; i < j; i += 32) xv[i] = fma(-Ls[j + (size_t)i * m], xj, xv[i]);
+        __syncwarp();
+      }
     }
   }
   __syncthreads();

@@ -52,7 +52,7 @@ struct nmpc_handle {
   double* d_stage = nullptr;  // staging of host parameter arrays
   int* h_flags = nullptr;     // pinned
   std::vector<int> lvl_ptr;
-  std::vector<int> lvl_smem_factor, lvl_smem_solve;  // bytes per level
+  std::vector<int> lvl_smem_factor, lvl_smem_solve, lvl_smem_bwd;  // bytes per level
   std::vector<int> lvl_cluster;                      // CTAs per front (0 = single-CTA kernel)
   std::vector<int> lvl_cluster_smem;                 // bytes per CTA of the cluster kernel
   int n_sm = 152;
@@ -127,7 +127,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   h->d_tgt_inst = cv.take<int>(A.tgt_L.size());
   h->d_Drow = cv.take<double>(m);
   h->d_inst_Lbeg = cv.take<long long>(ni); h->d_inst_Lend = cv.take<long long>(ni);
-  h->d_flags = cv.take<int>(4);
+  h->d_flags = cv.take<int>(8);  // [0..2] summary, [3] wait timeout, [4..7] adjoint norms
   h->d_stage = cv.take<double>((size_t)ni * (A.mc.nx + A.sp_stride + 1));
   h->d_ctl_save = cv.take<Ctl>(ni);
   d.trace = cv.take<double>((size_t)ni * (h->opt.max_iter + 2) * 8);
@@ -139,10 +139,13 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.level_ptr = cv.take<int>(A.level_ptr.size()); s.level_sn = cv.take<int>(ns);
   s.sn_uvptr = cv.take<long long>(ns + 1);
   s.U = cv.take<double>(A.nU);
+  s.W = cv.take<double>(A.nnzL);
   s.uv = cv.take<double>(A.nuv);
   s.L = d.Lval;
   s.Kdiag = d.Kdiag;
   s.pivtol = A.mc.pivtol;
+  s.spin_limit = h->opt.spin_limit > 0 ? h->opt.spin_limit : 10000000LL;
+  s.timeout = h->d_flags + 3;
   s.sn_inst = d.sn_inst;
   s.ns = (int)ns;
   d.mc = A.mc; d.n_inst = ni; d.n = n; d.m = m; d.nW = A.nW; d.sp_stride = A.sp_stride;
@@ -158,8 +161,9 @@ cudaError_t up(const T* dst, const std::vector<T>& src, cudaStream_t st) {
 nmpc_status read_flags(nmpc_handle* h) {
   k_summary<<<1, 256, 0, h->stream>>>(h->d, h->d_flags);
   ++h->launches;
-  CUDA_TRY(h, cudaMemcpyAsync(h->h_flags, h->d_flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_flags, h->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (h->h_flags[3]) return fail(h, NMPC_TIMEOUT, "a bounded wait between the CTAs of a front factorization ran out");
   return NMPC_OK;
 }
 
@@ -202,7 +206,7 @@ nmpc_status launch_solve(nmpc_handle* h) {
   }
   for (int l = nl - 1; l >= 0; --l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
-    if (cnt) k_bwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+    if (cnt) k_bwd_level<<<cnt, 128, h->lvl_smem_bwd[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
                                                                         h->smem_cap_doubles);
     ++h->launches;
   }
@@ -281,28 +285,35 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   h->lvl_cluster_smem.assign(nl, 0);
   for (int l = 0; l < nl; ++l) {
     const int cnt = A.level_ptr[l + 1] - A.level_ptr[l];
+    int max_blocks = 1;
+    for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd)
+      max_blocks = std::max(max_blocks, (A.sn_nrow[A.level_sn[qd]] + CLUSTER_PB - 1) / CLUSTER_PB);
     int Q = 1;
-    while (Q < 8 && 2 * Q * cnt <= h->n_sm) Q *= 2;
+    while (Q < 8 && 2 * Q * cnt <= h->n_sm && 2 * Q <= max_blocks) Q *= 2;
     long long worst = 0;
     bool fits = true;
     for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1] && fits; ++qd) {
       const int sn = A.level_sn[qd];
       const long long mm = A.sn_nrow[sn];
       const long long nblk = (mm + CLUSTER_PB - 1) / CLUSTER_PB;
-      const long long need = ((nblk + Q - 1) / Q * CLUSTER_PB + CLUSTER_PB) * mm;  // doubles
+      const long long ncl = (nblk + Q - 1) / Q * CLUSTER_PB;
+      const long long need = mm * (ncl + 2 * CLUSTER_PB) + 2 * ncl;  // doubles (layout in k_factor_cluster)
       if (need * 8 > SMEM_FACTOR_CAP_BYTES) fits = false;
       worst = std::max(worst, need * 8);
     }
     if (fits && h->opt.factor_mode == 0) { h->lvl_cluster[l] = Q; h->lvl_cluster_smem[l] = (int)worst; }
   }
+  h->lvl_smem_bwd.assign(nl, 8);
   for (int l = 0; l < nl; ++l)
     for (int q = A.level_ptr[l]; q < A.level_ptr[l + 1]; ++q) {
       const int sn = A.level_sn[q];
       const long long mm = A.sn_nrow[sn], cc = A.sn_ncol[sn];
-      const long long need = mm * mm + cc;  // whole front plus the pivots' reciprocal square roots
-      if (need <= h->smem_cap_doubles) h->lvl_smem_factor[l] = std::max<int>(h->lvl_smem_factor[l], (int)(need * 8));
-      const long long sneed = (mm * cc + mm <= h->smem_cap_doubles) ? mm * cc + mm : mm;
-      h->lvl_smem_solve[l] = std::max<int>(h->lvl_smem_solve[l], (int)(sneed * 8));
+      const long long need = mm * mm + mm;  // whole front plus one unscaled column
+      h->lvl_smem_factor[l] = std::max<int>(h->lvl_smem_factor[l], (int)((need <= h->smem_cap_doubles ? need : mm) * 8));
+      const long long fneed = (mm * cc + mm <= h->smem_cap_doubles) ? mm * cc + mm : mm;
+      h->lvl_smem_solve[l] = std::max<int>(h->lvl_smem_solve[l], (int)(fneed * 8));
+      const long long bneed = (mm * cc + cc * cc + mm <= h->smem_cap_doubles) ? mm * cc + cc * cc + mm : mm;
+      h->lvl_smem_bwd[l] = std::max<int>(h->lvl_smem_bwd[l], (int)(bneed * 8));
     }
   *out = h;
   return NMPC_OK;
@@ -375,11 +386,10 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   CUDA_TRY(h, up(s.level_sn, A.level_sn, st)); CUDA_TRY(h, up(s.sn_uvptr, A.sn_uvptr, st));
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
-  int maxs = *std::max_element(h->lvl_smem_solve.begin(), h->lvl_smem_solve.end());
-  if (maxs > 48 * 1024) {
-    CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
-    CUDA_TRY(h, cudaFuncSetAttribute(k_bwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs));
-  }
+  const int maxf = *std::max_element(h->lvl_smem_solve.begin(), h->lvl_smem_solve.end());
+  const int maxb = *std::max_element(h->lvl_smem_bwd.begin(), h->lvl_smem_bwd.end());
+  if (maxf > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxf));
+  if (maxb > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_bwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb));
   CUDA_TRY(h, cudaStreamSynchronize(st));
   h->d.max_iter = h->opt.max_iter;
   h->h_ctl.resize(A.n_inst);
@@ -446,6 +456,7 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
   const double mu0 = warm ? h->opt.mu0_warm : h->opt.mu0_cold;
   const double push = warm ? h->opt.push_warm : h->opt.push_cold;
   if (h->ev0) CUDA_TRY(h, cudaEventRecord(h->ev0, st));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_flags + 3, 0, sizeof(int), st));
   k_ctl_init<<<blocks_for(ni), TPB, 0, st>>>(d, mu0);
   ++h->launches;
   k_init_vars<<<blocks_for(n, EW), EW, 0, st>>>(d, warm, push);
@@ -609,6 +620,7 @@ nmpc_status nmpc_sensitivity(nmpc_handle* h, int instance, const double* dloss_d
   double* ta = d.dwp;    // their absolute values (backward error)
   double* sc = d.dzL;    // (|K||x|)_v + |g_v|
   CUDA_TRY(h, cudaMemcpyAsync(h->d_ctl_save, d.ctl, ni * sizeof(Ctl), cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_flags + 3, 0, sizeof(int), st));
   k_ctl_select<<<blocks_for(ni), TPB, 0, st>>>(d.ctl, ni, instance, 0);
   ++h->launches;
   // residual data at the converged point
@@ -623,7 +635,7 @@ nmpc_status nmpc_sensitivity(nmpc_handle* h, int instance, const double* dloss_d
   // (the slack weights changed too much in the last step), K(z*) is
   // refactored in place (same symbolic analysis, delta_w = 0) and the
   // refinement repeated.
-  unsigned long long* d_norms = reinterpret_cast<unsigned long long*>(h->d_flags);  // 16 bytes, free here
+  unsigned long long* d_norms = reinterpret_cast<unsigned long long*>(h->d_flags + 4);  // 16 bytes
   auto refine = [&](int sweeps) -> nmpc_status {
     k_to_factor_order<<<blocks_for(n, EW), EW, 0, st>>>(d, g, instance);
     launch_solve(h);

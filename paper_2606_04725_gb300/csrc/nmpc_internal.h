@@ -149,10 +149,13 @@ struct SnDev {
   const int* level_ptr; const int* level_sn;    // supernodes by level (height)
   const long long* sn_uvptr;  // offset of the (m_s-c_s) update vector (solves)
   double* L;
+  double* W;                  // unscaled factor panels W = L D (scratch of the cluster kernel)
   double* U;
   double* uv;                 // update vectors of the forward solve
   const double* Kdiag;        // assembled diagonal in factor order
   double pivtol;
+  long long spin_limit;       // polls of a bounded wait between CTAs
+  int* timeout;               // set to 1 when a bounded wait ran out
 };
 
 }  // namespace nmpc
