@@ -274,23 +274,22 @@ __device__ __forceinline__ int tri_lane(int r, int k) { return r * (r - 1) / 2 +
 
 // Factor pivot panel of this CTA: block columns jb .. kend-1 (pivots
 // jb .. jb+w-1) at local columns lc0 ..; the previous panel (Pl, Pw, width
-// wprev; wprev = 0 for none) is applied to the block first.
+// wprev; wprev = 0 for none) is applied to the block first.  Expects 256
+// threads: warp 0 runs the pivot chain; warps 1-3 and 5-7 (the other three
+// sub-partitions) do the bulk work; warp 4 idles so that no bulk FP64
+// instruction shares warp 0's sub-partition.
+// Warp 0 publishes each finished pivot column (W of the diagonal block and
+// 1/d_j) through shared memory and the progress counter s_col, so the rows
+// below are solved one column behind the chain instead of after it.
+constexpr int FCT = 256;
+constexpr int NBULK = 192;  // threads of warps 1-3, 5-7
+
 __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* thr, double* Lg, double* Wg,
                              const double* Pl, const double* Pw, int wprev, int m, int jb, int w, int lc0,
-                             double* sB) {
+                             double* sB, volatile int* s_col, int* s_timeout, long long limit) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   double* Fp = Fl + (size_t)lc0 * m;  // block column kk at Fp + kk*m
   const int kend = min(jb + PB, m), nb = kend - jb;
-  // ---- phase 1
-  if (warp == 1) {
-    // column 0 of the diagonal block: previous panel applied, handed to warp 0
-    if (lane < nb) {
-      double b = Fp[jb + lane];
-      for (int j = 0; j < wprev; ++j) b = fma(-Pl[(jb + lane) + (size_t)j * m], Pw[jb + (size_t)j * m], b);
-      sB[lane] = b;
-    }
-    bar_pair();
-  }
   if (warp == 0) {
     const int rA0 = 1 + (lane >= 1) + (lane >= 3) + (lane >= 6) + (lane >= 10) + (lane >= 15) + (lane >= 21);
     const bool inA = lane < 28;
@@ -300,7 +299,9 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
     double a = vA ? Fp[(jb + rA) + (size_t)kA * m] : 0.0;
     for (int j = 0; j < wprev; ++j)
       if (vA) a = fma(-Pl[(jb + rA) + (size_t)j * m], Pw[(jb + kA) + (size_t)j * m], a);
-    bar_pair();
+    // rows of the block below the pivots are solved by the bulk warps: hand them over
+    if (vA && rA >= w && kA < w) Fp[(jb + rA) + (size_t)kA * m] = a;
+    bar_pair();  // column 0 of the block from warp 1
     const int rB = lane & 7;
     double b = (lane < nb) ? sB[lane] : 0.0;
     double inv[PB];
@@ -309,7 +310,12 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
     for (int jj = 0; jj < PB; ++jj) {
       inv[jj] = 0.0;
       if (jj < w) {
-        // operands of this column's update, independent of the pivot
+        // column jj of the diagonal block is final: publish it
+        if (jj == 0) {
+          if (lane < w) Fp[jb + lane] = b;
+        } else if (vA && kA == jj && rA < w) {
+          Fp[(jb + rA) + (size_t)jj * m] = a;
+        }
         double x, y;
         if (jj == 0) {
           x = __shfl_sync(FULL, b, rA);
@@ -321,74 +327,85 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
         const double p = (jj == 0) ? __shfl_sync(FULL, b, 0) : __shfl_sync(FULL, a, tri_lane(jj, jj));
         const double iv = recip_nr(p);
         inv[jj] = iv;
-        if (lane == 0) bad = bad || !pivot_ok(p, thr[jj]);
+        if (lane == 0) {
+          bad = bad || !pivot_ok(p, thr[jj]);
+          invd[jj] = iv;
+        }
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) *s_col = jj + 1;
         if (vA && kA > jj && rA < w) a = fma(-(x * iv), y, a);
       }
     }
-    // outputs: W in place (phase 2 reads it), L and W to global memory
+    // outputs of the pivot block: L and W to global memory, trailing block columns in place
     double ik = inv[1];
 #pragma unroll
     for (int k = 2; k < PB; ++k)
       if (kA == k) ik = inv[k];
-    if (vA) {
-      Fp[(jb + rA) + (size_t)kA * m] = a;
-      if (kA < w) {
-        const size_t g = (jb + rA) + (size_t)(jb + kA) * m;
-        Lg[g] = (rA == kA) ? ik : a * ik;
-        Wg[g] = a;
-      }
+    if (vA && rA < w && kA < w) {
+      const size_t g = (jb + rA) + (size_t)(jb + kA) * m;
+      Lg[g] = (rA == kA) ? ik : a * ik;
+      Wg[g] = a;
     }
-    if (lane < nb) {
-      Fp[jb + rB] = b;
-      if (w > 0) {
-        const size_t g = jb + rB;
-        Lg[g + (size_t)jb * m] = (rB == 0) ? inv[0] : b * inv[0];
-        Wg[g + (size_t)jb * m] = b;
-      }
-    }
+    if (vA && kA >= w) Fp[(jb + rA) + (size_t)kA * m] = a;
     if (lane < w) {
-      double mine = inv[0];
-#pragma unroll
-      for (int k = 1; k < PB; ++k)
-        if (lane == k) mine = inv[k];
-      invd[lane] = mine;
+      const size_t g = (jb + rB) + (size_t)jb * m;
+      Lg[g] = (rB == 0) ? inv[0] : b * inv[0];
+      Wg[g] = b;
     }
     if (lane == 0 && bad) flag_fail(ctl);
-  } else if (wprev > 0 && (warp & 3) != 0) {
-    // rows below the diagonal block: previous panel applied (warps off warp 0's sub-partition)
-    const int bw = (warp < 4) ? warp - 1 : warp - 2;  // 0..5
-    const int nbw = (blockDim.x / 32 >= 8) ? 6 : 3;
-    const int rows = m - kend;
-    for (int t = bw * 32 + lane; t < rows * nb; t += nbw * 32) {
-      const int kk = t / rows;
-      const int i = kend + (t - kk * rows);
-      double acc = Fp[i + (size_t)kk * m];
-#pragma unroll
-      for (int j = 0; j < PB; ++j)
-        if (j < wprev) acc = fma(-Pl[i + (size_t)j * m], Pw[(jb + kk) + (size_t)j * m], acc);
-      Fp[i + (size_t)kk * m] = acc;
+  } else if ((warp & 3) != 0) {
+    const int bt = ((warp < 4) ? warp - 1 : warp - 2) * 32 + lane;  // 0 .. NBULK-1
+    if (warp == 1) {
+      // column 0 of the diagonal block: previous panel applied, handed to warp 0
+      if (lane < nb) {
+        double v = Fp[jb + lane];
+        for (int j = 0; j < wprev; ++j) v = fma(-Pl[(jb + lane) + (size_t)j * m], Pw[jb + (size_t)j * m], v);
+        sB[lane] = v;
+        if (lane >= w) Fp[jb + lane] = v;
+      }
+      bar_pair();
     }
-  }
-  __syncthreads();
-  // ---- phase 2: rows below the pivot block, l_ij = (F_ij - sum_{k<j} l_ik W_jk) / d_j
-  for (int i = jb + w + tid; i < m; i += blockDim.x) {
-    double f[PB];
+    if (wprev > 0) {
+      // rows below the diagonal block: previous panel applied, one entry per thread
+      const int rows = m - kend;
+      for (int t = bt; t < rows * nb; t += NBULK) {
+        const int kk = t / rows;
+        const int i = kend + (t - kk * rows);
+        double acc = Fp[i + (size_t)kk * m];
 #pragma unroll
-    for (int k = 0; k < PB; ++k) f[k] = (k < w) ? Fp[i + (size_t)k * m] : 0.0;
+        for (int j = 0; j < PB; ++j)
+          if (j < wprev) acc = fma(-Pl[i + (size_t)j * m], Pw[(jb + kk) + (size_t)j * m], acc);
+        Fp[i + (size_t)kk * m] = acc;
+      }
+      asm volatile("bar.sync 2, %0;" ::"r"(NBULK) : "memory");
+    }
+    // rows below the pivot block, one column behind the chain:
+    // l_ij = (F_ij - sum_{k<j} l_ik W_jk) / d_j
+    for (int i = jb + w + bt; i < m; i += NBULK) {
+      double f[PB];
 #pragma unroll
-    for (int jj = 0; jj < PB; ++jj) {
-      if (jj < w) {
-        const double lj = f[jj] * invd[jj];
-        const size_t g = i + (size_t)(jb + jj) * m;
-        Lg[g] = lj;
-        Wg[g] = f[jj];
+      for (int k = 0; k < PB; ++k) f[k] = (k < w) ? Fp[i + (size_t)k * m] : 0.0;
 #pragma unroll
-        for (int k = jj + 1; k < PB; ++k)
-          if (k < w) f[k] = fma(-lj, Fp[(jb + k) + (size_t)jj * m], f[k]);
+      for (int jj = 0; jj < PB; ++jj) {
+        if (jj < w) {
+          long long it = 0;
+          while (*s_col <= jj && !*(volatile int*)s_timeout)
+            if (++it > limit) *(volatile int*)s_timeout = 1;
+          __threadfence_block();
+          const double lj = f[jj] * invd[jj];
+          const size_t g = i + (size_t)(jb + jj) * m;
+          Lg[g] = lj;
+          Wg[g] = f[jj];
+#pragma unroll
+          for (int k = jj + 1; k < PB; ++k)
+            if (k < w) f[k] = fma(-lj, Fp[(jb + k) + (size_t)jj * m], f[k]);
+        }
       }
     }
   }
   __syncthreads();
+  if (tid == 0) *s_col = 0;
 }
 
 __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
@@ -415,32 +432,55 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
   double* invd = thr + ncl;                  // ncl: 1/d of own pivot columns
   __shared__ int s_pub;                      // panels of this CTA published so far
   __shared__ int s_timeout;
+  __shared__ int s_col;                      // pivot columns of the current panel published by warp 0
   __shared__ double sB[PB];
   auto lcol = [&](int k) { return ((k / PB) / Q) * PB + (k % PB); };
   // ---- assemble: own columns from the condensed values, then the children
-  for (int t = tid; t < m * ncl; t += nt) {
-    const int i = t % m, lc = t / m;
-    const int k = ((lc / PB) * Q + q) * PB + lc % PB;
-    Fl[t] = (k < c) ? Lp[i + (size_t)k * m] : 0.0;
+  for (int t0 = tid; t0 < m * ncl; t0 += 4 * nt) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u * nt;
+      const int i = t % m, lc = t / m;
+      const int k = ((lc / PB) * Q + q) * PB + lc % PB;
+      v[u] = (t < m * ncl && k < c) ? Lp[i + (size_t)k * m] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (t0 + u * nt < m * ncl) Fl[t0 + u * nt] = v[u];
   }
   for (int lc = tid; lc < ncl; lc += nt) {
     const int k = ((lc / PB) * Q + q) * PB + lc % PB;
     thr[lc] = (k < c) ? s.pivtol * fabs(kd[k]) : 0.0;
   }
-  if (tid == 0) { s_pub = 0; s_timeout = 0; }
+  if (tid == 0) { s_pub = 0; s_timeout = 0; s_col = 0; }
   __syncthreads();
+  // children's update matrices, four entries per thread in flight (the loads
+  // of the row map and the values do not depend on each other)
   for (int qq = s.sn_child_ptr[J]; qq < s.sn_child_ptr[J + 1]; ++qq) {
     const int C = s.sn_child[qq];
     const int mc = s.sn_nrow[C] - s.sn_ncol[C];
     const int* rel = s.sn_rel + s.sn_relptr[C];
     const double* UC = s.U + s.sn_Uptr[C];
     const int tot = mc * (mc + 1) / 2;
-    for (int t = tid; t < tot; t += nt) {
-      const int b = tri_col(t, mc);
-      const int rb = rel[b];
-      if ((rb / PB) % Q != q) continue;
-      const int a = b + (t - (b * mc - b * (b - 1) / 2));
-      Fl[rel[a] + (size_t)lcol(rb) * m] += UC[a + (size_t)b * mc];
+    for (int t0 = tid; t0 < tot; t0 += 4 * nt) {
+      int ra[4], rb[4];
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u * nt;
+        ra[u] = -1;
+        if (t < tot) {
+          const int b = tri_col(t, mc);
+          const int a = b + (t - (b * mc - b * (b - 1) / 2));
+          rb[u] = rel[b];
+          ra[u] = rel[a];
+          v[u] = UC[a + (size_t)b * mc];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ra[u] >= 0 && (rb[u] / PB) % Q == q) Fl[ra[u] + (size_t)lcol(rb[u]) * m] += v[u];
     }
     __syncthreads();
   }
@@ -448,7 +488,7 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
   const int npan = (c + PB - 1) / PB;
   const long long limit = s.spin_limit;
   if (q == 0 && npan > 0) {
-    panel_factor(ctl, Fl, invd, thr, Lp, Wp, Pl, Pw, 0, m, 0, min(PB, c), 0, sB);
+    panel_factor(ctl, Fl, invd, thr, Lp, Wp, Pl, Pw, 0, m, 0, min(PB, c), 0, sB, &s_col, &s_timeout, limit);
     if (tid == 0) st_release_cluster(&s_pub, 1);
   }
   for (int p = 0; p < npan; ++p) {
@@ -467,12 +507,25 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
     }
     {
       const int r0 = jb + w, rows = m - r0;
-      for (int t = tid; t < rows * w; t += nt) {
-        const int jj = t / rows;
-        const int i = r0 + (t - jj * rows);
-        const size_t g = i + (size_t)(jb + jj) * m;
-        Pw[i + (size_t)jj * m] = __ldcg(Wp + g);
-        Pl[i + (size_t)jj * m] = __ldcg(Lp + g);
+      for (int t0 = tid; t0 < rows * w; t0 += 2 * nt) {
+        double vw[2], vl[2];
+        int o[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int t = t0 + u * nt;
+          o[u] = -1;
+          if (t < rows * w) {
+            const int jj = t / rows;
+            const int i = r0 + (t - jj * rows);
+            const size_t g = i + (size_t)(jb + jj) * m;
+            vw[u] = __ldcg(Wp + g);
+            vl[u] = __ldcg(Lp + g);
+            o[u] = i + jj * m;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (o[u] >= 0) { Pw[o[u]] = vw[u]; Pl[o[u]] = vl[u]; }
       }
     }
     __syncthreads();
@@ -482,7 +535,7 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
     if (look) {
       const int k0 = nx * PB;
       panel_factor(ctl, Fl, invd + (nx / Q) * PB, thr + (nx / Q) * PB, Lp, Wp, Pl, Pw, w, m, k0,
-                   min(PB, c - k0), (nx / Q) * PB, sB);
+                   min(PB, c - k0), (nx / Q) * PB, sB, &s_col, &s_timeout, limit);
       if (tid == 0) st_release_cluster(&s_pub, nx / Q + 1);
     }
     // ---- rank-w update of the remaining own columns
@@ -512,22 +565,49 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
 }
 
 // ---------------------------------------------------------------------------
-// Triangular solves with K = L D L^T, one thread block per supernode of a
-// level.  Forward: L y = P b over the tree (children first), then z = D^{-1} y;
-// backward: L^T x = z (parents first).  The c x c unit triangle runs in one
-// warp with the vector's pivot entries held in lanes' registers (row r in
-// lane r % 32, slot r / 32): one shuffle and one FMA per column on the
-// critical path.  The rectangular parts are dot products split over groups
-// of threads with shuffle reductions.
+// Triangular solves with K = L D L^T, one thread block (4 warps) per
+// supernode of a level.  Forward: L y = P b over the tree (children first),
+// then z = D^{-1} y; backward: L^T x = z (parents first).
+//
+// The panel (m x c, contiguous, 16-byte aligned) is staged in shared memory
+// by one bulk asynchronous copy (cp.async.bulk, completion on an mbarrier)
+// while the right-hand side is gathered.  The c x c unit triangle is a
+// pipeline over the four warps: warp s holds rows 32s .. 32s+31 of the vector
+// in registers and applies columns in order, one FMA instruction per column;
+// the warp that owns column j takes y_j from its own lane by a shuffle and
+// publishes it through shared memory and a per-warp progress counter, which
+// the other warps wait on.  The critical path is one shuffle, one FMA and a
+// shared-memory store per column.  The rectangular parts are dot products
+// split over groups of threads with shuffle reductions.
 // ---------------------------------------------------------------------------
-constexpr int SOLVE_SLOTS = 4;  // register path for c <= 128
+constexpr int ST = 128;  // threads of a solve block
 
-__device__ __forceinline__ double pick(const double (&v)[SOLVE_SLOTS], int sl) {
-  double r = v[0];
-#pragma unroll
-  for (int s = 1; s < SOLVE_SLOTS; ++s)
-    if (sl == s) r = v[s];
-  return r;
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// bounded wait for phase 0 of the barrier; false if the limit ran out
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, long long limit) {
+  unsigned done = 0;
+  long long it = 0;
+  do {
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar))
+        : "memory");
+  } while (!done && ++it < limit);
+  return done != 0;
 }
 
 // threads per dot product so that `count` products fill the block
@@ -537,17 +617,40 @@ __device__ __forceinline__ int group_width(int count, int nt) {
   return g;
 }
 
-__global__ void k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
+// spin until the progress counter reaches `need` (bounded)
+__device__ __forceinline__ void wait_progress(volatile int* ctr, int need, long long limit, int* timeout) {
+  long long it = 0;
+  while (*ctr < need) {
+    if (++it > limit) {
+      *(volatile int*)timeout = 1;
+      break;
+    }
+  }
+  __threadfence_block();
+}
+
+__global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
+  __shared__ unsigned long long bar;
+  __shared__ int prog[ST / 32];
+  __shared__ int s_to;
   const int J = list[blockIdx.x];
   if (d.ctl[s.sn_inst[J]].status != ST_RUNNING) return;
   const int m = s.sn_nrow[J], c = s.sn_ncol[J], first = s.sn_first[J];
   const double* Lg = s.L + s.sn_Lptr[J];
-  const bool stage = (long long)m * c + m <= smem_cap;  // else read the panel from global memory
-  double* fv = dsm + (stage ? (size_t)m * c : 0);       // m
-  const double* Ls = stage ? dsm : Lg;                   // m x c
+  const long long lsz = ((long long)m * c + 1) & ~1LL;
+  const bool stage = lsz + m + c <= smem_cap;
+  double* fv = dsm + (stage ? lsz : 0);  // m
+  double* ys = fv + m;                   // c: published pivot values
+  const double* Ls = stage ? dsm : Lg;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (stage)
-    for (int t = tid; t < m * c; t += nt) dsm[t] = Lg[t];
+  if (tid < ST / 32) prog[tid] = 0;
+  if (tid == 0) {
+    s_to = 0;
+    if (stage) {
+      mbar_init(&bar);
+      bulk_load(dsm, Lg, (unsigned)(lsz * 8), &bar);
+    }
+  }
   for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
   __syncthreads();
   for (int q = s.sn_child_ptr[J]; q < s.sn_child_ptr[J + 1]; ++q) {
@@ -558,32 +661,39 @@ __global__ void k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
     for (int a = tid; a < mc; a += nt) fv[rel[a]] += uvC[a];
     __syncthreads();
   }
-  // unit lower triangle
-  if (tid < 32) {
-    const int lane = tid;
-    if (c <= 32 * SOLVE_SLOTS) {
-      double v[SOLVE_SLOTS];
-#pragma unroll
-      for (int sl = 0; sl < SOLVE_SLOTS; ++sl) v[sl] = (lane + 32 * sl < c) ? fv[lane + 32 * sl] : 0.0;
-      for (int j = 0; j < c; ++j) {
-        const double yj = __shfl_sync(FULL, pick(v, j >> 5), j & 31);
-        const double* col = Ls + (size_t)j * m;
-#pragma unroll
-        for (int sl = 0; sl < SOLVE_SLOTS; ++sl) {
-          const int i = lane + 32 * sl;
-          if (i > j && i < c) v[sl] = fma(-col[i], yj, v[sl]);
+  if (stage && !mbar_wait(&bar, s.spin_limit)) s_to = 1;
+  __syncthreads();
+  const int wp = tid >> 5, lane = tid & 31;
+  if (stage && c <= ST) {
+    // pipelined unit lower triangle
+    if (32 * wp < c) {
+      const int r = 32 * wp + lane;
+      double v = (r < c) ? fv[r] : 0.0;
+      const int jmax = min(c, 32 * wp + 32);
+      for (int j = 0; j < jmax; ++j) {
+        const double lv = (r > j && r < c) ? Ls[r + (size_t)j * m] : 0.0;
+        double yj;
+        if (j < 32 * wp) {
+          wait_progress(&prog[j >> 5], (j & 31) + 1, s.spin_limit, &s_to);
+          yj = ys[j];
+        } else {
+          yj = __shfl_sync(FULL, v, j & 31);
+          if (lane == (j & 31)) {
+            ys[j] = yj;
+            __threadfence_block();
+            *(volatile int*)&prog[wp] = (j & 31) + 1;
+          }
         }
+        v = fma(-lv, yj, v);
       }
-#pragma unroll
-      for (int sl = 0; sl < SOLVE_SLOTS; ++sl)
-        if (lane + 32 * sl < c) fv[lane + 32 * sl] = v[sl];
-    } else {
-      for (int j = 0; j < c; ++j) {
-        const double yj = fv[j];
-        __syncwarp();
-        for (int i = j + 1 + lane; i < c; i += 32) fv[i] = fma(-Ls[i + (size_t)j * m], yj, fv[i]);
-        __syncwarp();
-      }
+      if (r < c) fv[r] = v;
+    }
+  } else if (tid < 32) {
+    for (int j = 0; j < c; ++j) {
+      const double yj = fv[j];
+      __syncwarp();
+      for (int i = j + 1 + lane; i < c; i += 32) fv[i] = fma(-Ls[i + (size_t)j * m], yj, fv[i]);
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -603,28 +713,34 @@ __global__ void k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
     }
   }
   for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
+  if (tid == 0 && s_to) atomicExch(s.timeout, 1);
 }
 
-__global__ void k_bwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
+__global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
+  __shared__ unsigned long long bar;
+  __shared__ int prog[ST / 32];
+  __shared__ int s_to;
   const int J = list[blockIdx.x];
   if (d.ctl[s.sn_inst[J]].status != ST_RUNNING) return;
   const int m = s.sn_nrow[J], c = s.sn_ncol[J], first = s.sn_first[J];
   const double* Lg = s.L + s.sn_Lptr[J];
   const int* rows_idx = s.sn_rows + s.sn_rowptr[J];
-  // staged: the panel (m x c) and the transposed pivot block T(i, j) = L(j, i) (c x c)
-  const bool stage = (long long)m * c + (long long)c * c + m <= smem_cap;
-  double* xv = dsm + (stage ? (size_t)m * c + (size_t)c * c : 0);  // m
+  const long long lsz = ((long long)m * c + 1) & ~1LL;
+  const bool stage = lsz + m + c <= smem_cap;
+  double* xv = dsm + (stage ? lsz : 0);  // m
+  double* xs = xv + m;                   // c: published solution values
   const double* Ls = stage ? dsm : Lg;
-  double* T = dsm + (size_t)m * c;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (stage) {
-    for (int t = tid; t < m * c; t += nt) dsm[t] = Lg[t];
-    for (int t = tid; t < c * c; t += nt) {
-      const int i = t % c, j = t / c;
-      T[t] = (i < j) ? Lg[j + (size_t)i * m] : 0.0;
+  if (tid < ST / 32) prog[tid] = 0;
+  if (tid == 0) {
+    s_to = 0;
+    if (stage) {
+      mbar_init(&bar);
+      bulk_load(dsm, Lg, (unsigned)(lsz * 8), &bar);
     }
   }
   for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : d.b[rows_idx[i]];
+  if (stage && !mbar_wait(&bar, s.spin_limit)) s_to = 1;
   __syncthreads();
   // t_j = z_j - sum_{i >= c} L_ij x_i  (x_i of ancestors, already solved)
   const int below = m - c;
@@ -641,36 +757,45 @@ __global__ void k_bwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
     }
   }
   __syncthreads();
-  // unit upper triangle L_cc^T x = t, last column first
-  if (tid < 32) {
-    const int lane = tid;
-    if (stage && c <= 32 * SOLVE_SLOTS) {
-      double v[SOLVE_SLOTS];
-#pragma unroll
-      for (int sl = 0; sl < SOLVE_SLOTS; ++sl) v[sl] = (lane + 32 * sl < c) ? xv[lane + 32 * sl] : 0.0;
-      for (int j = c - 1; j >= 0; --j) {
-        const double xj = __shfl_sync(FULL, pick(v, j >> 5), j & 31);
-        const double* col = T + (size_t)j * c;  // col[i] = L(j, i)
-#pragma unroll
-        for (int sl = 0; sl < SOLVE_SLOTS; ++sl) {
-          const int i = lane + 32 * sl;
-          if (i < j) v[sl] = fma(-col[i], xj, v[sl]);
+  const int wp = tid >> 5, lane = tid & 31;
+  if (stage && c <= ST) {
+    // pipelined unit upper triangle L_cc^T x = t, last column first; warp w
+    // publishes its columns top-down, prog[w] counting them
+    if (32 * wp < c) {
+      const int i = 32 * wp + lane;
+      double v = (i < c) ? xv[i] : 0.0;
+      const int top = min(c, 32 * wp + 32) - 1;  // highest row of this warp
+      for (int j = c - 1; j >= 32 * wp; --j) {
+        const double lv = (i < j) ? Ls[j + (size_t)i * m] : 0.0;  // L(j, i)
+        double xj;
+        if (j > top) {
+          const int w2 = j >> 5;
+          const int top2 = min(c, 32 * w2 + 32) - 1;
+          wait_progress(&prog[w2], top2 - j + 1, s.spin_limit, &s_to);
+          xj = xs[j];
+        } else {
+          xj = __shfl_sync(FULL, v, j & 31);
+          if (lane == (j & 31)) {
+            xs[j] = xj;
+            __threadfence_block();
+            *(volatile int*)&prog[wp] = top - j + 1;
+          }
         }
+        v = fma(-lv, xj, v);
       }
-#pragma unroll
-      for (int sl = 0; sl < SOLVE_SLOTS; ++sl)
-        if (lane + 32 * sl < c) xv[lane + 32 * sl] = v[sl];
-    } else {
-      for (int j = c - 1; j >= 0; --j) {
-        const double xj = xv[j];
-        __syncwarp();
-        for (int i = lane; i < j; i += 32) xv[i] = fma(-Ls[j + (size_t)i * m], xj, xv[i]);
-        __syncwarp();
-      }
+      if (i < c) xv[i] = v;
+    }
+  } else if (tid < 32) {
+    for (int j = c - 1; j >= 0; --j) {
+      const double xj = xv[j];
+      __syncwarp();
+      for (int i = lane; i < j; i += 32) xv[i] = fma(-Ls[j + (size_t)i * m], xj, xv[i]);
+      __syncwarp();
     }
   }
   __syncthreads();
   for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
+  if (tid == 0 && s_to) atomicExch(s.timeout, 1);
 }
 
 }  // namespace nmpc

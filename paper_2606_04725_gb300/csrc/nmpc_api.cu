@@ -68,7 +68,7 @@ namespace {
 
 constexpr int SMEM_FACTOR_CAP_BYTES = 200 * 1024;
 constexpr int FACTOR_THREADS = 1024;  // 32 warps per front hide FP64 and shared-memory latency
-constexpr int CLUSTER_THREADS = 256;  // per CTA of the cluster-cooperative front kernel
+constexpr int CLUSTER_THREADS = 256;  // per CTA of the cluster-cooperative front kernel (FCT in factor_kernels.cu)
 constexpr int CLUSTER_PB = 8;         // column block of the cluster kernel (PB in factor_kernels.cu)
 constexpr int SENS_REFINE = 6;        // refinement sweeps of the adjoint solve
 
@@ -310,10 +310,10 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
       const long long mm = A.sn_nrow[sn], cc = A.sn_ncol[sn];
       const long long need = mm * mm + mm;  // whole front plus one unscaled column
       h->lvl_smem_factor[l] = std::max<int>(h->lvl_smem_factor[l], (int)((need <= h->smem_cap_doubles ? need : mm) * 8));
-      const long long fneed = (mm * cc + mm <= h->smem_cap_doubles) ? mm * cc + mm : mm;
-      h->lvl_smem_solve[l] = std::max<int>(h->lvl_smem_solve[l], (int)(fneed * 8));
-      const long long bneed = (mm * cc + cc * cc + mm <= h->smem_cap_doubles) ? mm * cc + cc * cc + mm : mm;
-      h->lvl_smem_bwd[l] = std::max<int>(h->lvl_smem_bwd[l], (int)(bneed * 8));
+      const long long lsz = (mm * cc + 1) & ~1LL;  // staged panel (k_fwd_level / k_bwd_level)
+      const long long sneed = (lsz + mm + cc <= h->smem_cap_doubles) ? lsz + mm + cc : mm + cc;
+      h->lvl_smem_solve[l] = std::max<int>(h->lvl_smem_solve[l], (int)(sneed * 8));
+      h->lvl_smem_bwd[l] = std::max<int>(h->lvl_smem_bwd[l], (int)(sneed * 8));
     }
   *out = h;
   return NMPC_OK;

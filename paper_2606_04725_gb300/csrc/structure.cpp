@@ -495,7 +495,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
     for (int s = 0; s < ns; ++s) {
       const long long c = A.sn_ncol[s], r = A.sn_nrow[s];
       A.sn_rowptr[s + 1] = A.sn_rowptr[s] + r;
-      A.sn_Lptr[s + 1] = A.sn_Lptr[s] + r * c;
+      A.sn_Lptr[s + 1] = A.sn_Lptr[s] + (((long long)r * c + 1) & ~1LL);  // panels start on 16-byte boundaries
       A.sn_Uptr[s + 1] = A.sn_Uptr[s] + (r - c) * (r - c);
       A.sn_uvptr[s + 1] = A.sn_uvptr[s] + (r - c);
       for (long long j = 0; j < c; ++j) {
