@@ -246,6 +246,25 @@ __device__ __forceinline__ int ld_acquire_cluster(const int* p) {
 __device__ __forceinline__ void st_release_cluster(int* p, int v) {
   asm volatile("st.release.cluster.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Hand-off of single values between warps of a CTA without fences: a slot
+// holds SENTINEL (a signaling NaN, which no arithmetic produces: arithmetic
+// results are quiet NaNs at worst) until its value is stored; one 64-bit
+// store publishes the value together with its readiness.
+constexpr long long SENTINEL = 0x7ff4deadbeef0001LL;
+__device__ __forceinline__ double take(const double* slot, long long limit, int* timeout) {
+  const volatile double* v = slot;
+  double x = *v;
+  long long it = 0;
+  while (__double_as_longlong(x) == SENTINEL) {
+    if (++it > limit) {
+      *(volatile int*)timeout = 1;
+      break;
+    }
+    x = *v;
+  }
+  return x;
+}
+
 __device__ __forceinline__ void bar_pair() { asm volatile("bar.sync 1, 64;" ::: "memory"); }  // warps 0 and 1
 
 // Fl[i + lc*m] -= sum_{jj<w} Pl[i + jj*m] * Pw[k + jj*m] for own columns
@@ -279,14 +298,14 @@ __device__ __forceinline__ int tri_lane(int r, int k) { return r * (r - 1) / 2 +
 // sub-partitions) do the bulk work; warp 4 idles so that no bulk FP64
 // instruction shares warp 0's sub-partition.
 // Warp 0 publishes each finished pivot column (W of the diagonal block and
-// 1/d_j) through shared memory and the progress counter s_col, so the rows
-// below are solved one column behind the chain instead of after it.
+// 1/d_j) through the sentinel slots pub[j*PB + k] (pub[j*PB + j] = 1/d_j), so
+// the rows below are solved one column behind the chain instead of after it.
 constexpr int FCT = 256;
 constexpr int NBULK = 192;  // threads of warps 1-3, 5-7
 
 __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* thr, double* Lg, double* Wg,
                              const double* Pl, const double* Pw, int wprev, int m, int jb, int w, int lc0,
-                             double* sB, volatile int* s_col, int* s_timeout, long long limit) {
+                             double* sB, double* pub, int* s_timeout, long long limit) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   double* Fp = Fl + (size_t)lc0 * m;  // block column kk at Fp + kk*m
   const int kend = min(jb + PB, m), nb = kend - jb;
@@ -313,8 +332,10 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
         // column jj of the diagonal block is final: publish it
         if (jj == 0) {
           if (lane < w) Fp[jb + lane] = b;
+          if (lane > 0 && lane < w) pub[lane] = b;
         } else if (vA && kA == jj && rA < w) {
           Fp[(jb + rA) + (size_t)jj * m] = a;
+          if (rA > jj) pub[jj * PB + rA] = a;
         }
         double x, y;
         if (jj == 0) {
@@ -330,10 +351,8 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
         if (lane == 0) {
           bad = bad || !pivot_ok(p, thr[jj]);
           invd[jj] = iv;
+          pub[jj * PB + jj] = iv;
         }
-        __threadfence_block();
-        __syncwarp();
-        if (lane == 0) *s_col = jj + 1;
         if (vA && kA > jj && rA < w) a = fma(-(x * iv), y, a);
       }
     }
@@ -357,6 +376,7 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
   } else if ((warp & 3) != 0) {
     const int bt = ((warp < 4) ? warp - 1 : warp - 2) * 32 + lane;  // 0 .. NBULK-1
     if (warp == 1) {
+      for (int t = lane; t < PB * PB; t += 32) pub[t] = __longlong_as_double(SENTINEL);
       // column 0 of the diagonal block: previous panel applied, handed to warp 0
       if (lane < nb) {
         double v = Fp[jb + lane];
@@ -378,8 +398,8 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
           if (j < wprev) acc = fma(-Pl[i + (size_t)j * m], Pw[(jb + kk) + (size_t)j * m], acc);
         Fp[i + (size_t)kk * m] = acc;
       }
-      asm volatile("bar.sync 2, %0;" ::"r"(NBULK) : "memory");
     }
+    asm volatile("bar.sync 2, %0;" ::"r"(NBULK) : "memory");
     // rows below the pivot block, one column behind the chain:
     // l_ij = (F_ij - sum_{k<j} l_ik W_jk) / d_j
     for (int i = jb + w + bt; i < m; i += NBULK) {
@@ -389,23 +409,18 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
 #pragma unroll
       for (int jj = 0; jj < PB; ++jj) {
         if (jj < w) {
-          long long it = 0;
-          while (*s_col <= jj && !*(volatile int*)s_timeout)
-            if (++it > limit) *(volatile int*)s_timeout = 1;
-          __threadfence_block();
-          const double lj = f[jj] * invd[jj];
+          const double lj = f[jj] * take(pub + jj * PB + jj, limit, s_timeout);
           const size_t g = i + (size_t)(jb + jj) * m;
           Lg[g] = lj;
           Wg[g] = f[jj];
 #pragma unroll
           for (int k = jj + 1; k < PB; ++k)
-            if (k < w) f[k] = fma(-lj, Fp[(jb + k) + (size_t)jj * m], f[k]);
+            if (k < w) f[k] = fma(-lj, take(pub + jj * PB + k, limit, s_timeout), f[k]);
         }
       }
     }
   }
   __syncthreads();
-  if (tid == 0) *s_col = 0;
 }
 
 __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
@@ -432,7 +447,7 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
   double* invd = thr + ncl;                  // ncl: 1/d of own pivot columns
   __shared__ int s_pub;                      // panels of this CTA published so far
   __shared__ int s_timeout;
-  __shared__ int s_col;                      // pivot columns of the current panel published by warp 0
+  __shared__ double s_pubv[PB * PB];         // pivot columns of the current panel, published by warp 0
   __shared__ double sB[PB];
   auto lcol = [&](int k) { return ((k / PB) / Q) * PB + (k % PB); };
   // ---- assemble: own columns from the condensed values, then the children
@@ -453,7 +468,7 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
     const int k = ((lc / PB) * Q + q) * PB + lc % PB;
     thr[lc] = (k < c) ? s.pivtol * fabs(kd[k]) : 0.0;
   }
-  if (tid == 0) { s_pub = 0; s_timeout = 0; s_col = 0; }
+  if (tid == 0) { s_pub = 0; s_timeout = 0; }
   __syncthreads();
   // children's update matrices, four entries per thread in flight (the loads
   // of the row map and the values do not depend on each other)
@@ -488,7 +503,7 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
   const int npan = (c + PB - 1) / PB;
   const long long limit = s.spin_limit;
   if (q == 0 && npan > 0) {
-    panel_factor(ctl, Fl, invd, thr, Lp, Wp, Pl, Pw, 0, m, 0, min(PB, c), 0, sB, &s_col, &s_timeout, limit);
+    panel_factor(ctl, Fl, invd, thr, Lp, Wp, Pl, Pw, 0, m, 0, min(PB, c), 0, sB, s_pubv, &s_timeout, limit);
     if (tid == 0) st_release_cluster(&s_pub, 1);
   }
   for (int p = 0; p < npan; ++p) {
@@ -535,7 +550,7 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
     if (look) {
       const int k0 = nx * PB;
       panel_factor(ctl, Fl, invd + (nx / Q) * PB, thr + (nx / Q) * PB, Lp, Wp, Pl, Pw, w, m, k0,
-                   min(PB, c - k0), (nx / Q) * PB, sB, &s_col, &s_timeout, limit);
+                   min(PB, c - k0), (nx / Q) * PB, sB, s_pubv, &s_timeout, limit);
       if (tid == 0) st_release_cluster(&s_pub, nx / Q + 1);
     }
     // ---- rank-w update of the remaining own columns
@@ -575,10 +590,10 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
 // pipeline over the four warps: warp s holds rows 32s .. 32s+31 of the vector
 // in registers and applies columns in order, one FMA instruction per column;
 // the warp that owns column j takes y_j from its own lane by a shuffle and
-// publishes it through shared memory and a per-warp progress counter, which
-// the other warps wait on.  The critical path is one shuffle, one FMA and a
-// shared-memory store per column.  The rectangular parts are dot products
-// split over groups of threads with shuffle reductions.
+// stores it into its sentinel slot, from which the other warps take it.  The
+// critical path is one shuffle, one FMA and a shared-memory store per column.
+// The rectangular parts are dot products split over groups of threads with
+// shuffle reductions.
 // ---------------------------------------------------------------------------
 constexpr int ST = 128;  // threads of a solve block
 
@@ -617,21 +632,8 @@ __device__ __forceinline__ int group_width(int count, int nt) {
   return g;
 }
 
-// spin until the progress counter reaches `need` (bounded)
-__device__ __forceinline__ void wait_progress(volatile int* ctr, int need, long long limit, int* timeout) {
-  long long it = 0;
-  while (*ctr < need) {
-    if (++it > limit) {
-      *(volatile int*)timeout = 1;
-      break;
-    }
-  }
-  __threadfence_block();
-}
-
 __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
   __shared__ unsigned long long bar;
-  __shared__ int prog[ST / 32];
   __shared__ int s_to;
   const int J = list[blockIdx.x];
   if (d.ctl[s.sn_inst[J]].status != ST_RUNNING) return;
@@ -643,7 +645,6 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* lis
   double* ys = fv + m;                   // c: published pivot values
   const double* Ls = stage ? dsm : Lg;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid < ST / 32) prog[tid] = 0;
   if (tid == 0) {
     s_to = 0;
     if (stage) {
@@ -652,6 +653,7 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* lis
     }
   }
   for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
+  for (int j = tid; j < c; j += nt) ys[j] = __longlong_as_double(SENTINEL);
   __syncthreads();
   for (int q = s.sn_child_ptr[J]; q < s.sn_child_ptr[J + 1]; ++q) {
     const int C = s.sn_child[q];
@@ -674,15 +676,10 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* lis
         const double lv = (r > j && r < c) ? Ls[r + (size_t)j * m] : 0.0;
         double yj;
         if (j < 32 * wp) {
-          wait_progress(&prog[j >> 5], (j & 31) + 1, s.spin_limit, &s_to);
-          yj = ys[j];
+          yj = take(ys + j, s.spin_limit, &s_to);
         } else {
           yj = __shfl_sync(FULL, v, j & 31);
-          if (lane == (j & 31)) {
-            ys[j] = yj;
-            __threadfence_block();
-            *(volatile int*)&prog[wp] = (j & 31) + 1;
-          }
+          if (lane == (j & 31)) *(volatile double*)(ys + j) = yj;
         }
         v = fma(-lv, yj, v);
       }
@@ -718,7 +715,6 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* lis
 
 __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
   __shared__ unsigned long long bar;
-  __shared__ int prog[ST / 32];
   __shared__ int s_to;
   const int J = list[blockIdx.x];
   if (d.ctl[s.sn_inst[J]].status != ST_RUNNING) return;
@@ -731,7 +727,6 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const int* lis
   double* xs = xv + m;                   // c: published solution values
   const double* Ls = stage ? dsm : Lg;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid < ST / 32) prog[tid] = 0;
   if (tid == 0) {
     s_to = 0;
     if (stage) {
@@ -740,6 +735,7 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const int* lis
     }
   }
   for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : d.b[rows_idx[i]];
+  for (int j = tid; j < c; j += nt) xs[j] = __longlong_as_double(SENTINEL);
   if (stage && !mbar_wait(&bar, s.spin_limit)) s_to = 1;
   __syncthreads();
   // t_j = z_j - sum_{i >= c} L_ij x_i  (x_i of ancestors, already solved)
@@ -759,8 +755,7 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const int* lis
   __syncthreads();
   const int wp = tid >> 5, lane = tid & 31;
   if (stage && c <= ST) {
-    // pipelined unit upper triangle L_cc^T x = t, last column first; warp w
-    // publishes its columns top-down, prog[w] counting them
+    // pipelined unit upper triangle L_cc^T x = t, last column first
     if (32 * wp < c) {
       const int i = 32 * wp + lane;
       double v = (i < c) ? xv[i] : 0.0;
@@ -769,17 +764,10 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const int* lis
         const double lv = (i < j) ? Ls[j + (size_t)i * m] : 0.0;  // L(j, i)
         double xj;
         if (j > top) {
-          const int w2 = j >> 5;
-          const int top2 = min(c, 32 * w2 + 32) - 1;
-          wait_progress(&prog[w2], top2 - j + 1, s.spin_limit, &s_to);
-          xj = xs[j];
+          xj = take(xs + j, s.spin_limit, &s_to);
         } else {
           xj = __shfl_sync(FULL, v, j & 31);
-          if (lane == (j & 31)) {
-            xs[j] = xj;
-            __threadfence_block();
-            *(volatile int*)&prog[wp] = top - j + 1;
-          }
+          if (lane == (j & 31)) *(volatile double*)(xs + j) = xj;
         }
         v = fma(-lv, xj, v);
       }

@@ -4,9 +4,12 @@
 // control of barrier parameter, inertia correction and termination
 // (eqs. infiniteOCP-innerTol/outerTol, Algorithm 2).
 //
-// Reductions are deterministic: every chunk of 2048 elements (never crossing
-// an instance) is reduced by one block in a fixed tree order, and the
-// per-instance control thread combines its chunks in index order.
+// Reductions are deterministic: every chunk of RED_CHUNK elements (never
+// crossing an instance) is reduced by one block in a fixed tree order, and
+// one warp per instance combines its chunks in a fixed lane order and tree.
+// Maxima and minima of non-negative values are taken on the bit patterns
+// (integer operations), which order like the values: on this GPU every FP64
+// instruction, compares included, costs tens of cycles.
 #include <cfloat>
 
 #include "kernels.h"
@@ -36,28 +39,66 @@ constexpr double LN2 = 0.69314718055994530941723212145818;
 // combine chunk partials (mantissa products) exactly as elements: one log at the end
 __device__ __forceinline__ double logacc_value(double m, double e) { return log(m) + e * LN2; }
 
-// Fixed-order block reduction of NV doubles per thread with operator OP
-// (0 sum, 1 max, 2 min, 3 product).  Result valid in thread 0.
+// max / min of doubles that are non-negative or -0 (negative values lose
+// against 0 in max, which is how the callers use it: max(0, x_1, x_2, ...))
+__device__ __forceinline__ double max_nn(double a, double b) {
+  return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ double min_nn(double a, double b) {
+  return __longlong_as_double(min(__double_as_longlong(a), __double_as_longlong(b)));
+}
+
+// combine one partial into another with operator op (0 sum, 1 max, 2 min)
+__device__ __forceinline__ double combine(int op, double a, double b) {
+  return op == 0 ? a + b : (op == 1 ? max_nn(a, b) : min_nn(a, b));
+}
+
+// Fixed-order warp reduction of NV doubles; result in lane 0.  Operator 3
+// marks a log-product pair (mantissa in slot q, exponent sum in slot q+1).
+template <int NV>
+__device__ __forceinline__ void warp_reduce(double (&v)[NV], const int (&op)[NV]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const double t = __shfl_down_sync(0xffffffffu, v[q], o);
+      if (op[q] == 3) {
+        const double te = __shfl_down_sync(0xffffffffu, v[q + 1], o);
+        logacc_mul(v[q], v[q + 1], t);
+        v[q + 1] += te;
+        ++q;
+      } else {
+        v[q] = combine(op[q], v[q], t);
+      }
+    }
+  }
+}
+
+// Fixed-order block reduction (RED_CHUNK threads); result in thread 0.
 template <int NV>
 __device__ void block_reduce(double (&v)[NV], const int (&op)[NV]) {
-  __shared__ double sh[NV][TPB / 32];
+  constexpr int NW = RED_CHUNK / 32;
+  __shared__ double sh[NV][NW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  warp_reduce<NV>(v, op);
+  if (lane == 0)
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    for (int o = 16; o > 0; o >>= 1) {
-      double t = __shfl_down_sync(0xffffffffu, v[q], o);
-      v[q] = op[q] == 0 ? v[q] + t : (op[q] == 1 ? fmax(v[q], t) : (op[q] == 2 ? fmin(v[q], t) : v[q] * t));
-    }
-    if (lane == 0) sh[q][wid] = v[q];
-  }
+    for (int q = 0; q < NV; ++q) sh[q][wid] = v[q];
   __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double a = sh[q][0];
-      for (int w = 1; w < TPB / 32; ++w)
-        a = op[q] == 0 ? a + sh[q][w] : (op[q] == 1 ? fmax(a, sh[q][w]) : (op[q] == 2 ? fmin(a, sh[q][w]) : a * sh[q][w]));
-      v[q] = a;
+    for (int q = 0; q < NV; ++q) v[q] = sh[q][0];
+    for (int w = 1; w < NW; ++w) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        if (op[q] == 3) {
+          logacc_mul(v[q], v[q + 1], sh[q][w]);
+          v[q + 1] += sh[q + 1][w];
+          ++q;
+        } else {
+          v[q] = combine(op[q], v[q], sh[q][w]);
+        }
+      }
     }
   }
   __syncthreads();
@@ -88,7 +129,7 @@ __global__ void k_red_eval(Dev d) {
   double v[11] = {0.0, 0.0, 0.0, DBL_MAX, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
   const int op[11] = {1, 1, 1, 2, 0, 0, 0, 3, 0, 0, 0};
   if (ch.kind == 0) {
-    for (int j = ch.begin + threadIdx.x; j < ch.end; j += TPB) {
+    for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
       double r = d.grad[j];
       for (int q = d.Hcsc_ptr[j]; q < d.Hcsc_ptr[j + 1]; ++q) {
         const int s = d.Hcsc_slot[q], row = s / WH;
@@ -98,30 +139,30 @@ __global__ void k_red_eval(Dev d) {
       if (fin(lo)) {
         r -= d.zL[j];
         const double p = (yj - lo) * d.zL[j];
-        v[2] = fmax(v[2], p); v[3] = fmin(v[3], p);
+        v[2] = max_nn(v[2], p); v[3] = min_nn(v[3], p);
         v[5] += d.zL[j];
         logacc_mul(v[7], v[8], yj - lo);
       }
       if (fin(hi)) {
         r += d.zU[j];
         const double p = (hi - yj) * d.zU[j];
-        v[2] = fmax(v[2], p); v[3] = fmin(v[3], p);
+        v[2] = max_nn(v[2], p); v[3] = min_nn(v[3], p);
         v[5] += d.zU[j];
         logacc_mul(v[7], v[8], hi - yj);
       }
       if (!fin(r)) v[10] += 1.0;
-      v[0] = fmax(v[0], fabs(r));
+      v[0] = max_nn(v[0], fabs(r));
       v[6] += d.fvar[j];
     }
   } else {
-    for (int r = ch.begin + threadIdx.x; r < ch.end; r += TPB) {
+    for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
       const double h = d.h[r];
       if (!fin(h)) v[10] += 1.0;
-      v[0] = fmax(v[0], fmax(fabs(d.wp[r] - d.bp[r]), fabs(d.wm[r] - d.bm[r])));
+      v[0] = max_nn(v[0], max_nn(fabs(d.wp[r] - d.bp[r]), fabs(d.wm[r] - d.bm[r])));
       const double cp = h - gam + d.sp[r], cm = -h - gam + d.sm[r];
-      v[1] = fmax(v[1], fmax(fabs(cp), fabs(cm)));
+      v[1] = max_nn(v[1], max_nn(fabs(cp), fabs(cm)));
       const double pp = d.sp[r] * d.bp[r], pm = d.sm[r] * d.bm[r];
-      v[2] = fmax(v[2], fmax(pp, pm)); v[3] = fmin(v[3], fmin(pp, pm));
+      v[2] = max_nn(v[2], max_nn(pp, pm)); v[3] = min_nn(v[3], min_nn(pp, pm));
       v[4] += fabs(d.wp[r]) + fabs(d.wm[r]);
       v[5] += d.bp[r] + d.bm[r];
       logacc_mul(v[7], v[8], d.sp[r]);
@@ -140,20 +181,24 @@ __global__ void k_red_eval(Dev d) {
 
 // Convergence tests and barrier update (Algorithm 2 outer loop; W&B A-2/A-3).
 __global__ void k_ctl_pre(Dev d, int max_iter) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= d.n_inst) return;
   Ctl c = d.ctl[i];
   if (c.status != ST_RUNNING) return;
-  double dual = 0, prim = 0, cmax = 0, cmin = DBL_MAX, sl = 0, sz = 0, f = 0, lg = 0, th = 0, nf = 0;
-  double lgm = 1.0, lge = 0.0;
-  for (int q = d.inst_chunk_ptr[i]; q < d.inst_chunk_ptr[i + 1]; ++q) {
+  // chunk partials: lanes in chunk order, then a fixed shuffle tree
+  double v[11] = {0.0, 0.0, 0.0, DBL_MAX, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
+  const int op[11] = {1, 1, 1, 2, 0, 0, 0, 3, 0, 0, 0};
+  for (int q = d.inst_chunk_ptr[i] + lane; q < d.inst_chunk_ptr[i + 1]; q += 32) {
     const RedEval& e = d.red_eval[d.inst_chunk_list[q]];
-    dual = fmax(dual, e.dual); prim = fmax(prim, e.prim); cmax = fmax(cmax, e.cmax); cmin = fmin(cmin, e.cmin);
-    sl += e.sum_l; sz += e.sum_z; f += e.f; th += e.theta; nf += e.nonfinite;
-    logacc_mul(lgm, lge, e.lgm);
-    lge += e.lge;
+    v[0] = max_nn(v[0], e.dual); v[1] = max_nn(v[1], e.prim); v[2] = max_nn(v[2], e.cmax); v[3] = min_nn(v[3], e.cmin);
+    v[4] += e.sum_l; v[5] += e.sum_z; v[6] += e.f; v[9] += e.theta; v[10] += e.nonfinite;
+    logacc_mul(v[7], v[8], e.lgm);
+    v[8] += e.lge;
   }
-  lg = logacc_value(lgm, lge);
+  warp_reduce<11>(v, op);
+  if (lane) return;
+  const double dual = v[0], prim = v[1], cmax = v[2], cmin = v[3], sl = v[4], sz = v[5], f = v[6], th = v[9], nf = v[10];
+  const double lg = logacc_value(v[7], v[8]);
   const double mrows = d.inst_m[i], nz = d.inst_nz[i];
   const double sd = fmax(S_MAX, (sl + sz) / (2.0 * mrows + nz)) / S_MAX;
   const double sc = fmax(S_MAX, sz / nz) / S_MAX;
@@ -328,28 +373,28 @@ __global__ void k_red_dir(Dev d) {
   double v[3] = {0.0, 0.0, 0.0};  // max primal ratio, max dual ratio, gphi
   const int op[3] = {1, 1, 0};
   if (ch.kind == 0) {
-    for (int j = ch.begin + threadIdx.x; j < ch.end; j += TPB) {
+    for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
       const double dy = d.dy[j];
       double gp = d.grad[j];
       if (fin(d.yL[j])) {
         const double ig = d.igL[j];
-        v[0] = fmax(v[0], -dy * ig);
+        v[0] = max_nn(v[0], -dy * ig);
         gp -= mu * ig;
-        v[1] = fmax(v[1], -d.dzL[j] * d.izL[j]);
+        v[1] = max_nn(v[1], -d.dzL[j] * d.izL[j]);
       }
       if (fin(d.yU[j])) {
         const double ig = d.igU[j];
-        v[0] = fmax(v[0], dy * ig);
+        v[0] = max_nn(v[0], dy * ig);
         gp += mu * ig;
-        v[1] = fmax(v[1], -d.dzU[j] * d.izU[j]);
+        v[1] = max_nn(v[1], -d.dzU[j] * d.izU[j]);
       }
       v[2] += gp * dy;
     }
   } else {
-    for (int r = ch.begin + threadIdx.x; r < ch.end; r += TPB) {
+    for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
       const double isp = d.isp[r], ism = d.ism[r];
-      v[0] = fmax(v[0], fmax(-d.dsp[r] * isp, -d.dsm[r] * ism));
-      v[1] = fmax(v[1], fmax(-d.dbp[r] * d.ibp[r], -d.dbm[r] * d.ibm[r]));
+      v[0] = max_nn(v[0], max_nn(-d.dsp[r] * isp, -d.dsm[r] * ism));
+      v[1] = max_nn(v[1], max_nn(-d.dbp[r] * d.ibp[r], -d.dbm[r] * d.ibm[r]));
       v[2] -= mu * (d.dsp[r] * isp + d.dsm[r] * ism);
     }
   }
@@ -363,15 +408,19 @@ __global__ void k_red_dir(Dev d) {
 
 // start of the backtracking filter line search (W&B Sec. 2.3): alpha_min
 __global__ void k_ctl_dir(Dev d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= d.n_inst) return;
   Ctl c = d.ctl[i];
   if (c.status != ST_RUNNING) return;
-  double ap = 1.0, ad = 1.0, g = 0.0;
-  for (int q = d.inst_chunk_ptr[i]; q < d.inst_chunk_ptr[i + 1]; ++q) {
+  double v[3] = {1.0, 1.0, 0.0};
+  const int op[3] = {2, 2, 0};
+  for (int q = d.inst_chunk_ptr[i] + lane; q < d.inst_chunk_ptr[i + 1]; q += 32) {
     const RedDir& e = d.red_dir[d.inst_chunk_list[q]];
-    ap = fmin(ap, e.ap); ad = fmin(ad, e.ad); g += e.gphi;
+    v[0] = min_nn(v[0], e.ap); v[1] = min_nn(v[1], e.ad); v[2] += e.gphi;
   }
+  warp_reduce<3>(v, op);
+  if (lane) return;
+  const double ap = v[0], ad = v[1], g = v[2];
   c.alpha_pri = ap;
   c.alpha_dual = ad;
   c.gphi = g;
@@ -420,14 +469,14 @@ __global__ void k_red_trial(Dev d) {
   double v[5] = {0.0, 1.0, 0.0, 0.0, 0.0};  // f, log-mantissa, log-exponent, theta, nonfinite
   const int op[5] = {0, 3, 0, 0, 0};
   if (ch.kind == 0) {
-    for (int j = ch.begin + threadIdx.x; j < ch.end; j += TPB) {
+    for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
       const double y = d.yt[j];
       v[0] += d.fvart[j];
       if (fin(d.yL[j])) logacc_mul(v[1], v[2], y - d.yL[j]);
       if (fin(d.yU[j])) logacc_mul(v[1], v[2], d.yU[j] - y);
     }
   } else {
-    for (int r = ch.begin + threadIdx.x; r < ch.end; r += TPB) {
+    for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
       const double h = d.ht[r];
       if (!fin(h)) v[4] += 1.0;
       logacc_mul(v[1], v[2], d.spt[r]);
@@ -441,25 +490,35 @@ __global__ void k_red_trial(Dev d) {
 
 // filter acceptance test of one trial (W&B Sec. 2.3, A-5.2 .. A-5.4)
 __global__ void k_ctl_ls(Dev d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= d.n_inst) return;
   Ctl c = d.ctl[i];
   if (!c.ls_active) return;
-  double f = 0, th = 0, nf = 0, lgm = 1.0, lge = 0.0;
-  for (int q = d.inst_chunk_ptr[i]; q < d.inst_chunk_ptr[i + 1]; ++q) {
+  double v[5] = {0.0, 1.0, 0.0, 0.0, 0.0};  // f, log-mantissa, log-exponent, theta, nonfinite
+  const int op[5] = {0, 3, 0, 0, 0};
+  for (int q = d.inst_chunk_ptr[i] + lane; q < d.inst_chunk_ptr[i + 1]; q += 32) {
     const RedTrial& e = d.red_trial[d.inst_chunk_list[q]];
-    f += e.f; th += e.theta; nf += e.nonfinite;
-    logacc_mul(lgm, lge, e.lgm);
-    lge += e.lge;
+    v[0] += e.f; v[3] += e.theta; v[4] += e.nonfinite;
+    logacc_mul(v[1], v[2], e.lgm);
+    v[2] += e.lge;
   }
-  const double lg = logacc_value(lgm, lge);
-  c.ls_trials++;
+  warp_reduce<5>(v, op);
+  const double f = __shfl_sync(0xffffffffu, v[0], 0), th = __shfl_sync(0xffffffffu, v[3], 0);
+  const double nf = __shfl_sync(0xffffffffu, v[4], 0);
+  const double lg = logacc_value(__shfl_sync(0xffffffffu, v[1], 0), __shfl_sync(0xffffffffu, v[2], 0));
   const double phit = f - c.mu * lg, thetat = th;
+  // filter test: lanes over the entries, any rejecting entry rejects
+  bool blocked = false;
+  {
+    const double* fth = d.filt_th + (size_t)i * FILTER_CAP;
+    const double* fph = d.filt_ph + (size_t)i * FILTER_CAP;
+    for (int q = lane; q < c.nf; q += 32) blocked = blocked || (thetat >= fth[q] && phit >= fph[q]);
+  }
+  blocked = __any_sync(0xffffffffu, blocked);
+  if (lane) return;
+  c.ls_trials++;
   c.ft = f; c.logsum_t = lg; c.theta_t = th;
-  bool ok = nf == 0 && fin(phit) && fin(thetat) && thetat <= c.theta_max;
-  const double* fth = d.filt_th + (size_t)i * FILTER_CAP;
-  const double* fph = d.filt_ph + (size_t)i * FILTER_CAP;
-  for (int q = 0; ok && q < c.nf; ++q) if (thetat >= fth[q] && phit >= fph[q]) ok = false;
+  const bool ok = nf == 0 && fin(phit) && fin(thetat) && thetat <= c.theta_max && !blocked;
   bool accepted = false;
   if (ok) {
     const bool sw = c.gphi < 0.0 && c.alpha * c.sw_gphi > c.sw_theta;
@@ -551,6 +610,64 @@ __global__ void k_summary(Dev d, int* flags) {
   }
   __syncthreads();
   if (threadIdx.x < 3) flags[threadIdx.x] = f[threadIdx.x];
+}
+
+// ------------------------------------------------ graph loop conditions
+// The interior-point loop runs as one CUDA graph with conditional nodes
+// (WHILE over iterations, IF on "still running", WHILE over inertia
+// corrections and over line-search trials).  These one-block kernels end each
+// step: they set the next condition from the per-instance control state and
+// count the trips (counters[0] outer steps, [1] factorization attempts,
+// [2] line-search trials), so the host learns the kernel count afterwards.
+// Every loop also stops at a trip limit (cap), whatever the control state
+// says, so a graph launch always ends.
+__device__ __forceinline__ void any_flags(const Dev& d, int* run, int* fac, int* ls) {
+  __shared__ int f[3];
+  if (threadIdx.x < 3) f[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < d.n_inst; i += blockDim.x) {
+    const Ctl& c = d.ctl[i];
+    if (c.status == ST_RUNNING) atomicOr(&f[0], 1);
+    if (c.need_factor) atomicOr(&f[1], 1);
+    if (c.ls_active) atomicOr(&f[2], 1);
+  }
+  __syncthreads();
+  *run = f[0];
+  *fac = f[1];
+  *ls = f[2];
+}
+
+__global__ void k_cond_pre(Dev d, cudaGraphConditionalHandle h_run, cudaGraphConditionalHandle h_if,
+                           cudaGraphConditionalHandle h_fac, int* counters, int cap) {
+  int run, fac, ls;
+  any_flags(d, &run, &fac, &ls);
+  if (threadIdx.x == 0) {
+    if (counters[0] >= cap) run = 0;
+    cudaGraphSetConditional(h_run, run ? 1u : 0u);
+    cudaGraphSetConditional(h_if, run ? 1u : 0u);
+    cudaGraphSetConditional(h_fac, (run && fac) ? 1u : 0u);
+    ++counters[0];
+  }
+}
+
+__global__ void k_cond_fac(Dev d, cudaGraphConditionalHandle h_fac, int* counters, int cap) {
+  int run, fac, ls;
+  any_flags(d, &run, &fac, &ls);
+  if (threadIdx.x == 0) {
+    if (counters[1] >= cap) fac = 0;
+    cudaGraphSetConditional(h_fac, fac ? 1u : 0u);
+    ++counters[1];
+  }
+}
+
+__global__ void k_cond_ls(Dev d, cudaGraphConditionalHandle h_ls, int* counters, int trial, int cap) {
+  int run, fac, ls;
+  any_flags(d, &run, &fac, &ls);
+  if (threadIdx.x == 0) {
+    if (counters[2] >= cap) ls = 0;
+    cudaGraphSetConditional(h_ls, ls ? 1u : 0u);
+    if (trial) ++counters[2];
+  }
 }
 
 }  // namespace nmpc

@@ -6,7 +6,7 @@
 
 namespace nmpc {
 
-constexpr int TPB = 256;  // reductions (fixed tree shape)
+constexpr int TPB = 256;  // generic element-wise and per-instance launches
 constexpr int EW = 128;   // element-wise kernels: smaller blocks spread FP64 work over more SMs
 
 // model_kernels.cu
@@ -36,6 +36,10 @@ __global__ void k_update_vars(Dev d);
 __global__ void k_update_rows(Dev d);
 __global__ void k_ctl_post(Dev d);
 __global__ void k_summary(Dev d, int* flags);
+__global__ void k_cond_pre(Dev d, cudaGraphConditionalHandle h_run, cudaGraphConditionalHandle h_if,
+                           cudaGraphConditionalHandle h_fac, int* counters, int cap);
+__global__ void k_cond_fac(Dev d, cudaGraphConditionalHandle h_fac, int* counters, int cap);
+__global__ void k_cond_ls(Dev d, cudaGraphConditionalHandle h_ls, int* counters, int trial, int cap);
 
 // factor_kernels.cu
 __global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap);

@@ -62,6 +62,11 @@ struct nmpc_handle {
   Ctl* d_ctl_save = nullptr;
   long long launches = 0;
   double sens_residual = 0.0;  // relative residual of the last adjoint solve
+  // the interior-point loop as one CUDA graph with conditional nodes
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_off = false;  // host-driven loop only (allocation-free one-shot solve)
+  long long nodes_eval = 0, nodes_factor = 0, nodes_solve = 0, nodes_trial = 0, nodes_update = 0;
 };
 
 namespace {
@@ -127,7 +132,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   h->d_tgt_inst = cv.take<int>(A.tgt_L.size());
   h->d_Drow = cv.take<double>(m);
   h->d_inst_Lbeg = cv.take<long long>(ni); h->d_inst_Lend = cv.take<long long>(ni);
-  h->d_flags = cv.take<int>(8);  // [0..2] summary, [3] wait timeout, [4..7] adjoint norms
+  h->d_flags = cv.take<int>(16);  // [0..2] summary, [3] wait timeout, [4..7] adjoint norms, [8..10] graph trip counts
   h->d_stage = cv.take<double>((size_t)ni * (A.mc.nx + A.sp_stride + 1));
   h->d_ctl_save = cv.take<Ctl>(ni);
   d.trace = cv.take<double>((size_t)ni * (h->opt.max_iter + 2) * 8);
@@ -192,6 +197,7 @@ nmpc_status launch_factor(nmpc_handle* h) {
     }
     k_factor_level<<<cnt, FACTOR_THREADS, h->lvl_smem_factor[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
                                                                    h->smem_cap_doubles);
+    ++h->launches;
   }
   return NMPC_OK;
 }
@@ -200,16 +206,208 @@ nmpc_status launch_solve(nmpc_handle* h) {
   const int nl = (int)h->lvl_ptr.size() - 1;
   for (int l = 0; l < nl; ++l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
-    if (cnt) k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
-                                                                        h->smem_cap_doubles);
+    if (!cnt) continue;
+    k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+                                                               h->smem_cap_doubles);
     ++h->launches;
   }
   for (int l = nl - 1; l >= 0; --l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
-    if (cnt) k_bwd_level<<<cnt, 128, h->lvl_smem_bwd[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
-                                                                        h->smem_cap_doubles);
+    if (!cnt) continue;
+    k_bwd_level<<<cnt, 128, h->lvl_smem_bwd[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+                                                             h->smem_cap_doubles);
     ++h->launches;
   }
+  return NMPC_OK;
+}
+
+
+// Kernel sequences of one interior-point iteration (Algorithm 2), shared by
+// the host-driven loop and the graph.  Each returns the number of launches.
+long long seq_eval(nmpc_handle* h) {
+  Dev& d = h->d;
+  cudaStream_t st = h->stream;
+  const int ni = h->A.n_inst;
+  k_eval_rows<<<blocks_for(d.m, EW), EW, 0, st>>>(d, 0, 1);
+  k_eval_vars<<<blocks_for(d.n, EW), EW, 0, st>>>(d, 0);
+  k_red_eval<<<d.n_chunks, RED_CHUNK, 0, st>>>(d);
+  k_ctl_pre<<<blocks_for(32LL * ni), TPB, 0, st>>>(d, h->opt.max_iter);
+  return 4;
+}
+
+long long seq_factor(nmpc_handle* h) {
+  Dev& d = h->d;
+  cudaStream_t st = h->stream;
+  const int ni = h->A.n_inst;
+  const dim3 zgrid(std::max(1u, std::min(1024u, blocks_for(h->A.nnzL / std::max(1, ni) + 1))), ni);
+  const long long l0 = h->launches;
+  k_zero_L<<<zgrid, TPB, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend);
+  k_rows_pre<<<blocks_for(d.m, EW), EW, 0, st>>>(d, h->d_Drow);
+  k_assemble<<<blocks_for(d.n_tgt, EW), EW, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
+  launch_factor(h);
+  k_ctl_factor<<<blocks_for(ni), TPB, 0, st>>>(d);
+  const long long levels = h->launches - l0;
+  h->launches = l0;
+  return 4 + levels;
+}
+
+long long seq_solve(nmpc_handle* h) {
+  Dev& d = h->d;
+  cudaStream_t st = h->stream;
+  const int ni = h->A.n_inst;
+  const long long l0 = h->launches;
+  k_rhs<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
+  launch_solve(h);
+  k_recover_vars<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
+  k_recover_rows<<<blocks_for(d.m, EW), EW, 0, st>>>(d);
+  k_red_dir<<<d.n_chunks, RED_CHUNK, 0, st>>>(d);
+  k_ctl_dir<<<blocks_for(32LL * ni), TPB, 0, st>>>(d);
+  const long long levels = h->launches - l0;
+  h->launches = l0;
+  return 5 + levels;
+}
+
+long long seq_trial(nmpc_handle* h) {
+  Dev& d = h->d;
+  cudaStream_t st = h->stream;
+  const int ni = h->A.n_inst;
+  k_trial_point<<<blocks_for((long long)d.n + d.m), TPB, 0, st>>>(d);
+  k_eval_rows<<<blocks_for(d.m, EW), EW, 0, st>>>(d, 1, 0);
+  k_eval_vars<<<blocks_for(d.n, EW), EW, 0, st>>>(d, 1);
+  k_red_trial<<<d.n_chunks, RED_CHUNK, 0, st>>>(d);
+  k_ctl_ls<<<blocks_for(32LL * ni), TPB, 0, st>>>(d);
+  return 5;
+}
+
+long long seq_update(nmpc_handle* h) {
+  Dev& d = h->d;
+  cudaStream_t st = h->stream;
+  const int ni = h->A.n_inst;
+  k_update_vars<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
+  k_update_rows<<<blocks_for(d.m, EW), EW, 0, st>>>(d);
+  k_ctl_post<<<blocks_for(ni), TPB, 0, st>>>(d);
+  return 3;
+}
+
+// Add a conditional node at the current point of a stream capture; the
+// capture continues after it.  Returns the node's body graph.
+cudaError_t capture_conditional(cudaStream_t cs, cudaGraphConditionalHandle hc, cudaGraphConditionalNodeType type,
+                                cudaGraph_t* body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hc;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, cg, deps, nullptr, nd, &p);
+  if (e != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// The interior-point loop (after the initialization kernels) as one graph:
+//   WHILE any instance runs:
+//     evaluate, errors, barrier update (k_ctl_pre)
+//     IF any instance runs:
+//       WHILE any instance needs a factorization: assemble, factor, inertia test
+//       right-hand side, solves, step recovery, step limits (k_ctl_dir)
+//       WHILE any line search is active: trial point, evaluate, filter test
+//       accept the step
+// The conditions are set on the device, so a solve needs no host round trip.
+nmpc_status build_graph(nmpc_handle* h) {
+  cudaStream_t cs = nullptr;
+  CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = h->stream;
+  h->stream = cs;
+  cudaGraph_t g = nullptr;
+  const char* step = "create";
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  int* ctr = h->d_flags + 8;
+  Dev& d = h->d;
+  // trip limits: outer steps, and factorization attempts / line-search trials
+  // (64 per step: far above what the inertia correction and the backtracking
+  // can take before they stop by themselves)
+  const int cap_iter = h->opt.max_iter + 2, cap_inner = 64 * cap_iter;
+  cudaGraphConditionalHandle h_run = 0, h_if = 0, h_fac = 0, h_ls = 0;  // one per conditional node
+  cudaGraph_t body_iter = nullptr, body_run = nullptr, body_fac = nullptr, body_ls = nullptr;
+  if (e == cudaSuccess) { step = "handles"; e = cudaGraphConditionalHandleCreate(&h_run, g, 1, cudaGraphCondAssignDefault); }
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_if, g, 0, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_fac, g, 0, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_ls, g, 0, 0);
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h_run;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    step = "outer while node";
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+    if (e == cudaSuccess) body_iter = p.conditional.phGraph_out[0];
+  }
+  // iteration body: evaluation, then IF running
+  if (e == cudaSuccess) step = "capture iteration body";
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body_iter, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    h->nodes_eval = seq_eval(h) + 1;
+    k_cond_pre<<<1, 256, 0, cs>>>(d, h_run, h_if, h_fac, ctr, cap_iter);
+    step = "IF node";
+    e = capture_conditional(cs, h_if, cudaGraphCondTypeIf, &body_run);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  // running: factorization loop, solves, line-search loop, update
+  if (e == cudaSuccess) step = "capture running body";
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body_run, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    step = "factor WHILE node";
+    e = capture_conditional(cs, h_fac, cudaGraphCondTypeWhile, &body_fac);
+    if (e == cudaSuccess) {
+      h->nodes_solve = seq_solve(h) + 1;
+      k_cond_ls<<<1, 256, 0, cs>>>(d, h_ls, ctr, 0, cap_inner);
+      step = "line-search WHILE node";
+      e = capture_conditional(cs, h_ls, cudaGraphCondTypeWhile, &body_ls);
+    }
+    if (e == cudaSuccess) h->nodes_update = seq_update(h);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) step = "capture factor body";
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body_fac, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    h->nodes_factor = seq_factor(h) + 1;
+    k_cond_fac<<<1, 256, 0, cs>>>(d, h_fac, ctr, cap_inner);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(cs, &out);
+  }
+  if (e == cudaSuccess) step = "capture line-search body";
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body_ls, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    h->nodes_trial = seq_trial(h) + 1;
+    k_cond_ls<<<1, 256, 0, cs>>>(d, h_ls, ctr, 1, cap_inner);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(cs, &out);
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (e == cudaSuccess) step = "instantiate";
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  h->stream = saved;
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(h, NMPC_ERR_CUDA, std::string("building the interior-point graph (") + step + "): " + cudaGetErrorString(e));
+  }
+  h->graph = g;
+  h->gexec = ex;
   return NMPC_OK;
 }
 
@@ -466,69 +664,48 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
   k_init_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, warm, push);
   ++h->launches;
   CUDA_TRY(h, cudaGetLastError());
-  const dim3 zgrid(std::max(1u, std::min(1024u, blocks_for(A.nnzL / std::max(1, ni) + 1))), ni);
-  for (int it = 0; it <= h->opt.max_iter + 1; ++it) {
-    k_eval_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, 0, 1);
-    ++h->launches;
-    k_eval_vars<<<blocks_for(n, EW), EW, 0, st>>>(d, 0);
-    ++h->launches;
-    k_red_eval<<<d.n_chunks, TPB, 0, st>>>(d);
-    ++h->launches;
-    k_ctl_pre<<<blocks_for(ni), TPB, 0, st>>>(d, h->opt.max_iter);
-    ++h->launches;
-    nmpc_status rs = read_flags(h);
-    if (rs != NMPC_OK) return rs;
-    if (!h->h_flags[0]) break;
-    for (;;) {
-      k_zero_L<<<zgrid, TPB, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend);
-      ++h->launches;
-      k_rows_pre<<<blocks_for(m, EW), EW, 0, st>>>(d, h->d_Drow);
-      ++h->launches;
-      k_assemble<<<blocks_for(d.n_tgt, EW), EW, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
-      ++h->launches;
-      launch_factor(h);
-      k_ctl_factor<<<blocks_for(ni), TPB, 0, st>>>(d);
-      ++h->launches;
+  if (h->opt.use_graph && !h->graph_off) {
+    if (!h->gexec) {
+      const nmpc_status gs = build_graph(h);
+      if (gs != NMPC_OK) return gs;
+    }
+    CUDA_TRY(h, cudaMemsetAsync(h->d_flags + 8, 0, 3 * sizeof(int), st));
+    CUDA_TRY(h, cudaGraphLaunch(h->gexec, st));
+    int ctr[4] = {0, 0, 0, 0};
+    CUDA_TRY(h, cudaMemcpyAsync(ctr, h->d_flags + 8, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaMemcpyAsync(ctr + 3, h->d_flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    // kernels the graph ran: outer steps x evaluation, running steps x (solve +
+    // update), factorization attempts, line-search trials
+    const long long running = std::max(0, ctr[0] - 1);
+    h->launches += (long long)ctr[0] * h->nodes_eval + running * (h->nodes_solve + h->nodes_update) +
+                   (long long)ctr[1] * h->nodes_factor + (long long)ctr[2] * h->nodes_trial;
+    if (ctr[3]) return fail(h, NMPC_TIMEOUT, "a bounded wait between the CTAs of a front factorization ran out");
+  } else {
+    for (int it = 0; it <= h->opt.max_iter + 1; ++it) {
+      h->launches += seq_eval(h);
+      nmpc_status rs = read_flags(h);
+      if (rs != NMPC_OK) return rs;
+      if (!h->h_flags[0]) break;
+      for (;;) {
+        h->launches += seq_factor(h);
+        CUDA_TRY(h, cudaGetLastError());
+        rs = read_flags(h);
+        if (rs != NMPC_OK) return rs;
+        if (!h->h_flags[1]) break;
+      }
+      h->launches += seq_solve(h);
       CUDA_TRY(h, cudaGetLastError());
       rs = read_flags(h);
       if (rs != NMPC_OK) return rs;
-      if (!h->h_flags[1]) break;
+      while (h->h_flags[2]) {
+        h->launches += seq_trial(h);
+        CUDA_TRY(h, cudaGetLastError());
+        rs = read_flags(h);
+        if (rs != NMPC_OK) return rs;
+      }
+      h->launches += seq_update(h);
     }
-    k_rhs<<<blocks_for(n, EW), EW, 0, st>>>(d);
-    ++h->launches;
-    launch_solve(h);
-    k_recover_vars<<<blocks_for(n, EW), EW, 0, st>>>(d);
-    ++h->launches;
-    k_recover_rows<<<blocks_for(m, EW), EW, 0, st>>>(d);
-    ++h->launches;
-    k_red_dir<<<d.n_chunks, TPB, 0, st>>>(d);
-    ++h->launches;
-    k_ctl_dir<<<blocks_for(ni), TPB, 0, st>>>(d);
-    ++h->launches;
-    CUDA_TRY(h, cudaGetLastError());
-    rs = read_flags(h);
-    if (rs != NMPC_OK) return rs;
-    while (h->h_flags[2]) {
-      k_trial_point<<<blocks_for((long long)n + m), TPB, 0, st>>>(d);
-      ++h->launches;
-      k_eval_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, 1, 0);
-      ++h->launches;
-      k_eval_vars<<<blocks_for(n, EW), EW, 0, st>>>(d, 1);
-      ++h->launches;
-      k_red_trial<<<d.n_chunks, TPB, 0, st>>>(d);
-      ++h->launches;
-      k_ctl_ls<<<blocks_for(ni), TPB, 0, st>>>(d);
-      ++h->launches;
-      CUDA_TRY(h, cudaGetLastError());
-      rs = read_flags(h);
-      if (rs != NMPC_OK) return rs;
-    }
-    k_update_vars<<<blocks_for(n, EW), EW, 0, st>>>(d);
-    ++h->launches;
-    k_update_rows<<<blocks_for(m, EW), EW, 0, st>>>(d);
-    ++h->launches;
-    k_ctl_post<<<blocks_for(ni), TPB, 0, st>>>(d);
-    ++h->launches;
   }
   if (h->ev1) CUDA_TRY(h, cudaEventRecord(h->ev1, st));
   CUDA_TRY(h, cudaMemcpyAsync(h->h_ctl.data(), d.ctl, ni * sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -815,6 +992,8 @@ void nmpc_destroy(nmpc_handle* h) {
     if (h->h_flags) cudaFreeHost(h->h_flags);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
   }
   delete h;
 }
@@ -893,6 +1072,7 @@ extern "C" nmpc_status nmpc_solve_static(const nmpc_problem* prob, const nmpc_op
   int host_flags[4] = {0, 0, 0, 0};
   if (st == NMPC_OK) {
     h->h_flags = host_flags;  // pageable host memory: no pinned allocation
+    h->graph_off = true;      // the host-driven loop: instantiating a graph allocates
     h->bound = true;
     const auto t0 = std::chrono::steady_clock::now();
     st = nmpc_set_params(h, -1, x0, setpoint, u_prev, on_device);

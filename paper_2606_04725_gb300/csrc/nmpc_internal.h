@@ -61,6 +61,9 @@ struct ModelConst {
 };
 
 // Reduction chunks never straddle an instance.  kind 0: variables, 1: rows.
+// One chunk is reduced by one block of RED_CHUNK threads (one element per
+// thread): small chunks spread the FP64 work of a reduction over many SMs.
+constexpr int RED_CHUNK = 128;
 struct Chunk {
   int inst, kind, begin, end;
 };

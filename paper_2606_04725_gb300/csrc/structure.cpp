@@ -605,7 +605,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       A.th_ptr.push_back((int)A.th_a.size());
     }
     // reduction chunks (never crossing an instance)
-    const int CH = 512;
+    const int CH = RED_CHUNK;
     A.chunks.clear();
     A.inst_chunk_ptr.assign(ni + 1, 0);
     for (int i = 0; i < ni; ++i) {
