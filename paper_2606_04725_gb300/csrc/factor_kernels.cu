@@ -30,6 +30,28 @@ extern __shared__ double dsm[];
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Copy a front descriptor into shared memory (one round of loads by the
+// first threads of the block); the caller synchronizes before reading it.
+__device__ __forceinline__ void load_desc(FrontDesc* dst, const FrontDesc* src) {
+  static_assert(sizeof(FrontDesc) % 8 == 0, "descriptor size");
+  const long long* a = reinterpret_cast<const long long*>(src);
+  long long* b = reinterpret_cast<long long*>(dst);
+  for (int t = threadIdx.x; t < (int)(sizeof(FrontDesc) / 8); t += blockDim.x) b[t] = a[t];
+}
+
+// Child k of a front: size of its update matrix/vector and where they live.
+struct ChildRef {
+  int mc;
+  const int* rel;
+  const double* U;
+  const double* uv;
+};
+__device__ __forceinline__ ChildRef child_ref(const SnDev& s, const FrontDesc& fd, int k) {
+  if (k < DESC_CH) return {fd.ch_mc[k], s.sn_rel + fd.ch_relptr[k], s.U + fd.ch_Uptr[k], s.uv + fd.ch_uvptr[k]};
+  const int C = s.sn_child[s.sn_child_ptr[fd.J] + k];
+  return {s.sn_nrow[C] - s.sn_ncol[C], s.sn_rel + s.sn_relptr[C], s.U + s.sn_Uptr[C], s.uv + s.sn_uvptr[C]};
+}
+
 // Column index kk of flat position t in the column-major lower triangle of
 // an nn x nn matrix (column kk holds nn - kk entries, starting at
 // kk*nn - kk*(kk-1)/2).  Single-precision square root plus an exact integer
@@ -109,15 +131,16 @@ __device__ void factor_front_smem(Ctl* ctl, double* F, int m, int c, double* wco
   }
 }
 
-__global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap) {
-  const int J = list[blockIdx.x];
-  const int inst = s.sn_inst[J];
-  Ctl* ctl = d.ctl + inst;
+__global__ void k_factor_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {
+  __shared__ FrontDesc fd;
+  load_desc(&fd, dl + blockIdx.x);
+  __syncthreads();
+  Ctl* ctl = d.ctl + fd.inst;
   if (!ctl->need_factor) return;
-  const int m = s.sn_nrow[J], c = s.sn_ncol[J], mu = m - c;
-  double* Lp = s.L + s.sn_Lptr[J];
-  double* Up = s.U + s.sn_Uptr[J];
-  const double* kd = s.Kdiag + s.sn_first[J];
+  const int m = fd.m, c = fd.c, mu = m - c;
+  double* Lp = s.L + fd.Lptr;
+  double* Up = s.U + fd.Uptr;
+  const double* kd = s.Kdiag + fd.first;
   const int tid = threadIdx.x, nt = blockDim.x;
   if ((long long)m * m + m <= smem_cap) {
     // ---- whole front in shared memory
@@ -126,11 +149,11 @@ __global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap) {
     for (int t = tid; t < m * c; t += nt) F[t] = Lp[t];
     for (int t = m * c + tid; t < m * m; t += nt) F[t] = 0.0;
     __syncthreads();
-    for (int q = s.sn_child_ptr[J]; q < s.sn_child_ptr[J + 1]; ++q) {
-      const int C = s.sn_child[q];
-      const int mc = s.sn_nrow[C] - s.sn_ncol[C];
-      const int* rel = s.sn_rel + s.sn_relptr[C];
-      const double* UC = s.U + s.sn_Uptr[C];
+    for (int q = 0; q < fd.nchild; ++q) {
+      const ChildRef ch = child_ref(s, fd, q);
+      const int mc = ch.mc;
+      const int* rel = ch.rel;
+      const double* UC = ch.U;
       const int tot = mc * (mc + 1) / 2;
       for (int t = tid; t < tot; t += nt) {
         const int b = tri_col(t, mc);
@@ -154,11 +177,11 @@ __global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap) {
   double* wcol = dsm;
   for (int t = tid; t < mu * mu; t += nt) G[t] = 0.0;
   __syncthreads();
-  for (int q = s.sn_child_ptr[J]; q < s.sn_child_ptr[J + 1]; ++q) {
-    const int C = s.sn_child[q];
-    const int mc = s.sn_nrow[C] - s.sn_ncol[C];
-    const int* rel = s.sn_rel + s.sn_relptr[C];
-    const double* UC = s.U + s.sn_Uptr[C];
+  for (int q = 0; q < fd.nchild; ++q) {
+    const ChildRef ch = child_ref(s, fd, q);
+    const int mc = ch.mc;
+    const int* rel = ch.rel;
+    const double* UC = ch.U;
     const int tot = mc * (mc + 1) / 2;
     for (int t = tid; t < tot; t += nt) {
       const int b = tri_col(t, mc);
@@ -423,19 +446,21 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
   __syncthreads();
 }
 
-__global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
+__global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int Q = (int)cluster.num_blocks();
   const int q = (int)cluster.block_rank();
-  const int J = list[blockIdx.x / Q];
-  Ctl* ctl = d.ctl + s.sn_inst[J];
+  __shared__ FrontDesc fd;
+  load_desc(&fd, dl + blockIdx.x / Q);
+  __syncthreads();
+  Ctl* ctl = d.ctl + fd.inst;
   if (!ctl->need_factor) return;  // uniform over the cluster: same instance
-  const int m = s.sn_nrow[J], c = s.sn_ncol[J], mu = m - c;
-  double* Lp = s.L + s.sn_Lptr[J];
-  double* Wp = s.W + s.sn_Lptr[J];
-  double* Up = s.U + s.sn_Uptr[J];
-  const double* kd = s.Kdiag + s.sn_first[J];
+  const int m = fd.m, c = fd.c, mu = m - c;
+  double* Lp = s.L + fd.Lptr;
+  double* Wp = s.W + fd.Lptr;
+  double* Up = s.U + fd.Uptr;
+  const double* kd = s.Kdiag + fd.first;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nblk = (m + PB - 1) / PB;
   const int my_blocks = (nblk - q + Q - 1) / Q;  // blocks q, q+Q, ...
@@ -470,34 +495,31 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const int* list) {
   }
   if (tid == 0) { s_pub = 0; s_timeout = 0; }
   __syncthreads();
-  // children's update matrices, four entries per thread in flight (the loads
-  // of the row map and the values do not depend on each other)
-  for (int qq = s.sn_child_ptr[J]; qq < s.sn_child_ptr[J + 1]; ++qq) {
-    const int C = s.sn_child[qq];
-    const int mc = s.sn_nrow[C] - s.sn_ncol[C];
-    const int* rel = s.sn_rel + s.sn_relptr[C];
-    const double* UC = s.U + s.sn_Uptr[C];
-    const int tot = mc * (mc + 1) / 2;
-    for (int t0 = tid; t0 < tot; t0 += 4 * nt) {
-      int ra[4], rb[4];
-      double v[4];
+  // children's update matrices through the precomputed extend-add map: this
+  // CTA's entries only, four per thread in flight
+  {
+    const long long* ap = s.amap_ptr + fd.abase + (long long)q * (fd.nchild + 1);
+    for (int k = 0; k < fd.nchild; ++k) {
+      const double* UC = child_ref(s, fd, k).U;
+      const long long b0 = ap[k], b1 = ap[k + 1];
+      for (long long e0 = b0 + tid; e0 < b1; e0 += 4 * nt) {
+        IdxPair pr[4];
+        double v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int t = t0 + u * nt;
-        ra[u] = -1;
-        if (t < tot) {
-          const int b = tri_col(t, mc);
-          const int a = b + (t - (b * mc - b * (b - 1) / 2));
-          rb[u] = rel[b];
-          ra[u] = rel[a];
-          v[u] = UC[a + (size_t)b * mc];
+        for (int u = 0; u < 4; ++u) {
+          const long long e = e0 + (long long)u * nt;
+          pr[u].dst = -1;
+          if (e < b1) {
+            pr[u] = s.amap[e];
+            v[u] = UC[pr[u].src];
+          }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (ra[u] >= 0 && (rb[u] / PB) % Q == q) Fl[ra[u] + (size_t)lcol(rb[u]) * m] += v[u];
+        for (int u = 0; u < 4; ++u)
+          if (pr[u].dst >= 0) Fl[pr[u].dst] += v[u];
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   cluster.sync();  // every CTA assembled and initialized its counter
   const int npan = (c + PB - 1) / PB;
@@ -632,13 +654,15 @@ __device__ __forceinline__ int group_width(int count, int nt) {
   return g;
 }
 
-__global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
+__global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {
   __shared__ unsigned long long bar;
   __shared__ int s_to;
-  const int J = list[blockIdx.x];
-  if (d.ctl[s.sn_inst[J]].status != ST_RUNNING) return;
-  const int m = s.sn_nrow[J], c = s.sn_ncol[J], first = s.sn_first[J];
-  const double* Lg = s.L + s.sn_Lptr[J];
+  __shared__ FrontDesc fd;
+  load_desc(&fd, dl + blockIdx.x);
+  __syncthreads();
+  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+  const int m = fd.m, c = fd.c, first = fd.first;
+  const double* Lg = s.L + fd.Lptr;
   const long long lsz = ((long long)m * c + 1) & ~1LL;
   const bool stage = lsz + m + c <= smem_cap;
   double* fv = dsm + (stage ? lsz : 0);  // m
@@ -655,12 +679,9 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* lis
   for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
   for (int j = tid; j < c; j += nt) ys[j] = __longlong_as_double(SENTINEL);
   __syncthreads();
-  for (int q = s.sn_child_ptr[J]; q < s.sn_child_ptr[J + 1]; ++q) {
-    const int C = s.sn_child[q];
-    const int mc = s.sn_nrow[C] - s.sn_ncol[C];
-    const int* rel = s.sn_rel + s.sn_relptr[C];
-    const double* uvC = s.uv + s.sn_uvptr[C];
-    for (int a = tid; a < mc; a += nt) fv[rel[a]] += uvC[a];
+  for (int q = 0; q < fd.nchild; ++q) {
+    const ChildRef ch = child_ref(s, fd, q);
+    for (int a = tid; a < ch.mc; a += nt) fv[ch.rel[a]] += ch.uv[a];
     __syncthreads();
   }
   if (stage && !mbar_wait(&bar, s.spin_limit)) s_to = 1;
@@ -695,7 +716,7 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* lis
   }
   __syncthreads();
   // update vector u_i = f_i - sum_j L_ij y_j (rows c..m-1), and z = D^{-1} y
-  double* uvJ = s.uv + s.sn_uvptr[J];
+  double* uvJ = s.uv + fd.uvptr;
   const int rows = m - c;
   if (rows > 0) {
     const int g = group_width(rows, nt);
@@ -713,14 +734,16 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const int* lis
   if (tid == 0 && s_to) atomicExch(s.timeout, 1);
 }
 
-__global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const int* list, int smem_cap) {
+__global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {
   __shared__ unsigned long long bar;
   __shared__ int s_to;
-  const int J = list[blockIdx.x];
-  if (d.ctl[s.sn_inst[J]].status != ST_RUNNING) return;
-  const int m = s.sn_nrow[J], c = s.sn_ncol[J], first = s.sn_first[J];
-  const double* Lg = s.L + s.sn_Lptr[J];
-  const int* rows_idx = s.sn_rows + s.sn_rowptr[J];
+  __shared__ FrontDesc fd;
+  load_desc(&fd, dl + blockIdx.x);
+  __syncthreads();
+  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+  const int m = fd.m, c = fd.c, first = fd.first;
+  const double* Lg = s.L + fd.Lptr;
+  const int* rows_idx = s.sn_rows + fd.rowptr;
   const long long lsz = ((long long)m * c + 1) & ~1LL;
   const bool stage = lsz + m + c <= smem_cap;
   double* xv = dsm + (stage ? lsz : 0);  // m

@@ -42,10 +42,10 @@ __global__ void k_cond_fac(Dev d, cudaGraphConditionalHandle h_fac, int* counter
 __global__ void k_cond_ls(Dev d, cudaGraphConditionalHandle h_ls, int* counters, int trial, int cap);
 
 // factor_kernels.cu
-__global__ void k_factor_level(Dev d, SnDev s, const int* list, int smem_cap);
-__global__ void k_factor_cluster(Dev d, SnDev s, const int* list);
-__global__ void k_fwd_level(Dev d, SnDev s, const int* list, int smem_cap);
-__global__ void k_bwd_level(Dev d, SnDev s, const int* list, int smem_cap);
+__global__ void k_factor_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
+__global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl);
+__global__ void k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
+__global__ void k_bwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
 
 // adjoint_kernels.cu
 __global__ void k_kmat_rows(Dev d, const double* Drow, const double* x, double* t, double* ta, int inst);

@@ -54,6 +54,9 @@ struct nmpc_handle {
   std::vector<int> lvl_ptr;
   std::vector<int> lvl_smem_factor, lvl_smem_solve, lvl_smem_bwd;  // bytes per level
   std::vector<int> lvl_cluster;                      // CTAs per front (0 = single-CTA kernel)
+  std::vector<long long> desc_abase;                 // per level position: first extend-add range (-1 none)
+  std::vector<int> amap;                             // extend-add pairs (source, destination)
+  std::vector<long long> amap_ptr;                   // ranges per (front, CTA, child)
   std::vector<int> lvl_cluster_smem;                 // bytes per CTA of the cluster kernel
   int n_sm = 152;
   int smem_cap_doubles = 0;
@@ -143,6 +146,9 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.sn_relptr = cv.take<long long>(ns + 1); s.sn_rel = cv.take<int>(A.sn_rel.size());
   s.level_ptr = cv.take<int>(A.level_ptr.size()); s.level_sn = cv.take<int>(ns);
   s.sn_uvptr = cv.take<long long>(ns + 1);
+  s.desc = cv.take<FrontDesc>(ns);
+  s.amap = cv.take<IdxPair>(h->amap.size() / 2);
+  s.amap_ptr = cv.take<long long>(h->amap_ptr.size());
   s.U = cv.take<double>(A.nU);
   s.W = cv.take<double>(A.nnzL);
   s.uv = cv.take<double>(A.nuv);
@@ -191,11 +197,11 @@ nmpc_status launch_factor(nmpc_handle* h) {
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_factor_cluster, h->d, h->s, (const int*)(h->s.level_sn + h->lvl_ptr[l])));
+      CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_factor_cluster, h->d, h->s, (const FrontDesc*)(h->s.desc + h->lvl_ptr[l])));
       ++h->launches;
       continue;
     }
-    k_factor_level<<<cnt, FACTOR_THREADS, h->lvl_smem_factor[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+    k_factor_level<<<cnt, FACTOR_THREADS, h->lvl_smem_factor[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
                                                                    h->smem_cap_doubles);
     ++h->launches;
   }
@@ -207,14 +213,14 @@ nmpc_status launch_solve(nmpc_handle* h) {
   for (int l = 0; l < nl; ++l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
-    k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+    k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
                                                                h->smem_cap_doubles);
     ++h->launches;
   }
   for (int l = nl - 1; l >= 0; --l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
-    k_bwd_level<<<cnt, 128, h->lvl_smem_bwd[l], h->stream>>>(h->d, h->s, h->s.level_sn + h->lvl_ptr[l],
+    k_bwd_level<<<cnt, 128, h->lvl_smem_bwd[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
                                                              h->smem_cap_doubles);
     ++h->launches;
   }
@@ -462,9 +468,6 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
     delete h;
     return NMPC_ERR_INVALID;
   }
-  Carver cv;
-  carve(h, cv);
-  h->ws_bytes = (cv.off + 255) & ~size_t(255);
   // per-level launch shapes
   const Analysis& A = h->A;
   h->lvl_ptr = A.level_ptr;
@@ -513,6 +516,42 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
       h->lvl_smem_solve[l] = std::max<int>(h->lvl_smem_solve[l], (int)(sneed * 8));
       h->lvl_smem_bwd[l] = std::max<int>(h->lvl_smem_bwd[l], (int)(sneed * 8));
     }
+  // extend-add maps of the cluster levels: for every front, cluster CTA q and
+  // child k, the (source in the child's update matrix, destination in the
+  // CTA's own columns) pairs of the entries that land in q's columns
+  h->desc_abase.assign(A.level_sn.size(), -1);
+  h->amap.clear();
+  h->amap_ptr.clear();
+  for (int l = 0; l < nl; ++l) {
+    const int Q = h->lvl_cluster[l];
+    if (Q <= 0) continue;
+    for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd) {
+      const int J = A.level_sn[qd];
+      const int m = A.sn_nrow[J];
+      h->desc_abase[qd] = (long long)h->amap_ptr.size();
+      for (int q = 0; q < Q; ++q) {
+        for (int k = A.sn_child_ptr[J]; k < A.sn_child_ptr[J + 1]; ++k) {
+          h->amap_ptr.push_back((long long)h->amap.size() / 2);
+          const int C = A.sn_child[k];
+          const int mc = A.sn_nrow[C] - A.sn_ncol[C];
+          const int* rel = A.sn_rel.data() + A.sn_relptr[C];
+          for (int b = 0; b < mc; ++b) {
+            const int rb = rel[b];
+            if ((rb / CLUSTER_PB) % Q != q) continue;
+            const int lc = ((rb / CLUSTER_PB) / Q) * CLUSTER_PB + rb % CLUSTER_PB;
+            for (int a = b; a < mc; ++a) {
+              h->amap.push_back(a + b * mc);
+              h->amap.push_back(rel[a] + lc * m);
+            }
+          }
+        }
+        h->amap_ptr.push_back((long long)h->amap.size() / 2);
+      }
+    }
+  }
+  Carver cv;
+  carve(h, cv);
+  h->ws_bytes = (cv.off + 255) & ~size_t(255);
   *out = h;
   return NMPC_OK;
 }
@@ -582,6 +621,28 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   CUDA_TRY(h, up(s.sn_child, A.sn_child, st)); CUDA_TRY(h, up(s.sn_relptr, A.sn_relptr, st));
   CUDA_TRY(h, up(s.sn_rel, A.sn_rel, st)); CUDA_TRY(h, up(s.level_ptr, A.level_ptr, st));
   CUDA_TRY(h, up(s.level_sn, A.level_sn, st)); CUDA_TRY(h, up(s.sn_uvptr, A.sn_uvptr, st));
+  {
+    std::vector<FrontDesc> desc(A.level_sn.size());
+    for (size_t q = 0; q < A.level_sn.size(); ++q) {
+      const int J = A.level_sn[q];
+      FrontDesc& f = desc[q];
+      std::memset(&f, 0, sizeof(f));
+      f.J = J; f.m = A.sn_nrow[J]; f.c = A.sn_ncol[J]; f.first = A.sn_first[J]; f.inst = A.sn_inst[J];
+      f.Lptr = A.sn_Lptr[J]; f.Uptr = A.sn_Uptr[J]; f.uvptr = A.sn_uvptr[J]; f.rowptr = A.sn_rowptr[J];
+      f.nchild = A.sn_child_ptr[J + 1] - A.sn_child_ptr[J];
+      f.abase = h->desc_abase[q];
+      for (int k = 0; k < std::min(f.nchild, DESC_CH); ++k) {
+        const int C = A.sn_child[A.sn_child_ptr[J] + k];
+        f.ch_mc[k] = A.sn_nrow[C] - A.sn_ncol[C];
+        f.ch_relptr[k] = A.sn_relptr[C]; f.ch_Uptr[k] = A.sn_Uptr[C]; f.ch_uvptr[k] = A.sn_uvptr[C];
+      }
+    }
+    CUDA_TRY(h, up(s.desc, desc, st));
+    if (!h->amap.empty())
+      CUDA_TRY(h, cudaMemcpyAsync(const_cast<IdxPair*>(s.amap), h->amap.data(), h->amap.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(h, up(s.amap_ptr, h->amap_ptr, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));  // the host vector goes out of scope
+  }
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
   const int maxf = *std::max_element(h->lvl_smem_solve.begin(), h->lvl_smem_solve.end());

@@ -136,6 +136,22 @@ struct Dev {
   double* trace;        // per instance: (max_iter + 2) x 8 doubles
 };
 
+// One record per supernode, stored in level order, with everything a factor
+// or solve block needs about its front and (up to DESC_CH of) its children:
+// a block reads it with one round of independent loads instead of a chain
+// of dependent index lookups.
+constexpr int DESC_CH = 4;
+struct alignas(8) IdxPair {
+  int src, dst;
+};
+struct FrontDesc {
+  long long Lptr, Uptr, uvptr, rowptr;
+  long long abase;                                      // extend-add ranges of the cluster kernel (-1: none)
+  int J, m, c, first, inst, nchild;
+  int ch_mc[DESC_CH];                                   // m - c of each child
+  long long ch_relptr[DESC_CH], ch_Uptr[DESC_CH], ch_uvptr[DESC_CH];
+};
+
 // Supernodal structure for the factor and solve kernels.
 struct SnDev {
   int ns;
@@ -150,6 +166,9 @@ struct SnDev {
   const long long* sn_relptr; const int* sn_rel; // update-row positions in the parent
   const int* sn_inst;
   const int* level_ptr; const int* level_sn;    // supernodes by level (height)
+  const FrontDesc* desc;      // descriptors in level_sn order
+  const IdxPair* amap;        // extend-add pairs (source in child U, destination in own columns)
+  const long long* amap_ptr;  // per (front, CTA, child) ranges, from FrontDesc::abase
   const long long* sn_uvptr;  // offset of the (m_s-c_s) update vector (solves)
   double* L;
   double* W;                  // unscaled factor panels W = L D (scratch of the cluster kernel)
