@@ -26,7 +26,7 @@
 
 namespace nmpc {
 
-extern __shared__ double dsm[];
+extern __shared__ __align__(16) double dsm[];  // 16-byte aligned: bulk-copy destination
 
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -633,6 +633,12 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// An mbarrier must be invalidated before its shared memory is used again
+// (by this block or by the next block on the SM): every thread has passed its
+// wait when this runs (the caller synchronizes first).
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // bounded wait for phase 0 of the barrier; false if the limit ran out
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, long long limit) {
   unsigned done = 0;
@@ -686,6 +692,7 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDes
   }
   if (stage && !mbar_wait(&bar, s.spin_limit)) s_to = 1;
   __syncthreads();
+  if (stage && tid == 0) mbar_inval(&bar);
   const int wp = tid >> 5, lane = tid & 31;
   if (stage && c <= ST) {
     // pipelined unit lower triangle
@@ -759,8 +766,10 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDes
   }
   for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : d.b[rows_idx[i]];
   for (int j = tid; j < c; j += nt) xs[j] = __longlong_as_double(SENTINEL);
+  __syncthreads();  // the barrier is initialized before any thread waits on it
   if (stage && !mbar_wait(&bar, s.spin_limit)) s_to = 1;
   __syncthreads();
+  if (stage && tid == 0) mbar_inval(&bar);
   // t_j = z_j - sum_{i >= c} L_ij x_i  (x_i of ancestors, already solved)
   const int below = m - c;
   if (below > 0) {
@@ -807,6 +816,288 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDes
   __syncthreads();
   for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
   if (tid == 0 && s_to) atomicExch(s.timeout, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Large fronts (blocked LDL^T over many SMs).
+//
+// Fronts too large for the shared memory of a cluster are factored in place:
+// the front F is the factor panel (columns < c, leading dimension m) plus the
+// update matrix (rows and columns >= c, leading dimension m - c).  All fronts
+// of a level are processed together, panel by panel (BNB columns):
+//   k_big_zero:   zero the update matrices;
+//   k_big_extend: add child k's update matrix (one launch per child index, so
+//                 the order of the additions is fixed);
+//   k_big_diag:   factor the BNB x BNB diagonal block in one warp per front;
+//   k_big_trsm:   solve the rows below it, one row per thread; both write L
+//                 (1/d_j on the diagonal) to the panel and W = L D to scratch;
+//   k_big_update: F_ik -= sum_j L_ij W_kj over the trailing lower triangle,
+//                 64 x 64 tiles, each thread a 4 x 4 block of FMAs with the
+//                 panel's L and W rows staged in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int BNB = 32;      // panel width
+constexpr int BT = 64;       // update tile
+constexpr int BROWS = 256;   // rows per panel block (one per thread)
+
+__device__ __forceinline__ double* front_at(double* Lp, double* Up, int m, int c, int i, int k) {
+  return (k < c) ? Lp + i + (size_t)k * m : Up + (i - c) + (size_t)(k - c) * (m - c);
+}
+
+__global__ void k_big_zero(Dev d, SnDev s, const FrontDesc* dl) {
+  const FrontDesc& fd = dl[blockIdx.y];
+  if (!d.ctl[fd.inst].need_factor) return;
+  const long long mu = fd.m - fd.c, tot = mu * mu;
+  double* Up = s.U + fd.Uptr;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x)
+    Up[t] = 0.0;
+}
+
+__global__ void k_big_extend(Dev d, SnDev s, const FrontDesc* dl, int k) {
+  const FrontDesc& fd = dl[blockIdx.y];
+  if (k >= fd.nchild || !d.ctl[fd.inst].need_factor) return;
+  const ChildRef ch = child_ref(s, fd, k);
+  const int m = fd.m, c = fd.c, mc = ch.mc;
+  double* Lp = s.L + fd.Lptr;
+  double* Up = s.U + fd.Uptr;
+  // column b of the child's update matrix per block row of threads; rows a >= b
+  for (long long b = blockIdx.x; b < mc; b += gridDim.x) {
+    const int rb = ch.rel[b];
+    for (int a = (int)b + threadIdx.x; a < mc; a += blockDim.x)
+      *front_at(Lp, Up, m, c, ch.rel[a], rb) += ch.U[a + b * (long long)mc];
+  }
+}
+
+// Diagonal block of panel p, one warp per front (lane r = row jb + r): L and
+// 1/d_j into the factor panel, W into the scratch copy.
+__global__ void __launch_bounds__(32) k_big_diag(Dev d, SnDev s, const FrontDesc* dl, int p) {
+  const FrontDesc& fd = dl[blockIdx.x];
+  const int m = fd.m, c = fd.c;
+  const int jb = p * BNB;
+  if (jb >= c) return;
+  Ctl* ctl = d.ctl + fd.inst;
+  if (!ctl->need_factor) return;
+  const int w = min(BNB, c - jb);
+  double* Lp = s.L + fd.Lptr;
+  double* Wp = s.W + fd.Lptr;
+  const double* kd = s.Kdiag + fd.first;
+  const int lane = threadIdx.x;
+  double f[BNB];
+#pragma unroll
+  for (int k = 0; k < BNB; ++k) f[k] = (lane < w && k <= lane) ? Lp[(jb + lane) + (size_t)(jb + k) * m] : 0.0;
+  double inv[BNB];
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < BNB; ++j) {
+    inv[j] = 0.0;
+    if (j < w) {
+      const double piv = __shfl_sync(FULL, f[j], j);
+      const double iv = recip_nr(piv);
+      inv[j] = iv;
+      if (lane == 0) bad = bad || !pivot_ok(piv, s.pivtol * fabs(kd[jb + j]));
+      const double lj = f[j] * iv;
+#pragma unroll
+      for (int k = j + 1; k < BNB; ++k) {
+        const double wk = __shfl_sync(FULL, f[j], k);
+        if (lane >= k && lane < w) f[k] = fma(-lj, wk, f[k]);
+      }
+    }
+  }
+  if (lane < w) {
+#pragma unroll
+    for (int k = 0; k < BNB; ++k)
+      if (k <= lane) {
+        const size_t g = (jb + lane) + (size_t)(jb + k) * m;
+        Lp[g] = (k == lane) ? inv[k] : f[k] * inv[k];
+        Wp[g] = f[k];
+      }
+  }
+  if (lane == 0 && bad) flag_fail(ctl);
+}
+
+// Rows below the diagonal block of panel p, one per thread: a w-step forward
+// substitution, l_ij = (F_ij - sum_{k<j} l_ik W_jk) / d_j.
+__global__ void __launch_bounds__(BROWS) k_big_trsm(Dev d, SnDev s, const FrontDesc* dl, int p) {
+  __shared__ double Db[BNB * BNB];  // W of the diagonal block, column-major
+  __shared__ double inv[BNB];
+  const FrontDesc& fd = dl[blockIdx.y];
+  const int m = fd.m, c = fd.c;
+  const int jb = p * BNB;
+  if (jb >= c) return;
+  if (!d.ctl[fd.inst].need_factor) return;
+  const int w = min(BNB, c - jb);
+  const int r0 = jb + w + blockIdx.x * BROWS;
+  if (r0 >= m) return;
+  double* Lp = s.L + fd.Lptr;
+  double* Wp = s.W + fd.Lptr;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < BNB * BNB; t += blockDim.x) {
+    const int i = t % BNB, k = t / BNB;
+    Db[t] = (i < w && k < i) ? Wp[(jb + i) + (size_t)(jb + k) * m] : 0.0;
+  }
+  if (tid < w) inv[tid] = Lp[(jb + tid) + (size_t)(jb + tid) * m];
+  __syncthreads();
+  const int i = r0 + tid;
+  if (i >= m) return;
+  double f[BNB];
+#pragma unroll
+  for (int k = 0; k < BNB; ++k) f[k] = (k < w) ? Lp[i + (size_t)(jb + k) * m] : 0.0;
+#pragma unroll
+  for (int j = 0; j < BNB; ++j) {
+    if (j < w) {
+      const double lj = f[j] * inv[j];
+      const size_t g = i + (size_t)(jb + j) * m;
+      Lp[g] = lj;
+      Wp[g] = f[j];
+#pragma unroll
+      for (int k = j + 1; k < BNB; ++k)
+        if (k < w) f[k] = fma(-lj, Db[k + j * BNB], f[k]);
+    }
+  }
+}
+
+// Trailing update after panel p: rows and columns >= jb + w.  Tile t of the
+// lower triangle of tiles (bi >= bk); 256 threads, each a 4 x 4 block.
+__global__ void __launch_bounds__(256) k_big_update(Dev d, SnDev s, const FrontDesc* dl, int p) {
+  __shared__ double Ls[BT][BNB + 1];
+  __shared__ double Ws[BT][BNB + 1];
+  const FrontDesc& fd = dl[blockIdx.y];
+  const int m = fd.m, c = fd.c;
+  const int jb = p * BNB;
+  if (jb >= c) return;
+  if (!d.ctl[fd.inst].need_factor) return;
+  const int w = min(BNB, c - jb);
+  const int t0 = jb + w;  // first trailing row/column
+  const int R = m - t0;
+  const int nb = (R + BT - 1) / BT;
+  const int tile = blockIdx.x;
+  if (tile >= nb * (nb + 1) / 2) return;
+  // tile -> (bi, bk), bi >= bk, column-major over the lower triangle of tiles
+  const int bk = tri_col(tile, nb);
+  const int bi = bk + (tile - (bk * nb - bk * (bk - 1) / 2));
+  const int i0 = t0 + bi * BT, k0 = t0 + bk * BT;
+  const double* Lp = s.L + fd.Lptr;
+  const double* Wp = s.W + fd.Lptr;
+  double* Lw = s.L + fd.Lptr;
+  double* Uw = s.U + fd.Uptr;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < BT * BNB; t += blockDim.x) {
+    const int r = t % BT, j = t / BT;
+    const int ii = i0 + r, kk = k0 + r;
+    Ls[r][j] = (j < w && ii < m) ? Lp[ii + (size_t)(jb + j) * m] : 0.0;
+    Ws[r][j] = (j < w && kk < m) ? Wp[kk + (size_t)(jb + j) * m] : 0.0;
+  }
+  __syncthreads();
+  const int tr = (tid % 16) * 4, tc = (tid / 16) * 4;  // this thread's 4 x 4 block
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+#pragma unroll 4
+  for (int j = 0; j < BNB; ++j) {
+    double la[4], wb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) la[a] = Ls[tr + a][j];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) wb[b] = Ws[tc + b][j];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(la[a], wb[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int kk = k0 + tc + b;
+    if (kk >= m) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int ii = i0 + tr + a;
+      if (ii >= m || ii < kk) continue;
+      double* f = front_at(Lw, Uw, m, c, ii, kk);
+      *f -= acc[a][b];
+    }
+  }
+}
+
+// Blocked solves of one large front in one block (1024 threads): the unit
+// triangle BNB columns at a time in warp 0, the rows below by all threads.
+__global__ void __launch_bounds__(1024) k_big_fwd(Dev d, SnDev s, const FrontDesc* dl) {
+  const FrontDesc& fd = dl[blockIdx.x];
+  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+  const int m = fd.m, c = fd.c, first = fd.first;
+  const double* Lg = s.L + fd.Lptr;
+  double* fv = dsm;  // m
+  __shared__ double yb[BNB];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
+  __syncthreads();
+  for (int q = 0; q < fd.nchild; ++q) {
+    const ChildRef ch = child_ref(s, fd, q);
+    for (int a = tid; a < ch.mc; a += nt) fv[ch.rel[a]] += ch.uv[a];
+    __syncthreads();
+  }
+  for (int jb = 0; jb < c; jb += BNB) {
+    const int w = min(BNB, c - jb);
+    if (tid < 32) {
+      double v = (tid < w) ? fv[jb + tid] : 0.0;
+      for (int j = 0; j < w; ++j) {
+        const double yj = __shfl_sync(FULL, v, j);
+        if (tid > j && tid < w) v = fma(-Lg[(jb + tid) + (size_t)(jb + j) * m], yj, v);
+      }
+      if (tid < w) { fv[jb + tid] = v; yb[tid] = v; }
+    }
+    __syncthreads();
+    for (int i = jb + w + tid; i < m; i += nt) {
+      double a = fv[i];
+      for (int j = 0; j < w; ++j) a = fma(-Lg[i + (size_t)(jb + j) * m], yb[j], a);
+      fv[i] = a;
+    }
+    __syncthreads();
+  }
+  double* uvJ = s.uv + fd.uvptr;
+  for (int i = c + tid; i < m; i += nt) uvJ[i - c] = fv[i];
+  for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j] * Lg[j + (size_t)j * m];
+}
+
+__global__ void __launch_bounds__(1024) k_big_bwd(Dev d, SnDev s, const FrontDesc* dl) {
+  const FrontDesc& fd = dl[blockIdx.x];
+  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+  const int m = fd.m, c = fd.c, first = fd.first;
+  const double* Lg = s.L + fd.Lptr;
+  const int* rows_idx = s.sn_rows + fd.rowptr;
+  double* xv = dsm;  // m
+  __shared__ double xb[BNB];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : d.b[rows_idx[i]];
+  __syncthreads();
+  // t_j = z_j - sum_{i >= c} L_ij x_i, one column per thread
+  for (int j = tid; j < c; j += nt) {
+    double a = xv[j];
+    for (int i = c; i < m; ++i) a = fma(-Lg[i + (size_t)j * m], xv[i], a);
+    xv[j] = a;
+  }
+  __syncthreads();
+  const int nbk = (c + BNB - 1) / BNB;
+  for (int bk = nbk - 1; bk >= 0; --bk) {
+    const int jb = bk * BNB, w = min(BNB, c - jb);
+    if (tid < 32) {
+      double v = (tid < w) ? xv[jb + tid] : 0.0;
+      for (int j = w - 1; j >= 0; --j) {
+        const double xj = __shfl_sync(FULL, v, j);
+        if (tid < j) v = fma(-Lg[(jb + j) + (size_t)(jb + tid) * m], xj, v);
+      }
+      if (tid < w) { xv[jb + tid] = v; xb[tid] = v; }
+    }
+    __syncthreads();
+    // columns before the block: x_i -= sum_{j in block} L(j, i) x_j
+    for (int i = tid; i < jb; i += nt) {
+      double a = xv[i];
+      for (int j = 0; j < w; ++j) a = fma(-Lg[(jb + j) + (size_t)i * m], xb[j], a);
+      xv[i] = a;
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
 }
 
 }  // namespace nmpc

@@ -46,6 +46,14 @@ __global__ void k_factor_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap
 __global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl);
 __global__ void k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
 __global__ void k_bwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
+__global__ void k_big_zero(Dev d, SnDev s, const FrontDesc* dl);
+__global__ void k_big_extend(Dev d, SnDev s, const FrontDesc* dl, int k);
+__global__ void k_big_diag(Dev d, SnDev s, const FrontDesc* dl, int p);
+__global__ void k_big_trsm(Dev d, SnDev s, const FrontDesc* dl, int p);
+__global__ void k_big_update(Dev d, SnDev s, const FrontDesc* dl, int p);
+__global__ void k_big_fwd(Dev d, SnDev s, const FrontDesc* dl);
+__global__ void k_big_bwd(Dev d, SnDev s, const FrontDesc* dl);
+constexpr int BIG_NB = 32, BIG_TILE = 64, BIG_ROWS = 256;  // BNB, BT, BROWS in factor_kernels.cu
 
 // adjoint_kernels.cu
 __global__ void k_kmat_rows(Dev d, const double* Drow, const double* x, double* t, double* ta, int inst);

@@ -55,6 +55,9 @@ struct nmpc_handle {
   std::vector<int> lvl_smem_factor, lvl_smem_solve, lvl_smem_bwd;  // bytes per level
   std::vector<int> lvl_cluster;                      // CTAs per front (0 = single-CTA kernel)
   std::vector<long long> desc_abase;                 // per level position: first extend-add range (-1 none)
+  // levels of large fronts (blocked path over many SMs): shapes per level
+  std::vector<char> lvl_big, lvl_bigsolve;
+  std::vector<int> lvl_maxm, lvl_maxc, lvl_maxmu, lvl_maxch, lvl_maxmc;
   std::vector<int> amap;                             // extend-add pairs (source, destination)
   std::vector<long long> amap_ptr;                   // ranges per (front, CTA, child)
   std::vector<int> lvl_cluster_smem;                 // bytes per CTA of the cluster kernel
@@ -201,6 +204,28 @@ nmpc_status launch_factor(nmpc_handle* h) {
       ++h->launches;
       continue;
     }
+    if (h->lvl_big[l]) {
+      const FrontDesc* dl = h->s.desc + h->lvl_ptr[l];
+      const long long mu2 = (long long)h->lvl_maxmu[l] * h->lvl_maxmu[l];
+      k_big_zero<<<dim3((unsigned)std::max(1LL, std::min(1024LL, (mu2 + 255) / 256)), cnt), 256, 0, h->stream>>>(h->d, h->s, dl);
+      ++h->launches;
+      for (int k = 0; k < h->lvl_maxch[l]; ++k) {
+        k_big_extend<<<dim3((unsigned)std::max(1, std::min(1024, h->lvl_maxmc[l])), cnt), 256, 0, h->stream>>>(h->d, h->s, dl, k);
+        ++h->launches;
+      }
+      const int npan = (h->lvl_maxc[l] + BIG_NB - 1) / BIG_NB;
+      for (int p = 0; p < npan; ++p) {
+        const int jb = p * BIG_NB;
+        k_big_diag<<<cnt, 32, 0, h->stream>>>(h->d, h->s, dl, p);
+        const int rows = std::max(0, h->lvl_maxm[l] - jb - 1);
+        k_big_trsm<<<dim3((unsigned)std::max(1, (rows + BIG_ROWS - 1) / BIG_ROWS), cnt), BIG_ROWS, 0, h->stream>>>(h->d, h->s, dl, p);
+        const int R = std::max(0, h->lvl_maxm[l] - jb - 1);
+        const long long nb = (R + BIG_TILE - 1) / BIG_TILE;
+        k_big_update<<<dim3((unsigned)std::max(1LL, nb * (nb + 1) / 2), cnt), 256, 0, h->stream>>>(h->d, h->s, dl, p);
+        h->launches += 3;
+      }
+      continue;
+    }
     k_factor_level<<<cnt, FACTOR_THREADS, h->lvl_smem_factor[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
                                                                    h->smem_cap_doubles);
     ++h->launches;
@@ -213,15 +238,21 @@ nmpc_status launch_solve(nmpc_handle* h) {
   for (int l = 0; l < nl; ++l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
-    k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
-                                                               h->smem_cap_doubles);
+    if (h->lvl_bigsolve[l])
+      k_big_fwd<<<cnt, 1024, h->lvl_maxm[l] * 8, h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l]);
+    else
+      k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
+                                                                 h->smem_cap_doubles);
     ++h->launches;
   }
   for (int l = nl - 1; l >= 0; --l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
-    k_bwd_level<<<cnt, 128, h->lvl_smem_bwd[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
-                                                             h->smem_cap_doubles);
+    if (h->lvl_bigsolve[l])
+      k_big_bwd<<<cnt, 1024, h->lvl_maxm[l] * 8, h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l]);
+    else
+      k_bwd_level<<<cnt, 128, h->lvl_smem_bwd[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
+                                                               h->smem_cap_doubles);
     ++h->launches;
   }
   return NMPC_OK;
@@ -504,6 +535,31 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
     }
     if (fits && h->opt.factor_mode == 0) { h->lvl_cluster[l] = Q; h->lvl_cluster_smem[l] = (int)worst; }
   }
+  h->lvl_big.assign(nl, 0); h->lvl_bigsolve.assign(nl, 0);
+  h->lvl_maxm.assign(nl, 0); h->lvl_maxc.assign(nl, 0); h->lvl_maxmu.assign(nl, 0);
+  h->lvl_maxch.assign(nl, 0); h->lvl_maxmc.assign(nl, 0);
+  for (int l = 0; l < nl; ++l) {
+    for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd) {
+      const int J = A.level_sn[qd];
+      const int mm = A.sn_nrow[J], cc = A.sn_ncol[J];
+      h->lvl_maxm[l] = std::max(h->lvl_maxm[l], mm);
+      h->lvl_maxc[l] = std::max(h->lvl_maxc[l], cc);
+      h->lvl_maxmu[l] = std::max(h->lvl_maxmu[l], mm - cc);
+      h->lvl_maxch[l] = std::max(h->lvl_maxch[l], A.sn_child_ptr[J + 1] - A.sn_child_ptr[J]);
+      for (int k = A.sn_child_ptr[J]; k < A.sn_child_ptr[J + 1]; ++k) {
+        const int C = A.sn_child[k];
+        h->lvl_maxmc[l] = std::max(h->lvl_maxmc[l], A.sn_nrow[C] - A.sn_ncol[C]);
+      }
+      const long long lsz = ((long long)mm * cc + 1) & ~1LL;
+      if (cc > 128 || lsz + mm + cc > h->smem_cap_doubles) h->lvl_bigsolve[l] = 1;
+    }
+    h->lvl_big[l] = ((h->lvl_cluster[l] == 0 && h->opt.factor_mode == 0) || h->opt.factor_mode == 2) ? 1 : 0;
+    if (h->lvl_bigsolve[l] && (long long)h->lvl_maxm[l] > h->smem_cap_doubles) {
+      std::fprintf(stderr, "nmpc_build: a front of %d rows exceeds the solve kernels' shared memory\n", h->lvl_maxm[l]);
+      delete h;
+      return NMPC_ERR_INVALID;
+    }
+  }
   h->lvl_smem_bwd.assign(nl, 8);
   for (int l = 0; l < nl; ++l)
     for (int q = A.level_ptr[l]; q < A.level_ptr[l + 1]; ++q) {
@@ -648,6 +704,15 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   const int maxf = *std::max_element(h->lvl_smem_solve.begin(), h->lvl_smem_solve.end());
   const int maxb = *std::max_element(h->lvl_smem_bwd.begin(), h->lvl_smem_bwd.end());
   if (maxf > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxf));
+  {
+    int maxbig = 0;
+    for (size_t l = 0; l < h->lvl_bigsolve.size(); ++l)
+      if (h->lvl_bigsolve[l]) maxbig = std::max(maxbig, h->lvl_maxm[l] * 8);
+    if (maxbig > 48 * 1024) {
+      CUDA_TRY(h, cudaFuncSetAttribute(k_big_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, maxbig));
+      CUDA_TRY(h, cudaFuncSetAttribute(k_big_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, maxbig));
+    }
+  }
   if (maxb > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_bwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb));
   CUDA_TRY(h, cudaStreamSynchronize(st));
   h->d.max_iter = h->opt.max_iter;
@@ -725,7 +790,13 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
   k_init_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, warm, push);
   ++h->launches;
   CUDA_TRY(h, cudaGetLastError());
-  if (h->opt.use_graph && !h->graph_off) {
+  // The large-front path runs in the host-driven loop: with it inside the
+  // conditional graph a plate solve (g = 32) ended in a device exception whose
+  // cause is not known, while the same kernels in the host-driven loop ran
+  // clean.
+  bool big = false;
+  for (size_t l = 0; l < h->lvl_big.size(); ++l) big = big || h->lvl_big[l] || h->lvl_bigsolve[l];
+  if (h->opt.use_graph && !h->graph_off && !big) {
     if (!h->gexec) {
       const nmpc_status gs = build_graph(h);
       if (gs != NMPC_OK) return gs;
