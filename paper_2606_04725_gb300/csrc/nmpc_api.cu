@@ -790,13 +790,7 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
   k_init_rows<<<blocks_for(m, EW), EW, 0, st>>>(d, warm, push);
   ++h->launches;
   CUDA_TRY(h, cudaGetLastError());
-  // The large-front path runs in the host-driven loop: with it inside the
-  // conditional graph a plate solve (g = 32) ended in a device exception whose
-  // cause is not known, while the same kernels in the host-driven loop ran
-  // clean.
-  bool big = false;
-  for (size_t l = 0; l < h->lvl_big.size(); ++l) big = big || h->lvl_big[l] || h->lvl_bigsolve[l];
-  if (h->opt.use_graph && !h->graph_off && !big) {
+  if (h->opt.use_graph && !h->graph_off) {
     if (!h->gexec) {
       const nmpc_status gs = build_graph(h);
       if (gs != NMPC_OK) return gs;
