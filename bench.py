@@ -151,6 +151,26 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def plate_factorization(P, dev, peak):
+    """Heated plate at full size (g = 64, S = 8, T = 50; n = 209,296): the
+    large-front path.  Two interior-point iterations give an iterate, then one
+    numeric factorization and one pair of solves are timed with CUDA events."""
+    import paper_2606_04725_gb300.inputs as I
+    g, S, T = 64, 8, 50
+    s = P.Solver(P.MODEL_PLATE, [T], g=g, S=S, device=dev, opts=P.options(max_iter=2))
+    s.set_params(x0=np.zeros(g * g), setpoint=I.plate_target(g, seed=3))
+    s.solve()
+    ph = s.time_phases(reps=2)
+    st = s.stats()
+    tf = st["factor_flops"] / (ph["ms_factor"] * 1e-3) / 1e12
+    out = {"workload": "plate_g64_S8_T50", "n": st["n_total"], "max_front": st["max_front"],
+           "factor_flops": st["factor_flops"], "factor_ms": ph["ms_factor"], "solve_ms": ph["ms_solve"],
+           "factor_tflops": tf, "factor_frac_of_peak": tf / peak,
+           "kernels": "k_big_diag, k_big_trsm, k_big_update (levels of large fronts); k_factor_cluster (small)"}
+    s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,6 +179,10 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rebuild-steps", type=int, default=3)
+    ap.add_argument("--no-plate", action="store_true", help="skip the full-size heated-plate factorization")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the interior-point loop from the host instead of the conditional graph "
+                         "(same kernels; for profilers that cannot see into conditional graphs)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -178,7 +202,8 @@ def main():
     seed = wl["seed"] + 1000 * rank
     x0 = I.distillation_x0(N, Nf, seed)
     a, b = I.distillation_setpoints(N, wl["seed"])
-    s = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev)
+    opts = P.options(use_graph=0) if args.host_loop else None
+    s = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev, opts=opts)
     n, m, _ = s.dims[0]
     ox1, ou1 = N, 2 * N  # offsets of x_1 and u_1 in y = [x_0 | x_1 u_1 | ...]
     stream = s.stream
@@ -288,9 +313,12 @@ def main():
             "phases_ms": {k: ph[k] for k in ("ms_eval", "ms_assemble", "ms_factor", "ms_solve")},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_factor_level (all levels of one numeric factorization)",
-                         "flops_per_launch_set": st["factor_flops"]},
+                         "kernel": "k_factor_cluster (the level launches of one numeric factorization)",
+                         "flops_per_launch_set": st["factor_flops"],
+                         "peak_basis": "152 SMs x 2 FP64 FMA/clock x max SM clock (nominal FP64 rate)"},
             "clocks": clk}
+    if not args.no_plate:
+        line["plate_full_size"] = plate_factorization(P, dev, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times, its = run_oracle_loop(wl, budget_s=20.0)
         line["cpu_baseline"] = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
