@@ -3,7 +3,8 @@
  * The library implements the per-iteration hot path of the parametric
  * interior-point method of arXiv 2606.04725 (Sec. 3.2, Algorithms 1 and 2):
  * stage-parallel derivative evaluation, assembly of the condensed Lifted-KKT
- * matrix (eq. liftedkkt-pd) into a fixed pattern, numeric supernodal Cholesky
+ * matrix (eq. liftedkkt-pd) into a fixed pattern, numeric supernodal factorization
+ * (the Cholesky of eq. cholesky-numeric in its square-root-free form K = L D L^T)
  * against a symbolic analysis done once (eqs. cholesky-symCholesky,
  * cholesky-numCholesky), triangular solves (eqs. cholesky-lower/upper/delta),
  * line search (eq. infiniteOCP-lineSearch) and barrier/termination control
@@ -92,10 +93,12 @@ typedef struct {
   int max_iter;          /* interior-point iteration limit (200) */
   int ordering;          /* nmpc_ordering */
   int nd_leaf;           /* nested dissection: stages per leaf (1) */
-  int use_graph;         /* capture one interior-point iteration in a CUDA graph (1) */
+  int use_graph;         /* run the interior-point loop as one CUDA graph with device-set
+                            conditional nodes (1, default); 0: host-driven loop, same kernels */
   long long spin_limit;  /* iteration limit of bounded device waits (1e7) */
   double pivtol;         /* inertia test: a pivot must exceed pivtol * |K_jj| (1e-12) */
-  int factor_mode;       /* 0: cluster-cooperative fronts where they fit (default); 1: one CTA per front */
+  int factor_mode;       /* 0: cluster-cooperative fronts where they fit, the blocked large-front
+                            path elsewhere (default); 1: one CTA per front; 2: blocked path everywhere */
 } nmpc_options;
 
 /* Per-instance result of a solve.  Times are measured with CUDA events on
@@ -130,7 +133,7 @@ typedef struct {
 typedef struct {
   double ms_eval;            /* stage-parallel residual/Jacobian/Hessian evaluation */
   double ms_assemble;        /* condensed-matrix assembly into the factor pattern */
-  double ms_factor;          /* numeric supernodal Cholesky */
+  double ms_factor;          /* numeric supernodal factorization (L D L^T) */
   double ms_solve;           /* right-hand side, forward and backward solves */
   int reps;
 } nmpc_phase_times;
@@ -184,7 +187,7 @@ nmpc_status nmpc_set_start(nmpc_handle* h, int instance, const double* y, const 
 
 /* Adjoint sensitivity at the converged point (not in the paper): for a loss
  * l(y*) with gradient dloss_dy (n of the instance), solve the transposed
- * condensed KKT system with the stored Cholesky factor (plus iterative
+ * condensed KKT system with the stored L D L^T factor (plus iterative
  * refinement) and return dl/dp_x0 (nx) and dl/dsetpoint (T values or g*g).
  * Either output may be NULL. */
 nmpc_status nmpc_sensitivity(nmpc_handle* h, int instance, const double* dloss_dy,
