@@ -171,6 +171,46 @@ def plate_factorization(P, dev, peak):
     return out
 
 
+def batch_resolves(P, dev, peak, n_inst=256, resolves=3):
+    """Batch of 256 distillation columns (N = 34, T_i ~ U{50..200}) in one
+    block-diagonal system: instance re-solves per second over warm re-solves
+    of the whole batch (each instance restarted from its measured state), and
+    the factorization rate."""
+    import torch
+    import paper_2606_04725_gb300.inputs as I
+    wl = I.WORKLOADS["batch256_distillation_N34_T50_200"]
+    hz = I.batch_horizons(n_inst, wl["T_lo"], wl["T_hi"], wl["seed"])
+    x0s, sps = I.batch_distillation(n_inst, 34, 17, wl["seed"])
+    s = P.Solver(P.MODEL_DISTILLATION, hz, N=34, Nf=17, device=dev)
+    for i, T in enumerate(hz):
+        s.set_params(instance=i, x0=x0s[i], setpoint=np.full(T, sps[i]), u_prev=np.array([I.U_REF]))
+    infos = s.solve()
+    ok = all(f["status"] == 0 for f in infos)
+    ms, iters = [], []
+    stream = s.stream
+    for _ in range(resolves):
+        for i, T in enumerate(hz):
+            y = s.get_solution(i)
+            s.set_params(instance=i, x0=y[34:68].copy(), setpoint=np.full(T, sps[i]), u_prev=y[68:69].copy())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = s.solve(warm=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        iters.append(max(f["iters"] for f in infos))
+        ok = ok and all(f["status"] == 0 for f in infos)
+    ph = s.time_phases(reps=2)
+    st = s.stats()
+    tf = st["factor_flops"] / (ph["ms_factor"] * 1e-3) / 1e12
+    out = {"workload": "batch256_distillation_N34_T50_200", "instances": n_inst, "n": st["n_total"],
+           "instance_resolves_per_s": n_inst * len(ms) / (sum(ms) * 1e-3), "ms_per_batch_resolve": sum(ms) / len(ms),
+           "max_ipm_iters_per_batch_resolve": max(iters), "statuses_ok": ok,
+           "factor_ms": ph["ms_factor"], "factor_tflops": tf, "factor_frac_of_peak": tf / peak}
+    s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +220,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rebuild-steps", type=int, default=3)
     ap.add_argument("--no-plate", action="store_true", help="skip the full-size heated-plate factorization")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the interior-point loop from the host instead of the conditional graph "
                          "(same kernels; for profilers that cannot see into conditional graphs)")
@@ -319,6 +360,8 @@ def main():
             "clocks": clk}
     if not args.no_plate:
         line["plate_full_size"] = plate_factorization(P, dev, peak)
+    if not args.no_batch:
+        line["batch_256"] = batch_resolves(P, dev, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times, its = run_oracle_loop(wl, budget_s=20.0)
         line["cpu_baseline"] = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
