@@ -99,6 +99,8 @@ typedef struct {
   double pivtol;         /* inertia test: a pivot must exceed pivtol * |K_jj| (1e-12) */
   int factor_mode;       /* 0: cluster-cooperative fronts where they fit, the blocked large-front
                             path elsewhere (default); 1: one CTA per front; 2: blocked path everywhere */
+  int solve_mode;        /* 0: persistent dataflow solves over the levels of small fronts (default);
+                            1: one launch per level */
 } nmpc_options;
 
 /* Per-instance result of a solve.  Times are measured with CUDA events on

@@ -660,13 +660,11 @@ __device__ __forceinline__ int group_width(int count, int nt) {
   return g;
 }
 
-__global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {
-  __shared__ unsigned long long bar;
-  __shared__ int s_to;
-  __shared__ FrontDesc fd;
-  load_desc(&fd, dl + blockIdx.x);
-  __syncthreads();
-  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+// Forward solve of one front (all threads of the block).  Values written by
+// other blocks of the same launch (children's update vectors) are read
+// through L2 (__ldcg).
+__device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int smem_cap, unsigned long long* bar,
+                          int* s_to) {
   const int m = fd.m, c = fd.c, first = fd.first;
   const double* Lg = s.L + fd.Lptr;
   const long long lsz = ((long long)m * c + 1) & ~1LL;
@@ -675,24 +673,24 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDes
   double* ys = fv + m;                   // c: published pivot values
   const double* Ls = stage ? dsm : Lg;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    s_to = 0;
-    if (stage) {
-      mbar_init(&bar);
-      bulk_load(dsm, Lg, (unsigned)(lsz * 8), &bar);
-    }
+  if (tid == 0 && stage) {
+    // earlier generic accesses to this shared memory (a previous front of
+    // this block) are ordered before the asynchronous copy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_init(bar);
+    bulk_load(dsm, Lg, (unsigned)(lsz * 8), bar);
   }
   for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
   for (int j = tid; j < c; j += nt) ys[j] = __longlong_as_double(SENTINEL);
   __syncthreads();
   for (int q = 0; q < fd.nchild; ++q) {
     const ChildRef ch = child_ref(s, fd, q);
-    for (int a = tid; a < ch.mc; a += nt) fv[ch.rel[a]] += ch.uv[a];
+    for (int a = tid; a < ch.mc; a += nt) fv[ch.rel[a]] += __ldcg(ch.uv + a);
     __syncthreads();
   }
-  if (stage && !mbar_wait(&bar, s.spin_limit)) s_to = 1;
+  if (stage && !mbar_wait(bar, s.spin_limit)) *s_to = 1;
   __syncthreads();
-  if (stage && tid == 0) mbar_inval(&bar);
+  if (stage && tid == 0) mbar_inval(bar);
   const int wp = tid >> 5, lane = tid & 31;
   if (stage && c <= ST) {
     // pipelined unit lower triangle
@@ -704,7 +702,7 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDes
         const double lv = (r > j && r < c) ? Ls[r + (size_t)j * m] : 0.0;
         double yj;
         if (j < 32 * wp) {
-          yj = take(ys + j, s.spin_limit, &s_to);
+          yj = take(ys + j, s.spin_limit, s_to);
         } else {
           yj = __shfl_sync(FULL, v, j & 31);
           if (lane == (j & 31)) *(volatile double*)(ys + j) = yj;
@@ -738,16 +736,12 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDes
     }
   }
   for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
-  if (tid == 0 && s_to) atomicExch(s.timeout, 1);
 }
 
-__global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {
-  __shared__ unsigned long long bar;
-  __shared__ int s_to;
-  __shared__ FrontDesc fd;
-  load_desc(&fd, dl + blockIdx.x);
-  __syncthreads();
-  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+// Backward solve of one front; ancestors' solution values (written by other
+// blocks of the same launch) are read through L2.
+__device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int smem_cap, unsigned long long* bar,
+                          int* s_to) {
   const int m = fd.m, c = fd.c, first = fd.first;
   const double* Lg = s.L + fd.Lptr;
   const int* rows_idx = s.sn_rows + fd.rowptr;
@@ -757,19 +751,19 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDes
   double* xs = xv + m;                   // c: published solution values
   const double* Ls = stage ? dsm : Lg;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    s_to = 0;
-    if (stage) {
-      mbar_init(&bar);
-      bulk_load(dsm, Lg, (unsigned)(lsz * 8), &bar);
-    }
+  if (tid == 0 && stage) {
+    // earlier generic accesses to this shared memory (a previous front of
+    // this block) are ordered before the asynchronous copy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_init(bar);
+    bulk_load(dsm, Lg, (unsigned)(lsz * 8), bar);
   }
-  for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : d.b[rows_idx[i]];
+  for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : __ldcg(d.b + rows_idx[i]);
   for (int j = tid; j < c; j += nt) xs[j] = __longlong_as_double(SENTINEL);
   __syncthreads();  // the barrier is initialized before any thread waits on it
-  if (stage && !mbar_wait(&bar, s.spin_limit)) s_to = 1;
+  if (stage && !mbar_wait(bar, s.spin_limit)) *s_to = 1;
   __syncthreads();
-  if (stage && tid == 0) mbar_inval(&bar);
+  if (stage && tid == 0) mbar_inval(bar);
   // t_j = z_j - sum_{i >= c} L_ij x_i  (x_i of ancestors, already solved)
   const int below = m - c;
   if (below > 0) {
@@ -796,7 +790,7 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDes
         const double lv = (i < j) ? Ls[j + (size_t)i * m] : 0.0;  // L(j, i)
         double xj;
         if (j > top) {
-          xj = take(xs + j, s.spin_limit, &s_to);
+          xj = take(xs + j, s.spin_limit, s_to);
         } else {
           xj = __shfl_sync(FULL, v, j & 31);
           if (lane == (j & 31)) *(volatile double*)(xs + j) = xj;
@@ -815,7 +809,105 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDes
   }
   __syncthreads();
   for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
+}
+
+__global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {
+  __shared__ unsigned long long bar;
+  __shared__ int s_to;
+  __shared__ FrontDesc fd;
+  load_desc(&fd, dl + blockIdx.x);
+  if (threadIdx.x == 0) s_to = 0;
+  __syncthreads();
+  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+  fwd_front(d, s, fd, smem_cap, &bar, &s_to);
+  if (threadIdx.x == 0 && s_to) atomicExch(s.timeout, 1);
+}
+
+__global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {
+  __shared__ unsigned long long bar;
+  __shared__ int s_to;
+  __shared__ FrontDesc fd;
+  load_desc(&fd, dl + blockIdx.x);
+  if (threadIdx.x == 0) s_to = 0;
+  __syncthreads();
+  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+  bwd_front(d, s, fd, smem_cap, &bar, &s_to);
+  if (threadIdx.x == 0 && s_to) atomicExch(s.timeout, 1);
+}
+
+// Persistent forms: one launch for the fronts desc[0 .. nf) in level order.
+// Each block claims the next front from a counter, waits for the fronts it
+// depends on (forward: its children; backward: its parent, which waited for
+// its own parent), solves it and publishes it with a release flag.  A front
+// is waited on only after a running block has claimed it, so the launch
+// needs no co-residency.  flags[0] is the claim counter and flags[1 + q]
+// front q's completion (both zeroed before the launch).
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void wait_done(const int* flag, long long limit, int* s_to) {
+  long long it = 0;
+  while (ld_acquire_gpu(flag) == 0) {
+    if (++it > limit) {
+      *s_to = 1;
+      break;
+    }
+  }
+}
+
+template <bool FWD>
+__device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* dl, int nf, int smem_cap, int* flags) {
+  __shared__ unsigned long long bar;
+  __shared__ int s_to;
+  __shared__ int s_q;
+  __shared__ FrontDesc fd;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_to = 0;
+  for (;;) {
+    if (tid == 0) s_q = atomicAdd(flags, 1);
+    __syncthreads();
+    const int k = s_q;
+    if (k >= nf) break;
+    const int q = FWD ? k : nf - 1 - k;  // backward: parents first
+    load_desc(&fd, dl + q);
+    __syncthreads();
+    if (tid == 0) {
+      if (FWD) {
+        for (int c = 0; c < fd.nchild; ++c) {
+          const int cp = (c < DESC_CH) ? fd.ch_pos[c] : s.pos_of_sn[s.sn_child[s.sn_child_ptr[fd.J] + c]];
+          if (cp >= 0 && cp < nf) wait_done(flags + 1 + cp, s.spin_limit, &s_to);
+        }
+      } else if (fd.par_pos >= 0 && fd.par_pos < nf) {
+        wait_done(flags + 1 + fd.par_pos, s.spin_limit, &s_to);
+      }
+    }
+    __syncthreads();
+    if (d.ctl[fd.inst].status == ST_RUNNING) {
+      if (FWD) fwd_front(d, s, fd, smem_cap, &bar, &s_to);
+      else bwd_front(d, s, fd, smem_cap, &bar, &s_to);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release_gpu(flags + 1 + q, 1);
+    }
+  }
   if (tid == 0 && s_to) atomicExch(s.timeout, 1);
+}
+
+__global__ void __launch_bounds__(ST) k_fwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
+                                                    int* flags) {
+  solve_persistent<true>(d, s, dl, nf, smem_cap, flags);
+}
+__global__ void __launch_bounds__(ST) k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
+                                                    int* flags) {
+  solve_persistent<false>(d, s, dl, nf, smem_cap, flags);
 }
 
 // ---------------------------------------------------------------------------

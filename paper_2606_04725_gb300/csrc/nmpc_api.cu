@@ -57,6 +57,10 @@ struct nmpc_handle {
   std::vector<long long> desc_abase;                 // per level position: first extend-add range (-1 none)
   // levels of large fronts (blocked path over many SMs): shapes per level
   std::vector<char> lvl_big, lvl_bigsolve;
+  // persistent solves over the first solve_prefix levels (fronts in level order)
+  int solve_prefix = 0, solve_prefix_fronts = 0, persist_blocks_fwd = 0, persist_blocks_bwd = 0;
+  int persist_smem_fwd = 0, persist_smem_bwd = 0;
+  int* d_solve_flags = nullptr;
   std::vector<int> lvl_maxm, lvl_maxc, lvl_maxmu, lvl_maxch, lvl_maxmc;
   std::vector<int> amap;                             // extend-add pairs (source, destination)
   std::vector<long long> amap_ptr;                   // ranges per (front, CTA, child)
@@ -150,6 +154,8 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.level_ptr = cv.take<int>(A.level_ptr.size()); s.level_sn = cv.take<int>(ns);
   s.sn_uvptr = cv.take<long long>(ns + 1);
   s.desc = cv.take<FrontDesc>(ns);
+  s.pos_of_sn = cv.take<int>(ns);
+  h->d_solve_flags = cv.take<int>(ns + 1);
   s.amap = cv.take<IdxPair>(h->amap.size() / 2);
   s.amap_ptr = cv.take<long long>(h->amap_ptr.size());
   s.U = cv.take<double>(A.nU);
@@ -235,7 +241,15 @@ nmpc_status launch_factor(nmpc_handle* h) {
 
 nmpc_status launch_solve(nmpc_handle* h) {
   const int nl = (int)h->lvl_ptr.size() - 1;
-  for (int l = 0; l < nl; ++l) {
+  const int L = h->opt.solve_mode == 1 ? 0 : h->solve_prefix;  // levels covered by one persistent launch
+  const size_t fbytes = (size_t)(h->solve_prefix_fronts + 1) * sizeof(int);
+  if (L > 0) {
+    CUDA_TRY(h, cudaMemsetAsync(h->d_solve_flags, 0, fbytes, h->stream));
+    k_fwd_persist<<<h->persist_blocks_fwd, 128, h->persist_smem_fwd, h->stream>>>(
+        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, h->d_solve_flags);
+    ++h->launches;
+  }
+  for (int l = L; l < nl; ++l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
     if (h->lvl_bigsolve[l])
@@ -245,7 +259,7 @@ nmpc_status launch_solve(nmpc_handle* h) {
                                                                  h->smem_cap_doubles);
     ++h->launches;
   }
-  for (int l = nl - 1; l >= 0; --l) {
+  for (int l = nl - 1; l >= L; --l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
     if (h->lvl_bigsolve[l])
@@ -255,9 +269,14 @@ nmpc_status launch_solve(nmpc_handle* h) {
                                                                h->smem_cap_doubles);
     ++h->launches;
   }
+  if (L > 0) {
+    CUDA_TRY(h, cudaMemsetAsync(h->d_solve_flags, 0, fbytes, h->stream));
+    k_bwd_persist<<<h->persist_blocks_bwd, 128, h->persist_smem_bwd, h->stream>>>(
+        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, h->d_solve_flags);
+    ++h->launches;
+  }
   return NMPC_OK;
 }
-
 
 // Kernel sequences of one interior-point iteration (Algorithm 2), shared by
 // the host-driven loop and the graph.  Each returns the number of launches.
@@ -679,6 +698,9 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   CUDA_TRY(h, up(s.level_sn, A.level_sn, st)); CUDA_TRY(h, up(s.sn_uvptr, A.sn_uvptr, st));
   {
     std::vector<FrontDesc> desc(A.level_sn.size());
+    std::vector<int> pos_of(A.level_sn.size());
+    for (size_t q = 0; q < A.level_sn.size(); ++q) pos_of[A.level_sn[q]] = (int)q;
+    CUDA_TRY(h, up(s.pos_of_sn, pos_of, st));
     for (size_t q = 0; q < A.level_sn.size(); ++q) {
       const int J = A.level_sn[q];
       FrontDesc& f = desc[q];
@@ -687,10 +709,13 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
       f.Lptr = A.sn_Lptr[J]; f.Uptr = A.sn_Uptr[J]; f.uvptr = A.sn_uvptr[J]; f.rowptr = A.sn_rowptr[J];
       f.nchild = A.sn_child_ptr[J + 1] - A.sn_child_ptr[J];
       f.abase = h->desc_abase[q];
+      f.pos = (int)q;
+      f.par_pos = A.sn_parent[J] >= 0 ? pos_of[A.sn_parent[J]] : -1;
       for (int k = 0; k < std::min(f.nchild, DESC_CH); ++k) {
         const int C = A.sn_child[A.sn_child_ptr[J] + k];
         f.ch_mc[k] = A.sn_nrow[C] - A.sn_ncol[C];
         f.ch_relptr[k] = A.sn_relptr[C]; f.ch_Uptr[k] = A.sn_Uptr[C]; f.ch_uvptr[k] = A.sn_uvptr[C];
+        f.ch_pos[k] = pos_of[C];
       }
     }
     CUDA_TRY(h, up(s.desc, desc, st));
@@ -701,6 +726,27 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   }
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
+  // persistent solves: the longest prefix of levels without large fronts
+  {
+    int L = 0, nf = 0, smf = 8, smb = 8;
+    while (L < (int)h->lvl_bigsolve.size() && !h->lvl_bigsolve[L]) {
+      nf += A.level_ptr[L + 1] - A.level_ptr[L];
+      smf = std::max(smf, h->lvl_smem_solve[L]);
+      smb = std::max(smb, h->lvl_smem_bwd[L]);
+      ++L;
+    }
+    h->solve_prefix = L;
+    h->solve_prefix_fronts = nf;
+    h->persist_smem_fwd = smf;
+    h->persist_smem_bwd = smb;
+    if (smf > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, smf));
+    if (smb > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_bwd_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+    int bf = 0, bb = 0;
+    CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_fwd_persist, 128, smf));
+    CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_bwd_persist, 128, smb));
+    h->persist_blocks_fwd = std::max(1, std::min(nf, std::max(1, bf) * h->n_sm));
+    h->persist_blocks_bwd = std::max(1, std::min(nf, std::max(1, bb) * h->n_sm));
+  }
   const int maxf = *std::max_element(h->lvl_smem_solve.begin(), h->lvl_smem_solve.end());
   const int maxb = *std::max_element(h->lvl_smem_bwd.begin(), h->lvl_smem_bwd.end());
   if (maxf > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxf));

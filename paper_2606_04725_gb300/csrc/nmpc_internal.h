@@ -148,6 +148,8 @@ struct FrontDesc {
   long long Lptr, Uptr, uvptr, rowptr;
   long long abase;                                      // extend-add ranges of the cluster kernel (-1: none)
   int J, m, c, first, inst, nchild;
+  int pos, par_pos;                                     // own and parent's level-order position (-1: root)
+  int ch_pos[DESC_CH];                                  // children's level-order positions
   int ch_mc[DESC_CH];                                   // m - c of each child
   long long ch_relptr[DESC_CH], ch_Uptr[DESC_CH], ch_uvptr[DESC_CH];
 };
@@ -167,6 +169,7 @@ struct SnDev {
   const int* sn_inst;
   const int* level_ptr; const int* level_sn;    // supernodes by level (height)
   const FrontDesc* desc;      // descriptors in level_sn order
+  const int* pos_of_sn;       // level-order position of each supernode
   const IdxPair* amap;        // extend-add pairs (source in child U, destination in own columns)
   const long long* amap_ptr;  // per (front, CTA, child) ranges, from FrontDesc::abase
   const long long* sn_uvptr;  // offset of the (m_s-c_s) update vector (solves)
