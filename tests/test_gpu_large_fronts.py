@@ -10,7 +10,9 @@ beyond a cluster's shared memory; those levels run the blocked path.  Pins:
     converged primal-dual point is checked by the oracle's KKT evaluator,
     which shares no code with the CUDA path: scaled E_0 <= 1e-8;
   * the full-size plate (g = 64, S = 8, T = 50: n = 209,296) likewise, plus
-    the bounds of the controls and the state upper bound hold at the point.
+    the bounds of the controls and the state upper bound hold at the point,
+    and the adjoint there satisfies the envelope theorem (dl/dx0 = -lambda
+    for l = f).
 """
 import numpy as np
 import pytest
@@ -82,9 +84,20 @@ def test_plate_g32_converges_to_oracle_kkt_point(P, oracle):
 
 
 def test_plate_full_size(P, oracle):
-    """g = 64, S = 8, T = 50 (n = 209,296): one cold solve at tol 1e-8."""
+    """g = 64, S = 8, T = 50 (n = 209,296): one cold solve at tol 1e-8, then
+    the adjoint at that point: for the loss l = f(y*) the envelope theorem
+    gives dl/dx0 = -lambda on the initial-condition rows."""
     g, S, T = 64, 8, 50
     s, info = _plate_solve(P, g, S, T)
     assert info["status"] == 0, info
     assert s.stats()["n_total"] == 209296
     _check_kkt_and_bounds(oracle, s, g, S, T)
+    prob = oracle.plate(g, S, T, np.zeros(g * g), I.plate_target(g, seed=3))
+    y, du = s.get_solution(0, duals=True)
+    _, grad_f, _, _ = oracle.evaluate(prob, y)
+    dx0 = np.zeros(g * g)
+    dsp = np.zeros(g * g)
+    s.sensitivity(0, grad_f, dx0, dsp)
+    lam0 = du["w_p"][:g * g] - du["w_m"][:g * g]
+    scale = max(1e-12, np.max(np.abs(lam0)))
+    assert np.max(np.abs(dx0 + lam0)) <= 1e-4 * scale, (np.max(np.abs(dx0 + lam0)), scale)
