@@ -66,6 +66,7 @@ struct nmpc_handle {
   std::vector<long long> amap_ptr;                   // ranges per (front, CTA, child)
   std::vector<int> lvl_cluster_smem;                 // bytes per CTA of the cluster kernel
   int n_sm = 152;
+  int cluster_ctas_per_sm = 1;  // CTAs of the cluster kernel per SM aimed at when choosing Q (2 measured no faster)
   int smem_cap_doubles = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<Ctl> h_ctl;
@@ -540,7 +541,8 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
     for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd)
       max_blocks = std::max(max_blocks, (A.sn_nrow[A.level_sn[qd]] + CLUSTER_PB - 1) / CLUSTER_PB);
     int Q = 1;
-    while (Q < 8 && 2 * Q * cnt <= h->n_sm && 2 * Q <= max_blocks) Q *= 2;
+    // clusters spread over the SMs (a second CTA per SM did not speed up the distillation levels)
+    while (Q < 8 && 2 * Q * cnt <= h->cluster_ctas_per_sm * h->n_sm && 2 * Q <= max_blocks) Q *= 2;
     long long worst = 0;
     bool fits = true;
     for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1] && fits; ++qd) {
