@@ -458,7 +458,7 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl) {
   if (!ctl->need_factor) return;  // uniform over the cluster: same instance
   const int m = fd.m, c = fd.c, mu = m - c;
   double* Lp = s.L + fd.Lptr;
-  double* Wp = s.W + fd.Lptr;
+  double* Wp = s.W + fd.Wptr;
   double* Up = s.U + fd.Uptr;
   const double* kd = s.Kdiag + fd.first;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -922,7 +922,8 @@ __global__ void __launch_bounds__(ST) k_bwd_persist(Dev d, SnDev s, const FrontD
 //                 the order of the additions is fixed);
 //   k_big_diag:   factor the BNB x BNB diagonal block in one warp per front;
 //   k_big_trsm:   solve the rows below it, one row per thread; both write L
-//                 (1/d_j on the diagonal) to the panel and W = L D to scratch;
+//                 (1/d_j on the diagonal) to the panel, and the pivots d_j go
+//                 to dpiv, from which W = L D is formed where it is needed;
 //   k_big_update: F_ik -= sum_j L_ij W_kj over the trailing lower triangle,
 //                 64 x 64 tiles, each thread a 4 x 4 block of FMAs with the
 //                 panel's L and W rows staged in shared memory.
@@ -970,7 +971,7 @@ __global__ void __launch_bounds__(32) k_big_diag(Dev d, SnDev s, const FrontDesc
   if (!ctl->need_factor) return;
   const int w = min(BNB, c - jb);
   double* Lp = s.L + fd.Lptr;
-  double* Wp = s.W + fd.Lptr;
+  double* dp = s.dpiv + fd.first;
   const double* kd = s.Kdiag + fd.first;
   const int lane = threadIdx.x;
   double f[BNB];
@@ -1000,9 +1001,9 @@ __global__ void __launch_bounds__(32) k_big_diag(Dev d, SnDev s, const FrontDesc
       if (k <= lane) {
         const size_t g = (jb + lane) + (size_t)(jb + k) * m;
         Lp[g] = (k == lane) ? inv[k] : f[k] * inv[k];
-        Wp[g] = f[k];
       }
   }
+  if (lane < w) dp[jb + lane] = f[lane];  // the pivot d_j (W = L D is formed from it where needed)
   if (lane == 0 && bad) flag_fail(ctl);
 }
 
@@ -1020,11 +1021,11 @@ __global__ void __launch_bounds__(BROWS) k_big_trsm(Dev d, SnDev s, const FrontD
   const int r0 = jb + w + blockIdx.x * BROWS;
   if (r0 >= m) return;
   double* Lp = s.L + fd.Lptr;
-  double* Wp = s.W + fd.Lptr;
+  const double* dp = s.dpiv + fd.first;
   const int tid = threadIdx.x;
   for (int t = tid; t < BNB * BNB; t += blockDim.x) {
     const int i = t % BNB, k = t / BNB;
-    Db[t] = (i < w && k < i) ? Wp[(jb + i) + (size_t)(jb + k) * m] : 0.0;
+    Db[t] = (i < w && k < i) ? Lp[(jb + i) + (size_t)(jb + k) * m] * dp[jb + k] : 0.0;  // W = L D
   }
   if (tid < w) inv[tid] = Lp[(jb + tid) + (size_t)(jb + tid) * m];
   __syncthreads();
@@ -1039,7 +1040,6 @@ __global__ void __launch_bounds__(BROWS) k_big_trsm(Dev d, SnDev s, const FrontD
       const double lj = f[j] * inv[j];
       const size_t g = i + (size_t)(jb + j) * m;
       Lp[g] = lj;
-      Wp[g] = f[j];
 #pragma unroll
       for (int k = j + 1; k < BNB; ++k)
         if (k < w) f[k] = fma(-lj, Db[k + j * BNB], f[k]);
@@ -1068,7 +1068,7 @@ __global__ void __launch_bounds__(256) k_big_update(Dev d, SnDev s, const FrontD
   const int bi = bk + (tile - (bk * nb - bk * (bk - 1) / 2));
   const int i0 = t0 + bi * BT, k0 = t0 + bk * BT;
   const double* Lp = s.L + fd.Lptr;
-  const double* Wp = s.W + fd.Lptr;
+  const double* dp = s.dpiv + fd.first;
   double* Lw = s.L + fd.Lptr;
   double* Uw = s.U + fd.Uptr;
   const int tid = threadIdx.x;
@@ -1076,7 +1076,7 @@ __global__ void __launch_bounds__(256) k_big_update(Dev d, SnDev s, const FrontD
     const int r = t % BT, j = t / BT;
     const int ii = i0 + r, kk = k0 + r;
     Ls[r][j] = (j < w && ii < m) ? Lp[ii + (size_t)(jb + j) * m] : 0.0;
-    Ws[r][j] = (j < w && kk < m) ? Wp[kk + (size_t)(jb + j) * m] : 0.0;
+    Ws[r][j] = (j < w && kk < m) ? Lp[kk + (size_t)(jb + j) * m] * dp[jb + j] : 0.0;  // W = L D
   }
   __syncthreads();
   const int tr = (tid % 16) * 4, tc = (tid / 16) * 4;  // this thread's 4 x 4 block
@@ -1113,12 +1113,14 @@ __global__ void __launch_bounds__(256) k_big_update(Dev d, SnDev s, const FrontD
 
 // Blocked solves of one large front in one block (1024 threads): the unit
 // triangle BNB columns at a time in warp 0, the rows below by all threads.
-__global__ void __launch_bounds__(1024) k_big_fwd(Dev d, SnDev s, const FrontDesc* dl) {
+// The front vector lives in shared memory when it fits (smem_doubles), else
+// in the front's slot of a global scratch vector (offset: its row list).
+__global__ void __launch_bounds__(1024) k_big_fwd(Dev d, SnDev s, const FrontDesc* dl, int smem_doubles) {
   const FrontDesc& fd = dl[blockIdx.x];
   if (d.ctl[fd.inst].status != ST_RUNNING) return;
   const int m = fd.m, c = fd.c, first = fd.first;
   const double* Lg = s.L + fd.Lptr;
-  double* fv = dsm;  // m
+  double* fv = (m <= smem_doubles) ? dsm : s.fvec + fd.rowptr;  // m
   __shared__ double yb[BNB];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
@@ -1151,13 +1153,13 @@ __global__ void __launch_bounds__(1024) k_big_fwd(Dev d, SnDev s, const FrontDes
   for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j] * Lg[j + (size_t)j * m];
 }
 
-__global__ void __launch_bounds__(1024) k_big_bwd(Dev d, SnDev s, const FrontDesc* dl) {
+__global__ void __launch_bounds__(1024) k_big_bwd(Dev d, SnDev s, const FrontDesc* dl, int smem_doubles) {
   const FrontDesc& fd = dl[blockIdx.x];
   if (d.ctl[fd.inst].status != ST_RUNNING) return;
   const int m = fd.m, c = fd.c, first = fd.first;
   const double* Lg = s.L + fd.Lptr;
   const int* rows_idx = s.sn_rows + fd.rowptr;
-  double* xv = dsm;  // m
+  double* xv = (m <= smem_doubles) ? dsm : s.fvec + fd.rowptr;  // m
   __shared__ double xb[BNB];
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : d.b[rows_idx[i]];

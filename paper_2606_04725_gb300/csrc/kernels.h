@@ -53,8 +53,8 @@ __global__ void k_big_extend(Dev d, SnDev s, const FrontDesc* dl, int k);
 __global__ void k_big_diag(Dev d, SnDev s, const FrontDesc* dl, int p);
 __global__ void k_big_trsm(Dev d, SnDev s, const FrontDesc* dl, int p);
 __global__ void k_big_update(Dev d, SnDev s, const FrontDesc* dl, int p);
-__global__ void k_big_fwd(Dev d, SnDev s, const FrontDesc* dl);
-__global__ void k_big_bwd(Dev d, SnDev s, const FrontDesc* dl);
+__global__ void k_big_fwd(Dev d, SnDev s, const FrontDesc* dl, int smem_doubles);
+__global__ void k_big_bwd(Dev d, SnDev s, const FrontDesc* dl, int smem_doubles);
 constexpr int BIG_NB = 32, BIG_TILE = 64, BIG_ROWS = 256;  // BNB, BT, BROWS in factor_kernels.cu
 
 // adjoint_kernels.cu

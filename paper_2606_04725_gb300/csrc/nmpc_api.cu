@@ -55,6 +55,8 @@ struct nmpc_handle {
   std::vector<int> lvl_smem_factor, lvl_smem_solve, lvl_smem_bwd;  // bytes per level
   std::vector<int> lvl_cluster;                      // CTAs per front (0 = single-CTA kernel)
   std::vector<long long> desc_abase;                 // per level position: first extend-add range (-1 none)
+  std::vector<long long> desc_wptr;                  // per level position: W scratch offset (cluster fronts)
+  long long nW_cluster = 0;
   // levels of large fronts (blocked path over many SMs): shapes per level
   std::vector<char> lvl_big, lvl_bigsolve;
   // persistent solves over the first solve_prefix levels (fronts in level order)
@@ -160,8 +162,10 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.amap = cv.take<IdxPair>(h->amap.size() / 2);
   s.amap_ptr = cv.take<long long>(h->amap_ptr.size());
   s.U = cv.take<double>(A.nU);
-  s.W = cv.take<double>(A.nnzL);
+  s.W = cv.take<double>(h->nW_cluster);
+  s.dpiv = cv.take<double>(n);
   s.uv = cv.take<double>(A.nuv);
+  s.fvec = cv.take<double>(A.sn_rows.size());
   s.L = d.Lval;
   s.Kdiag = d.Kdiag;
   s.pivtol = A.mc.pivtol;
@@ -240,6 +244,12 @@ nmpc_status launch_factor(nmpc_handle* h) {
   return NMPC_OK;
 }
 
+// doubles of shared memory a large-front solve block uses for its front
+// vector (0: every front of the level keeps it in global scratch)
+int big_solve_smem(const nmpc_handle* h, int l) {
+  return (long long)h->lvl_maxm[l] <= h->smem_cap_doubles ? h->lvl_maxm[l] : 0;
+}
+
 nmpc_status launch_solve(nmpc_handle* h) {
   const int nl = (int)h->lvl_ptr.size() - 1;
   const int L = h->opt.solve_mode == 1 ? 0 : h->solve_prefix;  // levels covered by one persistent launch
@@ -254,7 +264,8 @@ nmpc_status launch_solve(nmpc_handle* h) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
     if (h->lvl_bigsolve[l])
-      k_big_fwd<<<cnt, 1024, h->lvl_maxm[l] * 8, h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l]);
+      k_big_fwd<<<cnt, 1024, big_solve_smem(h, l) * 8, h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
+                                                                   big_solve_smem(h, l));
     else
       k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
                                                                  h->smem_cap_doubles);
@@ -264,7 +275,8 @@ nmpc_status launch_solve(nmpc_handle* h) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
     if (h->lvl_bigsolve[l])
-      k_big_bwd<<<cnt, 1024, h->lvl_maxm[l] * 8, h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l]);
+      k_big_bwd<<<cnt, 1024, big_solve_smem(h, l) * 8, h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
+                                                                   big_solve_smem(h, l));
     else
       k_bwd_level<<<cnt, 128, h->lvl_smem_bwd[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
                                                                h->smem_cap_doubles);
@@ -575,11 +587,6 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
       if (cc > 128 || lsz + mm + cc > h->smem_cap_doubles) h->lvl_bigsolve[l] = 1;
     }
     h->lvl_big[l] = ((h->lvl_cluster[l] == 0 && h->opt.factor_mode == 0) || h->opt.factor_mode == 2) ? 1 : 0;
-    if (h->lvl_bigsolve[l] && (long long)h->lvl_maxm[l] > h->smem_cap_doubles) {
-      std::fprintf(stderr, "nmpc_build: a front of %d rows exceeds the solve kernels' shared memory\n", h->lvl_maxm[l]);
-      delete h;
-      return NMPC_ERR_INVALID;
-    }
   }
   h->lvl_smem_bwd.assign(nl, 8);
   for (int l = 0; l < nl; ++l)
@@ -589,6 +596,7 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
       const long long need = mm * mm + mm;  // whole front plus one unscaled column
       h->lvl_smem_factor[l] = std::max<int>(h->lvl_smem_factor[l], (int)((need <= h->smem_cap_doubles ? need : mm) * 8));
       const long long lsz = (mm * cc + 1) & ~1LL;  // staged panel (k_fwd_level / k_bwd_level)
+      if (h->lvl_bigsolve[l]) continue;           // the large-front solves size their own
       const long long sneed = (lsz + mm + cc <= h->smem_cap_doubles) ? lsz + mm + cc : mm + cc;
       h->lvl_smem_solve[l] = std::max<int>(h->lvl_smem_solve[l], (int)(sneed * 8));
       h->lvl_smem_bwd[l] = std::max<int>(h->lvl_smem_bwd[l], (int)(sneed * 8));
@@ -597,6 +605,16 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   // child k, the (source in the child's update matrix, destination in the
   // CTA's own columns) pairs of the entries that land in q's columns
   h->desc_abase.assign(A.level_sn.size(), -1);
+  h->desc_wptr.assign(A.level_sn.size(), 0);
+  h->nW_cluster = 0;
+  for (int l = 0; l < nl; ++l) {
+    if (h->lvl_cluster[l] <= 0) continue;
+    for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd) {
+      const int J = A.level_sn[qd];
+      h->desc_wptr[qd] = h->nW_cluster;
+      h->nW_cluster += (A.sn_Lptr[J + 1] - A.sn_Lptr[J]);  // same padded size as the panel
+    }
+  }
   h->amap.clear();
   h->amap_ptr.clear();
   for (int l = 0; l < nl; ++l) {
@@ -711,6 +729,7 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
       f.Lptr = A.sn_Lptr[J]; f.Uptr = A.sn_Uptr[J]; f.uvptr = A.sn_uvptr[J]; f.rowptr = A.sn_rowptr[J];
       f.nchild = A.sn_child_ptr[J + 1] - A.sn_child_ptr[J];
       f.abase = h->desc_abase[q];
+      f.Wptr = h->desc_wptr[q];
       f.pos = (int)q;
       f.par_pos = A.sn_parent[J] >= 0 ? pos_of[A.sn_parent[J]] : -1;
       for (int k = 0; k < std::min(f.nchild, DESC_CH); ++k) {
@@ -755,7 +774,7 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   {
     int maxbig = 0;
     for (size_t l = 0; l < h->lvl_bigsolve.size(); ++l)
-      if (h->lvl_bigsolve[l]) maxbig = std::max(maxbig, h->lvl_maxm[l] * 8);
+      if (h->lvl_bigsolve[l]) maxbig = std::max(maxbig, big_solve_smem(h, (int)l) * 8);
     if (maxbig > 48 * 1024) {
       CUDA_TRY(h, cudaFuncSetAttribute(k_big_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, maxbig));
       CUDA_TRY(h, cudaFuncSetAttribute(k_big_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, maxbig));

@@ -147,6 +147,7 @@ struct alignas(8) IdxPair {
 struct FrontDesc {
   long long Lptr, Uptr, uvptr, rowptr;
   long long abase;                                      // extend-add ranges of the cluster kernel (-1: none)
+  long long Wptr;                                       // unscaled-panel scratch of the cluster kernel
   int J, m, c, first, inst, nchild;
   int pos, par_pos;                                     // own and parent's level-order position (-1: root)
   int ch_pos[DESC_CH];                                  // children's level-order positions
@@ -174,9 +175,11 @@ struct SnDev {
   const long long* amap_ptr;  // per (front, CTA, child) ranges, from FrontDesc::abase
   const long long* sn_uvptr;  // offset of the (m_s-c_s) update vector (solves)
   double* L;
-  double* W;                  // unscaled factor panels W = L D (scratch of the cluster kernel)
+  double* W;                  // unscaled factor panels W = L D of the cluster-factored fronts
+  double* dpiv;               // pivots d_j of the large-front path, factor order
   double* U;
   double* uv;                 // update vectors of the forward solve
+  double* fvec;               // front vectors of large-front solves (offset: the front's row list)
   const double* Kdiag;        // assembled diagonal in factor order
   double pivtol;
   long long spin_limit;       // polls of a bounded wait between CTAs
