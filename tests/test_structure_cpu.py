@@ -105,3 +105,34 @@ def test_invalid_problems_are_rejected(P):
         P.Structure(model=1, horizons=[3], g=10, S=12)     # g % (S/4) != 0
     with pytest.raises(P.NmpcError):
         P.Structure(model=0, horizons=[0], N=12, Nf=5)
+
+
+@pytest.mark.parametrize("name,prob,opt", CASES, ids=[c[0] for c in CASES])
+def test_levels_order_every_child_before_its_parent(P, name, prob, opt):
+    """The level sets (supernodes by height) put every supernode at a strictly
+    lower level than its parent.  The factorization runs level by level and the
+    persistent solves claim fronts in level order, waiting only on children
+    (forward) or the parent (backward); both rely on this order."""
+    kw = {k: v for k, v in prob.items() if k not in ("model", "horizons")}
+    s = P.Structure(prob["model"], prob["horizons"], opts=P.options(**opt), **kw)
+    lp, ls, par = s.export(6), s.export(7), s.export(5)
+    ns = len(par)
+    assert sorted(ls.tolist()) == list(range(ns))
+    level = np.empty(ns, dtype=int)
+    for l in range(len(lp) - 1):
+        level[ls[lp[l]:lp[l + 1]]] = l
+    for j in range(ns):
+        if par[j] >= 0:
+            assert level[j] < level[par[j]], (j, par[j])
+    # a front's rows are its columns followed by rows of its ancestors: the
+    # update rows of a child are rows of its parent
+    first, ncol, nrow = s.export(1), s.export(2), s.export(3)
+    rows_ptr = np.concatenate([[0], np.cumsum(nrow)])
+    rows = s.export(4)
+    for j in range(ns):
+        rj = rows[rows_ptr[j]:rows_ptr[j + 1]]
+        assert np.array_equal(rj[:ncol[j]], np.arange(first[j], first[j] + ncol[j]))
+        assert np.all(np.diff(rj) > 0)
+        if par[j] >= 0:
+            rp = set(rows[rows_ptr[par[j]]:rows_ptr[par[j] + 1]].tolist())
+            assert set(rj[ncol[j]:].tolist()) <= rp, j
