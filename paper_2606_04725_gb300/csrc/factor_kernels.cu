@@ -608,14 +608,23 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl) {
 //
 // The panel (m x c, contiguous, 16-byte aligned) is staged in shared memory
 // by one bulk asynchronous copy (cp.async.bulk, completion on an mbarrier)
-// while the right-hand side is gathered.  The c x c unit triangle is a
-// pipeline over the four warps: warp s holds rows 32s .. 32s+31 of the vector
-// in registers and applies columns in order, one FMA instruction per column;
-// the warp that owns column j takes y_j from its own lane by a shuffle and
-// stores it into its sentinel slot, from which the other warps take it.  The
-// critical path is one shuffle, one FMA and a shared-memory store per column.
-// The rectangular parts are dot products split over groups of threads with
-// shuffle reductions.
+// while the right-hand side is gathered.
+//
+// Blocked by IB columns.  A column-by-column substitution puts one FP64 FMA
+// and one hand-off between lanes (shuffle or shared memory) on the critical
+// path of every column, about 285 cycles each on this GPU, so a 70-column
+// triangle costs about 20k cycles.  Instead the panel is transformed once per
+// factorization (k_diag_inv, k_panel_scale; in place): block K of columns
+// s0 .. e-1 holds X_K = T_K^{-1} on its diagonal block (T_K = unit lower
+// diagonal block of L) and M_K = L_{e..m-1,K} X_K below.  Then every block of
+// a solve is ONE dense product (one reduction, one barrier):
+//   forward   with v the right-hand side as updated by the blocks before K,
+//             y_K = X_K v_K  and  v_r -= M_rK v_K  for r >= e, since
+//             L_rK y_K = L_rK X_K v_K; the update rows r >= c come out as
+//             u = v_{c..m-1};
+//   backward  (last block first) x_K = X_K^T z_K - M_K^T x_{e..m-1}, the
+//             rows below e being the blocks already solved and the
+//             ancestors' x, since L_{e..,K}^T x = X_K^{-T} M_K^T x.
 // ---------------------------------------------------------------------------
 constexpr int ST = 128;  // threads of a solve block
 
@@ -653,11 +662,37 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, long long lim
   return done != 0;
 }
 
-// threads per dot product so that `count` products fill the block
-__device__ __forceinline__ int group_width(int count, int nt) {
+// One thread's share of a dot product: sum over k = k0, k0 + g, ... < len of
+// a(k) x(k).  Four terms per round, their loads issued together, two
+// accumulators: the FP64 pipe, not load latency, sets the pace.
+template <class A, class X>
+__device__ __forceinline__ double dot_part(int k0, int len, int g, A a, X x) {
+  double s0 = 0.0, s1 = 0.0;
+  int k = k0;
+  for (; k + 3 * g < len; k += 4 * g) {
+    const double a0 = a(k), a1 = a(k + g), a2 = a(k + 2 * g), a3 = a(k + 3 * g);
+    const double x0 = x(k), x1 = x(k + g), x2 = x(k + 2 * g), x3 = x(k + 3 * g);
+    s0 = fma(a0, x0, s0);
+    s1 = fma(a1, x1, s1);
+    s0 = fma(a2, x2, s0);
+    s1 = fma(a3, x3, s1);
+  }
+  for (; k < len; k += g) s0 = fma(a(k), x(k), s0);
+  return s0 + s1;
+}
+
+// Threads per output for count outputs: the largest power of two g with
+// g * count <= the block's threads, at most 32 and at most len rounded up.
+__device__ __forceinline__ int dot_group(int count, int len, int nt) {
   int g = 1;
-  while (g < 32 && g * 2 * count <= nt) g *= 2;
+  while (g < 32 && g < len && 2 * g * count <= nt) g *= 2;
   return g;
+}
+
+// sum over g consecutive lanes (g a power of two; every lane of the warp calls)
+__device__ __forceinline__ double group_sum(double v, int g) {
+  for (int off = g >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+  return v;
 }
 
 // Forward solve of one front (all threads of the block).  Values written by
@@ -669,8 +704,8 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   const double* Lg = s.L + fd.Lptr;
   const long long lsz = ((long long)m * c + 1) & ~1LL;
   const bool stage = lsz + m + c <= smem_cap;
-  double* fv = dsm + (stage ? lsz : 0);  // m
-  double* ys = fv + m;                   // c: published pivot values
+  double* fv = dsm + (stage ? lsz : 0);  // m: right-hand side, updated block by block
+  double* ys = fv + m;                   // c: y
   const double* Ls = stage ? dsm : Lg;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0 && stage) {
@@ -680,10 +715,32 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
     mbar_init(bar);
     bulk_load(dsm, Lg, (unsigned)(lsz * 8), bar);
   }
+  // The first ST entries of each of the first DESC_CH children's update
+  // vectors are loaded together with the right-hand side (one round of L2
+  // latency); the additions then go child by child, in ascending order.
+  double cv[DESC_CH];
+  int cr[DESC_CH];
+#pragma unroll
+  for (int q = 0; q < DESC_CH; ++q) {
+    cr[q] = -1;
+    cv[q] = 0.0;
+    if (q < fd.nchild && tid < fd.ch_mc[q]) {
+      cr[q] = s.sn_rel[fd.ch_relptr[q] + tid];
+      cv[q] = __ldcg(s.uv + fd.ch_uvptr[q] + tid);
+    }
+  }
   for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
-  for (int j = tid; j < c; j += nt) ys[j] = __longlong_as_double(SENTINEL);
   __syncthreads();
-  for (int q = 0; q < fd.nchild; ++q) {
+#pragma unroll
+  for (int q = 0; q < DESC_CH; ++q) {
+    if (q < fd.nchild) {  // uniform over the block
+      if (cr[q] >= 0) fv[cr[q]] += cv[q];
+      const ChildRef ch = child_ref(s, fd, q);
+      for (int a = nt + tid; a < ch.mc; a += nt) fv[ch.rel[a]] += __ldcg(ch.uv + a);
+      __syncthreads();
+    }
+  }
+  for (int q = DESC_CH; q < fd.nchild; ++q) {
     const ChildRef ch = child_ref(s, fd, q);
     for (int a = tid; a < ch.mc; a += nt) fv[ch.rel[a]] += __ldcg(ch.uv + a);
     __syncthreads();
@@ -691,51 +748,35 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   if (stage && !mbar_wait(bar, s.spin_limit)) *s_to = 1;
   __syncthreads();
   if (stage && tid == 0) mbar_inval(bar);
-  const int wp = tid >> 5, lane = tid & 31;
-  if (stage && c <= ST) {
-    // pipelined unit lower triangle
-    if (32 * wp < c) {
-      const int r = 32 * wp + lane;
-      double v = (r < c) ? fv[r] : 0.0;
-      const int jmax = min(c, 32 * wp + 32);
-      for (int j = 0; j < jmax; ++j) {
-        const double lv = (r > j && r < c) ? Ls[r + (size_t)j * m] : 0.0;
-        double yj;
-        if (j < 32 * wp) {
-          yj = take(ys + j, s.spin_limit, s_to);
-        } else {
-          yj = __shfl_sync(FULL, v, j & 31);
-          if (lane == (j & 31)) *(volatile double*)(ys + j) = yj;
-        }
-        v = fma(-lv, yj, v);
+  for (int s0 = 0; s0 < c; s0 += IB) {
+    const int bk = min(IB, c - s0), cnt = m - s0;
+    const double* P = Ls + s0 + (size_t)s0 * m;  // rows s0.. of the block's columns: X_K, then M_K
+    const double* v = fv + s0;
+    // output r < bk: y_{s0+r} = sum_j X_rj v_j (X_rr = 1, X_rj = 0 for j > r);
+    // r >= bk: v_{s0+r} -= sum_j M_rj v_j.  Every P(r, j) read is inside the panel.
+    const int g = dot_group(cnt, bk, nt);
+    for (int o0 = 0; o0 < cnt; o0 += nt / g) {
+      const int r = o0 + tid / g, part = tid & (g - 1);
+      const int rr = min(r, cnt - 1);
+      const double* Pr = P + rr;
+      double acc = dot_part(
+          part, bk, g,
+          [&](int j) {
+            const double p = Pr[(size_t)j * m];
+            return j < rr ? p : (j == rr ? 1.0 : 0.0);
+          },
+          [&](int j) { return v[j]; });
+      acc = group_sum(acc, g);
+      if (part == 0 && r < cnt) {
+        if (r < bk) ys[s0 + r] = acc;
+        else fv[s0 + r] -= acc;
       }
-      if (r < c) fv[r] = v;
     }
-  } else if (tid < 32) {
-    for (int j = 0; j < c; ++j) {
-      const double yj = fv[j];
-      __syncwarp();
-      for (int i = j + 1 + lane; i < c; i += 32) fv[i] = fma(-Ls[i + (size_t)j * m], yj, fv[i]);
-      __syncwarp();
-    }
+    __syncthreads();
   }
-  __syncthreads();
-  // update vector u_i = f_i - sum_j L_ij y_j (rows c..m-1), and z = D^{-1} y
-  double* uvJ = s.uv + fd.uvptr;
-  const int rows = m - c;
-  if (rows > 0) {
-    const int g = group_width(rows, nt);
-    for (int base = 0; base < rows * g; base += nt) {
-      const int t = base + tid;
-      const int r = t / g, part = t % g;
-      double a = 0.0;
-      if (r < rows)
-        for (int j = part; j < c; j += g) a = fma(-Ls[(c + r) + (size_t)j * m], fv[j], a);
-      for (int off = g >> 1; off > 0; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-      if (r < rows && part == 0) uvJ[r] = fv[c + r] + a;
-    }
-  }
-  for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
+  double* uvJ = s.uv + fd.uvptr;  // u_i = f_i - sum_j L_ij y_j (rows c..m-1)
+  for (int r = c + tid; r < m; r += nt) uvJ[r - c] = fv[r];
+  for (int j = tid; j < c; j += nt) d.b[first + j] = ys[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
 }
 
 // Backward solve of one front; ancestors' solution values (written by other
@@ -747,8 +788,8 @@ __device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   const int* rows_idx = s.sn_rows + fd.rowptr;
   const long long lsz = ((long long)m * c + 1) & ~1LL;
   const bool stage = lsz + m + c <= smem_cap;
-  double* xv = dsm + (stage ? lsz : 0);  // m
-  double* xs = xv + m;                   // c: published solution values
+  double* xv = dsm + (stage ? lsz : 0);  // m: x (pivot rows solved block by block, ancestors' x below)
+  double* zs = xv + m;                   // c: z
   const double* Ls = stage ? dsm : Lg;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0 && stage) {
@@ -758,57 +799,112 @@ __device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
     mbar_init(bar);
     bulk_load(dsm, Lg, (unsigned)(lsz * 8), bar);
   }
-  for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : __ldcg(d.b + rows_idx[i]);
-  for (int j = tid; j < c; j += nt) xs[j] = __longlong_as_double(SENTINEL);
+  for (int i = tid; i < m; i += nt) {
+    if (i < c) zs[i] = d.b[first + i];
+    else xv[i] = __ldcg(d.b + rows_idx[i]);
+  }
   __syncthreads();  // the barrier is initialized before any thread waits on it
   if (stage && !mbar_wait(bar, s.spin_limit)) *s_to = 1;
   __syncthreads();
   if (stage && tid == 0) mbar_inval(bar);
-  // t_j = z_j - sum_{i >= c} L_ij x_i  (x_i of ancestors, already solved)
-  const int below = m - c;
-  if (below > 0) {
-    const int g = group_width(c, nt);
-    for (int base = 0; base < c * g; base += nt) {
-      const int t = base + tid;
-      const int j = t / g, part = t % g;
-      double a = 0.0;
-      if (j < c)
-        for (int i = c + part; i < m; i += g) a = fma(-Ls[i + (size_t)j * m], xv[i], a);
-      for (int off = g >> 1; off > 0; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-      if (j < c && part == 0) xv[j] += a;
-    }
+  for (int s0 = (c - 1) / IB * IB; s0 >= 0; s0 -= IB) {
+    const int bk = min(IB, c - s0), len = m - s0;
+    const double* P = Ls + s0 + (size_t)s0 * m;
+    // x_{s0+j} = sum_{j <= i < bk} X_ij z_{s0+i} - sum_{bk <= i < len} M_ij x_{s0+i}
+    // (column j of P, contiguous); one group of g threads per output j
+    const int g = dot_group(bk, len, nt);
+    const int j = min(tid / g, bk - 1), part = tid & (g - 1);
+    const double* Pj = P + (size_t)j * m;
+    const double* z = zs + s0;
+    const double* x = xv + s0;
+    const double az = dot_part(
+        part, bk, g,
+        [&](int i) {
+          const double p = Pj[i];
+          return i > j ? p : (i == j ? 1.0 : 0.0);
+        },
+        [&](int i) { return z[i]; });
+    const double ax = dot_part(bk + part, len, g, [&](int i) { return Pj[i]; }, [&](int i) { return x[i]; });
+    const double acc = group_sum(az - ax, g);
+    if (part == 0 && tid / g < bk) xv[s0 + j] = acc;
+    __syncthreads();
   }
-  __syncthreads();
-  const int wp = tid >> 5, lane = tid & 31;
-  if (stage && c <= ST) {
-    // pipelined unit upper triangle L_cc^T x = t, last column first
-    if (32 * wp < c) {
-      const int i = 32 * wp + lane;
-      double v = (i < c) ? xv[i] : 0.0;
-      const int top = min(c, 32 * wp + 32) - 1;  // highest row of this warp
-      for (int j = c - 1; j >= 32 * wp; --j) {
-        const double lv = (i < j) ? Ls[j + (size_t)i * m] : 0.0;  // L(j, i)
-        double xj;
-        if (j > top) {
-          xj = take(xs + j, s.spin_limit, s_to);
-        } else {
-          xj = __shfl_sync(FULL, v, j & 31);
-          if (lane == (j & 31)) *(volatile double*)(xs + j) = xj;
-        }
-        v = fma(-lv, xj, v);
-      }
-      if (i < c) xv[i] = v;
-    }
-  } else if (tid < 32) {
-    for (int j = c - 1; j >= 0; --j) {
-      const double xj = xv[j];
-      __syncwarp();
-      for (int i = lane; i < j; i += 32) xv[i] = fma(-Ls[j + (size_t)i * m], xj, xv[i]);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
   for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
+}
+
+// In-place inverses of the unit lower triangular IB x IB diagonal blocks of
+// the panels solved by fwd_front/bwd_front (one InvItem per block, one block
+// of 256 threads per item), for the instances factored in this pass.  The
+// block is staged in shared memory; warp w computes columns 2w and 2w+1 of
+// X = T^{-1} (one per half-warp, lane i holding x_i) by substitution
+// T x = e_k: x_i = 0 for i < k, x_k = 1, then for j = k, k+1, ...: x_j is
+// final and x_i -= T_ij x_j for i > j (one FMA instruction per step, x_j
+// shuffled from its lane).  Warp w starts at j = 2w, so the 8 warps issue
+// 64 FMA instructions in all.
+__global__ void __launch_bounds__(256) k_diag_inv(Dev d, SnDev s, int i0) {
+  __shared__ double sT[IB * IB];
+  const InvItem it = s.inv[i0 + blockIdx.x];
+  if (!d.ctl[it.inst].need_factor) return;  // uniform over the block
+  double* T = s.L + it.off;
+  const int ld = it.ld, bk = it.bk, tid = threadIdx.x;
+  {
+    const int i = tid & (IB - 1), j = tid / IB;  // 256 threads = IB x IB entries
+    sT[tid] = (i > j && i < bk) ? T[i + (size_t)j * ld] : 0.0;
+  }
+  __syncthreads();
+  const int w = tid >> 5, lane = tid & 31, hf = lane >> 4, i = lane & 15;
+  const int k = 2 * w + hf;
+  double x = i == k ? 1.0 : 0.0;
+  for (int j = 2 * w; j < IB - 1; ++j) {
+    const double xj = __shfl_sync(FULL, x, (hf << 4) + j);
+    if (i > j) x = fma(-sT[i + j * IB], xj, x);
+  }
+  if (i > k && i < bk) T[i + (size_t)k * ld] = x;
+}
+
+// M_K = L_{e..m-1,K} X_K in place, after k_diag_inv: one block of 128
+// threads per ScaleUnit (32 rows of one block), X_K staged in shared memory,
+// lane r of every warp holding row r of the slice.  Output column j,
+// M_j = l_j + sum_{i>j} l_i X_ij, takes IB-1-j FMAs; warp w computes the
+// columns w, IB-1-w, w+4, IB-5-w (30 FMAs for IB = 16, the same in every warp).
+__global__ void __launch_bounds__(128) k_panel_scale(Dev d, SnDev s, int u0) {
+  static_assert(IB == 16, "column split of k_panel_scale");
+  __shared__ double sX[IB * IB];
+  const ScaleUnit su = s.scale[u0 + blockIdx.x];
+  const InvItem it = s.inv[su.item];
+  if (!d.ctl[it.inst].need_factor) return;  // uniform over the block
+  const int ld = it.ld, bk = it.bk, tid = threadIdx.x;
+  const double* X = s.L + it.off;
+  for (int t = tid; t < IB * IB; t += blockDim.x) {
+    const int i = t & (IB - 1), j = t / IB;
+    sX[t] = (i > j && i < bk) ? X[i + (size_t)j * ld] : 0.0;
+  }
+  const int rr = su.r0 + (tid & 31), w = tid >> 5;
+  const bool act = rr < it.rows;
+  double* B = s.L + it.off + bk + rr;  // L(e + rr, s0 + i) = B[i ld]
+  double l[IB];
+#pragma unroll
+  for (int i = 0; i < IB; ++i) l[i] = (act && i < bk) ? B[(size_t)i * ld] : 0.0;
+  __syncthreads();
+  double out[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = (q == 0) ? w : (q == 1) ? IB - 1 - w : (q == 2) ? w + 4 : IB - 5 - w;
+    double acc = l[0];  // l_j, selected without indexing registers by j
+#pragma unroll
+    for (int i = 1; i < IB; ++i) acc = (i == j) ? l[i] : acc;
+#pragma unroll
+    for (int i = 1; i < IB; ++i)
+      if (i > j) acc = fma(l[i], sX[i + j * IB], acc);
+    out[q] = acc;
+  }
+  // every warp has read its row's L before any column of it is overwritten
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = (q == 0) ? w : (q == 1) ? IB - 1 - w : (q == 2) ? w + 4 : IB - 5 - w;
+    if (act && j < bk) B[(size_t)j * ld] = out[q];
+  }
 }
 
 __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {

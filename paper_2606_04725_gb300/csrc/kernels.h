@@ -48,6 +48,8 @@ __global__ void k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
 __global__ void k_bwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
 __global__ void k_fwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap, int* flags);
 __global__ void k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap, int* flags);
+__global__ void k_diag_inv(Dev d, SnDev s, int i0);
+__global__ void k_panel_scale(Dev d, SnDev s, int u0);
 __global__ void k_big_zero(Dev d, SnDev s, const FrontDesc* dl);
 __global__ void k_big_extend(Dev d, SnDev s, const FrontDesc* dl, int k);
 __global__ void k_big_diag(Dev d, SnDev s, const FrontDesc* dl, int p);

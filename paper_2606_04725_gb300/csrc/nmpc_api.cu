@@ -67,10 +67,16 @@ struct nmpc_handle {
   std::vector<int> amap;                             // extend-add pairs (source, destination)
   std::vector<long long> amap_ptr;                   // ranges per (front, CTA, child)
   std::vector<int> lvl_cluster_smem;                 // bytes per CTA of the cluster kernel
+  std::vector<InvItem> inv_items;                    // blocks transformed after each factorization
+  std::vector<ScaleUnit> scale_units;                // 32-row slices below them
+  std::vector<int> lvl_inv_ptr, lvl_scale_ptr;       // their ranges per level
   int n_sm = 152;
   int cluster_ctas_per_sm = 1;  // CTAs of the cluster kernel per SM aimed at when choosing Q (2 measured no faster)
   int smem_cap_doubles = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // side stream of the panel transforms (forked per level, joined after the factorization)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<Ctl> h_ctl;
   Ctl* d_ctl_save = nullptr;
   long long launches = 0;
@@ -166,6 +172,10 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.dpiv = cv.take<double>(n);
   s.uv = cv.take<double>(A.nuv);
   s.fvec = cv.take<double>(A.sn_rows.size());
+  s.inv = cv.take<InvItem>(h->inv_items.size());
+  s.n_inv = (int)h->inv_items.size();
+  s.scale = cv.take<ScaleUnit>(h->scale_units.size());
+  s.n_scale = (int)h->scale_units.size();
   s.L = d.Lval;
   s.Kdiag = d.Kdiag;
   s.pivtol = A.mc.pivtol;
@@ -192,54 +202,89 @@ nmpc_status read_flags(nmpc_handle* h) {
   return NMPC_OK;
 }
 
+// the factorization of one level
+nmpc_status launch_factor_level(nmpc_handle* h, int l) {
+  const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
+  if (!cnt) return NMPC_OK;
+  if (h->lvl_cluster[l] > 0) {
+    const int Q = h->lvl_cluster[l];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cnt * Q);
+    cfg.blockDim = dim3(CLUSTER_THREADS);
+    cfg.dynamicSmemBytes = h->lvl_cluster_smem[l];
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = Q;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_factor_cluster, h->d, h->s, (const FrontDesc*)(h->s.desc + h->lvl_ptr[l])));
+    ++h->launches;
+    return NMPC_OK;
+  }
+  if (h->lvl_big[l]) {
+    const FrontDesc* dl = h->s.desc + h->lvl_ptr[l];
+    const long long mu2 = (long long)h->lvl_maxmu[l] * h->lvl_maxmu[l];
+    k_big_zero<<<dim3((unsigned)std::max(1LL, std::min(1024LL, (mu2 + 255) / 256)), cnt), 256, 0, h->stream>>>(h->d, h->s, dl);
+    ++h->launches;
+    for (int k = 0; k < h->lvl_maxch[l]; ++k) {
+      k_big_extend<<<dim3((unsigned)std::max(1, std::min(1024, h->lvl_maxmc[l])), cnt), 256, 0, h->stream>>>(h->d, h->s, dl, k);
+      ++h->launches;
+    }
+    const int npan = (h->lvl_maxc[l] + BIG_NB - 1) / BIG_NB;
+    for (int p = 0; p < npan; ++p) {
+      const int jb = p * BIG_NB;
+      k_big_diag<<<cnt, 32, 0, h->stream>>>(h->d, h->s, dl, p);
+      const int rows = std::max(0, h->lvl_maxm[l] - jb - 1);
+      k_big_trsm<<<dim3((unsigned)std::max(1, (rows + BIG_ROWS - 1) / BIG_ROWS), cnt), BIG_ROWS, 0, h->stream>>>(h->d, h->s, dl, p);
+      const int R = std::max(0, h->lvl_maxm[l] - jb - 1);
+      const long long nb = (R + BIG_TILE - 1) / BIG_TILE;
+      k_big_update<<<dim3((unsigned)std::max(1LL, nb * (nb + 1) / 2), cnt), 256, 0, h->stream>>>(h->d, h->s, dl, p);
+      h->launches += 3;
+    }
+    return NMPC_OK;
+  }
+  k_factor_level<<<cnt, FACTOR_THREADS, h->lvl_smem_factor[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
+                                                                 h->smem_cap_doubles);
+  ++h->launches;
+  return NMPC_OK;
+}
+
+// All levels.  The panel transform of a level (k_diag_inv, then
+// k_panel_scale) only needs that level's factor, so it runs on the side
+// stream as soon as the level is factored, alongside the factorization of the
+// levels above (which leave most SMs idle near the root); the main stream
+// waits for it at the end, before the inertia test and the solves.  (The
+// one-shot static solve creates no stream: there the transforms run in order
+// on the main stream.)
 nmpc_status launch_factor(nmpc_handle* h) {
   const int nl = (int)h->lvl_ptr.size() - 1;
+  const bool fork = h->side != nullptr;
+  cudaStream_t ts = fork ? h->side : h->stream;
+  bool forked = false;
   for (int l = 0; l < nl; ++l) {
-    const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
-    if (!cnt) continue;
-    if (h->lvl_cluster[l] > 0) {
-      const int Q = h->lvl_cluster[l];
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(cnt * Q);
-      cfg.blockDim = dim3(CLUSTER_THREADS);
-      cfg.dynamicSmemBytes = h->lvl_cluster_smem[l];
-      cfg.stream = h->stream;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = Q;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_factor_cluster, h->d, h->s, (const FrontDesc*)(h->s.desc + h->lvl_ptr[l])));
-      ++h->launches;
-      continue;
+    const nmpc_status st = launch_factor_level(h, l);
+    if (st != NMPC_OK) return st;
+    const int i0 = h->lvl_inv_ptr[l], i1 = h->lvl_inv_ptr[l + 1];
+    const int u0 = h->lvl_scale_ptr[l], u1 = h->lvl_scale_ptr[l + 1];
+    if (i1 == i0) continue;
+    if (fork) {
+      CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
+      CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+      forked = true;
     }
-    if (h->lvl_big[l]) {
-      const FrontDesc* dl = h->s.desc + h->lvl_ptr[l];
-      const long long mu2 = (long long)h->lvl_maxmu[l] * h->lvl_maxmu[l];
-      k_big_zero<<<dim3((unsigned)std::max(1LL, std::min(1024LL, (mu2 + 255) / 256)), cnt), 256, 0, h->stream>>>(h->d, h->s, dl);
-      ++h->launches;
-      for (int k = 0; k < h->lvl_maxch[l]; ++k) {
-        k_big_extend<<<dim3((unsigned)std::max(1, std::min(1024, h->lvl_maxmc[l])), cnt), 256, 0, h->stream>>>(h->d, h->s, dl, k);
-        ++h->launches;
-      }
-      const int npan = (h->lvl_maxc[l] + BIG_NB - 1) / BIG_NB;
-      for (int p = 0; p < npan; ++p) {
-        const int jb = p * BIG_NB;
-        k_big_diag<<<cnt, 32, 0, h->stream>>>(h->d, h->s, dl, p);
-        const int rows = std::max(0, h->lvl_maxm[l] - jb - 1);
-        k_big_trsm<<<dim3((unsigned)std::max(1, (rows + BIG_ROWS - 1) / BIG_ROWS), cnt), BIG_ROWS, 0, h->stream>>>(h->d, h->s, dl, p);
-        const int R = std::max(0, h->lvl_maxm[l] - jb - 1);
-        const long long nb = (R + BIG_TILE - 1) / BIG_TILE;
-        k_big_update<<<dim3((unsigned)std::max(1LL, nb * (nb + 1) / 2), cnt), 256, 0, h->stream>>>(h->d, h->s, dl, p);
-        h->launches += 3;
-      }
-      continue;
-    }
-    k_factor_level<<<cnt, FACTOR_THREADS, h->lvl_smem_factor[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
-                                                                   h->smem_cap_doubles);
+    k_diag_inv<<<i1 - i0, 256, 0, ts>>>(h->d, h->s, i0);
     ++h->launches;
+    if (u1 > u0) {
+      k_panel_scale<<<u1 - u0, 128, 0, ts>>>(h->d, h->s, u0);
+      ++h->launches;
+    }
+  }
+  if (forked) {
+    CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side));
+    CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   }
   return NMPC_OK;
 }
@@ -588,6 +633,29 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
     }
     h->lvl_big[l] = ((h->lvl_cluster[l] == 0 && h->opt.factor_mode == 0) || h->opt.factor_mode == 2) ? 1 : 0;
   }
+  // blocks of the fronts solved one block per front (fwd_front/bwd_front)
+  h->inv_items.clear();
+  h->scale_units.clear();
+  h->lvl_inv_ptr.assign(nl + 1, 0);
+  h->lvl_scale_ptr.assign(nl + 1, 0);
+  for (int l = 0; l < nl; ++l) {
+    h->lvl_inv_ptr[l] = (int)h->inv_items.size();
+    h->lvl_scale_ptr[l] = (int)h->scale_units.size();
+    if (h->lvl_bigsolve[l]) continue;
+    for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd) {
+      const int J = A.level_sn[qd];
+      const int mm = A.sn_nrow[J], cc = A.sn_ncol[J];
+      for (int s0 = 0; s0 < cc; s0 += IB) {
+        const int bk = std::min(IB, cc - s0);
+        if (bk < 2) continue;
+        const int rows = mm - s0 - bk;
+        for (int r0 = 0; r0 < rows; r0 += 32) h->scale_units.push_back({(int)h->inv_items.size(), r0});
+        h->inv_items.push_back({A.sn_Lptr[J] + s0 + (long long)s0 * mm, mm, bk, A.sn_inst[J], rows});
+      }
+    }
+  }
+  h->lvl_inv_ptr[nl] = (int)h->inv_items.size();
+  h->lvl_scale_ptr[nl] = (int)h->scale_units.size();
   h->lvl_smem_bwd.assign(nl, 8);
   for (int l = 0; l < nl; ++l)
     for (int q = A.level_ptr[l]; q < A.level_ptr[l + 1]; ++q) {
@@ -743,6 +811,8 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
     if (!h->amap.empty())
       CUDA_TRY(h, cudaMemcpyAsync(const_cast<IdxPair*>(s.amap), h->amap.data(), h->amap.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     CUDA_TRY(h, up(s.amap_ptr, h->amap_ptr, st));
+    CUDA_TRY(h, up(s.inv, h->inv_items, st));
+    CUDA_TRY(h, up(s.scale, h->scale_units, st));
     CUDA_TRY(h, cudaStreamSynchronize(st));  // the host vector goes out of scope
   }
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
@@ -801,6 +871,9 @@ nmpc_status nmpc_bind(nmpc_handle* h, void* ws, size_t bytes) {
   CUDA_TRY(h, cudaMallocHost(&h->h_flags, 4 * sizeof(int)));
   CUDA_TRY(h, cudaEventCreate(&h->ev0));
   CUDA_TRY(h, cudaEventCreate(&h->ev1));
+  CUDA_TRY(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   h->bound = true;
   return NMPC_OK;
 }
@@ -1183,8 +1256,12 @@ void nmpc_destroy(nmpc_handle* h) {
   if (h->bound) {
     cudaStreamSynchronize(h->stream);
     if (h->h_flags) cudaFreeHost(h->h_flags);
+    if (h->side) cudaStreamSynchronize(h->side);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
   }

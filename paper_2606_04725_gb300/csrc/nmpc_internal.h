@@ -155,6 +155,26 @@ struct FrontDesc {
   long long ch_relptr[DESC_CH], ch_Uptr[DESC_CH], ch_uvptr[DESC_CH];
 };
 
+// The triangular solves of the fronts solved one block per front work on a
+// transformed panel, written over the factor after each factorization (the
+// pivots 1/d_j on the diagonal are kept).  For each block K of IB columns
+// (s0 .. e-1, e = s0 + bk):
+//   diagonal block: X_K = T_K^{-1} below its diagonal, T_K the unit lower
+//                   triangular diagonal block of L;
+//   rows e .. m-1:  M_K = L_{e..m-1,K} X_K.
+// One InvItem per block with at least two columns: offset of its first entry
+// (s0, s0) in L, leading dimension (m of the front), order bk <= IB,
+// instance and the number m - e of rows below it.  One ScaleUnit per 32 of
+// those rows.
+constexpr int IB = 16;
+struct alignas(8) InvItem {
+  long long off;
+  int ld, bk, inst, rows;
+};
+struct alignas(8) ScaleUnit {
+  int item, r0;
+};
+
 // Supernodal structure for the factor and solve kernels.
 struct SnDev {
   int ns;
@@ -180,6 +200,9 @@ struct SnDev {
   double* U;
   double* uv;                 // update vectors of the forward solve
   double* fvec;               // front vectors of large-front solves (offset: the front's row list)
+  const InvItem* inv;         // diagonal blocks transformed after each factorization
+  const ScaleUnit* scale;     // 32-row slices of the rows below them
+  int n_inv, n_scale;
   const double* Kdiag;        // assembled diagonal in factor order
   double pivtol;
   long long spin_limit;       // polls of a bounded wait between CTAs
