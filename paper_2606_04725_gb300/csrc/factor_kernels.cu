@@ -244,7 +244,9 @@ __global__ void k_factor_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap
 //       the 8 entries of column 0 by warp 1), then runs the pivot chain: per
 //       column a shuffle of the pivot, its reciprocal (recip_nr: a seed and
 //       three FMAs), and one multiply and one FMA that update every remaining
-//       entry of the block at once -- five FP64 instructions per column;
+//       entry of the block at once -- five FP64 instructions per column, of
+//       which four are on the chain (the product of the two column entries is
+//       formed while the reciprocal is computed);
 //     warps 1-3, 5-7: apply the previous panel to the rows below the block;
 //   phase 2: every row below the pivot block is solved against it (w-step
 //     forward substitution, one row per thread).
@@ -325,6 +327,7 @@ __device__ __forceinline__ int tri_lane(int r, int k) { return r * (r - 1) / 2 +
 // the rows below are solved one column behind the chain instead of after it.
 constexpr int FCT = 256;
 constexpr int NBULK = 192;  // threads of warps 1-3, 5-7
+static_assert(NBULK == FCT - 64, "warps 0 and 4 are not bulk warps");
 
 __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* thr, double* Lg, double* Wg,
                              const double* Pl, const double* Pw, int wprev, int m, int jb, int w, int lc0,
@@ -369,6 +372,7 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
           y = __shfl_sync(FULL, a, tri_lane(max(kA, jj), jj));
         }
         const double p = (jj == 0) ? __shfl_sync(FULL, b, 0) : __shfl_sync(FULL, a, tri_lane(jj, jj));
+        const double xy = x * y;  // independent of the pivot: off the chain p -> 1/p -> next pivot
         const double iv = recip_nr(p);
         inv[jj] = iv;
         if (lane == 0) {
@@ -376,7 +380,7 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
           invd[jj] = iv;
           pub[jj * PB + jj] = iv;
         }
-        if (vA && kA > jj && rA < w) a = fma(-(x * iv), y, a);
+        if (vA && kA > jj && rA < w) a = fma(-xy, iv, a);
       }
     }
     // outputs of the pivot block: L and W to global memory, trailing block columns in place
@@ -474,7 +478,6 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl) {
   __shared__ int s_timeout;
   __shared__ double s_pubv[PB * PB];         // pivot columns of the current panel, published by warp 0
   __shared__ double sB[PB];
-  auto lcol = [&](int k) { return ((k / PB) / Q) * PB + (k % PB); };
   // ---- assemble: own columns from the condensed values, then the children
   for (int t0 = tid; t0 < m * ncl; t0 += 4 * nt) {
     double v[4];

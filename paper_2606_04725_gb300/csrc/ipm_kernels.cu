@@ -115,74 +115,155 @@ __global__ void k_ctl_init(Dev d, double mu0) {
   d.ctl[i] = c;
 }
 
+// ---------------------------------------------------- fused step endings
+// Every reduction kernel ends its step itself.  A chunk block stores its
+// partial, then thread 0 fences (device scope) and arrives on its instance's
+// counter; the block that arrives last sees every partial of the instance,
+// and its warp 0 combines them and runs the instance's control step.  In the
+// graph-driven loop the last instance to finish (a second counter) then sets
+// the graph's conditions.  The block that completes a counter resets it, so
+// every counter is zero again when the kernel ends.
+__device__ __forceinline__ bool arrive_last(int* cnt, int total) {  // thread 0 only
+  __threadfence();
+  const int t = atomicAdd(cnt, 1);
+  if (t != total - 1) return false;
+  *cnt = 0;
+  __threadfence();
+  return true;
+}
+// uniform over the block: this block is the last of instance inst to arrive
+__device__ __forceinline__ bool last_of_instance(const Dev& d, int inst) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) s_last = arrive_last(d.red_cnt + inst, d.inst_chunk_ptr[inst + 1] - d.inst_chunk_ptr[inst]);
+  __syncthreads();
+  return s_last != 0;
+}
+// uniform over the block: this block finished the last instance
+__device__ __forceinline__ bool last_instance(const Dev& d) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) s_last = arrive_last(d.red_cnt + d.n_inst, d.n_inst);
+  __syncthreads();
+  return s_last != 0;
+}
+
+// any instance running / needing a factorization / searching (block-wide)
+__device__ __forceinline__ void any_flags(const Dev& d, int* run, int* fac, int* ls) {
+  __shared__ int f[3];
+  if (threadIdx.x < 3) f[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < d.n_inst; i += blockDim.x) {
+    const Ctl& c = d.ctl[i];
+    if (c.status == ST_RUNNING) atomicOr(&f[0], 1);
+    if (c.need_factor) atomicOr(&f[1], 1);
+    if (c.ls_active) atomicOr(&f[2], 1);
+  }
+  __syncthreads();
+  *run = f[0];
+  *fac = f[1];
+  *ls = f[2];
+}
+
+// Set the graph's conditions at the end of a step (block-wide) and count the
+// trip.  The interior-point loop runs as one CUDA graph with conditional
+// nodes: WHILE over iterations, IF on "still running", WHILE over inertia
+// corrections, WHILE over line-search trials.  Every loop also stops at a trip
+// limit, whatever the control state says, so a graph launch always ends.
+enum StepEnd { END_EVAL = 0, END_FACTOR = 1, END_DIR = 2, END_TRIAL = 3 };
+__device__ void set_conditions(const Dev& d, const CondArgs& ca, int kind) {
+  int run, fac, ls;
+  any_flags(d, &run, &fac, &ls);
+  if (threadIdx.x != 0) return;
+  int* ctr = ca.counters;
+  if (kind == END_EVAL) {
+    if (ctr[0] >= ca.cap_iter) run = 0;
+    cudaGraphSetConditional(ca.h_run, run ? 1u : 0u);
+    cudaGraphSetConditional(ca.h_if, run ? 1u : 0u);
+    cudaGraphSetConditional(ca.h_fac, (run && fac) ? 1u : 0u);
+    ++ctr[0];
+  } else if (kind == END_FACTOR) {
+    if (ctr[1] >= ca.cap_inner) fac = 0;
+    cudaGraphSetConditional(ca.h_fac, fac ? 1u : 0u);
+    ++ctr[1];
+  } else {
+    if (ctr[2] >= ca.cap_inner) ls = 0;
+    cudaGraphSetConditional(ca.h_ls, ls ? 1u : 0u);
+    if (kind == END_TRIAL) ++ctr[2];
+  }
+}
+
 // ----------------------------------------------------------- evaluation
 
 // Stationarity, feasibility and complementarity of the lifted barrier
 // problem (W&B eq. (5)) plus objective, log-barrier and theta sums.
-__global__ void k_red_eval(Dev d) {
+__device__ void ctl_pre_warp(const Dev& d, int i, int lane, int max_iter);
+
+__global__ void k_red_eval(Dev d, int max_iter, CondArgs ca) {
   const Chunk ch = d.chunks[blockIdx.x];
   const Ctl& c = d.ctl[ch.inst];
-  if (c.status != ST_RUNNING) return;
-  const double gam = d.mc.gamma;
-  const int WH = d.mc.WH;
-  // dual, prim, cmax, cmin, sum_l, sum_z, f, log-mantissa, log-exponent, theta, nonfinite
-  double v[11] = {0.0, 0.0, 0.0, DBL_MAX, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
-  const int op[11] = {1, 1, 1, 2, 0, 0, 0, 3, 0, 0, 0};
-  if (ch.kind == 0) {
-    for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
-      double r = d.grad[j];
-      for (int q = d.Hcsc_ptr[j]; q < d.Hcsc_ptr[j + 1]; ++q) {
-        const int s = d.Hcsc_slot[q], row = s / WH;
-        r += d.Hv[s] * (d.wp[row] - d.wm[row]);
+  if (c.status == ST_RUNNING) {  // uniform over the block
+    const double gam = d.mc.gamma;
+    const int WH = d.mc.WH;
+    // dual, prim, cmax, cmin, sum_l, sum_z, f, log-mantissa, log-exponent, theta, nonfinite
+    double v[11] = {0.0, 0.0, 0.0, DBL_MAX, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
+    const int op[11] = {1, 1, 1, 2, 0, 0, 0, 3, 0, 0, 0};
+    if (ch.kind == 0) {
+      for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
+        double r = d.grad[j];
+        for (int q = d.Hcsc_ptr[j]; q < d.Hcsc_ptr[j + 1]; ++q) {
+          const int s = d.Hcsc_slot[q], row = s / WH;
+          r += d.Hv[s] * (d.wp[row] - d.wm[row]);
+        }
+        const double yj = d.y[j], lo = d.yL[j], hi = d.yU[j];
+        if (fin(lo)) {
+          r -= d.zL[j];
+          const double p = (yj - lo) * d.zL[j];
+          v[2] = max_nn(v[2], p); v[3] = min_nn(v[3], p);
+          v[5] += d.zL[j];
+          logacc_mul(v[7], v[8], yj - lo);
+        }
+        if (fin(hi)) {
+          r += d.zU[j];
+          const double p = (hi - yj) * d.zU[j];
+          v[2] = max_nn(v[2], p); v[3] = min_nn(v[3], p);
+          v[5] += d.zU[j];
+          logacc_mul(v[7], v[8], hi - yj);
+        }
+        if (!fin(r)) v[10] += 1.0;
+        v[0] = max_nn(v[0], fabs(r));
+        v[6] += d.fvar[j];
       }
-      const double yj = d.y[j], lo = d.yL[j], hi = d.yU[j];
-      if (fin(lo)) {
-        r -= d.zL[j];
-        const double p = (yj - lo) * d.zL[j];
-        v[2] = max_nn(v[2], p); v[3] = min_nn(v[3], p);
-        v[5] += d.zL[j];
-        logacc_mul(v[7], v[8], yj - lo);
+    } else {
+      for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
+        const double h = d.h[r];
+        if (!fin(h)) v[10] += 1.0;
+        v[0] = max_nn(v[0], max_nn(fabs(d.wp[r] - d.bp[r]), fabs(d.wm[r] - d.bm[r])));
+        const double cp = h - gam + d.sp[r], cm = -h - gam + d.sm[r];
+        v[1] = max_nn(v[1], max_nn(fabs(cp), fabs(cm)));
+        const double pp = d.sp[r] * d.bp[r], pm = d.sm[r] * d.bm[r];
+        v[2] = max_nn(v[2], max_nn(pp, pm)); v[3] = min_nn(v[3], min_nn(pp, pm));
+        v[4] += fabs(d.wp[r]) + fabs(d.wm[r]);
+        v[5] += d.bp[r] + d.bm[r];
+        logacc_mul(v[7], v[8], d.sp[r]);
+        logacc_mul(v[7], v[8], d.sm[r]);
+        v[9] += fabs(cp) + fabs(cm);
       }
-      if (fin(hi)) {
-        r += d.zU[j];
-        const double p = (hi - yj) * d.zU[j];
-        v[2] = max_nn(v[2], p); v[3] = min_nn(v[3], p);
-        v[5] += d.zU[j];
-        logacc_mul(v[7], v[8], hi - yj);
-      }
-      if (!fin(r)) v[10] += 1.0;
-      v[0] = max_nn(v[0], fabs(r));
-      v[6] += d.fvar[j];
     }
-  } else {
-    for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
-      const double h = d.h[r];
-      if (!fin(h)) v[10] += 1.0;
-      v[0] = max_nn(v[0], max_nn(fabs(d.wp[r] - d.bp[r]), fabs(d.wm[r] - d.bm[r])));
-      const double cp = h - gam + d.sp[r], cm = -h - gam + d.sm[r];
-      v[1] = max_nn(v[1], max_nn(fabs(cp), fabs(cm)));
-      const double pp = d.sp[r] * d.bp[r], pm = d.sm[r] * d.bm[r];
-      v[2] = max_nn(v[2], max_nn(pp, pm)); v[3] = min_nn(v[3], min_nn(pp, pm));
-      v[4] += fabs(d.wp[r]) + fabs(d.wm[r]);
-      v[5] += d.bp[r] + d.bm[r];
-      logacc_mul(v[7], v[8], d.sp[r]);
-      logacc_mul(v[7], v[8], d.sm[r]);
-      v[9] += fabs(cp) + fabs(cm);
+    block_reduce<11>(v, op);
+    if (threadIdx.x == 0) {
+      RedEval e;
+      e.dual = v[0]; e.prim = v[1]; e.cmax = v[2]; e.cmin = v[3]; e.sum_l = v[4]; e.sum_z = v[5];
+      e.f = v[6]; e.lgm = v[7]; e.lge = v[8]; e.theta = v[9]; e.nonfinite = v[10];
+      d.red_eval[blockIdx.x] = e;
     }
   }
-  block_reduce<11>(v, op);
-  if (threadIdx.x == 0) {
-    RedEval e;
-    e.dual = v[0]; e.prim = v[1]; e.cmax = v[2]; e.cmin = v[3]; e.sum_l = v[4]; e.sum_z = v[5];
-    e.f = v[6]; e.lgm = v[7]; e.lge = v[8]; e.theta = v[9]; e.nonfinite = v[10];
-    d.red_eval[blockIdx.x] = e;
-  }
+  if (!last_of_instance(d, ch.inst)) return;
+  if (threadIdx.x < 32) ctl_pre_warp(d, ch.inst, threadIdx.x, max_iter);
+  if (ca.on && last_instance(d)) set_conditions(d, ca, END_EVAL);
 }
 
 // Convergence tests and barrier update (Algorithm 2 outer loop; W&B A-2/A-3).
-__global__ void k_ctl_pre(Dev d, int max_iter) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= d.n_inst) return;
+// (warp 0 of the last chunk block of instance i)
+__device__ void ctl_pre_warp(const Dev& d, int i, int lane, int max_iter) {
   Ctl c = d.ctl[i];
   if (c.status != ST_RUNNING) return;
   // chunk partials: lanes in chunk order, then a fixed shuffle tree
@@ -284,9 +365,7 @@ __global__ void k_assemble(Dev d, const int* tgt_inst, const double* Drow) {
 
 // Inertia correction after a factorization attempt (W&B Algorithm IC on
 // delta_w only; positive pivots <=> inertia of eq. infiniteOCP-inertia).
-__global__ void k_ctl_factor(Dev d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n_inst) return;
+__device__ void ctl_factor_one(const Dev& d, int i) {
   Ctl c = d.ctl[i];
   if (!c.need_factor) return;
   if (!c.factor_fail) {
@@ -301,6 +380,16 @@ __global__ void k_ctl_factor(Dev d) {
   }
   d.ctl[i] = c;
 }
+
+// One block: a thread per instance, then the graph's conditions.
+__global__ void k_ctl_factor(Dev d, CondArgs ca) {
+  for (int i = threadIdx.x; i < d.n_inst; i += blockDim.x) ctl_factor_one(d, i);
+  if (ca.on) {
+    __syncthreads();
+    set_conditions(d, ca, END_FACTOR);
+  }
+}
+
 
 // right-hand side of eq. liftedkkt-pd, scattered into the factor ordering
 __global__ void k_rhs(Dev d) {
@@ -321,9 +410,7 @@ __global__ void k_rhs(Dev d) {
 
 // --------------------------------------------------------------- recovery
 
-__global__ void k_recover_vars(Dev d) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= d.n) return;
+__device__ void recover_var(const Dev& d, int v) {
   const Ctl& c = d.ctl[d.var_inst[v]];
   if (c.status != ST_RUNNING) return;
   const double mu = c.mu;
@@ -338,9 +425,7 @@ __global__ void k_recover_vars(Dev d) {
 
 // ds = -r4 -+ H dy, dw = -r2 - Q ds, db = mu/s - b - Q ds (eliminated rows of
 // eq. infiniteOCP-augmented for both lifted sides)
-__global__ void k_recover_rows(Dev d) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= d.m) return;
+__device__ void recover_row(const Dev& d, int r) {
   const Ctl& c = d.ctl[d.row_inst[r]];
   if (c.status != ST_RUNNING) return;
   const int WH = d.mc.WH;
@@ -348,7 +433,7 @@ __global__ void k_recover_rows(Dev d) {
   double Hd = 0.0;
   for (int s = 0; s < WH; ++s) {
     const int col = d.Hcol[(size_t)r * WH + s];
-    if (col >= 0) Hd += d.Hv[(size_t)r * WH + s] * d.dy[col];
+    if (col >= 0) Hd += d.Hv[(size_t)r * WH + s] * d.b[d.perm[col]];  // dy, read where the solve left it
   }
   const double sp = d.sp[r], sm = d.sm[r], isp = d.isp[r], ism = d.ism[r];
   const double Qp = d.bp[r] * isp, Qm = d.bm[r] * ism;
@@ -362,54 +447,67 @@ __global__ void k_recover_rows(Dev d) {
   d.dbm[r] = mu * ism - d.bm[r] - Qm * dsm;
 }
 
+// variables (threads 0 .. n-1) and rows (n .. n+m-1) in one launch: the rows
+// read dy from the solve's output, not from the variables' copy
+__global__ void k_recover(Dev d) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < d.n) recover_var(d, t);
+  else if (t < d.n + d.m) recover_row(d, t - d.n);
+}
+
 // Fraction-to-the-boundary step limits and grad(phi_mu)^T d.  The limits are
 // tau / max_i(-dv_i / v_i) over components moving toward their bound, with
 // the stored reciprocals, so the chunk needs no division per element.
-__global__ void k_red_dir(Dev d) {
+__device__ void ctl_dir_warp(const Dev& d, int i, int lane);
+
+__global__ void k_red_dir(Dev d, CondArgs ca) {
   const Chunk ch = d.chunks[blockIdx.x];
   const Ctl& c = d.ctl[ch.inst];
-  if (c.status != ST_RUNNING) return;
-  const double mu = c.mu, tau = c.tau;
-  double v[3] = {0.0, 0.0, 0.0};  // max primal ratio, max dual ratio, gphi
-  const int op[3] = {1, 1, 0};
-  if (ch.kind == 0) {
-    for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
-      const double dy = d.dy[j];
-      double gp = d.grad[j];
-      if (fin(d.yL[j])) {
-        const double ig = d.igL[j];
-        v[0] = max_nn(v[0], -dy * ig);
-        gp -= mu * ig;
-        v[1] = max_nn(v[1], -d.dzL[j] * d.izL[j]);
+  if (c.status == ST_RUNNING) {  // uniform over the block
+    const double mu = c.mu, tau = c.tau;
+    double v[3] = {0.0, 0.0, 0.0};  // max primal ratio, max dual ratio, gphi
+    const int op[3] = {1, 1, 0};
+    if (ch.kind == 0) {
+      for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
+        const double dy = d.dy[j];
+        double gp = d.grad[j];
+        if (fin(d.yL[j])) {
+          const double ig = d.igL[j];
+          v[0] = max_nn(v[0], -dy * ig);
+          gp -= mu * ig;
+          v[1] = max_nn(v[1], -d.dzL[j] * d.izL[j]);
+        }
+        if (fin(d.yU[j])) {
+          const double ig = d.igU[j];
+          v[0] = max_nn(v[0], dy * ig);
+          gp += mu * ig;
+          v[1] = max_nn(v[1], -d.dzU[j] * d.izU[j]);
+        }
+        v[2] += gp * dy;
       }
-      if (fin(d.yU[j])) {
-        const double ig = d.igU[j];
-        v[0] = max_nn(v[0], dy * ig);
-        gp += mu * ig;
-        v[1] = max_nn(v[1], -d.dzU[j] * d.izU[j]);
+    } else {
+      for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
+        const double isp = d.isp[r], ism = d.ism[r];
+        v[0] = max_nn(v[0], max_nn(-d.dsp[r] * isp, -d.dsm[r] * ism));
+        v[1] = max_nn(v[1], max_nn(-d.dbp[r] * d.ibp[r], -d.dbm[r] * d.ibm[r]));
+        v[2] -= mu * (d.dsp[r] * isp + d.dsm[r] * ism);
       }
-      v[2] += gp * dy;
     }
-  } else {
-    for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
-      const double isp = d.isp[r], ism = d.ism[r];
-      v[0] = max_nn(v[0], max_nn(-d.dsp[r] * isp, -d.dsm[r] * ism));
-      v[1] = max_nn(v[1], max_nn(-d.dbp[r] * d.ibp[r], -d.dbm[r] * d.ibm[r]));
-      v[2] -= mu * (d.dsp[r] * isp + d.dsm[r] * ism);
+    block_reduce<3>(v, op);
+    if (threadIdx.x == 0) {
+      const double ap = v[0] > tau ? tau / v[0] : 1.0;
+      const double ad = v[1] > tau ? tau / v[1] : 1.0;
+      d.red_dir[blockIdx.x] = RedDir{ap, ad, v[2], 0.0};
     }
   }
-  block_reduce<3>(v, op);
-  if (threadIdx.x == 0) {
-    const double ap = v[0] > tau ? tau / v[0] : 1.0;
-    const double ad = v[1] > tau ? tau / v[1] : 1.0;
-    d.red_dir[blockIdx.x] = RedDir{ap, ad, v[2], 0.0};
-  }
+  if (!last_of_instance(d, ch.inst)) return;
+  if (threadIdx.x < 32) ctl_dir_warp(d, ch.inst, threadIdx.x);
+  if (ca.on && last_instance(d)) set_conditions(d, ca, END_DIR);
 }
 
 // start of the backtracking filter line search (W&B Sec. 2.3): alpha_min
-__global__ void k_ctl_dir(Dev d) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= d.n_inst) return;
+// (warp 0 of the last chunk block of instance i)
+__device__ void ctl_dir_warp(const Dev& d, int i, int lane) {
   Ctl c = d.ctl[i];
   if (c.status != ST_RUNNING) return;
   double v[3] = {1.0, 1.0, 0.0};
@@ -461,37 +559,42 @@ __global__ void k_trial_point(Dev d) {
   }
 }
 
-__global__ void k_red_trial(Dev d) {
+__device__ void ctl_ls_warp(const Dev& d, int i, int lane);
+
+__global__ void k_red_trial(Dev d, CondArgs ca) {
   const Chunk ch = d.chunks[blockIdx.x];
   const Ctl& c = d.ctl[ch.inst];
-  if (!c.ls_active) return;
-  const double gam = d.mc.gamma;
-  double v[5] = {0.0, 1.0, 0.0, 0.0, 0.0};  // f, log-mantissa, log-exponent, theta, nonfinite
-  const int op[5] = {0, 3, 0, 0, 0};
-  if (ch.kind == 0) {
-    for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
-      const double y = d.yt[j];
-      v[0] += d.fvart[j];
-      if (fin(d.yL[j])) logacc_mul(v[1], v[2], y - d.yL[j]);
-      if (fin(d.yU[j])) logacc_mul(v[1], v[2], d.yU[j] - y);
+  if (c.ls_active) {  // uniform over the block
+    const double gam = d.mc.gamma;
+    double v[5] = {0.0, 1.0, 0.0, 0.0, 0.0};  // f, log-mantissa, log-exponent, theta, nonfinite
+    const int op[5] = {0, 3, 0, 0, 0};
+    if (ch.kind == 0) {
+      for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
+        const double y = d.yt[j];
+        v[0] += d.fvart[j];
+        if (fin(d.yL[j])) logacc_mul(v[1], v[2], y - d.yL[j]);
+        if (fin(d.yU[j])) logacc_mul(v[1], v[2], d.yU[j] - y);
+      }
+    } else {
+      for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
+        const double h = d.ht[r];
+        if (!fin(h)) v[4] += 1.0;
+        logacc_mul(v[1], v[2], d.spt[r]);
+        logacc_mul(v[1], v[2], d.smt[r]);
+        v[3] += fabs(h - gam + d.spt[r]) + fabs(-h - gam + d.smt[r]);
+      }
     }
-  } else {
-    for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
-      const double h = d.ht[r];
-      if (!fin(h)) v[4] += 1.0;
-      logacc_mul(v[1], v[2], d.spt[r]);
-      logacc_mul(v[1], v[2], d.smt[r]);
-      v[3] += fabs(h - gam + d.spt[r]) + fabs(-h - gam + d.smt[r]);
-    }
+    block_reduce<5>(v, op);
+    if (threadIdx.x == 0) d.red_trial[blockIdx.x] = RedTrial{v[0], v[1], v[2], v[3], v[4]};
   }
-  block_reduce<5>(v, op);
-  if (threadIdx.x == 0) d.red_trial[blockIdx.x] = RedTrial{v[0], v[1], v[2], v[3], v[4]};
+  if (!last_of_instance(d, ch.inst)) return;
+  if (threadIdx.x < 32) ctl_ls_warp(d, ch.inst, threadIdx.x);
+  if (ca.on && last_instance(d)) set_conditions(d, ca, END_TRIAL);
 }
 
 // filter acceptance test of one trial (W&B Sec. 2.3, A-5.2 .. A-5.4)
-__global__ void k_ctl_ls(Dev d) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= d.n_inst) return;
+// (warp 0 of the last chunk block of instance i)
+__device__ void ctl_ls_warp(const Dev& d, int i, int lane) {
   Ctl c = d.ctl[i];
   if (!c.ls_active) return;
   double v[5] = {0.0, 1.0, 0.0, 0.0, 0.0};  // f, log-mantissa, log-exponent, theta, nonfinite
@@ -550,9 +653,7 @@ __device__ __forceinline__ double safeguard(double z, double g, double mu) {
 
 // accept the step; bound multipliers take the dual step and the safeguard
 // of W&B eq. (16)
-__global__ void k_update_vars(Dev d) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= d.n) return;
+__device__ void update_var(const Dev& d, int v) {
   const Ctl& c = d.ctl[d.var_inst[v]];
   if (c.phase != 1 || c.status != ST_RUNNING) return;
   const double y = d.yt[v], mu = c.mu, ad = c.alpha_dual;
@@ -561,9 +662,7 @@ __global__ void k_update_vars(Dev d) {
   if (fin(d.yU[v])) d.zU[v] = safeguard(d.zU[v] + ad * d.dzU[v], d.yU[v] - y, mu);
 }
 
-__global__ void k_update_rows(Dev d) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= d.m) return;
+__device__ void update_row(const Dev& d, int r) {
   const Ctl& c = d.ctl[d.row_inst[r]];
   if (c.phase != 1 || c.status != ST_RUNNING) return;
   const double a = c.alpha, ad = c.alpha_dual, mu = c.mu;
@@ -574,6 +673,13 @@ __global__ void k_update_rows(Dev d) {
   d.wm[r] += a * d.dwm[r];
   d.bp[r] = safeguard(d.bp[r] + ad * d.dbp[r], sp, mu);
   d.bm[r] = safeguard(d.bm[r] + ad * d.dbm[r], sm, mu);
+}
+
+// variables (threads 0 .. n-1) and rows (n .. n+m-1) in one launch
+__global__ void k_update(Dev d) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < d.n) update_var(d, t);
+  else if (t < d.n + d.m) update_row(d, t - d.n);
 }
 
 __global__ void k_ctl_post(Dev d) {
@@ -610,64 +716,6 @@ __global__ void k_summary(Dev d, int* flags) {
   }
   __syncthreads();
   if (threadIdx.x < 3) flags[threadIdx.x] = f[threadIdx.x];
-}
-
-// ------------------------------------------------ graph loop conditions
-// The interior-point loop runs as one CUDA graph with conditional nodes
-// (WHILE over iterations, IF on "still running", WHILE over inertia
-// corrections and over line-search trials).  These one-block kernels end each
-// step: they set the next condition from the per-instance control state and
-// count the trips (counters[0] outer steps, [1] factorization attempts,
-// [2] line-search trials), so the host learns the kernel count afterwards.
-// Every loop also stops at a trip limit (cap), whatever the control state
-// says, so a graph launch always ends.
-__device__ __forceinline__ void any_flags(const Dev& d, int* run, int* fac, int* ls) {
-  __shared__ int f[3];
-  if (threadIdx.x < 3) f[threadIdx.x] = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < d.n_inst; i += blockDim.x) {
-    const Ctl& c = d.ctl[i];
-    if (c.status == ST_RUNNING) atomicOr(&f[0], 1);
-    if (c.need_factor) atomicOr(&f[1], 1);
-    if (c.ls_active) atomicOr(&f[2], 1);
-  }
-  __syncthreads();
-  *run = f[0];
-  *fac = f[1];
-  *ls = f[2];
-}
-
-__global__ void k_cond_pre(Dev d, cudaGraphConditionalHandle h_run, cudaGraphConditionalHandle h_if,
-                           cudaGraphConditionalHandle h_fac, int* counters, int cap) {
-  int run, fac, ls;
-  any_flags(d, &run, &fac, &ls);
-  if (threadIdx.x == 0) {
-    if (counters[0] >= cap) run = 0;
-    cudaGraphSetConditional(h_run, run ? 1u : 0u);
-    cudaGraphSetConditional(h_if, run ? 1u : 0u);
-    cudaGraphSetConditional(h_fac, (run && fac) ? 1u : 0u);
-    ++counters[0];
-  }
-}
-
-__global__ void k_cond_fac(Dev d, cudaGraphConditionalHandle h_fac, int* counters, int cap) {
-  int run, fac, ls;
-  any_flags(d, &run, &fac, &ls);
-  if (threadIdx.x == 0) {
-    if (counters[1] >= cap) fac = 0;
-    cudaGraphSetConditional(h_fac, fac ? 1u : 0u);
-    ++counters[1];
-  }
-}
-
-__global__ void k_cond_ls(Dev d, cudaGraphConditionalHandle h_ls, int* counters, int trial, int cap) {
-  int run, fac, ls;
-  any_flags(d, &run, &fac, &ls);
-  if (threadIdx.x == 0) {
-    if (counters[2] >= cap) ls = 0;
-    cudaGraphSetConditional(h_ls, ls ? 1u : 0u);
-    if (trial) ++counters[2];
-  }
 }
 
 }  // namespace nmpc

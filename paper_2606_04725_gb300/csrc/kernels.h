@@ -12,34 +12,26 @@ constexpr int EW = 128;   // element-wise kernels: smaller blocks spread FP64 wo
 // model_kernels.cu
 __global__ void k_eval_rows(Dev d, int use_trial, int with_jac);
 __global__ void k_eval_vars(Dev d, int use_trial);
+__global__ void k_eval(Dev d, int use_trial, int with_jac, int nbr);
 __global__ void k_set_params(Dev d, int i0, int i1, const double* x0, const double* sp, const double* up, int sp_len);
 __global__ void k_init_vars(Dev d, int warm, double push);
 __global__ void k_init_rows(Dev d, int warm, double push);
 
 // ipm_kernels.cu
 __global__ void k_ctl_init(Dev d, double mu0);
-__global__ void k_red_eval(Dev d);
-__global__ void k_ctl_pre(Dev d, int max_iter);
+__global__ void k_red_eval(Dev d, int max_iter, CondArgs ca);
 __global__ void k_zero_L(Dev d, const long long* inst_Lbeg, const long long* inst_Lend);
 __global__ void k_rows_pre(Dev d, double* Drow);
 __global__ void k_assemble(Dev d, const int* tgt_inst, const double* Drow);
-__global__ void k_ctl_factor(Dev d);
+__global__ void k_ctl_factor(Dev d, CondArgs ca);
 __global__ void k_rhs(Dev d);
-__global__ void k_recover_vars(Dev d);
-__global__ void k_recover_rows(Dev d);
-__global__ void k_red_dir(Dev d);
-__global__ void k_ctl_dir(Dev d);
+__global__ void k_recover(Dev d);
+__global__ void k_red_dir(Dev d, CondArgs ca);
 __global__ void k_trial_point(Dev d);
-__global__ void k_red_trial(Dev d);
-__global__ void k_ctl_ls(Dev d);
-__global__ void k_update_vars(Dev d);
-__global__ void k_update_rows(Dev d);
+__global__ void k_red_trial(Dev d, CondArgs ca);
+__global__ void k_update(Dev d);
 __global__ void k_ctl_post(Dev d);
 __global__ void k_summary(Dev d, int* flags);
-__global__ void k_cond_pre(Dev d, cudaGraphConditionalHandle h_run, cudaGraphConditionalHandle h_if,
-                           cudaGraphConditionalHandle h_fac, int* counters, int cap);
-__global__ void k_cond_fac(Dev d, cudaGraphConditionalHandle h_fac, int* counters, int cap);
-__global__ void k_cond_ls(Dev d, cudaGraphConditionalHandle h_ls, int* counters, int trial, int cap);
 
 // factor_kernels.cu
 __global__ void k_factor_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);

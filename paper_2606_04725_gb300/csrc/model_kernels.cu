@@ -152,9 +152,7 @@ __device__ void eval_row(const Dev& d, const double* y, int r, double* hout, dou
   }
 }
 
-__global__ void k_eval_rows(Dev d, int use_trial, int with_jac) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= d.m) return;
+__device__ void eval_row_at(const Dev& d, int r, int use_trial, int with_jac) {
   const Ctl& c = d.ctl[d.row_inst[r]];
   if (use_trial) {
     if (!c.ls_active) return;
@@ -169,6 +167,11 @@ __global__ void k_eval_rows(Dev d, int use_trial, int with_jac) {
       d.ibm[r] = 1.0 / d.bm[r];
     }
   }
+}
+
+__global__ void k_eval_rows(Dev d, int use_trial, int with_jac) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < d.m) eval_row_at(d, r, use_trial, with_jac);
 }
 
 // --------------------------------------------------------------- variables
@@ -276,9 +279,7 @@ __device__ void eval_var_hess(const Dev& d, int v) {
   }
 }
 
-__global__ void k_eval_vars(Dev d, int use_trial) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= d.n) return;
+__device__ void eval_var_at(const Dev& d, int v, int use_trial) {
   const Ctl& c = d.ctl[d.var_inst[v]];
   if (use_trial) {
     if (!c.ls_active) return;
@@ -293,6 +294,23 @@ __global__ void k_eval_vars(Dev d, int use_trial) {
     d.igU[v] = isfinite(hi) ? 1.0 / (hi - y) : 0.0;
     d.izL[v] = isfinite(lo) ? 1.0 / d.zL[v] : 0.0;
     d.izU[v] = isfinite(hi) ? 1.0 / d.zU[v] : 0.0;
+  }
+}
+
+__global__ void k_eval_vars(Dev d, int use_trial) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < d.n) eval_var_at(d, v, use_trial);
+}
+
+// rows (blocks 0 .. nbr-1) and variables (the rest) in one launch; the two
+// are independent (the Hessian terms read the multipliers, not the rows' values)
+__global__ void k_eval(Dev d, int use_trial, int with_jac, int nbr) {
+  if ((int)blockIdx.x < nbr) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < d.m) eval_row_at(d, r, use_trial, with_jac);
+  } else {
+    const int v = (blockIdx.x - nbr) * blockDim.x + threadIdx.x;
+    if (v < d.n) eval_var_at(d, v, use_trial);
   }
 }
 

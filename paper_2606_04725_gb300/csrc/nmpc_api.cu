@@ -86,6 +86,7 @@ struct nmpc_handle {
   cudaGraphExec_t gexec = nullptr;
   bool graph_off = false;  // host-driven loop only (allocation-free one-shot solve)
   long long nodes_eval = 0, nodes_factor = 0, nodes_solve = 0, nodes_trial = 0, nodes_update = 0;
+  CondArgs cond{};  // passed to the step-ending kernels; on only while the graph is captured
 };
 
 namespace {
@@ -155,6 +156,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   h->d_stage = cv.take<double>((size_t)ni * (A.mc.nx + A.sp_stride + 1));
   h->d_ctl_save = cv.take<Ctl>(ni);
   d.trace = cv.take<double>((size_t)ni * (h->opt.max_iter + 2) * 8);
+  d.red_cnt = cv.take<int>(ni + 1);
   s.sn_first = cv.take<int>(ns); s.sn_ncol = cv.take<int>(ns); s.sn_nrow = cv.take<int>(ns);
   s.sn_Lptr = cv.take<long long>(ns + 1); s.sn_Uptr = cv.take<long long>(ns + 1);
   s.sn_rowptr = cv.take<long long>(ns + 1); s.sn_rows = cv.take<int>(A.sn_rows.size());
@@ -341,12 +343,10 @@ nmpc_status launch_solve(nmpc_handle* h) {
 long long seq_eval(nmpc_handle* h) {
   Dev& d = h->d;
   cudaStream_t st = h->stream;
-  const int ni = h->A.n_inst;
-  k_eval_rows<<<blocks_for(d.m, EW), EW, 0, st>>>(d, 0, 1);
-  k_eval_vars<<<blocks_for(d.n, EW), EW, 0, st>>>(d, 0);
-  k_red_eval<<<d.n_chunks, RED_CHUNK, 0, st>>>(d);
-  k_ctl_pre<<<blocks_for(32LL * ni), TPB, 0, st>>>(d, h->opt.max_iter);
-  return 4;
+  const int nbr = (int)blocks_for(d.m, EW);
+  k_eval<<<nbr + blocks_for(d.n, EW), EW, 0, st>>>(d, 0, 1, nbr);
+  k_red_eval<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->opt.max_iter, h->cond);
+  return 2;
 }
 
 long long seq_factor(nmpc_handle* h) {
@@ -359,7 +359,7 @@ long long seq_factor(nmpc_handle* h) {
   k_rows_pre<<<blocks_for(d.m, EW), EW, 0, st>>>(d, h->d_Drow);
   k_assemble<<<blocks_for(d.n_tgt, EW), EW, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
   launch_factor(h);
-  k_ctl_factor<<<blocks_for(ni), TPB, 0, st>>>(d);
+  k_ctl_factor<<<1, TPB, 0, st>>>(d, h->cond);
   const long long levels = h->launches - l0;
   h->launches = l0;
   return 4 + levels;
@@ -368,39 +368,33 @@ long long seq_factor(nmpc_handle* h) {
 long long seq_solve(nmpc_handle* h) {
   Dev& d = h->d;
   cudaStream_t st = h->stream;
-  const int ni = h->A.n_inst;
   const long long l0 = h->launches;
   k_rhs<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
   launch_solve(h);
-  k_recover_vars<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
-  k_recover_rows<<<blocks_for(d.m, EW), EW, 0, st>>>(d);
-  k_red_dir<<<d.n_chunks, RED_CHUNK, 0, st>>>(d);
-  k_ctl_dir<<<blocks_for(32LL * ni), TPB, 0, st>>>(d);
+  k_recover<<<blocks_for((long long)d.n + d.m, EW), EW, 0, st>>>(d);
+  k_red_dir<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);
   const long long levels = h->launches - l0;
   h->launches = l0;
-  return 5 + levels;
+  return 3 + levels;
 }
 
 long long seq_trial(nmpc_handle* h) {
   Dev& d = h->d;
   cudaStream_t st = h->stream;
-  const int ni = h->A.n_inst;
   k_trial_point<<<blocks_for((long long)d.n + d.m), TPB, 0, st>>>(d);
-  k_eval_rows<<<blocks_for(d.m, EW), EW, 0, st>>>(d, 1, 0);
-  k_eval_vars<<<blocks_for(d.n, EW), EW, 0, st>>>(d, 1);
-  k_red_trial<<<d.n_chunks, RED_CHUNK, 0, st>>>(d);
-  k_ctl_ls<<<blocks_for(32LL * ni), TPB, 0, st>>>(d);
-  return 5;
+  const int nbr = (int)blocks_for(d.m, EW);
+  k_eval<<<nbr + blocks_for(d.n, EW), EW, 0, st>>>(d, 1, 0, nbr);
+  k_red_trial<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);
+  return 3;
 }
 
 long long seq_update(nmpc_handle* h) {
   Dev& d = h->d;
   cudaStream_t st = h->stream;
   const int ni = h->A.n_inst;
-  k_update_vars<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
-  k_update_rows<<<blocks_for(d.m, EW), EW, 0, st>>>(d);
+  k_update<<<blocks_for((long long)d.n + d.m, EW), EW, 0, st>>>(d);
   k_ctl_post<<<blocks_for(ni), TPB, 0, st>>>(d);
-  return 3;
+  return 2;
 }
 
 // Add a conditional node at the current point of a stream capture; the
@@ -427,10 +421,10 @@ cudaError_t capture_conditional(cudaStream_t cs, cudaGraphConditionalHandle hc, 
 
 // The interior-point loop (after the initialization kernels) as one graph:
 //   WHILE any instance runs:
-//     evaluate, errors, barrier update (k_ctl_pre)
+//     evaluate, errors, barrier update (k_red_eval: reduction, then control)
 //     IF any instance runs:
 //       WHILE any instance needs a factorization: assemble, factor, inertia test
-//       right-hand side, solves, step recovery, step limits (k_ctl_dir)
+//       right-hand side, solves, step recovery, step limits (k_red_dir)
 //       WHILE any line search is active: trial point, evaluate, filter test
 //       accept the step
 // The conditions are set on the device, so a solve needs no host round trip.
@@ -443,13 +437,13 @@ nmpc_status build_graph(nmpc_handle* h) {
   const char* step = "create";
   cudaError_t e = cudaGraphCreate(&g, 0);
   int* ctr = h->d_flags + 8;
-  Dev& d = h->d;
   // trip limits: outer steps, and factorization attempts / line-search trials
   // (64 per step: far above what the inertia correction and the backtracking
   // can take before they stop by themselves)
   const int cap_iter = h->opt.max_iter + 2, cap_inner = 64 * cap_iter;
   cudaGraphConditionalHandle h_run = 0, h_if = 0, h_fac = 0, h_ls = 0;  // one per conditional node
   cudaGraph_t body_iter = nullptr, body_run = nullptr, body_fac = nullptr, body_ls = nullptr;
+  // the step-ending kernels set the conditions (restored to off below)
   if (e == cudaSuccess) { step = "handles"; e = cudaGraphConditionalHandleCreate(&h_run, g, 1, cudaGraphCondAssignDefault); }
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_if, g, 0, 0);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_fac, g, 0, 0);
@@ -465,12 +459,12 @@ nmpc_status build_graph(nmpc_handle* h) {
     e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
     if (e == cudaSuccess) body_iter = p.conditional.phGraph_out[0];
   }
-  // iteration body: evaluation, then IF running
+  h->cond = CondArgs{h_run, h_if, h_fac, h_ls, ctr, cap_iter, cap_inner, 1};
+  // iteration body: evaluation (k_red_eval sets the conditions), then IF running
   if (e == cudaSuccess) step = "capture iteration body";
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body_iter, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    h->nodes_eval = seq_eval(h) + 1;
-    k_cond_pre<<<1, 256, 0, cs>>>(d, h_run, h_if, h_fac, ctr, cap_iter);
+    h->nodes_eval = seq_eval(h);
     step = "IF node";
     e = capture_conditional(cs, h_if, cudaGraphCondTypeIf, &body_run);
     cudaGraph_t out = nullptr;
@@ -484,8 +478,7 @@ nmpc_status build_graph(nmpc_handle* h) {
     step = "factor WHILE node";
     e = capture_conditional(cs, h_fac, cudaGraphCondTypeWhile, &body_fac);
     if (e == cudaSuccess) {
-      h->nodes_solve = seq_solve(h) + 1;
-      k_cond_ls<<<1, 256, 0, cs>>>(d, h_ls, ctr, 0, cap_inner);
+      h->nodes_solve = seq_solve(h);
       step = "line-search WHILE node";
       e = capture_conditional(cs, h_ls, cudaGraphCondTypeWhile, &body_ls);
     }
@@ -497,19 +490,18 @@ nmpc_status build_graph(nmpc_handle* h) {
   if (e == cudaSuccess) step = "capture factor body";
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body_fac, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    h->nodes_factor = seq_factor(h) + 1;
-    k_cond_fac<<<1, 256, 0, cs>>>(d, h_fac, ctr, cap_inner);
+    h->nodes_factor = seq_factor(h);
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(cs, &out);
   }
   if (e == cudaSuccess) step = "capture line-search body";
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body_ls, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    h->nodes_trial = seq_trial(h) + 1;
-    k_cond_ls<<<1, 256, 0, cs>>>(d, h_ls, ctr, 1, cap_inner);
+    h->nodes_trial = seq_trial(h);
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(cs, &out);
   }
+  h->cond = CondArgs{};
   cudaGraphExec_t ex = nullptr;
   if (e == cudaSuccess) step = "instantiate";
   if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);

@@ -134,6 +134,17 @@ struct Dev {
   const int* sn_inst;
   int max_iter;
   double* trace;        // per instance: (max_iter + 2) x 8 doubles
+  int* red_cnt;         // n_inst + 1 arrival counters of the fused reduction kernels (zero between launches)
+};
+
+// Conditions of the graph-driven loop, set by the kernels that end each step
+// (handles are cudaGraphConditionalHandle values; on = 0 in the host-driven
+// loop, which reads the control state itself).  counters: [0] outer steps,
+// [1] factorization attempts, [2] line-search trials; cap_*: trip limits.
+struct CondArgs {
+  unsigned long long h_run, h_if, h_fac, h_ls;
+  int* counters;
+  int cap_iter, cap_inner, on;
 };
 
 // One record per supernode, stored in level order, with everything a factor
