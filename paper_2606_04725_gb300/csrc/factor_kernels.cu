@@ -698,11 +698,14 @@ __device__ __forceinline__ double group_sum(double v, int g) {
   return v;
 }
 
-// Forward solve of one front (all threads of the block).  Values written by
-// other blocks of the same launch (children's update vectors) are read
+// Forward solve of one front (all threads of the block).  The panel copy and
+// the front's own right-hand side are started first; wait() (every thread
+// calls it; it ends with a block barrier) then waits for the children, whose
+// update vectors, written by other blocks of the same launch, are read
 // through L2 (__ldcg).
+template <class Wait>
 __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int smem_cap, unsigned long long* bar,
-                          int* s_to) {
+                          int* s_to, Wait wait) {
   const int m = fd.m, c = fd.c, first = fd.first;
   const double* Lg = s.L + fd.Lptr;
   const long long lsz = ((long long)m * c + 1) & ~1LL;
@@ -718,9 +721,11 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
     mbar_init(bar);
     bulk_load(dsm, Lg, (unsigned)(lsz * 8), bar);
   }
+  for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
+  wait();
   // The first ST entries of each of the first DESC_CH children's update
-  // vectors are loaded together with the right-hand side (one round of L2
-  // latency); the additions then go child by child, in ascending order.
+  // vectors are loaded in one round (one L2 latency); the additions then go
+  // child by child, in ascending order.
   double cv[DESC_CH];
   int cr[DESC_CH];
 #pragma unroll
@@ -732,8 +737,6 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
       cv[q] = __ldcg(s.uv + fd.ch_uvptr[q] + tid);
     }
   }
-  for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
-  __syncthreads();
 #pragma unroll
   for (int q = 0; q < DESC_CH; ++q) {
     if (q < fd.nchild) {  // uniform over the block
@@ -782,10 +785,13 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   for (int j = tid; j < c; j += nt) d.b[first + j] = ys[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
 }
 
-// Backward solve of one front; ancestors' solution values (written by other
-// blocks of the same launch) are read through L2.
+// Backward solve of one front.  The panel copy and z are started first;
+// wait() (as in fwd_front) then waits for the parent, after which the
+// ancestors' solution values (written by other blocks of the same launch)
+// are read through L2.
+template <class Wait>
 __device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int smem_cap, unsigned long long* bar,
-                          int* s_to) {
+                          int* s_to, Wait wait) {
   const int m = fd.m, c = fd.c, first = fd.first;
   const double* Lg = s.L + fd.Lptr;
   const int* rows_idx = s.sn_rows + fd.rowptr;
@@ -802,11 +808,9 @@ __device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
     mbar_init(bar);
     bulk_load(dsm, Lg, (unsigned)(lsz * 8), bar);
   }
-  for (int i = tid; i < m; i += nt) {
-    if (i < c) zs[i] = d.b[first + i];
-    else xv[i] = __ldcg(d.b + rows_idx[i]);
-  }
-  __syncthreads();  // the barrier is initialized before any thread waits on it
+  for (int i = tid; i < c; i += nt) zs[i] = d.b[first + i];
+  wait();  // (also orders the barrier's initialization before any thread waits on it)
+  for (int i = c + tid; i < m; i += nt) xv[i] = __ldcg(d.b + rows_idx[i]);
   if (stage && !mbar_wait(bar, s.spin_limit)) *s_to = 1;
   __syncthreads();
   if (stage && tid == 0) mbar_inval(bar);
@@ -918,7 +922,7 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDes
   if (threadIdx.x == 0) s_to = 0;
   __syncthreads();
   if (d.ctl[fd.inst].status != ST_RUNNING) return;
-  fwd_front(d, s, fd, smem_cap, &bar, &s_to);
+  fwd_front(d, s, fd, smem_cap, &bar, &s_to, [] { __syncthreads(); });
   if (threadIdx.x == 0 && s_to) atomicExch(s.timeout, 1);
 }
 
@@ -930,7 +934,7 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDes
   if (threadIdx.x == 0) s_to = 0;
   __syncthreads();
   if (d.ctl[fd.inst].status != ST_RUNNING) return;
-  bwd_front(d, s, fd, smem_cap, &bar, &s_to);
+  bwd_front(d, s, fd, smem_cap, &bar, &s_to, [] { __syncthreads(); });
   if (threadIdx.x == 0 && s_to) atomicExch(s.timeout, 1);
 }
 
@@ -939,8 +943,10 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDes
 // depends on (forward: its children; backward: its parent, which waited for
 // its own parent), solves it and publishes it with a release flag.  A front
 // is waited on only after a running block has claimed it, so the launch
-// needs no co-residency.  flags[0] is the claim counter and flags[1 + q]
-// front q's completion (both zeroed before the launch).
+// needs no co-residency.  flags[0] is the claim counter, flags[1 + q] front
+// q's completion and flags[nf + 1] counts the blocks that have left; the last
+// block to leave zeroes all of them for the next launch (they start zeroed
+// with the workspace).
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -976,28 +982,37 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
     const int q = FWD ? k : nf - 1 - k;  // backward: parents first
     load_desc(&fd, dl + q);
     __syncthreads();
-    if (tid == 0) {
-      if (FWD) {
-        for (int c = 0; c < fd.nchild; ++c) {
-          const int cp = (c < DESC_CH) ? fd.ch_pos[c] : s.pos_of_sn[s.sn_child[s.sn_child_ptr[fd.J] + c]];
-          if (cp >= 0 && cp < nf) wait_done(flags + 1 + cp, s.spin_limit, &s_to);
+    if (d.ctl[fd.inst].status == ST_RUNNING) {  // uniform over the block
+      // started before the wait: the panel copy and the front's own values
+      auto wait = [&] {
+        if (tid == 0) {
+          if (FWD) {
+            for (int c = 0; c < fd.nchild; ++c) {
+              const int cp = (c < DESC_CH) ? fd.ch_pos[c] : s.pos_of_sn[s.sn_child[s.sn_child_ptr[fd.J] + c]];
+              if (cp >= 0 && cp < nf) wait_done(flags + 1 + cp, s.spin_limit, &s_to);
+            }
+          } else if (fd.par_pos >= 0 && fd.par_pos < nf) {
+            wait_done(flags + 1 + fd.par_pos, s.spin_limit, &s_to);
+          }
         }
-      } else if (fd.par_pos >= 0 && fd.par_pos < nf) {
-        wait_done(flags + 1 + fd.par_pos, s.spin_limit, &s_to);
-      }
+        __syncthreads();
+      };
+      if (FWD) fwd_front(d, s, fd, smem_cap, &bar, &s_to, wait);
+      else bwd_front(d, s, fd, smem_cap, &bar, &s_to, wait);
     }
+    // Every thread's stores are ordered before thread 0's release store by
+    // the block barrier (release is cumulative), and a waiting block reads
+    // them after its acquire load and its own barrier.
     __syncthreads();
-    if (d.ctl[fd.inst].status == ST_RUNNING) {
-      if (FWD) fwd_front(d, s, fd, smem_cap, &bar, &s_to);
-      else bwd_front(d, s, fd, smem_cap, &bar, &s_to);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      st_release_gpu(flags + 1 + q, 1);
-    }
+    if (tid == 0) st_release_gpu(flags + 1 + q, 1);
   }
   if (tid == 0 && s_to) atomicExch(s.timeout, 1);
+  // no block touches the flags after it has arrived here
+  __shared__ int s_last;
+  if (tid == 0) s_last = atomicAdd(flags + nf + 1, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (s_last)
+    for (int i = tid; i < nf + 2; i += blockDim.x) flags[i] = 0;
 }
 
 __global__ void __launch_bounds__(ST) k_fwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,

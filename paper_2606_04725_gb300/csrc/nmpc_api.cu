@@ -166,7 +166,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.sn_uvptr = cv.take<long long>(ns + 1);
   s.desc = cv.take<FrontDesc>(ns);
   s.pos_of_sn = cv.take<int>(ns);
-  h->d_solve_flags = cv.take<int>(ns + 1);
+  h->d_solve_flags = cv.take<int>(2 * (ns + 2));  // forward and backward persistent solves
   s.amap = cv.take<IdxPair>(h->amap.size() / 2);
   s.amap_ptr = cv.take<long long>(h->amap_ptr.size());
   s.U = cv.take<double>(A.nU);
@@ -300,11 +300,11 @@ int big_solve_smem(const nmpc_handle* h, int l) {
 nmpc_status launch_solve(nmpc_handle* h) {
   const int nl = (int)h->lvl_ptr.size() - 1;
   const int L = h->opt.solve_mode == 1 ? 0 : h->solve_prefix;  // levels covered by one persistent launch
-  const size_t fbytes = (size_t)(h->solve_prefix_fronts + 1) * sizeof(int);
+  int* fwd_flags = h->d_solve_flags;                              // zero between launches
+  int* bwd_flags = h->d_solve_flags + h->solve_prefix_fronts + 2;
   if (L > 0) {
-    CUDA_TRY(h, cudaMemsetAsync(h->d_solve_flags, 0, fbytes, h->stream));
     k_fwd_persist<<<h->persist_blocks_fwd, 128, h->persist_smem_fwd, h->stream>>>(
-        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, h->d_solve_flags);
+        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, fwd_flags);
     ++h->launches;
   }
   for (int l = L; l < nl; ++l) {
@@ -330,9 +330,8 @@ nmpc_status launch_solve(nmpc_handle* h) {
     ++h->launches;
   }
   if (L > 0) {
-    CUDA_TRY(h, cudaMemsetAsync(h->d_solve_flags, 0, fbytes, h->stream));
     k_bwd_persist<<<h->persist_blocks_bwd, 128, h->persist_smem_bwd, h->stream>>>(
-        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, h->d_solve_flags);
+        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, bwd_flags);
     ++h->launches;
   }
   return NMPC_OK;
