@@ -101,6 +101,14 @@ typedef struct {
                             path elsewhere (default); 1: one CTA per front; 2: blocked path everywhere */
   int solve_mode;        /* 0: persistent dataflow solves over the levels of small fronts (default);
                             1: one launch per level */
+  int panel_scale;       /* triangular solves of the fronts solved one block per front:
+                            0: automatic (default): form 1 below when the solves are latency-bound
+                               (at most 4 fronts per SM in every level), else form 3;
+                            1: after each factorization the 16x16 unit diagonal blocks of L are
+                               inverted in place and the rows below each block are multiplied by
+                               its inverse: one dense product per block and solve;
+                            2: the diagonal blocks only: two products per block;
+                            3: no transform: column-by-column substitution */
 } nmpc_options;
 
 /* Per-instance result of a solve.  Times are measured with CUDA events on

@@ -44,7 +44,8 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("gamma", C.c_double), ("mu0_cold", C.c_double), ("mu0_warm", C.c_double),
                 ("push_cold", C.c_double), ("push_warm", C.c_double), ("max_iter", C.c_int),
                 ("ordering", C.c_int), ("nd_leaf", C.c_int), ("use_graph", C.c_int), ("spin_limit", C.c_longlong),
-                ("pivtol", C.c_double), ("factor_mode", C.c_int), ("solve_mode", C.c_int)]
+                ("pivtol", C.c_double), ("factor_mode", C.c_int), ("solve_mode", C.c_int),
+                ("panel_scale", C.c_int)]
 
 
 class Info(C.Structure):

@@ -698,6 +698,96 @@ __device__ __forceinline__ double group_sum(double v, int g) {
   return v;
 }
 
+// count dot products over the block, out_o = sum_{k < len} a(o, k) x(k), with
+// dot_group threads per output; emit(o, out_o) runs on one thread per output.
+// Threads past the last output compute with o clamped (every address a(o, k)
+// reads stays in range) and emit nothing.  Every thread of the block calls.
+template <class A, class X, class E>
+__device__ __forceinline__ void block_dots(int count, int len, A a, X x, E emit) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int g = dot_group(count, len, nt);
+  for (int o0 = 0; o0 < count; o0 += nt / g) {
+    const int o = o0 + tid / g, part = tid & (g - 1);
+    const int oc = min(o, count - 1);
+    double acc = dot_part(part, len, g, [&](int k) { return a(oc, k); }, x);
+    acc = group_sum(acc, g);
+    if (part == 0 && o < count) emit(o, acc);
+  }
+}
+
+// Column substitution on the untransformed panel (SnDev::solve_form 0, for
+// throughput-bound solves: the least FP64 work, no transform).  The c x c
+// unit triangle is a pipeline over the four warps: warp w holds rows
+// 32w .. 32w+31 of the vector in registers and applies the columns in order;
+// the warp that owns column j takes y_j from its own lane by a shuffle and
+// stores it into its sentinel slot (slots[j]), from which the other warps
+// take it.  Beyond 128 columns, or with the panel in global memory, one warp
+// substitutes column by column.  The slots hold SENTINEL on entry.
+__device__ void subst_lower(double* v, double* slots, const double* Ls, int m, int c, bool stage, const SnDev& s,
+                            int* s_to) {
+  const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
+  if (stage && c <= ST) {
+    if (32 * wp < c) {
+      const int r = 32 * wp + lane;
+      double x = (r < c) ? v[r] : 0.0;
+      const int jmax = min(c, 32 * wp + 32);
+      for (int j = 0; j < jmax; ++j) {
+        const double lv = (r > j && r < c) ? Ls[r + (size_t)j * m] : 0.0;
+        double yj;
+        if (j < 32 * wp) {
+          yj = take(slots + j, s.spin_limit, s_to);
+        } else {
+          yj = __shfl_sync(FULL, x, j & 31);
+          if (lane == (j & 31)) *(volatile double*)(slots + j) = yj;
+        }
+        x = fma(-lv, yj, x);
+      }
+      if (r < c) v[r] = x;
+    }
+  } else if (tid < 32) {
+    for (int j = 0; j < c; ++j) {
+      const double yj = v[j];
+      __syncwarp();
+      for (int i = j + 1 + lane; i < c; i += 32) v[i] = fma(-Ls[i + (size_t)j * m], yj, v[i]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// L_cc^T x = t in place, the last column first (same scheme as subst_lower)
+__device__ void subst_upper(double* v, double* slots, const double* Ls, int m, int c, bool stage, const SnDev& s,
+                            int* s_to) {
+  const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31;
+  if (stage && c <= ST) {
+    if (32 * wp < c) {
+      const int i = 32 * wp + lane;
+      double x = (i < c) ? v[i] : 0.0;
+      const int top = min(c, 32 * wp + 32) - 1;  // highest row of this warp
+      for (int j = c - 1; j >= 32 * wp; --j) {
+        const double lv = (i < j) ? Ls[j + (size_t)i * m] : 0.0;  // L(j, i)
+        double xj;
+        if (j > top) {
+          xj = take(slots + j, s.spin_limit, s_to);
+        } else {
+          xj = __shfl_sync(FULL, x, j & 31);
+          if (lane == (j & 31)) *(volatile double*)(slots + j) = xj;
+        }
+        x = fma(-lv, xj, x);
+      }
+      if (i < c) v[i] = x;
+    }
+  } else if (tid < 32) {
+    for (int j = c - 1; j >= 0; --j) {
+      const double xj = v[j];
+      __syncwarp();
+      for (int i = lane; i < j; i += 32) v[i] = fma(-Ls[j + (size_t)i * m], xj, v[i]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 // Forward solve of one front (all threads of the block).  The panel copy and
 // the front's own right-hand side are started first; wait() (every thread
 // calls it; it ends with a block barrier) then waits for the children, whose
@@ -722,6 +812,8 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
     bulk_load(dsm, Lg, (unsigned)(lsz * 8), bar);
   }
   for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
+  if (s.solve_form == 0)
+    for (int j = tid; j < c; j += nt) ys[j] = __longlong_as_double(SENTINEL);
   wait();
   // The first ST entries of each of the first DESC_CH children's update
   // vectors are loaded in one round (one L2 latency); the additions then go
@@ -754,33 +846,42 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   if (stage && !mbar_wait(bar, s.spin_limit)) *s_to = 1;
   __syncthreads();
   if (stage && tid == 0) mbar_inval(bar);
+  double* uvJ = s.uv + fd.uvptr;  // u_i = f_i - sum_j L_ij y_j (rows c..m-1)
+  if (s.solve_form == 0) {
+    subst_lower(fv, ys, Ls, m, c, stage, s, s_to);  // y in place of f_0..c-1
+    block_dots(
+        m - c, c, [&](int r, int j) { return Ls[(c + r) + (size_t)j * m]; }, [&](int j) { return fv[j]; },
+        [&](int r, double a) { uvJ[r] = fv[c + r] - a; });
+    for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
+    return;
+  }
   for (int s0 = 0; s0 < c; s0 += IB) {
-    const int bk = min(IB, c - s0), cnt = m - s0;
-    const double* P = Ls + s0 + (size_t)s0 * m;  // rows s0.. of the block's columns: X_K, then M_K
+    const int bk = min(IB, c - s0), e = s0 + bk;
+    const double* P = Ls + s0 + (size_t)s0 * m;  // rows s0.. of the block's columns: X_K, then M_K or L
     const double* v = fv + s0;
-    // output r < bk: y_{s0+r} = sum_j X_rj v_j (X_rr = 1, X_rj = 0 for j > r);
-    // r >= bk: v_{s0+r} -= sum_j M_rj v_j.  Every P(r, j) read is inside the panel.
-    const int g = dot_group(cnt, bk, nt);
-    for (int o0 = 0; o0 < cnt; o0 += nt / g) {
-      const int r = o0 + tid / g, part = tid & (g - 1);
-      const int rr = min(r, cnt - 1);
-      const double* Pr = P + rr;
-      double acc = dot_part(
-          part, bk, g,
-          [&](int j) {
-            const double p = Pr[(size_t)j * m];
-            return j < rr ? p : (j == rr ? 1.0 : 0.0);
-          },
-          [&](int j) { return v[j]; });
-      acc = group_sum(acc, g);
-      if (part == 0 && r < cnt) {
-        if (r < bk) ys[s0 + r] = acc;
-        else fv[s0 + r] -= acc;
+    // P(r, j) with the unit diagonal of X_K and its zeros above the diagonal
+    auto xk = [&](int r, int j) {
+      const double p = P[r + (size_t)j * m];
+      return j < r ? p : (j == r ? 1.0 : 0.0);
+    };
+    if (s.solve_form == 2) {
+      // output r < bk: y_{s0+r} = sum_j X_rj v_j; r >= bk: v_{s0+r} -= sum_j M_rj v_j
+      block_dots(m - s0, bk, xk, [&](int j) { return v[j]; }, [&](int r, double a) {
+        if (r < bk) ys[s0 + r] = a;
+        else fv[s0 + r] -= a;
+      });
+      __syncthreads();
+    } else {
+      block_dots(bk, bk, xk, [&](int j) { return v[j]; }, [&](int r, double a) { ys[s0 + r] = a; });
+      __syncthreads();
+      if (e < m) {  // v_r -= L_rK y_K for r >= e
+        block_dots(
+            m - e, bk, [&](int r, int j) { return P[(bk + r) + (size_t)j * m]; }, [&](int j) { return ys[s0 + j]; },
+            [&](int r, double a) { fv[e + r] -= a; });
+        __syncthreads();
       }
     }
-    __syncthreads();
   }
-  double* uvJ = s.uv + fd.uvptr;  // u_i = f_i - sum_j L_ij y_j (rows c..m-1)
   for (int r = c + tid; r < m; r += nt) uvJ[r - c] = fv[r];
   for (int j = tid; j < c; j += nt) d.b[first + j] = ys[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
 }
@@ -814,27 +915,57 @@ __device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   if (stage && !mbar_wait(bar, s.spin_limit)) *s_to = 1;
   __syncthreads();
   if (stage && tid == 0) mbar_inval(bar);
-  for (int s0 = (c - 1) / IB * IB; s0 >= 0; s0 -= IB) {
-    const int bk = min(IB, c - s0), len = m - s0;
-    const double* P = Ls + s0 + (size_t)s0 * m;
-    // x_{s0+j} = sum_{j <= i < bk} X_ij z_{s0+i} - sum_{bk <= i < len} M_ij x_{s0+i}
-    // (column j of P, contiguous); one group of g threads per output j
-    const int g = dot_group(bk, len, nt);
-    const int j = min(tid / g, bk - 1), part = tid & (g - 1);
-    const double* Pj = P + (size_t)j * m;
-    const double* z = zs + s0;
-    const double* x = xv + s0;
-    const double az = dot_part(
-        part, bk, g,
-        [&](int i) {
-          const double p = Pj[i];
-          return i > j ? p : (i == j ? 1.0 : 0.0);
-        },
-        [&](int i) { return z[i]; });
-    const double ax = dot_part(bk + part, len, g, [&](int i) { return Pj[i]; }, [&](int i) { return x[i]; });
-    const double acc = group_sum(az - ax, g);
-    if (part == 0 && tid / g < bk) xv[s0 + j] = acc;
+  if (s.solve_form == 0) {
+    // t_j = z_j - sum_{i >= c} L_ij x_i, then L_cc^T x = t (z's slots become the sentinel slots)
+    block_dots(
+        c, m - c, [&](int j, int i) { return Ls[(c + i) + (size_t)j * m]; }, [&](int i) { return xv[c + i]; },
+        [&](int j, double a) { xv[j] = zs[j] - a; });
     __syncthreads();
+    for (int j = tid; j < c; j += nt) zs[j] = __longlong_as_double(SENTINEL);
+    __syncthreads();
+    subst_upper(xv, zs, Ls, m, c, stage, s, s_to);
+    for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
+    return;
+  }
+  for (int s0 = (c - 1) / IB * IB; s0 >= 0; s0 -= IB) {
+    const int bk = min(IB, c - s0), e = s0 + bk, len = m - s0;
+    const double* P = Ls + s0 + (size_t)s0 * m;
+    if (s.solve_form == 2) {
+      // x_{s0+j} = sum_{j <= i < bk} X_ij z_{s0+i} - sum_{bk <= i < len} M_ij x_{s0+i}
+      // (column j of P, contiguous); one group of g threads per output j
+      const int g = dot_group(bk, len, nt);
+      const int j = min(tid / g, bk - 1), part = tid & (g - 1);
+      const double* Pj = P + (size_t)j * m;
+      const double* z = zs + s0;
+      const double* x = xv + s0;
+      const double az = dot_part(
+          part, bk, g,
+          [&](int i) {
+            const double p = Pj[i];
+            return i > j ? p : (i == j ? 1.0 : 0.0);
+          },
+          [&](int i) { return z[i]; });
+      const double ax = dot_part(bk + part, len, g, [&](int i) { return Pj[i]; }, [&](int i) { return x[i]; });
+      const double acc = group_sum(az - ax, g);
+      if (part == 0 && tid / g < bk) xv[s0 + j] = acc;
+      __syncthreads();
+    } else {
+      if (e < m) {  // t_K = z_K - L_{e..,K}^T x_{e..}, in place of z_K
+        block_dots(
+            bk, m - e, [&](int j, int i) { return P[(bk + i) + (size_t)j * m]; }, [&](int i) { return xv[e + i]; },
+            [&](int j, double a) { zs[s0 + j] -= a; });
+        __syncthreads();
+      }
+      // x_K = X_K^T t_K
+      block_dots(
+          bk, bk,
+          [&](int j, int i) {
+            const double p = P[i + (size_t)j * m];
+            return i > j ? p : (i == j ? 1.0 : 0.0);
+          },
+          [&](int i) { return zs[s0 + i]; }, [&](int j, double a) { xv[s0 + j] = a; });
+      __syncthreads();
+    }
   }
   for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
 }

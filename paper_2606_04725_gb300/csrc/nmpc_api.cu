@@ -70,6 +70,7 @@ struct nmpc_handle {
   std::vector<InvItem> inv_items;                    // blocks transformed after each factorization
   std::vector<ScaleUnit> scale_units;                // 32-row slices below them
   std::vector<int> lvl_inv_ptr, lvl_scale_ptr;       // their ranges per level
+  int s_form = 2;                                    // SnDev::solve_form
   int n_sm = 152;
   int cluster_ctas_per_sm = 1;  // CTAs of the cluster kernel per SM aimed at when choosing Q (2 measured no faster)
   int smem_cap_doubles = 0;
@@ -178,6 +179,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.n_inv = (int)h->inv_items.size();
   s.scale = cv.take<ScaleUnit>(h->scale_units.size());
   s.n_scale = (int)h->scale_units.size();
+  s.solve_form = h->s_form;
   s.L = d.Lval;
   s.Kdiag = d.Kdiag;
   s.pivtol = A.mc.pivtol;
@@ -629,10 +631,22 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   h->scale_units.clear();
   h->lvl_inv_ptr.assign(nl + 1, 0);
   h->lvl_scale_ptr.assign(nl + 1, 0);
+  // Solve form (SnDev::solve_form).  When the solves are latency-bound (at most
+  // 4 fronts per SM in every level) the panels are transformed (form 2): the
+  // transform takes about eight solves' worth of FP64 work per factorization,
+  // hidden under the upper levels' factorization, and cuts the per-front
+  // critical path 2-3x.  When they are throughput-bound (wide batches) the
+  // plain substitution does the least work (form 0).
+  int widest = 0;
+  for (int l = 0; l < nl; ++l) widest = std::max(widest, A.level_ptr[l + 1] - A.level_ptr[l]);
+  const int form = h->opt.panel_scale == 1 ? 2 : h->opt.panel_scale == 2 ? 1 : h->opt.panel_scale == 3 ? 0
+                   : (widest <= 4 * h->n_sm ? 2 : 0);
+  h->s_form = form;
+  const bool scaled = form == 2;
   for (int l = 0; l < nl; ++l) {
     h->lvl_inv_ptr[l] = (int)h->inv_items.size();
     h->lvl_scale_ptr[l] = (int)h->scale_units.size();
-    if (h->lvl_bigsolve[l]) continue;
+    if (h->lvl_bigsolve[l] || form == 0) continue;
     for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd) {
       const int J = A.level_sn[qd];
       const int mm = A.sn_nrow[J], cc = A.sn_ncol[J];
@@ -640,7 +654,8 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
         const int bk = std::min(IB, cc - s0);
         if (bk < 2) continue;
         const int rows = mm - s0 - bk;
-        for (int r0 = 0; r0 < rows; r0 += 32) h->scale_units.push_back({(int)h->inv_items.size(), r0});
+        if (scaled)
+          for (int r0 = 0; r0 < rows; r0 += 32) h->scale_units.push_back({(int)h->inv_items.size(), r0});
         h->inv_items.push_back({A.sn_Lptr[J] + s0 + (long long)s0 * mm, mm, bk, A.sn_inst[J], rows});
       }
     }

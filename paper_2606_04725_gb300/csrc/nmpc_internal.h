@@ -176,7 +176,9 @@ struct FrontDesc {
 // One InvItem per block with at least two columns: offset of its first entry
 // (s0, s0) in L, leading dimension (m of the front), order bk <= IB,
 // instance and the number m - e of rows below it.  One ScaleUnit per 32 of
-// those rows.
+// those rows when the rows are scaled (SnDev::solve_form 2; with form 1 they
+// keep L and the solves take two products per block; form 0 transforms
+// nothing).
 constexpr int IB = 16;
 struct alignas(8) InvItem {
   long long off;
@@ -214,6 +216,8 @@ struct SnDev {
   const InvItem* inv;         // diagonal blocks transformed after each factorization
   const ScaleUnit* scale;     // 32-row slices of the rows below them
   int n_inv, n_scale;
+  int solve_form;             // solves of small fronts: 0 column substitution on L (no transform);
+                              // 1 X_K on the diagonal blocks; 2 X_K and M_K (one product per block)
   const double* Kdiag;        // assembled diagonal in factor order
   double pivtol;
   long long spin_limit;       // polls of a bounded wait between CTAs

@@ -292,6 +292,34 @@ def test_cluster_and_single_cta_factorizations_agree(P):
     assert np.max(np.abs(ys[0] - ys[1])) < 1e-6
 
 
+@pytest.mark.parametrize("hz", [[200], [30, 45, 60, 20]])
+def test_solve_forms_agree(P, oracle, hz):
+    """The three forms of the small-front solves: the panel transformed with
+    the rows below each 16-column block scaled by the block's inverse (one
+    product per block), the diagonal blocks inverted only (two products per
+    block), and plain column substitution.  Same solution and iteration counts
+    up to rounding, and every point is KKT-optimal by the oracle's evaluator."""
+    x0s = [I.distillation_x0(34, 17, seed=40 + i) for i in range(len(hz))]
+    sps = [0.78 + 0.02 * i for i in range(len(hz))]
+    ys, its = [], []
+    for mode in (1, 2, 3):
+        s = _gpu_solver(P, "distill34", hz, opts=P.options(panel_scale=mode, ordering=2))
+        for i, T in enumerate(hz):
+            s.set_params(instance=i, x0=x0s[i], setpoint=np.full(T, sps[i]), u_prev=np.array([I.U_REF]))
+        infos = s.solve()
+        assert all(inf["status"] == 0 for inf in infos), infos
+        ys.append([s.get_solution(i) for i in range(len(hz))])
+        its.append([inf["iters"] for inf in infos])
+        for i, T in enumerate(hz):
+            prob = oracle.distillation(34, 17, T, x0s[i], np.full(T, sps[i]), I.U_REF)
+            es, _ = oracle.kkt_error(prob, _state_from_gpu(oracle, s, i, prob.n, prob.m))
+            assert es <= TOL_KKT, (mode, i, es)
+    for k in (1, 2):
+        for i in range(len(hz)):
+            assert abs(its[0][i] - its[k][i]) <= 1, its
+            assert np.max(np.abs(ys[0][i] - ys[k][i])) < 1e-6
+
+
 def test_device_parameters_equal_host_parameters_and_runs_are_deterministic(P):
     import torch
     T = 20
