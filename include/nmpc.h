@@ -269,6 +269,50 @@ nmpc_status nmpc_solve_static(const nmpc_problem* prob, const nmpc_options* opts
                               const double* x0, const double* setpoint, const double* u_prev,
                               double* y_out, nmpc_info* info, int on_device);
 
+/* ------------------------------------------------------------------------
+ * Autotuner (the batch path's tuning of the supernodal schedule; not in the
+ * paper).  The symbolic analysis and the kernels' schedule depend on options
+ * the problem does not fix: the ordering (nested dissection with leaves of
+ * 1, 2 or 4 stages; stage order for short horizons) and the solve form
+ * (panel_scale 1 or 3).  nmpc_autotune builds every candidate (reusing
+ * those nmpc_autotune_workspace_bytes just built for the same problem),
+ * binds it to the caller's workspace, runs one cold solve of the given
+ * parameters and, if every instance converged, times one iteration's
+ * evaluation, assembly, factorization and solves at that point (as
+ * nmpc_time_phases); the rest of an iteration is the same for every
+ * candidate.  It keeps the fastest candidate and writes its ordering,
+ * nd_leaf and panel_scale into *opts (the other fields are kept).
+ * Results are cached per problem (model, sizes, horizons, constants) and
+ * remaining options for the life of the process: a repeated call returns
+ * the cached choice without running anything.
+ *   workspace, bytes: device memory of at least the size that
+ *                 nmpc_autotune_workspace_bytes reports (256-byte aligned);
+ *                 its contents are overwritten
+ *   x0, setpoint, u_prev: packed instance after instance, as nmpc_set_params
+ *                 (instance = -1) would take them, except that setpoints of
+ *                 instances with different horizons follow one another (T_i
+ *                 values each); NULL keeps zeros
+ *   report:       may be NULL; candidates in the order tried
+ * Returns NMPC_ERR_WORKSPACE if the workspace is too small for every
+ * candidate, NMPC_ERR_CUDA on a CUDA error, NMPC_MAX_ITER (or the first
+ * failing status) if no candidate converged, else NMPC_OK. */
+#define NMPC_TUNE_MAX 16
+typedef struct {
+  int ordering, nd_leaf, panel_scale;
+  int status;            /* of the cold solve (NMPC_ERR_WORKSPACE: skipped, too large) */
+  int iters;             /* largest over instances */
+  double ms_per_iter;    /* evaluation + assembly + factorization + solves at the converged point */
+} nmpc_tune_candidate;
+typedef struct {
+  int n_candidates, best, cached;
+  nmpc_tune_candidate cand[NMPC_TUNE_MAX];
+} nmpc_tune_report;
+
+nmpc_status nmpc_autotune_workspace_bytes(const nmpc_problem* prob, const nmpc_options* opts, size_t* bytes);
+nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cuda_stream, void* workspace,
+                          size_t bytes, const double* x0, const double* setpoint, const double* u_prev,
+                          int on_device, nmpc_tune_report* report);
+
 /* Release host memory of the handle (the caller frees the workspace).
  * Synchronizes the library stream.  NULL is ignored. */
 void nmpc_destroy(nmpc_handle* h);

@@ -4,5 +4,5 @@ The compute path is the CUDA library libnmpc.so (include/nmpc.h); this
 package only marshals arguments to it.
 """
 from ._lib import (MODEL_DISTILLATION, MODEL_PLATE, MODEL_TOY, ORDER_AUTO, ORDER_NATURAL, ORDER_ND,  # noqa: F401
-                   NmpcError, Solver, Structure, lib, options, unpack_duals)
+                   NmpcError, Solver, Structure, autotune, lib, options, unpack_duals)
 from .build import build  # noqa: F401

@@ -26,6 +26,7 @@ STATUS = {0: "ok", 1: "invalid", 2: "cuda_error", 3: "workspace", 10: "max_iter"
 EXPORTED = ["nmpc_problem_defaults", "nmpc_options_defaults", "nmpc_build", "nmpc_workspace_bytes",
             "nmpc_bind", "nmpc_set_params", "nmpc_solve", "nmpc_get_solution", "nmpc_set_start",
             "nmpc_sensitivity", "nmpc_get_trace", "nmpc_time_phases", "nmpc_get_stats", "nmpc_instance_dims", "nmpc_structure_export",
+            "nmpc_autotune_workspace_bytes", "nmpc_autotune",
             "nmpc_solve_static", "nmpc_destroy", "nmpc_status_string", "nmpc_last_error"]
 
 STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
@@ -66,6 +67,19 @@ class PhaseTimes(C.Structure):
                 ("ms_solve", C.c_double), ("reps", C.c_int)]
 
 
+class TuneCandidate(C.Structure):
+    _fields_ = [("ordering", C.c_int), ("nd_leaf", C.c_int), ("panel_scale", C.c_int), ("status", C.c_int),
+                ("iters", C.c_int), ("ms_per_iter", C.c_double)]
+
+
+TUNE_MAX = 16
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("n_candidates", C.c_int), ("best", C.c_int), ("cached", C.c_int),
+                ("cand", TuneCandidate * TUNE_MAX)]
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 
@@ -103,6 +117,10 @@ def lib():
             L.nmpc_structure_export.restype = C.c_longlong
             L.nmpc_solve_static.argtypes = [C.POINTER(Problem), C.POINTER(Options), _P, _P, _P, _P, _P,
                                             C.POINTER(Info), C.c_int]
+            L.nmpc_autotune_workspace_bytes.argtypes = [C.POINTER(Problem), C.POINTER(Options),
+                                                        C.POINTER(C.c_size_t)]
+            L.nmpc_autotune.argtypes = [C.POINTER(Problem), C.POINTER(Options), _P, _P, C.c_size_t, _P, _P, _P,
+                                        C.c_int, C.POINTER(TuneReport)]
             L.nmpc_destroy.argtypes = [_P]
             L.nmpc_destroy.restype = None
             L.nmpc_status_string.argtypes = [C.c_int]
@@ -117,6 +135,43 @@ class NmpcError(RuntimeError):
     def __init__(self, status, msg=""):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+def autotune(model, horizons, x0=None, setpoint=None, u_prev=None, opts=None, device="cuda", stream=None,
+             **prob_kw):
+    """nmpc_autotune: the options (ordering, nd_leaf, panel_scale) with the
+    least time per interior-point iteration for this problem and these
+    parameters, found by timing one cold solve per candidate in a scratch
+    workspace.  Parameters are packed instance after instance (setpoints of
+    T_i values each for the distillation).  Returns (options, report)."""
+    import torch
+    dev = torch.device(device)
+    p, hz = problem(model, horizons, **prob_kw)
+    p.horizons = hz.ctypes.data_as(C.POINTER(C.c_int))
+    o = Options()
+    C.memmove(C.byref(o), C.byref(opts if opts is not None else options()), C.sizeof(Options))
+    L = lib()
+    b = C.c_size_t()
+    st = L.nmpc_autotune_workspace_bytes(C.byref(p), C.byref(o), C.byref(b))
+    if st != 0:
+        raise NmpcError(st, "nmpc_autotune_workspace_bytes failed")
+    with torch.cuda.device(dev):
+        strm = stream if stream is not None else torch.cuda.current_stream(dev)
+        ws = torch.empty(b.value + 256, dtype=torch.uint8, device=dev)
+        aligned = (ws.data_ptr() + 255) & ~255
+        ptrs = [_ptr(a) for a in (x0, setpoint, u_prev)]
+        flags = {q[1] for q in ptrs if q[0] is not None}
+        if len(flags) > 1:
+            raise ValueError("mix of host and device parameter arrays")
+        on_dev = flags.pop() if flags else 0
+        rep = TuneReport()
+        st = L.nmpc_autotune(C.byref(p), C.byref(o), C.c_void_p(strm.cuda_stream), C.c_void_p(aligned), b.value,
+                             ptrs[0][0], ptrs[1][0], ptrs[2][0], on_dev, C.byref(rep))
+        torch.cuda.synchronize(dev)
+    if st != 0:
+        raise NmpcError(st, "nmpc_autotune found no converging candidate")
+    cands = [{k: getattr(rep.cand[i], k) for k, _ in TuneCandidate._fields_} for i in range(rep.n_candidates)]
+    return o, {"cached": bool(rep.cached), "best": rep.best, "candidates": cands}
 
 
 def problem(model, horizons, **kw):

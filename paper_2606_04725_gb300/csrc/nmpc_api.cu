@@ -691,16 +691,28 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   }
   h->amap.clear();
   h->amap_ptr.clear();
-  for (int l = 0; l < nl; ++l) {
-    const int Q = h->lvl_cluster[l];
-    if (Q <= 0) continue;
-    for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd) {
+  {
+    // per front (on several host threads), then concatenated in level order
+    struct FrontMap {
+      std::vector<int> pairs;        // (source, destination) pairs
+      std::vector<long long> ptr;    // pair offsets of each (CTA, child) range, relative
+    };
+    std::vector<int> fronts;  // level positions of the cluster-factored fronts
+    for (int l = 0; l < nl; ++l)
+      if (h->lvl_cluster[l] > 0)
+        for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd) fronts.push_back(qd);
+    std::vector<int> lvl_of(A.level_sn.size(), 0);
+    for (int l = 0; l < nl; ++l)
+      for (int qd = A.level_ptr[l]; qd < A.level_ptr[l + 1]; ++qd) lvl_of[qd] = l;
+    std::vector<FrontMap> fm(fronts.size());
+    parallel_for((int)fronts.size(), [&](int f) {
+      const int qd = fronts[f], Q = h->lvl_cluster[lvl_of[qd]];
       const int J = A.level_sn[qd];
       const int m = A.sn_nrow[J];
-      h->desc_abase[qd] = (long long)h->amap_ptr.size();
+      FrontMap& M = fm[f];
       for (int q = 0; q < Q; ++q) {
         for (int k = A.sn_child_ptr[J]; k < A.sn_child_ptr[J + 1]; ++k) {
-          h->amap_ptr.push_back((long long)h->amap.size() / 2);
+          M.ptr.push_back((long long)M.pairs.size() / 2);
           const int C = A.sn_child[k];
           const int mc = A.sn_nrow[C] - A.sn_ncol[C];
           const int* rel = A.sn_rel.data() + A.sn_relptr[C];
@@ -709,13 +721,19 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
             if ((rb / CLUSTER_PB) % Q != q) continue;
             const int lc = ((rb / CLUSTER_PB) / Q) * CLUSTER_PB + rb % CLUSTER_PB;
             for (int a = b; a < mc; ++a) {
-              h->amap.push_back(a + b * mc);
-              h->amap.push_back(rel[a] + lc * m);
+              M.pairs.push_back(a + b * mc);
+              M.pairs.push_back(rel[a] + lc * m);
             }
           }
         }
-        h->amap_ptr.push_back((long long)h->amap.size() / 2);
+        M.ptr.push_back((long long)M.pairs.size() / 2);
       }
+    });
+    for (size_t f = 0; f < fronts.size(); ++f) {
+      const long long base = (long long)h->amap.size() / 2;
+      h->desc_abase[fronts[f]] = (long long)h->amap_ptr.size();
+      for (long long o : fm[f].ptr) h->amap_ptr.push_back(base + o);
+      h->amap.insert(h->amap.end(), fm[f].pairs.begin(), fm[f].pairs.end());
     }
   }
   Carver cv;
@@ -1375,3 +1393,194 @@ extern "C" nmpc_status nmpc_solve_static(const nmpc_problem* prob, const nmpc_op
   delete h;
   return st;
 }
+
+// ------------------------------------------------------------------------
+// Autotuner: candidate option sets for the analysis and the schedule, each
+// timed by one cold solve in the caller's workspace; the choice is cached per
+// problem and remaining options.
+// ------------------------------------------------------------------------
+namespace {
+
+std::vector<nmpc_options> tune_candidates(const nmpc_problem* p, const nmpc_options& base) {
+  int Tmax = 0;
+  for (int i = 0; i < p->n_instances; ++i) Tmax = std::max(Tmax, p->horizons[i]);
+  std::vector<nmpc_options> c;
+  for (int form : {1, 3}) {
+    if (Tmax >= 8)
+      for (int leaf : {1, 2, 4}) {
+        nmpc_options o = base;
+        o.ordering = NMPC_ORDER_ND;
+        o.nd_leaf = leaf;
+        o.panel_scale = form;
+        c.push_back(o);
+      }
+    if (Tmax < 32) {  // a chain of at most 31 stages: its depth is no worse than a tree's
+      nmpc_options o = base;
+      o.ordering = NMPC_ORDER_NATURAL;
+      o.nd_leaf = 1;
+      o.panel_scale = form;
+      c.push_back(o);
+    }
+  }
+  return c;
+}
+
+// The problem and every option except the tuned ones, byte for byte.
+std::string tune_key(const nmpc_problem* p, const nmpc_options* o) {
+  nmpc_problem q = *p;
+  q.horizons = nullptr;
+  nmpc_options r = *o;
+  r.ordering = 0;
+  r.nd_leaf = 0;
+  r.panel_scale = 0;
+  std::string k(reinterpret_cast<const char*>(&q), sizeof(q));
+  k.append(reinterpret_cast<const char*>(p->horizons), sizeof(int) * (size_t)p->n_instances);
+  k.append(reinterpret_cast<const char*>(&r), sizeof(r));
+  return k;
+}
+
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, nmpc_options>> g_tune_cache;
+// candidates built (not bound) by nmpc_autotune_workspace_bytes for the last
+// problem it sized, reused by nmpc_autotune
+std::string g_tune_built_key;
+std::vector<nmpc_handle*> g_tune_built;
+
+void tune_drop_built() {  // caller holds g_tune_mu
+  for (nmpc_handle* h : g_tune_built) nmpc_destroy(h);
+  g_tune_built.clear();
+  g_tune_built_key.clear();
+}
+
+// Set the packed parameters instance by instance (horizons may differ).
+nmpc_status tune_set_params(nmpc_handle* h, const nmpc_problem* p, const double* x0, const double* sp,
+                            const double* up, int on_device) {
+  const Analysis& A = h->A;
+  const int nx = A.mc.nx;
+  size_t so = 0;
+  for (int i = 0; i < A.n_inst; ++i) {
+    const size_t sl = (A.mc.model == MODEL_PLATE) ? (size_t)A.sp_stride : (size_t)p->horizons[i];
+    const nmpc_status st = nmpc_set_params(h, i, x0 ? x0 + (size_t)i * nx : nullptr, sp ? sp + so : nullptr,
+                                           up ? up + i : nullptr, on_device);
+    if (st != NMPC_OK) return st;
+    so += sl;
+  }
+  return NMPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nmpc_status nmpc_autotune_workspace_bytes(const nmpc_problem* prob, const nmpc_options* opts, size_t* bytes) {
+  if (!prob || !bytes) return NMPC_ERR_INVALID;
+  nmpc_options base;
+  if (opts) base = *opts;
+  else nmpc_options_defaults(&base);
+  size_t need = 0;
+  std::vector<nmpc_handle*> built;
+  for (const nmpc_options& o : tune_candidates(prob, base)) {
+    nmpc_handle* h = nullptr;
+    const nmpc_status st = nmpc_build(prob, &o, nullptr, &h);
+    if (st != NMPC_OK) {
+      for (nmpc_handle* b : built) nmpc_destroy(b);
+      return st;
+    }
+    need = std::max(need, h->ws_bytes);
+    built.push_back(h);
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_drop_built();
+  g_tune_built_key = tune_key(prob, &base);
+  g_tune_built = built;
+  *bytes = need;
+  return NMPC_OK;
+}
+
+nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cuda_stream, void* workspace,
+                          size_t bytes, const double* x0, const double* setpoint, const double* u_prev,
+                          int on_device, nmpc_tune_report* report) {
+  if (!prob || !opts || !workspace || prob->n_instances < 1 || !prob->horizons) return NMPC_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(workspace) & 255) return NMPC_ERR_WORKSPACE;
+  if (report) std::memset(report, 0, sizeof(*report));
+  const std::string key = tune_key(prob, opts);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& e : g_tune_cache)
+      if (e.first == key) {
+        opts->ordering = e.second.ordering;
+        opts->nd_leaf = e.second.nd_leaf;
+        opts->panel_scale = e.second.panel_scale;
+        if (report) report->cached = 1;
+        return NMPC_OK;
+      }
+  }
+  const std::vector<nmpc_options> cand = tune_candidates(prob, *opts);
+  std::vector<nmpc_handle*> built;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (g_tune_built_key == key && g_tune_built.size() == cand.size()) {
+      built = g_tune_built;
+      g_tune_built.clear();
+      g_tune_built_key.clear();
+    } else {
+      tune_drop_built();
+    }
+  }
+  int best = -1, fitted = 0;
+  double best_ms = 0.0;
+  nmpc_status first_fail = NMPC_OK;
+  std::vector<nmpc_info> info(prob->n_instances);
+  for (size_t c = 0; c < cand.size() && (int)c < NMPC_TUNE_MAX; ++c) {
+    nmpc_tune_candidate rc{cand[c].ordering, cand[c].nd_leaf, cand[c].panel_scale, NMPC_ERR_WORKSPACE, 0, 0.0};
+    nmpc_handle* h = built.empty() ? nullptr : built[c];
+    nmpc_status st = NMPC_OK;
+    if (h) h->stream = static_cast<cudaStream_t>(cuda_stream);  // built without a stream
+    else st = nmpc_build(prob, &cand[c], cuda_stream, &h);
+    if (st != NMPC_OK) {
+      for (size_t k = c + 1; k < built.size(); ++k) nmpc_destroy(built[k]);
+      return st;
+    }
+    if (h->ws_bytes <= bytes) {
+      ++fitted;
+      st = nmpc_bind(h, workspace, bytes);
+      if (st == NMPC_OK) st = tune_set_params(h, prob, x0, setpoint, u_prev, on_device);
+      if (st == NMPC_OK) st = nmpc_solve(h, 0, info.data());
+      // the time of one iteration's evaluation, assembly, factorization and
+      // solves at the converged point (the rest of an iteration is the same
+      // for every candidate; a cold solve's total would also weigh its
+      // inertia corrections, which warm re-solves rarely need)
+      nmpc_phase_times pt{};
+      if (st == NMPC_OK) st = nmpc_time_phases(h, 3, &pt);
+      if (st == NMPC_ERR_CUDA || st == NMPC_ERR_INVALID || st == NMPC_TIMEOUT) {
+        if (!h->err.empty()) std::fprintf(stderr, "nmpc_autotune: %s\n", h->err.c_str());
+        nmpc_destroy(h);
+        for (size_t k = c + 1; k < built.size(); ++k) nmpc_destroy(built[k]);
+        return st;
+      }
+      int iters = 0;
+      for (const nmpc_info& f : info) iters = std::max(iters, f.iters);
+      rc.status = st;
+      rc.iters = iters;
+      rc.ms_per_iter = pt.ms_eval + pt.ms_assemble + pt.ms_factor + pt.ms_solve;
+      if (st == NMPC_OK && (best < 0 || rc.ms_per_iter < best_ms)) {
+        best = (int)c;
+        best_ms = rc.ms_per_iter;
+      }
+      if (st != NMPC_OK && first_fail == NMPC_OK) first_fail = st;
+    }
+    nmpc_destroy(h);
+    if (report) report->cand[report->n_candidates++] = rc;
+  }
+  if (report) report->best = best;
+  if (!fitted) return NMPC_ERR_WORKSPACE;
+  if (best < 0) return first_fail == NMPC_OK ? NMPC_MAX_ITER : first_fail;
+  opts->ordering = cand[best].ordering;
+  opts->nd_leaf = cand[best].nd_leaf;
+  opts->panel_scale = cand[best].panel_scale;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.emplace_back(key, *opts);
+  return NMPC_OK;
+}
+
+}  // extern "C"

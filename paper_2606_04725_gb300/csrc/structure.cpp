@@ -8,11 +8,14 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <functional>
 #include <numeric>
+#include <mutex>
 #include <stdexcept>
+#include <thread>
 
 namespace nmpc {
 namespace {
@@ -277,6 +280,32 @@ void symbolic_instance(int n, const std::vector<std::pair<int, int>>& lower_edge
 
 }  // namespace
 
+// Run f(0 .. n-1) on up to hardware_concurrency host threads; the first
+// exception thrown by any task is rethrown after all threads have joined.
+void parallel_for(int n, const std::function<void(int)>& f) {
+  const int nt = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+  std::atomic<int> next{0};
+  std::mutex mu;
+  std::exception_ptr err;
+  auto work = [&] {
+    for (;;) {
+      const int q = next.fetch_add(1);
+      if (q >= n) return;
+      try {
+        f(q);
+      } catch (...) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!err) err = std::current_exception();
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  if (err) std::rethrow_exception(err);
+}
+
 std::string analyze(const ProblemSpec& sp, Analysis& A) {
   auto t0 = std::chrono::steady_clock::now();
   try {
@@ -384,6 +413,31 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
           ws(1, L.offu(k), L.offu(k));
         }
       }
+    }
+    // The symbolic analysis of an instance (condensed pattern, ordering,
+    // elimination tree, supernodes) depends only on its horizon: it runs once
+    // per distinct horizon, for the first instance that has it, on several
+    // host threads, and the other instances copy it.
+    auto ord_of = [&](int T) { return sp.ordering != 0 ? sp.ordering : (T < 8 ? 1 : 2); };  // short horizons: a chain
+    std::vector<int> rep_of(ni), reps;
+    {
+      std::vector<std::pair<int, int>> firsts;  // (T, first instance), sorted by T
+      for (int i = 0; i < ni; ++i) {
+        auto it = std::lower_bound(firsts.begin(), firsts.end(), std::make_pair(sp.T[i], -1));
+        if (it != firsts.end() && it->first == sp.T[i]) {
+          rep_of[i] = it->second;
+        } else {
+          firsts.insert(it, {sp.T[i], i});
+          rep_of[i] = i;
+          reps.push_back(i);
+        }
+      }
+    }
+    auto symbolic_of = [&](int i) {
+      Layout L{nx, nu, sp.T[i]};
+      const int wo = A.inst_woff[i], ro = A.inst_roff[i];
+      const int nl = L.n(), ml = L.m();
+      auto hc = [&](int r, int s) -> int { return A.Hcol[(size_t)(ro + r) * WH + s]; };
       // condensed pattern K_c = W + Sigma + H^T D H (local lower edges)
       std::vector<std::pair<int, int>> edges;
       edges.reserve((size_t)ml * WH * (WH + 1) / 2 + (size_t)L.T * WS + nl);
@@ -403,9 +457,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       std::sort(edges.begin(), edges.end());
       edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
       // ordering
-      int ord = sp.ordering;
-      if (ord == 0) ord = (L.T < 8) ? 1 : 2;  // short horizons: a chain; else nested dissection (also for batches)
-      A.ordering_used = ord;
+      const int ord = ord_of(L.T);
       std::vector<int> order(nl);
       if (ord == 1) {
         std::iota(order.begin(), order.end(), 0);
@@ -440,6 +492,16 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
         if ((int)order.size() != nl) throw std::runtime_error("nested dissection lost vertices");
       }
       symbolic_instance(nl, edges, order, syms[i]);
+    };
+    parallel_for((int)reps.size(), [&](int q) { symbolic_of(reps[q]); });
+    for (int i = 0; i < ni; ++i)
+      if (rep_of[i] != i) syms[i] = syms[rep_of[i]];
+    A.ordering_used = ord_of(sp.T[ni - 1]);
+    for (int i = 0; i < ni; ++i) {
+      Layout L{nx, nu, sp.T[i]};
+      const int vo = A.inst_voff[i], ro = A.inst_roff[i], wo = A.inst_woff[i];
+      const int nl = L.n(), ml = L.m();
+      auto hc = [&](int r, int s) -> int& { return A.Hcol[(size_t)(ro + r) * WH + s]; };
       for (int v = 0; v < nl; ++v) { A.perm[vo + v] = vo + syms[i].pos[v]; A.iperm[vo + syms[i].pos[v]] = vo + v; }
       // convert H columns to global indices
       for (int r = 0; r < ml; ++r)
@@ -569,40 +631,65 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       if (it == R + A.sn_nrow[s] || *it != r) throw std::runtime_error("matrix entry outside the factor pattern");
       return A.sn_Lptr[s] + (long long)(c - A.sn_first[s]) * A.sn_nrow[s] + (it - R);
     };
-    // assembly map: every stored term of K_c, grouped by its factor position
+    // assembly map: every stored term of K_c, grouped by its factor position.
+    // Each instance's terms land in its own panels, which follow the previous
+    // instance's, so the map is built per instance (on several host threads)
+    // and the instances' parts are concatenated in order.
     struct Term { long long L; int type, a, b; };  // type 0 diag (a = var), 1 W (a = slot), 2 HDH (a, b slots)
-    std::vector<Term> terms;
-    terms.reserve((size_t)n + nW + (size_t)m * WH * 3);
-    for (int v = 0; v < n; ++v) terms.push_back({lidx(v, v), 0, v, -1});
-    for (long long s = 0; s < nW; ++s) if (Wi[s] >= 0) terms.push_back({lidx(Wi[s], Wj[s]), 1, (int)s, -1});
-    for (long long r = 0; r < m; ++r)
-      for (int a = 0; a < WH; ++a) {
-        const int ca = A.Hcol[r * WH + a];
-        if (ca < 0) continue;
-        for (int b = 0; b <= a; ++b) {
-          const int cb = A.Hcol[r * WH + b];
-          if (cb < 0) continue;
-          terms.push_back({lidx(ca, cb), 2, (int)(r * WH + a), (int)(r * WH + b)});
+    struct MapPart {
+      std::vector<long long> tgt_L;
+      std::vector<int> tgt_diag, tw_cnt, tw_idx, th_cnt, th_a, th_b;
+    };
+    std::vector<MapPart> parts(ni);
+    parallel_for(ni, [&](int i) {
+      const int vo = A.inst_voff[i], nl = A.inst_n[i];
+      const long long wo = A.inst_woff[i], nWi = (long long)sp.T[i] * WS;
+      const long long ro = A.inst_roff[i], ml = A.inst_m[i];
+      std::vector<Term> terms;
+      terms.reserve((size_t)nl + nWi + (size_t)ml * WH * 3);
+      for (int v = vo; v < vo + nl; ++v) terms.push_back({lidx(v, v), 0, v, -1});
+      for (long long s = wo; s < wo + nWi; ++s) if (Wi[s] >= 0) terms.push_back({lidx(Wi[s], Wj[s]), 1, (int)s, -1});
+      for (long long r = ro; r < ro + ml; ++r)
+        for (int a = 0; a < WH; ++a) {
+          const int ca = A.Hcol[r * WH + a];
+          if (ca < 0) continue;
+          for (int b = 0; b <= a; ++b) {
+            const int cb = A.Hcol[r * WH + b];
+            if (cb < 0) continue;
+            terms.push_back({lidx(ca, cb), 2, (int)(r * WH + a), (int)(r * WH + b)});
+          }
         }
+      std::stable_sort(terms.begin(), terms.end(), [](const Term& x, const Term& y) {
+        return x.L < y.L || (x.L == y.L && x.type < y.type);
+      });
+      MapPart& P = parts[i];
+      for (size_t q = 0; q < terms.size();) {
+        const long long L = terms[q].L;
+        P.tgt_L.push_back(L);
+        int diag = -1, nw = 0, nh = 0;
+        for (; q < terms.size() && terms[q].L == L; ++q) {
+          const Term& t = terms[q];
+          if (t.type == 0) diag = t.a;
+          else if (t.type == 1) { P.tw_idx.push_back(t.a); ++nw; }
+          else { P.th_a.push_back(t.a); P.th_b.push_back(t.b); ++nh; }
+        }
+        P.tgt_diag.push_back(diag);
+        P.tw_cnt.push_back(nw);
+        P.th_cnt.push_back(nh);
       }
-    std::stable_sort(terms.begin(), terms.end(), [](const Term& x, const Term& y) {
-      return x.L < y.L || (x.L == y.L && x.type < y.type);
     });
-    A.tgt_L.clear(); A.tgt_diag.clear();
+    A.tgt_L.clear(); A.tgt_diag.clear(); A.tw_idx.clear(); A.th_a.clear(); A.th_b.clear();
     A.tw_ptr.assign(1, 0); A.th_ptr.assign(1, 0);
-    for (size_t q = 0; q < terms.size();) {
-      const long long L = terms[q].L;
-      A.tgt_L.push_back(L);
-      int diag = -1;
-      for (; q < terms.size() && terms[q].L == L; ++q) {
-        const Term& t = terms[q];
-        if (t.type == 0) diag = t.a;
-        else if (t.type == 1) A.tw_idx.push_back(t.a);
-        else { A.th_a.push_back(t.a); A.th_b.push_back(t.b); }
+    for (const MapPart& P : parts) {
+      A.tgt_L.insert(A.tgt_L.end(), P.tgt_L.begin(), P.tgt_L.end());
+      A.tgt_diag.insert(A.tgt_diag.end(), P.tgt_diag.begin(), P.tgt_diag.end());
+      A.tw_idx.insert(A.tw_idx.end(), P.tw_idx.begin(), P.tw_idx.end());
+      A.th_a.insert(A.th_a.end(), P.th_a.begin(), P.th_a.end());
+      A.th_b.insert(A.th_b.end(), P.th_b.begin(), P.th_b.end());
+      for (size_t t = 0; t < P.tgt_L.size(); ++t) {
+        A.tw_ptr.push_back(A.tw_ptr.back() + P.tw_cnt[t]);
+        A.th_ptr.push_back(A.th_ptr.back() + P.th_cnt[t]);
       }
-      A.tgt_diag.push_back(diag);
-      A.tw_ptr.push_back((int)A.tw_idx.size());
-      A.th_ptr.push_back((int)A.th_a.size());
     }
     // reduction chunks (never crossing an instance)
     const int CH = RED_CHUNK;

@@ -3,6 +3,7 @@
 // to re-run the numeric work of Algorithm 2 without touching structure again.
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -54,5 +55,9 @@ struct Analysis {
 
 // Returns an empty string on success, else an error message.
 std::string analyze(const ProblemSpec& spec, Analysis& out);
+
+// Run f(0 .. n-1) on up to hardware_concurrency host threads (the first
+// exception thrown by a task is rethrown after all threads have joined).
+void parallel_for(int n, const std::function<void(int)>& f);
 
 }  // namespace nmpc
