@@ -1360,83 +1360,190 @@ __global__ void __launch_bounds__(256) k_big_update(Dev d, SnDev s, const FrontD
 // triangle BNB columns at a time in warp 0, the rows below by all threads.
 // The front vector lives in shared memory when it fits (smem_doubles), else
 // in the front's slot of a global scratch vector (offset: its row list).
-__global__ void __launch_bounds__(1024) k_big_fwd(Dev d, SnDev s, const FrontDesc* dl, int smem_doubles) {
+// ---------------------------------------------------------------------------
+// Solves of the large fronts, one launch sequence per level.  A single block
+// per front would carry all of a front's FP64 work on one SM (m c FMAs each
+// way: 53M for the 7296-row root of the g = 64 plate); instead the columns go
+// in blocks of SBW, and per block
+//   forward:  one CTA per front solves the block's unit lower triangle
+//             (k_bigs_fwd_diag: 32-column sub-blocks by a warp's shuffle
+//             chain, each followed by the rest of the block's rows), then a
+//             grid of CTAs applies the block to every row below it
+//             (k_bigs_fwd_rows: rows across lanes, the block's columns split
+//             over the warps, coalesced reads of L);
+//   backward: first the ancestors' rows for every column (k_bigs_bwd_anc:
+//             a warp per column, rows across lanes), then, last block first,
+//             one CTA per front solves the block's upper triangle
+//             (k_bigs_bwd_diag) and a grid of CTAs applies it to every
+//             column before it (k_bigs_bwd_cols: a warp per column).
+// The front vector lives in global scratch (fvec), L2-resident between the
+// launches.  k_bigs_*_pre and k_bigs_*_post gather the right-hand side and
+// the children's update vectors, and write the outputs.
+// ---------------------------------------------------------------------------
+constexpr int SBW = BIG_SBW;  // column block of the large-front solves (128)
+constexpr int SBT = BIG_SBT;  // threads per CTA (256)
+
+__device__ __forceinline__ bool big_active(const Dev& d, const FrontDesc& fd) {
+  return d.ctl[fd.inst].status == ST_RUNNING;
+}
+
+// f = P b on the pivot rows, 0 below, plus the children's update vectors
+__global__ void __launch_bounds__(SBT) k_bigs_fwd_pre(Dev d, SnDev s, const FrontDesc* dl) {
   const FrontDesc& fd = dl[blockIdx.x];
-  if (d.ctl[fd.inst].status != ST_RUNNING) return;
-  const int m = fd.m, c = fd.c, first = fd.first;
-  const double* Lg = s.L + fd.Lptr;
-  double* fv = (m <= smem_doubles) ? dsm : s.fvec + fd.rowptr;  // m
-  __shared__ double yb[BNB];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[first + i] : 0.0;
+  if (!big_active(d, fd)) return;
+  double* fv = s.fvec + fd.rowptr;
+  const int m = fd.m, c = fd.c, tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < m; i += nt) fv[i] = (i < c) ? d.b[fd.first + i] : 0.0;
   __syncthreads();
   for (int q = 0; q < fd.nchild; ++q) {
     const ChildRef ch = child_ref(s, fd, q);
     for (int a = tid; a < ch.mc; a += nt) fv[ch.rel[a]] += ch.uv[a];
     __syncthreads();
   }
-  for (int jb = 0; jb < c; jb += BNB) {
-    const int w = min(BNB, c - jb);
-    if (tid < 32) {
-      double v = (tid < w) ? fv[jb + tid] : 0.0;
-      for (int j = 0; j < w; ++j) {
-        const double yj = __shfl_sync(FULL, v, j);
-        if (tid > j && tid < w) v = fma(-Lg[(jb + tid) + (size_t)(jb + j) * m], yj, v);
-      }
-      if (tid < w) { fv[jb + tid] = v; yb[tid] = v; }
-    }
-    __syncthreads();
-    for (int i = jb + w + tid; i < m; i += nt) {
-      double a = fv[i];
-      for (int j = 0; j < w; ++j) a = fma(-Lg[i + (size_t)(jb + j) * m], yb[j], a);
-      fv[i] = a;
-    }
-    __syncthreads();
-  }
-  double* uvJ = s.uv + fd.uvptr;
-  for (int i = c + tid; i < m; i += nt) uvJ[i - c] = fv[i];
-  for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j] * Lg[j + (size_t)j * m];
 }
 
-__global__ void __launch_bounds__(1024) k_big_bwd(Dev d, SnDev s, const FrontDesc* dl, int smem_doubles) {
+// unit lower triangle of columns jb .. jb+w-1, in place on f
+__global__ void __launch_bounds__(SBT) k_bigs_fwd_diag(Dev d, SnDev s, const FrontDesc* dl, int jb) {
   const FrontDesc& fd = dl[blockIdx.x];
-  if (d.ctl[fd.inst].status != ST_RUNNING) return;
-  const int m = fd.m, c = fd.c, first = fd.first;
-  const double* Lg = s.L + fd.Lptr;
-  const int* rows_idx = s.sn_rows + fd.rowptr;
-  double* xv = (m <= smem_doubles) ? dsm : s.fvec + fd.rowptr;  // m
-  __shared__ double xb[BNB];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < m; i += nt) xv[i] = (i < c) ? d.b[first + i] : d.b[rows_idx[i]];
+  if (!big_active(d, fd) || jb >= fd.c) return;
+  const int m = fd.m, w = min(SBW, fd.c - jb), tid = threadIdx.x, nt = blockDim.x;
+  double* fv = s.fvec + fd.rowptr;
+  const double* Lb = s.L + fd.Lptr + jb + (size_t)jb * m;  // L(jb + r, jb + j) = Lb[r + j m]
+  __shared__ double v[SBW];
+  for (int t = tid; t < w; t += nt) v[t] = fv[jb + t];
   __syncthreads();
-  // t_j = z_j - sum_{i >= c} L_ij x_i, one column per thread
-  for (int j = tid; j < c; j += nt) {
-    double a = xv[j];
-    for (int i = c; i < m; ++i) a = fma(-Lg[i + (size_t)j * m], xv[i], a);
-    xv[j] = a;
-  }
-  __syncthreads();
-  const int nbk = (c + BNB - 1) / BNB;
-  for (int bk = nbk - 1; bk >= 0; --bk) {
-    const int jb = bk * BNB, w = min(BNB, c - jb);
+  for (int sb = 0; sb < w; sb += 32) {
+    const int ws = min(32, w - sb);
     if (tid < 32) {
-      double v = (tid < w) ? xv[jb + tid] : 0.0;
-      for (int j = w - 1; j >= 0; --j) {
-        const double xj = __shfl_sync(FULL, v, j);
-        if (tid < j) v = fma(-Lg[(jb + j) + (size_t)(jb + tid) * m], xj, v);
+      double x = (tid < ws) ? v[sb + tid] : 0.0;
+      for (int j = 0; j < ws; ++j) {
+        const double yj = __shfl_sync(FULL, x, j);
+        if (tid > j && tid < ws) x = fma(-Lb[(sb + tid) + (size_t)(sb + j) * m], yj, x);
       }
-      if (tid < w) { xv[jb + tid] = v; xb[tid] = v; }
+      if (tid < ws) v[sb + tid] = x;
     }
     __syncthreads();
-    // columns before the block: x_i -= sum_{j in block} L(j, i) x_j
-    for (int i = tid; i < jb; i += nt) {
-      double a = xv[i];
-      for (int j = 0; j < w; ++j) a = fma(-Lg[(jb + j) + (size_t)i * m], xb[j], a);
-      xv[i] = a;
+    for (int r = sb + ws + tid; r < w; r += nt) {
+      double a = v[r];
+      for (int j = 0; j < ws; ++j) a = fma(-Lb[r + (size_t)(sb + j) * m], v[sb + j], a);
+      v[r] = a;
     }
     __syncthreads();
   }
-  for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
+  for (int t = tid; t < w; t += nt) fv[jb + t] = v[t];
+}
+
+// f_r -= sum_{j < w} L(r, jb + j) y_{jb+j} for rows r >= jb + w: 64 rows per
+// CTA across the lanes, the block's columns split over 4 groups of 2 warps
+__global__ void __launch_bounds__(SBT) k_bigs_fwd_rows(Dev d, SnDev s, const FrontDesc* dl, int jb) {
+  const FrontDesc& fd = dl[blockIdx.y];
+  if (!big_active(d, fd) || jb >= fd.c) return;
+  const int m = fd.m, w = min(SBW, fd.c - jb), r0 = jb + w;
+  const int row0 = r0 + blockIdx.x * 64;
+  if (row0 >= m) return;  // uniform over the CTA
+  double* fv = s.fvec + fd.rowptr;
+  const double* Lg = s.L + fd.Lptr;
+  __shared__ double y[SBW];
+  __shared__ double part[4][64];
+  const int tid = threadIdx.x, rr = tid & 63, grp = tid >> 6;
+  for (int t = tid; t < w; t += blockDim.x) y[t] = fv[jb + t];
+  __syncthreads();
+  const int r = row0 + rr;
+  double a = 0.0;
+  if (r < m)
+    for (int j = grp; j < w; j += 4) a = fma(Lg[r + (size_t)(jb + j) * m], y[j], a);
+  part[grp][rr] = a;
+  __syncthreads();
+  if (grp == 0 && r < m) fv[r] -= (part[0][rr] + part[1][rr]) + (part[2][rr] + part[3][rr]);
+}
+
+// outputs: update vector u (rows c..m-1) and z = D^{-1} y
+__global__ void __launch_bounds__(SBT) k_bigs_fwd_post(Dev d, SnDev s, const FrontDesc* dl) {
+  const FrontDesc& fd = dl[blockIdx.x];
+  if (!big_active(d, fd)) return;
+  const double* fv = s.fvec + fd.rowptr;
+  const double* Lg = s.L + fd.Lptr;
+  const int m = fd.m, c = fd.c, tid = threadIdx.x, nt = blockDim.x;
+  double* uvJ = s.uv + fd.uvptr;
+  for (int i = c + tid; i < m; i += nt) uvJ[i - c] = fv[i];
+  for (int j = tid; j < c; j += nt) d.b[fd.first + j] = fv[j] * Lg[j + (size_t)j * m];  // diagonal holds 1/d_j
+}
+
+// x = z on the pivot rows, the ancestors' solution below
+__global__ void __launch_bounds__(SBT) k_bigs_bwd_pre(Dev d, SnDev s, const FrontDesc* dl) {
+  const FrontDesc& fd = dl[blockIdx.x];
+  if (!big_active(d, fd)) return;
+  double* xv = s.fvec + fd.rowptr;
+  const int* rows_idx = s.sn_rows + fd.rowptr;
+  for (int i = threadIdx.x; i < fd.m; i += blockDim.x) xv[i] = (i < fd.c) ? d.b[fd.first + i] : d.b[rows_idx[i]];
+}
+
+// t_j = z_j - sum_{i >= c} L_ij x_i: a warp per column j, rows across lanes
+__global__ void __launch_bounds__(SBT) k_bigs_bwd_anc(Dev d, SnDev s, const FrontDesc* dl) {
+  const FrontDesc& fd = dl[blockIdx.y];
+  if (!big_active(d, fd)) return;
+  const int j = blockIdx.x * (SBT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (j >= fd.c || fd.m == fd.c) return;  // uniform over the warp
+  double* xv = s.fvec + fd.rowptr;
+  const double* Lj = s.L + fd.Lptr + (size_t)j * fd.m;
+  double a = 0.0;
+  for (int i = fd.c + lane; i < fd.m; i += 32) a = fma(Lj[i], xv[i], a);
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+  if (lane == 0) xv[j] -= a;
+}
+
+// unit upper triangle L_KK^T of columns jb .. jb+w-1, last sub-block first
+__global__ void __launch_bounds__(SBT) k_bigs_bwd_diag(Dev d, SnDev s, const FrontDesc* dl, int jb) {
+  const FrontDesc& fd = dl[blockIdx.x];
+  if (!big_active(d, fd) || jb >= fd.c) return;
+  const int m = fd.m, w = min(SBW, fd.c - jb), tid = threadIdx.x, nt = blockDim.x;
+  double* xv = s.fvec + fd.rowptr;
+  const double* Lb = s.L + fd.Lptr + jb + (size_t)jb * m;  // L(jb + r, jb + j) = Lb[r + j m]
+  __shared__ double v[SBW];
+  for (int t = tid; t < w; t += nt) v[t] = xv[jb + t];
+  __syncthreads();
+  for (int sb = (w - 1) / 32 * 32; sb >= 0; sb -= 32) {
+    const int ws = min(32, w - sb);
+    if (tid < 32) {
+      double x = (tid < ws) ? v[sb + tid] : 0.0;
+      for (int j = ws - 1; j >= 0; --j) {
+        const double xj = __shfl_sync(FULL, x, j);
+        if (tid < j) x = fma(-Lb[(sb + j) + (size_t)(sb + tid) * m], xj, x);  // L(sb+j, sb+tid)
+      }
+      if (tid < ws) v[sb + tid] = x;
+    }
+    __syncthreads();
+    for (int i = tid; i < sb; i += nt) {  // x_i -= sum_j L(sb + j, i) x_{sb+j}
+      double a = v[i];
+      for (int j = 0; j < ws; ++j) a = fma(-Lb[(sb + j) + (size_t)i * m], v[sb + j], a);
+      v[i] = a;
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < w; t += nt) xv[jb + t] = v[t];
+}
+
+// x_i -= sum_{j < w} L(jb + j, i) x_{jb+j} for columns i < jb: a warp per
+// column, the block's rows across lanes (column i is contiguous there)
+__global__ void __launch_bounds__(SBT) k_bigs_bwd_cols(Dev d, SnDev s, const FrontDesc* dl, int jb) {
+  const FrontDesc& fd = dl[blockIdx.y];
+  if (!big_active(d, fd) || jb >= fd.c) return;
+  const int i = blockIdx.x * (SBT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= jb) return;  // uniform over the warp
+  const int m = fd.m, w = min(SBW, fd.c - jb);
+  double* xv = s.fvec + fd.rowptr;
+  const double* Li = s.L + fd.Lptr + jb + (size_t)i * m;  // L(jb + j, i) = Li[j]
+  double a = 0.0;
+  for (int j = lane; j < w; j += 32) a = fma(Li[j], xv[jb + j], a);
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+  if (lane == 0) xv[i] -= a;
+}
+
+__global__ void __launch_bounds__(SBT) k_bigs_bwd_post(Dev d, SnDev s, const FrontDesc* dl) {
+  const FrontDesc& fd = dl[blockIdx.x];
+  if (!big_active(d, fd)) return;
+  const double* xv = s.fvec + fd.rowptr;
+  for (int j = threadIdx.x; j < fd.c; j += blockDim.x) d.b[fd.first + j] = xv[j];
 }
 
 }  // namespace nmpc

@@ -47,8 +47,16 @@ __global__ void k_big_extend(Dev d, SnDev s, const FrontDesc* dl, int k);
 __global__ void k_big_diag(Dev d, SnDev s, const FrontDesc* dl, int p);
 __global__ void k_big_trsm(Dev d, SnDev s, const FrontDesc* dl, int p);
 __global__ void k_big_update(Dev d, SnDev s, const FrontDesc* dl, int p);
-__global__ void k_big_fwd(Dev d, SnDev s, const FrontDesc* dl, int smem_doubles);
-__global__ void k_big_bwd(Dev d, SnDev s, const FrontDesc* dl, int smem_doubles);
+__global__ void k_bigs_fwd_pre(Dev d, SnDev s, const FrontDesc* dl);
+__global__ void k_bigs_fwd_diag(Dev d, SnDev s, const FrontDesc* dl, int jb);
+__global__ void k_bigs_fwd_rows(Dev d, SnDev s, const FrontDesc* dl, int jb);
+__global__ void k_bigs_fwd_post(Dev d, SnDev s, const FrontDesc* dl);
+__global__ void k_bigs_bwd_pre(Dev d, SnDev s, const FrontDesc* dl);
+__global__ void k_bigs_bwd_anc(Dev d, SnDev s, const FrontDesc* dl);
+__global__ void k_bigs_bwd_diag(Dev d, SnDev s, const FrontDesc* dl, int jb);
+__global__ void k_bigs_bwd_cols(Dev d, SnDev s, const FrontDesc* dl, int jb);
+__global__ void k_bigs_bwd_post(Dev d, SnDev s, const FrontDesc* dl);
+constexpr int BIG_SBW = 128, BIG_SBT = 256;  // SBW, SBT in factor_kernels.cu
 constexpr int BIG_NB = 32, BIG_TILE = 64, BIG_ROWS = 256;  // BNB, BT, BROWS in factor_kernels.cu
 
 // adjoint_kernels.cu

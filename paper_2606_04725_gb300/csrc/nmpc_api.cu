@@ -293,10 +293,42 @@ nmpc_status launch_factor(nmpc_handle* h) {
   return NMPC_OK;
 }
 
-// doubles of shared memory a large-front solve block uses for its front
-// vector (0: every front of the level keeps it in global scratch)
-int big_solve_smem(const nmpc_handle* h, int l) {
-  return (long long)h->lvl_maxm[l] <= h->smem_cap_doubles ? h->lvl_maxm[l] : 0;
+// The large-front solves of level l (see the k_bigs_* kernels): per column
+// block a one-CTA-per-front triangle and a many-CTA product.
+long long launch_big_fwd(nmpc_handle* h, int l) {
+  const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
+  const FrontDesc* dl = h->s.desc + h->lvl_ptr[l];
+  cudaStream_t st = h->stream;
+  long long n = 2;
+  k_bigs_fwd_pre<<<cnt, BIG_SBT, 0, st>>>(h->d, h->s, dl);
+  for (int jb = 0; jb < h->lvl_maxc[l]; jb += BIG_SBW) {
+    k_bigs_fwd_diag<<<cnt, BIG_SBT, 0, st>>>(h->d, h->s, dl, jb);
+    const int below = h->lvl_maxm[l] - jb;
+    k_bigs_fwd_rows<<<dim3((unsigned)std::max(1, (below + 63) / 64), cnt), BIG_SBT, 0, st>>>(h->d, h->s, dl, jb);
+    n += 2;
+  }
+  k_bigs_fwd_post<<<cnt, BIG_SBT, 0, st>>>(h->d, h->s, dl);
+  return n;
+}
+
+long long launch_big_bwd(nmpc_handle* h, int l) {
+  const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
+  const FrontDesc* dl = h->s.desc + h->lvl_ptr[l];
+  cudaStream_t st = h->stream;
+  const int warps = BIG_SBT / 32;
+  long long n = 3;
+  k_bigs_bwd_pre<<<cnt, BIG_SBT, 0, st>>>(h->d, h->s, dl);
+  k_bigs_bwd_anc<<<dim3((unsigned)std::max(1, (h->lvl_maxc[l] + warps - 1) / warps), cnt), BIG_SBT, 0, st>>>(h->d, h->s, dl);
+  for (int jb = (h->lvl_maxc[l] - 1) / BIG_SBW * BIG_SBW; jb >= 0; jb -= BIG_SBW) {
+    k_bigs_bwd_diag<<<cnt, BIG_SBT, 0, st>>>(h->d, h->s, dl, jb);
+    ++n;
+    if (jb > 0) {
+      k_bigs_bwd_cols<<<dim3((unsigned)((jb + warps - 1) / warps), cnt), BIG_SBT, 0, st>>>(h->d, h->s, dl, jb);
+      ++n;
+    }
+  }
+  k_bigs_bwd_post<<<cnt, BIG_SBT, 0, st>>>(h->d, h->s, dl);
+  return n;
 }
 
 nmpc_status launch_solve(nmpc_handle* h) {
@@ -312,24 +344,24 @@ nmpc_status launch_solve(nmpc_handle* h) {
   for (int l = L; l < nl; ++l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
-    if (h->lvl_bigsolve[l])
-      k_big_fwd<<<cnt, 1024, big_solve_smem(h, l) * 8, h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
-                                                                   big_solve_smem(h, l));
-    else
+    if (h->lvl_bigsolve[l]) {
+      h->launches += launch_big_fwd(h, l);
+    } else {
       k_fwd_level<<<cnt, 128, h->lvl_smem_solve[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
                                                                  h->smem_cap_doubles);
-    ++h->launches;
+      ++h->launches;
+    }
   }
   for (int l = nl - 1; l >= L; --l) {
     const int cnt = h->lvl_ptr[l + 1] - h->lvl_ptr[l];
     if (!cnt) continue;
-    if (h->lvl_bigsolve[l])
-      k_big_bwd<<<cnt, 1024, big_solve_smem(h, l) * 8, h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
-                                                                   big_solve_smem(h, l));
-    else
+    if (h->lvl_bigsolve[l]) {
+      h->launches += launch_big_bwd(h, l);
+    } else {
       k_bwd_level<<<cnt, 128, h->lvl_smem_bwd[l], h->stream>>>(h->d, h->s, h->s.desc + h->lvl_ptr[l],
                                                                h->smem_cap_doubles);
-    ++h->launches;
+      ++h->launches;
+    }
   }
   if (L > 0) {
     k_bwd_persist<<<h->persist_blocks_bwd, 128, h->persist_smem_bwd, h->stream>>>(
@@ -865,15 +897,6 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   const int maxf = *std::max_element(h->lvl_smem_solve.begin(), h->lvl_smem_solve.end());
   const int maxb = *std::max_element(h->lvl_smem_bwd.begin(), h->lvl_smem_bwd.end());
   if (maxf > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxf));
-  {
-    int maxbig = 0;
-    for (size_t l = 0; l < h->lvl_bigsolve.size(); ++l)
-      if (h->lvl_bigsolve[l]) maxbig = std::max(maxbig, big_solve_smem(h, (int)l) * 8);
-    if (maxbig > 48 * 1024) {
-      CUDA_TRY(h, cudaFuncSetAttribute(k_big_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, maxbig));
-      CUDA_TRY(h, cudaFuncSetAttribute(k_big_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, maxbig));
-    }
-  }
   if (maxb > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_bwd_level, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb));
   CUDA_TRY(h, cudaStreamSynchronize(st));
   h->d.max_iter = h->opt.max_iter;
