@@ -65,21 +65,6 @@ __device__ __forceinline__ int tri_col(int t, int nn) {
   return kk;
 }
 
-// 1/d in double precision.  Seed: the PTX approximate reciprocal (relative
-// error below 2^-20).  Refinement: one third-order Newton-Raphson step for
-// f(y) = 1/y - d, i.e. with e = 1 - d*y the truncated series
-// 1/d = y/(1 - e) = y (1 + e + e^2 + ...), y <- y + y (e + e^2), which leaves
-// a relative error of order e^3 < 2^-60 plus the rounding of the last FMA.
-// Near the ends of the exponent range (and for zero, subnormal, infinite or
-// NaN input) the plain division is used.
-__device__ __forceinline__ double recip_nr(double d) {
-  const int ex = (__double2hiint(d) >> 20) & 0x7ff;
-  if (ex < 3 || ex > 2044) return 1.0 / d;
-  double y;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
-  const double e = fma(-d, y, 1.0);
-  return fma(y, fma(e, e, e), y);
-}
 
 // A pivot counts as positive only if it exceeds thr = pivtol * |K_jj| (K_jj
 // the assembled diagonal): a pivot at rounding level is a zero eigenvalue,

@@ -19,9 +19,15 @@ __device__ __forceinline__ int offu(const ModelConst& mc, int k) { return offx(m
 
 // ------------------------------------------------------------ distillation
 
-__device__ __forceinline__ double vle(double a, double x) { return a * x / (1.0 + (a - 1.0) * x); }
-__device__ __forceinline__ double vle_d1(double a, double x) { double d = 1.0 + (a - 1.0) * x; return a / (d * d); }
-__device__ __forceinline__ double vle_d2(double a, double x) { double d = 1.0 + (a - 1.0) * x; return -2.0 * a * (a - 1.0) / (d * d * d); }
+// Equilibrium y = a x / (1 + (a-1) x) and its first two derivatives
+// a / d^2 and -2 a (a-1) / d^3 (d = 1 + (a-1) x), all from one reciprocal
+// of d: every FP64 division costs tens of instructions on this GPU.
+struct Vle { double y, d1, d2; };
+__device__ __forceinline__ Vle vle_all(double a, double x) {
+  const double r = recip_nr(fma(a - 1.0, x, 1.0));
+  const double ar = a * r;
+  return {ar * x, ar * r, -2.0 * (a - 1.0) * ar * r * r};
+}
 
 // Tray i (1-based) balance f_i(x, u) with L = uD, V = L + D, S = L + F, and its
 // partial derivatives w.r.t. x_{i-1}, x_i, x_{i+1}, u (eq. distill-ocp).
@@ -34,34 +40,37 @@ __device__ TrayEval tray_eval(const ModelConst& mc, const double* x, double u, i
   TrayEval e{0, 0, 0, 0, 0};
   const double xi = x[i - 1];
   if (i == 1) {  // total condenser
-    const double x2 = x[1];
-    const double y2 = vle(a, x2);
-    e.f = V * (y2 - xi) / mc.Ac;
-    e.d0 = -V / mc.Ac;
-    e.dp = V * vle_d1(a, x2) / mc.Ac;
-    e.du = D * (y2 - xi) / mc.Ac;
+    const Vle v2 = vle_all(a, x[1]);
+    const double ic = mc.inv_Ac;
+    e.f = V * (v2.y - xi) * ic;
+    e.d0 = -V * ic;
+    e.dp = V * v2.d1 * ic;
+    e.du = D * (v2.y - xi) * ic;
     return e;
   }
   if (i == N) {  // reboiler
-    const double xm = x[N - 2], yN = vle(a, xi);
-    e.f = (S * xm - (mc.F - D) * xi - V * yN) / mc.Ar;
-    e.dm = S / mc.Ar;
-    e.d0 = (-(mc.F - D) - V * vle_d1(a, xi)) / mc.Ar;
-    e.du = D * (xm - yN) / mc.Ar;
+    const double xm = x[N - 2];
+    const Vle vN = vle_all(a, xi);
+    const double ir = mc.inv_Ar;
+    e.f = (S * xm - (mc.F - D) * xi - V * vN.y) * ir;
+    e.dm = S * ir;
+    e.d0 = (-(mc.F - D) - V * vN.d1) * ir;
+    e.du = D * (xm - vN.y) * ir;
     return e;
   }
   const double xm = x[i - 2], xp = x[i];
-  const double yi = vle(a, xi), yp = vle(a, xp);
+  const Vle vi = vle_all(a, xi), vp = vle_all(a, xp);
+  const double yi = vi.y, yp = vp.y, it = mc.inv_At;
   // liquid entering from above: L above the feed tray, L onto the feed tray,
   // S below it; liquid leaving: L above the feed, S from the feed tray down
   const double lin = (i <= Nf) ? L : S;
   const double lout = (i < Nf) ? L : S;
   const double feed = (i == Nf) ? mc.F * mc.xF : 0.0;
-  e.f = (feed + lin * xm - lout * xi - V * (yi - yp)) / mc.At;
-  e.dm = lin / mc.At;
-  e.d0 = (-lout - V * vle_d1(a, xi)) / mc.At;
-  e.dp = V * vle_d1(a, xp) / mc.At;
-  e.du = D * (xm - xi - (yi - yp)) / mc.At;
+  e.f = (feed + lin * xm - lout * xi - V * (yi - yp)) * it;
+  e.dm = lin * it;
+  e.d0 = (-lout - V * vi.d1) * it;
+  e.dp = V * vp.d1 * it;
+  e.du = D * (xm - xi - (yi - yp)) * it;
   return e;
 }
 
@@ -161,10 +170,10 @@ __device__ void eval_row_at(const Dev& d, int r, int use_trial, int with_jac) {
     if (c.status != ST_RUNNING) return;
     eval_row(d, d.y, r, d.h, with_jac ? d.Hv : nullptr);
     if (with_jac) {  // reciprocals of the slacks and their duals, reused by every later kernel
-      d.isp[r] = 1.0 / d.sp[r];
-      d.ism[r] = 1.0 / d.sm[r];
-      d.ibp[r] = 1.0 / d.bp[r];
-      d.ibm[r] = 1.0 / d.bm[r];
+      d.isp[r] = recip_nr(d.sp[r]);
+      d.ism[r] = recip_nr(d.sm[r]);
+      d.ibp[r] = recip_nr(d.bp[r]);
+      d.ibm[r] = recip_nr(d.bm[r]);
     }
   }
 }
@@ -257,20 +266,21 @@ __device__ void eval_var_hess(const Dev& d, int v) {
   const double u = yi[offu(mc, k)];
   const double V = (u + 1.0) * D;
   auto coef = [&](int tray) { const int r = rbase + tray - 1; return -dt * (d.wp[r] - d.wm[r]); };
-  auto hold = [&](int tray) { return tray == 1 ? mc.Ac : (tray == N ? mc.Ar : mc.At); };
+  auto ihold = [&](int tray) { return tray == 1 ? mc.inv_Ac : (tray == N ? mc.inv_Ar : mc.inv_At); };
   if (q < N) {
     const int j = q + 1;  // tray
     const double xj = x[j - 1];
-    const double y1 = vle_d1(a, xj), y2 = vle_d2(a, xj);
+    const Vle vj = vle_all(a, xj);
+    const double y1 = vj.d1, y2 = vj.d2;
     double wdiag = (j == 1) ? 2.0 * dt : 0.0;
-    if (j >= 2) wdiag += coef(j) * (-V * y2) / hold(j);           // own row: -V y''(x_j)
-    if (j >= 2) wdiag += coef(j - 1) * (V * y2) / hold(j - 1);    // row above: +V y''(x_{i+1})
+    if (j >= 2) wdiag += coef(j) * (-V * y2) * ihold(j);           // own row: -V y''(x_j)
+    if (j >= 2) wdiag += coef(j - 1) * (V * y2) * ihold(j - 1);    // row above: +V y''(x_{i+1})
     double wux = 0.0;
-    if (j >= 2) wux += coef(j - 1) * (D * y1) / hold(j - 1);      // row j-1: D y'(x_{i+1})
-    if (j == 1) wux += coef(1) * (-D) / mc.Ac;
-    else if (j < N) wux += coef(j) * (-D * (1.0 + y1)) / mc.At;
-    else wux += coef(N) * (-D * y1) / mc.Ar;
-    if (j + 1 <= N) wux += coef(j + 1) * D / hold(j + 1);         // row j+1: D from x_{i-1}
+    if (j >= 2) wux += coef(j - 1) * (D * y1) * ihold(j - 1);      // row j-1: D y'(x_{i+1})
+    if (j == 1) wux += coef(1) * (-D) * mc.inv_Ac;
+    else if (j < N) wux += coef(j) * (-D * (1.0 + y1)) * mc.inv_At;
+    else wux += coef(N) * (-D * y1) * mc.inv_Ar;
+    if (j + 1 <= N) wux += coef(j + 1) * D * ihold(j + 1);         // row j+1: D from x_{i-1}
     W[q] = wdiag;
     W[N + q] = wux;
   } else {
@@ -290,10 +300,10 @@ __device__ void eval_var_at(const Dev& d, int v, int use_trial) {
     eval_var_hess(d, v);
     // reciprocals of the bound gaps and bound duals (0 where the bound is absent)
     const double y = d.y[v], lo = d.yL[v], hi = d.yU[v];
-    d.igL[v] = isfinite(lo) ? 1.0 / (y - lo) : 0.0;
-    d.igU[v] = isfinite(hi) ? 1.0 / (hi - y) : 0.0;
-    d.izL[v] = isfinite(lo) ? 1.0 / d.zL[v] : 0.0;
-    d.izU[v] = isfinite(hi) ? 1.0 / d.zU[v] : 0.0;
+    d.igL[v] = isfinite(lo) ? recip_nr(y - lo) : 0.0;
+    d.igU[v] = isfinite(hi) ? recip_nr(hi - y) : 0.0;
+    d.izL[v] = isfinite(lo) ? recip_nr(d.zL[v]) : 0.0;
+    d.izU[v] = isfinite(hi) ? recip_nr(d.zU[v]) : 0.0;
   }
 }
 

@@ -297,8 +297,11 @@ def test_solve_forms_agree(P, oracle, hz):
     """The three forms of the small-front solves: the panel transformed with
     the rows below each 16-column block scaled by the block's inverse (one
     product per block), the diagonal blocks inverted only (two products per
-    block), and plain column substitution.  Same solution and iteration counts
-    up to rounding, and every point is KKT-optimal by the oracle's evaluator."""
+    block), and plain column substitution.  Same iteration counts up to
+    rounding, every point KKT-optimal by the oracle's evaluator, and primal
+    points within 2 TOL_Y of each other (relative to max(1, |y|)): each is held
+    to TOL_Y of the converged point by the parity bar, so two of them may
+    differ by twice that."""
     x0s = [I.distillation_x0(34, 17, seed=40 + i) for i in range(len(hz))]
     sps = [0.78 + 0.02 * i for i in range(len(hz))]
     ys, its = [], []
@@ -317,7 +320,7 @@ def test_solve_forms_agree(P, oracle, hz):
     for k in (1, 2):
         for i in range(len(hz)):
             assert abs(its[0][i] - its[k][i]) <= 1, its
-            assert np.max(np.abs(ys[0][i] - ys[k][i])) < 1e-6
+            assert np.max(np.abs(ys[0][i] - ys[k][i])) / max(1.0, np.max(np.abs(ys[0][i]))) <= 2 * TOL_Y
 
 
 def test_device_parameters_equal_host_parameters_and_runs_are_deterministic(P):
