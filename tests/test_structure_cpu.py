@@ -136,3 +136,29 @@ def test_levels_order_every_child_before_its_parent(P, name, prob, opt):
         if par[j] >= 0:
             rp = set(rows[rows_ptr[par[j]]:rows_ptr[par[j] + 1]].tolist())
             assert set(rj[ncol[j]:].tolist()) <= rp, j
+
+
+def test_batch_analysis_equals_each_instance_analysed_alone(P):
+    """The batch analysis runs the symbolic work once per distinct horizon,
+    on several host threads, and copies it to the other instances.  Every
+    instance of an uneven batch with repeated horizons must then have the
+    structure of the same horizon analysed alone: the same factor ordering
+    (shifted by the instance's first variable), supernode sizes and row lists
+    (shifted), and parents (shifted by its first supernode)."""
+    hz = [50, 9, 80, 50, 9, 120, 80]
+    kw = dict(N=12, Nf=5)
+    b = P.Structure(P.MODEL_DISTILLATION, hz, **kw)
+    perm_b, nc_b, nr_b = b.export(0), b.export(2), b.export(3)
+    rows_b, par_b = b.export(4), b.export(5)
+    vo = so = ro = 0
+    for T in hz:
+        s = P.Structure(P.MODEL_DISTILLATION, [T], **kw)
+        perm, nc, nr, rows, par = s.export(0), s.export(2), s.export(3), s.export(4), s.export(5)
+        n, ns, nrows = perm.size, nc.size, rows.size
+        assert np.array_equal(perm_b[vo:vo + n], perm + vo)
+        assert np.array_equal(nc_b[so:so + ns], nc) and np.array_equal(nr_b[so:so + ns], nr)
+        assert np.array_equal(rows_b[ro:ro + nrows], rows + vo)
+        assert np.array_equal(par_b[so:so + ns], np.where(par < 0, -1, par + so))
+        vo, so, ro = vo + n, so + ns, ro + nrows
+        s.close()
+    assert vo == perm_b.size and so == nc_b.size
