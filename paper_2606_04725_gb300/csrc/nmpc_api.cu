@@ -78,6 +78,7 @@ struct nmpc_handle {
   // side stream of the panel transforms (forked per level, joined after the factorization)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool side_pending = false;  // work queued on the side stream since the last join
   std::vector<Ctl> h_ctl;
   Ctl* d_ctl_save = nullptr;
   long long launches = 0;
@@ -267,7 +268,7 @@ nmpc_status launch_factor(nmpc_handle* h) {
   const int nl = (int)h->lvl_ptr.size() - 1;
   const bool fork = h->side != nullptr;
   cudaStream_t ts = fork ? h->side : h->stream;
-  bool forked = false;
+  bool forked = h->side_pending;
   for (int l = 0; l < nl; ++l) {
     const nmpc_status st = launch_factor_level(h, l);
     if (st != NMPC_OK) return st;
@@ -289,6 +290,7 @@ nmpc_status launch_factor(nmpc_handle* h) {
   if (forked) {
     CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side));
     CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    h->side_pending = false;
   }
   return NMPC_OK;
 }
@@ -390,25 +392,40 @@ long long seq_factor(nmpc_handle* h) {
   const long long l0 = h->launches;
   k_zero_L<<<zgrid, TPB, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend);
   k_rows_pre<<<blocks_for(d.m, EW), EW, 0, st>>>(d, h->d_Drow);
+  long long rhs = 0;
+  if (h->side) {
+    // the solves' right-hand side needs the rows' terms, not the factor:
+    // computed on the side stream during the factorization (joined with the
+    // panel transforms before the inertia test)
+    cudaEventRecord(h->ev_fork, st);
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    k_rhs<<<blocks_for(d.n, EW), EW, 0, h->side>>>(d);
+    h->side_pending = true;
+    rhs = 1;
+  }
   k_assemble<<<blocks_for(d.n_tgt, EW), EW, 0, st>>>(d, h->d_tgt_inst, h->d_Drow);
   launch_factor(h);
   k_ctl_factor<<<1, TPB, 0, st>>>(d, h->cond);
   const long long levels = h->launches - l0;
   h->launches = l0;
-  return 4 + levels;
+  return 4 + rhs + levels;
 }
 
 long long seq_solve(nmpc_handle* h) {
   Dev& d = h->d;
   cudaStream_t st = h->stream;
   const long long l0 = h->launches;
-  k_rhs<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
+  long long rhs = 0;
+  if (!h->side) {  // otherwise computed during the factorization (seq_factor)
+    k_rhs<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
+    rhs = 1;
+  }
   launch_solve(h);
   k_recover<<<blocks_for((long long)d.n + d.m, EW), EW, 0, st>>>(d);
   k_red_dir<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);
   const long long levels = h->launches - l0;
   h->launches = l0;
-  return 3 + levels;
+  return 2 + rhs + levels;
 }
 
 long long seq_trial(nmpc_handle* h) {
