@@ -196,6 +196,7 @@ __device__ void set_conditions(const Dev& d, const CondArgs& ca, int kind) {
 // Stationarity, feasibility and complementarity of the lifted barrier
 // problem (W&B eq. (5)) plus objective, log-barrier and theta sums.
 __device__ void ctl_pre_warp(const Dev& d, int i, int lane, int max_iter);
+__device__ void ctl_post(const Dev& d, int i, Ctl& c, bool write);
 
 __global__ void k_red_eval(Dev d, int max_iter, CondArgs ca) {
   const Chunk ch = d.chunks[blockIdx.x];
@@ -265,6 +266,13 @@ __global__ void k_red_eval(Dev d, int max_iter, CondArgs ca) {
 // (warp 0 of the last chunk block of instance i)
 __device__ void ctl_pre_warp(const Dev& d, int i, int lane, int max_iter) {
   Ctl c = d.ctl[i];
+  if (c.phase == 1) {  // the previous iteration accepted a step
+    ctl_post(d, i, c, lane == 0);
+    if (c.status != ST_RUNNING) {
+      if (lane == 0) d.ctl[i] = c;
+      return;
+    }
+  }
   if (c.status != ST_RUNNING) return;
   // chunk partials: lanes in chunk order, then a fixed shuffle tree
   double v[11] = {0.0, 0.0, 0.0, DBL_MAX, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
@@ -447,13 +455,6 @@ __device__ void recover_row(const Dev& d, int r) {
   d.dbm[r] = mu * ism - d.bm[r] - Qm * dsm;
 }
 
-// variables (threads 0 .. n-1) and rows (n .. n+m-1) in one launch: the rows
-// read dy from the solve's output, not from the variables' copy
-__global__ void k_recover(Dev d) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < d.n) recover_var(d, t);
-  else if (t < d.n + d.m) recover_row(d, t - d.n);
-}
 
 // Fraction-to-the-boundary step limits and grad(phi_mu)^T d.  The limits are
 // tau / max_i(-dv_i / v_i) over components moving toward their bound, with
@@ -467,8 +468,10 @@ __global__ void k_red_dir(Dev d, CondArgs ca) {
     const double mu = c.mu, tau = c.tau;
     double v[3] = {0.0, 0.0, 0.0};  // max primal ratio, max dual ratio, gphi
     const int op[3] = {1, 1, 0};
+    // the chunk's elements are recovered by the threads that reduce them
     if (ch.kind == 0) {
       for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
+        recover_var(d, j);
         const double dy = d.dy[j];
         double gp = d.grad[j];
         if (fin(d.yL[j])) {
@@ -487,6 +490,7 @@ __global__ void k_red_dir(Dev d, CondArgs ca) {
       }
     } else {
       for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
+        recover_row(d, r);
         const double isp = d.isp[r], ism = d.ism[r];
         v[0] = max_nn(v[0], max_nn(-d.dsp[r] * isp, -d.dsm[r] * ism));
         v[1] = max_nn(v[1], max_nn(-d.dbp[r] * d.ibp[r], -d.dbm[r] * d.ibm[r]));
@@ -682,24 +686,24 @@ __global__ void k_update(Dev d) {
   else if (t < d.n + d.m) update_row(d, t - d.n);
 }
 
-__global__ void k_ctl_post(Dev d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n_inst) return;
-  Ctl c = d.ctl[i];
-  if (c.phase != 1) return;
-  if (c.iter <= d.max_iter) {
+// The bookkeeping of the step accepted in the previous iteration (trace
+// record, filter entry on an augmenting step, iteration count), run by the
+// evaluation's control step (ctl_pre_warp) before its tests.
+__device__ void ctl_post(const Dev& d, int i, Ctl& c, bool write) {
+  if (write && c.iter <= d.max_iter) {
     double* t = d.trace + ((size_t)i * (d.max_iter + 2) + c.iter) * 8;
     t[0] = c.mu; t[1] = c.alpha; t[2] = c.alpha_dual; t[3] = c.dw;
     t[4] = c.theta; t[5] = c.phi; t[6] = c.Emu; t[7] = c.ls_trials - c.ls_trials0;
   }
   if (c.augment && c.nf < FILTER_CAP) {
-    d.filt_th[(size_t)i * FILTER_CAP + c.nf] = (1.0 - GAMMA_THETA) * c.theta;
-    d.filt_ph[(size_t)i * FILTER_CAP + c.nf] = c.phi - GAMMA_PHI * c.theta;
+    if (write) {
+      d.filt_th[(size_t)i * FILTER_CAP + c.nf] = (1.0 - GAMMA_THETA) * c.theta;
+      d.filt_ph[(size_t)i * FILTER_CAP + c.nf] = c.phi - GAMMA_PHI * c.theta;
+    }
     c.nf++;
   }
   c.iter++;
   c.phase = 0;
-  d.ctl[i] = c;
 }
 
 // flags[0] = any instance running, [1] = any needs a factorization,

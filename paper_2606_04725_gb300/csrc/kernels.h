@@ -41,12 +41,10 @@ __global__ void k_rows_pre(Dev d, double* Drow);
 __global__ void k_assemble(Dev d, const int* tgt_inst, const double* Drow);
 __global__ void k_ctl_factor(Dev d, CondArgs ca);
 __global__ void k_rhs(Dev d);
-__global__ void k_recover(Dev d);
 __global__ void k_red_dir(Dev d, CondArgs ca);
 __global__ void k_trial_point(Dev d);
 __global__ void k_red_trial(Dev d, CondArgs ca);
 __global__ void k_update(Dev d);
-__global__ void k_ctl_post(Dev d);
 __global__ void k_summary(Dev d, int* flags);
 
 // factor_kernels.cu

@@ -421,11 +421,10 @@ long long seq_solve(nmpc_handle* h) {
     rhs = 1;
   }
   launch_solve(h);
-  k_recover<<<blocks_for((long long)d.n + d.m, EW), EW, 0, st>>>(d);
-  k_red_dir<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);
+  k_red_dir<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);  // recovery, step limits, control
   const long long levels = h->launches - l0;
   h->launches = l0;
-  return 2 + rhs + levels;
+  return 1 + rhs + levels;
 }
 
 long long seq_trial(nmpc_handle* h) {
@@ -440,11 +439,10 @@ long long seq_trial(nmpc_handle* h) {
 
 long long seq_update(nmpc_handle* h) {
   Dev& d = h->d;
-  cudaStream_t st = h->stream;
-  const int ni = h->A.n_inst;
-  k_update<<<blocks_for((long long)d.n + d.m, EW), EW, 0, st>>>(d);
-  k_ctl_post<<<blocks_for(ni), TPB, 0, st>>>(d);
-  return 2;
+  // the step's bookkeeping (trace, filter, count) runs in the next
+  // evaluation's control step
+  k_update<<<blocks_for((long long)d.n + d.m, EW), EW, 0, h->stream>>>(d);
+  return 1;
 }
 
 // Add a conditional node at the current point of a stream capture; the
