@@ -334,9 +334,7 @@ __global__ void k_zero_L(Dev d, const long long* inst_Lbeg, const long long* ins
 // Per row: D_r = Q+ + Q- (the lifted pair's barrier weight) and
 // v_r = (w+ - w-) + (Q+ r4+ - r2+) - (Q- r4- - r2-), so that the condensed
 // right-hand side is -(grad f - mu/(y-yL) + mu/(yU-y) + H^T v).
-__global__ void k_rows_pre(Dev d, double* Drow) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= d.m) return;
+__device__ void rows_pre_at(const Dev& d, double* Drow, int r) {
   const Ctl& c = d.ctl[d.row_inst[r]];
   if (c.status != ST_RUNNING) return;
   const double mu = c.mu, gam = d.mc.gamma;
@@ -346,6 +344,28 @@ __global__ void k_rows_pre(Dev d, double* Drow) {
   const double r4p = d.h[r] - gam + sp, r4m = -d.h[r] - gam + sm;
   const double r2p = d.wp[r] - mu * isp, r2m = d.wm[r] - mu * ism;
   d.rowv[r] = (d.wp[r] - d.wm[r]) + (Qp * r4p - r2p) - (Qm * r4m - r2m);
+}
+
+__global__ void k_rows_pre(Dev d, double* Drow) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < d.m) rows_pre_at(d, Drow, r);
+}
+
+// k_zero_L and k_rows_pre in one launch (both precede the assembly and are
+// independent): blocks 0 .. zx*n_inst-1 zero instance b / zx's panels with zx
+// blocks each, the rest evaluate the rows
+__global__ void k_zero_rows(Dev d, const long long* inst_Lbeg, const long long* inst_Lend, double* Drow, int zx) {
+  const int zb = zx * d.n_inst;
+  if ((int)blockIdx.x < zb) {
+    const int i = blockIdx.x / zx, bx = blockIdx.x % zx;
+    if (!d.ctl[i].need_factor) return;
+    const long long e = inst_Lend[i];
+    for (long long t = inst_Lbeg[i] + bx * (long long)blockDim.x + threadIdx.x; t < e; t += (long long)zx * blockDim.x)
+      d.Lval[t] = 0.0;
+  } else {
+    const int r = (blockIdx.x - zb) * blockDim.x + threadIdx.x;
+    if (r < d.m) rows_pre_at(d, Drow, r);
+  }
 }
 
 // K_c = W + Sigma_y + delta_w I + H^T D H gathered per stored factor entry

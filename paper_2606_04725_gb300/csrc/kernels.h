@@ -38,6 +38,7 @@ __global__ void k_ctl_init(Dev d, double mu0);
 __global__ void k_red_eval(Dev d, int max_iter, CondArgs ca);
 __global__ void k_zero_L(Dev d, const long long* inst_Lbeg, const long long* inst_Lend);
 __global__ void k_rows_pre(Dev d, double* Drow);
+__global__ void k_zero_rows(Dev d, const long long* inst_Lbeg, const long long* inst_Lend, double* Drow, int zx);
 __global__ void k_assemble(Dev d, const int* tgt_inst, const double* Drow);
 __global__ void k_ctl_factor(Dev d, CondArgs ca);
 __global__ void k_rhs(Dev d);

@@ -388,10 +388,10 @@ long long seq_factor(nmpc_handle* h) {
   Dev& d = h->d;
   cudaStream_t st = h->stream;
   const int ni = h->A.n_inst;
-  const dim3 zgrid(std::max(1u, std::min(1024u, blocks_for(h->A.nnzL / std::max(1, ni) + 1))), ni);
+  const int zx = (int)std::max(1u, std::min(1024u, blocks_for(h->A.nnzL / std::max(1, ni) + 1, EW)));
   const long long l0 = h->launches;
-  k_zero_L<<<zgrid, TPB, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend);
-  k_rows_pre<<<blocks_for(d.m, EW), EW, 0, st>>>(d, h->d_Drow);
+  k_zero_rows<<<(unsigned)((long long)zx * ni + blocks_for(d.m, EW)), EW, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend,
+                                                                                    h->d_Drow, zx);
   long long rhs = 0;
   if (h->side) {
     // the solves' right-hand side needs the rows' terms, not the factor:
@@ -408,7 +408,7 @@ long long seq_factor(nmpc_handle* h) {
   k_ctl_factor<<<1, TPB, 0, st>>>(d, h->cond);
   const long long levels = h->launches - l0;
   h->launches = l0;
-  return 4 + rhs + levels;
+  return 3 + rhs + levels;
 }
 
 long long seq_solve(nmpc_handle* h) {
