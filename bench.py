@@ -47,6 +47,26 @@ def _peaks():
         return {}
 
 
+def hbm_rooflines(st, ph, latency_bound=False):
+    """Achieved bandwidth of the HBM-bound phases against the measured copy
+    bandwidth, with algorithmic bytes per iteration: evaluation + assembly move
+    8 (n + 5m) (iterate, slacks, multipliers) + 8 nnz(L) (the panels written,
+    fill included) + 8 n (right-hand side); the two solves read the factor
+    twice, 16 nnz(L).  Times from the phase timing (host-launched, warm)."""
+    peak = _peaks().get("hbm_gbs")
+    n, m, nnz = st["n_total"], st["m_total"], st["nnz_L"]
+    out = {}
+    for name, b, ms in (("eval_assembly", 8.0 * (n + 5 * m) + 8.0 * nnz + 8.0 * n, ph["ms_eval"] + ph["ms_assemble"]),
+                        ("solves", 16.0 * nnz, ph["ms_solve"])):
+        gbs = b / (ms * 1e-3) / 1e9
+        out[name] = {"bound": "hbm", "algorithmic_bytes": b, "ms": ms, "achieved": gbs, "unit": "GB/s",
+                     "peak": peak, "frac": gbs / peak if peak else None,
+                     "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        if latency_bound:
+            out[name]["note"] = "working set L2-resident; latency-bound, not bandwidth-bound"
+    return out
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) during the timed region."""
 
@@ -170,7 +190,8 @@ def plate_factorization(P, dev, peak):
     out = {"workload": "plate_g64_S8_T50", "n": st["n_total"], "max_front": st["max_front"],
            "factor_flops": st["factor_flops"], "factor_ms": ph["ms_factor"], "solve_ms": ph["ms_solve"],
            "factor_tflops": tf, "factor_frac_of_peak": tf / peak,
-           "kernels": "k_big_diag, k_big_trsm, k_big_update (levels of large fronts); k_factor_cluster (small)"}
+           "kernels": "k_big_diag, k_big_trsm, k_big_update (levels of large fronts); k_factor_cluster (small)",
+           "hbm": hbm_rooflines(st, ph)}
     s.close()
     return out
 
@@ -217,6 +238,7 @@ def batch_resolves(P, dev, peak, n_inst=256, resolves=3):
            "instance_resolves_per_s": n_inst * len(ms) / (sum(ms) * 1e-3), "ms_per_batch_resolve": sum(ms) / len(ms),
            "max_ipm_iters_per_batch_resolve": max(iters), "statuses_ok": ok,
            "factor_ms": ph["ms_factor"], "factor_tflops": tf, "factor_frac_of_peak": tf / peak,
+           "hbm": hbm_rooflines(st, ph),
            "autotune": {"seconds": tune_s,
                         "chosen": {"ordering": opts.ordering, "nd_leaf": opts.nd_leaf, "panel_scale": opts.panel_scale},
                         "ms_per_ipm_iter_by_candidate": [
@@ -367,6 +389,7 @@ def main():
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * (N + T + 1), "d2h_bytes_per_step": 8 * n},
             "gpu_launches": int(launches),
             "phases_ms": {k: ph[k] for k in ("ms_eval", "ms_assemble", "ms_factor", "ms_solve")},
+            "hbm": hbm_rooflines(st, ph, latency_bound=True),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": FACTOR_DRAM_BYTES,
                          "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of the 8 level launches of "
