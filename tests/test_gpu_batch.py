@@ -1,4 +1,4 @@
-"""Batched instances (the block-diagonal batch of SURVEY config 4) on the GPU.
+"""Batched instances (a block-diagonal batch of distillation columns with uneven horizons) on the GPU.
 
 Pin: every instance of a batch with uneven horizons (distillation N=34,
 T in {50..200}) reaches the same solution and iteration count as the same
