@@ -131,6 +131,29 @@ def _dist():
     return rank, world, local
 
 
+def rank_seed(wl, rank):
+    """Seed of the column a rank solves: every rank gets its own initial state
+    (instances shard across ranks with no exchange)."""
+    return wl["seed"] + 1000 * rank
+
+
+def max_over_ranks(x, world, device=None):
+    """Largest value of x over the ranks (the job takes as long as its slowest
+    rank); x itself when there is one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds, world, device=None):
+    """Units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(seconds, world, device)
+
+
 def run_oracle_loop(wl, budget_s, max_steps=None, skip_cold=True):
     """The oracle's closed loop on the same workload (CPU baseline)."""
     import oracle as O
@@ -281,7 +304,7 @@ def main():
     P.build()
     wl = I.WORKLOADS[WORKLOAD]
     N, Nf, T = wl["N"], wl["Nf"], wl["T"]
-    seed = wl["seed"] + 1000 * rank
+    seed = rank_seed(wl, rank)
     x0 = I.distillation_x0(N, Nf, seed)
     a, b = I.distillation_setpoints(N, wl["seed"])
     opts = P.options(use_graph=0) if args.host_loop else None
@@ -327,12 +350,8 @@ def main():
     wall = time.perf_counter() - wall0
     launches = s.stats()["kernel_launches"] - launches0
     ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    tot_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms * 1e-3)
+    tot_ms = max_over_ranks(sum(ms), world, dev)
+    value = whole_job_rate(args.steps, tot_ms * 1e-3, world, dev)
     ms_iter = tot_ms / max(1, sum(iters))
 
     # end to end: host inputs (pinned), host result, copies inside the timed region
@@ -342,6 +361,8 @@ def main():
     hy = torch.empty(n, dtype=torch.float64).pin_memory()
     s.get_solution(0, out=(hy, None))
     e2e_steps = min(args.steps, 20)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for q in range(e2e_steps):
@@ -352,7 +373,7 @@ def main():
         s.solve(warm=True)
         s.get_solution(0, out=(hy.numpy(), None))
     torch.cuda.synchronize()
-    e2e = e2e_steps / (time.perf_counter() - t0) * world
+    e2e = whole_job_rate(e2e_steps, time.perf_counter() - t0, world, dev)
 
     # rebuild-every-solve comparison (paper Base / WS): destroy + build + bind + solve
     rb = {}
