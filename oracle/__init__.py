@@ -44,6 +44,7 @@ class _Problem(C.Structure):
                 ("g", C.c_int), ("S", C.c_int), ("dt", C.c_double),
                 ("alpha", C.c_double), ("D", C.c_double), ("F", C.c_double), ("xF", C.c_double),
                 ("Ac", C.c_double), ("At", C.c_double), ("Ar", C.c_double), ("wdu", C.c_double),
+                ("wu", C.c_double), ("ubar", C.c_double),
                 ("kappa", C.c_double), ("cq", C.c_double), ("rho_u", C.c_double),
                 ("xlo", C.c_double), ("xhi", C.c_double), ("ulo", C.c_double), ("uhi", C.c_double),
                 ("x0", C.POINTER(C.c_double)), ("sp", C.POINTER(C.c_double)), ("uprev", C.c_double)]
@@ -108,13 +109,14 @@ class Problem:
     """One transcribed OCP instance (keeps its parameter arrays alive)."""
 
     def __init__(self, model, T, dt, x0, sp, *, N=0, Nf=0, g=0, S=0, uprev=0.0,
-                 alpha=1.6, D=0.2, F=0.4, xF=0.5, Ac=1.0, At=1.0, Ar=1.0, wdu=0.01,
+                 alpha=1.6, D=0.2, F=0.4, xF=0.5, Ac=1.0, At=1.0, Ar=1.0, wdu=0.01, wu=0.0, ubar=0.0,
                  kappa=0.01, cq=0.01, rho_u=1e-3, xlo=0.0, xhi=1.0, ulo=1.0, uhi=5.0):
         self.x0 = np.ascontiguousarray(x0, dtype=np.float64)
         self.sp = np.ascontiguousarray(sp, dtype=np.float64)
         p = _Problem()
         p.model, p.T, p.dt, p.N, p.Nf, p.g, p.S = model, T, dt, N, Nf, g, S
         p.alpha, p.D, p.F, p.xF, p.Ac, p.At, p.Ar, p.wdu = alpha, D, F, xF, Ac, At, Ar, wdu
+        p.wu, p.ubar = wu, ubar
         p.kappa, p.cq, p.rho_u = kappa, cq, rho_u
         p.xlo, p.xhi, p.ulo, p.uhi = xlo, xhi, ulo, uhi
         p.uprev = uprev

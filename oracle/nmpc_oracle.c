@@ -148,7 +148,7 @@ int or_hessian(const or_problem* p, const double* y, const double* lam,
     int ox = or_off_x(p, t), ou = or_off_u(p, t);
     if (p->model == OR_DISTILL) {
       k = push_trip(rows, cols, vals, cap, k, ox, ox, 2.0 * p->dt);
-      k = push_trip(rows, cols, vals, cap, k, ou, ou, 2.0 * p->wdu);
+      k = push_trip(rows, cols, vals, cap, k, ou, ou, 2.0 * p->wdu + 2.0 * p->wu * p->dt);
       if (t > 1) {
         int oup = or_off_u(p, t - 1);
         k = push_trip(rows, cols, vals, cap, k, oup, oup, 2.0 * p->wdu);

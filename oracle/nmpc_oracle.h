@@ -33,6 +33,7 @@ typedef struct {
   int g, S;           /* plate: grid side, actuator segments */
   double dt;
   double alpha, D, F, xF, Ac, At, Ar, wdu; /* distillation constants */
+  double wu, ubar;    /* distillation: weight of the control-tracking cost (u - ubar)^2 per unit time */
   double kappa, cq, rho_u;                 /* plate constants */
   double xlo, xhi, ulo, uhi;               /* bounds on x_1..x_T, u_1..u_T (+-inf allowed) */
   const double* x0;   /* nx: initial state parameter */

@@ -148,7 +148,7 @@ def test_distillation_N12_closed_loop(P, oracle):
 
 
 def test_distillation_N34_T200_resolves(P, oracle):
-    """Config-2 size: cold solve plus warm re-solves across a setpoint switch."""
+    """Distillation N=34, T=200: cold solve plus warm re-solves across a setpoint switch."""
     T = 200
     x0 = I.distillation_x0(34, 17, seed=2)
     a, b = I.distillation_setpoints(34, seed=2)

@@ -248,7 +248,7 @@ def test_toy_code_listing_problem_converges(oracle):
 
 
 def test_distillation_closed_loop_small(oracle):
-    """Config-1-sized column (N=12, feed tray 5, T=20): a cold solve and four
+    """A small column (N=12, feed tray 5, T=20): a cold solve and four
     warm re-solves, each converged with FD-stationary primal-dual point."""
     O = oracle
     N, Nf, T = 12, 5, 20
@@ -265,3 +265,22 @@ def test_distillation_closed_loop_small(oracle):
         assert info["status"] == 0 and info["iters"] < 20
     r = _fd_stationarity(O, p, st)
     assert np.max(np.abs(r)) < 1e-5
+
+
+def test_paper_distillation_at_steady_state_stays_there(oracle):
+    """The paper's column and cost (Sec. 4.1: N = 32, N_f = 17, holdups
+    0.5 / 0.25 / 1.0, dt = 2, 90 intervals, cost (x_1 - xbar)^2 + 0.1 (u - ubar)^2).
+    Started at the steady state of ubar with xbar its tray-1 value, the
+    constant trajectory has zero cost and is feasible, so it is the optimum:
+    the solver must return u = ubar and x = the steady state at every stage."""
+    O = oracle
+    N, Nf, T, ubar = 32, 17, 90, 2.51459
+    kw = dict(dt=2.0, Ac=0.5, At=0.25, Ar=1.0, wdu=0.0, wu=0.1, ubar=ubar)
+    xs = O.steady_state(O.distillation(N, Nf, 1, np.zeros(N), np.zeros(1), ubar), ubar)
+    p = O.distillation(N, Nf, T, xs, np.full(T, xs[0]), ubar, **kw)
+    st, info, _ = O.solve(p)
+    assert info["status"] == 0
+    u = np.array([st.y[p.off_u(k)] for k in range(1, T + 1)])
+    X = np.stack([st.y[p.off_x(k):p.off_x(k) + N] for k in range(1, T + 1)])
+    assert np.max(np.abs(u - ubar)) < 1e-6
+    assert np.max(np.abs(X - xs)) < 1e-6

@@ -36,6 +36,7 @@ def _interior_point(prob, seed=5):
 
 def _models(O):
     return [("distill", _distill(O)), ("distill_paper_holdups", _distill(O, Ac=0.5, At=0.25, Ar=1.0)),
+            ("distill_paper_cost", _distill(O, Ac=0.5, At=0.25, Ar=1.0, wdu=0.0, wu=0.1, ubar=2.51459)),
             ("plate", _plate(O)), ("toy", _toy(O))]
 
 
@@ -183,3 +184,19 @@ def test_objective_closed_forms(oracle):
         y[q.off_u(k):q.off_u(k) + 4] = 2.0
     f, _, _, _ = oracle.evaluate(q, y)
     assert abs(f - (2 * 0.5 * 0.25 + 2 * 1e-3 * 0.5 * 4 * 4.0)) < 1e-14
+
+
+def test_paper_control_cost_is_the_integral_for_a_constant_control(oracle):
+    """Eq. (distill-ocp) integrates 0.1 (u - ubar)^2 over the prediction
+    horizon: for a constant control c and states on the setpoint the cost is
+    0.1 (c - ubar)^2 t_p, with t_p = T dt (Sec. 4.1: t_p = 180 s, dt = 2 s)."""
+    N, T, dt, ubar = 5, 90, 2.0, 2.51459
+    sp = np.linspace(0.5, 0.9, T)
+    p = oracle.distillation(N, 2, T, np.zeros(N), sp, uprev=3.0, dt=dt, wdu=0.0, wu=0.1, ubar=ubar)
+    for c in (1.0, 2.51459, 4.2):
+        y = np.zeros(p.n)
+        for k in range(1, T + 1):
+            y[p.off_x(k)] = sp[k - 1]
+            y[p.off_u(k)] = c
+        f, _, _, _ = oracle.evaluate(p, y)
+        assert abs(f - 0.1 * (c - ubar) ** 2 * 180.0) < 1e-12 * max(1.0, f), (c, f)
