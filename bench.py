@@ -275,6 +275,50 @@ def batch_resolves(P, dev, peak, n_inst=256, resolves=3):
     return out
 
 
+def paper_column_resolves(P, dev, resolves=40, warmup=3):
+    """The paper's own column and cost (N = 32, feed tray 17, holdups 0.5 /
+    0.25 / 1.0, dt = 2, 90 intervals, (x_1 - xbar)^2 + 0.1 (u - ubar)^2):
+    warm re-solves of its closed loop with inputs resident on the device,
+    each timed with CUDA events on the library stream.  The paper's figure
+    for this workload is its per-step GPU solve time with warm start and
+    parameter update, on other hardware (context, not a target)."""
+    import torch
+    import paper_2606_04725_gb300.inputs as I
+    wl = I.WORKLOADS["paper_distillation_N32_T90"]
+    N, Nf, T = wl["N"], wl["Nf"], wl["T"]
+    s = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev, **I.PAPER_COLUMN)
+    n = s.dims[0][0]
+    ox1, ou1 = N, 2 * N
+    sp = torch.full((T,), I.PAPER_XBAR, dtype=torch.float64, device=dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    s.set_params(x0=I.distillation_x0(N, Nf, wl["seed"]), setpoint=np.full(T, I.PAPER_XBAR),
+                 u_prev=np.array([I.U_REF]))
+    first = s.solve(warm=False)[0]
+    s.get_solution(0, out=(y, None))
+    stream = s.stream
+    ms, iters, ok = [], [], first["status"] == 0
+    for q in range(warmup + resolves):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.set_params(x0=y[ox1:ox1 + N], setpoint=sp, u_prev=y[ou1:ou1 + 1])
+        inf = s.solve(warm=True)[0]
+        s.get_solution(0, out=(y, None))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ok = ok and inf["status"] == 0
+        if q >= warmup:
+            ms.append(e0.elapsed_time(e1))
+            iters.append(inf["iters"])
+    out = {"workload": "paper_distillation_N32_T90", "n": n, "resolves_per_s": len(ms) / (sum(ms) * 1e-3),
+           "ms_per_resolve": sum(ms) / len(ms), "ms_per_ipm_iter": sum(ms) / max(1, sum(iters)),
+           "ipm_iters_per_resolve": sum(iters) / len(iters), "cold_solve_iters": first["iters"],
+           "statuses_ok": ok,
+           "paper_gpu_ws_pu_s_per_step": {"value": 0.02, "hardware": "RTX 6000 Ada (MadNLP + cuDSS)",
+                                          "note": "context only: other hardware and software"}}
+    s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -285,6 +329,7 @@ def main():
     ap.add_argument("--rebuild-steps", type=int, default=3)
     ap.add_argument("--no-plate", action="store_true", help="skip the full-size heated-plate factorization")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch")
+    ap.add_argument("--no-paper-column", action="store_true", help="skip the paper's own column (N=32, T=90)")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the interior-point loop from the host instead of the conditional graph "
                          "(same kernels; for profilers that cannot see into conditional graphs)")
@@ -427,6 +472,8 @@ def main():
         line["plate_full_size"] = plate_factorization(P, dev, peak)
     if not args.no_batch:
         line["batch_256"] = batch_resolves(P, dev, peak)
+    if not args.no_paper_column:
+        line["paper_column"] = paper_column_resolves(P, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         times, its = run_oracle_loop(wl, budget_s=20.0)
         line["cpu_baseline"] = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",

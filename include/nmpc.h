@@ -80,6 +80,9 @@ typedef struct {
   double alpha, D, F, xF, Ac, At, Ar, wdu; /* distillation constants */
   double kappa, cq, rho_u;                 /* plate constants */
   double xlo, xhi, ulo, uhi;               /* bounds of x_1..x_T and u_1..u_T (+-INFINITY allowed) */
+  double wu, ubar;       /* distillation: control-tracking stage cost wu dt (u_k - ubar)^2, the
+                            0.1 (u - ubar)^2 integrand of eq. (distill-ocp), Sec. 4.1, by the
+                            rectangle rule; wu = 0 (default) leaves it out */
 } nmpc_problem;
 
 /* Solver options.  Defaults from nmpc_options_defaults. */

@@ -38,7 +38,8 @@ class Problem(C.Structure):
                 ("alpha", C.c_double), ("D", C.c_double), ("F", C.c_double), ("xF", C.c_double),
                 ("Ac", C.c_double), ("At", C.c_double), ("Ar", C.c_double), ("wdu", C.c_double),
                 ("kappa", C.c_double), ("cq", C.c_double), ("rho_u", C.c_double),
-                ("xlo", C.c_double), ("xhi", C.c_double), ("ulo", C.c_double), ("uhi", C.c_double)]
+                ("xlo", C.c_double), ("xhi", C.c_double), ("ulo", C.c_double), ("uhi", C.c_double),
+                ("wu", C.c_double), ("ubar", C.c_double)]
 
 
 class Options(C.Structure):

@@ -206,9 +206,9 @@ __device__ void eval_var_obj(const Dev& d, const double* y, int v, double* fshar
         gr = 2.0 * dt * e;
       } else if (q == nx) {
         const double up = (k == 1) ? d.p_uprev[i] : yi[offu(mc, k - 1)];
-        const double du = yi[lv] - up;
-        f = mc.wdu * du * du;
-        gr = 2.0 * mc.wdu * du;
+        const double du = yi[lv] - up, eu = yi[lv] - mc.ubar;
+        f = mc.wdu * du * du + mc.wu * dt * eu * eu;
+        gr = 2.0 * mc.wdu * du + 2.0 * mc.wu * dt * eu;
         if (k < T) gr -= 2.0 * mc.wdu * (yi[offu(mc, k + 1)] - yi[lv]);
       }
     } else if (mc.model == MODEL_PLATE) {
@@ -284,7 +284,7 @@ __device__ void eval_var_hess(const Dev& d, int v) {
     W[q] = wdiag;
     W[N + q] = wux;
   } else {
-    W[2 * N] = 2.0 * mc.wdu * (k < T ? 2.0 : 1.0);
+    W[2 * N] = 2.0 * mc.wdu * (k < T ? 2.0 : 1.0) + 2.0 * mc.wu * dt;
     W[2 * N + 1] = (k >= 2) ? -2.0 * mc.wdu : 0.0;
   }
 }

@@ -604,6 +604,7 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   sp.Ac = prob->Ac; sp.At = prob->At; sp.Ar = prob->Ar; sp.wdu = prob->wdu;
   sp.kappa = prob->kappa; sp.cq = prob->cq; sp.rho_u = prob->rho_u;
   sp.xlo = prob->xlo; sp.xhi = prob->xhi; sp.ulo = prob->ulo; sp.uhi = prob->uhi;
+  sp.wu = prob->wu; sp.ubar = prob->ubar;
   sp.gamma = h->opt.gamma; sp.tol = h->opt.tol;
   sp.ordering = h->opt.ordering; sp.nd_leaf = h->opt.nd_leaf; sp.pivtol = h->opt.pivtol;
   if (!(prob->dt > 0) || h->opt.max_iter < 1 || !(h->opt.tol > 0) || !(h->opt.gamma > 0)) {

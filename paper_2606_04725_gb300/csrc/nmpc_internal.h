@@ -57,6 +57,7 @@ struct ModelConst {
   int model, nx, nu, N, Nf, g, S, WH, WS;
   double dt, alpha, D, F, xF, Ac, At, Ar, wdu, kappa, cq, rho_u;
   double xlo, xhi, ulo, uhi;
+  double wu, ubar;                    // control-tracking cost wu dt (u - ubar)^2 (distillation)
   double inv_Ac, inv_At, inv_Ar;      // 1/holdups (distillation), computed once on the host
   double gamma, tol, pivtol;
 };

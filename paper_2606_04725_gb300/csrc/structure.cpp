@@ -330,6 +330,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
     mc.Ac = sp.Ac; mc.At = sp.At; mc.Ar = sp.Ar; mc.wdu = sp.wdu;
     mc.kappa = sp.kappa; mc.cq = sp.cq; mc.rho_u = sp.rho_u;
     mc.xlo = sp.xlo; mc.xhi = sp.xhi; mc.ulo = sp.ulo; mc.uhi = sp.uhi;
+    mc.wu = sp.wu; mc.ubar = sp.ubar;
     mc.inv_Ac = 1.0 / sp.Ac; mc.inv_At = 1.0 / sp.At; mc.inv_Ar = 1.0 / sp.Ar;
     mc.gamma = sp.gamma; mc.tol = sp.tol; mc.pivtol = sp.pivtol;
     const int nx = mc.nx, nu = mc.nu, WH = mc.WH, WS = mc.WS;

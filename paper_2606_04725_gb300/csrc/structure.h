@@ -19,6 +19,7 @@ struct ProblemSpec {
   double alpha = 1.6, D = 0.2, F = 0.4, xF = 0.5, Ac = 1, At = 1, Ar = 1, wdu = 0.01;
   double kappa = 0.01, cq = 0.01, rho_u = 1e-3;
   double xlo = 0, xhi = 1, ulo = 1, uhi = 5;
+  double wu = 0, ubar = 0;
   double gamma = 1e-8, tol = 1e-8, pivtol = 1e-12;
   int ordering = 0;  // 0 auto, 1 natural, 2 nested dissection
   int nd_leaf = 1;

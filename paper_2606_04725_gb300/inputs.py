@@ -13,6 +13,11 @@ Recipes (one per workload):
                 closed loop switching between them every 10 re-solves.
   batched       256 columns with N = 34, horizons U{50..200}, per-instance
                 seeds for noise and setpoint U[0.90, 0.99].
+  paper column  the paper's own column (Sec. 4.1, table distill-params):
+                N = 32, feed tray 17, holdups 0.5 / 0.25 / 1.0, dt = 2,
+                90 intervals (180 s prediction horizon), stage cost
+                (x_1 - 0.8958)^2 + 0.1 (u - 2.51459)^2 per unit time;
+                x0 as for the other columns (steady state plus noise).
   plate         target field = sum of 3 Gaussian bumps with amplitude
                 U[0.3, 0.8], centre U[0.2, 0.8]^2, width U[0.08, 0.2];
                 initial field 0.
@@ -90,4 +95,10 @@ WORKLOADS = {
     "batch256_distillation_N34_T50_200": dict(model=0, N=34, Nf=17, n_instances=256, T_lo=50, T_hi=200,
                                               resolves=50, seed=4),
     "plate_g128_S16_T100": dict(model=1, g=128, S=16, T=100, resolves=20, seed=5),
+    "paper_distillation_N32_T90": dict(model=0, N=32, Nf=17, T=90, resolves=150, seed=6),
 }
+
+# The paper's column: problem constants (keyword names of nmpc_problem and
+# of the oracle's problem) and the tray-1 setpoint of its parameter table.
+PAPER_COLUMN = dict(dt=2.0, Ac=0.5, At=0.25, Ar=1.0, wdu=0.0, wu=0.1, ubar=U_REF)
+PAPER_XBAR = 0.8958

@@ -166,6 +166,26 @@ def test_distillation_N34_T200_resolves(P, oracle):
         prob.set_params(x0=st_or.y[prob.off_x(1):prob.off_x(1) + 34].copy(), uprev=uprev)
 
 
+def test_paper_distillation_closed_loop(P, oracle):
+    """The paper's own column (Sec. 4.1: N = 32, feed tray 17, holdups
+    0.5 / 0.25 / 1.0, dt = 2, 90 intervals, stage cost (x_1 - xbar)^2 +
+    0.1 (u - ubar)^2): a cold solve and four warm re-solves of the closed loop."""
+    N, Nf, T = 32, 17, 90
+    x0 = I.distillation_x0(N, Nf, seed=6)
+    sp = np.full(T, I.PAPER_XBAR)
+    prob = oracle.distillation(N, Nf, T, x0, sp, I.U_REF, **I.PAPER_COLUMN)
+    s = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, opts=P.options(ordering=NATURAL), **I.PAPER_COLUMN)
+    st_or, uprev = None, I.U_REF
+    for k in range(5):
+        s.set_params(x0=prob.x0.copy(), setpoint=sp, u_prev=np.array([uprev]))
+        spread = _oracle_spread(oracle, prob, state=st_or, warm=k > 0)
+        st_or, info_or, tr = oracle.solve(prob, state=st_or, warm=k > 0)
+        info = s.solve(warm=k > 0)[0]
+        _compare(oracle, prob, s, 0, st_or, info_or, info, spread=spread, tr_or=tr)
+        uprev = st_or.y[prob.off_u(1)]
+        prob.set_params(x0=st_or.y[prob.off_x(1):prob.off_x(1) + N].copy(), uprev=uprev)
+
+
 def test_toy_code_listing_problem(P, oracle):
     T = 14
     dt = 10.0 / T

@@ -28,12 +28,48 @@ def test_library_exports_every_declared_symbol(P):
     assert declared == set(P._lib.EXPORTED)
 
 
+def _header_struct_fields(header, name):
+    """Field names, in order, of `typedef struct { ... } name;` in the header."""
+    end = re.search(r"\}\s*" + name + r";", header).start()
+    body = header[header.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "double a, b, c" / "const int* horizons" / "struct {...} cand[16]"
+        parts = decl.split(",")
+        names.append(re.findall(r"\w+", parts[0])[-1])
+        names.extend(re.findall(r"\w+", p)[-1] for p in parts[1:])
+    return names
+
+
+def test_binding_structs_mirror_the_header(P):
+    """The ctypes structures lay out nmpc_problem, nmpc_options, nmpc_info
+    and nmpc_stats field by field as the header declares them."""
+    header = open(os.path.join(ROOT, "include", "nmpc.h")).read()
+    L = P._lib
+    for cname, pyst in (("nmpc_problem", L.Problem), ("nmpc_options", L.Options),
+                        ("nmpc_info", L.Info), ("nmpc_stats", L.Stats)):
+        assert _header_struct_fields(header, cname) == [f[0] for f in pyst._fields_], cname
+
+
+def test_problem_defaults_leave_the_control_tracking_cost_out(P):
+    import ctypes as C
+    p = P._lib.Problem()
+    P.lib().nmpc_problem_defaults(0, C.byref(p))
+    assert (p.wu, p.ubar, p.wdu, p.dt, p.N, p.Nf) == (0.0, 0.0, 0.01, 1.0, 12, 5)
+
+
 CASES = [
     ("distill_nd", dict(model=0, horizons=[20], N=12, Nf=5), dict(ordering=2)),
     ("distill_nat", dict(model=0, horizons=[20], N=12, Nf=5), dict(ordering=1)),
     ("distill_batch", dict(model=0, horizons=[3, 7, 5], N=6, Nf=3), dict(ordering=0)),
     ("plate", dict(model=1, horizons=[4], g=8, S=8), dict(ordering=2)),
     ("toy", dict(model=2, horizons=[14]), dict(ordering=2)),
+    ("distill_paper", dict(model=0, horizons=[90], N=32, Nf=17, dt=2.0, Ac=0.5, At=0.25, Ar=1.0, wdu=0.0,
+                           wu=0.1, ubar=2.51459), dict(ordering=2)),
 ]
 
 
