@@ -267,9 +267,10 @@ def batch_resolves(P, dev, peak, n_inst=256, resolves=3):
            "factor_ms": ph["ms_factor"], "factor_tflops": tf, "factor_frac_of_peak": tf / peak,
            "hbm": hbm_rooflines(st, ph),
            "autotune": {"seconds": tune_s,
-                        "chosen": {"ordering": opts.ordering, "nd_leaf": opts.nd_leaf, "panel_scale": opts.panel_scale},
+                        "chosen": {"ordering": opts.ordering, "nd_leaf": opts.nd_leaf, "panel_scale": opts.panel_scale,
+                                   "amalgamation": opts.amalgamation},
                         "ms_per_ipm_iter_by_candidate": [
-                            [c["ordering"], c["nd_leaf"], c["panel_scale"], round(c["ms_per_iter"], 3)]
+                            [c["ordering"], c["nd_leaf"], c["panel_scale"], c["amalgamation"], round(c["ms_per_iter"], 3)]
                             for c in rep["candidates"]]}}
     s.close()
     return out

@@ -112,6 +112,14 @@ typedef struct {
                                its inverse: one dense product per block and solve;
                             2: the diagonal blocks only: two products per block;
                             3: no transform: column-by-column substitution */
+  int amalgamation;      /* relaxed amalgamation of fundamental supernodes (Sec. 3.2.3 supernodes):
+                            0: automatic (default);
+                            1: relaxed: a supernode whose columns end right before its parent's
+                               merges into it while the merged panel's explicit zeros stay
+                               under a limit that falls with the panel's width;
+                            2: sibling-limited: as 1, but a supernode whose parent has other
+                               children merges only into a panel of at most 16 columns, so
+                               the separators of nested dissection stay separate fronts */
 } nmpc_options;
 
 /* Per-instance result of a solve.  Times are measured with CUDA events on
@@ -276,15 +284,17 @@ nmpc_status nmpc_solve_static(const nmpc_problem* prob, const nmpc_options* opts
  * Autotuner (the batch path's tuning of the supernodal schedule; not in the
  * paper).  The symbolic analysis and the kernels' schedule depend on options
  * the problem does not fix: the ordering (nested dissection with leaves of
- * 1, 2 or 4 stages; stage order for short horizons) and the solve form
- * (panel_scale 1 or 3).  nmpc_autotune builds every candidate (reusing
+ * 1, 2 or 4 stages; stage order for short horizons), the supernode
+ * amalgamation under nested dissection (amalgamation 1 or 2) and the solve
+ * form (panel_scale 1 or 3).  nmpc_autotune builds every candidate (reusing
  * those nmpc_autotune_workspace_bytes just built for the same problem),
  * binds it to the caller's workspace, runs one cold solve of the given
  * parameters and, if every instance converged, times one iteration's
  * evaluation, assembly, factorization and solves at that point (as
  * nmpc_time_phases); the rest of an iteration is the same for every
  * candidate.  It keeps the fastest candidate and writes its ordering,
- * nd_leaf and panel_scale into *opts (the other fields are kept).
+ * nd_leaf, amalgamation and panel_scale into *opts (the other fields are
+ * kept).
  * Results are cached per problem (model, sizes, horizons, constants) and
  * remaining options for the life of the process: a repeated call returns
  * the cached choice without running anything.
@@ -305,6 +315,7 @@ typedef struct {
   int status;            /* of the cold solve (NMPC_ERR_WORKSPACE: skipped, too large) */
   int iters;             /* largest over instances */
   double ms_per_iter;    /* evaluation + assembly + factorization + solves at the converged point */
+  int amalgamation;      /* nmpc_options.amalgamation of the candidate */
 } nmpc_tune_candidate;
 typedef struct {
   int n_candidates, best, cached;

@@ -47,7 +47,7 @@ class Options(C.Structure):
                 ("push_cold", C.c_double), ("push_warm", C.c_double), ("max_iter", C.c_int),
                 ("ordering", C.c_int), ("nd_leaf", C.c_int), ("use_graph", C.c_int), ("spin_limit", C.c_longlong),
                 ("pivtol", C.c_double), ("factor_mode", C.c_int), ("solve_mode", C.c_int),
-                ("panel_scale", C.c_int)]
+                ("panel_scale", C.c_int), ("amalgamation", C.c_int)]
 
 
 class Info(C.Structure):
@@ -70,7 +70,7 @@ class PhaseTimes(C.Structure):
 
 class TuneCandidate(C.Structure):
     _fields_ = [("ordering", C.c_int), ("nd_leaf", C.c_int), ("panel_scale", C.c_int), ("status", C.c_int),
-                ("iters", C.c_int), ("ms_per_iter", C.c_double)]
+                ("iters", C.c_int), ("ms_per_iter", C.c_double), ("amalgamation", C.c_int)]
 
 
 TUNE_MAX = 16

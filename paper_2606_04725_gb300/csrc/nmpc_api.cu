@@ -607,6 +607,7 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   sp.wu = prob->wu; sp.ubar = prob->ubar;
   sp.gamma = h->opt.gamma; sp.tol = h->opt.tol;
   sp.ordering = h->opt.ordering; sp.nd_leaf = h->opt.nd_leaf; sp.pivtol = h->opt.pivtol;
+  sp.amalgamation = h->opt.amalgamation;
   if (!(prob->dt > 0) || h->opt.max_iter < 1 || !(h->opt.tol > 0) || !(h->opt.gamma > 0)) {
     delete h;
     return NMPC_ERR_INVALID;
@@ -1446,18 +1447,21 @@ std::vector<nmpc_options> tune_candidates(const nmpc_problem* p, const nmpc_opti
   std::vector<nmpc_options> c;
   for (int form : {1, 3}) {
     if (Tmax >= 8)
-      for (int leaf : {1, 2, 4}) {
-        nmpc_options o = base;
-        o.ordering = NMPC_ORDER_ND;
-        o.nd_leaf = leaf;
-        o.panel_scale = form;
-        c.push_back(o);
-      }
+      for (int leaf : {1, 2, 4})
+        for (int am : {1, 2}) {
+          nmpc_options o = base;
+          o.ordering = NMPC_ORDER_ND;
+          o.nd_leaf = leaf;
+          o.panel_scale = form;
+          o.amalgamation = am;
+          c.push_back(o);
+        }
     if (Tmax < 32) {  // a chain of at most 31 stages: its depth is no worse than a tree's
       nmpc_options o = base;
       o.ordering = NMPC_ORDER_NATURAL;
       o.nd_leaf = 1;
       o.panel_scale = form;
+      o.amalgamation = 1;  // a chain: both modes give the same partition
       c.push_back(o);
     }
   }
@@ -1472,6 +1476,7 @@ std::string tune_key(const nmpc_problem* p, const nmpc_options* o) {
   r.ordering = 0;
   r.nd_leaf = 0;
   r.panel_scale = 0;
+  r.amalgamation = 0;
   std::string k(reinterpret_cast<const char*>(&q), sizeof(q));
   k.append(reinterpret_cast<const char*>(p->horizons), sizeof(int) * (size_t)p->n_instances);
   k.append(reinterpret_cast<const char*>(&r), sizeof(r));
@@ -1550,6 +1555,7 @@ nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cu
         opts->ordering = e.second.ordering;
         opts->nd_leaf = e.second.nd_leaf;
         opts->panel_scale = e.second.panel_scale;
+        opts->amalgamation = e.second.amalgamation;
         if (report) report->cached = 1;
         return NMPC_OK;
       }
@@ -1571,7 +1577,8 @@ nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cu
   nmpc_status first_fail = NMPC_OK;
   std::vector<nmpc_info> info(prob->n_instances);
   for (size_t c = 0; c < cand.size() && (int)c < NMPC_TUNE_MAX; ++c) {
-    nmpc_tune_candidate rc{cand[c].ordering, cand[c].nd_leaf, cand[c].panel_scale, NMPC_ERR_WORKSPACE, 0, 0.0};
+    nmpc_tune_candidate rc{cand[c].ordering, cand[c].nd_leaf, cand[c].panel_scale, NMPC_ERR_WORKSPACE, 0, 0.0,
+                           cand[c].amalgamation};
     nmpc_handle* h = built.empty() ? nullptr : built[c];
     nmpc_status st = NMPC_OK;
     if (h) h->stream = static_cast<cudaStream_t>(cuda_stream);  // built without a stream
@@ -1617,6 +1624,7 @@ nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cu
   opts->ordering = cand[best].ordering;
   opts->nd_leaf = cand[best].nd_leaf;
   opts->panel_scale = cand[best].panel_scale;
+  opts->amalgamation = cand[best].amalgamation;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache.emplace_back(key, *opts);
   return NMPC_OK;

@@ -136,8 +136,15 @@ std::vector<int> etree(int n, const std::vector<std::vector<int>>& lower_rows) {
   return parent;
 }
 
+// Sibling-limited amalgamation (mode 2) merges a supernode into a parent that
+// has other children only while the merged panel stays this narrow.
+constexpr int AMALG_SIBLING_COLS = 16;
+// Automatic amalgamation chooses the sibling-limited mode when no front of the
+// relaxed partition has more rows than this.
+constexpr int AUTO_SMALL_FRONT_ROWS = 128;
+
 void symbolic_instance(int n, const std::vector<std::pair<int, int>>& lower_edges,
-                       const std::vector<int>& order, InstSym& out) {
+                       const std::vector<int>& order, int amalg, InstSym& out) {
   // order[q] = local variable eliminated q-th
   std::vector<int> pos(n);
   for (int q = 0; q < n; ++q) pos[order[q]] = q;
@@ -222,6 +229,8 @@ void symbolic_instance(int n, const std::vector<std::pair<int, int>>& lower_edge
     rowsz[s] = count[ff[s]];
   }
   std::vector<char> merged(nf, 0);
+  std::vector<int> nch(nf, 0);   // children of each (possibly merged) supernode
+  for (int s = 0; s < nf; ++s) if (fpar[s] >= 0) nch[fpar[s]]++;
   auto stored = [](long long c, long long r) { return c * r - c * (c - 1) / 2; };
   for (int s = 0; s < nf; ++s) {
     const int p = fpar[s];
@@ -232,7 +241,9 @@ void symbolic_instance(int n, const std::vector<std::pair<int, int>>& lower_edge
     const double zf = double(st - nz) / double(st);
     const double lim = c <= 4 ? 0.8 : (c <= 16 ? 0.5 : (c <= 48 ? 0.35 : (c <= 128 ? 0.15 : 0.05)));
     if (zf > lim) continue;
+    if (amalg == 2 && nch[p] > 1 && c > AMALG_SIBLING_COLS) continue;
     merged[s] = 1;
+    nch[p] += nch[s] - 1;
     gfirst[p] = gfirst[s];
     gcols[p] = (int)c;
     rowsz[p] = (int)r;
@@ -311,6 +322,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
   try {
     const int ni = (int)sp.T.size();
     if (ni < 1) return "n_instances must be >= 1";
+    if (sp.amalgamation < 0 || sp.amalgamation > 2) return "amalgamation must be 0, 1 or 2";
     ModelConst& mc = A.mc;
     mc = ModelConst{};
     mc.model = sp.model;
@@ -421,6 +433,12 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
     // per distinct horizon, for the first instance that has it, on several
     // host threads, and the other instances copy it.
     auto ord_of = [&](int T) { return sp.ordering != 0 ? sp.ordering : (T < 8 ? 1 : 2); };  // short horizons: a chain
+    // Automatic amalgamation: relaxed, unless every front of the relaxed
+    // partition has at most AUTO_SMALL_FRONT_ROWS rows.  Such fronts are
+    // factored in shared memory, and their time is set by the chain of
+    // pivots of the widest front of each level, not by flops: there the
+    // separators of nested dissection are kept apart (sibling-limited), so
+    // that no level waits on a separator merged with one below it.
     std::vector<int> rep_of(ni), reps;
     {
       std::vector<std::pair<int, int>> firsts;  // (T, first instance), sorted by T
@@ -493,7 +511,14 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
         order = nd.order;
         if ((int)order.size() != nl) throw std::runtime_error("nested dissection lost vertices");
       }
-      symbolic_instance(nl, edges, order, syms[i]);
+      if (sp.amalgamation != 0) {
+        symbolic_instance(nl, edges, order, sp.amalgamation, syms[i]);
+      } else {
+        symbolic_instance(nl, edges, order, 1, syms[i]);
+        size_t rows = 0;
+        for (const auto& R : syms[i].sn_rows) rows = std::max(rows, R.size());
+        if (rows <= (size_t)AUTO_SMALL_FRONT_ROWS) symbolic_instance(nl, edges, order, 2, syms[i]);
+      }
     };
     parallel_for((int)reps.size(), [&](int q) { symbolic_of(reps[q]); });
     for (int i = 0; i < ni; ++i)

@@ -23,6 +23,7 @@ struct ProblemSpec {
   double gamma = 1e-8, tol = 1e-8, pivtol = 1e-12;
   int ordering = 0;  // 0 auto, 1 natural, 2 nested dissection
   int nd_leaf = 1;
+  int amalgamation = 0;
 };
 
 struct Analysis {

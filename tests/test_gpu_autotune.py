@@ -1,7 +1,7 @@
 """The autotuner (nmpc_autotune) on the GPU.
 
 It times one cold solve per candidate option set (ordering and nested-
-dissection leaf size, solve form) and keeps the fastest per interior-point
+dissection leaf size, supernode amalgamation, solve form) and keeps the fastest per interior-point
 iteration.  Pins: every candidate converges on these problems; the chosen
 options are one of the candidates; a solver built with them reaches the
 default options' solution (1e-6 relative) and iteration count (within 3:
@@ -44,12 +44,14 @@ def test_autotune_picks_a_converging_candidate_and_caches_it(P, hz):
     o, rep = P.autotune(P.MODEL_DISTILLATION, hz, x0=x0, setpoint=sp, u_prev=up, N=12, Nf=5)
     assert not rep["cached"]
     cands = rep["candidates"]
-    # ND leaves 1, 2, 4 (horizons >= 8) and stage order (horizons < 32), in two solve forms
-    assert len(cands) == (8 if max(hz) < 32 else 6)
+    # ND leaves 1, 2, 4 in two amalgamation modes (horizons >= 8) and stage
+    # order (horizons < 32), in two solve forms
+    assert len(cands) == (14 if max(hz) < 32 else 12)
     assert all(c["status"] == 0 and c["iters"] > 0 and c["ms_per_iter"] > 0 for c in cands), cands
     b = cands[rep["best"]]
     assert b["ms_per_iter"] == min(c["ms_per_iter"] for c in cands)
-    assert (o.ordering, o.nd_leaf, o.panel_scale) == (b["ordering"], b["nd_leaf"], b["panel_scale"])
+    assert (o.ordering, o.nd_leaf, o.panel_scale, o.amalgamation) == \
+        (b["ordering"], b["nd_leaf"], b["panel_scale"], b["amalgamation"])
     y_t, inf_t = _solve(P, hz, x0s, sps, o)
     y_d, inf_d = _solve(P, hz, x0s, sps, P.options())
     for i in range(len(hz)):
@@ -58,4 +60,5 @@ def test_autotune_picks_a_converging_candidate_and_caches_it(P, hz):
         assert np.max(np.abs(y_t[i] - y_d[i])) / max(1.0, np.max(np.abs(y_d[i]))) <= 1e-6
     o2, rep2 = P.autotune(P.MODEL_DISTILLATION, hz, x0=x0, setpoint=sp, u_prev=up, N=12, Nf=5)
     assert rep2["cached"]
-    assert (o2.ordering, o2.nd_leaf, o2.panel_scale) == (o.ordering, o.nd_leaf, o.panel_scale)
+    assert (o2.ordering, o2.nd_leaf, o2.panel_scale, o2.amalgamation) == \
+        (o.ordering, o.nd_leaf, o.panel_scale, o.amalgamation)

@@ -312,6 +312,30 @@ def test_cluster_and_single_cta_factorizations_agree(P):
     assert np.max(np.abs(ys[0] - ys[1])) < 1e-6
 
 
+def test_amalgamation_modes_agree(P, oracle):
+    """Relaxed and sibling-limited supernode partitions of the nested-
+    dissection ordering factor the same matrix in other groupings: the same
+    solution up to rounding (each within the parity bar of the converged
+    point, so within twice it of each other), both KKT-optimal by the
+    oracle's evaluator, iteration counts within one."""
+    T = 200
+    x0 = I.distillation_x0(34, 17, seed=2)
+    a, _ = I.distillation_setpoints(34, seed=2)
+    prob = _oracle_problem(oracle, "distill34", T, x0, a)
+    ys, its = [], []
+    for am in (1, 2):
+        s = _gpu_solver(P, "distill34", [T], opts=P.options(amalgamation=am, ordering=2))
+        s.set_params(x0=x0, setpoint=np.full(T, a), u_prev=np.array([I.U_REF]))
+        info = s.solve()[0]
+        assert info["status"] == 0
+        es, _ = oracle.kkt_error(prob, _state_from_gpu(oracle, s, 0, prob.n, prob.m))
+        assert es <= TOL_KKT, (am, es)
+        ys.append(s.get_solution(0))
+        its.append(info["iters"])
+    assert abs(its[0] - its[1]) <= 1, its
+    assert np.max(np.abs(ys[0] - ys[1])) / max(1.0, np.max(np.abs(ys[0]))) <= 2 * TOL_Y
+
+
 @pytest.mark.parametrize("hz", [[200], [30, 45, 60, 20]])
 def test_solve_forms_agree(P, oracle, hz):
     """The three forms of the small-front solves: the panel transformed with

@@ -33,6 +33,7 @@ def _header_struct_fields(header, name):
     end = re.search(r"\}\s*" + name + r";", header).start()
     body = header[header.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    body = re.sub(r"\[[^]]*\]", "", body)  # array extents
     names = []
     for decl in body.split(";"):
         decl = decl.strip()
@@ -46,12 +47,14 @@ def _header_struct_fields(header, name):
 
 
 def test_binding_structs_mirror_the_header(P):
-    """The ctypes structures lay out nmpc_problem, nmpc_options, nmpc_info
-    and nmpc_stats field by field as the header declares them."""
+    """The ctypes structures lay out the header's structs field by field as
+    it declares them."""
     header = open(os.path.join(ROOT, "include", "nmpc.h")).read()
     L = P._lib
     for cname, pyst in (("nmpc_problem", L.Problem), ("nmpc_options", L.Options),
-                        ("nmpc_info", L.Info), ("nmpc_stats", L.Stats)):
+                        ("nmpc_info", L.Info), ("nmpc_stats", L.Stats),
+                        ("nmpc_tune_candidate", L.TuneCandidate), ("nmpc_tune_report", L.TuneReport),
+                        ("nmpc_phase_times", L.PhaseTimes)):
         assert _header_struct_fields(header, cname) == [f[0] for f in pyst._fields_], cname
 
 
@@ -198,3 +201,32 @@ def test_batch_analysis_equals_each_instance_analysed_alone(P):
         vo, so, ro = vo + n, so + ns, ro + nrows
         s.close()
     assert vo == perm_b.size and so == nc_b.size
+
+
+def test_automatic_amalgamation_keeps_small_separators_apart(P):
+    """Automatic amalgamation: where every front of the relaxed partition is
+    small (the distillation columns under nested dissection), the partition
+    is the sibling-limited one, whose top separators are single stage blocks
+    (x_k and u_k, N + 1 columns); where fronts are large (the heated plate at
+    g = 32) it is the relaxed one.  Stage order gives a chain, where both
+    modes agree.  Mode 2 only splits what mode 1 merged: every relaxed
+    supernode is a union of sibling-limited ones."""
+    def same(a, b):
+        return all(np.array_equal(a.export(w), b.export(w)) for w in (0, 1, 2, 3, 5, 6, 7))
+
+    auto, relaxed, sib = [P.Structure(model=0, horizons=[200], N=34, Nf=17, opts=P.options(ordering=2, amalgamation=am))
+                          for am in (0, 1, 2)]
+    assert same(auto, sib) and not same(relaxed, sib)
+    assert max(relaxed.stats()["max_front"], sib.stats()["max_front"]) <= 128
+    lp, lsn, ncol = sib.export(6), sib.export(7), sib.export(2)
+    assert all(ncol[q] == 35 for q in lsn[lp[-4]:lp[-1]])       # the four top levels
+    assert set(relaxed.export(1)) <= set(sib.export(1))           # relaxed = coarsening
+    assert relaxed.stats()["nnz_L"] >= sib.stats()["nnz_L"]
+    auto, relaxed, sib = [P.Structure(model=1, horizons=[20], g=32, S=8, opts=P.options(ordering=2, amalgamation=am))
+                          for am in (0, 1, 2)]
+    assert relaxed.stats()["max_front"] > 128 and same(auto, relaxed) and not same(relaxed, sib)
+    chain = [P.Structure(model=0, horizons=[200], N=34, Nf=17, opts=P.options(ordering=1, amalgamation=am))
+             for am in (0, 1, 2)]
+    assert same(chain[0], chain[1]) and same(chain[1], chain[2])
+    with pytest.raises(P.NmpcError):
+        P.Structure(model=0, horizons=[20], N=12, Nf=5, opts=P.options(amalgamation=3))
