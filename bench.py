@@ -34,9 +34,9 @@ UNIT = "re-solves/s"
 FP64_DFMA_PER_CLK_PER_SM = 2.0   # GB300: FP64 FMA rate 1/64 of FP32; probe measured 1.9
 N_SM = 152
 # DRAM bytes (read + write) of one numeric factorization of the workload above:
-# the 8 level launches of k_factor_cluster, one ncu capture of the current kernel
-# (profiles/k_factor_cluster_distillation_N34_T200.md)
-FACTOR_DRAM_BYTES = 15.53e6
+# the 11 level launches of k_factor_cluster, one ncu capture of the current kernel
+# and supernode partition (profiles/k_factor_cluster_distillation_N34_T200.md)
+FACTOR_DRAM_BYTES = 17.51e6
 
 
 def _peaks():
@@ -463,8 +463,8 @@ def main():
             "hbm": hbm_rooflines(st, ph, latency_bound=True),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": FACTOR_DRAM_BYTES,
-                         "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of the 8 level launches of "
-                                          "one factorization, one ncu capture",
+                         "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of the 11 level launches "
+                                          "of one factorization, one ncu capture",
                          "kernel": "k_factor_cluster (the level launches of one numeric factorization)",
                          "flops_per_launch_set": st["factor_flops"],
                          "peak_basis": "152 SMs x 2 FP64 FMA/clock x max SM clock (nominal FP64 rate)"},
