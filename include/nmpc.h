@@ -113,7 +113,10 @@ typedef struct {
                             2: the diagonal blocks only: two products per block;
                             3: no transform: column-by-column substitution */
   int amalgamation;      /* relaxed amalgamation of fundamental supernodes (Sec. 3.2.3 supernodes):
-                            0: automatic (default);
+                            0: automatic (default): 2 where every front of the partition
+                               of 1 has at most 128 rows (small, latency-bound fronts),
+                               else 1; values outside 0..2 make nmpc_build fail with
+                               NMPC_ERR_INVALID;
                             1: relaxed: a supernode whose columns end right before its parent's
                                merges into it while the merged panel's explicit zeros stay
                                under a limit that falls with the panel's width;
