@@ -354,7 +354,10 @@ def main():
     x0 = I.distillation_x0(N, Nf, seed)
     a, b = I.distillation_setpoints(N, wl["seed"])
     opts = P.options(use_graph=0) if args.host_loop else None
+    torch.cuda.synchronize()
+    t_build = time.perf_counter()
     s = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev, opts=opts)
+    build_s = time.perf_counter() - t_build
     n, m, _ = s.dims[0]
     ox1, ou1 = N, 2 * N  # offsets of x_1 and u_1 in y = [x_0 | x_1 u_1 | ...]
     stream = s.stream
@@ -364,10 +367,14 @@ def main():
                           dtype=torch.float64, device=dev)
     y_dev = torch.empty(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    t_cold = time.perf_counter()
     s.set_params(x0=x0, setpoint=np.full(T, a), u_prev=np.array([I.U_REF]))
     info0 = s.solve(warm=False)[0]
     assert info0["status"] == 0, info0
     s.get_solution(0, out=(y_dev, None))
+    torch.cuda.synchronize()
+    cold_s = time.perf_counter() - t_cold
 
     def step(k, warm=True):
         s.set_params(x0=y_dev[ox1:ox1 + N], setpoint=sp_dev[k], u_prev=y_dev[ou1:ou1 + 1])
@@ -451,9 +458,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "Nf": Nf, "T": T, "n": n, "m": m, "tol": 1e-8,
                        "ordering": ["auto", "natural", "nested_dissection"][st["ordering_used"]],
+                       "amalgamation": ["auto", "relaxed", "sibling_limited"][st["amalgamation_used"]],
                        "l2": "flushed between re-solves (256 MB write)"},
             "ms_per_ipm_iter": ms_iter, "ipm_iters_per_resolve": sum(iters) / len(iters),
             "statuses_ok": all(x == 0 for x in stats_),
+            "step_ms": {"median": statistics.median(ms), "min": min(ms), "max": max(ms)},
+            "closed_loop": {"build_s": build_s, "cold_solve_s": cold_s, "cold_solve_iters": info0["iters"],
+                            "resolves": args.steps + 1,
+                            "resolves_per_s_incl_build": (args.steps + 1) / (build_s + cold_s + tot_ms * 1e-3)},
             "rebuild": {"cold_resolves_per_s": rb["cold"], "warm_resolves_per_s": rb["warm"],
                         "parametric_over_rebuild_cold": value / rb["cold"]},
             "wall_s_timed": wall,

@@ -150,6 +150,7 @@ typedef struct {
   int max_front;             /* largest frontal matrix order */
   int ordering_used;
   long long kernel_launches; /* kernels launched by this handle so far */
+  int amalgamation_used;     /* supernode amalgamation of the last instance (1 relaxed, 2 sibling-limited) */
 } nmpc_stats;
 
 /* Average device time (CUDA events on the library stream) of the phases of

@@ -60,7 +60,7 @@ class Stats(C.Structure):
     _fields_ = [("n_total", C.c_int), ("m_total", C.c_int), ("n_supernodes", C.c_int), ("n_levels", C.c_int),
                 ("nnz_L", C.c_longlong), ("factor_flops", C.c_double), ("solve_flops", C.c_double),
                 ("workspace_bytes", C.c_longlong), ("analysis_ms", C.c_double), ("max_front", C.c_int),
-                ("ordering_used", C.c_int), ("kernel_launches", C.c_longlong)]
+                ("ordering_used", C.c_int), ("kernel_launches", C.c_longlong), ("amalgamation_used", C.c_int)]
 
 
 class PhaseTimes(C.Structure):

@@ -1272,6 +1272,7 @@ nmpc_status nmpc_get_stats(const nmpc_handle* h, nmpc_stats* st) {
   st->max_front = A.max_front;
   st->ordering_used = A.ordering_used;
   st->kernel_launches = h->launches;
+  st->amalgamation_used = A.amalgamation_used;
   return NMPC_OK;
 }
 

@@ -120,6 +120,7 @@ struct InstSym {
   std::vector<int> sn_first, sn_ncol;
   std::vector<std::vector<int>> sn_rows;
   std::vector<int> sn_parent;
+  int amalg = 0;               // amalgamation mode of this partition
 };
 
 // Elimination tree by Liu's algorithm with path compression.
@@ -511,19 +512,26 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
         order = nd.order;
         if ((int)order.size() != nl) throw std::runtime_error("nested dissection lost vertices");
       }
-      if (sp.amalgamation != 0) {
-        symbolic_instance(nl, edges, order, sp.amalgamation, syms[i]);
+      int am = sp.amalgamation;
+      if (am != 0) {
+        symbolic_instance(nl, edges, order, am, syms[i]);
       } else {
-        symbolic_instance(nl, edges, order, 1, syms[i]);
+        am = 1;
+        symbolic_instance(nl, edges, order, am, syms[i]);
         size_t rows = 0;
         for (const auto& R : syms[i].sn_rows) rows = std::max(rows, R.size());
-        if (rows <= (size_t)AUTO_SMALL_FRONT_ROWS) symbolic_instance(nl, edges, order, 2, syms[i]);
+        if (rows <= (size_t)AUTO_SMALL_FRONT_ROWS) {
+          am = 2;
+          symbolic_instance(nl, edges, order, am, syms[i]);
+        }
       }
+      syms[i].amalg = am;
     };
     parallel_for((int)reps.size(), [&](int q) { symbolic_of(reps[q]); });
     for (int i = 0; i < ni; ++i)
       if (rep_of[i] != i) syms[i] = syms[rep_of[i]];
     A.ordering_used = ord_of(sp.T[ni - 1]);
+    A.amalgamation_used = syms[ni - 1].amalg;
     for (int i = 0; i < ni; ++i) {
       Layout L{nx, nu, sp.T[i]};
       const int vo = A.inst_voff[i], ro = A.inst_roff[i], wo = A.inst_woff[i];

@@ -52,7 +52,7 @@ struct Analysis {
   // stats
   double factor_flops = 0, solve_flops = 0, analysis_ms = 0;
   long long nnzL_true = 0;
-  int max_front = 0, ordering_used = 0;
+  int max_front = 0, ordering_used = 0, amalgamation_used = 0;
 };
 
 // Returns an empty string on success, else an error message.

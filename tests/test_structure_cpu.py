@@ -230,3 +230,10 @@ def test_automatic_amalgamation_keeps_small_separators_apart(P):
     assert same(chain[0], chain[1]) and same(chain[1], chain[2])
     with pytest.raises(P.NmpcError):
         P.Structure(model=0, horizons=[20], N=12, Nf=5, opts=P.options(amalgamation=3))
+
+
+def test_stats_report_the_amalgamation_used(P):
+    used = [P.Structure(model=0, horizons=[200], N=34, Nf=17, opts=P.options(ordering=2, amalgamation=am))
+            .stats()["amalgamation_used"] for am in (0, 1, 2)]
+    assert used == [2, 1, 2]
+    assert P.Structure(model=1, horizons=[20], g=32, S=8, opts=P.options(ordering=2)).stats()["amalgamation_used"] == 1
