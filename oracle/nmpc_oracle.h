@@ -12,6 +12,8 @@
  *   banded Cholesky              pinned (numpy.linalg.cholesky, Laplacian)
  *   SymCholesky                  pinned (Fig. cholesky-symExample, brute force)
  *   Newton step / condensation   pinned (uncondensed primal-dual Newton system)
+ *   optimality error E_mu, E_0   pinned (lifted KKT residual from the dense
+ *                                Jacobian, scaled and unscaled)
  *   converged solutions          pinned (dense KKT solve of LQ cases,
  *                                brute-force active sets, FD stationarity)
  *   iteration counts             parity unpinned (no external count exists)

@@ -1,5 +1,7 @@
 """Pins of the oracle's interior-point method (CPU only).
 
+* Optimality error: E_mu and E_0 equal the norms of the lifted KKT residual
+  built from the dense Jacobian.
 * Newton step: the condensed Lifted-KKT solve plus recovery (eqs.
   liftedkkt-pd, cholesky-lower/upper/delta, infiniteOCP-augmented) equals the
   solution of the full primal-dual Newton system of the barrier KKT
@@ -79,15 +81,66 @@ def _full_newton(O, p, st, mu, dw):
                 b_p=parts[5], b_m=parts[6], zL=dzL, zU=dzU)
 
 
+def _small_problem(O, model):
+    if model == "distill":
+        return O.distillation(5, 3, 3, np.full(5, 0.5), np.full(3, 0.6), 2.0, dt=0.5)
+    if model == "plate":
+        return O.plate(4, 8, 2, np.zeros(16), np.full(16, 0.3), dt=0.5)
+    return O.toy(4, 1.0, np.sin(np.arange(4)), dt=0.7)
+
+
+def _residual_norms(O, p, st, mu):
+    """Max-norms of the lifted barrier KKT conditions at st, from the dense
+    Jacobian and the evaluated gradient and constraints: stationarity in y and
+    in the slacks (dual), the lifted constraints (primal), complementarity;
+    and the multiplier sums of the scaling of W&B eq. (5)."""
+    yL, yU = p.bounds()
+    L, U = np.isfinite(yL), np.isfinite(yU)
+    _, g, h, _ = O.evaluate(p, st.y)
+    H = O.jacobian_dense(p, st.y)
+    ry = g + H.T @ (st.w_p - st.w_m) - np.where(L, st.zL, 0.0) + np.where(U, st.zU, 0.0)
+    dual = max(np.abs(ry).max(), np.abs(st.w_p - st.b_p).max(), np.abs(st.w_m - st.b_m).max())
+    prim = max(np.abs(h - GAMMA + st.s_p).max(), np.abs(-h - GAMMA + st.s_m).max())
+    comp = max(np.abs(st.s_p * st.b_p - mu).max(), np.abs(st.s_m * st.b_m - mu).max(),
+               np.abs((st.y - yL)[L] * st.zL[L] - mu).max(initial=0.0),
+               np.abs((yU - st.y)[U] * st.zU[U] - mu).max(initial=0.0))
+    sum_w = np.abs(st.w_p).sum() + np.abs(st.w_m).sum()
+    sum_z = np.abs(st.zL[L]).sum() + np.abs(st.zU[U]).sum() + np.abs(st.b_p).sum() + np.abs(st.b_m).sum()
+    n_z = L.sum() + U.sum() + 2 * p.m
+    return dual, prim, comp, sum_w, sum_z, n_z
+
+
+@pytest.mark.parametrize("model", ["distill", "plate", "toy"])
+def test_optimality_error_is_the_kkt_residual(oracle, model):
+    """The oracle's optimality error (the termination test of eqs.
+    infiniteOCP-innerTol/outerTol, W&B eq. (5)) against the lifted KKT
+    residual built from the dense Jacobian: unscaled, it is the largest of the
+    dual, primal and complementarity residuals; scaled, the dual part is
+    divided by s_d and the complementarity by s_c, each max(100, mean
+    multiplier)/100.  States with small multipliers (s_d = s_c = 1, E scaled =
+    unscaled) and with multipliers 1e3 times larger (scaling active)."""
+    O = oracle
+    p = _small_problem(O, model)
+    for seed, mu, big in [(1, 0.0, 1.0), (2, 0.05, 1.0), (3, 0.0, 1e3), (4, 0.3, 1e3)]:
+        st = _random_state(O, p, seed)
+        for k in ("zL", "zU", "w_p", "w_m", "b_p", "b_m"):
+            getattr(st, k)[:] *= big
+        dual, prim, comp, sum_w, sum_z, n_z = _residual_norms(O, p, st, mu)
+        es, eu = O.kkt_error(p, st, mu=mu, gamma=GAMMA)
+        assert eu == pytest.approx(max(dual, prim, comp), rel=1e-12), (model, seed)
+        sd = max(100.0, (sum_w + sum_z) / (2 * p.m + n_z)) / 100.0
+        sc = max(100.0, sum_z / n_z) / 100.0
+        assert es == pytest.approx(max(dual / sd, prim, comp / sc), rel=1e-12), (model, seed)
+        if big == 1.0:
+            assert es == eu
+        else:
+            assert sd > 1.0 and sc > 1.0
+
+
 @pytest.mark.parametrize("model", ["distill", "plate", "toy"])
 def test_newton_step_equals_uncondensed_solve(oracle, model):
     O = oracle
-    if model == "distill":
-        p = O.distillation(5, 3, 3, np.full(5, 0.5), np.full(3, 0.6), 2.0, dt=0.5)
-    elif model == "plate":
-        p = O.plate(4, 8, 2, np.zeros(16), np.full(16, 0.3), dt=0.5)
-    else:
-        p = O.toy(4, 1.0, np.sin(np.arange(4)), dt=0.7)
+    p = _small_problem(O, model)
     for seed, mu, dw in [(1, 0.1, 0.0), (2, 1e-3, 0.5), (3, 1.0, 2.0)]:
         st = _random_state(O, p, seed)
         rc, d = O.newton_step(p, st, mu, dw, gamma=GAMMA)
