@@ -14,6 +14,9 @@
  *   Newton step / condensation   pinned (uncondensed primal-dual Newton system)
  *   optimality error E_mu, E_0   pinned (lifted KKT residual from the dense
  *                                Jacobian, scaled and unscaled)
+ *   line search, step update     pinned (step by step against the Newton
+ *                                direction, merits recomputed from the model,
+ *                                fraction to the boundary, filter tests)
  *   converged solutions          pinned (dense KKT solve of LQ cases,
  *                                brute-force active sets, FD stationarity)
  *   iteration counts             parity unpinned (no external count exists)

@@ -2,6 +2,8 @@
 
 * Optimality error: E_mu and E_0 equal the norms of the lifted KKT residual
   built from the dense Jacobian.
+* Line search: each step of cold solves against the Newton direction, the
+  fraction to the boundary and the filter tests with recomputed merits.
 * Newton step: the condensed Lifted-KKT solve plus recovery (eqs.
   liftedkkt-pd, cholesky-lower/upper/delta, infiniteOCP-augmented) equals the
   solution of the full primal-dual Newton system of the barrier KKT
@@ -337,3 +339,115 @@ def test_paper_distillation_at_steady_state_stays_there(oracle):
     X = np.stack([st.y[p.off_x(k):p.off_x(k) + N] for k in range(1, T + 1)])
     assert np.max(np.abs(u - ubar)) < 1e-6
     assert np.max(np.abs(X - xs)) < 1e-6
+
+
+LS_PROBLEMS = {
+    "distill": lambda O: O.distillation(5, 3, 6, np.full(5, 0.5), np.full(6, 0.6), 2.0, dt=0.5),
+    "distill_long_dt": lambda O: O.distillation(5, 3, 6, np.full(5, 0.2), np.full(6, 0.9), 1.0, dt=2.0),
+    "toy": lambda O: O.toy(14, 1.0, np.sin(np.arange(1, 15) * 10 / 14), dt=10 / 14),
+    "toy_far": lambda O: O.toy(6, 2.0, np.full(6, -1.0), dt=0.5),
+    "plate": lambda O: O.plate(4, 8, 3, np.zeros(16), np.full(16, 1.5), dt=0.5),
+}
+
+
+@pytest.mark.parametrize("name", list(LS_PROBLEMS))
+def test_line_search_steps_follow_the_filter_method(oracle, name):
+    """The oracle's steps against the filter line search of W&B Sec. 2 as the
+    paper's step z += alpha delta (eq. infiniteOCP-lineSearch) is read:
+    iterates after k and k + 1 iterations (max_iter = k, k + 1), the Newton
+    direction at the k-th iterate (pinned above) and the merit functions
+    recomputed here from the evaluated objective and constraints.  Per step:
+    the traced phi_mu, theta and E_mu are those of the iterate, E_mu exceeds
+    kappa_eps mu unless mu is at its floor (the barrier loop's exit); the dual
+    step is the fraction-to-the-boundary step with tau = max(0.99, 1 - mu);
+    the primal step is the primal fraction-to-the-boundary step halved
+    (trials - 1) times; y, s and the constraint multipliers take the primal
+    step, the bound and slack multipliers the dual step and then the kappa_Sigma
+    safeguard; the accepted trial point is not blocked by the filter and
+    decreases theta or phi_mu enough (or meets the Armijo condition); every
+    longer trial step failed those tests, or was blocked by the filter, which is rebuilt here
+    from the traced (theta, phi_mu) of the steps that were not Armijo steps
+    and emptied at every barrier update.  Every iteration of cold solves that
+    backtrack (up to 9 trials), correct the inertia (delta_w > 0) and lower
+    mu."""
+    O = oracle
+    p = LS_PROBLEMS[name](O)
+    yL, yU = p.bounds()
+    L, U = np.isfinite(yL), np.isfinite(yU)
+    gam, tol, ks = 1e-8, 1e-8, 1e10
+
+    def merit(y, sp, sm, mu):
+        f, g, h, _ = O.evaluate(p, y)
+        lg = np.log((y - yL)[L]).sum() + np.log((yU - y)[U]).sum() + np.log(sp).sum() + np.log(sm).sum()
+        return f - mu * lg, (np.abs(h - gam + sp) + np.abs(-h - gam + sm)).sum(), g
+
+    def ftb(v, dv, tau):
+        neg = dv < 0
+        return min(1.0, np.min(tau * v[neg] / -dv[neg], initial=np.inf))
+
+    def armijo_case(th, alpha, gphi, th_min):
+        return th <= th_min and gphi < 0 and alpha * (-gphi) ** 2.3 > th ** 1.1
+
+    def accepted(phi_t, th_t, phi, th, alpha, gphi, th_min):
+        if armijo_case(th, alpha, gphi, th_min):
+            return phi_t <= phi + 1e-4 * alpha * gphi
+        return th_t <= (1 - 1e-5) * th or phi_t <= phi - 1e-5 * th
+
+    def acceptable(phi_t, th_t, phi, th, alpha, gphi, filt):
+        return (np.isfinite(phi_t) and th_t <= th_max and not any(th_t >= a and phi_t >= b for a, b in filt)
+                and accepted(phi_t, th_t, phi, th, alpha, gphi, th_min))
+
+    _, info, trace = O.solve(p)
+    assert info["status"] == 0
+    trace = np.asarray(trace)
+    assert trace[:, 7].max() >= 2 and (np.diff(trace[:, 0]) != 0).any()
+    th_min = th_max = None
+    filt = []
+    checked = 0
+    z1, _, _ = O.solve(p, max_iter=0)
+    for k in range(info["iters"]):
+        zk = z1
+        z1, _, tr = O.solve(p, max_iter=k + 1)
+        np.testing.assert_array_equal(tr[k], trace[k])
+        mu, alpha, ad, dw, theta, phi, emu, trials = tr[k]
+        tau = max(0.99, 1.0 - mu)
+        phi_k, th_k, g = merit(zk.y, zk.s_p, zk.s_m, mu)
+        if k == 0:
+            th_min, th_max = 1e-4 * max(1.0, th_k), 1e4 * max(1.0, th_k)
+        if k == 0 or trace[k, 0] != trace[k - 1, 0]:
+            filt = []                                   # reset with every barrier update
+        assert phi == pytest.approx(phi_k, rel=1e-12) and theta == pytest.approx(th_k, rel=1e-12, abs=1e-300)
+        assert emu == pytest.approx(O.kkt_error(p, zk, mu=mu)[0], rel=1e-12)
+        assert emu > 10.0 * mu or mu == pytest.approx(tol / 10.0)
+        rc, d = O.newton_step(p, zk, mu, dw)
+        assert rc == 0
+        a_max = min(ftb((zk.y - yL)[L], d.y[L], tau), ftb((yU - zk.y)[U], -d.y[U], tau),
+                    ftb(zk.s_p, d.s_p, tau), ftb(zk.s_m, d.s_m, tau))
+        d_max = min(ftb(zk.zL[L], d.zL[L], tau), ftb(zk.zU[U], d.zU[U], tau),
+                    ftb(zk.b_p, d.b_p, tau), ftb(zk.b_m, d.b_m, tau))
+        assert ad == pytest.approx(d_max, rel=1e-12)
+        assert alpha == pytest.approx(a_max * 0.5 ** (trials - 1), rel=1e-12)
+        close = dict(rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(z1.y, zk.y + alpha * d.y, **close)
+        for a in ("s_p", "s_m", "w_p", "w_m"):
+            np.testing.assert_allclose(getattr(z1, a), getattr(zk, a) + alpha * getattr(d, a), **close)
+
+        def guard(v, gap):
+            return np.maximum(np.minimum(v, ks * mu / gap), mu / (ks * gap))
+        np.testing.assert_allclose(z1.zL[L], guard(zk.zL[L] + ad * d.zL[L], (z1.y - yL)[L]), **close)
+        np.testing.assert_allclose(z1.zU[U], guard(zk.zU[U] + ad * d.zU[U], (yU - z1.y)[U]), **close)
+        np.testing.assert_allclose(z1.b_p, guard(zk.b_p + ad * d.b_p, z1.s_p), **close)
+        np.testing.assert_allclose(z1.b_m, guard(zk.b_m + ad * d.b_m, z1.s_m), **close)
+        gb = g - np.where(L, mu / np.where(L, zk.y - yL, 1.0), 0.0) + np.where(U, mu / np.where(U, yU - zk.y, 1.0), 0.0)
+        gphi = gb @ d.y - mu * (d.s_p / zk.s_p + d.s_m / zk.s_m).sum()
+        phi_t, th_t, _ = merit(z1.y, z1.s_p, z1.s_m, mu)
+        assert acceptable(phi_t, th_t, phi_k, th_k, alpha, gphi, filt), k
+        with np.errstate(invalid="ignore", divide="ignore"):
+            for j in range(int(trials) - 1):           # every longer step was rejected
+                a = a_max * 0.5 ** j
+                ph, th, _ = merit(zk.y + a * d.y, zk.s_p + a * d.s_p, zk.s_m + a * d.s_m, mu)
+                assert not acceptable(ph, th, phi_k, th_k, a, gphi, filt), (k, j)
+        if not armijo_case(th_k, alpha, gphi, th_min):
+            filt.append(((1 - 1e-5) * th_k, phi_k - 1e-5 * th_k))
+        checked += 1
+    assert checked == info["iters"]
