@@ -17,6 +17,9 @@
  *   line search, step update     pinned (step by step against the Newton
  *                                direction, merits recomputed from the model,
  *                                fraction to the boundary, filter tests)
+ *   inertia correction           pinned (delta_w sequence of W&B Algorithm IC,
+ *                                definiteness by dense eigenvalues where they
+ *                                can decide it)
  *   converged solutions          pinned (dense KKT solve of LQ cases,
  *                                brute-force active sets, FD stationarity)
  *   iteration counts             parity unpinned (no external count exists)

@@ -341,6 +341,18 @@ def test_paper_distillation_at_steady_state_stays_there(oracle):
     assert np.max(np.abs(X - xs)) < 1e-6
 
 
+def _kc_extremes(O, p, st):
+    """Smallest eigenvalue and largest diagonal entry of the condensed matrix
+    K_c = W + Sigma_y + H^T (Q+ + Q-) H at st (eq. liftedkkt-pd), dense."""
+    yL, yU = p.bounds()
+    L, U = np.isfinite(yL), np.isfinite(yU)
+    H = O.jacobian_dense(p, st.y)
+    W = O.hessian_dense(p, st.y, st.w_p - st.w_m)
+    sig = np.where(L, st.zL / np.where(L, st.y - yL, 1.0), 0.0) + np.where(U, st.zU / np.where(U, yU - st.y, 1.0), 0.0)
+    Kc = W + np.diag(sig) + H.T @ np.diag(st.b_p / st.s_p + st.b_m / st.s_m) @ H
+    return np.linalg.eigvalsh(Kc)[0], np.abs(np.diag(Kc)).max()
+
+
 LS_PROBLEMS = {
     "distill": lambda O: O.distillation(5, 3, 6, np.full(5, 0.5), np.full(6, 0.6), 2.0, dt=0.5),
     "distill_long_dt": lambda O: O.distillation(5, 3, 6, np.full(5, 0.2), np.full(6, 0.9), 1.0, dt=2.0),
@@ -367,9 +379,11 @@ def test_line_search_steps_follow_the_filter_method(oracle, name):
     decreases theta or phi_mu enough (or meets the Armijo condition); every
     longer trial step failed those tests, or was blocked by the filter, which is rebuilt here
     from the traced (theta, phi_mu) of the steps that were not Armijo steps
-    and emptied at every barrier update.  Every iteration of cold solves that
-    backtrack (up to 9 trials), correct the inertia (delta_w > 0) and lower
-    mu."""
+    and emptied at every barrier update; delta_w is the first value of the
+    inertia-correction sequence (0, then 1e-4 or delta_last / 3, raised by 100
+    until a first success, by 8 after) at which K_c + delta_w I, from dense
+    matrices, is positive definite.  Every iteration of cold solves that
+    backtrack (up to 9 trials), correct the inertia and lower mu."""
     O = oracle
     p = LS_PROBLEMS[name](O)
     yL, yU = p.bounds()
@@ -403,7 +417,8 @@ def test_line_search_steps_follow_the_filter_method(oracle, name):
     assert trace[:, 7].max() >= 2 and (np.diff(trace[:, 0]) != 0).any()
     th_min = th_max = None
     filt = []
-    checked = 0
+    checked = corrected = decided = 0
+    dw_last = 0.0
     z1, _, _ = O.solve(p, max_iter=0)
     for k in range(info["iters"]):
         zk = z1
@@ -419,6 +434,29 @@ def test_line_search_steps_follow_the_filter_method(oracle, name):
         assert phi == pytest.approx(phi_k, rel=1e-12) and theta == pytest.approx(th_k, rel=1e-12, abs=1e-300)
         assert emu == pytest.approx(O.kkt_error(p, zk, mu=mu)[0], rel=1e-12)
         assert emu > 10.0 * mu or mu == pytest.approx(tol / 10.0)
+        # inertia correction (W&B Algorithm IC): delta_w is a value of the
+        # sequence 0, first, first * kappa, ... and the first at which K_c +
+        # delta_w I is positive definite (pivots above 1e-12 |K_jj|).  The
+        # eigenvalues of the dense K_c decide definiteness where their rounding
+        # error (about 1e-14 n max|K_jj|) is far below the 1e-4 scale of delta_w;
+        # near convergence the slack weights b/s reach 1e15 and they cannot.
+        lam_min, kdiag = _kc_extremes(O, p, zk)
+        err = 1e-14 * p.n * kdiag
+        decide = err < 1e-6
+        cands = [0.0]
+        if dw > 0.0:
+            c = 1e-4 if dw_last == 0.0 else max(1e-20, dw_last / 3.0)
+            while c < dw * (1 - 1e-14):
+                cands.append(c)
+                c *= 100.0 if dw_last == 0.0 else 8.0
+            assert c == pytest.approx(dw, rel=1e-14), (k, c, dw)
+            dw_last = dw
+            corrected += 1
+        if decide:
+            assert lam_min + dw > -err, (k, dw)
+            for c in cands if dw > 0.0 else []:
+                assert lam_min + c <= err + 1e-11 * kdiag, (k, c, dw)
+            decided += dw > 0.0
         rc, d = O.newton_step(p, zk, mu, dw)
         assert rc == 0
         a_max = min(ftb((zk.y - yL)[L], d.y[L], tau), ftb((yU - zk.y)[U], -d.y[U], tau),
@@ -450,4 +488,5 @@ def test_line_search_steps_follow_the_filter_method(oracle, name):
         if not armijo_case(th_k, alpha, gphi, th_min):
             filt.append(((1 - 1e-5) * th_k, phi_k - 1e-5 * th_k))
         checked += 1
-    assert checked == info["iters"]
+    assert checked == info["iters"] and corrected > 0
+    assert decided >= (2 if name.startswith("toy") else 0)
