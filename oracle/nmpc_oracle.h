@@ -17,6 +17,8 @@
  *   line search, step update     pinned (step by step against the Newton
  *                                direction, merits recomputed from the model,
  *                                fraction to the boundary, filter tests)
+ *   barrier update               pinned (the mu chain and its E_mu tests, per
+ *                                iteration)
  *   inertia correction           pinned (delta_w sequence of W&B Algorithm IC,
  *                                definiteness by dense eigenvalues where they
  *                                can decide it)

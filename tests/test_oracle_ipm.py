@@ -417,7 +417,7 @@ def test_line_search_steps_follow_the_filter_method(oracle, name):
     assert trace[:, 7].max() >= 2 and (np.diff(trace[:, 0]) != 0).any()
     th_min = th_max = None
     filt = []
-    checked = corrected = decided = 0
+    checked = corrected = decided = mu_updates = 0
     dw_last = 0.0
     z1, _, _ = O.solve(p, max_iter=0)
     for k in range(info["iters"]):
@@ -434,6 +434,15 @@ def test_line_search_steps_follow_the_filter_method(oracle, name):
         assert phi == pytest.approx(phi_k, rel=1e-12) and theta == pytest.approx(th_k, rel=1e-12, abs=1e-300)
         assert emu == pytest.approx(O.kkt_error(p, zk, mu=mu)[0], rel=1e-12)
         assert emu > 10.0 * mu or mu == pytest.approx(tol / 10.0)
+        # barrier update (eq. infiniteOCP-innerTol): from the previous mu, the
+        # update max(tol/10, min(0.2 mu, mu^1.5)) repeats while E_mu <= 10 mu
+        m_prev = 0.1 if k == 0 else trace[k - 1, 0]
+        while m_prev != mu:
+            assert O.kkt_error(p, zk, mu=m_prev)[0] <= 10.0 * m_prev, (k, m_prev, mu)
+            assert m_prev > tol / 10.0
+            m_prev = max(tol / 10.0, min(0.2 * m_prev, m_prev ** 1.5))
+            assert m_prev >= mu * (1 - 1e-12), (k, m_prev, mu)
+        mu_updates += k > 0 and trace[k - 1, 0] != mu
         # inertia correction (W&B Algorithm IC): delta_w is a value of the
         # sequence 0, first, first * kappa, ... and the first at which K_c +
         # delta_w I is positive definite (pivots above 1e-12 |K_jj|).  The
@@ -488,5 +497,5 @@ def test_line_search_steps_follow_the_filter_method(oracle, name):
         if not armijo_case(th_k, alpha, gphi, th_min):
             filt.append(((1 - 1e-5) * th_k, phi_k - 1e-5 * th_k))
         checked += 1
-    assert checked == info["iters"] and corrected > 0
+    assert checked == info["iters"] and corrected > 0 and mu_updates > 0
     assert decided >= (2 if name.startswith("toy") else 0)
