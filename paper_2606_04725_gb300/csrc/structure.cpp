@@ -434,12 +434,6 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
     // per distinct horizon, for the first instance that has it, on several
     // host threads, and the other instances copy it.
     auto ord_of = [&](int T) { return sp.ordering != 0 ? sp.ordering : (T < 8 ? 1 : 2); };  // short horizons: a chain
-    // Automatic amalgamation: relaxed, unless every front of the relaxed
-    // partition has at most AUTO_SMALL_FRONT_ROWS rows.  Such fronts are
-    // factored in shared memory, and their time is set by the chain of
-    // pivots of the widest front of each level, not by flops: there the
-    // separators of nested dissection are kept apart (sibling-limited), so
-    // that no level waits on a separator merged with one below it.
     std::vector<int> rep_of(ni), reps;
     {
       std::vector<std::pair<int, int>> firsts;  // (T, first instance), sorted by T
@@ -512,6 +506,12 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
         order = nd.order;
         if ((int)order.size() != nl) throw std::runtime_error("nested dissection lost vertices");
       }
+      // Automatic amalgamation: relaxed, unless every front of the relaxed
+      // partition has at most AUTO_SMALL_FRONT_ROWS rows.  Such fronts are
+      // factored in shared memory, and their time is set by the chain of
+      // pivots of the widest front of each level, not by flops: there the
+      // separators of nested dissection are kept apart (sibling-limited), so
+      // that no level waits on a separator merged with one below it.
       int am = sp.amalgamation;
       if (am != 0) {
         symbolic_instance(nl, edges, order, am, syms[i]);
