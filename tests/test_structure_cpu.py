@@ -237,3 +237,19 @@ def test_stats_report_the_amalgamation_used(P):
             .stats()["amalgamation_used"] for am in (0, 1, 2)]
     assert used == [2, 1, 2]
     assert P.Structure(model=1, horizons=[20], g=32, S=8, opts=P.options(ordering=2)).stats()["amalgamation_used"] == 1
+
+
+def test_library_and_oracle_default_to_the_same_model_constants(P, oracle):
+    """Both sides solve the same problems by default: nmpc_problem_defaults
+    and the oracle's problem constructors agree on every model constant and
+    bound (the models of Sec. 4.1 with the benchmark readings)."""
+    O = oracle
+    fields = ("dt", "alpha", "D", "F", "xF", "Ac", "At", "Ar", "wdu", "wu", "ubar", "kappa", "cq", "rho_u",
+              "xlo", "xhi", "ulo", "uhi")
+    cases = [(0, O.distillation(12, 5, 3, np.zeros(12), np.zeros(3), 0.0)),
+             (1, O.plate(8, 8, 2, np.zeros(64), np.zeros(64))),
+             (2, O.toy(3, 1.0, np.zeros(3), dt=1.0))]
+    for model, op in cases:
+        gp, _ = P._lib.problem(model, [3])
+        for f in fields:
+            assert getattr(gp, f) == getattr(op._p, f), (model, f, getattr(gp, f), getattr(op._p, f))
