@@ -499,3 +499,26 @@ def test_line_search_steps_follow_the_filter_method(oracle, name):
         checked += 1
     assert checked == info["iters"] and corrected > 0 and mu_updates > 0
     assert decided >= (2 if name.startswith("toy") else 0)
+
+
+def test_paper_distillation_closed_loop(oracle):
+    """The paper's column and cost (Sec. 4.1: N = 32, feed tray 17, holdups
+    0.5 / 0.25 / 1.0, dt = 2, 90 intervals, (x_1 - 0.8958)^2 + 0.1 (u - ubar)^2)
+    from a perturbed steady state: a cold solve and three warm re-solves of
+    the closed loop, each converged; the last point stationary by central
+    differences of the objective and constraints."""
+    O = oracle
+    N, Nf, T, ubar = 32, 17, 90, 2.51459
+    kw = dict(dt=2.0, Ac=0.5, At=0.25, Ar=1.0, wdu=0.0, wu=0.1, ubar=ubar)
+    xs = np.loadtxt(__import__("os").path.join(__import__("os").path.dirname(__file__),
+                                                "golden", "steady_state_N32_Nf17.txt"))
+    x0 = np.clip(xs + np.random.default_rng(6).normal(0, 0.02, N), 0, 1)
+    p = O.distillation(N, Nf, T, x0, np.full(T, 0.8958), ubar, **kw)
+    st, info, _ = O.solve(p)
+    assert info["status"] == 0 and info["E0_scaled"] <= 1e-8
+    for k in range(3):
+        p.set_params(x0=st.y[p.off_x(1):p.off_x(1) + N].copy(), uprev=st.y[p.off_u(1)])
+        st, info, _ = O.solve(p, state=st, warm=True)
+        assert info["status"] == 0 and info["iters"] < 10
+    r = _fd_stationarity(O, p, st)
+    assert np.max(np.abs(r)) < 1e-5
