@@ -636,6 +636,13 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 __device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// Bound of a wait for this block's own bulk copy.  The copy completes by
+// itself, so the wait does not take spin_limit (which bounds the waits on
+// other blocks, and which a caller may set tiny to make those run out); this
+// bound only guards against a copy that never lands.  Each poll is one
+// mbarrier.try_wait, so the bound is well under a second on this GPU.
+constexpr long long COPY_WAIT_LIMIT = 1LL << 24;
+
 // bounded wait for phase 0 of the barrier; false if the limit ran out
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, long long limit) {
   unsigned done = 0;
@@ -779,8 +786,8 @@ __device__ void subst_upper(double* v, double* slots, const double* Ls, int m, i
 // update vectors, written by other blocks of the same launch, are read
 // through L2 (__ldcg).
 template <class Wait>
-__device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int smem_cap, unsigned long long* bar,
-                          int* s_to, Wait wait) {
+__device__ bool fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int smem_cap, unsigned long long* bar,
+                          int* s_to, int* s_lost, Wait wait) {
   const int m = fd.m, c = fd.c, first = fd.first;
   const double* Lg = s.L + fd.Lptr;
   const long long lsz = ((long long)m * c + 1) & ~1LL;
@@ -828,8 +835,11 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
     for (int a = tid; a < ch.mc; a += nt) fv[ch.rel[a]] += __ldcg(ch.uv + a);
     __syncthreads();
   }
-  if (stage && !mbar_wait(bar, s.spin_limit)) *s_to = 1;
+  if (stage && !mbar_wait(bar, COPY_WAIT_LIMIT)) *s_lost = 1;
   __syncthreads();
+  // a copy that did not land may still write this shared memory: neither the
+  // barrier nor the buffer is touched again, and the block leaves
+  if (*s_lost) return false;  // uniform after the barrier
   if (stage && tid == 0) mbar_inval(bar);
   double* uvJ = s.uv + fd.uvptr;  // u_i = f_i - sum_j L_ij y_j (rows c..m-1)
   if (s.solve_form == 0) {
@@ -838,7 +848,7 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
         m - c, c, [&](int r, int j) { return Ls[(c + r) + (size_t)j * m]; }, [&](int j) { return fv[j]; },
         [&](int r, double a) { uvJ[r] = fv[c + r] - a; });
     for (int j = tid; j < c; j += nt) d.b[first + j] = fv[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
-    return;
+    return true;
   }
   for (int s0 = 0; s0 < c; s0 += IB) {
     const int bk = min(IB, c - s0), e = s0 + bk;
@@ -869,6 +879,7 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   }
   for (int r = c + tid; r < m; r += nt) uvJ[r - c] = fv[r];
   for (int j = tid; j < c; j += nt) d.b[first + j] = ys[j] * Ls[j + (size_t)j * m];  // diagonal holds 1/d_j
+  return true;
 }
 
 // Backward solve of one front.  The panel copy and z are started first;
@@ -876,8 +887,8 @@ __device__ void fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
 // ancestors' solution values (written by other blocks of the same launch)
 // are read through L2.
 template <class Wait>
-__device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int smem_cap, unsigned long long* bar,
-                          int* s_to, Wait wait) {
+__device__ bool bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int smem_cap, unsigned long long* bar,
+                          int* s_to, int* s_lost, Wait wait) {
   const int m = fd.m, c = fd.c, first = fd.first;
   const double* Lg = s.L + fd.Lptr;
   const int* rows_idx = s.sn_rows + fd.rowptr;
@@ -897,8 +908,9 @@ __device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   for (int i = tid; i < c; i += nt) zs[i] = d.b[first + i];
   wait();  // (also orders the barrier's initialization before any thread waits on it)
   for (int i = c + tid; i < m; i += nt) xv[i] = __ldcg(d.b + rows_idx[i]);
-  if (stage && !mbar_wait(bar, s.spin_limit)) *s_to = 1;
+  if (stage && !mbar_wait(bar, COPY_WAIT_LIMIT)) *s_lost = 1;
   __syncthreads();
+  if (*s_lost) return false;  // as in fwd_front
   if (stage && tid == 0) mbar_inval(bar);
   if (s.solve_form == 0) {
     // t_j = z_j - sum_{i >= c} L_ij x_i, then L_cc^T x = t (z's slots become the sentinel slots)
@@ -910,7 +922,7 @@ __device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
     __syncthreads();
     subst_upper(xv, zs, Ls, m, c, stage, s, s_to);
     for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
-    return;
+    return true;
   }
   for (int s0 = (c - 1) / IB * IB; s0 >= 0; s0 -= IB) {
     const int bk = min(IB, c - s0), e = s0 + bk, len = m - s0;
@@ -953,6 +965,7 @@ __device__ void bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
     }
   }
   for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
+  return true;
 }
 
 // In-place inverses of the unit lower triangular IB x IB diagonal blocks of
@@ -1032,26 +1045,26 @@ __global__ void __launch_bounds__(128) k_panel_scale(Dev d, SnDev s, int u0) {
 
 __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {
   __shared__ unsigned long long bar;
-  __shared__ int s_to;
+  __shared__ int s_to, s_lost;
   __shared__ FrontDesc fd;
   load_desc(&fd, dl + blockIdx.x);
-  if (threadIdx.x == 0) s_to = 0;
+  if (threadIdx.x == 0) s_to = s_lost = 0;
   __syncthreads();
   if (d.ctl[fd.inst].status != ST_RUNNING) return;
-  fwd_front(d, s, fd, smem_cap, &bar, &s_to, [] { __syncthreads(); });
-  if (threadIdx.x == 0 && s_to) atomicExch(s.timeout, 1);
+  fwd_front(d, s, fd, smem_cap, &bar, &s_to, &s_lost, [] { __syncthreads(); });
+  if (threadIdx.x == 0 && (s_to || s_lost)) atomicExch(s.timeout, 1);
 }
 
 __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap) {
   __shared__ unsigned long long bar;
-  __shared__ int s_to;
+  __shared__ int s_to, s_lost;
   __shared__ FrontDesc fd;
   load_desc(&fd, dl + blockIdx.x);
-  if (threadIdx.x == 0) s_to = 0;
+  if (threadIdx.x == 0) s_to = s_lost = 0;
   __syncthreads();
   if (d.ctl[fd.inst].status != ST_RUNNING) return;
-  bwd_front(d, s, fd, smem_cap, &bar, &s_to, [] { __syncthreads(); });
-  if (threadIdx.x == 0 && s_to) atomicExch(s.timeout, 1);
+  bwd_front(d, s, fd, smem_cap, &bar, &s_to, &s_lost, [] { __syncthreads(); });
+  if (threadIdx.x == 0 && (s_to || s_lost)) atomicExch(s.timeout, 1);
 }
 
 // Persistent forms: one launch for the fronts desc[0 .. nf) in level order.
@@ -1085,11 +1098,11 @@ __device__ __forceinline__ void wait_done(const int* flag, long long limit, int*
 template <bool FWD>
 __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* dl, int nf, int smem_cap, int* flags) {
   __shared__ unsigned long long bar;
-  __shared__ int s_to;
+  __shared__ int s_to, s_lost;
   __shared__ int s_q;
   __shared__ FrontDesc fd;
   const int tid = threadIdx.x;
-  if (tid == 0) s_to = 0;
+  if (tid == 0) s_to = s_lost = 0;
   for (;;) {
     if (tid == 0) s_q = atomicAdd(flags, 1);
     __syncthreads();
@@ -1113,16 +1126,19 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
         }
         __syncthreads();
       };
-      if (FWD) fwd_front(d, s, fd, smem_cap, &bar, &s_to, wait);
-      else bwd_front(d, s, fd, smem_cap, &bar, &s_to, wait);
+      if (FWD) fwd_front(d, s, fd, smem_cap, &bar, &s_to, &s_lost, wait);
+      else bwd_front(d, s, fd, smem_cap, &bar, &s_to, &s_lost, wait);
     }
     // Every thread's stores are ordered before thread 0's release store by
     // the block barrier (release is cumulative), and a waiting block reads
     // them after its acquire load and its own barrier.
     __syncthreads();
     if (tid == 0) st_release_gpu(flags + 1 + q, 1);
+    // a panel copy that did not land may still write this block's shared
+    // memory: the block claims no further front (s_lost is uniform here)
+    if (s_lost) break;
   }
-  if (tid == 0 && s_to) atomicExch(s.timeout, 1);
+  if (tid == 0 && (s_to || s_lost)) atomicExch(s.timeout, 1);
   // no block touches the flags after it has arrived here
   __shared__ int s_last;
   if (tid == 0) s_last = atomicAdd(flags + nf + 1, 1) == (int)gridDim.x - 1;
