@@ -123,6 +123,9 @@ typedef struct {
                             2: sibling-limited: as 1, but a supernode whose parent has other
                                children merges only into a panel of at most 16 columns, so
                                the separators of nested dissection stay separate fronts */
+  double dw_max;         /* inertia correction (eq. infiniteOCP-inertia, W&B Algorithm IC):
+                            an instance whose regularization delta_w would exceed dw_max
+                            stops with NMPC_INERTIA_FAIL (1e40) */
 } nmpc_options;
 
 /* Per-instance result of a solve.  Times are measured with CUDA events on
@@ -189,7 +192,9 @@ nmpc_status nmpc_bind(nmpc_handle* h, void* workspace, size_t bytes);
  * NULL to keep that parameter.
  *   x0:       nx values per instance (initial state p_x0)
  *   setpoint: distillation/toy: T values per instance (setpoint of x_{k,1}
- *             resp. y_k, k = 1..T); plate: g*g target field per instance
+ *             resp. y_k, k = 1..T); plate: g*g target field per instance.
+ *             With instance = -1 and unequal horizons, instance i takes its
+ *             own T_i values, one instance after another (sum of T_i)
  *   u_prev:   distillation: 1 value per instance (u_0 of the Delta-u term) */
 nmpc_status nmpc_set_params(nmpc_handle* h, int instance, const double* x0, const double* setpoint,
                             const double* u_prev, int on_device);
@@ -202,7 +207,10 @@ nmpc_status nmpc_set_params(nmpc_handle* h, int instance, const double* x0, cons
 nmpc_status nmpc_solve(nmpc_handle* h, int warm_start, nmpc_info* info);
 
 /* Copy an instance's solution: y (n of that instance); duals (nullable)
- * receives [zL (n), zU (n), s+ (m), s- (m), w+ (m), w- (m), b+ (m), b- (m)]. */
+ * receives [zL (n), zU (n), s+ (m), s- (m), w+ (m), w- (m), b+ (m), b- (m)].
+ * instance = -1 copies every instance, packed one after another (n and m
+ * then count all instances; y of instance i starts at the sum of the n of
+ * the instances before it). */
 nmpc_status nmpc_get_solution(nmpc_handle* h, int instance, double* y, double* duals, int on_device);
 
 /* Overwrite an instance's primal-dual point (same layout as get_solution);
@@ -330,6 +338,25 @@ nmpc_status nmpc_autotune_workspace_bytes(const nmpc_problem* prob, const nmpc_o
 nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cuda_stream, void* workspace,
                           size_t bytes, const double* x0, const double* setpoint, const double* u_prev,
                           int on_device, nmpc_tune_report* report);
+
+/* ------------------------------------------------------------------------
+ * Measurement and self-test hooks (not in the paper).
+ *
+ * nmpc_debug_recip: out[i] = the reciprocal the factorization uses for its
+ * pivots (reading of eq. cholesky-numeric in L D L^T form: one reciprocal per
+ * column), computed by the same device routine, for n device values in[i]
+ * (in, out: device pointers, n >= 0).  Ordered on cuda_stream; returns
+ * without synchronizing.  For tests that compare it with IEEE division.
+ *
+ * nmpc_probe_fp64: measured FP64 throughput of this GPU in TFLOP/s, the peak
+ * that the factorization's FP64 rate is compared with.  kind 0: independent
+ * FMA chains on every thread; kind 1: the f64 tensor-core instruction
+ * mma.sync.m8n8k4 with independent accumulators on every warp.
+ * blocks_per_sm (1..8) blocks of 256 threads per SM, iters steps each; one
+ * warm-up launch, then one launch timed with CUDA events on cuda_stream
+ * (synchronizes it).  Allocates no device memory. */
+nmpc_status nmpc_debug_recip(const double* in, double* out, long long n, void* cuda_stream);
+nmpc_status nmpc_probe_fp64(int kind, int blocks_per_sm, int iters, void* cuda_stream, double* tflops);
 
 /* Release host memory of the handle (the caller frees the workspace).
  * Synchronizes the library stream.  NULL is ignored. */

@@ -53,7 +53,7 @@ class _Problem(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("gamma", C.c_double), ("mu0_cold", C.c_double),
                 ("mu0_warm", C.c_double), ("push_cold", C.c_double), ("push_warm", C.c_double),
-                ("max_iter", C.c_int), ("refine", C.c_int), ("pivtol", C.c_double)]
+                ("max_iter", C.c_int), ("pivtol", C.c_double), ("dw_max", C.c_double)]
 
 
 class _Info(C.Structure):
@@ -234,7 +234,7 @@ def steady_state(prob, u):
 
 def default_options(**kw):
     o = dict(tol=1e-8, gamma=1e-8, mu0_cold=0.1, mu0_warm=1e-8, push_cold=1e-2, push_warm=1e-9,
-             max_iter=200, refine=0, pivtol=1e-12)
+             max_iter=200, pivtol=1e-12, dw_max=1e40)
     o.update(kw)
     return o
 

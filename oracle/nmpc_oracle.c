@@ -392,7 +392,6 @@ int or_symbolic(int n, const int* colptr, const int* rowidx, int* parent,
 #define GAMMA_ALPHA 0.05
 #define DELTA_W0 1e-4       /* first regularization trial */
 #define DELTA_WMIN 1e-20
-#define DELTA_WMAX 1e40
 #define KAPPA_W_MINUS (1.0 / 3.0)
 #define KAPPA_W_PLUS 8.0
 #define KAPPA_W_PLUS_BAR 100.0
@@ -593,7 +592,7 @@ static void direction(work* w, const or_state* z, double mu, or_state* d) {
 
 /* Inertia correction (W&B Algorithm IC restricted to delta_w, since the
  * lifted system has no equality block): factor with 0, then 1e-4 or
- * last/3, then x100 (first) or x8, failing above 1e40.  Returns 0 on
+ * last/3, then x100 (first) or x8, failing above dw_max (1e40 by default).  Returns 0 on
  * success and sets *dw; -1 on failure. */
 static int factor_with_correction(work* w, const or_state* z, double* dw_last, double* dw, int* retries) {
   const double tol = w->o->pivtol;
@@ -605,7 +604,7 @@ static int factor_with_correction(work* w, const or_state* z, double* dw_last, d
     assemble(w, z, d);
     if (band_cholesky_tol(w->n, w->b, w->band, tol) == 0) { *dw = d; *dw_last = d; return 0; }
     d = (*dw_last == 0.0) ? KAPPA_W_PLUS_BAR * d : KAPPA_W_PLUS * d;
-    if (d > DELTA_WMAX) return -1;
+    if (d > w->o->dw_max) return -1;
   }
 }
 

@@ -57,8 +57,8 @@ typedef struct {
   double mu0_cold, mu0_warm;
   double push_cold, push_warm;
   int max_iter;
-  int refine;        /* iterative-refinement sweeps on the condensed system (0 = none) */
   double pivtol;     /* relative pivot tolerance of the inertia test */
+  double dw_max;     /* largest regularization delta_w of the inertia correction (W&B Algorithm IC: 1e40) */
 } or_options;
 
 typedef struct {

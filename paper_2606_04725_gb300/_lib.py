@@ -27,7 +27,8 @@ EXPORTED = ["nmpc_problem_defaults", "nmpc_options_defaults", "nmpc_build", "nmp
             "nmpc_bind", "nmpc_set_params", "nmpc_solve", "nmpc_get_solution", "nmpc_set_start",
             "nmpc_sensitivity", "nmpc_get_trace", "nmpc_time_phases", "nmpc_get_stats", "nmpc_instance_dims", "nmpc_structure_export",
             "nmpc_autotune_workspace_bytes", "nmpc_autotune",
-            "nmpc_solve_static", "nmpc_destroy", "nmpc_status_string", "nmpc_last_error"]
+            "nmpc_solve_static", "nmpc_debug_recip", "nmpc_probe_fp64",
+            "nmpc_destroy", "nmpc_status_string", "nmpc_last_error"]
 
 STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
@@ -47,7 +48,7 @@ class Options(C.Structure):
                 ("push_cold", C.c_double), ("push_warm", C.c_double), ("max_iter", C.c_int),
                 ("ordering", C.c_int), ("nd_leaf", C.c_int), ("use_graph", C.c_int), ("spin_limit", C.c_longlong),
                 ("pivtol", C.c_double), ("factor_mode", C.c_int), ("solve_mode", C.c_int),
-                ("panel_scale", C.c_int), ("amalgamation", C.c_int)]
+                ("panel_scale", C.c_int), ("amalgamation", C.c_int), ("dw_max", C.c_double)]
 
 
 class Info(C.Structure):
@@ -122,6 +123,8 @@ def lib():
                                                         C.POINTER(C.c_size_t)]
             L.nmpc_autotune.argtypes = [C.POINTER(Problem), C.POINTER(Options), _P, _P, C.c_size_t, _P, _P, _P,
                                         C.c_int, C.POINTER(TuneReport)]
+            L.nmpc_debug_recip.argtypes = [_P, _P, C.c_longlong, _P]
+            L.nmpc_probe_fp64.argtypes = [C.c_int, C.c_int, C.c_int, _P, C.POINTER(C.c_double)]
             L.nmpc_destroy.argtypes = [_P]
             L.nmpc_destroy.restype = None
             L.nmpc_status_string.argtypes = [C.c_int]
@@ -303,13 +306,11 @@ class Solver(Structure):
         model = self._p.model
         nx = {0: self._p.N, 1: self._p.g * self._p.g, 2: 1}[model]
         if model == 1:
-            sp_len = nx
+            sp_total = cnt * nx
         else:
-            Ts = {self.dims[i][2] for i in (range(self.n_instances) if instance < 0 else [instance])}
-            if len(Ts) != 1:
-                raise NmpcError(1, "set_params for several instances needs equal horizons")
-            sp_len = Ts.pop()
-        for a, want, name in ((x0, cnt * nx, "x0"), (setpoint, cnt * sp_len, "setpoint"), (u_prev, cnt, "u_prev")):
+            # all instances: T_i setpoints each, one instance after another
+            sp_total = sum(self.dims[i][2] for i in (range(self.n_instances) if instance < 0 else [instance]))
+        for a, want, name in ((x0, cnt * nx, "x0"), (setpoint, sp_total, "setpoint"), (u_prev, cnt, "u_prev")):
             if a is not None and _numel(a) != want:
                 raise ValueError(f"{name} has {_numel(a)} values, expected {want}")
         ptrs = [_ptr(a) for a in (x0, setpoint, u_prev)]
@@ -329,7 +330,12 @@ class Solver(Structure):
         return [{k: getattr(infos[i], k) for k, _ in Info._fields_} for i in range(self.n_instances)]
 
     def get_solution(self, instance=0, duals=False, out=None):
-        n, m, _ = self.dims[instance]
+        """Primal solution (and duals) of one instance, or of all instances
+        packed one after another for instance = -1."""
+        if instance < 0:
+            n, m = sum(d[0] for d in self.dims), sum(d[1] for d in self.dims)
+        else:
+            n, m, _ = self.dims[instance]
         if out is None:
             y = np.empty(n)
             dv = np.empty(2 * n + 6 * m) if duals else None
@@ -390,6 +396,32 @@ def solve_static(model, horizons, x0, setpoint, u_prev, y_out, opts=None, stream
     st = lib().nmpc_solve_static(C.byref(p), C.byref(o), stream, ptrs[0][0], ptrs[1][0], ptrs[2][0],
                                  ptrs[3][0], infos, on_dev)
     return st, [{k: getattr(infos[i], k) for k, _ in Info._fields_} for i in range(int(hz.size))]
+
+
+def debug_recip(x):
+    """nmpc_debug_recip: the pivot reciprocal of the factorization applied to a
+    float64 CUDA tensor (returns a new tensor)."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise TypeError("a contiguous float64 CUDA tensor is required")
+    out = torch.empty_like(x)
+    strm = torch.cuda.current_stream(x.device)
+    st = lib().nmpc_debug_recip(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), x.numel(),
+                                C.c_void_p(strm.cuda_stream))
+    if st != 0:
+        raise NmpcError(st, "nmpc_debug_recip failed")
+    return out
+
+
+def probe_fp64(kind=0, blocks_per_sm=4, iters=20000):
+    """nmpc_probe_fp64: measured FP64 TFLOP/s (kind 0: FMA, 1: f64 mma.sync)."""
+    import torch
+    v = C.c_double()
+    st = lib().nmpc_probe_fp64(int(kind), int(blocks_per_sm), int(iters),
+                               C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(v))
+    if st != 0:
+        raise NmpcError(st, "nmpc_probe_fp64 failed")
+    return v.value
 
 
 def _numel(a):

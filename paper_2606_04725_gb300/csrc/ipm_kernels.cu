@@ -402,9 +402,13 @@ __device__ void ctl_factor_one(const Dev& d, int i) {
   } else {
     c.factor_fail = 0;
     c.inertia_retries++;
-    if (c.dw == 0.0) c.dw = (c.dw_last == 0.0) ? DELTA_W0 : fmax(DELTA_WMIN, KAPPA_W_MINUS * c.dw_last);
-    else c.dw = (c.dw_last == 0.0) ? KAPPA_W_PLUS_BAR * c.dw : KAPPA_W_PLUS * c.dw;
-    if (c.dw > DELTA_WMAX) { c.status = 12; c.need_factor = 0; }
+    // the first trial value is always tried; a raised value above dw_max ends the instance
+    if (c.dw == 0.0) {
+      c.dw = (c.dw_last == 0.0) ? DELTA_W0 : fmax(DELTA_WMIN, KAPPA_W_MINUS * c.dw_last);
+    } else {
+      c.dw = (c.dw_last == 0.0) ? KAPPA_W_PLUS_BAR * c.dw : KAPPA_W_PLUS * c.dw;
+      if (c.dw > d.mc.dw_max) { c.status = 12; c.need_factor = 0; }
+    }
   }
   d.ctl[i] = c;
 }

@@ -50,7 +50,7 @@ constexpr int ST_CONVERGED = 1;  // mapped to NMPC_OK at the API
 constexpr double KAPPA_EPS = 10.0, KAPPA_MU = 0.2, THETA_MU = 1.5, TAU_MIN = 0.99, S_MAX = 100.0;
 constexpr double KAPPA_SIGMA = 1e10, GAMMA_THETA = 1e-5, GAMMA_PHI = 1e-5, DELTA_SW = 1.0;
 constexpr double S_THETA = 1.1, S_PHI = 2.3, ETA_PHI = 1e-4, GAMMA_ALPHA = 0.05;
-constexpr double DELTA_W0 = 1e-4, DELTA_WMIN = 1e-20, DELTA_WMAX = 1e40;
+constexpr double DELTA_W0 = 1e-4, DELTA_WMIN = 1e-20;
 constexpr double KAPPA_W_MINUS = 1.0 / 3.0, KAPPA_W_PLUS = 8.0, KAPPA_W_PLUS_BAR = 100.0;
 
 struct ModelConst {
@@ -60,6 +60,7 @@ struct ModelConst {
   double wu, ubar;                    // control-tracking cost wu dt (u - ubar)^2 (distillation)
   double inv_Ac, inv_At, inv_Ar;      // 1/holdups (distillation), computed once on the host
   double gamma, tol, pivtol;
+  double dw_max;                      // largest delta_w of the inertia correction
 };
 
 // Reduction chunks never straddle an instance.  kind 0: variables, 1: rows.

@@ -345,7 +345,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
     mc.xlo = sp.xlo; mc.xhi = sp.xhi; mc.ulo = sp.ulo; mc.uhi = sp.uhi;
     mc.wu = sp.wu; mc.ubar = sp.ubar;
     mc.inv_Ac = 1.0 / sp.Ac; mc.inv_At = 1.0 / sp.At; mc.inv_Ar = 1.0 / sp.Ar;
-    mc.gamma = sp.gamma; mc.tol = sp.tol; mc.pivtol = sp.pivtol;
+    mc.gamma = sp.gamma; mc.tol = sp.tol; mc.pivtol = sp.pivtol; mc.dw_max = sp.dw_max;
     const int nx = mc.nx, nu = mc.nu, WH = mc.WH, WS = mc.WS;
     A.n_inst = ni;
     A.sp_stride = (sp.model == MODEL_PLATE) ? nx : *std::max_element(sp.T.begin(), sp.T.end());
