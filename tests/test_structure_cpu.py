@@ -21,7 +21,7 @@ def P():
 
 def test_library_exports_every_declared_symbol(P):
     header = open(os.path.join(ROOT, "include", "nmpc.h")).read()
-    declared = set(re.findall(r"\b(nmpc_[a-z_]+)\s*\(", header))
+    declared = set(re.findall(r"\b(nmpc_[a-z0-9_]+)\s*\(", header))
     lib = P.lib()
     missing = [name for name in sorted(declared) if not hasattr(lib, name)]
     assert not missing, missing
