@@ -1,16 +1,22 @@
 """Benchmark: NMPC re-solves per second and ms per interior-point iteration at
-KKT tolerance 1e-8, parametric (one build, warm start + parameter update)
-versus rebuild-every-solve, on the distillation workload of 34 trays,
-200 intervals (the closed loop of 50 re-solves switching setpoint every 10).
+KKT tolerance 1e-8, parametric vs rebuild, on the batched workload: 256
+independent distillation columns (34 trays, feed tray 17) with horizons drawn
+from U{50..200}, solved together as one block-diagonal system.
 
-One step = one NMPC re-solve: parameter update (new initial state = the
-predicted state x_1 of the previous solution, new setpoint, u_prev) plus a
-warm-started solve to E_0 <= 1e-8, all on the GPU through the C ABI.
+One step = one closed-loop re-solve of the whole batch: the parameter update
+of every instance (new initial state = the predicted state x_1 of its
+previous solution, its setpoint, u_prev = its previous u_1) in one call, a
+warm-started solve of all instances to E_0 <= 1e-8, and the read of all
+solutions, through the C ABI.  `value` is instance re-solves per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Multi-GPU: one process per GPU (torchrun); each rank solves its own
-independently seeded column (instances shard with no exchange): weak scaling.
+Multi-GPU: one process per GPU (torchrun).  The batch is split into
+contiguous instance ranges balanced by each instance's factorization flops;
+each rank builds and solves its range with no exchange (the only collectives
+are the barrier and the max/sum of the timings): the total work is fixed.
+The reference arm (--impl reference) is the reference CPU implementation of
+the method, timed on the same closed loop on all host cores.
 """
 from __future__ import annotations
 
@@ -28,15 +34,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "distillation_N34_T200"
+WORKLOAD = "batch256_distillation_N34_T50_200"
+SINGLE = "distillation_N34_T200"
 METRIC = "NMPC re-solves/sec and ms per IPM iteration at 1e-8 KKT tol, parametric vs rebuild"
 UNIT = "re-solves/s"
-FP64_DFMA_PER_CLK_PER_SM = 2.0   # GB300: FP64 FMA rate 1/64 of FP32; probe measured 1.9
+FP64_DFMA_PER_CLK_PER_SM = 2.0   # GB300: FP64 FMA per clock and SM (the probe measures about 1.9)
 N_SM = 152
-# DRAM bytes (read + write) of one numeric factorization of the workload above:
-# the 11 level launches of k_factor_cluster, one ncu capture of the current kernel
-# and supernode partition (profiles/k_factor_cluster_distillation_N34_T200.md)
-FACTOR_DRAM_BYTES = 17.51e6
 
 
 def _peaks():
@@ -45,6 +48,11 @@ def _peaks():
             return json.load(f)
     except Exception:
         return {}
+
+
+def fp64_nominal_tflops(sm_max_mhz):
+    """Nominal FP64 rate: 152 SMs x 2 FMA per clock x 2 flops x the maximum SM clock."""
+    return N_SM * FP64_DFMA_PER_CLK_PER_SM * 2 * (sm_max_mhz or 2070.0) * 1e6 / 1e12
 
 
 def hbm_rooflines(st, ph, latency_bound=False):
@@ -131,10 +139,14 @@ def _dist():
     return rank, world, local
 
 
-def rank_seed(wl, rank):
-    """Seed of the column a rank solves: every rank gets its own initial state
-    (instances shard across ranks with no exchange)."""
-    return wl["seed"] + 1000 * rank
+def _reduce(x, world, op, device=None):
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
 
 
 def max_over_ranks(x, world, device=None):
@@ -142,20 +154,46 @@ def max_over_ranks(x, world, device=None):
     rank); x itself when there is one rank."""
     if world <= 1:
         return float(x)
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.MAX, device)
 
 
-def whole_job_rate(units_per_rank, seconds, world, device=None):
+def sum_over_ranks(x, world, device=None):
+    if world <= 1:
+        return float(x)
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.SUM, device)
+
+
+def whole_job_rate(units_this_rank, seconds, world, device=None):
     """Units all ranks processed over the slowest rank's time."""
-    return world * units_per_rank / max_over_ranks(seconds, world, device)
+    return sum_over_ranks(units_this_rank, world, device) / max_over_ranks(seconds, world, device)
 
 
+def batch_inputs(wl):
+    """Horizons, initial states and setpoints of the batch (seeded)."""
+    import paper_2606_04725_gb300.inputs as I
+    hz = I.batch_horizons(wl["n_instances"], wl["T_lo"], wl["T_hi"], wl["seed"])
+    x0s, sps = I.batch_distillation(wl["n_instances"], wl["N"], wl["Nf"], wl["seed"])
+    return hz, x0s, sps
+
+
+def packed_setpoints(hz, sps):
+    return np.concatenate([np.full(int(T), float(v)) for T, v in zip(hz, sps)])
+
+
+def closed_loop_index(hz, N):
+    """Positions of x_1 (N per instance) and u_1 in the packed solutions of
+    instances with horizons hz (y_i = [x_0 | x_1 u_1 | ...], n_i = N + T_i (N + 1))."""
+    offs = np.concatenate([[0], np.cumsum([N + int(T) * (N + 1) for T in hz])[:-1]])
+    ix = (offs[:, None] + N + np.arange(N)[None, :]).ravel()
+    iu = offs + 2 * N
+    return ix, iu
+
+
+# --------------------------------------------------------------- CPU legs
 def run_oracle_loop(wl, budget_s, max_steps=None, skip_cold=True):
-    """The oracle's closed loop on the same workload (CPU baseline)."""
+    """The oracle's closed loop on one column (single thread)."""
     import oracle as O
     import paper_2606_04725_gb300.inputs as I
     N, Nf, T, seed = wl["N"], wl["Nf"], wl["T"], wl["seed"]
@@ -181,25 +219,152 @@ def run_oracle_loop(wl, budget_s, max_steps=None, skip_cold=True):
     return times, iters
 
 
+def host_cores():
+    """Cores this process may run on (affinity) and the machine's count."""
+    try:
+        aff = len(os.sched_getaffinity(0))
+    except AttributeError:
+        aff = os.cpu_count() or 1
+    return aff, os.cpu_count() or aff
+
+
+def oracle_batch_loop(hz, x0s, sps, N, Nf, steps, threads, instances=None, budget_s=None):
+    """The oracle's closed loop on a batch: every instance solved cold, then
+    `steps` warm re-solves of all instances, each instance restarted from its
+    own previous solution (x0 <- x_1, u_prev <- u_1), as the GPU batch does.
+    The instances of a step run on `threads` host threads (the oracle's C
+    solver releases the interpreter lock).  Returns per-step seconds, the
+    iterations of every re-solve and the cold solves' seconds."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle as O
+    import paper_2606_04725_gb300.inputs as I
+    idx = list(range(len(hz))) if instances is None else list(instances)
+    probs = {i: O.distillation(N, Nf, int(hz[i]), x0s[i].copy(), np.full(int(hz[i]), sps[i]), I.U_REF) for i in idx}
+    states = {}
+
+    def cold(i):
+        st, info, _ = O.solve(probs[i])
+        states[i] = st
+        return info["iters"]
+
+    def warm(i):
+        p, st = probs[i], states[i]
+        p.set_params(x0=st.y[p.off_x(1):p.off_x(1) + N].copy(), uprev=st.y[p.off_u(1)])
+        st, info, _ = O.solve(p, state=st, warm=True)
+        states[i] = st
+        return info["iters"]
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(cold, idx))
+        cold_s = time.perf_counter() - t0
+        times, iters = [], []
+        for _ in range(steps):
+            if budget_s is not None and times and sum(times) > budget_s:
+                break
+            t0 = time.perf_counter()
+            its = list(ex.map(warm, idx))
+            times.append(time.perf_counter() - t0)
+            iters.append(its)
+    return times, iters, cold_s
+
+
 def reference_arm(args):
+    """--impl reference: the reference CPU implementation on the same batch
+    and closed loop, all host cores (rank 0 only under torchrun)."""
     rank, world, _ = _dist()
     if rank != 0:
         return
     import paper_2606_04725_gb300.inputs as I
     wl = I.WORKLOADS[WORKLOAD]
-    # each step: one warm oracle re-solve (bounded so the run ends in minutes)
-    times, iters = run_oracle_loop(wl, budget_s=240.0, max_steps=args.warmup + args.steps)
+    hz, x0s, sps = batch_inputs(wl)
+    cores, ncpu = host_cores()
+    times, iters, cold_s = oracle_batch_loop(hz, x0s, sps, wl["N"], wl["Nf"], args.warmup + args.steps, cores)
     t = times[args.warmup:] or times
-    v = len(t) / sum(t)
+    its = [i for step in (iters[args.warmup:] or iters) for i in step]
+    ni = len(hz)
+    v = ni * len(t) / sum(t)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": len(t), "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "N": wl["N"], "T": wl["T"], "tol": 1e-8},
-            "ms_per_ipm_iter": 1e3 * sum(t) / max(1, sum(iters[args.warmup:] or iters)),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(t)} warm re-solves of the closed loop"},
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "instances": ni, "N": wl["N"], "Nf": wl["Nf"],
+                                            "T_range": [wl["T_lo"], wl["T_hi"]], "tol": 1e-8},
+            "cpu_ms_per_instance_ipm_iter": 1e3 * sum(t) * cores / max(1, sum(its)),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"the whole batch ({ni} instances), {len(t)} warm closed-loop re-solves after "
+                                       f"{args.warmup} untimed ones, instances spread over {cores} threads "
+                                       f"(affinity {cores} of {ncpu} cores)",
+                             "cold_solve_s": cold_s},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# --------------------------------------------------------------- GPU legs
+def single_column(P, dev, steps=30, warmup=3, rank=0):
+    """The N = 34, T = 200 column alone (its closed loop of warm re-solves,
+    setpoint switching every 10): re-solves per second with inputs on the
+    device, per-phase times and the roofline of its factorization."""
+    import torch
+    import paper_2606_04725_gb300.inputs as I
+    wl = I.WORKLOADS[SINGLE]
+    N, Nf, T = wl["N"], wl["Nf"], wl["T"]
+    x0 = I.distillation_x0(N, Nf, wl["seed"] + 1000 * rank)
+    a, b = I.distillation_setpoints(N, wl["seed"])
+    s = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev)
+    n = s.dims[0][0]
+    sp = torch.tensor(np.stack([np.full(T, I.setpoint_schedule(a, b, k)) for k in range(warmup + steps + 1)]),
+                      dtype=torch.float64, device=dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    s.set_params(x0=x0, setpoint=np.full(T, a), u_prev=np.array([I.U_REF]))
+    first = s.solve(warm=False)[0]
+    s.get_solution(0, out=(y, None))
+    ms, iters, ok = [], [], first["status"] == 0
+    for q in range(warmup + steps):
+        flush.fill_(float(q))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.set_params(x0=y[N:2 * N], setpoint=sp[q + 1], u_prev=y[2 * N:2 * N + 1])
+        inf = s.solve(warm=True)[0]
+        s.get_solution(0, out=(y, None))
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        ok = ok and inf["status"] == 0
+        if q >= warmup:
+            ms.append(e0.elapsed_time(e1))
+            iters.append(inf["iters"])
+    # rebuild every re-solve (the paper's Base: cold; its WS: warm) on the same GPU
+    rb = {}
+    y_prev, du_prev = s.get_solution(0, duals=True)
+    for mode in ("cold", "warm"):
+        tt = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            s2 = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev)
+            s2.set_params(x0=y_prev[N:2 * N].copy(), setpoint=np.full(T, a), u_prev=y_prev[2 * N:2 * N + 1].copy())
+            if mode == "warm":
+                s2.set_start(0, y_prev, np.concatenate([du_prev[k] for k in ("zL", "zU", "s_p", "s_m", "w_p", "w_m", "b_p", "b_m")]))
+            s2.solve(warm=(mode == "warm"))
+            torch.cuda.synchronize()
+            tt.append(time.perf_counter() - t1)
+            s2.close()
+        rb[mode] = len(tt) / sum(tt)
+    ph = s.time_phases(reps=20)
+    st = s.stats()
+    v = len(ms) / (sum(ms) * 1e-3)
+    out = {"workload": SINGLE, "n": n, "resolves_per_s": v, "ms_per_resolve": sum(ms) / len(ms),
+           "ms_per_ipm_iter": sum(ms) / max(1, sum(iters)), "ipm_iters_per_resolve": sum(iters) / len(iters),
+           "cold_solve_iters": first["iters"], "statuses_ok": ok,
+           "ordering": ["auto", "natural", "nested_dissection", "two_sided"][st["ordering_used"]],
+           "phases_ms": {k: ph[k] for k in ("ms_eval", "ms_assemble", "ms_factor", "ms_solve")},
+           "factor_flops": st["factor_flops"], "factor_tflops": st["factor_flops"] / (ph["ms_factor"] * 1e-3) / 1e12,
+           "hbm": hbm_rooflines(st, ph, latency_bound=True),
+           "rebuild": {"cold_resolves_per_s": rb["cold"], "warm_resolves_per_s": rb["warm"],
+                       "parametric_over_rebuild_cold": v / rb["cold"]}}
+    s.close()
+    return out
 
 
 def plate_factorization(P, dev, peak):
@@ -217,61 +382,9 @@ def plate_factorization(P, dev, peak):
     out = {"workload": "plate_g64_S8_T50", "n": st["n_total"], "max_front": st["max_front"],
            "factor_flops": st["factor_flops"], "factor_ms": ph["ms_factor"], "solve_ms": ph["ms_solve"],
            "factor_tflops": tf, "factor_frac_of_peak": tf / peak,
-           "kernels": "k_big_diag, k_big_trsm, k_big_update (levels of large fronts); k_factor_cluster (small)",
+           "workspace_bytes": st["workspace_bytes"],
+           "kernels": "k_big_diag, k_big_trsm, k_big_update (levels of large fronts); small fronts below them",
            "hbm": hbm_rooflines(st, ph)}
-    s.close()
-    return out
-
-
-def batch_resolves(P, dev, peak, n_inst=256, resolves=3):
-    """Batch of 256 distillation columns (N = 34, T_i ~ U{50..200}) in one
-    block-diagonal system: instance re-solves per second over warm re-solves
-    of the whole batch (each instance restarted from its measured state), and
-    the factorization rate."""
-    import torch
-    import paper_2606_04725_gb300.inputs as I
-    wl = I.WORKLOADS["batch256_distillation_N34_T50_200"]
-    hz = I.batch_horizons(n_inst, wl["T_lo"], wl["T_hi"], wl["seed"])
-    x0s, sps = I.batch_distillation(n_inst, 34, 17, wl["seed"])
-    # schedule chosen by the library's autotuner: one cold batch solve per candidate
-    t0 = time.perf_counter()
-    opts, rep = P.autotune(P.MODEL_DISTILLATION, hz, x0=np.concatenate(x0s),
-                           setpoint=np.concatenate([np.full(T, v) for T, v in zip(hz, sps)]),
-                           u_prev=np.full(n_inst, I.U_REF), device=dev, N=34, Nf=17)
-    tune_s = time.perf_counter() - t0
-    s = P.Solver(P.MODEL_DISTILLATION, hz, N=34, Nf=17, device=dev, opts=opts)
-    for i, T in enumerate(hz):
-        s.set_params(instance=i, x0=x0s[i], setpoint=np.full(T, sps[i]), u_prev=np.array([I.U_REF]))
-    infos = s.solve()
-    ok = all(f["status"] == 0 for f in infos)
-    ms, iters = [], []
-    stream = s.stream
-    for _ in range(resolves):
-        for i, T in enumerate(hz):
-            y = s.get_solution(i)
-            s.set_params(instance=i, x0=y[34:68].copy(), setpoint=np.full(T, sps[i]), u_prev=y[68:69].copy())
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        infos = s.solve(warm=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        iters.append(max(f["iters"] for f in infos))
-        ok = ok and all(f["status"] == 0 for f in infos)
-    ph = s.time_phases(reps=2)
-    st = s.stats()
-    tf = st["factor_flops"] / (ph["ms_factor"] * 1e-3) / 1e12
-    out = {"workload": "batch256_distillation_N34_T50_200", "instances": n_inst, "n": st["n_total"],
-           "instance_resolves_per_s": n_inst * len(ms) / (sum(ms) * 1e-3), "ms_per_batch_resolve": sum(ms) / len(ms),
-           "max_ipm_iters_per_batch_resolve": max(iters), "statuses_ok": ok,
-           "factor_ms": ph["ms_factor"], "factor_tflops": tf, "factor_frac_of_peak": tf / peak,
-           "hbm": hbm_rooflines(st, ph),
-           "autotune": {"seconds": tune_s,
-                        "chosen": {"ordering": opts.ordering, "nd_leaf": opts.nd_leaf, "panel_scale": opts.panel_scale,
-                                   "amalgamation": opts.amalgamation},
-                        "ms_per_ipm_iter_by_candidate": [
-                            [c["ordering"], c["nd_leaf"], c["panel_scale"], c["amalgamation"], round(c["ms_per_iter"], 3)]
-                            for c in rep["candidates"]]}}
     s.close()
     return out
 
@@ -289,22 +402,20 @@ def paper_column_resolves(P, dev, resolves=40, warmup=3):
     N, Nf, T = wl["N"], wl["Nf"], wl["T"]
     s = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev, **I.PAPER_COLUMN)
     n = s.dims[0][0]
-    ox1, ou1 = N, 2 * N
     sp = torch.full((T,), I.PAPER_XBAR, dtype=torch.float64, device=dev)
     y = torch.empty(n, dtype=torch.float64, device=dev)
     s.set_params(x0=I.distillation_x0(N, Nf, wl["seed"]), setpoint=np.full(T, I.PAPER_XBAR),
                  u_prev=np.array([I.U_REF]))
     first = s.solve(warm=False)[0]
     s.get_solution(0, out=(y, None))
-    stream = s.stream
     ms, iters, ok = [], [], first["status"] == 0
     for q in range(warmup + resolves):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.set_params(x0=y[ox1:ox1 + N], setpoint=sp, u_prev=y[ou1:ou1 + 1])
+        e0.record(s.stream)
+        s.set_params(x0=y[N:2 * N], setpoint=sp, u_prev=y[2 * N:2 * N + 1])
         inf = s.solve(warm=True)[0]
         s.get_solution(0, out=(y, None))
-        e1.record(stream)
+        e1.record(s.stream)
         torch.cuda.synchronize()
         ok = ok and inf["status"] == 0
         if q >= warmup:
@@ -320,17 +431,22 @@ def paper_column_resolves(P, dev, resolves=40, warmup=3):
     return out
 
 
+def fp64_probe(P):
+    """Measured FP64 rates of this GPU (library probe kernels): FMA chains and
+    the f64 tensor-core mma.sync, four 256-thread blocks per SM."""
+    return {"dfma_tflops": P._lib.probe_fp64(0, 4, 20000), "dmma_tflops": P._lib.probe_fp64(1, 4, 4000),
+            "note": "independent accumulators on every thread (FMA) or warp (mma.sync m8n8k4); one timed launch"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=47)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--rebuild-steps", type=int, default=3)
-    ap.add_argument("--no-plate", action="store_true", help="skip the full-size heated-plate factorization")
-    ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch")
-    ap.add_argument("--no-paper-column", action="store_true", help="skip the paper's own column (N=32, T=90)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the single column, the full-size plate, the paper's column and the rebuild variants")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the interior-point loop from the host instead of the conditional graph "
                          "(same kernels; for profilers that cannot see into conditional graphs)")
@@ -347,45 +463,59 @@ def main():
     dev = torch.device("cuda", local)
     import paper_2606_04725_gb300 as P
     import paper_2606_04725_gb300.inputs as I
+    from paper_2606_04725_gb300.partition import instance_weights, rank_slice
     P.build()
     wl = I.WORKLOADS[WORKLOAD]
-    N, Nf, T = wl["N"], wl["Nf"], wl["T"]
-    seed = rank_seed(wl, rank)
-    x0 = I.distillation_x0(N, Nf, seed)
-    a, b = I.distillation_setpoints(N, wl["seed"])
-    opts = P.options(use_graph=0) if args.host_loop else None
+    N, Nf = wl["N"], wl["Nf"]
+    hz_all, x0s_all, sps_all = batch_inputs(wl)
+    # contiguous instance ranges balanced by factorization flops (one range per rank)
+    weights = instance_weights(P.MODEL_DISTILLATION, hz_all, N=N, Nf=Nf)
+    i0, i1 = rank_slice(weights, rank, world)
+    hz, x0s, sps = hz_all[i0:i1], x0s_all[i0:i1], sps_all[i0:i1]
+    ni = len(hz)
+    sp_host = packed_setpoints(hz, sps)
+    # the schedule (ordering, amalgamation, solve form) chosen by the library's autotuner
+    t0 = time.perf_counter()
+    opts, rep = P.autotune(P.MODEL_DISTILLATION, hz, x0=x0s.ravel().copy(), setpoint=sp_host,
+                           u_prev=np.full(ni, I.U_REF), device=dev, N=N, Nf=Nf)
+    tune_s = time.perf_counter() - t0
+    if args.host_loop:
+        opts.use_graph = 0
     torch.cuda.synchronize()
-    t_build = time.perf_counter()
-    s = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev, opts=opts)
-    build_s = time.perf_counter() - t_build
-    n, m, _ = s.dims[0]
-    ox1, ou1 = N, 2 * N  # offsets of x_1 and u_1 in y = [x_0 | x_1 u_1 | ...]
-    stream = s.stream
-    # device-resident inputs: setpoint trajectories and the previous solution
-    total = args.warmup + args.steps
-    sp_dev = torch.tensor(np.stack([np.full(T, I.setpoint_schedule(a, b, k)) for k in range(total + 1)]),
-                          dtype=torch.float64, device=dev)
-    y_dev = torch.empty(n, dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    s = P.Solver(P.MODEL_DISTILLATION, hz, N=N, Nf=Nf, device=dev, opts=opts)
+    build_s = time.perf_counter() - t0
+    n_tot = sum(d[0] for d in s.dims)
+    ix_h, iu_h = closed_loop_index(hz, N)
+    ix, iu = torch.tensor(ix_h, device=dev), torch.tensor(iu_h, device=dev)
+    SP = torch.tensor(sp_host, dtype=torch.float64, device=dev)
+    X0 = torch.tensor(x0s.ravel(), dtype=torch.float64, device=dev)
+    U = torch.full((ni,), I.U_REF, dtype=torch.float64, device=dev)
+    Y = torch.empty(n_tot, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
-    t_cold = time.perf_counter()
-    s.set_params(x0=x0, setpoint=np.full(T, a), u_prev=np.array([I.U_REF]))
-    info0 = s.solve(warm=False)[0]
-    assert info0["status"] == 0, info0
-    s.get_solution(0, out=(y_dev, None))
+    t0 = time.perf_counter()
+    s.set_params(x0=X0, setpoint=SP, u_prev=U)
+    infos = s.solve(warm=False)
+    s.get_solution(-1, out=(Y, None))
     torch.cuda.synchronize()
-    cold_s = time.perf_counter() - t_cold
+    cold_s = time.perf_counter() - t0
+    cold_ok = all(f["status"] == 0 for f in infos)
+    cold_iters = max(f["iters"] for f in infos)
 
-    def step(k, warm=True):
-        s.set_params(x0=y_dev[ox1:ox1 + N], setpoint=sp_dev[k], u_prev=y_dev[ou1:ou1 + 1])
-        inf = s.solve(warm=warm)[0]
-        s.get_solution(0, out=(y_dev, None))
+    def step():
+        # closed loop on the device: x0 <- x_1, u_prev <- u_1 of every instance
+        torch.index_select(Y, 0, ix, out=X0)
+        torch.index_select(Y, 0, iu, out=U)
+        s.set_params(x0=X0, setpoint=SP, u_prev=U)
+        inf = s.solve(warm=True)
+        s.get_solution(-1, out=(Y, None))
         return inf
 
-    for k in range(1, args.warmup):
-        step(k)
+    for _ in range(args.warmup):
+        step()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    iters, stats_ = [], []
+    batch_iters, mean_iters, ok = [], [], cold_ok
     launches0 = s.stats()["kernel_launches"]
     if world > 1:
         torch.distributed.barrier()
@@ -394,104 +524,130 @@ def main():
     with ClockSampler(local) as clk:
         for q in range(args.steps):
             flush.fill_(float(q))                      # L2 flush outside the timed events
-            ev[q][0].record(stream)
-            inf = step(args.warmup + q)
-            ev[q][1].record(stream)
-            iters.append(inf["iters"])
-            stats_.append(inf["status"])
+            ev[q][0].record(s.stream)
+            inf = step()
+            ev[q][1].record(s.stream)
+            batch_iters.append(max(f["iters"] for f in inf))
+            mean_iters.append(sum(f["iters"] for f in inf) / ni)
+            ok = ok and all(f["status"] == 0 for f in inf)
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = s.stats()["kernel_launches"] - launches0
     ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     tot_ms = max_over_ranks(sum(ms), world, dev)
-    value = whole_job_rate(args.steps, tot_ms * 1e-3, world, dev)
-    ms_iter = tot_ms / max(1, sum(iters))
+    value = whole_job_rate(ni * args.steps, tot_ms * 1e-3, world, dev)
 
-    # end to end: host inputs (pinned), host result, copies inside the timed region
-    hx = torch.empty(N, dtype=torch.float64).pin_memory()
-    hsp = torch.empty(T, dtype=torch.float64).pin_memory()
-    hu = torch.empty(1, dtype=torch.float64).pin_memory()
-    hy = torch.empty(n, dtype=torch.float64).pin_memory()
-    s.get_solution(0, out=(hy, None))
-    e2e_steps = min(args.steps, 20)
+    # end to end through the C ABI with host buffers: the parameters of every
+    # instance copied in and every solution copied out inside the timed region
+    X0h = torch.empty(ni * N, dtype=torch.float64).pin_memory()
+    Uh = torch.empty(ni, dtype=torch.float64).pin_memory()
+    SPh = torch.tensor(sp_host, dtype=torch.float64).pin_memory()
+    Yh = torch.empty(n_tot, dtype=torch.float64).pin_memory()
+    s.get_solution(-1, out=(Yh.numpy(), None))
+    e2e_steps = min(args.steps, 10)
+    e2e_s = 0.0
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
     for q in range(e2e_steps):
-        hx.copy_(hy[ox1:ox1 + N])
-        hu[0] = hy[ou1]
-        hsp.fill_(I.setpoint_schedule(a, b, args.warmup + args.steps + q))
-        s.set_params(x0=hx.numpy(), setpoint=hsp.numpy(), u_prev=hu.numpy())
+        flush.fill_(float(q))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        yh = Yh.numpy()
+        np.take(yh, ix_h, out=X0h.numpy())
+        np.take(yh, iu_h, out=Uh.numpy())
+        s.set_params(x0=X0h.numpy(), setpoint=SPh.numpy(), u_prev=Uh.numpy())
         s.solve(warm=True)
-        s.get_solution(0, out=(hy.numpy(), None))
-    torch.cuda.synchronize()
-    e2e = whole_job_rate(e2e_steps, time.perf_counter() - t0, world, dev)
+        s.get_solution(-1, out=(yh, None))
+        e2e_s += time.perf_counter() - t0
+    e2e = whole_job_rate(ni * e2e_steps, e2e_s, world, dev)
 
-    # rebuild-every-solve comparison (paper Base / WS): destroy + build + bind + solve
-    rb = {}
-    y_prev, du_prev = s.get_solution(0, duals=True)
-    for mode in ("cold", "warm"):
-        tt = []
-        for q in range(args.rebuild_steps):
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            s2 = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev)
-            s2.set_params(x0=y_prev[ox1:ox1 + N].copy(), setpoint=np.full(T, a), u_prev=y_prev[ou1:ou1 + 1].copy())
-            if mode == "warm":
-                s2.set_start(0, y_prev, np.concatenate([du_prev[k] for k in ("zL", "zU", "s_p", "s_m", "w_p", "w_m", "b_p", "b_m")]))
-            s2.solve(warm=(mode == "warm"))
-            torch.cuda.synchronize()
-            tt.append(time.perf_counter() - t1)
-            s2.close()
-            del s2
-        rb[mode] = len(tt) / sum(tt)
-
-    # roofline of the dominant kernel (numeric factorization, FP64 FMA bound)
-    ph = s.time_phases(reps=20)
+    # roofline of the dominant kernel: the numeric factorization, FP64-bound
+    ph = s.time_phases(reps=5)
     st = s.stats()
-    achieved = st["factor_flops"] / (ph["ms_factor"] * 1e-3) / 1e12
     clk = clk.summary()
-    peak = N_SM * FP64_DFMA_PER_CLK_PER_SM * 2 * (clk["sm_max_mhz"] or 2070.0) * 1e6 / 1e12
+    peak = fp64_nominal_tflops(clk["sm_max_mhz"])
+    achieved = st["factor_flops"] / (ph["ms_factor"] * 1e-3) / 1e12
+    probe = fp64_probe(P)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N, "Nf": Nf, "T": T, "n": n, "m": m, "tol": 1e-8,
-                       "ordering": ["auto", "natural", "nested_dissection"][st["ordering_used"]],
-                       "amalgamation": ["auto", "relaxed", "sibling_limited"][st["amalgamation_used"]],
-                       "l2": "flushed between re-solves (256 MB write)"},
-            "ms_per_ipm_iter": ms_iter, "ipm_iters_per_resolve": sum(iters) / len(iters),
-            "statuses_ok": all(x == 0 for x in stats_),
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instances": len(hz_all), "instances_this_rank": ni,
+                       "N": N, "Nf": Nf, "T_range": [wl["T_lo"], wl["T_hi"]], "n": n_tot, "tol": 1e-8,
+                       "ordering": ["auto", "natural", "nested_dissection", "two_sided"][st["ordering_used"]],
+                       "nd_leaf": opts.nd_leaf, "amalgamation": opts.amalgamation, "panel_scale": opts.panel_scale,
+                       "factor_mode": opts.factor_mode,
+                       "l2": "flushed between re-solves (256 MB write); the batch's workspace is larger than L2"},
+            "ms_per_ipm_iter": sum(ms) / max(1, sum(batch_iters)),
+            "ipm_iters_per_resolve": {"batch": sum(batch_iters) / len(batch_iters),
+                                      "instance_mean": sum(mean_iters) / len(mean_iters)},
+            "statuses_ok": ok,
             "step_ms": {"median": statistics.median(ms), "min": min(ms), "max": max(ms)},
-            "closed_loop": {"build_s": build_s, "cold_solve_s": cold_s, "cold_solve_iters": info0["iters"],
-                            "resolves": args.steps + 1,
-                            "resolves_per_s_incl_build": (args.steps + 1) / (build_s + cold_s + tot_ms * 1e-3)},
-            "rebuild": {"cold_resolves_per_s": rb["cold"], "warm_resolves_per_s": rb["warm"],
-                        "parametric_over_rebuild_cold": value / rb["cold"]},
+            "closed_loop": {"autotune_s": tune_s, "build_s": build_s, "cold_solve_s": cold_s,
+                            "cold_solve_iters": cold_iters, "resolves": args.warmup + args.steps,
+                            "instance_resolves_per_s_incl_build":
+                                ni * (args.warmup + args.steps + 1) / (build_s + cold_s + tot_ms * 1e-3 * (args.warmup + args.steps) / args.steps)},
             "wall_s_timed": wall,
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * (N + T + 1), "d2h_bytes_per_step": 8 * n},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * (ni * N + sp_host.size + ni),
+                    "d2h_bytes_per_step": 8 * n_tot},
             "gpu_launches": int(launches),
             "phases_ms": {k: ph[k] for k in ("ms_eval", "ms_assemble", "ms_factor", "ms_solve")},
-            "hbm": hbm_rooflines(st, ph, latency_bound=True),
+            "hbm": hbm_rooflines(st, ph),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": FACTOR_DRAM_BYTES,
-                         "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of the 11 level launches "
-                                          "of one factorization, one ncu capture",
-                         "kernel": "k_factor_cluster (the level launches of one numeric factorization)",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "numeric factorization of the whole batch (the launches of one factorization)",
                          "flops_per_launch_set": st["factor_flops"],
-                         "peak_basis": "152 SMs x 2 FP64 FMA/clock x max SM clock (nominal FP64 rate)"},
+                         "peak_basis": "152 SMs x 2 FP64 FMA/clock x max SM clock (nominal FP64 rate)",
+                         "frac_of_measured_dfma": achieved / probe["dfma_tflops"]},
+            "fp64_probe": probe,
+            "autotune": {"seconds": tune_s,
+                         "candidates": [[c["ordering"], c["nd_leaf"], c["panel_scale"], c["amalgamation"],
+                                         round(c["ms_per_iter"], 3)] for c in rep["candidates"]]},
             "clocks": clk}
-    if not args.no_plate:
+    if not args.no_extras:
+        t0 = time.perf_counter()
+        rb = {}
+        y_prev, du_prev = s.get_solution(-1, duals=True)
+        offs_n = np.concatenate([[0], np.cumsum([d[0] for d in s.dims])])
+        offs_m = np.concatenate([[0], np.cumsum([d[1] for d in s.dims])])
+        for mode in ("cold", "warm"):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            s2 = P.Solver(P.MODEL_DISTILLATION, hz, N=N, Nf=Nf, device=dev, opts=opts)
+            s2.set_params(x0=np.ascontiguousarray(y_prev[ix_h]), setpoint=sp_host,
+                          u_prev=np.ascontiguousarray(y_prev[iu_h]))
+            if mode == "warm":
+                for i in range(ni):
+                    a, b = offs_n[i], offs_n[i + 1]
+                    c, d = offs_m[i], offs_m[i + 1]
+                    du = np.concatenate([du_prev["zL"][a:b], du_prev["zU"][a:b]] +
+                                        [du_prev[k][c:d] for k in ("s_p", "s_m", "w_p", "w_m", "b_p", "b_m")])
+                    s2.set_start(i, np.ascontiguousarray(y_prev[a:b]), du)
+            s2.solve(warm=(mode == "warm"))
+            torch.cuda.synchronize()
+            rb[mode] = ni / (time.perf_counter() - t1)
+            s2.close()
+        line["rebuild"] = {"cold_resolves_per_s": rb["cold"], "warm_resolves_per_s": rb["warm"],
+                           "parametric_over_rebuild_cold": value / rb["cold"] if world == 1 else None,
+                           "note": "destroy + analysis + bind + solve of the whole batch per re-solve, one each"}
+    s.close()
+    del flush
+    if not args.no_extras:
+        line["single_column"] = single_column(P, dev, rank=rank)
         line["plate_full_size"] = plate_factorization(P, dev, peak)
-    if not args.no_batch:
-        line["batch_256"] = batch_resolves(P, dev, peak)
-    if not args.no_paper_column:
         line["paper_column"] = paper_column_resolves(P, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times, its = run_oracle_loop(wl, budget_s=20.0)
-        line["cpu_baseline"] = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{len(times)} warm re-solves of the same closed loop (single thread)",
-                                "ms_per_ipm_iter": 1e3 * sum(times) / max(1, sum(its))}
+        cores, ncpu = host_cores()
+        t_all, it_all, cold_all = oracle_batch_loop(hz, x0s, sps, N, Nf, 3, cores)
+        sample = list(range(0, ni, 32))
+        t_one, it_one, _ = oracle_batch_loop(hz, x0s, sps, N, Nf, 3, 1, instances=sample)
+        line["cpu_baseline"] = {"value": ni * len(t_all) / sum(t_all), "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"the whole batch ({ni} instances): cold solves ({cold_all:.1f} s), then "
+                                          f"{len(t_all)} warm closed-loop re-solves, instances over {cores} threads "
+                                          f"(affinity {cores} of {ncpu} cores)",
+                                "single_thread": {"value": len(sample) * len(t_one) / sum(t_one), "unit": UNIT,
+                                                  "cores": 1,
+                                                  "sample": f"{len(sample)} instances (every 32nd), {len(t_one)} "
+                                                            f"warm closed-loop re-solves each"}}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

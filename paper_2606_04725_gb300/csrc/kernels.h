@@ -30,6 +30,7 @@ __global__ void k_eval_rows(Dev d, int use_trial, int with_jac);
 __global__ void k_eval_vars(Dev d, int use_trial);
 __global__ void k_eval(Dev d, int use_trial, int with_jac, int nbr);
 __global__ void k_set_params(Dev d, int i0, int i1, const double* x0, const double* sp, const double* up, int sp_len);
+__global__ void k_set_params_packed(Dev d, const int* spoff, const double* x0, const double* sp, const double* up);
 __global__ void k_init_vars(Dev d, int warm, double push);
 __global__ void k_init_rows(Dev d, int warm, double push);
 

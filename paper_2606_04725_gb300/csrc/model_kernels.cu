@@ -349,6 +349,23 @@ __global__ void k_set_params(Dev d, int i0, int i1, const double* x0, const doub
   }
 }
 
+// All instances' parameters from arrays packed one instance after another,
+// with T_i setpoints for instance i (instances of unequal horizons): one
+// block per instance, spoff[i] = first setpoint of instance i.
+__global__ void k_set_params_packed(Dev d, const int* spoff, const double* x0, const double* sp, const double* up) {
+  const int i = blockIdx.x, nx = d.mc.nx;
+  const int s0 = spoff[i], len = spoff[i + 1] - s0;
+  for (int q = threadIdx.x; q < nx + len + 1; q += blockDim.x) {
+    if (q < nx) {
+      if (x0) d.p_x0[(size_t)i * nx + q] = x0[(size_t)i * nx + q];
+    } else if (q < nx + len) {
+      if (sp) d.p_sp[(size_t)i * d.sp_stride + (q - nx)] = sp[s0 + (q - nx)];
+    } else if (up) {
+      d.p_uprev[i] = up[i];
+    }
+  }
+}
+
 // Cold-start trajectory from the parameters: x_k = p_x0 for all k, controls
 // at u_prev (distillation) or the midpoint of their bounds, then pushed into
 // the bounds (W&B Sec. 3.6).  Warm start only pushes the previous point.

@@ -50,6 +50,8 @@ struct nmpc_handle {
   long long* d_inst_Lend = nullptr;
   int* d_flags = nullptr;
   double* d_stage = nullptr;  // staging of host parameter arrays
+  int* d_inst_spoff = nullptr;  // first setpoint of each instance in a packed all-instance array
+  long long sp_packed = 0;      // setpoints of all instances packed (sum of their horizons, or g*g each)
   int* h_flags = nullptr;     // pinned
   std::vector<int> lvl_ptr;
   std::vector<int> lvl_smem_factor, lvl_smem_solve, lvl_smem_bwd;  // bytes per level
@@ -156,6 +158,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   h->d_inst_Lbeg = cv.take<long long>(ni); h->d_inst_Lend = cv.take<long long>(ni);
   h->d_flags = cv.take<int>(16);  // [0..2] summary, [3] wait timeout, [4..7] adjoint norms, [8..10] graph trip counts
   h->d_stage = cv.take<double>((size_t)ni * (A.mc.nx + A.sp_stride + 1));
+  h->d_inst_spoff = cv.take<int>(ni + 1);
   h->d_ctl_save = cv.take<Ctl>(ni);
   d.trace = cv.take<double>((size_t)ni * (h->opt.max_iter + 2) * 8);
   d.red_cnt = cv.take<int>(ni + 1);
@@ -586,6 +589,7 @@ void nmpc_options_defaults(nmpc_options* o) {
   o->tol = 1e-8; o->gamma = 1e-8; o->mu0_cold = 0.1; o->mu0_warm = 1e-8;
   o->push_cold = 1e-2; o->push_warm = 1e-9; o->max_iter = 200; o->ordering = NMPC_ORDER_AUTO;
   o->nd_leaf = 1; o->use_graph = 1; o->spin_limit = 10000000LL; o->pivtol = 1e-12;
+  o->dw_max = 1e40;
 }
 
 nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void* cuda_stream, nmpc_handle** out) {
@@ -607,8 +611,9 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   sp.wu = prob->wu; sp.ubar = prob->ubar;
   sp.gamma = h->opt.gamma; sp.tol = h->opt.tol;
   sp.ordering = h->opt.ordering; sp.nd_leaf = h->opt.nd_leaf; sp.pivtol = h->opt.pivtol;
+  sp.dw_max = h->opt.dw_max;
   sp.amalgamation = h->opt.amalgamation;
-  if (!(prob->dt > 0) || h->opt.max_iter < 1 || !(h->opt.tol > 0) || !(h->opt.gamma > 0)) {
+  if (!(prob->dt > 0) || h->opt.max_iter < 1 || !(h->opt.tol > 0) || !(h->opt.gamma > 0) || !(h->opt.dw_max > 0)) {
     delete h;
     return NMPC_ERR_INVALID;
   }
@@ -815,6 +820,13 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   std::vector<Chunk> ch = A.chunks;
   CUDA_TRY(h, cudaMemsetAsync(ws, 0, h->ws_bytes, st));
   CUDA_TRY(h, up(d.inst_T, A.inst_T, st)); CUDA_TRY(h, up(d.inst_voff, A.inst_voff, st));
+  {
+    std::vector<int> spoff(A.n_inst + 1, 0);
+    for (int i = 0; i < A.n_inst; ++i) spoff[i + 1] = spoff[i] + (A.mc.model == MODEL_PLATE ? A.mc.nx : A.inst_T[i]);
+    h->sp_packed = spoff[A.n_inst];
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_inst_spoff, spoff.data(), spoff.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));  // spoff is a local
+  }
   CUDA_TRY(h, up(d.inst_roff, A.inst_roff, st)); CUDA_TRY(h, up(d.inst_woff, A.inst_woff, st));
   CUDA_TRY(h, up(d.inst_n, A.inst_n, st)); CUDA_TRY(h, up(d.inst_m, A.inst_m, st));
   CUDA_TRY(h, up(d.inst_nz, A.inst_nz, st));
@@ -951,10 +963,27 @@ nmpc_status nmpc_set_params(nmpc_handle* h, int instance, const double* x0, cons
   const int cnt = i1 - i0, nx = A.mc.nx;
   // setpoint values per instance as the caller packs them
   int sp_len = A.sp_stride;
+  bool packed = false;  // all instances, unequal horizons: T_i setpoints each, one after another
   if (A.mc.model != MODEL_PLATE) {
     for (int i = i0; i < i1; ++i)
-      if (A.inst_T[i] != A.inst_T[i0]) return fail(h, NMPC_ERR_INVALID, "set_params for several instances needs equal horizons; set them one by one");
+      if (A.inst_T[i] != A.inst_T[i0]) packed = true;
     sp_len = A.inst_T[i0];
+  }
+  if (packed) {
+    const double *sx = x0, *ss = setpoint, *su = u_prev;
+    if (!on_device) {
+      double* p = h->d_stage;  // nx + sp_stride + 1 doubles per instance: room for the packed setpoints
+      if (x0) { CUDA_TRY(h, cudaMemcpyAsync(p, x0, (size_t)cnt * nx * 8, cudaMemcpyHostToDevice, h->stream)); sx = p; }
+      p += (size_t)cnt * nx;
+      if (setpoint) { CUDA_TRY(h, cudaMemcpyAsync(p, setpoint, (size_t)h->sp_packed * 8, cudaMemcpyHostToDevice, h->stream)); ss = p; }
+      p += h->sp_packed;
+      if (u_prev) { CUDA_TRY(h, cudaMemcpyAsync(p, u_prev, (size_t)cnt * 8, cudaMemcpyHostToDevice, h->stream)); su = p; }
+    }
+    k_set_params_packed<<<cnt, TPB, 0, h->stream>>>(h->d, h->d_inst_spoff, sx, ss, su);
+    ++h->launches;
+    CUDA_TRY(h, cudaGetLastError());
+    if (!on_device) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return NMPC_OK;
   }
   const double *sx = x0, *ss = setpoint, *su = u_prev;
   if (!on_device) {
@@ -1060,10 +1089,12 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
 nmpc_status nmpc_get_solution(nmpc_handle* h, int instance, double* y, double* duals, int on_device) {
   if (!h || !h->bound) return fail(h, NMPC_ERR_INVALID, "handle not bound");
   const Analysis& A = h->A;
-  if (instance < 0 || instance >= A.n_inst) return fail(h, NMPC_ERR_INVALID, "instance out of range");
+  if (instance < -1 || instance >= A.n_inst) return fail(h, NMPC_ERR_INVALID, "instance out of range");
   if (!h->have_solution) return fail(h, NMPC_NOT_SOLVED, "no solution yet");
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  const int vo = A.inst_voff[instance], ro = A.inst_roff[instance], n = A.inst_n[instance], m = A.inst_m[instance];
+  // instance -1: every instance, packed one after another (the workspace's own layout)
+  const int vo = instance < 0 ? 0 : A.inst_voff[instance], ro = instance < 0 ? 0 : A.inst_roff[instance];
+  const int n = instance < 0 ? A.n : A.inst_n[instance], m = instance < 0 ? A.m : A.inst_m[instance];
   const Dev& d = h->d;
   if (y) CUDA_TRY(h, cudaMemcpyAsync(y, d.y + vo, n * 8, k, h->stream));
   if (duals) {

@@ -54,3 +54,29 @@ def test_oracle_closed_loop_is_bounded_and_converges():
     times, iters = bench.run_oracle_loop(wl, budget_s=30.0, max_steps=3)
     assert len(times) == 3 and all(t > 0 for t in times)
     assert all(0 < i < 30 for i in iters)
+
+
+def test_oracle_batch_loop_restarts_every_instance_from_its_own_solution():
+    """The CPU leg of the batch: cold solves, then warm closed-loop re-solves
+    of every instance on host threads; one thread and two give the same
+    iteration counts (the instances are independent)."""
+    import numpy as np
+    import paper_2606_04725_gb300.inputs as I
+    hz = np.array([20, 24, 16], dtype=np.int32)
+    x0s = np.stack([I.distillation_x0(12, 5, seed=30 + i) for i in range(3)])
+    sps = np.array([0.78, 0.8, 0.82])
+    t2, it2, _ = bench.oracle_batch_loop(hz, x0s, sps, 12, 5, steps=2, threads=2)
+    t1, it1, _ = bench.oracle_batch_loop(hz, x0s, sps, 12, 5, steps=2, threads=1)
+    assert len(t2) == 2 and all(t > 0 for t in t2)
+    assert it1 == it2 and all(len(s) == 3 and all(0 < i < 30 for i in s) for s in it2)
+
+
+def test_closed_loop_index_points_at_x1_and_u1():
+    import numpy as np
+    hz = [3, 5]
+    N = 4
+    ix, iu = bench.closed_loop_index(hz, N)
+    n0 = N + 3 * (N + 1)
+    assert list(ix) == [4, 5, 6, 7, n0 + 4, n0 + 5, n0 + 6, n0 + 7]
+    assert list(iu) == [8, n0 + 8]
+    assert np.array_equal(bench.packed_setpoints(hz, [0.9, 0.95]), [0.9] * 3 + [0.95] * 5)
