@@ -1,8 +1,9 @@
 """Seeded synthetic inputs shaped like the paper's workloads.
 
 Only random numbers and fixed recipes live here; none of the method's
-arithmetic.  The distillation initial states start from steady states that a
-committed oracle script wrote to tests/golden (steady_state_N*_Nf*.txt).
+arithmetic.  The distillation initial states start from steady states stored
+as package data (data/steady_state_N*_Nf*.txt), written once by a committed
+script of the test suite that runs the reference CPU implementation.
 
 Recipes (one per workload):
   distillation  x0 = steady state at u_ref = 2.51459 plus N(0, 0.02) noise,
@@ -28,13 +29,12 @@ import os
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-GOLDEN = os.path.join(ROOT, "tests", "golden")
+DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
 U_REF = 2.51459
 
 
 def steady_state(N: int, Nf: int) -> np.ndarray:
-    return np.loadtxt(os.path.join(GOLDEN, f"steady_state_N{N}_Nf{Nf}.txt"))
+    return np.loadtxt(os.path.join(DATA, f"steady_state_N{N}_Nf{Nf}.txt"))
 
 
 def distillation_x0(N: int, Nf: int, seed: int) -> np.ndarray:

@@ -307,8 +307,8 @@ def test_distillation_closed_loop_small(oracle):
     warm re-solves, each converged with FD-stationary primal-dual point."""
     O = oracle
     N, Nf, T = 12, 5, 20
-    xs = np.loadtxt(__import__("os").path.join(__import__("os").path.dirname(__file__),
-                                                "golden", "steady_state_N12_Nf5.txt"))
+    xs = np.loadtxt(__import__("os").path.join(__import__("os").path.dirname(__file__), "..",
+                                                "paper_2606_04725_gb300", "data", "steady_state_N12_Nf5.txt"))
     rng = np.random.default_rng(1)
     x0 = np.clip(xs + rng.normal(0, 0.02, N), 0, 1)
     p = O.distillation(N, Nf, T, x0, np.full(T, 0.8), 2.51459)
@@ -510,8 +510,8 @@ def test_paper_distillation_closed_loop(oracle):
     O = oracle
     N, Nf, T, ubar = 32, 17, 90, 2.51459
     kw = dict(dt=2.0, Ac=0.5, At=0.25, Ar=1.0, wdu=0.0, wu=0.1, ubar=ubar)
-    xs = np.loadtxt(__import__("os").path.join(__import__("os").path.dirname(__file__),
-                                                "golden", "steady_state_N32_Nf17.txt"))
+    xs = np.loadtxt(__import__("os").path.join(__import__("os").path.dirname(__file__), "..",
+                                                "paper_2606_04725_gb300", "data", "steady_state_N32_Nf17.txt"))
     x0 = np.clip(xs + np.random.default_rng(6).normal(0, 0.02, N), 0, 1)
     p = O.distillation(N, Nf, T, x0, np.full(T, 0.8958), ubar, **kw)
     st, info, _ = O.solve(p)

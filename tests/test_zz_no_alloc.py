@@ -5,7 +5,9 @@ Callers that cannot allocate device memory -- a control task restricted to
 memory fixed at start-up, or a plug-in handed only a stream and its buffers --
 cannot give nmpc_bind a workspace.  nmpc_solve_static runs the same kernels
 with all device scratch in the library's static 32 MiB array.  This file is
-named so that pytest collects it last.
+named so that pytest collects it last.  Besides matching the regular path on
+two calls in a row, the second call must leave the device's free memory
+unchanged (cudaMemGetInfo before and after it).
 """
 import numpy as np
 import pytest
@@ -53,8 +55,16 @@ def test_static_workspace_solve_matches_regular_solve_twice(P, device_arrays):
         else:
             args = [x0, sp, up]
             y_out = np.zeros(y_ref.size)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st, infos = P._lib.solve_static(P.MODEL_DISTILLATION, hz, *args, y_out, N=12, Nf=5)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
         assert st == 0, (call, st)
+        if call == 1:
+            # the first call loaded the kernels and looked up the array's
+            # address; the second takes no device memory at all
+            assert free1 == free0, (free0, free1)
         y = y_out.cpu().numpy() if device_arrays else y_out
         err = np.max(np.abs(y - y_ref)) / max(1.0, np.max(np.abs(y_ref)))
         assert err <= TOL_Y, (call, err)
