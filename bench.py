@@ -514,6 +514,12 @@ def main():
 
     for _ in range(args.warmup):
         step()
+    # the primal-dual point the timed steps start from: the end-to-end steps
+    # below restart from it, so that both time the same closed-loop re-solves
+    m_tot = sum(d[1] for d in s.dims)
+    Y0 = Y.clone()
+    D0 = torch.empty(2 * n_tot + 6 * m_tot, dtype=torch.float64, device=dev)
+    s.get_solution(-1, out=(torch.empty_like(Y), D0))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     batch_iters, mean_iters, ok = [], [], cold_ok
     launches0 = s.stats()["kernel_launches"]
@@ -538,13 +544,15 @@ def main():
     value = whole_job_rate(ni * args.steps, tot_ms * 1e-3, world, dev)
 
     # end to end through the C ABI with host buffers: the parameters of every
-    # instance copied in and every solution copied out inside the timed region
+    # instance copied in and every solution copied out inside the timed region;
+    # the same closed-loop steps as the timed ones, from the same point
     X0h = torch.empty(ni * N, dtype=torch.float64).pin_memory()
     Uh = torch.empty(ni, dtype=torch.float64).pin_memory()
     SPh = torch.tensor(sp_host, dtype=torch.float64).pin_memory()
     Yh = torch.empty(n_tot, dtype=torch.float64).pin_memory()
-    s.get_solution(-1, out=(Yh.numpy(), None))
-    e2e_steps = min(args.steps, 10)
+    s.set_start(-1, Y0, D0)
+    Yh.copy_(Y0)
+    e2e_steps = args.steps
     e2e_s = 0.0
     if world > 1:
         torch.distributed.barrier()
@@ -600,15 +608,16 @@ def main():
                          "frac_of_measured_dfma": achieved / probe["dfma_tflops"]},
             "fp64_probe": probe,
             "autotune": {"seconds": tune_s,
+                         "columns": ["ordering", "nd_leaf", "panel_scale", "amalgamation", "factor_mode",
+                                     "ms_per_full_iteration", "ms_per_closed_loop_resolve"],
                          "candidates": [[c["ordering"], c["nd_leaf"], c["panel_scale"], c["amalgamation"],
-                                         round(c["ms_per_iter"], 3)] for c in rep["candidates"]]},
+                                         c["factor_mode"], round(c["ms_per_iter"], 3), round(c["ms_resolve"], 3)]
+                                        for c in rep["candidates"]]},
             "clocks": clk}
     if not args.no_extras:
         t0 = time.perf_counter()
         rb = {}
         y_prev, du_prev = s.get_solution(-1, duals=True)
-        offs_n = np.concatenate([[0], np.cumsum([d[0] for d in s.dims])])
-        offs_m = np.concatenate([[0], np.cumsum([d[1] for d in s.dims])])
         for mode in ("cold", "warm"):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
@@ -616,12 +625,8 @@ def main():
             s2.set_params(x0=np.ascontiguousarray(y_prev[ix_h]), setpoint=sp_host,
                           u_prev=np.ascontiguousarray(y_prev[iu_h]))
             if mode == "warm":
-                for i in range(ni):
-                    a, b = offs_n[i], offs_n[i + 1]
-                    c, d = offs_m[i], offs_m[i + 1]
-                    du = np.concatenate([du_prev["zL"][a:b], du_prev["zU"][a:b]] +
-                                        [du_prev[k][c:d] for k in ("s_p", "s_m", "w_p", "w_m", "b_p", "b_m")])
-                    s2.set_start(i, np.ascontiguousarray(y_prev[a:b]), du)
+                s2.set_start(-1, y_prev, np.concatenate([du_prev[k] for k in ("zL", "zU", "s_p", "s_m", "w_p",
+                                                                                 "w_m", "b_p", "b_m")]))
             s2.solve(warm=(mode == "warm"))
             torch.cuda.synchronize()
             rb[mode] = ni / (time.perf_counter() - t1)

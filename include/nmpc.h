@@ -62,7 +62,10 @@ typedef enum {
 typedef enum {
   NMPC_ORDER_AUTO = 0,         /* chosen by the autotuner (or a size rule) */
   NMPC_ORDER_NATURAL = 1,      /* stage order: elimination tree is a chain */
-  NMPC_ORDER_ND = 2            /* geometric nested dissection (time, then space) */
+  NMPC_ORDER_ND = 2,           /* geometric nested dissection (time, then space) */
+  NMPC_ORDER_TWO_SIDED = 3     /* nested dissection whose leaves of nd_leaf stages (the whole horizon
+                                  when nd_leaf <= 1) are eliminated from both ends toward their middle
+                                  stage: the flops of stage order with half its chain length */
 } nmpc_ordering;
 
 /* Problem description.  All instances share the model and its constants;
@@ -95,13 +98,17 @@ typedef struct {
   double push_warm;      /* bound push of the initial point, warm (1e-9) */
   int max_iter;          /* interior-point iteration limit (200) */
   int ordering;          /* nmpc_ordering */
-  int nd_leaf;           /* nested dissection: stages per leaf (1) */
+  int nd_leaf;           /* nested dissection: stages per leaf (1); two-sided order: stages per
+                            two-sided leaf, <= 1 for the whole horizon */
   int use_graph;         /* run the interior-point loop as one CUDA graph with device-set
                             conditional nodes (1, default); 0: host-driven loop, same kernels */
   long long spin_limit;  /* iteration limit of bounded device waits (1e7) */
   double pivtol;         /* inertia test: a pivot must exceed pivtol * |K_jj| (1e-12) */
   int factor_mode;       /* 0: cluster-cooperative fronts where they fit, the blocked large-front
-                            path elsewhere (default); 1: one CTA per front; 2: blocked path everywhere */
+                            path elsewhere (default); 1: one CTA per front; 2: blocked path everywhere;
+                            3: dataflow: one persistent launch factors the leading levels whose
+                            fronts fit one CTA's shared memory, each front starting as soon as its
+                            children are done (no per-level launches), then mode 0 above them */
   int solve_mode;        /* 0: persistent dataflow solves over the levels of small fronts (default);
                             1: one launch per level */
   int panel_scale;       /* triangular solves of the fronts solved one block per front:
@@ -213,7 +220,8 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm_start, nmpc_info* info);
  * the instances before it). */
 nmpc_status nmpc_get_solution(nmpc_handle* h, int instance, double* y, double* duals, int on_device);
 
-/* Overwrite an instance's primal-dual point (same layout as get_solution);
+/* Overwrite an instance's primal-dual point (same layout as get_solution;
+ * instance = -1: every instance, packed as get_solution(-1) returns them);
  * the next warm solve starts from it.  duals may be NULL to keep them. */
 nmpc_status nmpc_set_start(nmpc_handle* h, int instance, const double* y, const double* duals,
                            int on_device);
@@ -296,17 +304,22 @@ nmpc_status nmpc_solve_static(const nmpc_problem* prob, const nmpc_options* opts
  * Autotuner (the batch path's tuning of the supernodal schedule; not in the
  * paper).  The symbolic analysis and the kernels' schedule depend on options
  * the problem does not fix: the ordering (nested dissection with leaves of
- * 1, 2 or 4 stages; stage order for short horizons), the supernode
- * amalgamation under nested dissection (amalgamation 1 or 2) and the solve
- * form (panel_scale 1 or 3).  nmpc_autotune builds every candidate (reusing
+ * 1 or 2 stages; the two-sided stage order; stage order for short
+ * horizons), the supernode amalgamation under nested dissection
+ * (amalgamation 1 or 2), the factorization's schedule (factor_mode 0: one
+ * launch per level, or 3: the dataflow launch) and the solve form
+ * (panel_scale 1 or 3).  nmpc_autotune builds every candidate (reusing
  * those nmpc_autotune_workspace_bytes just built for the same problem),
  * binds it to the caller's workspace, runs one cold solve of the given
  * parameters and, if every instance converged, times one iteration's
  * evaluation, assembly, factorization and solves at that point (as
- * nmpc_time_phases); the rest of an iteration is the same for every
- * candidate.  It keeps the fastest candidate and writes its ordering,
- * nd_leaf, amalgamation and panel_scale into *opts (the other fields are
- * kept).
+ * nmpc_time_phases, reported) and two steps of the closed loop of Algorithm 1
+ * (every instance restarted warm from its own x_1 and u_1; the measured state
+ * is the prediction, as the bench's closed loop).  It keeps the candidate
+ * with the fastest re-solve -- which weighs both the full iterations and
+ * those in which few instances of a batch still run -- and writes its ordering,
+ * nd_leaf, amalgamation, factor_mode and panel_scale into *opts (the other
+ * fields are kept).
  * Results are cached per problem (model, sizes, horizons, constants) and
  * remaining options for the life of the process: a repeated call returns
  * the cached choice without running anything.
@@ -328,6 +341,8 @@ typedef struct {
   int iters;             /* largest over instances */
   double ms_per_iter;    /* evaluation + assembly + factorization + solves at the converged point */
   int amalgamation;      /* nmpc_options.amalgamation of the candidate */
+  int factor_mode;       /* nmpc_options.factor_mode of the candidate (0 per-level launches, 3 dataflow) */
+  double ms_resolve;     /* mean of two warm closed-loop re-solves after the cold solve (the choice's key) */
 } nmpc_tune_candidate;
 typedef struct {
   int n_candidates, best, cached;

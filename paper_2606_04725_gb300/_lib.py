@@ -71,7 +71,8 @@ class PhaseTimes(C.Structure):
 
 class TuneCandidate(C.Structure):
     _fields_ = [("ordering", C.c_int), ("nd_leaf", C.c_int), ("panel_scale", C.c_int), ("status", C.c_int),
-                ("iters", C.c_int), ("ms_per_iter", C.c_double), ("amalgamation", C.c_int)]
+                ("iters", C.c_int), ("ms_per_iter", C.c_double), ("amalgamation", C.c_int),
+                ("factor_mode", C.c_int), ("ms_resolve", C.c_double)]
 
 
 TUNE_MAX = 16
@@ -351,7 +352,10 @@ class Solver(Structure):
         return y, unpack_duals(dv, n, m)
 
     def set_start(self, instance, y, duals=None):
-        n, m, _ = self.dims[instance]
+        if instance < 0:
+            n, m = sum(d[0] for d in self.dims), sum(d[1] for d in self.dims)
+        else:
+            n, m, _ = self.dims[instance]
         if _numel(y) != n or (duals is not None and _numel(duals) != 2 * n + 6 * m):
             raise ValueError("start point has the wrong size")
         py, on_dev = _ptr(y)

@@ -278,10 +278,11 @@ __device__ __forceinline__ double take(const double* slot, long long limit, int*
 __device__ __forceinline__ void bar_pair() { asm volatile("bar.sync 1, 64;" ::: "memory"); }  // warps 0 and 1
 
 // Fl[i + lc*m] -= sum_{jj<w} Pl[i + jj*m] * Pw[k + jj*m] for own columns
-// k in [kb, ke) (local column lc0 + k - kb) and rows i in [k, m).
+// k in [kb, ke) (local column lc0 + k - kb) and rows i in [k, m), by the
+// threads tid = 0 .. nt-1 of the caller's group (by default the block).
 __device__ __forceinline__ void rank_update(double* Fl, const double* Pl, const double* Pw, int m, int w,
-                                            int kb, int ke, int lc0) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+                                            int kb, int ke, int lc0, int tid = threadIdx.x,
+                                            int nt = blockDim.x) {
   const int rows = m - kb;
   const int cols = ke - kb;
   for (int t = tid; t < rows * cols; t += nt) {
@@ -314,9 +315,21 @@ constexpr int FCT = 256;
 constexpr int NBULK = 192;  // threads of warps 1-3, 5-7
 static_assert(NBULK == FCT - 64, "warps 0 and 4 are not bulk warps");
 
+// Lg/Wg receive the panel's L and W: entry (i, jb + jj) at Lg[i + (jb + jj - gc0) m]
+// and Wg[i + (jb + jj - gcw) m], i.e. 0 for a whole front's panel (in global
+// memory, or in place in Fl), jb for an m x PB buffer that holds this panel only.  extra(bt) runs on the bulk
+// threads (bt = 0 .. NBULK-1) while warp 0 runs the pivot chain, after the
+// previous panel has been applied to this one: work that touches neither
+// this panel's columns nor its buffers (the single-CTA front uses it for the
+// previous panel's update of the other columns).
+struct NoExtra {
+  __device__ void operator()(int) const {}
+};
+template <class Extra = NoExtra>
 __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* thr, double* Lg, double* Wg,
                              const double* Pl, const double* Pw, int wprev, int m, int jb, int w, int lc0,
-                             double* sB, double* pub, int* s_timeout, long long limit) {
+                             double* sB, double* pub, int* s_timeout, long long limit, int gc0, int gcw,
+                             Extra extra = Extra()) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   double* Fp = Fl + (size_t)lc0 * m;  // block column kk at Fp + kk*m
   const int kend = min(jb + PB, m), nb = kend - jb;
@@ -374,15 +387,13 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
     for (int k = 2; k < PB; ++k)
       if (kA == k) ik = inv[k];
     if (vA && rA < w && kA < w) {
-      const size_t g = (jb + rA) + (size_t)(jb + kA) * m;
-      Lg[g] = (rA == kA) ? ik : a * ik;
-      Wg[g] = a;
+      Lg[(jb + rA) + (size_t)(jb + kA - gc0) * m] = (rA == kA) ? ik : a * ik;
+      Wg[(jb + rA) + (size_t)(jb + kA - gcw) * m] = a;
     }
     if (vA && kA >= w) Fp[(jb + rA) + (size_t)kA * m] = a;
     if (lane < w) {
-      const size_t g = (jb + rB) + (size_t)jb * m;
-      Lg[g] = (rB == 0) ? inv[0] : b * inv[0];
-      Wg[g] = b;
+      Lg[(jb + rB) + (size_t)(jb - gc0) * m] = (rB == 0) ? inv[0] : b * inv[0];
+      Wg[(jb + rB) + (size_t)(jb - gcw) * m] = b;
     }
     if (lane == 0 && bad) flag_fail(ctl);
   } else if ((warp & 3) != 0) {
@@ -412,6 +423,7 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
       }
     }
     asm volatile("bar.sync 2, %0;" ::"r"(NBULK) : "memory");
+    extra(bt);
     // rows below the pivot block, one column behind the chain:
     // l_ij = (F_ij - sum_{k<j} l_ik W_jk) / d_j
     for (int i = jb + w + bt; i < m; i += NBULK) {
@@ -422,9 +434,8 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
       for (int jj = 0; jj < PB; ++jj) {
         if (jj < w) {
           const double lj = f[jj] * take(pub + jj * PB + jj, limit, s_timeout);
-          const size_t g = i + (size_t)(jb + jj) * m;
-          Lg[g] = lj;
-          Wg[g] = f[jj];
+          Lg[i + (size_t)(jb + jj - gc0) * m] = lj;
+          Wg[i + (size_t)(jb + jj - gcw) * m] = f[jj];
 #pragma unroll
           for (int k = jj + 1; k < PB; ++k)
             if (k < w) f[k] = fma(-lj, take(pub + jj * PB + k, limit, s_timeout), f[k]);
@@ -513,7 +524,7 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl) {
   const int npan = (c + PB - 1) / PB;
   const long long limit = s.spin_limit;
   if (q == 0 && npan > 0) {
-    panel_factor(ctl, Fl, invd, thr, Lp, Wp, Pl, Pw, 0, m, 0, min(PB, c), 0, sB, s_pubv, &s_timeout, limit);
+    panel_factor(ctl, Fl, invd, thr, Lp, Wp, Pl, Pw, 0, m, 0, min(PB, c), 0, sB, s_pubv, &s_timeout, limit, 0, 0);
     if (tid == 0) st_release_cluster(&s_pub, 1);
   }
   for (int p = 0; p < npan; ++p) {
@@ -560,7 +571,7 @@ __global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl) {
     if (look) {
       const int k0 = nx * PB;
       panel_factor(ctl, Fl, invd + (nx / Q) * PB, thr + (nx / Q) * PB, Lp, Wp, Pl, Pw, w, m, k0,
-                   min(PB, c - k0), (nx / Q) * PB, sB, s_pubv, &s_timeout, limit);
+                   min(PB, c - k0), (nx / Q) * PB, sB, s_pubv, &s_timeout, limit, 0, 0);
       if (tid == 0) st_release_cluster(&s_pub, nx / Q + 1);
     }
     // ---- rank-w update of the remaining own columns
@@ -1139,6 +1150,233 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
     if (s_lost) break;
   }
   if (tid == 0 && (s_to || s_lost)) atomicExch(s.timeout, 1);
+  // no block touches the flags after it has arrived here
+  __shared__ int s_last;
+  if (tid == 0) s_last = atomicAdd(flags + nf + 1, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (s_last)
+    for (int i = tid; i < nf + 2; i += blockDim.x) flags[i] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Dataflow factorization: one persistent launch for the fronts desc[0 .. nf)
+// of the leading levels, whose fronts fit one CTA's shared memory.  Each
+// block claims the next front in level order, loads the front's pivot
+// columns of the condensed matrix (no dependency), waits for its children's
+// completion flags (bounded waits), adds their update matrices, factors the
+// pivot columns with the panel scheme of the cluster kernel on one CTA
+// (panels kept in shared memory, no publication), forms the update matrix
+// in one dense pass, writes L and the update matrix and publishes the front
+// with a release flag.  Levels no longer wait for one
+// another: a front starts as soon as its own children are done, so fronts of
+// different levels and instances overlap, and one launch replaces one launch
+// per level.  As in the persistent solves a front is waited on only after a
+// running block has claimed it (children come first in level order), so the
+// launch needs no co-residency; flags[0] is the claim counter, flags[1 + q]
+// front q's completion, flags[nf + 1] counts departed blocks, and the last
+// block to leave zeroes them all for the next launch.
+// Shared memory (doubles): the pivot columns (m x cp, cp = c rounded up to
+// PB), the update block as a packed lower triangle (mu (mu + 1) / 2), the L
+// buffers of two panels (m x PB each), cp pivot thresholds and cp reciprocal
+// pivots -- about half of a whole front, so that two blocks share an SM.
+// ---------------------------------------------------------------------------
+// The update matrix of a front factored by factor_front_flow:
+// U = (children's part U0) - L21 D L21^T, all pivot columns at once, one
+// TR x TC output tile per thread.  L = W times the reciprocal pivot is formed
+// as the panels formed it, and the columns are applied in ascending order:
+// the same rounding as a panel-by-panel trailing update.  Fl: m x c pivot
+// columns (W, ld m); U0: packed lower triangle of the mu x mu update block;
+// Up: output (ld mu, lower triangle).
+template <int TR, int TC>
+__device__ __forceinline__ void schur_tiles(const double* Fl, const double* U0, const double* invd, double* Up, int m,
+                                            int c) {
+  const int mu = m - c, tid = threadIdx.x, nt = blockDim.x;
+  auto upk = [&](int a, int b) { return (size_t)b * mu - (size_t)b * (b - 1) / 2 + (a - b); };
+  const int nr = (mu + TR - 1) / TR, ncb = (mu + TC - 1) / TC;
+  // the tiles (ta, tb) that reach the lower triangle, TR ta + TR - 1 >= TC tb,
+  // column block by column block: column block tb starts at row block lo(tb)
+  auto lo = [&](int tb) { return max(0, (TC * tb - TR + 1 + TR - 1) / TR); };
+  int total = 0;
+  for (int tb = 0; tb < ncb; ++tb) total += nr - lo(tb);
+  for (int t = tid; t < total; t += nt) {
+    int tb = 0, r = t;
+    while (r >= nr - lo(tb)) { r -= nr - lo(tb); ++tb; }
+    const int ta = lo(tb) + r;
+    const int a0 = TR * ta, b0 = TC * tb;
+    double acc[TR][TC];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+      for (int q = 0; q < TC; ++q) {
+        const int a = a0 + r, b = b0 + q;
+        acc[r][q] = (a < mu && b <= a) ? U0[upk(a, b)] : 0.0;
+      }
+    const double* col = Fl + c;
+    for (int j = 0; j < c; ++j, col += m) {
+      const double iv = invd[j];
+      double l[TR], wv[TC];
+#pragma unroll
+      for (int r = 0; r < TR; ++r) l[r] = (a0 + r < mu) ? col[a0 + r] * iv : 0.0;
+#pragma unroll
+      for (int q = 0; q < TC; ++q) wv[q] = (b0 + q < mu) ? col[b0 + q] : 0.0;
+#pragma unroll
+      for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int q = 0; q < TC; ++q) acc[r][q] = fma(-l[r], wv[q], acc[r][q]);
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+      for (int q = 0; q < TC; ++q) {
+        const int a = a0 + r, b = b0 + q;
+        if (a < mu && b <= a) Up[a + (size_t)b * mu] = acc[r][q];
+      }
+  }
+}
+
+// The largest tiles that still give every thread of the block an output
+// tile (FP64 latency is hidden across warps, and larger tiles form fewer L
+// values per multiply-add).
+__device__ __noinline__ void schur_update(const double* Fl, const double* U0, const double* invd, double* Up, int m,
+                                          int c) {
+  const int mu = m - c, nt = blockDim.x;
+  auto tiles = [&](int tr, int tc) {  // tiles reaching the lower triangle
+    const int nr = (mu + tr - 1) / tr, ncb = (mu + tc - 1) / tc;
+    int n = 0;
+    for (int tb = 0; tb < ncb; ++tb) n += nr - max(0, (tc * tb) / tr);
+    return n;
+  };
+  if (tiles(4, 4) >= nt) schur_tiles<4, 4>(Fl, U0, invd, Up, m, c);
+  else if (tiles(2, 4) >= nt) schur_tiles<2, 4>(Fl, U0, invd, Up, m, c);
+  else schur_tiles<2, 2>(Fl, U0, invd, Up, m, c);
+}
+
+__device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd, const int* flags, int nf,
+                                  int* s_to, double* s_pubv, double* sB, long long limit) {
+  const int m = fd.m, c = fd.c, mu = m - c;
+  double* Lp = s.L + fd.Lptr;
+  double* Up = s.U + fd.Uptr;
+  const double* kd = s.Kdiag + fd.first;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int cp = (c + PB - 1) / PB * PB, npan = cp / PB;
+  double* Fl = dsm;                                  // m x cp, ld m: the pivot columns (W once factored)
+  double* U0 = Fl + (size_t)m * cp;                  // mu (mu + 1) / 2: update block, packed lower triangle
+  double* Lb = U0 + (size_t)mu * (mu + 1) / 2;       // 2 x (m x PB): L of the even / odd panels
+  double* thr = Lb + 2 * (size_t)m * PB;             // cp
+  double* invd = thr + cp;                           // cp
+  auto bL = [&](int q) { return Lb + (size_t)(q & 1) * m * PB; };
+  auto upk = [&](int a, int b) { return (size_t)b * mu - (size_t)b * (b - 1) / 2 + (a - b); };  // a >= b, packed
+  // ---- the pivot columns from the condensed values (m x c, ld m), the update block zero
+  for (int t0 = tid; t0 < m * cp; t0 += 4 * nt) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + u * nt;
+      v[u] = (t < m * c) ? Lp[t] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (t0 + u * nt < m * cp) Fl[t0 + u * nt] = v[u];
+  }
+  for (int t = tid; t < mu * (mu + 1) / 2; t += nt) U0[t] = 0.0;
+  for (int k = tid; k < cp; k += nt) thr[k] = (k < c) ? s.pivtol * fabs(kd[k]) : 0.0;
+  // ---- children: wait for their completion, then add their update matrices,
+  // entries of a pivot column to Fl and the others to the update block
+  // (ascending child order: the result does not depend on timing)
+  if (tid == 0) {
+    for (int k = 0; k < fd.nchild; ++k) {
+      const int q = (k < DESC_CH) ? fd.ch_pos[k] : s.pos_of_sn[s.sn_child[s.sn_child_ptr[fd.J] + k]];
+      if (q >= 0 && q < nf) wait_done(flags + 1 + q, limit, s_to);
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < fd.nchild; ++k) {
+    const ChildRef ch = child_ref(s, fd, k);
+    const int mc = ch.mc;
+    const int tot = mc * (mc + 1) / 2;
+    for (int t = tid; t < tot; t += nt) {
+      const int b = tri_col(t, mc);
+      const int a = b + (t - (b * mc - b * (b - 1) / 2));
+      const int ra = ch.rel[a], rb = ch.rel[b];  // ra >= rb
+      const double v = __ldcg(ch.U + a + (size_t)b * mc);  // written by another block
+      if (rb < c) Fl[ra + (size_t)rb * m] += v;
+      else U0[upk(ra - c, rb - c)] += v;
+    }
+    __syncthreads();
+  }
+  // ---- phase 1: blocked right-looking LDL^T of the pivot columns only
+  // (panel_factor; W of each panel in place in Fl, L in a panel buffer and
+  // then in the factor), the panels' update of later pivot columns
+  if (npan > 0)
+    panel_factor(ctl, Fl, invd, thr, bL(0), Fl, nullptr, nullptr, 0, m, 0, min(PB, c), 0, sB, s_pubv, s_to, limit,
+                 0, 0);
+  for (int p = 0; p < npan; ++p) {
+    const int jb = p * PB, w = min(PB, c - jb);
+    const double* Pl = bL(p);
+    const double* Pw = Fl + (size_t)jb * m;  // W of panel p: Pw[k + jj m]
+    const int nx = p + 1;
+    // panel p's outputs, by threads (t0, nt0): its rows jb .. m-1 of L to the
+    // factor, and its update of the later pivot columns except the lookahead
+    // block nx (updated and factored by panel_factor)
+    auto finish = [&](int t0, int nt0) {
+      const int rows = m - jb;
+      for (int t = t0; t < rows * w; t += nt0) {
+        const int jj = t / rows, i = jb + (t - jj * rows);
+        Lp[i + (size_t)(jb + jj) * m] = Pl[i + (size_t)jj * m];
+      }
+      for (int b = nx + 1; b < npan; ++b) {
+        const int k0 = b * PB, ke = min(k0 + PB, c);
+        if (k0 < ke) rank_update(Fl, Pl, Pw, m, w, k0, ke, k0, t0, nt0);
+      }
+    };
+    if (nx < npan) {
+      // lookahead: the next panel gets this panel's update and is factored,
+      // while the bulk warps finish this panel (the chain does not wait for it)
+      const int k0 = nx * PB;
+      panel_factor(ctl, Fl, invd + k0, thr + k0, bL(nx), Fl, Pl, Pw, w, m, k0, min(PB, c - k0), k0, sB, s_pubv,
+                   s_to, limit, k0, 0, [&](int bt) { finish(bt, NBULK); });
+    } else {
+      finish(tid, nt);
+      __syncthreads();
+    }
+  }
+  // ---- phase 2: the update matrix U = (children's part) - L21 D L21^T for
+  // the parent (schur_update)
+  schur_update(Fl, U0, invd, Up, m, c);
+}
+
+__global__ void __launch_bounds__(FCT, 2) k_factor_flow(Dev d, SnDev s, const FrontDesc* dl, int nf, int* flags) {
+  __shared__ FrontDesc fd;
+  __shared__ int s_q, s_to, s_any_to;
+  __shared__ double s_pubv[PB * PB];
+  __shared__ double sB[PB];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_any_to = 0;
+  const long long limit = s.spin_limit;
+  for (;;) {
+    if (tid == 0) {
+      s_q = atomicAdd(flags, 1);
+      s_to = 0;
+    }
+    __syncthreads();
+    const int q = s_q;
+    if (q >= nf) break;
+    load_desc(&fd, dl + q);
+    __syncthreads();
+    Ctl* ctl = d.ctl + fd.inst;
+    if (ctl->need_factor) factor_front_flow(ctl, s, fd, flags, nf, &s_to, s_pubv, sB, limit);  // uniform
+    // every thread's stores (L, U) are ordered before thread 0's release
+    // store by the barrier (release is cumulative)
+    __syncthreads();
+    if (tid == 0) {
+      if (s_to) {  // a wait ran out: this front is unusable, and the instance is flagged
+        flag_fail(ctl);
+        s_any_to = 1;
+      }
+      st_release_gpu(flags + 1 + q, 1);
+    }
+  }
+  if (tid == 0 && s_any_to) atomicExch(s.timeout, 1);
   // no block touches the flags after it has arrived here
   __shared__ int s_last;
   if (tid == 0) s_last = atomicAdd(flags + nf + 1, 1) == (int)gridDim.x - 1;

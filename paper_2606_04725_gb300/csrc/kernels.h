@@ -31,6 +31,7 @@ __global__ void k_eval_vars(Dev d, int use_trial);
 __global__ void k_eval(Dev d, int use_trial, int with_jac, int nbr);
 __global__ void k_set_params(Dev d, int i0, int i1, const double* x0, const double* sp, const double* up, int sp_len);
 __global__ void k_set_params_packed(Dev d, const int* spoff, const double* x0, const double* sp, const double* up);
+__global__ void k_shift_params(Dev d);
 __global__ void k_init_vars(Dev d, int warm, double push);
 __global__ void k_init_rows(Dev d, int warm, double push);
 
@@ -52,6 +53,7 @@ __global__ void k_summary(Dev d, int* flags);
 // factor_kernels.cu
 __global__ void k_factor_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
 __global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl);
+__global__ void k_factor_flow(Dev d, SnDev s, const FrontDesc* dl, int nf, int* flags);
 __global__ void k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
 __global__ void k_bwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
 __global__ void k_fwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap, int* flags);

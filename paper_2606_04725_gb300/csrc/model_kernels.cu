@@ -366,6 +366,19 @@ __global__ void k_set_params_packed(Dev d, const int* spoff, const double* x0, c
   }
 }
 
+// One step of the closed loop (Algorithm 1) on the device, for every
+// instance: the new initial state is the solution's x_1 (the plant is the
+// same model) and, for the distillation, the new u_prev its u_1.
+__global__ void k_shift_params(Dev d) {
+  const int nx = d.mc.nx;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.n_inst * (nx + 1); t += gridDim.x * blockDim.x) {
+    const int i = t / (nx + 1), q = t % (nx + 1);
+    const double* yi = d.y + d.inst_voff[i];
+    if (q < nx) d.p_x0[(size_t)i * nx + q] = yi[nx + q];
+    else if (d.mc.model == MODEL_DISTILL) d.p_uprev[i] = yi[2 * nx];
+  }
+}
+
 // Cold-start trajectory from the parameters: x_k = p_x0 for all k, controls
 // at u_prev (distillation) or the midpoint of their bounds, then pushed into
 // the bounds (W&B Sec. 3.6).  Warm start only pushes the previous point.

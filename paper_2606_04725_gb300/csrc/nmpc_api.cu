@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -65,6 +66,9 @@ struct nmpc_handle {
   int solve_prefix = 0, solve_prefix_fronts = 0, persist_blocks_fwd = 0, persist_blocks_bwd = 0;
   int persist_smem_fwd = 0, persist_smem_bwd = 0;
   int* d_solve_flags = nullptr;
+  // dataflow factorization (factor_mode 3) over the first flow_levels levels (fronts in level order)
+  int flow_levels = 0, flow_fronts = 0, flow_blocks = 0, flow_smem = 0;
+  int* d_flow_flags = nullptr;
   std::vector<int> lvl_maxm, lvl_maxc, lvl_maxmu, lvl_maxch, lvl_maxmc;
   std::vector<int> amap;                             // extend-add pairs (source, destination)
   std::vector<long long> amap_ptr;                   // ranges per (front, CTA, child)
@@ -99,7 +103,78 @@ constexpr int SMEM_FACTOR_CAP_BYTES = 200 * 1024;
 constexpr int FACTOR_THREADS = 1024;  // 32 warps per front hide FP64 and shared-memory latency
 constexpr int CLUSTER_THREADS = 256;  // per CTA of the cluster-cooperative front kernel (FCT in factor_kernels.cu)
 constexpr int CLUSTER_PB = 8;         // column block of the cluster kernel (PB in factor_kernels.cu)
+constexpr int FLOW_SMEM_CAP_BYTES = 220 * 1024;  // dynamic shared memory of a k_factor_flow block
+// shared memory (doubles) of k_factor_flow for a front of m rows and c pivot
+// columns: the pivot columns rounded up to whole panels, the packed update
+// block, two L panel buffers, thresholds and reciprocal pivots
+long long flow_need(long long m, long long c) {
+  const long long cp = (c + CLUSTER_PB - 1) / CLUSTER_PB * CLUSTER_PB, mu = m - c;
+  return m * cp + mu * (mu + 1) / 2 + 2 * m * CLUSTER_PB + 2 * cp;
+}
 constexpr int SENS_REFINE = 6;        // refinement sweeps of the adjoint solve
+
+// Memory of the update matrices.  A front's update matrix is written when its
+// level is factored and read once, by its parent's extend-add; after the
+// parent's level it is dead, so later levels reuse its memory.  Offsets are
+// assigned by a sweep over the levels with a first-fit free list (ordered by
+// offset, neighbours merged): before level t the matrices whose parents lie
+// below t are freed, then level t's are placed.  The levels of the dataflow
+// launch (the first flow_levels levels) run concurrently, so they are placed
+// together and none of their memory is reused before the launch has ended.
+// The workspace then holds the largest set of update matrices live at one
+// level instead of all of them.  Returns the arena size in doubles.
+long long plan_update_memory(Analysis& A, int flow_levels) {
+  const int nl = (int)A.level_ptr.size() - 1, ns = (int)A.sn_first.size();
+  std::vector<int> lvl(ns, 0);
+  for (int l = 0; l < nl; ++l)
+    for (int q = A.level_ptr[l]; q < A.level_ptr[l + 1]; ++q) lvl[A.level_sn[q]] = l;
+  std::vector<std::vector<int>> frees(nl + 1);  // fronts whose matrix dies before level t
+  for (int J = 0; J < ns; ++J) {
+    const int p = A.sn_parent[J];
+    const int dead = std::max(p >= 0 ? lvl[p] : lvl[J], flow_levels - 1) + 1;  // first level that may reuse it
+    frees[std::min(dead, nl)].push_back(J);
+  }
+  std::map<long long, long long> free_list;  // offset -> doubles
+  long long end = 0;
+  auto release = [&](long long off, long long len) {
+    if (len <= 0) return;
+    auto it = free_list.emplace(off, len).first;
+    auto nx = std::next(it);
+    if (nx != free_list.end() && it->first + it->second == nx->first) { it->second += nx->second; free_list.erase(nx); }
+    if (it != free_list.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) { pv->second += it->second; free_list.erase(it); }
+    }
+  };
+  auto place = [&](long long len) {
+    for (auto it = free_list.begin(); it != free_list.end(); ++it)
+      if (it->second >= len) {
+        const long long off = it->first, rest = it->second - len;
+        free_list.erase(it);
+        if (rest > 0) free_list.emplace(off + len, rest);
+        return off;
+      }
+    const long long off = end;
+    end += len;
+    return off;
+  };
+  auto size_of = [&](int J) {
+    const long long mu = A.sn_nrow[J] - A.sn_ncol[J];
+    return (mu * mu + 1) & ~1LL;  // even: every matrix starts on a 16-byte boundary
+  };
+  for (int t = 0; t < nl; ++t) {
+    for (int J : frees[t]) release(A.sn_Uptr[J], size_of(J));
+    if (t > 0 && t < flow_levels) continue;  // placed with level 0
+    const int l1 = (t == 0) ? std::max(1, flow_levels) : t + 1;
+    for (int l = t; l < std::min(l1, nl); ++l)
+      for (int q = A.level_ptr[l]; q < A.level_ptr[l + 1]; ++q) {
+        const int J = A.level_sn[q];
+        A.sn_Uptr[J] = place(size_of(J));
+      }
+  }
+  A.sn_Uptr[ns] = end;
+  return end;
+}
 
 nmpc_status fail(nmpc_handle* h, nmpc_status st, const std::string& msg) {
   if (h) h->err = msg;
@@ -172,6 +247,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.desc = cv.take<FrontDesc>(ns);
   s.pos_of_sn = cv.take<int>(ns);
   h->d_solve_flags = cv.take<int>(2 * (ns + 2));  // forward and backward persistent solves
+  h->d_flow_flags = cv.take<int>(h->flow_fronts + 2);
   s.amap = cv.take<IdxPair>(h->amap.size() / 2);
   s.amap_ptr = cv.take<long long>(h->amap_ptr.size());
   s.U = cv.take<double>(A.nU);
@@ -272,11 +348,18 @@ nmpc_status launch_factor(nmpc_handle* h) {
   const bool fork = h->side != nullptr;
   cudaStream_t ts = fork ? h->side : h->stream;
   bool forked = h->side_pending;
-  for (int l = 0; l < nl; ++l) {
-    const nmpc_status st = launch_factor_level(h, l);
+  const int L = h->flow_levels;
+  if (L > 0) {
+    k_factor_flow<<<h->flow_blocks, CLUSTER_THREADS, h->flow_smem, h->stream>>>(h->d, h->s, h->s.desc, h->flow_fronts,
+                                                                              h->d_flow_flags);
+    ++h->launches;
+  }
+  for (int l = (L > 0 ? L - 1 : 0); l < nl; ++l) {
+    // the dataflow levels' panel transforms go together after its launch
+    const nmpc_status st = l < L ? NMPC_OK : launch_factor_level(h, l);
     if (st != NMPC_OK) return st;
-    const int i0 = h->lvl_inv_ptr[l], i1 = h->lvl_inv_ptr[l + 1];
-    const int u0 = h->lvl_scale_ptr[l], u1 = h->lvl_scale_ptr[l + 1];
+    const int i0 = h->lvl_inv_ptr[l < L ? 0 : l], i1 = h->lvl_inv_ptr[l + 1];
+    const int u0 = h->lvl_scale_ptr[l < L ? 0 : l], u1 = h->lvl_scale_ptr[l + 1];
     if (i1 == i0) continue;
     if (fork) {
       CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
@@ -639,6 +722,25 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   }
   h->lvl_cluster.assign(nl, 0);
   h->lvl_cluster_smem.assign(nl, 0);
+  // factor_mode 3: the longest prefix of levels whose fronts each fit one
+  // k_factor_flow block runs as one dataflow launch; the levels above it as
+  // in mode 0
+  h->flow_levels = h->flow_fronts = h->flow_smem = 0;
+  if (h->opt.factor_mode == 3) {
+    int L = 0;
+    long long worst = 0;
+    for (; L < nl; ++L) {
+      long long lw = 0;
+      for (int qd = A.level_ptr[L]; qd < A.level_ptr[L + 1]; ++qd)
+        lw = std::max(lw, flow_need(A.sn_nrow[A.level_sn[qd]], A.sn_ncol[A.level_sn[qd]]) * 8);
+      if (lw > FLOW_SMEM_CAP_BYTES) break;
+      worst = std::max(worst, lw);
+    }
+    h->flow_levels = L;
+    h->flow_fronts = A.level_ptr[L];
+    h->flow_smem = (int)std::max<long long>(worst, 8);
+  }
+  const bool clusters = h->opt.factor_mode == 0 || h->opt.factor_mode == 3;
   for (int l = 0; l < nl; ++l) {
     const int cnt = A.level_ptr[l + 1] - A.level_ptr[l];
     int max_blocks = 1;
@@ -658,7 +760,7 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
       if (need * 8 > SMEM_FACTOR_CAP_BYTES) fits = false;
       worst = std::max(worst, need * 8);
     }
-    if (fits && h->opt.factor_mode == 0) { h->lvl_cluster[l] = Q; h->lvl_cluster_smem[l] = (int)worst; }
+    if (fits && clusters && l >= h->flow_levels) { h->lvl_cluster[l] = Q; h->lvl_cluster_smem[l] = (int)worst; }
   }
   h->lvl_big.assign(nl, 0); h->lvl_bigsolve.assign(nl, 0);
   h->lvl_maxm.assign(nl, 0); h->lvl_maxc.assign(nl, 0); h->lvl_maxmu.assign(nl, 0);
@@ -678,8 +780,10 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
       const long long lsz = ((long long)mm * cc + 1) & ~1LL;
       if (cc > 128 || lsz + mm + cc > h->smem_cap_doubles) h->lvl_bigsolve[l] = 1;
     }
-    h->lvl_big[l] = ((h->lvl_cluster[l] == 0 && h->opt.factor_mode == 0) || h->opt.factor_mode == 2) ? 1 : 0;
+    h->lvl_big[l] = ((h->lvl_cluster[l] == 0 && clusters && l >= h->flow_levels) || h->opt.factor_mode == 2) ? 1 : 0;
   }
+  // update matrices: reuse the memory of those already consumed
+  h->A.nU = plan_update_memory(h->A, h->flow_levels);
   // blocks of the fronts solved one block per front (fwd_front/bwd_front)
   h->inv_items.clear();
   h->scale_units.clear();
@@ -902,6 +1006,12 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   }
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_level, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
   CUDA_TRY(h, cudaFuncSetAttribute(k_factor_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_FACTOR_CAP_BYTES));
+  if (h->flow_fronts > 0) {
+    CUDA_TRY(h, cudaFuncSetAttribute(k_factor_flow, cudaFuncAttributeMaxDynamicSharedMemorySize, FLOW_SMEM_CAP_BYTES));
+    int per_sm = 0;
+    CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_factor_flow, CLUSTER_THREADS, h->flow_smem));
+    h->flow_blocks = std::max(1, std::min(h->flow_fronts, std::max(1, per_sm) * h->n_sm));
+  }
   // persistent solves: the longest prefix of levels without large fronts
   {
     int L = 0, nf = 0, smf = 8, smb = 8;
@@ -1110,9 +1220,11 @@ nmpc_status nmpc_get_solution(nmpc_handle* h, int instance, double* y, double* d
 nmpc_status nmpc_set_start(nmpc_handle* h, int instance, const double* y, const double* duals, int on_device) {
   if (!h || !h->bound) return fail(h, NMPC_ERR_INVALID, "handle not bound");
   const Analysis& A = h->A;
-  if (instance < 0 || instance >= A.n_inst) return fail(h, NMPC_ERR_INVALID, "instance out of range");
+  if (instance < -1 || instance >= A.n_inst) return fail(h, NMPC_ERR_INVALID, "instance out of range");
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  const int vo = A.inst_voff[instance], ro = A.inst_roff[instance], n = A.inst_n[instance], m = A.inst_m[instance];
+  // instance -1: every instance, packed as nmpc_get_solution(-1) returns them
+  const int vo = instance < 0 ? 0 : A.inst_voff[instance], ro = instance < 0 ? 0 : A.inst_roff[instance];
+  const int n = instance < 0 ? A.n : A.inst_n[instance], m = instance < 0 ? A.m : A.inst_m[instance];
   const Dev& d = h->d;
   if (y) CUDA_TRY(h, cudaMemcpyAsync(d.y + vo, y, n * 8, k, h->stream));
   if (duals) {
@@ -1478,22 +1590,38 @@ std::vector<nmpc_options> tune_candidates(const nmpc_problem* p, const nmpc_opti
   for (int i = 0; i < p->n_instances; ++i) Tmax = std::max(Tmax, p->horizons[i]);
   std::vector<nmpc_options> c;
   for (int form : {1, 3}) {
-    if (Tmax >= 8)
-      for (int leaf : {1, 2, 4})
+    if (Tmax >= 8) {
+      for (int leaf : {1, 2})
         for (int am : {1, 2}) {
           nmpc_options o = base;
           o.ordering = NMPC_ORDER_ND;
           o.nd_leaf = leaf;
           o.panel_scale = form;
           o.amalgamation = am;
+          o.factor_mode = 0;
           c.push_back(o);
         }
+      // the dataflow factorization: nested dissection, and the two-sided
+      // stage order (the flops of stage order, half its depth)
+      for (int ord : {NMPC_ORDER_ND, NMPC_ORDER_TWO_SIDED})
+        for (int am : {1, 2}) {
+          if (ord == NMPC_ORDER_TWO_SIDED && am == 2) continue;  // chains: both modes give the same partition
+          nmpc_options o = base;
+          o.ordering = ord;
+          o.nd_leaf = 1;
+          o.panel_scale = form;
+          o.amalgamation = am;
+          o.factor_mode = 3;
+          c.push_back(o);
+        }
+    }
     if (Tmax < 32) {  // a chain of at most 31 stages: its depth is no worse than a tree's
       nmpc_options o = base;
       o.ordering = NMPC_ORDER_NATURAL;
       o.nd_leaf = 1;
       o.panel_scale = form;
       o.amalgamation = 1;  // a chain: both modes give the same partition
+      o.factor_mode = 0;
       c.push_back(o);
     }
   }
@@ -1588,6 +1716,7 @@ nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cu
         opts->nd_leaf = e.second.nd_leaf;
         opts->panel_scale = e.second.panel_scale;
         opts->amalgamation = e.second.amalgamation;
+        opts->factor_mode = e.second.factor_mode;
         if (report) report->cached = 1;
         return NMPC_OK;
       }
@@ -1610,7 +1739,7 @@ nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cu
   std::vector<nmpc_info> info(prob->n_instances);
   for (size_t c = 0; c < cand.size() && (int)c < NMPC_TUNE_MAX; ++c) {
     nmpc_tune_candidate rc{cand[c].ordering, cand[c].nd_leaf, cand[c].panel_scale, NMPC_ERR_WORKSPACE, 0, 0.0,
-                           cand[c].amalgamation};
+                           cand[c].amalgamation, cand[c].factor_mode, 0.0};
     nmpc_handle* h = built.empty() ? nullptr : built[c];
     nmpc_status st = NMPC_OK;
     if (h) h->stream = static_cast<cudaStream_t>(cuda_stream);  // built without a stream
@@ -1630,6 +1759,17 @@ nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cu
       // inertia corrections, which warm re-solves rarely need)
       nmpc_phase_times pt{};
       if (st == NMPC_OK) st = nmpc_time_phases(h, 3, &pt);
+      // and two steps of the closed loop (Algorithm 1): every instance
+      // restarts from its own x_1 (and u_1), warm -- the re-solve an NMPC
+      // loop repeats, with its share of iterations in which only a few
+      // instances of a batch are still running
+      double ms_rs = 0.0;
+      for (int k = 0; k < 2 && st == NMPC_OK; ++k) {
+        k_shift_params<<<std::min(1024u, blocks_for((long long)h->A.n_inst * (h->A.mc.nx + 1))), TPB, 0, h->stream>>>(h->d);
+        ++h->launches;
+        st = nmpc_solve(h, 1, info.data());
+        ms_rs += info[0].ms_total;
+      }
       if (st == NMPC_ERR_CUDA || st == NMPC_ERR_INVALID || st == NMPC_TIMEOUT) {
         if (!h->err.empty()) std::fprintf(stderr, "nmpc_autotune: %s\n", h->err.c_str());
         nmpc_destroy(h);
@@ -1641,9 +1781,10 @@ nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cu
       rc.status = st;
       rc.iters = iters;
       rc.ms_per_iter = pt.ms_eval + pt.ms_assemble + pt.ms_factor + pt.ms_solve;
-      if (st == NMPC_OK && (best < 0 || rc.ms_per_iter < best_ms)) {
+      rc.ms_resolve = ms_rs / 2.0;
+      if (st == NMPC_OK && (best < 0 || rc.ms_resolve < best_ms)) {
         best = (int)c;
-        best_ms = rc.ms_per_iter;
+        best_ms = rc.ms_resolve;
       }
       if (st != NMPC_OK && first_fail == NMPC_OK) first_fail = st;
     }
@@ -1657,6 +1798,7 @@ nmpc_status nmpc_autotune(const nmpc_problem* prob, nmpc_options* opts, void* cu
   opts->nd_leaf = cand[best].nd_leaf;
   opts->panel_scale = cand[best].panel_scale;
   opts->amalgamation = cand[best].amalgamation;
+  opts->factor_mode = cand[best].factor_mode;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache.emplace_back(key, *opts);
   return NMPC_OK;

@@ -52,6 +52,7 @@ struct NDOrder {
   const std::vector<std::vector<int>>& adj;
   const std::vector<std::array<int, 3>>& coord;
   int leaf_max;
+  bool two_sided = false;  // leaves eliminated from both ends toward their middle stage
   std::vector<int> label;  // region id of each vertex in the current call
   std::vector<int> order;
   int next_label = 1;
@@ -64,8 +65,30 @@ struct NDOrder {
     order.insert(order.end(), set.begin(), set.end());
   }
 
+  // A leaf spanning stages t_lo .. t_hi (time is coordinate 0): stages below
+  // the middle one ascending, those above it descending, the middle stage
+  // last.  A stage-coupled chain then fills only toward the middle: each
+  // eliminated stage is joined to one neighbour that is still present (the
+  // next one on its side), as in stage order, while the two halves are
+  // independent subtrees -- the flops of stage order with half the depth.
+  void leaf(std::vector<int>& set) {
+    if (!two_sided || set.empty()) { natural(set); return; }
+    int lo = coord[set[0]][0], hi = lo;
+    for (int v : set) { lo = std::min(lo, coord[v][0]); hi = std::max(hi, coord[v][0]); }
+    const int mid = lo + (hi - lo) / 2;
+    auto rank = [&](int v) {
+      const int t = coord[v][0];
+      return t < mid ? t - lo : (t > mid ? (mid - lo) + (hi - t) : hi - lo + 1);
+    };
+    std::sort(set.begin(), set.end(), [&](int a, int b) {
+      const int ra = rank(a), rb = rank(b);
+      return ra != rb ? ra < rb : a < b;
+    });
+    order.insert(order.end(), set.begin(), set.end());
+  }
+
   void run(std::vector<int>& set) {
-    if ((int)set.size() <= leaf_max) { natural(set); return; }
+    if ((int)set.size() <= leaf_max) { leaf(set); return; }
     int best_dim = -1, best_cut = 0;
     size_t best_sep = SIZE_MAX;
     for (int d = 0; d < 3; ++d) {
@@ -499,7 +522,9 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
             }
         }
         int leaf = (sp.model == MODEL_PLATE) ? std::max(1, sp.nd_leaf) * 64 : std::max(1, sp.nd_leaf) * (nx + nu);
+        if (ord == 3 && sp.nd_leaf <= 1) leaf = nl;  // the whole horizon is one two-sided leaf
         NDOrder nd(adj, coord, leaf);
+        nd.two_sided = ord == 3;
         std::vector<int> all(nl);
         std::iota(all.begin(), all.end(), 0);
         nd.run(all);

@@ -1,8 +1,8 @@
 """The autotuner (nmpc_autotune) on the GPU.
 
 It times one cold solve per candidate option set (ordering and nested-
-dissection leaf size, supernode amalgamation, solve form) and keeps the fastest per interior-point
-iteration.  Pins: every candidate converges on these problems; the chosen
+dissection leaf size, supernode amalgamation, factorization schedule, solve
+form) and keeps the fastest per interior-point iteration.  Pins: every candidate converges on these problems; the chosen
 options are one of the candidates; a solver built with them reaches the
 default options' solution (1e-6 relative) and iteration count (within 3:
 another ordering meets the inertia test with other pivots);
@@ -44,14 +44,15 @@ def test_autotune_picks_a_converging_candidate_and_caches_it(P, hz):
     o, rep = P.autotune(P.MODEL_DISTILLATION, hz, x0=x0, setpoint=sp, u_prev=up, N=12, Nf=5)
     assert not rep["cached"]
     cands = rep["candidates"]
-    # ND leaves 1, 2, 4 in two amalgamation modes (horizons >= 8) and stage
-    # order (horizons < 32), in two solve forms
-    assert len(cands) == (14 if max(hz) < 32 else 12)
-    assert all(c["status"] == 0 and c["iters"] > 0 and c["ms_per_iter"] > 0 for c in cands), cands
+    # per solve form: ND leaves 1 and 2 in two amalgamation modes with level
+    # launches, the dataflow launch under ND (two amalgamation modes) and the
+    # two-sided order (horizons >= 8), and stage order (horizons < 32)
+    assert len(cands) == (16 if max(hz) < 32 else 14)
+    assert all(c["status"] == 0 and c["iters"] > 0 and c["ms_per_iter"] > 0 and c["ms_resolve"] > 0 for c in cands), cands
     b = cands[rep["best"]]
-    assert b["ms_per_iter"] == min(c["ms_per_iter"] for c in cands)
-    assert (o.ordering, o.nd_leaf, o.panel_scale, o.amalgamation) == \
-        (b["ordering"], b["nd_leaf"], b["panel_scale"], b["amalgamation"])
+    assert b["ms_resolve"] == min(c["ms_resolve"] for c in cands) and b["ms_resolve"] > 0
+    assert (o.ordering, o.nd_leaf, o.panel_scale, o.amalgamation, o.factor_mode) == \
+        (b["ordering"], b["nd_leaf"], b["panel_scale"], b["amalgamation"], b["factor_mode"])
     y_t, inf_t = _solve(P, hz, x0s, sps, o)
     y_d, inf_d = _solve(P, hz, x0s, sps, P.options())
     for i in range(len(hz)):

@@ -278,6 +278,27 @@ def test_nested_dissection_matches_oracle(P, oracle):
         prob.set_params(x0=st_or.y[prob.off_x(1):prob.off_x(1) + 34].copy(), uprev=uprev)
 
 
+def test_nested_dissection_default_options_exact_iteration_count(P, oracle):
+    """The library's defaults (nested dissection for this horizon, cluster
+    fronts, sibling-limited supernodes) on the 12-tray, 20-interval column of
+    seed 1: the cold solve and four warm closed-loop re-solves take exactly
+    the oracle's iteration counts (no rounding-spread allowance)."""
+    T = 20
+    x0 = I.distillation_x0(12, 5, seed=1)
+    sp, _ = I.distillation_setpoints(12, seed=1)
+    prob = _oracle_problem(oracle, "distill12", T, x0, sp)
+    s = P.Solver(P.MODEL_DISTILLATION, [T], N=12, Nf=5)
+    assert s.stats()["ordering_used"] == 2
+    st_or, uprev = None, I.U_REF
+    for k in range(5):
+        s.set_params(x0=prob.x0.copy(), setpoint=np.full(T, sp), u_prev=np.array([uprev]))
+        st_or, info_or, tr = oracle.solve(prob, state=st_or, warm=k > 0)
+        info = s.solve(warm=k > 0)[0]
+        _compare(oracle, prob, s, 0, st_or, info_or, info, check_iters=True, tr_or=tr)
+        uprev = st_or.y[prob.off_u(1)]
+        prob.set_params(x0=st_or.y[prob.off_x(1):prob.off_x(1) + 12].copy(), uprev=uprev)
+
+
 def test_ordering_does_not_change_the_solution(P):
     T = 40
     x0 = I.distillation_x0(12, 5, seed=5)
