@@ -389,6 +389,35 @@ def plate_factorization(P, dev, peak):
     return out
 
 
+def plate_g128_iteration(P, dev, peak):
+    """The 128 x 128 plate with 16 actuators and 100 intervals (n = 1,656,384):
+    analysis and binding, then one interior-point iteration from the cold
+    start, with its factorization and solves timed by the phase timer.  A
+    whole cold solve takes 50 to 60 such iterations."""
+    import torch
+    import paper_2606_04725_gb300.inputs as I
+    g, S, T = 128, 16, 100
+    t0 = time.perf_counter()
+    s = P.Solver(P.MODEL_PLATE, [T], g=g, S=S, device=dev, opts=P.options(max_iter=1))
+    build_s = time.perf_counter() - t0
+    s.set_params(x0=np.zeros(g * g), setpoint=I.plate_target(g, seed=5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = s.solve()[0]
+    torch.cuda.synchronize()
+    it_s = time.perf_counter() - t0
+    ph = s.time_phases(reps=1)
+    st = s.stats()
+    tf = st["factor_flops"] / (ph["ms_factor"] * 1e-3) / 1e12
+    out = {"workload": "plate_g128_S16_T100", "n": st["n_total"], "max_front": st["max_front"],
+           "nnz_L": st["nnz_L"], "factor_flops": st["factor_flops"], "workspace_bytes": st["workspace_bytes"],
+           "build_and_bind_s": build_s, "first_iteration_s": it_s, "iters": info["iters"],
+           "factor_ms": ph["ms_factor"], "solve_ms": ph["ms_solve"], "eval_ms": ph["ms_eval"],
+           "assemble_ms": ph["ms_assemble"], "factor_tflops": tf, "factor_frac_of_peak": tf / peak}
+    s.close()
+    return out
+
+
 def paper_column_resolves(P, dev, resolves=40, warmup=3):
     """The paper's own column and cost (N = 32, feed tray 17, holdups 0.5 /
     0.25 / 1.0, dt = 2, 90 intervals, (x_1 - xbar)^2 + 0.1 (u - ubar)^2):
@@ -447,6 +476,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the single column, the full-size plate, the paper's column and the rebuild variants")
+    ap.add_argument("--schedule", default="",
+                    help="fixed options instead of the autotuner's, e.g. ordering=2,nd_leaf=1,amalgamation=2,"
+                         "panel_scale=3,factor_mode=3 (for profiling runs)")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="solve only the first K instances of the batch (smaller profiling cases)")
+    ap.add_argument("--no-probe", action="store_true", help="skip the FP64 throughput probe")
+    ap.add_argument("--plate-g128", action="store_true",
+                    help="also time one interior-point iteration of the 128 x 128 plate (S = 16, T = 100)")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the interior-point loop from the host instead of the conditional graph "
                          "(same kernels; for profilers that cannot see into conditional graphs)")
@@ -468,6 +505,8 @@ def main():
     wl = I.WORKLOADS[WORKLOAD]
     N, Nf = wl["N"], wl["Nf"]
     hz_all, x0s_all, sps_all = batch_inputs(wl)
+    if args.instances > 0:
+        hz_all, x0s_all, sps_all = hz_all[:args.instances], x0s_all[:args.instances], sps_all[:args.instances]
     # contiguous instance ranges balanced by factorization flops (one range per rank)
     weights = instance_weights(P.MODEL_DISTILLATION, hz_all, N=N, Nf=Nf)
     i0, i1 = rank_slice(weights, rank, world)
@@ -476,8 +515,12 @@ def main():
     sp_host = packed_setpoints(hz, sps)
     # the schedule (ordering, amalgamation, solve form) chosen by the library's autotuner
     t0 = time.perf_counter()
-    opts, rep = P.autotune(P.MODEL_DISTILLATION, hz, x0=x0s.ravel().copy(), setpoint=sp_host,
-                           u_prev=np.full(ni, I.U_REF), device=dev, N=N, Nf=Nf)
+    if args.schedule:
+        opts = P.options(**{k: int(v) for k, v in (kv.split("=") for kv in args.schedule.split(","))})
+        rep = {"candidates": []}
+    else:
+        opts, rep = P.autotune(P.MODEL_DISTILLATION, hz, x0=x0s.ravel().copy(), setpoint=sp_host,
+                               u_prev=np.full(ni, I.U_REF), device=dev, N=N, Nf=Nf)
     tune_s = time.perf_counter() - t0
     if args.host_loop:
         opts.use_graph = 0
@@ -575,7 +618,7 @@ def main():
     clk = clk.summary()
     peak = fp64_nominal_tflops(clk["sm_max_mhz"])
     achieved = st["factor_flops"] / (ph["ms_factor"] * 1e-3) / 1e12
-    probe = fp64_probe(P)
+    probe = fp64_probe(P) if not args.no_probe else {}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -605,7 +648,7 @@ def main():
                          "kernel": "numeric factorization of the whole batch (the launches of one factorization)",
                          "flops_per_launch_set": st["factor_flops"],
                          "peak_basis": "152 SMs x 2 FP64 FMA/clock x max SM clock (nominal FP64 rate)",
-                         "frac_of_measured_dfma": achieved / probe["dfma_tflops"]},
+                         "frac_of_measured_dfma": achieved / probe["dfma_tflops"] if probe else None},
             "fp64_probe": probe,
             "autotune": {"seconds": tune_s,
                          "columns": ["ordering", "nd_leaf", "panel_scale", "amalgamation", "factor_mode",
@@ -636,6 +679,8 @@ def main():
                            "note": "destroy + analysis + bind + solve of the whole batch per re-solve, one each"}
     s.close()
     del flush
+    if args.plate_g128:
+        line["plate_g128"] = plate_g128_iteration(P, dev, peak)
     if not args.no_extras:
         line["single_column"] = single_column(P, dev, rank=rank)
         line["plate_full_size"] = plate_factorization(P, dev, peak)
