@@ -22,7 +22,7 @@ _SOURCES = [os.path.join(_HERE, f) for f in ("nmpc_oracle.c", "nmpc_oracle.h", "
 _lock = threading.Lock()
 _lib = None
 
-OR_DISTILL, OR_PLATE, OR_TOY = 0, 1, 2
+OR_DISTILL, OR_PLATE, OR_TOY, OR_PPLATE = 0, 1, 2, 3
 STATUS = {0: "converged", 10: "max_iter", 11: "linesearch_fail", 12: "inertia_fail", 13: "nonfinite", 2: "alloc"}
 
 
@@ -47,7 +47,8 @@ class _Problem(C.Structure):
                 ("wu", C.c_double), ("ubar", C.c_double),
                 ("kappa", C.c_double), ("cq", C.c_double), ("rho_u", C.c_double),
                 ("xlo", C.c_double), ("xhi", C.c_double), ("ulo", C.c_double), ("uhi", C.c_double),
-                ("x0", C.POINTER(C.c_double)), ("sp", C.POINTER(C.c_double)), ("uprev", C.c_double)]
+                ("x0", C.POINTER(C.c_double)), ("sp", C.POINTER(C.c_double)), ("uprev", C.c_double),
+                ("Tb", C.c_double), ("qloss", C.c_double)]
 
 
 class _Options(C.Structure):
@@ -110,7 +111,7 @@ class Problem:
 
     def __init__(self, model, T, dt, x0, sp, *, N=0, Nf=0, g=0, S=0, uprev=0.0,
                  alpha=1.6, D=0.2, F=0.4, xF=0.5, Ac=1.0, At=1.0, Ar=1.0, wdu=0.01, wu=0.0, ubar=0.0,
-                 kappa=0.01, cq=0.01, rho_u=1e-3, xlo=0.0, xhi=1.0, ulo=1.0, uhi=5.0):
+                 kappa=0.01, cq=0.01, rho_u=1e-3, xlo=0.0, xhi=1.0, ulo=1.0, uhi=5.0, Tb=50.0, qloss=10.0):
         self.x0 = np.ascontiguousarray(x0, dtype=np.float64)
         self.sp = np.ascontiguousarray(sp, dtype=np.float64)
         p = _Problem()
@@ -120,6 +121,7 @@ class Problem:
         p.kappa, p.cq, p.rho_u = kappa, cq, rho_u
         p.xlo, p.xhi, p.ulo, p.uhi = xlo, xhi, ulo, uhi
         p.uprev = uprev
+        p.Tb, p.qloss = Tb, qloss
         self._p = p
         if lib().or_setup(C.byref(p)) != 0:
             raise ValueError("invalid problem dimensions")
@@ -167,6 +169,20 @@ def plate(g, S, T, x0, target, dt=1.0, xhi=1.2, **kw):
     kw.setdefault("ulo", 0.0)
     kw.setdefault("uhi", 1.0)
     return Problem(OR_PLATE, T, dt, x0, target, g=g, S=S, xhi=xhi, **kw)
+
+
+def paper_plate(n, T, x0, sp, uprev, dt=0.08, **kw):
+    """The paper's heated plate (Sec. 4.2, eq. (pde-ocp), table pde-params):
+    n x n nodes on [-1, 1]^2, alpha = 230, T_b = 50, q_loss = 10, rho = 1e-8,
+    Q >= 50, dt = 0.08; sp holds the T stage setpoints T_sp(t_k); uprev is the
+    control of the cold start."""
+    kw.setdefault("kappa", 230.0)
+    kw.setdefault("rho_u", 1e-8)
+    kw.setdefault("xlo", -INF)
+    kw.setdefault("xhi", INF)
+    kw.setdefault("ulo", 50.0)
+    kw.setdefault("uhi", INF)
+    return Problem(OR_PPLATE, T, dt, x0, sp, g=n, S=1, uprev=uprev, **kw)
 
 
 def toy(T, y0, sp, dt, **kw):
@@ -277,7 +293,7 @@ def initial_guess(prob):
         if k >= 1:
             ou = prob.off_u(k)
             lo, hi = yL[ou:ou + prob.nu], yU[ou:ou + prob.nu]
-            if prob.model == OR_DISTILL:
+            if prob.model in (OR_DISTILL, OR_PPLATE):
                 y[ou] = prob._p.uprev
             else:
                 y[ou:ou + prob.nu] = np.where(np.isfinite(lo) & np.isfinite(hi), 0.5 * (lo + hi), 0.0)

@@ -45,27 +45,38 @@ static int or_plate_cell_segments(const or_problem* p, int c, int* segs) {
 #define SFX(name) name##_d
 #define SIN sin
 #define COS cos
+#define CBRT cbrt
+#define SQRT sqrt
 #include "or_model.inc"
 #undef R
 #undef SFX
 #undef SIN
 #undef COS
+#undef CBRT
+#undef SQRT
 
 #define R double complex
 #define SFX(name) name##_z
 #define SIN csin
 #define COS ccos
+#define CBRT(z) cpow((z), 1.0 / 3.0)
+#define SQRT csqrt
 #include "or_model.inc"
 #undef R
 #undef SFX
 #undef SIN
 #undef COS
+#undef CBRT
+#undef SQRT
 
 int or_setup(or_problem* p) {
   if (p->model == OR_DISTILL) { p->nx = p->N; p->nu = 1; }
   else if (p->model == OR_PLATE) {
     if (p->g < 2 || p->S < 4 || p->S % 4 || p->g % (p->S / 4)) return -1;
     p->nx = p->g * p->g; p->nu = p->S;
+  } else if (p->model == OR_PPLATE) {
+    if (p->g < 4) return -1;  /* g = n grid points per side; the states are the (n-2)^2 interior nodes */
+    p->nx = (p->g - 2) * (p->g - 2); p->nu = 1;
   } else { p->nx = 1; p->nu = 1; }
   if (p->T < 1) return -1;
   p->n = p->nx + p->T * (p->nx + p->nu);
@@ -82,6 +93,9 @@ int or_jac_nnz(const or_problem* p) {
       const int g = p->g, ci = i % g, cj = i / g;
       int segs[2];
       per = 1 + 1 + (ci > 0) + (ci < g - 1) + (cj > 0) + (cj < g - 1) + or_plate_cell_segments(p, i, segs);
+    } else if (p->model == OR_PPLATE) {
+      const int mm = p->g - 2, ii = i % mm, jj = i / mm; /* interior node (ii + 1, jj + 1) */
+      per = 1 + 1 + (ii > 0) + (ii < mm - 1) + (jj > 0) + (jj < mm - 1) + (ii == 0 || jj == 0);
     } else per = 3;
     nnz += per * p->T;
   }
@@ -158,11 +172,38 @@ int or_hessian(const or_problem* p, const double* y, const double* lam,
       const double h = 1.0 / p->g;
       for (int c = 0; c < nx; ++c) k = push_trip(rows, cols, vals, cap, k, ox + c, ox + c, 2.0 * p->dt * h * h);
       for (int s = 0; s < p->nu; ++s) k = push_trip(rows, cols, vals, cap, k, ou + s, ou + s, 2.0 * p->rho_u * p->dt);
+    } else if (p->model == OR_PPLATE) {
+      for (int c = 0; c < nx; ++c) {
+        const double w = pplate_weight_d(p, c);
+        if (w != 0.0) k = push_trip(rows, cols, vals, cap, k, ox + c, ox + c, 2.0 * p->dt * w);
+      }
+      k = push_trip(rows, cols, vals, cap, k, ou, ou, 2.0 * p->rho_u * p->dt);
     } else {
       k = push_trip(rows, cols, vals, cap, k, ox, ox, 2.0 * p->dt);
     }
   }
   if (p->model == OR_PLATE) return k; /* linear dynamics */
+  if (p->model == OR_PPLATE) {
+    /* the dynamics are linear in T; the boundary data are not in Q:
+     * d2/dQ2 4.1 Q^(1/3) = -(8.2/9) Q^(-5/3), d2/dQ2 Q^(1/2) = -Q^(-3/2) / 4 */
+    const int n = p->g, mm = n - 2;
+    const double h = 2.0 / (n - 1), c = p->kappa / (h * h), sc = pplate_row_scale_d(p);
+    for (int t = 0; t < p->T; ++t) {
+      const int oun = or_off_u(p, t + 1);
+      const double Q = y[oun];
+      const double* lk = lam + nx * (t + 1);
+      double s = 0.0;
+      for (int q = 0; q < nx; ++q) {
+        const int ii = q % mm + 1, jj = q / mm + 1;
+        double d2 = 0.0;
+        if (ii == 1) d2 += -(8.2 / 9.0) * pow(Q, -5.0 / 3.0);
+        if (jj == 1) d2 += -0.25 * pow(Q, -1.5);
+        s += lk[q] * sc * (-p->dt * c * d2);  /* the (scaled) constraint carries -sc dt f */
+      }
+      k = push_trip(rows, cols, vals, cap, k, oun, oun, s);
+    }
+    return k;
+  }
   for (int t = 0; t < p->T; ++t) {
     const int oxn = or_off_x(p, t + 1), oun = or_off_u(p, t + 1);
     const double* xn = y + oxn;

@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-enum { OR_DISTILL = 0, OR_PLATE = 1, OR_TOY = 2 };
+enum { OR_DISTILL = 0, OR_PLATE = 1, OR_TOY = 2, OR_PPLATE = 3 };
 
 typedef struct {
   int model;
@@ -48,7 +48,8 @@ typedef struct {
   double xlo, xhi, ulo, uhi;               /* bounds on x_1..x_T, u_1..u_T (+-inf allowed) */
   const double* x0;   /* nx: initial state parameter */
   const double* sp;   /* distillation/toy: T setpoints; plate: g*g target field */
-  double uprev;       /* distillation: u_0 */
+  double uprev;       /* distillation: u_0; paper's plate: the control of the cold start */
+  double Tb, qloss;   /* paper's plate (Sec. 4.2): fixed boundary temperature, heat loss */
 } or_problem;
 
 typedef struct {

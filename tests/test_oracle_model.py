@@ -4,7 +4,10 @@ Derivatives are pinned by complex-step differentiation of the oracle's own
 residual code (same source compiled for complex numbers), which is exact to
 rounding.  The residuals themselves are pinned by conservation laws that hold
 for any state and control, by the paper's steady state (Sec. 4.1, Table
-distill-params) and by exactness of the 5-point stencil on quadratics.
+distill-params) and by exactness of the 5-point stencil on quadratics.  The
+paper's heated plate (Sec. 4.2) is pinned by the discrete energy balance
+with its heat-loss term, by a uniform field that is stationary when the
+boundary data agree, and by the region integral of its tracking cost.
 """
 import numpy as np
 import pytest
@@ -22,6 +25,12 @@ def _plate(O, g=4, S=8, T=2):
     return O.plate(g, S, T, rng.uniform(0, 1, g * g), rng.uniform(0, 1, g * g), dt=0.9, cq=0.3)
 
 
+def _pplate(O, n=6, T=3, **kw):
+    """The paper's heated plate (Sec. 4.2) on a coarse grid, arbitrary data."""
+    rng = np.random.default_rng(13)
+    return O.paper_plate(n, T, rng.uniform(40, 70, (n - 2) ** 2), rng.uniform(50, 60, T), 3000.0, dt=0.08, **kw)
+
+
 def _toy(O, T=4):
     return O.toy(T, 1.0, np.sin(np.arange(1, T + 1) * 0.7), dt=0.7)
 
@@ -37,7 +46,7 @@ def _interior_point(prob, seed=5):
 def _models(O):
     return [("distill", _distill(O)), ("distill_paper_holdups", _distill(O, Ac=0.5, At=0.25, Ar=1.0)),
             ("distill_paper_cost", _distill(O, Ac=0.5, At=0.25, Ar=1.0, wdu=0.0, wu=0.1, ubar=2.51459)),
-            ("plate", _plate(O)), ("toy", _toy(O))]
+            ("plate", _plate(O)), ("paper_plate", _pplate(O)), ("toy", _toy(O))]
 
 
 def test_jacobian_complex_step(oracle):
@@ -200,3 +209,100 @@ def test_paper_control_cost_is_the_integral_for_a_constant_control(oracle):
             y[p.off_u(k)] = c
         f, _, _, _ = oracle.evaluate(p, y)
         assert abs(f - 0.1 * (c - ubar) ** 2 * 180.0) < 1e-12 * max(1.0, f), (c, f)
+
+
+def _pplate_f(O, p, x, Q):
+    """f_c(x, Q) of every interior node, from the residual of one step with
+    x_1 = x, x_0 = 0: the step rows are s (x - 0 - dt f), scaled by
+    s = 1 / (1 + 4 dt alpha / h^2) to a unit diagonal."""
+    y = np.zeros(p.n)
+    y[p.off_x(1):p.off_x(1) + p.nx] = x
+    y[p.off_u(1)] = Q
+    p.set_params(x0=np.zeros(p.nx))
+    _, _, h, _ = O.evaluate(p, y)
+    hh = 2.0 / (p._p.g - 1)
+    s = 1.0 / (1.0 + 4.0 * p._p.dt * p._p.kappa / hh ** 2)
+    return (x - h[p.nx:2 * p.nx] / s) / p._p.dt
+
+
+def test_paper_plate_step_rows_have_a_unit_diagonal(oracle):
+    """The scaled step row of node c has coefficient 1 on T_{k+1,c} and -s on
+    T_{k,c}, s = 1 / (1 + 4 dt alpha / h^2)."""
+    O = oracle
+    p = _pplate(O, n=7, T=2)
+    y = _interior_point(p)
+    J = O.jacobian_dense(p, y)
+    hh = 2.0 / 6
+    s = 1.0 / (1.0 + 4.0 * 0.08 * 230.0 / hh ** 2)
+    for c in range(p.nx):
+        r = p.nx + p.nx + c  # step 1 -> 2
+        assert abs(J[r, p.off_x(2) + c] - 1.0) <= 1e-14
+        assert abs(J[r, p.off_x(1) + c] + s) <= 1e-16
+
+
+def test_paper_plate_energy_balance(oracle):
+    """Discrete divergence theorem of the 5-point Laplacian: summed over the
+    interior nodes the interior edges cancel, so sum_c f_c = alpha (sum over
+    the edges to the boundary of (T_boundary - T_c) / h^2 - 5 q_loss^2 nx),
+    with the boundary data of eq. (pde-ocp): 4.1 Q^(1/3) at x1 = -1, Q^(1/2)
+    at x2 = -1, T_b at x1 = 1 and x2 = 1."""
+    O = oracle
+    rng = np.random.default_rng(21)
+    for n in (5, 9, 21):
+        p = O.paper_plate(n, 1, np.zeros((n - 2) ** 2), np.zeros(1), 100.0, Tb=47.0, qloss=3.0)
+        m = n - 2
+        h = 2.0 / (n - 1)
+        for _ in range(3):
+            x = rng.uniform(-100, 300, m * m)
+            Q = rng.uniform(50, 1e5)
+            f = _pplate_f(O, p, x, Q)
+            T = x.reshape(m, m)  # T[j, i] for node (i + 1, j + 1)
+            edges = (4.1 * np.cbrt(Q) - T[:, 0]).sum() + (47.0 - T[:, -1]).sum() \
+                + (np.sqrt(Q) - T[0, :]).sum() + (47.0 - T[-1, :]).sum()
+            want = 230.0 * (edges / h ** 2 - 5.0 * 3.0 ** 2 * m * m)
+            assert abs(f.sum() - want) <= 1e-11 * max(abs(want), 230.0 * np.abs(x).sum() / h ** 2), (n, f.sum(), want)
+
+
+def test_paper_plate_uniform_field_is_stationary_when_boundaries_agree(oracle):
+    """Without heat loss, a uniform field equal to all four boundary values is
+    stationary: 4.1 Q^(1/3) = Q^(1/2) at Q = 4.1^6, where both equal 4.1^3,
+    and T_b is set to that value."""
+    O = oracle
+    Q = 4.1 ** 6
+    Tb = 4.1 ** 3
+    for n in (4, 7, 12):
+        p = O.paper_plate(n, 1, np.zeros((n - 2) ** 2), np.zeros(1), 100.0, Tb=Tb, qloss=0.0)
+        f = _pplate_f(O, p, np.full((n - 2) ** 2, Tb), Q)
+        assert np.max(np.abs(f)) <= 1e-9 * 230.0 * Tb * (n - 1) ** 2, (n, np.max(np.abs(f)))
+        # and a perturbation of one boundary breaks it only next to that boundary
+        f2 = _pplate_f(O, p, np.full((n - 2) ** 2, Tb), Q * 1.1)
+        m = n - 2
+        F = f2.reshape(m, m)
+        assert np.all(F[1:, 1:] == 0) or m == 1
+        assert np.all(F[:, 0] > 0) and np.all(F[0, :] > 0)
+        # the x1 = -1 side (node column i = 1) carries 4.1 Q^(1/3), the x2 = -1
+        # side (node row j = 1) Q^(1/2): they move by different amounts
+        a = 230.0 * (n - 1) ** 2 / 4.0
+        left, bottom = a * (4.1 * np.cbrt(Q * 1.1) - Tb), a * (np.sqrt(Q * 1.1) - Tb)
+        assert np.allclose(F[1:, 0], left, rtol=1e-9) and np.allclose(F[0, 1:], bottom, rtol=1e-9)
+        assert np.isclose(F[0, 0], left + bottom, rtol=1e-9) and not np.isclose(left, bottom, rtol=1e-3)
+
+
+def test_paper_plate_tracking_cost_is_the_region_integral(oracle):
+    """The stage cost's region term integrates a constant deviation d over
+    [-0.5, 0.5]^2 exactly (area 1): with x_k = sp_k + d on every interior node
+    and Q_k = Q, f = T dt (d^2 + rho Q^2), for grids whose nodes fall on the
+    region's edges (n - 1 a multiple of 4)."""
+    O = oracle
+    for n in (5, 9, 21):
+        T = 3
+        sp = np.array([58.0, 55.0, 63.0])
+        p = O.paper_plate(n, T, np.zeros((n - 2) ** 2), sp, 100.0)
+        d, Q = 1.7, 2500.0
+        y = np.zeros(p.n)
+        for k in range(1, T + 1):
+            y[p.off_x(k):p.off_x(k) + p.nx] = sp[k - 1] + d
+            y[p.off_u(k)] = Q
+        f, _, _, _ = O.evaluate(p, y)
+        want = T * 0.08 * (d * d + 1e-8 * Q * Q)
+        assert abs(f - want) <= 1e-12 * want, (n, f, want)
