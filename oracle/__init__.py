@@ -22,7 +22,7 @@ _SOURCES = [os.path.join(_HERE, f) for f in ("nmpc_oracle.c", "nmpc_oracle.h", "
 _lock = threading.Lock()
 _lib = None
 
-OR_DISTILL, OR_PLATE, OR_TOY, OR_PPLATE = 0, 1, 2, 3
+OR_DISTILL, OR_PLATE, OR_TOY, OR_PPLATE, OR_DDAE = 0, 1, 2, 3, 4
 STATUS = {0: "converged", 10: "max_iter", 11: "linesearch_fail", 12: "inertia_fail", 13: "nonfinite", 2: "alloc"}
 
 
@@ -48,7 +48,7 @@ class _Problem(C.Structure):
                 ("kappa", C.c_double), ("cq", C.c_double), ("rho_u", C.c_double),
                 ("xlo", C.c_double), ("xhi", C.c_double), ("ulo", C.c_double), ("uhi", C.c_double),
                 ("x0", C.POINTER(C.c_double)), ("sp", C.POINTER(C.c_double)), ("uprev", C.c_double),
-                ("Tb", C.c_double), ("qloss", C.c_double)]
+                ("Tb", C.c_double), ("qloss", C.c_double), ("nr", C.c_int)]
 
 
 class _Options(C.Structure):
@@ -169,6 +169,13 @@ def plate(g, S, T, x0, target, dt=1.0, xhi=1.2, **kw):
     kw.setdefault("ulo", 0.0)
     kw.setdefault("uhi", 1.0)
     return Problem(OR_PLATE, T, dt, x0, target, g=g, S=S, xhi=xhi, **kw)
+
+
+def distillation_dae(N, Nf, T, x0, sp, uprev, dt=1.0, **kw):
+    """The column of eq. (distill-ocp) with its algebraic variables: per stage
+    [x (N) | y (N) u L V S], the equilibria and flow equations as rows,
+    y in [0, 1], L, V, S in [0, 10]."""
+    return Problem(OR_DDAE, T, dt, x0, sp, N=N, Nf=Nf, uprev=uprev, **kw)
 
 
 def paper_plate(n, T, x0, sp, uprev, dt=0.08, **kw):
@@ -295,6 +302,11 @@ def initial_guess(prob):
             lo, hi = yL[ou:ou + prob.nu], yU[ou:ou + prob.nu]
             if prob.model in (OR_DISTILL, OR_PPLATE):
                 y[ou] = prob._p.uprev
+            elif prob.model == OR_DDAE:
+                # the algebraic variables consistent with x0 and u_prev
+                p, u = prob._p, prob._p.uprev
+                y[ou:ou + prob.nx] = p.alpha * prob.x0 / (1.0 + (p.alpha - 1.0) * prob.x0)
+                y[ou + prob.nx:ou + prob.nx + 4] = [u, u * p.D, u * p.D + p.D, u * p.D + p.F]
             else:
                 y[ou:ou + prob.nu] = np.where(np.isfinite(lo) & np.isfinite(hi), 0.5 * (lo + hi), 0.0)
     return y

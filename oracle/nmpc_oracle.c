@@ -77,10 +77,15 @@ int or_setup(or_problem* p) {
   } else if (p->model == OR_PPLATE) {
     if (p->g < 4) return -1;  /* g = n grid points per side; the states are the (n-2)^2 interior nodes */
     p->nx = (p->g - 2) * (p->g - 2); p->nu = 1;
+  } else if (p->model == OR_DDAE) {
+    /* eq. (distill-ocp) with its algebraic variables: per stage [x (N) | y (N) u L V S],
+     * per step N balances, N equilibria and the 3 flow equations */
+    p->nx = p->N; p->nu = p->N + 4;
   } else { p->nx = 1; p->nu = 1; }
   if (p->T < 1) return -1;
+  p->nr = (p->model == OR_DDAE) ? 2 * p->N + 3 : p->nx;
   p->n = p->nx + p->T * (p->nx + p->nu);
-  p->m = p->nx * (p->T + 1);
+  p->m = p->nx + p->T * p->nr;
   return 0;
 }
 
@@ -96,8 +101,25 @@ int or_jac_nnz(const or_problem* p) {
     } else if (p->model == OR_PPLATE) {
       const int mm = p->g - 2, ii = i % mm, jj = i / mm; /* interior node (ii + 1, jj + 1) */
       per = 1 + 1 + (ii > 0) + (ii < mm - 1) + (jj > 0) + (jj < mm - 1) + (ii == 0 || jj == 0);
+    } else if (p->model == OR_DDAE) {
+      per = 0; /* counted below by row kind */
     } else per = 3;
     nnz += per * p->T;
+  }
+  if (p->model == OR_DDAE) {
+    const int N = p->N, Nf = p->Nf;
+    int step = 0;
+    for (int i = 1; i <= N; ++i) {
+      /* x_k,i, the x_{k+1} neighbours, the y_{k+1} entries, the flows */
+      if (i == 1) step += 1 + 1 + 1 + 1;                  /* x_k1 | x1 | y2 | V */
+      else if (i == N) step += 1 + 2 + 1 + 2;             /* x_kN | x_{N-1} x_N | y_N | V S */
+      else if (i < Nf) step += 1 + 2 + 2 + 2;             /* | x_{i-1} x_i | y_i y_{i+1} | L V */
+      else if (i == Nf) step += 1 + 2 + 2 + 3;            /* | ... | L V S */
+      else step += 1 + 2 + 2 + 2;                         /* | ... | V S */
+    }
+    step += 2 * N;      /* equilibria: x_i, y_i */
+    step += 2 + 2 + 2;  /* L - u D, V - L - D, S - L - F */
+    nnz += step * p->T;
   }
   return nnz;
 }
@@ -110,6 +132,10 @@ void or_bounds(const or_problem* p, double* yL, double* yU) {
     int ox = or_off_x(p, k), ou = or_off_u(p, k);
     for (int i = 0; i < p->nx; ++i) { yL[ox + i] = p->xlo; yU[ox + i] = p->xhi; }
     for (int s = 0; s < p->nu; ++s) { yL[ou + s] = p->ulo; yU[ou + s] = p->uhi; }
+    if (p->model == OR_DDAE) { /* y in [0, 1], u in [ulo, uhi], L, V, S in [0, 10] (eq. distill-ocp) */
+      for (int s = 0; s < p->N; ++s) { yL[ou + s] = 0.0; yU[ou + s] = 1.0; }
+      for (int s = p->N + 1; s < p->N + 4; ++s) { yL[ou + s] = 0.0; yU[ou + s] = 10.0; }
+    }
   }
 }
 
@@ -160,13 +186,14 @@ int or_hessian(const or_problem* p, const double* y, const double* lam,
   const int nx = p->nx;
   for (int t = 1; t <= p->T; ++t) {
     int ox = or_off_x(p, t), ou = or_off_u(p, t);
-    if (p->model == OR_DISTILL) {
+    if (p->model == OR_DISTILL || p->model == OR_DDAE) {
+      const int cu = (p->model == OR_DDAE) ? p->N : 0;  /* u within the control block */
       k = push_trip(rows, cols, vals, cap, k, ox, ox, 2.0 * p->dt);
-      k = push_trip(rows, cols, vals, cap, k, ou, ou, 2.0 * p->wdu + 2.0 * p->wu * p->dt);
+      k = push_trip(rows, cols, vals, cap, k, ou + cu, ou + cu, 2.0 * p->wdu + 2.0 * p->wu * p->dt);
       if (t > 1) {
-        int oup = or_off_u(p, t - 1);
+        int oup = or_off_u(p, t - 1) + cu;
         k = push_trip(rows, cols, vals, cap, k, oup, oup, 2.0 * p->wdu);
-        k = push_trip(rows, cols, vals, cap, k, ou, oup, -2.0 * p->wdu);
+        k = push_trip(rows, cols, vals, cap, k, ou + cu, oup, -2.0 * p->wdu);
       }
     } else if (p->model == OR_PLATE) {
       const double h = 1.0 / p->g;
@@ -183,6 +210,38 @@ int or_hessian(const or_problem* p, const double* y, const double* lam,
     }
   }
   if (p->model == OR_PLATE) return k; /* linear dynamics */
+  if (p->model == OR_DDAE) {
+    /* the balances are bilinear in (flow, composition); the equilibria carry
+     * -vle(x), whose second derivative is -2 a (a - 1) / (1 + (a - 1) x)^3 */
+    const int N = p->N, Nf = p->Nf;
+    const double a = p->alpha;
+    for (int t = 0; t < p->T; ++t) {
+      const int oxn = or_off_x(p, t + 1), oun = or_off_u(p, t + 1);
+      const int cL = oun + N + 1, cV = oun + N + 2, cS = oun + N + 3;
+      const double* lk = lam + nx + p->nr * t;
+      for (int i = 1; i <= N; ++i) {
+        const double c = -p->dt * lk[i - 1];  /* the balance carries -dt f_i */
+        if (i == 1) {
+          k = push_trip(rows, cols, vals, cap, k, cV, oun + 1, c / p->Ac);
+          k = push_trip(rows, cols, vals, cap, k, cV, oxn, -c / p->Ac);
+        } else if (i == N) {
+          k = push_trip(rows, cols, vals, cap, k, cS, oxn + N - 2, c / p->Ar);
+          k = push_trip(rows, cols, vals, cap, k, cV, oun + N - 1, -c / p->Ar);
+        } else {
+          const int cin = (i <= Nf) ? cL : cS, cout = (i < Nf) ? cL : cS;
+          k = push_trip(rows, cols, vals, cap, k, cin, oxn + i - 2, c / p->At);
+          k = push_trip(rows, cols, vals, cap, k, cout, oxn + i - 1, -c / p->At);
+          k = push_trip(rows, cols, vals, cap, k, cV, oun + i - 1, -c / p->At);
+          k = push_trip(rows, cols, vals, cap, k, cV, oun + i, c / p->At);
+        }
+      }
+      for (int i = 0; i < N; ++i) {
+        const double den = 1.0 + (a - 1.0) * y[oxn + i];
+        k = push_trip(rows, cols, vals, cap, k, oxn + i, oxn + i, lk[N + i] * 2.0 * a * (a - 1.0) / (den * den * den));
+      }
+    }
+    return k;
+  }
   if (p->model == OR_PPLATE) {
     /* the dynamics are linear in T; the boundary data are not in Q:
      * d2/dQ2 4.1 Q^(1/3) = -(8.2/9) Q^(-5/3), d2/dQ2 Q^(1/2) = -Q^(-3/2) / 4 */
@@ -191,7 +250,7 @@ int or_hessian(const or_problem* p, const double* y, const double* lam,
     for (int t = 0; t < p->T; ++t) {
       const int oun = or_off_u(p, t + 1);
       const double Q = y[oun];
-      const double* lk = lam + nx * (t + 1);
+      const double* lk = lam + nx + p->nr * t;
       double s = 0.0;
       for (int q = 0; q < nx; ++q) {
         const int ii = q % mm + 1, jj = q / mm + 1;
@@ -208,7 +267,7 @@ int or_hessian(const or_problem* p, const double* y, const double* lam,
     const int oxn = or_off_x(p, t + 1), oun = or_off_u(p, t + 1);
     const double* xn = y + oxn;
     const double u = y[oun];
-    const double* lk = lam + nx * (t + 1);
+    const double* lk = lam + nx + p->nr * t;
     if (p->model == OR_TOY) {
       k = push_trip(rows, cols, vals, cap, k, oxn, oxn, lk[0] * 6.0 * p->dt * xn[0]);
       k = push_trip(rows, cols, vals, cap, k, oun, oun, lk[0] * 4.0 * p->dt * sin(u));

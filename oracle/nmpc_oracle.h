@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-enum { OR_DISTILL = 0, OR_PLATE = 1, OR_TOY = 2, OR_PPLATE = 3 };
+enum { OR_DISTILL = 0, OR_PLATE = 1, OR_TOY = 2, OR_PPLATE = 3, OR_DDAE = 4 };
 
 typedef struct {
   int model;
@@ -50,6 +50,7 @@ typedef struct {
   const double* sp;   /* distillation/toy: T setpoints; plate: g*g target field */
   double uprev;       /* distillation: u_0; paper's plate: the control of the cold start */
   double Tb, qloss;   /* paper's plate (Sec. 4.2): fixed boundary temperature, heat loss */
+  int nr;             /* filled by or_setup: rows per backward-Euler step (nx except for OR_DDAE) */
 } or_problem;
 
 typedef struct {

@@ -31,6 +31,12 @@ def _pplate(O, n=6, T=3, **kw):
     return O.paper_plate(n, T, rng.uniform(40, 70, (n - 2) ** 2), rng.uniform(50, 60, T), 3000.0, dt=0.08, **kw)
 
 
+def _ddae(O, N=7, Nf=4, T=3, **kw):
+    """The column with its algebraic variables (eq. distill-ocp as printed)."""
+    rng = np.random.default_rng(14)
+    return O.distillation_dae(N, Nf, T, rng.uniform(0.1, 0.9, N), rng.uniform(0.3, 0.9, T), 2.2, dt=0.7, **kw)
+
+
 def _toy(O, T=4):
     return O.toy(T, 1.0, np.sin(np.arange(1, T + 1) * 0.7), dt=0.7)
 
@@ -46,7 +52,8 @@ def _interior_point(prob, seed=5):
 def _models(O):
     return [("distill", _distill(O)), ("distill_paper_holdups", _distill(O, Ac=0.5, At=0.25, Ar=1.0)),
             ("distill_paper_cost", _distill(O, Ac=0.5, At=0.25, Ar=1.0, wdu=0.0, wu=0.1, ubar=2.51459)),
-            ("plate", _plate(O)), ("paper_plate", _pplate(O)), ("toy", _toy(O))]
+            ("plate", _plate(O)), ("paper_plate", _pplate(O)), ("distill_dae", _ddae(O)),
+            ("distill_dae_paper", _ddae(O, Ac=0.5, At=0.25, Ar=1.0, wdu=0.0, wu=0.1, ubar=2.51459)), ("toy", _toy(O))]
 
 
 def test_jacobian_complex_step(oracle):
@@ -306,3 +313,52 @@ def test_paper_plate_tracking_cost_is_the_region_integral(oracle):
         f, _, _, _ = O.evaluate(p, y)
         want = T * 0.08 * (d * d + 1e-8 * Q * Q)
         assert abs(f - want) <= 1e-12 * want, (n, f, want)
+
+
+def test_jacobian_pattern_size_and_row_layout(oracle):
+    """The CSR Jacobian fills exactly or_jac_nnz entries, rows ascending in
+    columns; the DAE column has 2N + 3 rows per step (N balances, N
+    equilibria, 3 flow equations)."""
+    O = oracle
+    for name, p in _models(O):
+        y = _interior_point(p)
+        _, _, _, (rp, ci, _) = O.evaluate(p, y)
+        assert rp[-1] == p.jac_nnz() and rp.size == p.m + 1, name
+        for r in range(p.m):
+            assert np.all(np.diff(ci[rp[r]:rp[r + 1]]) > 0), (name, r)
+    p = _ddae(O, N=7, T=3)
+    assert p.m == 7 + 3 * (2 * 7 + 3) and p.n == 7 + 3 * (7 + 7 + 4)
+
+
+def test_distillation_dae_residual_vanishes_on_the_substituted_trajectory(oracle):
+    """Given any x, u trajectory, setting y = vle(x), L = u D, V = L + D,
+    S = L + F makes the algebraic rows zero and the balance rows equal to the
+    substituted model's rows (eq. distill-ocp with y, L, V, S eliminated)."""
+    O = oracle
+    N, Nf, T = 9, 5, 4
+    rng = np.random.default_rng(31)
+    x0 = rng.uniform(0.1, 0.9, N)
+    sp = rng.uniform(0.3, 0.9, T)
+    pd = O.distillation_dae(N, Nf, T, x0, sp, 2.2, dt=0.7, Ac=0.5, At=0.25)
+    ps = O.distillation(N, Nf, T, x0, sp, 2.2, dt=0.7, Ac=0.5, At=0.25)
+    ys = rng.uniform(0.1, 0.9, ps.n)
+    for k in range(1, T + 1):
+        ys[ps.off_u(k)] = rng.uniform(1, 5)
+    yd = np.zeros(pd.n)
+    yd[:N] = ys[:N]
+    a = 1.6
+    for k in range(1, T + 1):
+        x = ys[ps.off_x(k):ps.off_x(k) + N]
+        u = ys[ps.off_u(k)]
+        yd[pd.off_x(k):pd.off_x(k) + N] = x
+        o = pd.off_u(k)
+        yd[o:o + N] = a * x / (1 + (a - 1) * x)
+        yd[o + N:o + N + 4] = [u, u * 0.2, u * 0.2 + 0.2, u * 0.2 + 0.4]
+    fd, _, hd, _ = O.evaluate(pd, yd)
+    fs, _, hs, _ = O.evaluate(ps, ys)
+    assert abs(fd - fs) <= 1e-13 * max(1.0, abs(fs))
+    nr = 2 * N + 3
+    for k in range(T):
+        blk = hd[N + nr * k:N + nr * (k + 1)]
+        np.testing.assert_allclose(blk[:N], hs[N * (k + 1):N * (k + 2)], rtol=1e-13, atol=1e-14)
+        assert np.max(np.abs(blk[N:])) <= 1e-15
