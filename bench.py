@@ -76,7 +76,7 @@ def hbm_rooflines(st, ph, latency_bound=False):
 
 
 class ClockSampler:
-    """nvidia-smi samples (every 50 ms) during the timed region; entering waits
+    """nvidia-smi samples (every 200 ms) during the timed region; entering waits
     (up to 2 s) for the first sample so that the sampling covers the region."""
 
     def __init__(self, index=0):
@@ -90,7 +90,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -418,7 +418,7 @@ def plate_g128_iteration(P, dev, peak):
     return out
 
 
-def paper_column_resolves(P, dev, resolves=40, warmup=3):
+def paper_column_resolves(P, dev, resolves=40, warmup=3, model=None):
     """The paper's own column and cost (N = 32, feed tray 17, holdups 0.5 /
     0.25 / 1.0, dt = 2, 90 intervals, (x_1 - xbar)^2 + 0.1 (u - ubar)^2):
     warm re-solves of its closed loop with inputs resident on the device,
@@ -429,7 +429,9 @@ def paper_column_resolves(P, dev, resolves=40, warmup=3):
     import paper_2606_04725_gb300.inputs as I
     wl = I.WORKLOADS["paper_distillation_N32_T90"]
     N, Nf, T = wl["N"], wl["Nf"], wl["T"]
-    s = P.Solver(P.MODEL_DISTILLATION, [T], N=N, Nf=Nf, device=dev, **I.PAPER_COLUMN)
+    model = P.MODEL_DISTILLATION if model is None else model
+    cu = N if model == P.MODEL_DISTILLATION_DAE else 0  # u within a stage's control block
+    s = P.Solver(model, [T], N=N, Nf=Nf, device=dev, **I.PAPER_COLUMN)
     n = s.dims[0][0]
     sp = torch.full((T,), I.PAPER_XBAR, dtype=torch.float64, device=dev)
     y = torch.empty(n, dtype=torch.float64, device=dev)
@@ -441,7 +443,7 @@ def paper_column_resolves(P, dev, resolves=40, warmup=3):
     for q in range(warmup + resolves):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s.stream)
-        s.set_params(x0=y[N:2 * N], setpoint=sp, u_prev=y[2 * N:2 * N + 1])
+        s.set_params(x0=y[N:2 * N], setpoint=sp, u_prev=y[2 * N + cu:2 * N + cu + 1])
         inf = s.solve(warm=True)[0]
         s.get_solution(0, out=(y, None))
         e1.record(s.stream)
@@ -450,12 +452,70 @@ def paper_column_resolves(P, dev, resolves=40, warmup=3):
         if q >= warmup:
             ms.append(e0.elapsed_time(e1))
             iters.append(inf["iters"])
-    out = {"workload": "paper_distillation_N32_T90", "n": n, "resolves_per_s": len(ms) / (sum(ms) * 1e-3),
+    out = {"workload": "paper_distillation_N32_T90" + ("_dae" if cu else ""), "n": n, "resolves_per_s": len(ms) / (sum(ms) * 1e-3),
            "ms_per_resolve": sum(ms) / len(ms), "ms_per_ipm_iter": sum(ms) / max(1, sum(iters)),
            "ipm_iters_per_resolve": sum(iters) / len(iters), "cold_solve_iters": first["iters"],
            "statuses_ok": ok,
            "paper_gpu_ws_pu_s_per_step": {"value": 0.02, "hardware": "RTX 6000 Ada (MadNLP + cuDSS)",
                                           "note": "context only: other hardware and software"}}
+    s.close()
+    return out
+
+
+def paper_plate_resolves(P, dev, warmup=3):
+    """The paper's nonlinear heated plate (Sec. 4.2: 21 x 21 nodes, dt =
+    0.08, 12 intervals) over its 3.0 s closed loop (37 warm re-solves after
+    the cold one, the region setpoint stepping 58 / 55 / 63), each re-solve
+    timed with CUDA events on the library stream with its inputs on the
+    device; and one rebuild-every-solve re-solve (the paper's Base) for
+    comparison.  The paper's per-step figures are on other hardware (context)."""
+    import torch
+    import paper_2606_04725_gb300.inputs as I
+    wl = I.WORKLOADS["paper_plate_n21_T12"]
+    n, T, dt = wl["g"], wl["T"], wl["dt"]
+    nx = (n - 2) ** 2
+    s = P.Solver(P.MODEL_PAPER_PLATE, [T], g=n, device=dev)
+    nv = s.dims[0][0]
+    y = torch.empty(nv, dtype=torch.float64, device=dev)
+    u0 = torch.full((1,), 50.0, dtype=torch.float64, device=dev)
+    steps = int(round(wl["t_final"] / dt))
+    sps = torch.tensor(np.stack([I.paper_plate_setpoints(k * dt, T, dt) for k in range(steps + warmup + 1)]),
+                       dtype=torch.float64, device=dev)
+    s.set_params(x0=np.full(nx, 50.0), setpoint=I.paper_plate_setpoints(0.0, T, dt), u_prev=np.array([50.0]))
+    t0 = time.perf_counter()
+    first = s.solve(warm=False)[0]
+    cold_s = time.perf_counter() - t0
+    s.get_solution(0, out=(y, None))
+    ms, iters, ok = [], [], first["status"] == 0
+    for k in range(1, steps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.set_params(x0=y[nx:2 * nx], setpoint=sps[k], u_prev=u0)
+        inf = s.solve(warm=True)[0]
+        s.get_solution(0, out=(y, None))
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        ok = ok and inf["status"] == 0
+        ms.append(e0.elapsed_time(e1))
+        iters.append(inf["iters"])
+    yh = y.cpu().numpy()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    s2 = P.Solver(P.MODEL_PAPER_PLATE, [T], g=n, device=dev)
+    s2.set_params(x0=yh[nx:2 * nx].copy(), setpoint=I.paper_plate_setpoints(steps * dt, T, dt), u_prev=np.array([50.0]))
+    rb = s2.solve(warm=False)[0]
+    torch.cuda.synchronize()
+    rebuild_s = time.perf_counter() - t1
+    s2.close()
+    ph = s.time_phases(reps=5)
+    out = {"workload": "paper_plate_n21_T12", "n": nv, "resolves": len(ms),
+           "resolves_per_s": len(ms) / (sum(ms) * 1e-3), "ms_per_resolve": sum(ms) / len(ms),
+           "ms_per_ipm_iter": sum(ms) / max(1, sum(iters)), "ipm_iters_per_resolve": sum(iters) / len(iters),
+           "cold_solve_iters": first["iters"], "cold_solve_s": cold_s, "statuses_ok": ok and rb["status"] == 0,
+           "rebuild_cold_s_per_resolve": rebuild_s, "phases_ms": {k: ph[k] for k in ("ms_eval", "ms_assemble",
+                                                                                      "ms_factor", "ms_solve")},
+           "paper_gpu_s_per_step": {"ws_pu": 0.06, "base": 0.97, "hardware": "RTX 6000 Ada (MadNLP + cuDSS)",
+                                    "note": "context only: other hardware and software"}}
     s.close()
     return out
 
@@ -475,7 +535,8 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the single column, the full-size plate, the paper's column and the rebuild variants")
+                    help="skip the single column, the full-size plate, the paper's column and plate, and the "
+                         "rebuild variants")
     ap.add_argument("--schedule", default="",
                     help="fixed options instead of the autotuner's, e.g. ordering=2,nd_leaf=1,amalgamation=2,"
                          "panel_scale=3,factor_mode=3 (for profiling runs)")
@@ -685,6 +746,8 @@ def main():
         line["single_column"] = single_column(P, dev, rank=rank)
         line["plate_full_size"] = plate_factorization(P, dev, peak)
         line["paper_column"] = paper_column_resolves(P, dev)
+        line["paper_column_dae"] = paper_column_resolves(P, dev, model=P.MODEL_DISTILLATION_DAE)
+        line["paper_plate"] = paper_plate_resolves(P, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores, ncpu = host_cores()
         t_all, it_all, cold_all = oracle_batch_loop(hz, x0s, sps, N, Nf, 3, cores)

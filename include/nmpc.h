@@ -26,8 +26,10 @@
  *    with nmpc_bind.  The workspace must stay valid until nmpc_destroy.
  *  - Layout of one instance's primal vector y (stage-interleaved):
  *      y = [ x_0 | x_1 u_1 | ... | x_T u_T ],  n = nx + T (nx + nu)
- *    with nx states and nu controls per stage; rows of h are the initial
- *    condition x_0 - p_x0 = 0 followed by the T backward-Euler steps.
+ *    with nx states and nu controls per stage (for the DAE column the
+ *    "controls" are [y (N) u L V S]); rows of h are the initial condition
+ *    x_0 - p_x0 = 0 followed by the T backward-Euler steps, nr rows each
+ *    (nx, or 2N + 3 for the DAE column: its balances, then its algebraic rows).
  */
 #ifndef NMPC_H
 #define NMPC_H
@@ -56,7 +58,18 @@ typedef enum {
 typedef enum {
   NMPC_MODEL_DISTILLATION = 0, /* binary column of Sec. 4.1 (eq. distill-ocp) */
   NMPC_MODEL_PLATE = 1,        /* linear heated plate, boundary flux actuators */
-  NMPC_MODEL_TOY = 2           /* dy/dt = 4 sin u - y^3 of the paper's code listing */
+  NMPC_MODEL_TOY = 2,          /* dy/dt = 4 sin u - y^3 of the paper's code listing */
+  NMPC_MODEL_PAPER_PLATE = 3,  /* the paper's nonlinear heated plate (Sec. 4.2, eq. pde-ocp): n x n
+                                  nodes on [-1,1]^2 (n in g), the (n-2)^2 interior temperatures as
+                                  states, one control Q >= 50 that sets the Dirichlet data
+                                  4.1 Q^(1/3) at x1 = -1 and Q^(1/2) at x2 = -1 (T_b elsewhere),
+                                  heat loss, tracking of the region [-0.5,0.5]^2 to one setpoint
+                                  per stage, rho Q^2 */
+  NMPC_MODEL_DISTILLATION_DAE = 4 /* the column of eq. (distill-ocp) as printed, with its algebraic
+                                  variables: per stage [x (N) | y (N) u L V S], per step the N
+                                  balances, the N equilibria y = a x / (1 + (a-1) x) and
+                                  L = uD, V = L + D, S = L + F as rows; y in [0,1], L, V, S in
+                                  [0, 10]; the constants and cost of NMPC_MODEL_DISTILLATION */
 } nmpc_model;
 
 typedef enum {
@@ -86,6 +99,8 @@ typedef struct {
   double wu, ubar;       /* distillation: control-tracking stage cost wu dt (u_k - ubar)^2, the
                             0.1 (u - ubar)^2 integrand of eq. (distill-ocp), Sec. 4.1, by the
                             rectangle rule; wu = 0 (default) leaves it out */
+  double Tb, qloss;      /* paper's plate: fixed boundary temperature and heat loss (table
+                            pde-params: 50, 10); its alpha is kappa (230) and its rho rho_u (1e-8) */
 } nmpc_problem;
 
 /* Solver options.  Defaults from nmpc_options_defaults. */
@@ -199,10 +214,12 @@ nmpc_status nmpc_bind(nmpc_handle* h, void* workspace, size_t bytes);
  * NULL to keep that parameter.
  *   x0:       nx values per instance (initial state p_x0)
  *   setpoint: distillation/toy: T values per instance (setpoint of x_{k,1}
- *             resp. y_k, k = 1..T); plate: g*g target field per instance.
+ *             resp. y_k, k = 1..T); plate: g*g target field per instance;
+ *             paper's plate: T values (the region setpoint T_sp(t_k)).
  *             With instance = -1 and unequal horizons, instance i takes its
  *             own T_i values, one instance after another (sum of T_i)
- *   u_prev:   distillation: 1 value per instance (u_0 of the Delta-u term) */
+ *   u_prev:   distillation: 1 value per instance (u_0 of the Delta-u term);
+ *             paper's plate: the control Q of the cold start */
 nmpc_status nmpc_set_params(nmpc_handle* h, int instance, const double* x0, const double* setpoint,
                             const double* u_prev, int on_device);
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libnmpc.so")
 _lock = threading.Lock()
 _lib = None
 
-MODEL_DISTILLATION, MODEL_PLATE, MODEL_TOY = 0, 1, 2
+MODEL_DISTILLATION, MODEL_PLATE, MODEL_TOY, MODEL_PAPER_PLATE, MODEL_DISTILLATION_DAE = 0, 1, 2, 3, 4
 ORDER_AUTO, ORDER_NATURAL, ORDER_ND = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid", 2: "cuda_error", 3: "workspace", 10: "max_iter", 11: "linesearch_fail",
           12: "inertia_fail", 13: "nonfinite", 14: "timeout", 15: "not_solved"}
@@ -40,7 +40,7 @@ class Problem(C.Structure):
                 ("Ac", C.c_double), ("At", C.c_double), ("Ar", C.c_double), ("wdu", C.c_double),
                 ("kappa", C.c_double), ("cq", C.c_double), ("rho_u", C.c_double),
                 ("xlo", C.c_double), ("xhi", C.c_double), ("ulo", C.c_double), ("uhi", C.c_double),
-                ("wu", C.c_double), ("ubar", C.c_double)]
+                ("wu", C.c_double), ("ubar", C.c_double), ("Tb", C.c_double), ("qloss", C.c_double)]
 
 
 class Options(C.Structure):
@@ -305,7 +305,7 @@ class Solver(Structure):
             raise NmpcError(1, "instance out of range")
         cnt = self.n_instances if instance < 0 else 1
         model = self._p.model
-        nx = {0: self._p.N, 1: self._p.g * self._p.g, 2: 1}[model]
+        nx = {0: self._p.N, 1: self._p.g * self._p.g, 2: 1, 3: (self._p.g - 2) ** 2, 4: self._p.N}[model]
         if model == 1:
             sp_total = cnt * nx
         else:

@@ -90,6 +90,21 @@ __global__ void k_sens_out(Dev d, const double* v, const double* Drow, int inst,
       for (int k = 1; k <= T; ++k) a += vi[offx(k) + c];
       dsp[c] = 2.0 * mc.dt * hh * hh * a;
     }
+  } else if (mc.model == MODEL_PPLATE) {
+    // the setpoint of stage k enters the gradient of the region term:
+    // d(grad_{T_k,c} f)/d sp_k = -2 dt w_c
+    const int n = mc.g, mm = n - 2;
+    const double hh = 2.0 / (n - 1);
+    for (int k = 1 + tid; k <= T; k += nt) {
+      double a = 0.0;
+      for (int c = 0; c < nx; ++c) {
+        const int ci = c % mm + 1, cj = c / mm + 1;
+        const int ai = 2 * abs(2 * ci - (n - 1)), aj = 2 * abs(2 * cj - (n - 1));
+        if (ai > n - 1 || aj > n - 1) continue;
+        a += hh * hh * (ai == n - 1 ? 0.5 : 1.0) * (aj == n - 1 ? 0.5 : 1.0) * vi[offx(k) + c];
+      }
+      dsp[k - 1] = 2.0 * mc.dt * a;
+    }
   } else {
     for (int k = 1 + tid; k <= T; k += nt) dsp[k - 1] = 2.0 * mc.dt * vi[offx(k)];
   }

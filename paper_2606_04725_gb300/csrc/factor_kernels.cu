@@ -1176,19 +1176,20 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
 // front q's completion, flags[nf + 1] counts departed blocks, and the last
 // block to leave zeroes them all for the next launch.
 // Shared memory (doubles): the pivot columns (m x cp, cp = c rounded up to
-// PB), the update block as a packed lower triangle (mu (mu + 1) / 2), the L
-// buffers of two panels (m x PB each), cp pivot thresholds and cp reciprocal
-// pivots -- about half of a whole front, so that two blocks share an SM.
+// PB), the update block as a packed lower triangle (mu (mu + 1) / 2), L of
+// the update rows (mu x c), the L buffers of two panels (m x PB each), cp
+// pivot thresholds and cp reciprocal pivots -- about half of a whole front
+// more, so that two blocks share an SM.
 // ---------------------------------------------------------------------------
 // The update matrix of a front factored by factor_front_flow:
 // U = (children's part U0) - L21 D L21^T, all pivot columns at once, one
-// TR x TC output tile per thread.  L = W times the reciprocal pivot is formed
-// as the panels formed it, and the columns are applied in ascending order:
-// the same rounding as a panel-by-panel trailing update.  Fl: m x c pivot
-// columns (W, ld m); U0: packed lower triangle of the mu x mu update block;
-// Up: output (ld mu, lower triangle).
+// TR x TC output tile per thread, the columns applied in ascending order: the
+// same rounding as a panel-by-panel trailing update.  Fl: m x c pivot columns
+// (W, ld m); Lu: L of the update rows (mu x c, ld mu), W times the reciprocal
+// pivot as the panels formed it; U0: packed lower triangle of the mu x mu
+// update block; Up: output (ld mu, lower triangle).
 template <int TR, int TC>
-__device__ __forceinline__ void schur_tiles(const double* Fl, const double* U0, const double* invd, double* Up, int m,
+__device__ __forceinline__ void schur_tiles(const double* Fl, const double* Lu, const double* U0, double* Up, int m,
                                             int c) {
   const int mu = m - c, tid = threadIdx.x, nt = blockDim.x;
   auto upk = [&](int a, int b) { return (size_t)b * mu - (size_t)b * (b - 1) / 2 + (a - b); };
@@ -1212,11 +1213,11 @@ __device__ __forceinline__ void schur_tiles(const double* Fl, const double* U0, 
         acc[r][q] = (a < mu && b <= a) ? U0[upk(a, b)] : 0.0;
       }
     const double* col = Fl + c;
-    for (int j = 0; j < c; ++j, col += m) {
-      const double iv = invd[j];
+    const double* lcol = Lu;
+    for (int j = 0; j < c; ++j, col += m, lcol += mu) {
       double l[TR], wv[TC];
 #pragma unroll
-      for (int r = 0; r < TR; ++r) l[r] = (a0 + r < mu) ? col[a0 + r] * iv : 0.0;
+      for (int r = 0; r < TR; ++r) l[r] = (a0 + r < mu) ? lcol[a0 + r] : 0.0;
 #pragma unroll
       for (int q = 0; q < TC; ++q) wv[q] = (b0 + q < mu) ? col[b0 + q] : 0.0;
 #pragma unroll
@@ -1237,8 +1238,8 @@ __device__ __forceinline__ void schur_tiles(const double* Fl, const double* U0, 
 // The largest tiles that still give every thread of the block an output
 // tile (FP64 latency is hidden across warps, and larger tiles form fewer L
 // values per multiply-add).
-__device__ __noinline__ void schur_update(const double* Fl, const double* U0, const double* invd, double* Up, int m,
-                                          int c) {
+__device__ __noinline__ void schur_update(const double* Fl, double* Lu, const double* U0, const double* invd, double* Up,
+                                          int m, int c) {
   const int mu = m - c, nt = blockDim.x;
   auto tiles = [&](int tr, int tc) {  // tiles reaching the lower triangle
     const int nr = (mu + tr - 1) / tr, ncb = (mu + tc - 1) / tc;
@@ -1246,9 +1247,15 @@ __device__ __noinline__ void schur_update(const double* Fl, const double* U0, co
     for (int tb = 0; tb < ncb; ++tb) n += nr - max(0, (tc * tb) / tr);
     return n;
   };
-  if (tiles(4, 4) >= nt) schur_tiles<4, 4>(Fl, U0, invd, Up, m, c);
-  else if (tiles(2, 4) >= nt) schur_tiles<2, 4>(Fl, U0, invd, Up, m, c);
-  else schur_tiles<2, 2>(Fl, U0, invd, Up, m, c);
+  // L of the update rows, once: Lu(a, j) = W(c + a, j) / d_j
+  for (int t = threadIdx.x; t < mu * c; t += nt) {
+    const int j = t / mu, a = t - j * mu;
+    Lu[t] = Fl[(c + a) + (size_t)j * m] * invd[j];
+  }
+  __syncthreads();
+  if (tiles(4, 4) >= nt) schur_tiles<4, 4>(Fl, Lu, U0, Up, m, c);
+  else if (tiles(2, 4) >= nt) schur_tiles<2, 4>(Fl, Lu, U0, Up, m, c);
+  else schur_tiles<2, 2>(Fl, Lu, U0, Up, m, c);
 }
 
 __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd, const int* flags, int nf,
@@ -1261,7 +1268,8 @@ __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd,
   const int cp = (c + PB - 1) / PB * PB, npan = cp / PB;
   double* Fl = dsm;                                  // m x cp, ld m: the pivot columns (W once factored)
   double* U0 = Fl + (size_t)m * cp;                  // mu (mu + 1) / 2: update block, packed lower triangle
-  double* Lb = U0 + (size_t)mu * (mu + 1) / 2;       // 2 x (m x PB): L of the even / odd panels
+  double* Lu = U0 + (size_t)mu * (mu + 1) / 2;       // mu x c: L of the update rows (phase 2)
+  double* Lb = Lu + (size_t)mu * c;                  // 2 x (m x PB): L of the even / odd panels
   double* thr = Lb + 2 * (size_t)m * PB;             // cp
   double* invd = thr + cp;                           // cp
   auto bL = [&](int q) { return Lb + (size_t)(q & 1) * m * PB; };
@@ -1342,7 +1350,7 @@ __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd,
   }
   // ---- phase 2: the update matrix U = (children's part) - L21 D L21^T for
   // the parent (schur_update)
-  schur_update(Fl, U0, invd, Up, m, c);
+  schur_update(Fl, Lu, U0, invd, Up, m, c);
 }
 
 __global__ void __launch_bounds__(FCT, 2) k_factor_flow(Dev d, SnDev s, const FrontDesc* dl, int nf, int* flags) {

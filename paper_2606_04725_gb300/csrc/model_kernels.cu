@@ -87,6 +87,31 @@ __device__ __forceinline__ int plate_seg_of(const ModelConst& mc, int ci, int cj
   return k;
 }
 
+// ------------------------------------------------------- the paper's plate
+// Sec. 4.2, eq. (pde-ocp): n x n nodes on [-1, 1]^2 (n = mc.g, h = 2/(n-1)),
+// interior node q = cj m + ci (m = n - 2) at x1 = -1 + (ci + 1) h,
+// x2 = -1 + (cj + 1) h.  Boundary data: 4.1 Q^(1/3) at x1 = -1, Q^(1/2) at
+// x2 = -1, T_b at x1 = 1 and x2 = 1; dT/dt = alpha (Laplacian - 5 q_loss^2).
+
+// The step rows x_{k+1} - x_k - dt f are divided by their diagonal coefficient
+// 1 + 4 dt alpha / h^2 (7361 at n = 21), so that every row has a unit
+// diagonal as the other models' rows do.
+__device__ __forceinline__ double pplate_row_scale(const ModelConst& mc) {
+  const double hh = 2.0 / (mc.g - 1);
+  return 1.0 / (1.0 + 4.0 * mc.dt * mc.kappa / (hh * hh));
+}
+
+// Trapezoidal weight of node q in the tracking integral over [-0.5, 0.5]^2
+// (h^2 inside, halved on each edge of the region, 0 outside).
+__device__ __forceinline__ double pplate_weight(const ModelConst& mc, int q) {
+  const int n = mc.g, mm = n - 2;
+  const int i = q % mm + 1, j = q / mm + 1;
+  const int ai = 2 * abs(2 * i - (n - 1)), aj = 2 * abs(2 * j - (n - 1));
+  if (ai > n - 1 || aj > n - 1) return 0.0;
+  const double hh = 2.0 / (n - 1);
+  return hh * hh * (ai == n - 1 ? 0.5 : 1.0) * (aj == n - 1 ? 0.5 : 1.0);
+}
+
 // ------------------------------------------------------------------ rows
 
 // h and H for every row (at iterate y, or at the trial point when only the
@@ -107,12 +132,59 @@ __device__ void eval_row(const Dev& d, const double* y, int r, double* hout, dou
     }
     return;
   }
-  const int k = lr / nx - 1, q = lr % nx;
+  const int k = (lr - nx) / mc.nr, q = (lr - nx) % mc.nr;  // row q of step k -> k+1
   const double* xk = yi + offx(mc, k);
   const double* xn = yi + offx(mc, k + 1);
   const double* un = yi + offu(mc, k + 1);
   const double dt = mc.dt;
-  if (mc.model == MODEL_DISTILL) {
+  if (mc.model == MODEL_DDAE) {
+    double* H = Hv ? Hv + (size_t)r * WH : nullptr;
+    const int N = mc.N, Nf = mc.Nf;
+    const double* yn = un;  // y_{k+1}
+    const double L = un[N + 1], V = un[N + 2], S = un[N + 3];
+    if (q < N) {  // balance of tray i
+      const int i = q + 1;
+      double f, d1 = 0, d2, d3 = 0, d4 = 0, dL = 0, dV, dS = 0;  // d/d x_{i-1}, x_i, y_i, y_{i+1}, L, V, S
+      if (i == 1) {
+        const double ic = mc.inv_Ac;
+        f = V * (yn[1] - xn[0]) * ic;
+        d2 = -V * ic; d4 = V * ic; dV = (yn[1] - xn[0]) * ic;
+      } else if (i == N) {
+        const double ir = mc.inv_Ar;
+        f = (S * xn[N - 2] - (mc.F - mc.D) * xn[N - 1] - V * yn[N - 1]) * ir;
+        d1 = S * ir; d2 = -(mc.F - mc.D) * ir; d3 = -V * ir; dV = -yn[N - 1] * ir; dS = xn[N - 2] * ir;
+      } else {
+        const double it = mc.inv_At;
+        const double lin = (i <= Nf) ? L : S, lout = (i < Nf) ? L : S;
+        const double feed = (i == Nf) ? mc.F * mc.xF : 0.0;
+        f = (feed + lin * xn[i - 2] - lout * xn[i - 1] - V * (yn[i - 1] - yn[i])) * it;
+        d1 = lin * it; d2 = -lout * it; d3 = -V * it; d4 = V * it; dV = -(yn[i - 1] - yn[i]) * it;
+        if (i < Nf) dL = (xn[i - 2] - xn[i - 1]) * it;
+        else if (i == Nf) { dL = xn[i - 2] * it; dS = -xn[i - 1] * it; }
+        else dS = (xn[i - 2] - xn[i - 1]) * it;
+      }
+      hout[r] = xn[q] - xk[q] - dt * f;
+      if (H) {
+        H[0] = -1.0; H[1] = -dt * d1; H[2] = 1.0 - dt * d2; H[3] = -dt * d3; H[4] = -dt * d4;
+        H[5] = -dt * dL; H[6] = -dt * dV; H[7] = -dt * dS;
+      }
+    } else if (q < 2 * N) {  // equilibrium y_i - a x_i / (1 + (a - 1) x_i)
+      const int i = q - N;
+      const Vle v = vle_all(mc.alpha, xn[i]);
+      hout[r] = yn[i] - v.y;
+      if (H) {
+        H[0] = -v.d1; H[1] = 1.0;
+        for (int t = 2; t < WH; ++t) H[t] = 0.0;
+      }
+    } else {  // flows: L - u D, V - L - D, S - L - F
+      const int e = q - 2 * N;
+      hout[r] = (e == 0) ? L - un[N] * mc.D : (e == 1) ? V - L - mc.D : S - L - mc.F;
+      if (H) {
+        H[0] = (e == 0) ? -mc.D : -1.0; H[1] = 1.0;
+        for (int t = 2; t < WH; ++t) H[t] = 0.0;
+      }
+    }
+  } else if (mc.model == MODEL_DISTILL) {
     TrayEval e = tray_eval(mc, xn, un[0], q + 1);
     hout[r] = xn[q] - xk[q] - dt * e.f;
     if (Hv) {
@@ -148,6 +220,37 @@ __device__ void eval_row(const Dev& d, const double* y, int r, double* hout, dou
       H[5] = (cj < g - 1) ? -dt * c : 0.0;
       H[6] = (nsg > 0) ? -dt * mc.cq / hh : 0.0;
       H[7] = (nsg > 1) ? -dt * mc.cq / hh : 0.0;
+    }
+  } else if (mc.model == MODEL_PPLATE) {
+    const int mm = mc.g - 2, ci = q % mm, cj = q / mm;
+    const double hh = 2.0 / (mc.g - 1), c = mc.kappa / (hh * hh);
+    const double Q = un[0];
+    double sum = -4.0 * xn[q], dq = 0.0;
+    if (ci > 0) sum += xn[q - 1];
+    else {
+      const double cb = cbrt(Q);
+      sum += 4.1 * cb;
+      dq += 4.1 / 3.0 / (cb * cb);  // d/dQ 4.1 Q^(1/3)
+    }
+    sum += (ci < mm - 1) ? xn[q + 1] : mc.Tb;
+    if (cj > 0) sum += xn[q - mm];
+    else {
+      const double sq = sqrt(Q);
+      sum += sq;
+      dq += 0.5 / sq;  // d/dQ Q^(1/2)
+    }
+    sum += (cj < mm - 1) ? xn[q + mm] : mc.Tb;
+    const double s = pplate_row_scale(mc);
+    hout[r] = (xn[q] - xk[q] - dt * mc.kappa * (sum / (hh * hh) - 5.0 * mc.qloss * mc.qloss)) * s;
+    if (Hv) {
+      double* H = Hv + (size_t)r * WH;
+      H[0] = -1.0 * s;
+      H[1] = (cj > 0) ? -dt * c * s : 0.0;
+      H[2] = (ci > 0) ? -dt * c * s : 0.0;
+      H[3] = (1.0 + 4.0 * dt * c) * s;
+      H[4] = (ci < mm - 1) ? -dt * c * s : 0.0;
+      H[5] = (cj < mm - 1) ? -dt * c * s : 0.0;
+      H[6] = -dt * c * dq * s;  // 0 away from the controlled sides
     }
   } else {
     const double yn = xn[0], u = un[0];
@@ -199,17 +302,18 @@ __device__ void eval_var_obj(const Dev& d, const double* y, int v, double* fshar
     const int q = (lv - nx) % (nx + nu);
     const double* yi = y + vo;
     const double dt = mc.dt;
-    if (mc.model == MODEL_DISTILL) {
+    if (mc.model == MODEL_DISTILL || mc.model == MODEL_DDAE) {
+      const int cu = (mc.model == MODEL_DDAE) ? mc.N : 0;  // u within the control block
       if (q == 0) {
         const double e = yi[lv] - d.p_sp[(size_t)i * d.sp_stride + k - 1];
         f = dt * e * e;
         gr = 2.0 * dt * e;
-      } else if (q == nx) {
-        const double up = (k == 1) ? d.p_uprev[i] : yi[offu(mc, k - 1)];
+      } else if (q == nx + cu) {
+        const double up = (k == 1) ? d.p_uprev[i] : yi[offu(mc, k - 1) + cu];
         const double du = yi[lv] - up, eu = yi[lv] - mc.ubar;
         f = mc.wdu * du * du + mc.wu * dt * eu * eu;
         gr = 2.0 * mc.wdu * du + 2.0 * mc.wu * dt * eu;
-        if (k < T) gr -= 2.0 * mc.wdu * (yi[offu(mc, k + 1)] - yi[lv]);
+        if (k < T) gr -= 2.0 * mc.wdu * (yi[offu(mc, k + 1) + cu] - yi[lv]);
       }
     } else if (mc.model == MODEL_PLATE) {
       const double hh = 1.0 / mc.g;
@@ -217,6 +321,16 @@ __device__ void eval_var_obj(const Dev& d, const double* y, int v, double* fshar
         const double e = yi[lv] - d.p_sp[(size_t)i * d.sp_stride + q];
         f = dt * hh * hh * e * e;
         gr = 2.0 * dt * hh * hh * e;
+      } else {
+        f = mc.rho_u * dt * yi[lv] * yi[lv];
+        gr = 2.0 * mc.rho_u * dt * yi[lv];
+      }
+    } else if (mc.model == MODEL_PPLATE) {
+      if (q < nx) {
+        const double w = pplate_weight(mc, q);
+        const double e = yi[lv] - d.p_sp[(size_t)i * d.sp_stride + k - 1];
+        f = dt * w * e * e;
+        gr = 2.0 * dt * w * e;
       } else {
         f = mc.rho_u * dt * yi[lv] * yi[lv];
         gr = 2.0 * mc.rho_u * dt * yi[lv];
@@ -246,11 +360,62 @@ __device__ void eval_var_hess(const Dev& d, int v) {
   const int q = (lv - nx) % (nx + nu);
   double* W = d.Wv + d.inst_woff[i] + (size_t)(k - 1) * mc.WS;
   const double* yi = d.y + vo;
-  const int rbase = ro + nx * k;  // rows of step k-1 -> k
+  const int rbase = ro + nx + mc.nr * (k - 1);  // rows of step k-1 -> k
   const double dt = mc.dt;
   if (mc.model == MODEL_PLATE) {
     const double hh = 1.0 / mc.g;
     W[q] = (q < nx) ? 2.0 * dt * hh * hh : 2.0 * mc.rho_u * dt;
+    return;
+  }
+  if (mc.model == MODEL_DDAE) {
+    // W slots of stage k (see the slot conventions): the balances are
+    // bilinear in (flow, composition), the equilibria carry -vle(x_j)
+    const int N = mc.N, Nf = mc.Nf;
+    auto c = [&](int tray) { const int rr = rbase + tray - 1; return -dt * (d.wp[rr] - d.wm[rr]); };
+    auto mu = [&](int j) { const int rr = rbase + N + j - 1; return d.wp[rr] - d.wm[rr]; };
+    if (q < N) {  // x_j: its diagonal and its (flow, x_j) pair
+      const int j = q + 1;
+      const Vle v = vle_all(mc.alpha, yi[lv]);
+      W[q] = (j == 1 ? 2.0 * dt : 0.0) - mu(j) * v.d2;
+      if (j <= N - 1) {
+        // x_j enters the tray below (x_{(j+1)-1}, inflow) and its own tray (outflow)
+        double w = c(j + 1) * (j + 1 == N ? mc.inv_Ar : mc.inv_At);
+        if (j >= 2) w -= c(j) * mc.inv_At;
+        W[N + j - 1] = w;
+      }
+    } else if (q < 2 * N) {  // y_j, j >= 2: (V, y_j) from tray j-1 (y_{(j-1)+1}) and tray j (own)
+      const int j = q - N + 1;
+      if (j >= 2) {
+        double w = c(j - 1) * (j - 1 == 1 ? mc.inv_Ac : mc.inv_At);
+        w -= c(j) * (j == N ? mc.inv_Ar : mc.inv_At);
+        W[2 * N + j - 2] = w;
+      }
+    } else if (q == 2 * N) {  // u: diagonal and (u_k, u_{k-1})
+      W[3 * N - 1] = 2.0 * mc.wdu * (k < T ? 2.0 : 1.0) + 2.0 * mc.wu * dt;
+      W[3 * N] = (k >= 2) ? -2.0 * mc.wdu : 0.0;
+    } else if (q == 2 * N + 2) {  // V: (V, x_1) from the condenser
+      W[2 * N - 1] = -c(1) * mc.inv_Ac;
+    }
+    return;
+  }
+  if (mc.model == MODEL_PPLATE) {
+    if (q < nx) {
+      W[q] = 2.0 * dt * pplate_weight(mc, q);
+      return;
+    }
+    // the boundary data's curvature in Q, weighted by the multipliers of the
+    // rows next to the controlled sides (the scaled constraint carries -s dt f):
+    // d2/dQ2 4.1 Q^(1/3) = -(8.2/9) Q^(-5/3), d2/dQ2 Q^(1/2) = -Q^(-3/2) / 4
+    const int mm = mc.g - 2;
+    const double hh = 2.0 / (mc.g - 1), c = mc.kappa / (hh * hh);
+    double sl = 0.0, sb = 0.0;
+    for (int t = 0; t < mm; ++t) {
+      sl += d.wp[rbase + t * mm] - d.wm[rbase + t * mm];  // x1 = -1 side: nodes (0, t)
+      sb += d.wp[rbase + t] - d.wm[rbase + t];            // x2 = -1 side: nodes (t, 0)
+    }
+    const double Q = yi[lv], cb = cbrt(Q), sq = sqrt(Q);
+    const double d2l = -(8.2 / 9.0) / (Q * cb * cb), d2b = -0.25 / (Q * sq);
+    W[nx] = 2.0 * mc.rho_u * dt - pplate_row_scale(mc) * dt * c * (sl * d2l + sb * d2b);
     return;
   }
   if (mc.model == MODEL_TOY) {
@@ -376,6 +541,7 @@ __global__ void k_shift_params(Dev d) {
     const double* yi = d.y + d.inst_voff[i];
     if (q < nx) d.p_x0[(size_t)i * nx + q] = yi[nx + q];
     else if (d.mc.model == MODEL_DISTILL) d.p_uprev[i] = yi[2 * nx];
+    else if (d.mc.model == MODEL_DDAE) d.p_uprev[i] = yi[2 * nx + d.mc.N];
   }
 }
 
@@ -396,7 +562,18 @@ __global__ void k_init_vars(Dev d, int warm, double push) {
     else {
       const int q = (lv - nx) % (nx + nu);
       if (q < nx) y = d.p_x0[(size_t)i * nx + q];
-      else if (mc.model == MODEL_DISTILL) y = d.p_uprev[i];
+      else if (mc.model == MODEL_DISTILL || mc.model == MODEL_PPLATE) y = d.p_uprev[i];
+      else if (mc.model == MODEL_DDAE) {
+        // the algebraic variables consistent with x0 and u_prev
+        const int cq = q - nx, N = mc.N;
+        const double u = d.p_uprev[i];
+        if (cq < N) {
+          const double x = d.p_x0[(size_t)i * nx + cq];
+          y = mc.alpha * x / (1.0 + (mc.alpha - 1.0) * x);
+        } else {
+          y = (cq == N) ? u : (cq == N + 1) ? u * mc.D : (cq == N + 2) ? u * mc.D + mc.D : u * mc.D + mc.F;
+        }
+      }
       else y = (isfinite(lo) && isfinite(hi)) ? 0.5 * (lo + hi) : 0.0;
     }
   }

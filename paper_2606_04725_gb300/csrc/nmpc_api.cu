@@ -106,10 +106,11 @@ constexpr int CLUSTER_PB = 8;         // column block of the cluster kernel (PB 
 constexpr int FLOW_SMEM_CAP_BYTES = 220 * 1024;  // dynamic shared memory of a k_factor_flow block
 // shared memory (doubles) of k_factor_flow for a front of m rows and c pivot
 // columns: the pivot columns rounded up to whole panels, the packed update
-// block, two L panel buffers, thresholds and reciprocal pivots
+// block, L of the update rows, two L panel buffers, thresholds and
+// reciprocal pivots
 long long flow_need(long long m, long long c) {
   const long long cp = (c + CLUSTER_PB - 1) / CLUSTER_PB * CLUSTER_PB, mu = m - c;
-  return m * cp + mu * (mu + 1) / 2 + 2 * m * CLUSTER_PB + 2 * cp;
+  return m * cp + mu * (mu + 1) / 2 + mu * c + 2 * m * CLUSTER_PB + 2 * cp;
 }
 constexpr int SENS_REFINE = 6;        // refinement sweeps of the adjoint solve
 
@@ -662,8 +663,14 @@ void nmpc_problem_defaults(int model, nmpc_problem* p) {
   p->dt = 1.0;
   p->alpha = 1.6; p->D = 0.2; p->F = 0.4; p->xF = 0.5; p->Ac = 1.0; p->At = 1.0; p->Ar = 1.0; p->wdu = 0.01;
   p->kappa = 0.01; p->cq = 0.01; p->rho_u = 1e-3;
-  if (model == NMPC_MODEL_DISTILLATION) { p->N = 12; p->Nf = 5; p->xlo = 0; p->xhi = 1; p->ulo = 1; p->uhi = 5; }
+  if (model == NMPC_MODEL_DISTILLATION || model == NMPC_MODEL_DISTILLATION_DAE) {
+    p->N = 12; p->Nf = 5; p->xlo = 0; p->xhi = 1; p->ulo = 1; p->uhi = 5;
+  }
   else if (model == NMPC_MODEL_PLATE) { p->g = 64; p->S = 8; p->xlo = -INFINITY; p->xhi = 1.2; p->ulo = 0; p->uhi = 1; }
+  else if (model == NMPC_MODEL_PAPER_PLATE) {  // table pde-params, Sec. 4.2
+    p->g = 21; p->S = 1; p->dt = 0.08; p->kappa = 230.0; p->rho_u = 1e-8; p->Tb = 50.0; p->qloss = 10.0;
+    p->xlo = -INFINITY; p->xhi = INFINITY; p->ulo = 50.0; p->uhi = INFINITY;
+  }
   else { p->xlo = 0; p->xhi = INFINITY; p->ulo = 1; p->uhi = 3; }
 }
 
@@ -692,6 +699,7 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   sp.kappa = prob->kappa; sp.cq = prob->cq; sp.rho_u = prob->rho_u;
   sp.xlo = prob->xlo; sp.xhi = prob->xhi; sp.ulo = prob->ulo; sp.uhi = prob->uhi;
   sp.wu = prob->wu; sp.ubar = prob->ubar;
+  sp.Tb = prob->Tb; sp.qloss = prob->qloss;
   sp.gamma = h->opt.gamma; sp.tol = h->opt.tol;
   sp.ordering = h->opt.ordering; sp.nd_leaf = h->opt.nd_leaf; sp.pivtol = h->opt.pivtol;
   sp.dw_max = h->opt.dw_max;
@@ -926,7 +934,7 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   CUDA_TRY(h, up(d.inst_T, A.inst_T, st)); CUDA_TRY(h, up(d.inst_voff, A.inst_voff, st));
   {
     std::vector<int> spoff(A.n_inst + 1, 0);
-    for (int i = 0; i < A.n_inst; ++i) spoff[i + 1] = spoff[i] + (A.mc.model == MODEL_PLATE ? A.mc.nx : A.inst_T[i]);
+    for (int i = 0; i < A.n_inst; ++i) spoff[i + 1] = spoff[i] + (A.mc.model == MODEL_PLATE ? A.mc.nx : A.inst_T[i]);  // per stage otherwise
     h->sp_packed = spoff[A.n_inst];
     CUDA_TRY(h, cudaMemcpyAsync(h->d_inst_spoff, spoff.data(), spoff.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     CUDA_TRY(h, cudaStreamSynchronize(st));  // spoff is a local

@@ -5,6 +5,13 @@
 //     distillation (WH=5): [x_k,i | x_{k+1},i-1 | x_{k+1},i | x_{k+1},i+1 | u_{k+1}]
 //     plate        (WH=8): [x_k,c | x_{k+1},c-g | c-1 | c | c+1 | c+g | v_a | v_b]
 //     toy          (WH=3): [y_k | y_{k+1} | u_{k+1}]
+//     paper plate  (WH=7): [T_k,c | T_{k+1},c-m | c-1 | c | c+1 | c+m | Q_{k+1}] (m = g - 2
+//                          interior nodes per row; the Q slot only next to x1 = -1 or x2 = -1)
+//     DAE column   (WH=8): balance of tray i [x_k,i | x_{k+1},i-1 | x_{k+1},i | y_{k+1},i |
+//                          y_{k+1},i+1 | L | V | S]; equilibrium i [x_{k+1},i | y_{k+1},i];
+//                          L - uD [u | L]; V - L - D [L | V]; S - L - F [L | S]
+//   Rows per step: nr = nx, except the DAE column (2N + 3: N balances, N equilibria,
+//   3 flow equations); the rows of step k start at nx + nr k.
 //   Initial-condition rows use slot 0 only (coefficient 1).  Unused slots
 //   carry column -1 and value 0.
 //   W (Hessian of the Lagrangian, lower triangle) is stored per stage
@@ -12,12 +19,15 @@
 //     distillation (WS=2N+2): [x_k,i diag (N) | (u_k, x_k,i) (N) | u_k diag | (u_k, u_{k-1})]
 //     plate        (WS=g*g+S): [x_k,c diag | v_k,s diag]
 //     toy          (WS=2): [y_k diag | u_k diag]
+//     paper plate  (WS=(g-2)^2+1): [T_k,c diag | Q_k diag]
+//     DAE column   (WS=3N+1): [x_j diag (N) | (L or S, x_j), j < N (N-1: L above the feed,
+//                  S from it down) | (V, x_1) | (V, y_j), j >= 2 (N-1) | u diag | (u_k, u_{k-1})]
 #pragma once
 #include <cstdint>
 
 namespace nmpc {
 
-enum Model { MODEL_DISTILL = 0, MODEL_PLATE = 1, MODEL_TOY = 2 };
+enum Model { MODEL_DISTILL = 0, MODEL_PLATE = 1, MODEL_TOY = 2, MODEL_PPLATE = 3, MODEL_DDAE = 4 };
 
 // Per-instance control state of the interior-point method (device resident).
 // One record per instance; the control kernels run one thread per instance.
@@ -55,12 +65,14 @@ constexpr double KAPPA_W_MINUS = 1.0 / 3.0, KAPPA_W_PLUS = 8.0, KAPPA_W_PLUS_BAR
 
 struct ModelConst {
   int model, nx, nu, N, Nf, g, S, WH, WS;
+  int nr;                             // rows per backward-Euler step: nx, or 2N + 3 for the DAE column
   double dt, alpha, D, F, xF, Ac, At, Ar, wdu, kappa, cq, rho_u;
   double xlo, xhi, ulo, uhi;
   double wu, ubar;                    // control-tracking cost wu dt (u - ubar)^2 (distillation)
   double inv_Ac, inv_At, inv_Ar;      // 1/holdups (distillation), computed once on the host
   double gamma, tol, pivtol;
   double dw_max;                      // largest delta_w of the inertia correction
+  double Tb, qloss;                   // paper's plate: boundary temperature, heat loss
 };
 
 // Reduction chunks never straddle an instance.  kind 0: variables, 1: rows.

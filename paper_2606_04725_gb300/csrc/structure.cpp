@@ -21,11 +21,12 @@ namespace nmpc {
 namespace {
 
 struct Layout {
-  int nx, nu, T;
+  int nx, nu, T, nr;  // nr: rows per backward-Euler step (nx, or 2N + 3 for the DAE column)
   int offx(int k) const { return k == 0 ? 0 : nx + (k - 1) * (nx + nu); }
   int offu(int k) const { return offx(k) + nx; }
   int n() const { return nx + T * (nx + nu); }
-  int m() const { return nx * (T + 1); }
+  int m() const { return nx + T * nr; }
+  int row(int k, int q) const { return nx + nr * k + q; }  // row q of step k -> k+1
 };
 
 // Plate: actuator segments adjacent to cell (ci, cj).  Each of the four sides
@@ -358,6 +359,12 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       mc.nx = sp.g * sp.g; mc.nu = sp.S; mc.WH = 8; mc.WS = sp.g * sp.g + sp.S;
     } else if (sp.model == MODEL_TOY) {
       mc.nx = 1; mc.nu = 1; mc.WH = 3; mc.WS = 2;
+    } else if (sp.model == MODEL_PPLATE) {
+      if (sp.g < 4) return "the paper's plate needs g >= 4 grid points per side";
+      mc.nx = (sp.g - 2) * (sp.g - 2); mc.nu = 1; mc.WH = 7; mc.WS = mc.nx + 1;
+    } else if (sp.model == MODEL_DDAE) {
+      if (sp.N < 3 || sp.Nf < 2 || sp.Nf > sp.N - 1) return "distillation needs N >= 3 and 2 <= Nf <= N-1";
+      mc.nx = sp.N; mc.nu = sp.N + 4; mc.WH = 8; mc.WS = 3 * sp.N + 1;
     } else {
       return "unknown model";
     }
@@ -369,6 +376,8 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
     mc.wu = sp.wu; mc.ubar = sp.ubar;
     mc.inv_Ac = 1.0 / sp.Ac; mc.inv_At = 1.0 / sp.At; mc.inv_Ar = 1.0 / sp.Ar;
     mc.gamma = sp.gamma; mc.tol = sp.tol; mc.pivtol = sp.pivtol; mc.dw_max = sp.dw_max;
+    mc.Tb = sp.Tb; mc.qloss = sp.qloss;
+    mc.nr = (sp.model == MODEL_DDAE) ? 2 * sp.N + 3 : mc.nx;
     const int nx = mc.nx, nu = mc.nu, WH = mc.WH, WS = mc.WS;
     A.n_inst = ni;
     A.sp_stride = (sp.model == MODEL_PLATE) ? nx : *std::max_element(sp.T.begin(), sp.T.end());
@@ -378,7 +387,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
     long long n = 0, m = 0, nW = 0;
     for (int i = 0; i < ni; ++i) {
       if (sp.T[i] < 1) return "horizons must be >= 1";
-      Layout L{nx, nu, sp.T[i]};
+      Layout L{nx, nu, sp.T[i], mc.nr};
       A.inst_voff[i] = (int)n; A.inst_roff[i] = (int)m; A.inst_woff[i] = (int)nW;
       A.inst_n[i] = L.n(); A.inst_m[i] = L.m();
       n += L.n(); m += L.m(); nW += (long long)sp.T[i] * WS;
@@ -393,7 +402,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
 
     std::vector<InstSym> syms(ni);
     for (int i = 0; i < ni; ++i) {
-      Layout L{nx, nu, sp.T[i]};
+      Layout L{nx, nu, sp.T[i], mc.nr};
       const int vo = A.inst_voff[i], ro = A.inst_roff[i], wo = A.inst_woff[i];
       const int nl = L.n(), ml = L.m();
       for (int v = 0; v < nl; ++v) A.var_inst[vo + v] = i;
@@ -404,6 +413,10 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       for (int k = 1; k <= L.T; ++k) {
         for (int q = 0; q < nx; ++q) { A.yL[vo + L.offx(k) + q] = sp.xlo; A.yU[vo + L.offx(k) + q] = sp.xhi; }
         for (int q = 0; q < nu; ++q) { A.yL[vo + L.offu(k) + q] = sp.ulo; A.yU[vo + L.offu(k) + q] = sp.uhi; }
+        if (sp.model == MODEL_DDAE) {  // y in [0, 1], u as given, L, V, S in [0, 10] (eq. distill-ocp)
+          for (int q = 0; q < nx; ++q) { A.yL[vo + L.offu(k) + q] = 0.0; A.yU[vo + L.offu(k) + q] = 1.0; }
+          for (int q = nx + 1; q < nu; ++q) { A.yL[vo + L.offu(k) + q] = 0.0; A.yU[vo + L.offu(k) + q] = 10.0; }
+        }
       }
       for (int v = 0; v < nl; ++v) nz += std::isfinite(A.yL[vo + v]) + std::isfinite(A.yU[vo + v]);
       A.inst_nz[i] = nz;
@@ -411,8 +424,34 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       auto hc = [&](int r, int s) -> int& { return A.Hcol[(size_t)(ro + r) * WH + s]; };
       for (int q = 0; q < nx; ++q) hc(q, 0) = q;
       for (int k = 0; k < L.T; ++k) {
+        if (sp.model == MODEL_DDAE) {
+          // balance of tray i: [x_k,i | x_{k+1},i-1 | x_{k+1},i | y_{k+1},i | y_{k+1},i+1 | L | V | S]
+          const int N = sp.N, Nf = sp.Nf, bx = L.offx(k + 1), bu = L.offu(k + 1);
+          for (int i = 1; i <= N; ++i) {
+            const int r = L.row(k, i - 1);
+            hc(r, 0) = L.offx(k) + i - 1;
+            if (i >= 2) hc(r, 1) = bx + i - 2;
+            hc(r, 2) = bx + i - 1;
+            if (i >= 2) hc(r, 3) = bu + i - 1;
+            if (i <= N - 1) hc(r, 4) = bu + i;
+            if (i >= 2 && i <= Nf) hc(r, 5) = bu + N + 1;
+            hc(r, 6) = bu + N + 2;
+            if (i >= Nf) hc(r, 7) = bu + N + 3;
+          }
+          for (int i = 0; i < N; ++i) {  // equilibrium: [x_{k+1},i | y_{k+1},i]
+            hc(L.row(k, N + i), 0) = bx + i;
+            hc(L.row(k, N + i), 1) = bu + i;
+          }
+          hc(L.row(k, 2 * N), 0) = bu + N;          // L - u D: [u | L]
+          hc(L.row(k, 2 * N), 1) = bu + N + 1;
+          hc(L.row(k, 2 * N + 1), 0) = bu + N + 1;  // V - L - D: [L | V]
+          hc(L.row(k, 2 * N + 1), 1) = bu + N + 2;
+          hc(L.row(k, 2 * N + 2), 0) = bu + N + 1;  // S - L - F: [L | S]
+          hc(L.row(k, 2 * N + 2), 1) = bu + N + 3;
+          continue;
+        }
         for (int q = 0; q < nx; ++q) {
-          const int r = nx * (k + 1) + q;
+          const int r = L.row(k, q);
           hc(r, 0) = L.offx(k) + q;
           if (sp.model == MODEL_DISTILL) {
             if (q > 0) hc(r, 1) = L.offx(k + 1) + q - 1;
@@ -429,6 +468,14 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
             int segs[2];
             int ns = plate_segments(g, sp.S, ci, cj, segs);
             for (int t = 0; t < ns; ++t) hc(r, 6 + t) = L.offu(k + 1) + segs[t];
+          } else if (sp.model == MODEL_PPLATE) {
+            const int mm = sp.g - 2, ci = q % mm, cj = q / mm, b = L.offx(k + 1);
+            if (cj > 0) hc(r, 1) = b + q - mm;
+            if (ci > 0) hc(r, 2) = b + q - 1;
+            hc(r, 3) = b + q;
+            if (ci < mm - 1) hc(r, 4) = b + q + 1;
+            if (cj < mm - 1) hc(r, 5) = b + q + mm;
+            if (ci == 0 || cj == 0) hc(r, 6) = L.offu(k + 1);
           } else {
             hc(r, 1) = L.offx(k + 1);
             hc(r, 2) = L.offu(k + 1);
@@ -443,7 +490,16 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
           for (int q = 0; q < nx; ++q) { ws(q, L.offx(k) + q, L.offx(k) + q); ws(nx + q, L.offu(k), L.offx(k) + q); }
           ws(2 * nx, L.offu(k), L.offu(k));
           if (k >= 2) ws(2 * nx + 1, L.offu(k), L.offu(k - 1));
-        } else if (sp.model == MODEL_PLATE) {
+        } else if (sp.model == MODEL_DDAE) {
+          // [x_j diag (N) | (L or S, x_j), j < N (N-1) | (V, x_1) | (V, y_j), j >= 2 (N-1) | u diag | (u, u_prev)]
+          const int N = sp.N, Nf = sp.Nf, bx = L.offx(k), bu = L.offu(k);
+          for (int j = 0; j < N; ++j) ws(j, bx + j, bx + j);
+          for (int j = 1; j <= N - 1; ++j) ws(N + j - 1, bu + N + (j < Nf ? 1 : 3), bx + j - 1);
+          ws(2 * N - 1, bu + N + 2, bx);
+          for (int j = 2; j <= N; ++j) ws(2 * N + j - 2, bu + N + 2, bu + j - 1);
+          ws(3 * N - 1, bu + N, bu + N);
+          if (k >= 2) ws(3 * N, bu + N, L.offu(k - 1) + N);
+        } else if (sp.model == MODEL_PLATE || sp.model == MODEL_PPLATE) {
           for (int q = 0; q < nx; ++q) ws(q, L.offx(k) + q, L.offx(k) + q);
           for (int q = 0; q < nu; ++q) ws(nx + q, L.offu(k) + q, L.offu(k) + q);
         } else {
@@ -472,7 +528,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       }
     }
     auto symbolic_of = [&](int i) {
-      Layout L{nx, nu, sp.T[i]};
+      Layout L{nx, nu, sp.T[i], mc.nr};
       const int wo = A.inst_woff[i], ro = A.inst_roff[i];
       const int nl = L.n(), ml = L.m();
       auto hc = [&](int r, int s) -> int { return A.Hcol[(size_t)(ro + r) * WH + s]; };
@@ -508,6 +564,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
             auto& c = coord[L.offx(k) + q];
             c[0] = k;
             if (sp.model == MODEL_PLATE) { c[1] = q % sp.g; c[2] = q / sp.g; }
+            if (sp.model == MODEL_PPLATE) { c[1] = q % (sp.g - 2); c[2] = q / (sp.g - 2); }
           }
           if (k >= 1)
             for (int q = 0; q < nu; ++q) {
@@ -521,7 +578,8 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
               }
             }
         }
-        int leaf = (sp.model == MODEL_PLATE) ? std::max(1, sp.nd_leaf) * 64 : std::max(1, sp.nd_leaf) * (nx + nu);
+        int leaf = (sp.model == MODEL_PLATE || sp.model == MODEL_PPLATE) ? std::max(1, sp.nd_leaf) * 64
+                                                                         : std::max(1, sp.nd_leaf) * (nx + nu);
         if (ord == 3 && sp.nd_leaf <= 1) leaf = nl;  // the whole horizon is one two-sided leaf
         NDOrder nd(adj, coord, leaf);
         nd.two_sided = ord == 3;
@@ -558,7 +616,7 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
     A.ordering_used = ord_of(sp.T[ni - 1]);
     A.amalgamation_used = syms[ni - 1].amalg;
     for (int i = 0; i < ni; ++i) {
-      Layout L{nx, nu, sp.T[i]};
+      Layout L{nx, nu, sp.T[i], mc.nr};
       const int vo = A.inst_voff[i], ro = A.inst_roff[i], wo = A.inst_woff[i];
       const int nl = L.n(), ml = L.m();
       auto hc = [&](int r, int s) -> int& { return A.Hcol[(size_t)(ro + r) * WH + s]; };

@@ -20,6 +20,7 @@ struct ProblemSpec {
   double kappa = 0.01, cq = 0.01, rho_u = 1e-3;
   double xlo = 0, xhi = 1, ulo = 1, uhi = 5;
   double wu = 0, ubar = 0;
+  double Tb = 50.0, qloss = 10.0;
   double gamma = 1e-8, tol = 1e-8, pivtol = 1e-12, dw_max = 1e40;
   int ordering = 0;  // 0 auto, 1 natural, 2 nested dissection
   int nd_leaf = 1;

@@ -22,6 +22,11 @@ Recipes (one per workload):
   plate         target field = sum of 3 Gaussian bumps with amplitude
                 U[0.3, 0.8], centre U[0.2, 0.8]^2, width U[0.08, 0.2];
                 initial field 0.
+  paper plate   the paper's nonlinear plate (Sec. 4.2, table pde-params):
+                21 x 21 nodes, dt = 0.08, a 1.0 s prediction horizon
+                (12 intervals), the piecewise region setpoint 58 / 55 / 63
+                switching at t = 0.5 and 1.5 s of a 3.0 s run; initial field
+                T_b = 50 everywhere, cold-start control Q = 50 (its bound).
 """
 from __future__ import annotations
 
@@ -86,6 +91,13 @@ def unit_directions(dim: int, count: int, seed: int) -> np.ndarray:
     return d / np.linalg.norm(d, axis=1, keepdims=True)
 
 
+def paper_plate_setpoints(t0: float, T: int, dt: float = 0.08) -> np.ndarray:
+    """The region setpoint T_sp(t) of eq. (pde-ocp) at the stages
+    t0 + k dt, k = 1..T: 58 before 0.5 s, 55 before 1.5 s, 63 after."""
+    t = t0 + dt * np.arange(1, T + 1)
+    return np.where(t < 0.5, 58.0, np.where(t < 1.5, 55.0, 63.0))
+
+
 # Workloads by name: sizes as the paper's distillation and heated-plate
 # studies scaled per the benchmark configurations.
 WORKLOADS = {
@@ -96,6 +108,7 @@ WORKLOADS = {
                                               resolves=50, seed=4),
     "plate_g128_S16_T100": dict(model=1, g=128, S=16, T=100, resolves=20, seed=5),
     "paper_distillation_N32_T90": dict(model=0, N=32, Nf=17, T=90, resolves=150, seed=6),
+    "paper_plate_n21_T12": dict(model=3, g=21, T=12, dt=0.08, resolves=37, t_final=3.0),
 }
 
 # The paper's column: problem constants (keyword names of nmpc_problem and
