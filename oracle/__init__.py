@@ -54,13 +54,15 @@ class _Problem(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("gamma", C.c_double), ("mu0_cold", C.c_double),
                 ("mu0_warm", C.c_double), ("push_cold", C.c_double), ("push_warm", C.c_double),
-                ("max_iter", C.c_int), ("pivtol", C.c_double), ("dw_max", C.c_double)]
+                ("max_iter", C.c_int), ("pivtol", C.c_double), ("dw_max", C.c_double),
+                ("kkt", C.c_int), ("hy_gamma", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int)]
 
 
 class _Info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("inertia_retries", C.c_int),
                 ("ls_trials", C.c_int), ("mu_final", C.c_double), ("E0_scaled", C.c_double),
-                ("E0_unscaled", C.c_double), ("objective", C.c_double), ("delta_w_last", C.c_double)]
+                ("E0_unscaled", C.c_double), ("objective", C.c_double), ("delta_w_last", C.c_double),
+                ("cg_iters", C.c_int)]
 
 
 class _State(C.Structure):
@@ -104,6 +106,11 @@ def _ip(a):
 
 
 INF = float("inf")
+
+# Newton-system forms: Lifted-KKT (eq. liftedkkt-pd) and HyKKT (Sec. 3.2.2's
+# alternative: equalities kept, augmented-Lagrangian Cholesky plus CG).
+KKT_LIFTED, KKT_HYKKT = 0, 1
+HY_GAMMA, CG_TOL, CG_MAX_ITER = 1e4, 1e-12, 200
 
 
 class Problem:
@@ -257,7 +264,8 @@ def steady_state(prob, u):
 
 def default_options(**kw):
     o = dict(tol=1e-8, gamma=1e-8, mu0_cold=0.1, mu0_warm=1e-8, push_cold=1e-2, push_warm=1e-9,
-             max_iter=200, pivtol=1e-12, dw_max=1e40)
+             max_iter=200, pivtol=1e-12, dw_max=1e40, kkt=KKT_LIFTED, hy_gamma=HY_GAMMA, cg_tol=CG_TOL,
+             cg_max_iter=CG_MAX_ITER)
     o.update(kw)
     return o
 

@@ -10,6 +10,13 @@
  * band matrix in the natural stage order and factored by a textbook banded
  * Cholesky (no reordering, no supernodes).  Success of the Cholesky is the
  * inertia test of eq. (infiniteOCP-inertia).
+ *
+ * HyKKT form (options.kkt = 1), the alternative to Lifted-KKT that Sec. 3.2.2
+ * names, after the hybrid direct-iterative method it cites (Regev et al.
+ * 2023; Golub & Greif 2003): the equalities stay with multipliers lambda, the
+ * augmented matrix W + Sigma_y + delta_w I + gamma H^T H takes the same band
+ * Cholesky (and its success the same inertia test), and conjugate gradients on
+ * the Schur complement give lambda's step.
  */
 #include "nmpc_oracle.h"
 
@@ -505,6 +512,7 @@ typedef struct {
   int *rp, *ci;
   int *tr, *tc; double *tv; /* Hessian triplets */
   double *band, *rhs, *lam, *tmp;
+  double *gv, *cg_r, *cg_p, *cg_q, *cg_x; /* HyKKT: right-hand side g (n), CG vectors (m) */
   int nL, nU;
 } work;
 
@@ -539,12 +547,16 @@ static int work_init(work* w, const or_problem* p, const or_options* o) {
   w->band = malloc(sizeof(double) * (size_t)(b + 1) * n);
   w->rhs = malloc(sizeof(double) * n);
   w->tmp = malloc(sizeof(double) * (n > m ? n : m));
-  return (w->band && w->rhs) ? 0 : -1;
+  w->gv = malloc(sizeof(double) * n);
+  w->cg_r = malloc(sizeof(double) * m); w->cg_p = malloc(sizeof(double) * m);
+  w->cg_q = malloc(sizeof(double) * m); w->cg_x = malloc(sizeof(double) * m);
+  return (w->band && w->rhs && w->gv && w->cg_r && w->cg_p && w->cg_q && w->cg_x) ? 0 : -1;
 }
 
 static void work_free(work* w) {
   free(w->yL); free(w->yU); free(w->grad); free(w->h); free(w->Hv); free(w->rp); free(w->ci);
   free(w->lam); free(w->tr); free(w->tc); free(w->tv); free(w->band); free(w->rhs); free(w->tmp);
+  free(w->gv); free(w->cg_r); free(w->cg_p); free(w->cg_q); free(w->cg_x);
 }
 
 static void eval_all(work* w, const double* y) {
@@ -600,6 +612,47 @@ static void errors(work* w, const or_state* z, double mu, double* Es, double* Eu
   if (Eu) *Eu = fmax(fmax(dual, prim), comp);
 }
 
+/* Optimality error E_mu of the barrier problem with its equalities kept
+ * (HyKKT form, W&B eq. (5) as printed there): stationarity
+ * grad f + H^T lambda - zL + zU scaled by s_d, the constraint values h, and
+ * the bound complementarity scaled by s_c; s_d averages |lambda| and z over
+ * the m + n_z multipliers, s_c averages z over the n_z bound multipliers. */
+static void errors_hy(work* w, const or_state* z, double mu, double* Es, double* Eu) {
+  const int n = w->n, m = w->m;
+  double* ry = w->tmp;
+  jac_t_mult(w, z->w_p, ry);
+  double dual = 0.0, prim = 0.0, comp = 0.0, sum_l = 0.0, sum_z = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double v = w->grad[i] + ry[i];
+    if (isfinite(w->yL[i])) { v -= z->zL[i]; sum_z += fabs(z->zL[i]); comp = fmax(comp, fabs((z->y[i] - w->yL[i]) * z->zL[i] - mu)); }
+    if (isfinite(w->yU[i])) { v += z->zU[i]; sum_z += fabs(z->zU[i]); comp = fmax(comp, fabs((w->yU[i] - z->y[i]) * z->zU[i] - mu)); }
+    dual = fmax(dual, fabs(v));
+  }
+  for (int r = 0; r < m; ++r) {
+    prim = fmax(prim, fabs(w->h[r]));
+    sum_l += fabs(z->w_p[r]);
+  }
+  const double nz = (double)(w->nL + w->nU);
+  const double sd = fmax(S_MAX, (sum_l + sum_z) / (m + nz)) / S_MAX;
+  const double sc = fmax(S_MAX, sum_z / nz) / S_MAX;
+  *Es = fmax(fmax(dual / sd, prim), comp / sc);
+  if (Eu) *Eu = fmax(fmax(dual, prim), comp);
+}
+
+/* barrier objective phi_mu and constraint violation theta (1-norm) of the
+ * HyKKT form: phi = f - mu sum log(bound gaps), theta = ||h||_1 */
+static void merit_hy(work* w, const double* y, double f, const double* h, double mu,
+                     double* phi, double* theta) {
+  double lg = 0.0, th = 0.0;
+  for (int i = 0; i < w->n; ++i) {
+    if (isfinite(w->yL[i])) lg += log(y[i] - w->yL[i]);
+    if (isfinite(w->yU[i])) lg += log(w->yU[i] - y[i]);
+  }
+  for (int r = 0; r < w->m; ++r) th += fabs(h[r]);
+  *phi = f - mu * lg;
+  *theta = th;
+}
+
 /* barrier objective phi_mu and constraint violation theta (1-norm) at (y, s) */
 static void merit(work* w, const double* y, const double* sp, const double* sm,
                   double f, const double* h, double mu, double* phi, double* theta) {
@@ -617,12 +670,26 @@ static void merit(work* w, const double* y, const double* sp, const double* sm,
   *theta = th;
 }
 
+/* the optimality error and the merits of the form the options select */
+static void opt_error(work* w, const or_state* z, double mu, double* Es, double* Eu) {
+  if (w->o->kkt == 1) errors_hy(w, z, mu, Es, Eu);
+  else errors(w, z, mu, Es, Eu);
+}
+static void merit_of(work* w, const double* y, const double* sp, const double* sm,
+                     double f, const double* h, double mu, double* phi, double* theta) {
+  if (w->o->kkt == 1) merit_hy(w, y, f, h, mu, phi, theta);
+  else merit(w, y, sp, sm, f, h, mu, phi, theta);
+}
+
 /* Assemble K_c = W + Sigma_y + delta_w I + H^T (Q+ + Q-) H into band storage
- * (eq. liftedkkt-pd), from w->grad/h/Hv evaluated at z->y. */
+ * (eq. liftedkkt-pd), from w->grad/h/Hv evaluated at z->y.  In the HyKKT form
+ * the same pattern holds K_gamma = W + Sigma_y + delta_w I + gamma H^T H, the
+ * augmented-Lagrangian matrix, with W the Hessian at the multipliers lambda. */
 static void assemble(work* w, const or_state* z, double delta_w) {
   const int n = w->n, m = w->m, bw = w->b + 1;
+  const int hy = w->o->kkt == 1;
   memset(w->band, 0, sizeof(double) * (size_t)bw * n);
-  for (int r = 0; r < m; ++r) w->lam[r] = z->w_p[r] - z->w_m[r];
+  for (int r = 0; r < m; ++r) w->lam[r] = hy ? z->w_p[r] : z->w_p[r] - z->w_m[r];
   int cnt = or_hessian(w->p, z->y, w->lam, w->tr, w->tc, w->tv, w->ntrip_cap);
   for (int t = 0; t < cnt; ++t) w->band[(size_t)w->tc[t] * bw + (w->tr[t] - w->tc[t])] += w->tv[t];
   for (int i = 0; i < n; ++i) {
@@ -632,7 +699,7 @@ static void assemble(work* w, const or_state* z, double delta_w) {
     w->band[(size_t)i * bw] += sig;
   }
   for (int r = 0; r < m; ++r) {
-    const double D = z->b_p[r] / z->s_p[r] + z->b_m[r] / z->s_m[r];
+    const double D = hy ? w->o->hy_gamma : z->b_p[r] / z->s_p[r] + z->b_m[r] / z->s_m[r];
     for (int a = w->rp[r]; a < w->rp[r + 1]; ++a)
       for (int c = w->rp[r]; c <= a; ++c) {
         const int i = w->ci[a], j = w->ci[c]; /* columns ascending: i >= j */
@@ -690,6 +757,75 @@ static void direction(work* w, const or_state* z, double mu, or_state* d) {
   }
 }
 
+/* Newton direction of the HyKKT form from the factored K_gamma.  The
+ * primal-dual system of the barrier problem with its equalities kept,
+ *   [Wh  H^T] [dy  ]   [a]   a = -(grad phi_mu + H^T lambda)
+ *   [H   0  ] [dlam] = [c],  c = -h,   Wh = W + Sigma_y + delta_w I,
+ * is solved as in the hybrid direct-iterative method the paper cites
+ * (Regev et al. 2023, after Golub & Greif 2003): adding gamma H^T times the
+ * second block row to the first gives K_gamma dy + H^T dlam = a + gamma H^T c
+ * =: g, so with S = H K_gamma^-1 H^T
+ *   S dlam = H K_gamma^-1 g - c            (conjugate gradients on S),
+ *   dy = K_gamma^-1 (g - H^T dlam)         (one more solve).
+ * CG starts from dlam = 0 and stops when ||r||^2 <= cg_tol^2 ||r_0||^2, after
+ * cg_max_iter iterations, or when p^T S p is not positive.  The bound
+ * multipliers follow as in the lifted form.  Returns the CG iterations. */
+static int direction_hy(work* w, const or_state* z, double mu, or_state* d) {
+  const int n = w->n, m = w->m;
+  const double gam = w->o->hy_gamma;
+  double *g = w->gv, *r = w->cg_r, *p = w->cg_p, *q = w->cg_q, *x = w->cg_x, *v = w->rhs;
+  /* g = -(grad phi_mu + H^T (lambda + gamma h)) */
+  for (int i = 0; i < m; ++i) w->tmp[i] = z->w_p[i] + gam * w->h[i];
+  jac_t_mult(w, w->tmp, g);
+  for (int i = 0; i < n; ++i) {
+    double gp = w->grad[i] + g[i];
+    if (isfinite(w->yL[i])) gp -= mu / (z->y[i] - w->yL[i]);
+    if (isfinite(w->yU[i])) gp += mu / (w->yU[i] - z->y[i]);
+    g[i] = -gp;
+  }
+  /* r_0 = H K^-1 g - c = H K^-1 g + h */
+  memcpy(v, g, sizeof(double) * n);
+  band_solve(n, w->b, w->band, v);
+  jac_mult(w, v, r);
+  double rr = 0.0;
+  for (int i = 0; i < m; ++i) { r[i] += w->h[i]; x[i] = 0.0; p[i] = r[i]; rr += r[i] * r[i]; }
+  const double stop = w->o->cg_tol * w->o->cg_tol * rr;
+  int it = 0;
+  while (rr > stop && it < w->o->cg_max_iter) {
+    /* q = S p = H K^-1 H^T p */
+    jac_t_mult(w, p, v);
+    band_solve(n, w->b, w->band, v);
+    jac_mult(w, v, q);
+    double pq = 0.0;
+    for (int i = 0; i < m; ++i) pq += p[i] * q[i];
+    if (!(pq > 0.0)) break;
+    const double a = rr / pq;
+    double rr_new = 0.0;
+    for (int i = 0; i < m; ++i) { x[i] += a * p[i]; r[i] -= a * q[i]; rr_new += r[i] * r[i]; }
+    const double beta = rr_new / rr;
+    rr = rr_new;
+    for (int i = 0; i < m; ++i) p[i] = r[i] + beta * p[i];
+    ++it;
+  }
+  /* dy = K^-1 (g - H^T dlam) */
+  jac_t_mult(w, x, v);
+  for (int i = 0; i < n; ++i) d->y[i] = g[i] - v[i];
+  band_solve(n, w->b, w->band, d->y);
+  memcpy(d->w_p, x, sizeof(double) * m);
+  for (int i = 0; i < n; ++i) {
+    d->zL[i] = d->zU[i] = 0.0;
+    if (isfinite(w->yL[i])) {
+      const double gap = z->y[i] - w->yL[i];
+      d->zL[i] = mu / gap - z->zL[i] - z->zL[i] / gap * d->y[i];
+    }
+    if (isfinite(w->yU[i])) {
+      const double gap = w->yU[i] - z->y[i];
+      d->zU[i] = mu / gap - z->zU[i] + z->zU[i] / gap * d->y[i];
+    }
+  }
+  return it;
+}
+
 /* Inertia correction (W&B Algorithm IC restricted to delta_w, since the
  * lifted system has no equality block): factor with 0, then 1e-4 or
  * last/3, then x100 (first) or x8, failing above dw_max (1e40 by default).  Returns 0 on
@@ -736,6 +872,7 @@ int or_solve(const or_problem* p, const or_options* o, or_state* z, int warm,
   if (work_init(&w, p, o)) { work_free(&w); info->status = 2; return 2; }
   const int n = w.n, m = w.m;
   const double gam = o->gamma;
+  const int hy = o->kkt == 1;
   const double mu_min = o->tol / 10.0;
   double mu = warm ? o->mu0_warm : o->mu0_cold;
   const double push = warm ? o->push_warm : o->push_cold;
@@ -743,7 +880,14 @@ int or_solve(const or_problem* p, const or_options* o, or_state* z, int warm,
   /* initial point (Sec. 3.2.4: warm start from the previous solution) */
   for (int i = 0; i < n; ++i) z->y[i] = push_into(z->y[i], w.yL[i], w.yU[i], push);
   eval_all(&w, z->y);
-  if (!warm) {
+  if (!warm && hy) {
+    /* HyKKT form: equality multipliers start at 0 */
+    for (int r = 0; r < m; ++r) z->w_p[r] = 0.0;
+    for (int i = 0; i < n; ++i) {
+      z->zL[i] = isfinite(w.yL[i]) ? 1.0 : 0.0;
+      z->zU[i] = isfinite(w.yU[i]) ? 1.0 : 0.0;
+    }
+  } else if (!warm) {
     for (int r = 0; r < m; ++r) {
       z->s_p[r] = fmax(gam - w.h[r], push);
       z->s_m[r] = fmax(gam + w.h[r], push);
@@ -755,7 +899,7 @@ int or_solve(const or_problem* p, const or_options* o, or_state* z, int warm,
       z->zU[i] = isfinite(w.yU[i]) ? 1.0 : 0.0;
     }
   } else {
-    for (int r = 0; r < m; ++r) {
+    for (int r = 0; r < m && !hy; ++r) {
       z->s_p[r] = fmax(z->s_p[r], push); z->s_m[r] = fmax(z->s_m[r], push);
       z->b_p[r] = fmax(z->b_p[r], push); z->b_m[r] = fmax(z->b_m[r], push);
     }
@@ -778,7 +922,7 @@ int or_solve(const or_problem* p, const or_options* o, or_state* z, int warm,
   int nf = 0;
 
   double phi, theta;
-  merit(&w, z->y, z->s_p, z->s_m, w.f, w.h, mu, &phi, &theta);
+  merit_of(&w, z->y, z->s_p, z->s_m, w.f, w.h, mu, &phi, &theta);
   const double theta_max = 1e4 * fmax(1.0, theta);
   const double theta_min = 1e-4 * fmax(1.0, theta);
   double dw_last = 0.0;
@@ -789,35 +933,40 @@ int or_solve(const or_problem* p, const or_options* o, or_state* z, int warm,
     if (!isfinite(w.f) || !all_finite(w.h, m) || !all_finite(w.grad, n)) { status = 13; break; }
     /* A-2: overall convergence, eq. (infiniteOCP-outerTol) */
     double E0, E0u, Emu;
-    errors(&w, z, 0.0, &E0, &E0u);
+    opt_error(&w, z, 0.0, &E0, &E0u);
     info->E0_scaled = E0; info->E0_unscaled = E0u;
     if (E0 <= o->tol) { status = 0; break; }
     if (it == o->max_iter) { status = 10; break; }
     /* A-3: barrier subproblem convergence, eq. (infiniteOCP-innerTol) */
-    errors(&w, z, mu, &Emu, NULL);
+    opt_error(&w, z, mu, &Emu, NULL);
     while (Emu <= KAPPA_EPS * mu && mu > mu_min) {
       mu = fmax(mu_min, fmin(KAPPA_MU * mu, pow(mu, THETA_MU)));
       tau = fmax(TAU_MIN, 1.0 - mu);
       nf = 0;
-      errors(&w, z, mu, &Emu, NULL);
+      opt_error(&w, z, mu, &Emu, NULL);
     }
-    merit(&w, z->y, z->s_p, z->s_m, w.f, w.h, mu, &phi, &theta);
+    merit_of(&w, z->y, z->s_p, z->s_m, w.f, w.h, mu, &phi, &theta);
     /* A-4: Newton direction with inertia correction (Algorithm 2, l. 6-14) */
     double dw = 0.0;
     if (factor_with_correction(&w, z, &dw_last, &dw, &info->inertia_retries)) { status = 12; break; }
-    direction(&w, z, mu, &d);
+    if (hy) info->cg_iters += direction_hy(&w, z, mu, &d);
+    else direction(&w, z, mu, &d);
     /* fraction to the boundary */
     double ap = 1.0, ad = 1.0;
     for (int i = 0; i < n; ++i) {
       if (isfinite(w.yL[i]) && d.y[i] < 0.0) ap = fmin(ap, -tau * (z->y[i] - w.yL[i]) / d.y[i]);
       if (isfinite(w.yU[i]) && d.y[i] > 0.0) ap = fmin(ap, tau * (w.yU[i] - z->y[i]) / d.y[i]);
     }
-    ap = frac_to_boundary(z->s_p, d.s_p, tau, m, ap);
-    ap = frac_to_boundary(z->s_m, d.s_m, tau, m, ap);
+    if (!hy) {
+      ap = frac_to_boundary(z->s_p, d.s_p, tau, m, ap);
+      ap = frac_to_boundary(z->s_m, d.s_m, tau, m, ap);
+    }
     ad = frac_to_boundary(z->zL, d.zL, tau, n, ad);
     ad = frac_to_boundary(z->zU, d.zU, tau, n, ad);
-    ad = frac_to_boundary(z->b_p, d.b_p, tau, m, ad);
-    ad = frac_to_boundary(z->b_m, d.b_m, tau, m, ad);
+    if (!hy) {
+      ad = frac_to_boundary(z->b_p, d.b_p, tau, m, ad);
+      ad = frac_to_boundary(z->b_m, d.b_m, tau, m, ad);
+    }
     /* directional derivative of the barrier objective */
     double gphi = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -826,7 +975,7 @@ int or_solve(const or_problem* p, const or_options* o, or_state* z, int warm,
       if (isfinite(w.yU[i])) g += mu / (w.yU[i] - z->y[i]);
       gphi += g * d.y[i];
     }
-    for (int r = 0; r < m; ++r) gphi -= mu * (d.s_p[r] / z->s_p[r] + d.s_m[r] / z->s_m[r]);
+    for (int r = 0; r < m && !hy; ++r) gphi -= mu * (d.s_p[r] / z->s_p[r] + d.s_m[r] / z->s_m[r]);
     /* A-5: backtracking filter line search (eq. infiniteOCP-lineSearch) */
     double amin;
     if (gphi < 0.0) {
@@ -839,9 +988,9 @@ int or_solve(const or_problem* p, const or_options* o, or_state* z, int warm,
     while (alpha >= amin) {
       ++trials;
       for (int i = 0; i < n; ++i) zt.y[i] = z->y[i] + alpha * d.y[i];
-      for (int r = 0; r < m; ++r) { zt.s_p[r] = z->s_p[r] + alpha * d.s_p[r]; zt.s_m[r] = z->s_m[r] + alpha * d.s_m[r]; }
+      for (int r = 0; r < m && !hy; ++r) { zt.s_p[r] = z->s_p[r] + alpha * d.s_p[r]; zt.s_m[r] = z->s_m[r] + alpha * d.s_m[r]; }
       or_eval(p, zt.y, &ft, NULL, ht, NULL, NULL, NULL);
-      merit(&w, zt.y, zt.s_p, zt.s_m, ft, ht, mu, &phit, &thetat);
+      merit_of(&w, zt.y, zt.s_p, zt.s_m, ft, ht, mu, &phit, &thetat);
       int ok = isfinite(phit) && isfinite(thetat) && thetat <= theta_max;
       for (int q = 0; ok && q < nf; ++q) if (thetat >= filt_th[q] && phit >= filt_ph[q]) ok = 0;
       if (ok) {
@@ -869,8 +1018,10 @@ int or_solve(const or_problem* p, const or_options* o, or_state* z, int warm,
       z->zU[i] += ad * d.zU[i];
     }
     for (int r = 0; r < m; ++r) {
+      z->w_p[r] += alpha * d.w_p[r]; /* omega+, or lambda in the HyKKT form: the primal step */
+      if (hy) continue;
       z->s_p[r] = zt.s_p[r]; z->s_m[r] = zt.s_m[r];
-      z->w_p[r] += alpha * d.w_p[r]; z->w_m[r] += alpha * d.w_m[r];
+      z->w_m[r] += alpha * d.w_m[r];
       z->b_p[r] += ad * d.b_p[r]; z->b_m[r] += ad * d.b_m[r];
     }
     /* safeguard of the bound multipliers (W&B eq. (16)) */
@@ -878,7 +1029,7 @@ int or_solve(const or_problem* p, const or_options* o, or_state* z, int warm,
       if (isfinite(w.yL[i])) { double g = z->y[i] - w.yL[i]; z->zL[i] = fmax(fmin(z->zL[i], KAPPA_SIGMA * mu / g), mu / (KAPPA_SIGMA * g)); }
       if (isfinite(w.yU[i])) { double g = w.yU[i] - z->y[i]; z->zU[i] = fmax(fmin(z->zU[i], KAPPA_SIGMA * mu / g), mu / (KAPPA_SIGMA * g)); }
     }
-    for (int r = 0; r < m; ++r) {
+    for (int r = 0; r < m && !hy; ++r) {
       z->b_p[r] = fmax(fmin(z->b_p[r], KAPPA_SIGMA * mu / z->s_p[r]), mu / (KAPPA_SIGMA * z->s_p[r]));
       z->b_m[r] = fmax(fmin(z->b_m[r], KAPPA_SIGMA * mu / z->s_m[r]), mu / (KAPPA_SIGMA * z->s_m[r]));
     }
@@ -899,7 +1050,7 @@ void or_kkt_error(const or_problem* p, const or_options* o, const or_state* z, d
   work w;
   work_init(&w, p, o);
   eval_all(&w, z->y);
-  errors(&w, z, mu, E_scaled, E_unscaled);
+  opt_error(&w, z, mu, E_scaled, E_unscaled);
   work_free(&w);
 }
 
@@ -910,7 +1061,8 @@ int or_newton_step(const or_problem* p, const or_options* o, const or_state* z, 
   eval_all(&w, z->y);
   assemble(&w, z, delta_w);
   int rc = or_band_cholesky(w.n, w.b, w.band);
-  if (rc == 0) direction(&w, z, mu, d);
+  if (rc == 0 && o->kkt == 1) direction_hy(&w, z, mu, d);
+  else if (rc == 0) direction(&w, z, mu, d);
   work_free(&w);
   return rc;
 }

@@ -24,6 +24,11 @@
  *                                can decide it)
  *   converged solutions          pinned (dense KKT solve of LQ cases,
  *                                brute-force active sets, FD stationarity)
+ *   HyKKT Newton step            pinned (dense primal-dual Newton system of the
+ *                                unlifted barrier problem; independent of the
+ *                                augmentation weight)
+ *   HyKKT converged solutions    pinned (equality QP incl. its multipliers,
+ *                                brute-force active sets, FD stationarity)
  *   iteration counts             parity unpinned (no external count exists)
  */
 #ifndef NMPC_ORACLE_H
@@ -61,6 +66,10 @@ typedef struct {
   int max_iter;
   double pivtol;     /* relative pivot tolerance of the inertia test */
   double dw_max;     /* largest regularization delta_w of the inertia correction (W&B Algorithm IC: 1e40) */
+  int kkt;           /* Newton system: 0 Lifted-KKT (eq. liftedkkt-pd), 1 HyKKT (Sec. 3.2.2's alternative) */
+  double hy_gamma;   /* HyKKT: augmented-Lagrangian weight of H^T H */
+  double cg_tol;     /* HyKKT: CG stops when ||r||^2 <= cg_tol^2 ||r_0||^2 */
+  int cg_max_iter;   /* HyKKT: CG iterations per Newton step at most */
 } or_options;
 
 typedef struct {
@@ -69,12 +78,15 @@ typedef struct {
   int inertia_retries;
   int ls_trials;
   double mu_final, E0_scaled, E0_unscaled, objective, delta_w_last;
+  int cg_iters;      /* HyKKT: CG iterations over the whole solve */
 } or_info;
 
 /* Primal-dual state.  All arrays are caller-owned.
  *   y, zL, zU: n     s_p, s_m, w_p, w_m, b_p, b_m: m
  * (s = slacks, w = omega multipliers, b = beta slack-bound multipliers, for the
- * lifted rows  h - gamma + s_p = 0  and  -h - gamma + s_m = 0). */
+ * lifted rows  h - gamma + s_p = 0  and  -h - gamma + s_m = 0).
+ * With kkt = 1 (HyKKT) the equalities h = 0 stay and w_p holds their
+ * multipliers lambda; s_p, s_m, w_m, b_p and b_m are not used. */
 typedef struct {
   double *y, *zL, *zU;
   double *s_p, *s_m, *w_p, *w_m, *b_p, *b_m;
