@@ -418,7 +418,7 @@ def plate_g128_iteration(P, dev, peak):
     return out
 
 
-def paper_column_resolves(P, dev, resolves=40, warmup=3, model=None):
+def paper_column_resolves(P, dev, resolves=40, warmup=3, model=None, kkt=0):
     """The paper's own column and cost (N = 32, feed tray 17, holdups 0.5 /
     0.25 / 1.0, dt = 2, 90 intervals, (x_1 - xbar)^2 + 0.1 (u - ubar)^2):
     warm re-solves of its closed loop with inputs resident on the device,
@@ -431,7 +431,7 @@ def paper_column_resolves(P, dev, resolves=40, warmup=3, model=None):
     N, Nf, T = wl["N"], wl["Nf"], wl["T"]
     model = P.MODEL_DISTILLATION if model is None else model
     cu = N if model == P.MODEL_DISTILLATION_DAE else 0  # u within a stage's control block
-    s = P.Solver(model, [T], N=N, Nf=Nf, device=dev, **I.PAPER_COLUMN)
+    s = P.Solver(model, [T], N=N, Nf=Nf, device=dev, opts=P.options(kkt=kkt), **I.PAPER_COLUMN)
     n = s.dims[0][0]
     sp = torch.full((T,), I.PAPER_XBAR, dtype=torch.float64, device=dev)
     y = torch.empty(n, dtype=torch.float64, device=dev)
@@ -439,7 +439,7 @@ def paper_column_resolves(P, dev, resolves=40, warmup=3, model=None):
                  u_prev=np.array([I.U_REF]))
     first = s.solve(warm=False)[0]
     s.get_solution(0, out=(y, None))
-    ms, iters, ok = [], [], first["status"] == 0
+    ms, iters, cgs, ok = [], [], [], first["status"] == 0
     for q in range(warmup + resolves):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s.stream)
@@ -452,17 +452,23 @@ def paper_column_resolves(P, dev, resolves=40, warmup=3, model=None):
         if q >= warmup:
             ms.append(e0.elapsed_time(e1))
             iters.append(inf["iters"])
-    out = {"workload": "paper_distillation_N32_T90" + ("_dae" if cu else ""), "n": n, "resolves_per_s": len(ms) / (sum(ms) * 1e-3),
+            cgs.append(inf["cg_iters"])
+    name = "paper_distillation_N32_T90" + ("_dae" if cu else "") + ("_hykkt" if kkt else "")
+    out = {"workload": name, "n": n, "resolves_per_s": len(ms) / (sum(ms) * 1e-3),
            "ms_per_resolve": sum(ms) / len(ms), "ms_per_ipm_iter": sum(ms) / max(1, sum(iters)),
            "ipm_iters_per_resolve": sum(iters) / len(iters), "cold_solve_iters": first["iters"],
            "statuses_ok": ok,
            "paper_gpu_ws_pu_s_per_step": {"value": 0.02, "hardware": "RTX 6000 Ada (MadNLP + cuDSS)",
                                           "note": "context only: other hardware and software"}}
+    if kkt:
+        out["kkt"] = "hykkt"
+        out["cg_iters_per_resolve"] = sum(cgs) / len(cgs)
+        out["cold_solve_cg_iters"] = first["cg_iters"]
     s.close()
     return out
 
 
-def paper_plate_resolves(P, dev, warmup=3):
+def paper_plate_resolves(P, dev, warmup=3, kkt=0):
     """The paper's nonlinear heated plate (Sec. 4.2: 21 x 21 nodes, dt =
     0.08, 12 intervals) over its 3.0 s closed loop (37 warm re-solves after
     the cold one, the region setpoint stepping 58 / 55 / 63), each re-solve
@@ -474,7 +480,7 @@ def paper_plate_resolves(P, dev, warmup=3):
     wl = I.WORKLOADS["paper_plate_n21_T12"]
     n, T, dt = wl["g"], wl["T"], wl["dt"]
     nx = (n - 2) ** 2
-    s = P.Solver(P.MODEL_PAPER_PLATE, [T], g=n, device=dev)
+    s = P.Solver(P.MODEL_PAPER_PLATE, [T], g=n, device=dev, opts=P.options(kkt=kkt))
     nv = s.dims[0][0]
     y = torch.empty(nv, dtype=torch.float64, device=dev)
     u0 = torch.full((1,), 50.0, dtype=torch.float64, device=dev)
@@ -486,7 +492,7 @@ def paper_plate_resolves(P, dev, warmup=3):
     first = s.solve(warm=False)[0]
     cold_s = time.perf_counter() - t0
     s.get_solution(0, out=(y, None))
-    ms, iters, ok = [], [], first["status"] == 0
+    ms, iters, cgs, ok = [], [], [], first["status"] == 0
     for k in range(1, steps + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s.stream)
@@ -498,17 +504,18 @@ def paper_plate_resolves(P, dev, warmup=3):
         ok = ok and inf["status"] == 0
         ms.append(e0.elapsed_time(e1))
         iters.append(inf["iters"])
+        cgs.append(inf["cg_iters"])
     yh = y.cpu().numpy()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    s2 = P.Solver(P.MODEL_PAPER_PLATE, [T], g=n, device=dev)
+    s2 = P.Solver(P.MODEL_PAPER_PLATE, [T], g=n, device=dev, opts=P.options(kkt=kkt))
     s2.set_params(x0=yh[nx:2 * nx].copy(), setpoint=I.paper_plate_setpoints(steps * dt, T, dt), u_prev=np.array([50.0]))
     rb = s2.solve(warm=False)[0]
     torch.cuda.synchronize()
     rebuild_s = time.perf_counter() - t1
     s2.close()
     ph = s.time_phases(reps=5)
-    out = {"workload": "paper_plate_n21_T12", "n": nv, "resolves": len(ms),
+    out = {"workload": "paper_plate_n21_T12" + ("_hykkt" if kkt else ""), "n": nv, "resolves": len(ms),
            "resolves_per_s": len(ms) / (sum(ms) * 1e-3), "ms_per_resolve": sum(ms) / len(ms),
            "ms_per_ipm_iter": sum(ms) / max(1, sum(iters)), "ipm_iters_per_resolve": sum(iters) / len(iters),
            "cold_solve_iters": first["iters"], "cold_solve_s": cold_s, "statuses_ok": ok and rb["status"] == 0,
@@ -516,6 +523,10 @@ def paper_plate_resolves(P, dev, warmup=3):
                                                                                       "ms_factor", "ms_solve")},
            "paper_gpu_s_per_step": {"ws_pu": 0.06, "base": 0.97, "hardware": "RTX 6000 Ada (MadNLP + cuDSS)",
                                     "note": "context only: other hardware and software"}}
+    if kkt:
+        out["kkt"] = "hykkt"
+        out["cg_iters_per_resolve"] = sum(cgs) / len(cgs)
+        out["cold_solve_cg_iters"] = first["cg_iters"]
     s.close()
     return out
 
@@ -748,6 +759,9 @@ def main():
         line["paper_column"] = paper_column_resolves(P, dev)
         line["paper_column_dae"] = paper_column_resolves(P, dev, model=P.MODEL_DISTILLATION_DAE)
         line["paper_plate"] = paper_plate_resolves(P, dev)
+        # the HyKKT form of the Newton system on the paper's two workloads
+        line["hykkt"] = {"paper_column": paper_column_resolves(P, dev, kkt=1),
+                         "paper_plate": paper_plate_resolves(P, dev, kkt=1)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores, ncpu = host_cores()
         t_all, it_all, cold_all = oracle_batch_loop(hz, x0s, sps, N, Nf, 3, cores)

@@ -81,6 +81,11 @@ typedef enum {
                                   stage: the flops of stage order with half its chain length */
 } nmpc_ordering;
 
+typedef enum {
+  NMPC_KKT_LIFTED = 0,         /* Lifted-KKT (eqs. liftedkkt, liftedkkt-pd): h relaxed to |h| <= gamma */
+  NMPC_KKT_HYKKT = 1           /* HyKKT (Sec. 3.2.2): equalities kept, augmented Cholesky plus CG */
+} nmpc_kkt;
+
 /* Problem description.  All instances share the model and its constants;
  * each instance has its own horizon T (block-diagonal batch, one KKT block
  * per instance).  Fill it with nmpc_problem_defaults first. */
@@ -148,6 +153,18 @@ typedef struct {
   double dw_max;         /* inertia correction (eq. infiniteOCP-inertia, W&B Algorithm IC):
                             an instance whose regularization delta_w would exceed dw_max
                             stops with NMPC_INERTIA_FAIL (1e40) */
+  int kkt;               /* Newton system (nmpc_kkt): NMPC_KKT_LIFTED (default), or NMPC_KKT_HYKKT,
+                            the alternative to lifting that Sec. 3.2.2 names: the equalities
+                            h = 0 keep their multipliers lambda, K_gamma = W + Sigma_y +
+                            delta_w I + hykkt_gamma H^T H is assembled into the same factor
+                            pattern and factored by the same kernels (its positive pivots are
+                            the inertia test), and conjugate gradients on the Schur complement
+                            H K_gamma^-1 H^T, one pair of triangular solves per CG iteration,
+                            give lambda's step (Regev et al. 2023, after Golub & Greif 2003);
+                            gamma is then unused.  nmpc_sensitivity needs the lifted form. */
+  double hykkt_gamma;    /* HyKKT augmentation weight (1e4) */
+  double cg_tol;         /* HyKKT: CG stops when ||r||_2 <= cg_tol ||r_0||_2 (1e-12) */
+  int cg_max_iter;       /* HyKKT: CG iterations per Newton step at most (200) */
 } nmpc_options;
 
 /* Per-instance result of a solve.  Times are measured with CUDA events on
@@ -162,6 +179,7 @@ typedef struct {
   double kkt_unscaled;
   double objective;
   double ms_total;       /* whole solve call (same for all instances) */
+  int cg_iters;          /* HyKKT: conjugate-gradient iterations of this solve (0 for Lifted-KKT) */
 } nmpc_info;
 
 typedef struct {

@@ -20,6 +20,7 @@ _lib = None
 
 MODEL_DISTILLATION, MODEL_PLATE, MODEL_TOY, MODEL_PAPER_PLATE, MODEL_DISTILLATION_DAE = 0, 1, 2, 3, 4
 ORDER_AUTO, ORDER_NATURAL, ORDER_ND = 0, 1, 2
+KKT_LIFTED, KKT_HYKKT = 0, 1
 STATUS = {0: "ok", 1: "invalid", 2: "cuda_error", 3: "workspace", 10: "max_iter", 11: "linesearch_fail",
           12: "inertia_fail", 13: "nonfinite", 14: "timeout", 15: "not_solved"}
 
@@ -48,13 +49,14 @@ class Options(C.Structure):
                 ("push_cold", C.c_double), ("push_warm", C.c_double), ("max_iter", C.c_int),
                 ("ordering", C.c_int), ("nd_leaf", C.c_int), ("use_graph", C.c_int), ("spin_limit", C.c_longlong),
                 ("pivtol", C.c_double), ("factor_mode", C.c_int), ("solve_mode", C.c_int),
-                ("panel_scale", C.c_int), ("amalgamation", C.c_int), ("dw_max", C.c_double)]
+                ("panel_scale", C.c_int), ("amalgamation", C.c_int), ("dw_max", C.c_double),
+                ("kkt", C.c_int), ("hykkt_gamma", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("inertia_retries", C.c_int), ("ls_trials", C.c_int),
                 ("mu_final", C.c_double), ("kkt_scaled", C.c_double), ("kkt_unscaled", C.c_double),
-                ("objective", C.c_double), ("ms_total", C.c_double)]
+                ("objective", C.c_double), ("ms_total", C.c_double), ("cg_iters", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -1061,7 +1061,7 @@ __global__ void __launch_bounds__(ST) k_fwd_level(Dev d, SnDev s, const FrontDes
   load_desc(&fd, dl + blockIdx.x);
   if (threadIdx.x == 0) s_to = s_lost = 0;
   __syncthreads();
-  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+  if (!solve_on(d.ctl[fd.inst])) return;
   fwd_front(d, s, fd, smem_cap, &bar, &s_to, &s_lost, [] { __syncthreads(); });
   if (threadIdx.x == 0 && (s_to || s_lost)) atomicExch(s.timeout, 1);
 }
@@ -1073,7 +1073,7 @@ __global__ void __launch_bounds__(ST) k_bwd_level(Dev d, SnDev s, const FrontDes
   load_desc(&fd, dl + blockIdx.x);
   if (threadIdx.x == 0) s_to = s_lost = 0;
   __syncthreads();
-  if (d.ctl[fd.inst].status != ST_RUNNING) return;
+  if (!solve_on(d.ctl[fd.inst])) return;
   bwd_front(d, s, fd, smem_cap, &bar, &s_to, &s_lost, [] { __syncthreads(); });
   if (threadIdx.x == 0 && (s_to || s_lost)) atomicExch(s.timeout, 1);
 }
@@ -1122,7 +1122,7 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
     const int q = FWD ? k : nf - 1 - k;  // backward: parents first
     load_desc(&fd, dl + q);
     __syncthreads();
-    if (d.ctl[fd.inst].status == ST_RUNNING) {  // uniform over the block
+    if (solve_on(d.ctl[fd.inst])) {  // uniform over the block
       // started before the wait: the panel copy and the front's own values
       auto wait = [&] {
         if (tid == 0) {
@@ -1631,7 +1631,7 @@ constexpr int SBW = BIG_SBW;  // column block of the large-front solves (128)
 constexpr int SBT = BIG_SBT;  // threads per CTA (256)
 
 __device__ __forceinline__ bool big_active(const Dev& d, const FrontDesc& fd) {
-  return d.ctl[fd.inst].status == ST_RUNNING;
+  return solve_on(d.ctl[fd.inst]);
 }
 
 // f = P b on the pivot rows, 0 below, plus the children's update vectors

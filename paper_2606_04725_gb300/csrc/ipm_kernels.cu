@@ -146,21 +146,23 @@ __device__ __forceinline__ bool last_instance(const Dev& d) {
   return s_last != 0;
 }
 
-// any instance running / needing a factorization / searching (block-wide)
-__device__ __forceinline__ void any_flags(const Dev& d, int* run, int* fac, int* ls) {
-  __shared__ int f[3];
-  if (threadIdx.x < 3) f[threadIdx.x] = 0;
+// any instance running / needing a factorization / searching / in CG (block-wide)
+__device__ __forceinline__ void any_flags(const Dev& d, int* run, int* fac, int* ls, int* cg) {
+  __shared__ int f[4];
+  if (threadIdx.x < 4) f[threadIdx.x] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < d.n_inst; i += blockDim.x) {
     const Ctl& c = d.ctl[i];
     if (c.status == ST_RUNNING) atomicOr(&f[0], 1);
     if (c.need_factor) atomicOr(&f[1], 1);
     if (c.ls_active) atomicOr(&f[2], 1);
+    if (c.cg_active) atomicOr(&f[3], 1);
   }
   __syncthreads();
   *run = f[0];
   *fac = f[1];
   *ls = f[2];
+  *cg = f[3];
 }
 
 // Set the graph's conditions at the end of a step (block-wide) and count the
@@ -168,12 +170,18 @@ __device__ __forceinline__ void any_flags(const Dev& d, int* run, int* fac, int*
 // nodes: WHILE over iterations, IF on "still running", WHILE over inertia
 // corrections, WHILE over line-search trials.  Every loop also stops at a trip
 // limit, whatever the control state says, so a graph launch always ends.
-enum StepEnd { END_EVAL = 0, END_FACTOR = 1, END_DIR = 2, END_TRIAL = 3 };
+enum StepEnd { END_EVAL = 0, END_FACTOR = 1, END_DIR = 2, END_TRIAL = 3, END_CG0 = 4, END_CG = 5 };
 __device__ void set_conditions(const Dev& d, const CondArgs& ca, int kind) {
-  int run, fac, ls;
-  any_flags(d, &run, &fac, &ls);
+  int run, fac, ls, cg;
+  any_flags(d, &run, &fac, &ls, &cg);
   if (threadIdx.x != 0) return;
   int* ctr = ca.counters;
+  if (kind == END_CG0 || kind == END_CG) {  // the CG start, or a CG step (a trip)
+    if (ctr[3] >= ca.cap_cg) cg = 0;
+    cudaGraphSetConditional(ca.h_cg, cg ? 1u : 0u);
+    if (kind == END_CG) ++ctr[3];
+    return;
+  }
   if (kind == END_EVAL) {
     if (ctr[0] >= ca.cap_iter) run = 0;
     cudaGraphSetConditional(ca.h_run, run ? 1u : 0u);
@@ -233,6 +241,15 @@ __global__ void k_red_eval(Dev d, int max_iter, CondArgs ca) {
         v[0] = max_nn(v[0], fabs(r));
         v[6] += d.fvar[j];
       }
+    } else if (d.mc.kkt == 1) {
+      // HyKKT form: the equalities h = 0 themselves, multipliers lambda = wp
+      for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
+        const double h = d.h[r];
+        if (!fin(h)) v[10] += 1.0;
+        v[1] = max_nn(v[1], fabs(h));
+        v[4] += fabs(d.wp[r]);
+        v[9] += fabs(h);
+      }
     } else {
       for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
         const double h = d.h[r];
@@ -288,8 +305,11 @@ __device__ void ctl_pre_warp(const Dev& d, int i, int lane, int max_iter) {
   if (lane) return;
   const double dual = v[0], prim = v[1], cmax = v[2], cmin = v[3], sl = v[4], sz = v[5], f = v[6], th = v[9], nf = v[10];
   const double lg = logacc_value(v[7], v[8]);
-  const double mrows = d.inst_m[i], nz = d.inst_nz[i];
-  const double sd = fmax(S_MAX, (sl + sz) / (2.0 * mrows + nz)) / S_MAX;
+  // W&B eq. (5)'s scaling: s_d over the rows' multipliers (2m lifted, m HyKKT) and
+  // the bound multipliers (inst_nz counts the 2m slack bounds of the lifted rows)
+  const bool hy = d.mc.kkt == 1;
+  const double mrows = d.inst_m[i], nz = hy ? d.inst_nz[i] - 2.0 * mrows : (double)d.inst_nz[i];
+  const double sd = fmax(S_MAX, (sl + sz) / ((hy ? 1.0 : 2.0) * mrows + nz)) / S_MAX;
   const double sc = fmax(S_MAX, sz / nz) / S_MAX;
   c.E0 = fmax(fmax(dual / sd, prim), cmax / sc);
   c.E0u = fmax(fmax(dual, prim), cmax);
@@ -337,6 +357,15 @@ __global__ void k_zero_L(Dev d, const long long* inst_Lbeg, const long long* ins
 __device__ void rows_pre_at(const Dev& d, double* Drow, int r) {
   const Ctl& c = d.ctl[d.row_inst[r]];
   if (c.status != ST_RUNNING) return;
+  if (d.mc.kkt == 1) {
+    // HyKKT: K_gamma's weight gamma on every row, and v_r = lambda_r + gamma h_r,
+    // so that the right-hand side is g = a + gamma H^T c with a = -(grad phi_mu
+    // + H^T lambda), c = -h (the augmented first block row)
+    const double gh = d.mc.hy_gamma;
+    Drow[r] = gh;
+    d.rowv[r] = d.wp[r] + gh * d.h[r];
+    return;
+  }
   const double mu = c.mu, gam = d.mc.gamma;
   const double sp = d.sp[r], sm = d.sm[r], isp = d.isp[r], ism = d.ism[r];
   const double Qp = d.bp[r] * isp, Qm = d.bm[r] * ism;
@@ -512,7 +541,7 @@ __global__ void k_red_dir(Dev d, CondArgs ca) {
         }
         v[2] += gp * dy;
       }
-    } else {
+    } else if (d.mc.kkt != 1) {  // HyKKT: lambda's step is the CG iterate, no slacks
       for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
         recover_row(d, r);
         const double isp = d.isp[r], ism = d.ism[r];
@@ -580,7 +609,7 @@ __global__ void k_trial_point(Dev d) {
   } else if (t < d.n + d.m) {
     const int r = t - d.n;
     const Ctl& c = d.ctl[d.row_inst[r]];
-    if (c.ls_active) {
+    if (c.ls_active && d.mc.kkt != 1) {
       d.spt[r] = d.sp[r] + c.alpha * d.dsp[r];
       d.smt[r] = d.sm[r] + c.alpha * d.dsm[r];
     }
@@ -602,6 +631,12 @@ __global__ void k_red_trial(Dev d, CondArgs ca) {
         v[0] += d.fvart[j];
         if (fin(d.yL[j])) logacc_mul(v[1], v[2], y - d.yL[j]);
         if (fin(d.yU[j])) logacc_mul(v[1], v[2], d.yU[j] - y);
+      }
+    } else if (d.mc.kkt == 1) {  // HyKKT: theta = ||h||_1, no slack barrier terms
+      for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
+        const double h = d.ht[r];
+        if (!fin(h)) v[4] += 1.0;
+        v[3] += fabs(h);
       }
     } else {
       for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
@@ -693,6 +728,10 @@ __device__ void update_var(const Dev& d, int v) {
 __device__ void update_row(const Dev& d, int r) {
   const Ctl& c = d.ctl[d.row_inst[r]];
   if (c.phase != 1 || c.status != ST_RUNNING) return;
+  if (d.mc.kkt == 1) {  // HyKKT: lambda takes the primal step
+    d.wp[r] += c.alpha * d.dwp[r];
+    return;
+  }
   const double a = c.alpha, ad = c.alpha_dual, mu = c.mu;
   const double sp = d.spt[r], sm = d.smt[r];
   d.sp[r] = sp;
@@ -730,9 +769,176 @@ __device__ void ctl_post(const Dev& d, int i, Ctl& c, bool write) {
   c.phase = 0;
 }
 
+// ------------------------------------------------------------------ HyKKT
+// The Newton system with the equalities kept,
+//   [Wh  H^T] [dy  ]   [a]   a = -(grad phi_mu + H^T lambda), c = -h,
+//   [H   0  ] [dlam] = [c],  Wh = W + Sigma_y + delta_w I,
+// solved as the hybrid direct-iterative method that Sec. 3.2.2 cites
+// (Regev et al. 2023, after Golub & Greif 2003): with the factor of
+// K_gamma = Wh + gamma H^T H and g = a + gamma H^T c (k_rhs, rows_pre_at),
+//   u = K_gamma^-1 g,  S dlam = H u - c  with S = H K_gamma^-1 H^T  (CG),
+//   dy = K_gamma^-1 (g - H^T dlam).
+// Every instance runs its own CG (the batch's S is block diagonal) from
+// dlam = 0 until ||r||^2 <= cg_tol^2 ||r_0||^2, cg_max_iter steps, or
+// p^T S p <= 0.  One CG step:
+//   k_cg_apply  b = H^T (r + beta p)                       (variables)
+//   solves      b = K_gamma^-1 b, instances in CG only
+//   k_red_cg1   p = r + beta p, q = H b, alpha = r^T r / p^T q
+//   k_red_cg2   dlam += alpha p, r -= alpha q, beta = r'^T r' / r^T r, stop test
+// p's update happens in k_red_cg1 with the r and beta that k_cg_apply used.
+// Dot products are deterministic chunk reductions like the others.
+
+__device__ __forceinline__ double row_times_b(const Dev& d, int r) {  // (H b)_r, b in factor order
+  const int WH = d.mc.WH;
+  double s = 0.0;
+  for (int q = 0; q < WH; ++q) {
+    const int col = d.Hcol[(size_t)r * WH + q];
+    if (col >= 0) s += d.Hv[(size_t)r * WH + q] * d.b[d.perm[col]];
+  }
+  return s;
+}
+
+// control of instance i's CG after a dot product (warp 0 of the instance's
+// last chunk block): step 0 the start (r_0^T r_0), 1 alpha (p^T q), 2 beta and
+// the stop test (r^T r after the update)
+__device__ void ctl_cg_warp(const Dev& d, int i, int lane, int step) {
+  Ctl c = d.ctl[i];
+  if (c.status != ST_RUNNING || (step > 0 && !c.cg_active)) return;
+  double v[1] = {0.0};
+  const int op[1] = {0};
+  for (int q = d.inst_chunk_ptr[i] + lane; q < d.inst_chunk_ptr[i + 1]; q += 32) v[0] += d.red_cg[d.inst_chunk_list[q]];
+  warp_reduce<1>(v, op);
+  if (lane) return;
+  const double s = v[0];
+  if (step == 0) {
+    c.cg_rr = s;
+    c.cg_stop = d.mc.cg_tol * d.mc.cg_tol * s;
+    c.cg_beta = 0.0;
+    c.cg_it = 0;
+    c.cg_active = (s > c.cg_stop && d.mc.cg_max_iter > 0) ? 1 : 0;
+  } else if (step == 1) {
+    if (s > 0.0) c.cg_alpha = c.cg_rr / s;
+    else c.cg_active = 0;  // p^T S p <= 0 (or not finite): stop with the current dlam
+  } else {
+    c.cg_beta = s / c.cg_rr;
+    c.cg_rr = s;
+    c.cg_it++;
+    c.cg_total++;
+    c.cg_active = (s > c.cg_stop && c.cg_it < d.mc.cg_max_iter) ? 1 : 0;
+  }
+  c.solve_skip = c.cg_active ? 0 : 1;
+  d.ctl[i] = c;
+}
+
+// After u = K_gamma^-1 g (in b): r_0 = H u + h, p = 0 and dlam = 0, then r_0^T r_0
+__global__ void k_red_cg0(Dev d, CondArgs ca) {
+  const Chunk ch = d.chunks[blockIdx.x];
+  const Ctl& c = d.ctl[ch.inst];
+  if (c.status == ST_RUNNING && ch.kind == 1) {  // uniform over the block
+    double v[1] = {0.0};
+    const int op[1] = {0};
+    for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
+      const double t = row_times_b(d, r) + d.h[r];
+      d.cg_r[r] = t;
+      d.cg_p[r] = 0.0;
+      d.dwp[r] = 0.0;
+      v[0] += t * t;
+    }
+    block_reduce<1>(v, op);
+    if (threadIdx.x == 0) d.red_cg[blockIdx.x] = v[0];
+  } else if (threadIdx.x == 0) {
+    d.red_cg[blockIdx.x] = 0.0;
+  }
+  if (!last_of_instance(d, ch.inst)) return;
+  if (threadIdx.x < 32) ctl_cg_warp(d, ch.inst, threadIdx.x, 0);
+  if (ca.on && last_instance(d)) set_conditions(d, ca, END_CG0);
+}
+
+// b = H^T (r + beta p) in factor order, for the instances in CG
+__global__ void k_cg_apply(Dev d) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.n) return;
+  const Ctl& c = d.ctl[d.var_inst[v]];
+  if (c.status != ST_RUNNING || !c.cg_active) return;
+  const int WH = d.mc.WH;
+  const double beta = c.cg_beta;
+  double s = 0.0;
+  for (int q = d.Hcsc_ptr[v]; q < d.Hcsc_ptr[v + 1]; ++q) {
+    const int sl = d.Hcsc_slot[q], row = sl / WH;
+    s += d.Hv[sl] * (d.cg_r[row] + beta * d.cg_p[row]);
+  }
+  d.b[d.perm[v]] = s;
+}
+
+// p = r + beta p, q = H K^-1 H^T p (H times the solves' result), then p^T q
+__global__ void k_red_cg1(Dev d) {
+  const Chunk ch = d.chunks[blockIdx.x];
+  const Ctl& c = d.ctl[ch.inst];
+  if (c.status == ST_RUNNING && c.cg_active && ch.kind == 1) {  // uniform over the block
+    double v[1] = {0.0};
+    const int op[1] = {0};
+    const double beta = c.cg_beta;
+    for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
+      const double p = d.cg_r[r] + beta * d.cg_p[r];
+      const double q = row_times_b(d, r);
+      d.cg_p[r] = p;
+      d.cg_q[r] = q;
+      v[0] += p * q;
+    }
+    block_reduce<1>(v, op);
+    if (threadIdx.x == 0) d.red_cg[blockIdx.x] = v[0];
+  } else if (threadIdx.x == 0) {
+    d.red_cg[blockIdx.x] = 0.0;
+  }
+  if (!last_of_instance(d, ch.inst)) return;
+  if (threadIdx.x < 32) ctl_cg_warp(d, ch.inst, threadIdx.x, 1);
+}
+
+// dlam += alpha p, r -= alpha q, then r^T r and the stop test
+__global__ void k_red_cg2(Dev d, CondArgs ca) {
+  const Chunk ch = d.chunks[blockIdx.x];
+  const Ctl& c = d.ctl[ch.inst];
+  if (c.status == ST_RUNNING && c.cg_active && ch.kind == 1) {  // uniform over the block
+    double v[1] = {0.0};
+    const int op[1] = {0};
+    const double a = c.cg_alpha;
+    for (int r = ch.begin + threadIdx.x; r < ch.end; r += RED_CHUNK) {
+      d.dwp[r] += a * d.cg_p[r];
+      const double rn = d.cg_r[r] - a * d.cg_q[r];
+      d.cg_r[r] = rn;
+      v[0] += rn * rn;
+    }
+    block_reduce<1>(v, op);
+    if (threadIdx.x == 0) d.red_cg[blockIdx.x] = v[0];
+  } else if (threadIdx.x == 0) {
+    d.red_cg[blockIdx.x] = 0.0;
+  }
+  if (!last_of_instance(d, ch.inst)) return;
+  if (threadIdx.x < 32) ctl_cg_warp(d, ch.inst, threadIdx.x, 2);
+  if (ca.on && last_instance(d)) set_conditions(d, ca, END_CG);
+}
+
+// right-hand side of the final solve, g - H^T dlam = -(grad phi_mu + H^T (v + dlam))
+// with v = lambda + gamma h; every running instance solves again
+__global__ void k_hy_rhs(Dev d) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < d.n_inst) d.ctl[v].solve_skip = 0;  // no other thread of this launch reads that field
+  if (v >= d.n) return;
+  const Ctl& c = d.ctl[d.var_inst[v]];
+  if (c.status != ST_RUNNING) return;
+  const int WH = d.mc.WH;
+  double r1 = d.grad[v];
+  for (int q = d.Hcsc_ptr[v]; q < d.Hcsc_ptr[v + 1]; ++q) {
+    const int sl = d.Hcsc_slot[q], row = sl / WH;
+    r1 += d.Hv[sl] * (d.rowv[row] + d.dwp[row]);
+  }
+  r1 += c.mu * (d.igU[v] - d.igL[v]);
+  d.b[d.perm[v]] = -r1;
+}
+
 // flags[0] = any instance running, [1] = any needs a factorization,
-// [2] = any line search active
-__global__ void k_summary(Dev d, int* flags) {
+// [2] = any line search active (cg = 0) or any CG running (cg = 1)
+__global__ void k_summary(Dev d, int* flags, int cg) {
   __shared__ int f[3];
   if (threadIdx.x < 3) f[threadIdx.x] = 0;
   __syncthreads();
@@ -740,7 +946,7 @@ __global__ void k_summary(Dev d, int* flags) {
     const Ctl& c = d.ctl[i];
     if (c.status == ST_RUNNING) atomicOr(&f[0], 1);
     if (c.need_factor) atomicOr(&f[1], 1);
-    if (c.ls_active) atomicOr(&f[2], 1);
+    if (cg ? c.cg_active : c.ls_active) atomicOr(&f[2], 1);
   }
   __syncthreads();
   if (threadIdx.x < 3) flags[threadIdx.x] = f[threadIdx.x];

@@ -22,6 +22,10 @@ __device__ __forceinline__ double recip_nr(double d) {
   return fma(y, fma(e, e, e), y);
 }
 
+// The triangular solves work on an instance while it runs, except during a
+// HyKKT conjugate-gradient loop once that instance's CG has ended.
+__device__ __forceinline__ bool solve_on(const Ctl& c) { return c.status == ST_RUNNING && !c.solve_skip; }
+
 constexpr int TPB = 256;  // generic element-wise and per-instance launches
 constexpr int EW = 128;   // element-wise kernels: smaller blocks spread FP64 work over more SMs
 
@@ -48,7 +52,12 @@ __global__ void k_red_dir(Dev d, CondArgs ca);
 __global__ void k_trial_point(Dev d);
 __global__ void k_red_trial(Dev d, CondArgs ca);
 __global__ void k_update(Dev d);
-__global__ void k_summary(Dev d, int* flags);
+__global__ void k_summary(Dev d, int* flags, int cg);
+__global__ void k_red_cg0(Dev d, CondArgs ca);
+__global__ void k_cg_apply(Dev d);
+__global__ void k_red_cg1(Dev d);
+__global__ void k_red_cg2(Dev d, CondArgs ca);
+__global__ void k_hy_rhs(Dev d);
 
 // factor_kernels.cu
 __global__ void k_factor_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);

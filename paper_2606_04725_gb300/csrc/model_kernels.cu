@@ -272,7 +272,7 @@ __device__ void eval_row_at(const Dev& d, int r, int use_trial, int with_jac) {
   } else {
     if (c.status != ST_RUNNING) return;
     eval_row(d, d.y, r, d.h, with_jac ? d.Hv : nullptr);
-    if (with_jac) {  // reciprocals of the slacks and their duals, reused by every later kernel
+    if (with_jac && d.mc.kkt != 1) {  // reciprocals of the slacks and their duals, reused by every later kernel
       d.isp[r] = recip_nr(d.sp[r]);
       d.ism[r] = recip_nr(d.sm[r]);
       d.ibp[r] = recip_nr(d.bp[r]);
@@ -596,6 +596,14 @@ __global__ void k_init_rows(Dev d, int warm, double push) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= d.m) return;
   const double gam = d.mc.gamma;
+  if (d.mc.kkt == 1) {
+    // HyKKT form: the multipliers lambda (wp) start at 0 cold and are kept
+    // warm; wm stays 0 and the lifted slacks are unused (set to 1)
+    if (!warm) d.wp[r] = 0.0;
+    d.wm[r] = 0.0;
+    d.sp[r] = d.sm[r] = d.bp[r] = d.bm[r] = 1.0;
+    return;
+  }
   if (!warm) {
     d.sp[r] = fmax(gam - d.h[r], push);
     d.sm[r] = fmax(gam + d.h[r], push);

@@ -94,6 +94,7 @@ struct nmpc_handle {
   cudaGraphExec_t gexec = nullptr;
   bool graph_off = false;  // host-driven loop only (allocation-free one-shot solve)
   long long nodes_eval = 0, nodes_factor = 0, nodes_solve = 0, nodes_trial = 0, nodes_update = 0;
+  long long nodes_cg = 0, nodes_solve2 = 0;  // HyKKT: one CG step, the final solve and step limits
   CondArgs cond{};  // passed to the step-ending kernels; on only while the graph is captured
 };
 
@@ -216,6 +217,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   d.dy = cv.take<double>(n); d.dzL = cv.take<double>(n); d.dzU = cv.take<double>(n);
   d.dsp = cv.take<double>(m); d.dsm = cv.take<double>(m); d.dwp = cv.take<double>(m); d.dwm = cv.take<double>(m);
   d.dbp = cv.take<double>(m); d.dbm = cv.take<double>(m); d.rowv = cv.take<double>(m);
+  d.cg_r = d.dsp; d.cg_p = d.dsm; d.cg_q = d.dbp;  // HyKKT only, where these are unused
   d.yt = cv.take<double>(n); d.spt = cv.take<double>(m); d.smt = cv.take<double>(m); d.ht = cv.take<double>(m);
   d.fvart = cv.take<double>(n);
   d.perm = cv.take<int>(n); d.iperm = cv.take<int>(n); d.b = cv.take<double>(n);
@@ -223,6 +225,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   d.filt_th = cv.take<double>((size_t)ni * FILTER_CAP); d.filt_ph = cv.take<double>((size_t)ni * FILTER_CAP);
   d.chunks = cv.take<Chunk>(nch); d.inst_chunk_ptr = cv.take<int>(ni + 1); d.inst_chunk_list = cv.take<int>(nch);
   d.red_eval = cv.take<RedEval>(nch); d.red_dir = cv.take<RedDir>(nch); d.red_trial = cv.take<RedTrial>(nch);
+  d.red_cg = cv.take<double>(nch);
   d.tgt_L = cv.take<long long>(A.tgt_L.size()); d.tgt_diag = cv.take<int>(A.tgt_diag.size());
   d.tw_ptr = cv.take<int>(A.tw_ptr.size()); d.tw_idx = cv.take<int>(A.tw_idx.size());
   d.th_ptr = cv.take<int>(A.th_ptr.size()); d.th_a = cv.take<int>(A.th_a.size()); d.th_b = cv.take<int>(A.th_b.size());
@@ -232,7 +235,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   h->d_tgt_inst = cv.take<int>(A.tgt_L.size());
   h->d_Drow = cv.take<double>(m);
   h->d_inst_Lbeg = cv.take<long long>(ni); h->d_inst_Lend = cv.take<long long>(ni);
-  h->d_flags = cv.take<int>(16);  // [0..2] summary, [3] wait timeout, [4..7] adjoint norms, [8..10] graph trip counts
+  h->d_flags = cv.take<int>(16);  // [0..2] summary, [3] wait timeout, [4..7] adjoint norms, [8..11] graph trip counts
   h->d_stage = cv.take<double>((size_t)ni * (A.mc.nx + A.sp_stride + 1));
   h->d_inst_spoff = cv.take<int>(ni + 1);
   h->d_ctl_save = cv.take<Ctl>(ni);
@@ -278,8 +281,9 @@ cudaError_t up(const T* dst, const std::vector<T>& src, cudaStream_t st) {
   return cudaMemcpyAsync(const_cast<T*>(dst), src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
 }
 
-nmpc_status read_flags(nmpc_handle* h) {
-  k_summary<<<1, 256, 0, h->stream>>>(h->d, h->d_flags);
+// cg = 1: flag [2] says whether any HyKKT conjugate-gradient loop runs
+nmpc_status read_flags(nmpc_handle* h, int cg = 0) {
+  k_summary<<<1, 256, 0, h->stream>>>(h->d, h->d_flags, cg);
   ++h->launches;
   CUDA_TRY(h, cudaMemcpyAsync(h->h_flags, h->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -498,6 +502,8 @@ long long seq_factor(nmpc_handle* h) {
   return 3 + rhs + levels;
 }
 
+// Lifted-KKT: right-hand side, solves, recovery and step limits.  HyKKT:
+// right-hand side g, u = K^-1 g, and the CG start (seq_cg and seq_solve2 follow).
 long long seq_solve(nmpc_handle* h) {
   Dev& d = h->d;
   cudaStream_t st = h->stream;
@@ -508,10 +514,38 @@ long long seq_solve(nmpc_handle* h) {
     rhs = 1;
   }
   launch_solve(h);
-  k_red_dir<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);  // recovery, step limits, control
+  if (d.mc.kkt == 1) k_red_cg0<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);
+  else k_red_dir<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);  // recovery, step limits, control
   const long long levels = h->launches - l0;
   h->launches = l0;
   return 1 + rhs + levels;
+}
+
+// HyKKT: one conjugate-gradient step on S = H K^-1 H^T
+long long seq_cg(nmpc_handle* h) {
+  Dev& d = h->d;
+  cudaStream_t st = h->stream;
+  const long long l0 = h->launches;
+  k_cg_apply<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
+  launch_solve(h);
+  k_red_cg1<<<d.n_chunks, RED_CHUNK, 0, st>>>(d);
+  k_red_cg2<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);
+  const long long levels = h->launches - l0;
+  h->launches = l0;
+  return 3 + levels;
+}
+
+// HyKKT: dy = K^-1 (g - H^T dlam), then recovery and step limits
+long long seq_solve2(nmpc_handle* h) {
+  Dev& d = h->d;
+  cudaStream_t st = h->stream;
+  const long long l0 = h->launches;
+  k_hy_rhs<<<blocks_for(d.n, EW), EW, 0, st>>>(d);
+  launch_solve(h);
+  k_red_dir<<<d.n_chunks, RED_CHUNK, 0, st>>>(d, h->cond);
+  const long long levels = h->launches - l0;
+  h->launches = l0;
+  return 2 + levels;
 }
 
 long long seq_trial(nmpc_handle* h) {
@@ -560,6 +594,8 @@ cudaError_t capture_conditional(cudaStream_t cs, cudaGraphConditionalHandle hc, 
 //     IF any instance runs:
 //       WHILE any instance needs a factorization: assemble, factor, inertia test
 //       right-hand side, solves, step recovery, step limits (k_red_dir)
+//         (HyKKT: right-hand side, solves, CG start; WHILE any CG runs: one CG
+//          step; then the final right-hand side, solves, recovery, step limits)
 //       WHILE any line search is active: trial point, evaluate, filter test
 //       accept the step
 // The conditions are set on the device, so a solve needs no host round trip.
@@ -576,13 +612,16 @@ nmpc_status build_graph(nmpc_handle* h) {
   // (64 per step: far above what the inertia correction and the backtracking
   // can take before they stop by themselves)
   const int cap_iter = h->opt.max_iter + 2, cap_inner = 64 * cap_iter;
-  cudaGraphConditionalHandle h_run = 0, h_if = 0, h_fac = 0, h_ls = 0;  // one per conditional node
-  cudaGraph_t body_iter = nullptr, body_run = nullptr, body_fac = nullptr, body_ls = nullptr;
+  const int cap_cg = (std::max(0, h->opt.cg_max_iter) + 1) * cap_iter;
+  const bool hy = h->d.mc.kkt == 1;
+  cudaGraphConditionalHandle h_run = 0, h_if = 0, h_fac = 0, h_ls = 0, h_cg = 0;  // one per conditional node
+  cudaGraph_t body_iter = nullptr, body_run = nullptr, body_fac = nullptr, body_ls = nullptr, body_cg = nullptr;
   // the step-ending kernels set the conditions (restored to off below)
   if (e == cudaSuccess) { step = "handles"; e = cudaGraphConditionalHandleCreate(&h_run, g, 1, cudaGraphCondAssignDefault); }
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_if, g, 0, 0);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_fac, g, 0, 0);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_ls, g, 0, 0);
+  if (e == cudaSuccess && hy) e = cudaGraphConditionalHandleCreate(&h_cg, g, 0, 0);
   if (e == cudaSuccess) {
     cudaGraphNodeParams p = {};
     p.type = cudaGraphNodeTypeConditional;
@@ -594,7 +633,7 @@ nmpc_status build_graph(nmpc_handle* h) {
     e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
     if (e == cudaSuccess) body_iter = p.conditional.phGraph_out[0];
   }
-  h->cond = CondArgs{h_run, h_if, h_fac, h_ls, ctr, cap_iter, cap_inner, 1};
+  h->cond = CondArgs{h_run, h_if, h_fac, h_ls, h_cg, ctr, cap_iter, cap_inner, cap_cg, 1};
   // iteration body: evaluation (k_red_eval sets the conditions), then IF running
   if (e == cudaSuccess) step = "capture iteration body";
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body_iter, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
@@ -614,6 +653,13 @@ nmpc_status build_graph(nmpc_handle* h) {
     e = capture_conditional(cs, h_fac, cudaGraphCondTypeWhile, &body_fac);
     if (e == cudaSuccess) {
       h->nodes_solve = seq_solve(h);
+      if (hy) {
+        step = "CG WHILE node";
+        e = capture_conditional(cs, h_cg, cudaGraphCondTypeWhile, &body_cg);
+        if (e == cudaSuccess) h->nodes_solve2 = seq_solve2(h);
+      }
+    }
+    if (e == cudaSuccess) {
       step = "line-search WHILE node";
       e = capture_conditional(cs, h_ls, cudaGraphCondTypeWhile, &body_ls);
     }
@@ -628,6 +674,15 @@ nmpc_status build_graph(nmpc_handle* h) {
     h->nodes_factor = seq_factor(h);
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(cs, &out);
+  }
+  if (e == cudaSuccess && hy) {
+    step = "capture CG body";
+    e = cudaStreamBeginCaptureToGraph(cs, body_cg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      h->nodes_cg = seq_cg(h);
+      cudaGraph_t out = nullptr;
+      e = cudaStreamEndCapture(cs, &out);
+    }
   }
   if (e == cudaSuccess) step = "capture line-search body";
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, body_ls, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
@@ -680,6 +735,7 @@ void nmpc_options_defaults(nmpc_options* o) {
   o->push_cold = 1e-2; o->push_warm = 1e-9; o->max_iter = 200; o->ordering = NMPC_ORDER_AUTO;
   o->nd_leaf = 1; o->use_graph = 1; o->spin_limit = 10000000LL; o->pivtol = 1e-12;
   o->dw_max = 1e40;
+  o->kkt = NMPC_KKT_LIFTED; o->hykkt_gamma = 1e4; o->cg_tol = 1e-12; o->cg_max_iter = 200;
 }
 
 nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void* cuda_stream, nmpc_handle** out) {
@@ -704,7 +760,9 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
   sp.ordering = h->opt.ordering; sp.nd_leaf = h->opt.nd_leaf; sp.pivtol = h->opt.pivtol;
   sp.dw_max = h->opt.dw_max;
   sp.amalgamation = h->opt.amalgamation;
-  if (!(prob->dt > 0) || h->opt.max_iter < 1 || !(h->opt.tol > 0) || !(h->opt.gamma > 0) || !(h->opt.dw_max > 0)) {
+  if (!(prob->dt > 0) || h->opt.max_iter < 1 || !(h->opt.tol > 0) || !(h->opt.gamma > 0) || !(h->opt.dw_max > 0) ||
+      (h->opt.kkt != NMPC_KKT_LIFTED && h->opt.kkt != NMPC_KKT_HYKKT) ||
+      (h->opt.kkt == NMPC_KKT_HYKKT && (!(h->opt.hykkt_gamma > 0) || !(h->opt.cg_tol >= 0) || h->opt.cg_max_iter < 0))) {
     delete h;
     return NMPC_ERR_INVALID;
   }
@@ -714,6 +772,11 @@ nmpc_status nmpc_build(const nmpc_problem* prob, const nmpc_options* opts, void*
     delete h;
     return NMPC_ERR_INVALID;
   }
+  // the Newton-system form (the structure is the same for both)
+  h->A.mc.kkt = h->opt.kkt;
+  h->A.mc.hy_gamma = h->opt.hykkt_gamma;
+  h->A.mc.cg_tol = h->opt.cg_tol;
+  h->A.mc.cg_max_iter = h->opt.cg_max_iter;
   // per-level launch shapes
   const Analysis& A = h->A;
   h->lvl_ptr = A.level_ptr;
@@ -1146,18 +1209,20 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
       const nmpc_status gs = build_graph(h);
       if (gs != NMPC_OK) return gs;
     }
-    CUDA_TRY(h, cudaMemsetAsync(h->d_flags + 8, 0, 3 * sizeof(int), st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_flags + 8, 0, 4 * sizeof(int), st));
     CUDA_TRY(h, cudaGraphLaunch(h->gexec, st));
-    int ctr[4] = {0, 0, 0, 0};
-    CUDA_TRY(h, cudaMemcpyAsync(ctr, h->d_flags + 8, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(h, cudaMemcpyAsync(ctr + 3, h->d_flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int ctr[5] = {0, 0, 0, 0, 0};
+    CUDA_TRY(h, cudaMemcpyAsync(ctr, h->d_flags + 8, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaMemcpyAsync(ctr + 4, h->d_flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(h, cudaStreamSynchronize(st));
     // kernels the graph ran: outer steps x evaluation, running steps x (solve +
-    // update), factorization attempts, line-search trials
+    // update), factorization attempts, line-search trials, CG steps
     const long long running = std::max(0, ctr[0] - 1);
-    h->launches += (long long)ctr[0] * h->nodes_eval + running * (h->nodes_solve + h->nodes_update) +
-                   (long long)ctr[1] * h->nodes_factor + (long long)ctr[2] * h->nodes_trial;
-    if (ctr[3]) return fail(h, NMPC_TIMEOUT, "a bounded wait between the CTAs of a front factorization ran out");
+    h->launches += (long long)ctr[0] * h->nodes_eval +
+                   running * (h->nodes_solve + h->nodes_solve2 + h->nodes_update) +
+                   (long long)ctr[1] * h->nodes_factor + (long long)ctr[2] * h->nodes_trial +
+                   (long long)ctr[3] * h->nodes_cg;
+    if (ctr[4]) return fail(h, NMPC_TIMEOUT, "a bounded wait between the CTAs of a front factorization ran out");
   } else {
     for (int it = 0; it <= h->opt.max_iter + 1; ++it) {
       h->launches += seq_eval(h);
@@ -1173,6 +1238,19 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
       }
       h->launches += seq_solve(h);
       CUDA_TRY(h, cudaGetLastError());
+      if (d.mc.kkt == 1) {
+        // HyKKT: CG steps until every instance's CG has stopped (each stops
+        // after at most cg_max_iter steps), then the final solve
+        for (;;) {
+          rs = read_flags(h, 1);
+          if (rs != NMPC_OK) return rs;
+          if (!h->h_flags[2]) break;
+          h->launches += seq_cg(h);
+          CUDA_TRY(h, cudaGetLastError());
+        }
+        h->launches += seq_solve2(h);
+        CUDA_TRY(h, cudaGetLastError());
+      }
       rs = read_flags(h);
       if (rs != NMPC_OK) return rs;
       while (h->h_flags[2]) {
@@ -1199,6 +1277,7 @@ nmpc_status nmpc_solve(nmpc_handle* h, int warm, nmpc_info* info) {
       nmpc_info& o = info[i];
       o.status = stt; o.iters = c.iter; o.inertia_retries = c.inertia_retries; o.ls_trials = c.ls_trials;
       o.mu_final = c.mu; o.kkt_scaled = c.E0; o.kkt_unscaled = c.E0u; o.objective = c.f; o.ms_total = ms;
+      o.cg_iters = c.cg_total;
     }
   }
   return ret;
@@ -1264,6 +1343,7 @@ nmpc_status nmpc_sensitivity(nmpc_handle* h, int instance, const double* dloss_d
   const Analysis& A = h->A;
   if (instance < 0 || instance >= A.n_inst || !dloss_dy) return fail(h, NMPC_ERR_INVALID, "bad instance or gradient");
   if (!h->have_solution) return fail(h, NMPC_NOT_SOLVED, "no converged point");
+  if (A.mc.kkt != NMPC_KKT_LIFTED) return fail(h, NMPC_ERR_INVALID, "the adjoint needs the Lifted-KKT form");
   Dev& d = h->d;
   cudaStream_t st = h->stream;
   const int ni = A.n_inst, n = A.n, m = A.m;

@@ -50,6 +50,11 @@ struct Ctl {
   int inertia_retries, ls_trials, augment;
   int first;                          // first iteration of a solve
   int ls_trials0;                     // ls_trials at the start of this iteration's search
+  // HyKKT form: conjugate gradients on S dlam = t (S = H K^-1 H^T) of this iteration
+  double cg_rr, cg_stop, cg_alpha, cg_beta;  // r^T r, cg_tol^2 r_0^T r_0, step, p-update weight
+  int cg_active;                      // 1 while this instance's CG runs
+  int cg_it, cg_total;                // CG iterations of this Newton step / of the solve
+  int solve_skip;                     // 1: the triangular solves skip this instance (CG done)
 };
 
 constexpr int FILTER_CAP = 256;
@@ -73,6 +78,9 @@ struct ModelConst {
   double gamma, tol, pivtol;
   double dw_max;                      // largest delta_w of the inertia correction
   double Tb, qloss;                   // paper's plate: boundary temperature, heat loss
+  int kkt;                            // 0 Lifted-KKT, 1 HyKKT
+  int cg_max_iter;                    // HyKKT: CG iterations per Newton step at most
+  double hy_gamma, cg_tol;            // HyKKT: augmentation weight, CG relative tolerance
 };
 
 // Reduction chunks never straddle an instance.  kind 0: variables, 1: rows.
@@ -111,7 +119,9 @@ struct Dev {
   // parameters
   double* p_x0; double* p_sp; double* p_uprev;
   int sp_stride;        // setpoint values per instance
-  // iterate
+  // iterate.  In the HyKKT form wp holds the equality multipliers lambda and
+  // wm stays 0 (so wp - wm is the rows' multiplier in either form); sp, sm, bp
+  // and bm are not used.
   double *y, *zL, *zU, *sp, *sm, *wp, *wm, *bp, *bm;
   // evaluation
   double *grad, *h, *Hv, *Wv, *fvar;
@@ -120,8 +130,12 @@ struct Dev {
   const int* Hcol;
   const int* Hcsc_ptr; const int* Hcsc_slot;
   const int* Wadj_ptr; const int* Wadj_slot; const int* Wadj_other;
-  // direction
+  // direction (HyKKT: dwp is lambda's step, the CG iterate)
   double *dy, *dzL, *dzU, *dsp, *dsm, *dwp, *dwm, *dbp, *dbm;
+  // HyKKT CG residual, search direction and S p (m each; the storage of dsp,
+  // dsm and dbp, which that form does not use)
+  double *cg_r, *cg_p, *cg_q;
+  double* red_cg;       // per reduction chunk: partial sum of a CG dot product
   double* rowv;         // per-row scratch (H^T v products)
   // trial
   double *yt, *spt, *smt, *ht, *fvart;
@@ -157,9 +171,9 @@ struct Dev {
 // loop, which reads the control state itself).  counters: [0] outer steps,
 // [1] factorization attempts, [2] line-search trials; cap_*: trip limits.
 struct CondArgs {
-  unsigned long long h_run, h_if, h_fac, h_ls;
-  int* counters;
-  int cap_iter, cap_inner, on;
+  unsigned long long h_run, h_if, h_fac, h_ls, h_cg;
+  int* counters;        // [3]: CG iterations (HyKKT)
+  int cap_iter, cap_inner, cap_cg, on;
 };
 
 // One record per supernode, stored in level order, with everything a factor
