@@ -531,6 +531,22 @@ def paper_plate_resolves(P, dev, warmup=3, kkt=0):
     return out
 
 
+# DRAM bytes (read + write) of one k_factor_flow launch measured by ncu on the
+# first 64 instances of the batch (profiles/k_factor_flow_batch64_distillation_N34_T50_200.md),
+# with the flops of that case; the traffic grows with the instances as the flops do.
+FLOW64_DRAM_BYTES, FLOW64_FLOPS = 441.503744e6 + 350.516736e6, 1971262569.0
+
+
+def flow_traffic(opts, st):
+    """DRAM bytes per factorization for the schedule the capture was taken
+    with (nested dissection, leaves of one stage, sibling-limited supernodes,
+    the dataflow factorization), scaled to this batch by its flops; None for
+    any other schedule."""
+    same = (st["ordering_used"] == 2 and opts.nd_leaf == 1 and st["amalgamation_used"] == 2
+            and opts.factor_mode == 3)
+    return FLOW64_DRAM_BYTES * st["factor_flops"] / FLOW64_FLOPS if same else None
+
+
 def fp64_probe(P):
     """Measured FP64 rates of this GPU (library probe kernels): FMA chains and
     the f64 tensor-core mma.sync, four 256-thread blocks per SM."""
@@ -716,7 +732,7 @@ def main():
             "phases_ms": {k: ph[k] for k in ("ms_eval", "ms_assemble", "ms_factor", "ms_solve")},
             "hbm": hbm_rooflines(st, ph),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": flow_traffic(opts, st),
                          "kernel": "numeric factorization of the whole batch (the launches of one factorization)",
                          "flops_per_launch_set": st["factor_flops"],
                          "peak_basis": "152 SMs x 2 FP64 FMA/clock x max SM clock (nominal FP64 rate)",
