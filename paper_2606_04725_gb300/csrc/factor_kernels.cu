@@ -305,27 +305,30 @@ __device__ __forceinline__ int tri_lane(int r, int k) { return r * (r - 1) / 2 +
 // Factor pivot panel of this CTA: block columns jb .. kend-1 (pivots
 // jb .. jb+w-1) at local columns lc0 ..; the previous panel (Pl, Pw, width
 // wprev; wprev = 0 for none) is applied to the block first.  Expects 256
-// threads: warp 0 runs the pivot chain; warps 1-3 and 5-7 (the other three
-// sub-partitions) do the bulk work; warp 4 idles so that no bulk FP64
-// instruction shares warp 0's sub-partition.
+// threads: warp 0 runs the pivot chain; NB = 192: warps 1-3 and 5-7 (the
+// other three sub-partitions) do the bulk work and warp 4 idles, so that no
+// bulk FP64 instruction of this CTA shares warp 0's sub-partition (the
+// cluster kernel, one CTA per SM); NB = 224: warps 1-7 (the dataflow kernel,
+// whose second CTA on the SM shares that sub-partition anyway: measured 1%
+// faster there).
 // Warp 0 publishes each finished pivot column (W of the diagonal block and
 // 1/d_j) through the sentinel slots pub[j*PB + k] (pub[j*PB + j] = 1/d_j), so
 // the rows below are solved one column behind the chain instead of after it.
 constexpr int FCT = 256;
-constexpr int NBULK = 192;  // threads of warps 1-3, 5-7
-static_assert(NBULK == FCT - 64, "warps 0 and 4 are not bulk warps");
+constexpr int NBULK = 192;       // threads of warps 1-3, 5-7
+constexpr int NBULK_FLOW = 224;  // threads of warps 1-7
 
 // Lg/Wg receive the panel's L and W: entry (i, jb + jj) at Lg[i + (jb + jj - gc0) m]
 // and Wg[i + (jb + jj - gcw) m], i.e. 0 for a whole front's panel (in global
 // memory, or in place in Fl), jb for an m x PB buffer that holds this panel only.  extra(bt) runs on the bulk
-// threads (bt = 0 .. NBULK-1) while warp 0 runs the pivot chain, after the
+// threads (bt = 0 .. NB-1) while warp 0 runs the pivot chain, after the
 // previous panel has been applied to this one: work that touches neither
 // this panel's columns nor its buffers (the single-CTA front uses it for the
 // previous panel's update of the other columns).
 struct NoExtra {
   __device__ void operator()(int) const {}
 };
-template <class Extra = NoExtra>
+template <int NB = NBULK, class Extra = NoExtra>
 __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* thr, double* Lg, double* Wg,
                              const double* Pl, const double* Pw, int wprev, int m, int jb, int w, int lc0,
                              double* sB, double* pub, int* s_timeout, long long limit, int gc0, int gcw,
@@ -396,8 +399,9 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
       Wg[(jb + rB) + (size_t)(jb - gcw) * m] = b;
     }
     if (lane == 0 && bad) flag_fail(ctl);
-  } else if ((warp & 3) != 0) {
-    const int bt = ((warp < 4) ? warp - 1 : warp - 2) * 32 + lane;  // 0 .. NBULK-1
+  } else if (NB == FCT - 32 || (warp & 3) != 0) {
+    static_assert(NB == FCT - 32 || NB == FCT - 64, "bulk warps: 1-7, or 1-3 and 5-7");
+    const int bt = ((NB == FCT - 32 || warp < 4) ? warp - 1 : warp - 2) * 32 + lane;  // 0 .. NB-1
     if (warp == 1) {
       for (int t = lane; t < PB * PB; t += 32) pub[t] = __longlong_as_double(SENTINEL);
       // column 0 of the diagonal block: previous panel applied, handed to warp 0
@@ -412,7 +416,7 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
     if (wprev > 0) {
       // rows below the diagonal block: previous panel applied, one entry per thread
       const int rows = m - kend;
-      for (int t = bt; t < rows * nb; t += NBULK) {
+      for (int t = bt; t < rows * nb; t += NB) {
         const int kk = t / rows;
         const int i = kend + (t - kk * rows);
         double acc = Fp[i + (size_t)kk * m];
@@ -422,11 +426,11 @@ __device__ void panel_factor(Ctl* ctl, double* Fl, double* invd, const double* t
         Fp[i + (size_t)kk * m] = acc;
       }
     }
-    asm volatile("bar.sync 2, %0;" ::"r"(NBULK) : "memory");
+    asm volatile("bar.sync 2, %0;" ::"r"(NB) : "memory");
     extra(bt);
     // rows below the pivot block, one column behind the chain:
     // l_ij = (F_ij - sum_{k<j} l_ik W_jk) / d_j
-    for (int i = jb + w + bt; i < m; i += NBULK) {
+    for (int i = jb + w + bt; i < m; i += NB) {
       double f[PB];
 #pragma unroll
       for (int k = 0; k < PB; ++k) f[k] = (k < w) ? Fp[i + (size_t)k * m] : 0.0;
@@ -1186,13 +1190,11 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
 // TR x TC output tile per thread, the columns applied in ascending order: the
 // same rounding as a panel-by-panel trailing update.  Fl: m x c pivot columns
 // (W, ld m); Lu: L of the update rows (mu x c, ld mu), W times the reciprocal
-// pivot as the panels formed it; U0: packed lower triangle of the mu x mu
-// update block; Up: output (ld mu, lower triangle).
+// pivot as the panels formed it; Up: the children's part on entry and the
+// update matrix on return (global memory, ld mu, lower triangle).
 template <int TR, int TC>
-__device__ __forceinline__ void schur_tiles(const double* Fl, const double* Lu, const double* U0, double* Up, int m,
-                                            int c) {
+__device__ __forceinline__ void schur_tiles(const double* Fl, const double* Lu, double* Up, int m, int c) {
   const int mu = m - c, tid = threadIdx.x, nt = blockDim.x;
-  auto upk = [&](int a, int b) { return (size_t)b * mu - (size_t)b * (b - 1) / 2 + (a - b); };
   const int nr = (mu + TR - 1) / TR, ncb = (mu + TC - 1) / TC;
   // the tiles (ta, tb) that reach the lower triangle, TR ta + TR - 1 >= TC tb,
   // column block by column block: column block tb starts at row block lo(tb)
@@ -1210,7 +1212,7 @@ __device__ __forceinline__ void schur_tiles(const double* Fl, const double* Lu, 
 #pragma unroll
       for (int q = 0; q < TC; ++q) {
         const int a = a0 + r, b = b0 + q;
-        acc[r][q] = (a < mu && b <= a) ? U0[upk(a, b)] : 0.0;
+        acc[r][q] = (a < mu && b <= a) ? Up[a + (size_t)b * mu] : 0.0;
       }
     const double* col = Fl + c;
     const double* lcol = Lu;
@@ -1238,8 +1240,7 @@ __device__ __forceinline__ void schur_tiles(const double* Fl, const double* Lu, 
 // The largest tiles that still give every thread of the block an output
 // tile (FP64 latency is hidden across warps, and larger tiles form fewer L
 // values per multiply-add).
-__device__ __noinline__ void schur_update(const double* Fl, double* Lu, const double* U0, const double* invd, double* Up,
-                                          int m, int c) {
+__device__ __noinline__ void schur_update(const double* Fl, double* Lu, const double* invd, double* Up, int m, int c) {
   const int mu = m - c, nt = blockDim.x;
   auto tiles = [&](int tr, int tc) {  // tiles reaching the lower triangle
     const int nr = (mu + tr - 1) / tr, ncb = (mu + tc - 1) / tc;
@@ -1253,9 +1254,9 @@ __device__ __noinline__ void schur_update(const double* Fl, double* Lu, const do
     Lu[t] = Fl[(c + a) + (size_t)j * m] * invd[j];
   }
   __syncthreads();
-  if (tiles(4, 4) >= nt) schur_tiles<4, 4>(Fl, Lu, U0, Up, m, c);
-  else if (tiles(2, 4) >= nt) schur_tiles<2, 4>(Fl, Lu, U0, Up, m, c);
-  else schur_tiles<2, 2>(Fl, Lu, U0, Up, m, c);
+  if (tiles(4, 4) >= nt) schur_tiles<4, 4>(Fl, Lu, Up, m, c);
+  else if (tiles(2, 4) >= nt) schur_tiles<2, 4>(Fl, Lu, Up, m, c);
+  else schur_tiles<2, 2>(Fl, Lu, Up, m, c);
 }
 
 __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd, const int* flags, int nf,
@@ -1266,14 +1267,16 @@ __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd,
   const double* kd = s.Kdiag + fd.first;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int cp = (c + PB - 1) / PB * PB, npan = cp / PB;
+  // shared memory: the pivot columns, then the panel buffers of phase 1, whose
+  // space L of the update rows takes in phase 2; the update block itself is
+  // accumulated in its global matrix Up (L2-resident), which keeps a block
+  // small enough for three per SM
   double* Fl = dsm;                                  // m x cp, ld m: the pivot columns (W once factored)
-  double* U0 = Fl + (size_t)m * cp;                  // mu (mu + 1) / 2: update block, packed lower triangle
-  double* Lu = U0 + (size_t)mu * (mu + 1) / 2;       // mu x c: L of the update rows (phase 2)
-  double* Lb = Lu + (size_t)mu * c;                  // 2 x (m x PB): L of the even / odd panels
-  double* thr = Lb + 2 * (size_t)m * PB;             // cp
+  double* Lb = Fl + (size_t)m * cp;                  // 2 x (m x PB): L of the even / odd panels (phase 1)
+  double* Lu = Lb;                                   // mu x c: L of the update rows (phase 2)
+  double* thr = Lb + ((size_t)mu * c > 2 * (size_t)m * PB ? (size_t)mu * c : 2 * (size_t)m * PB);  // cp
   double* invd = thr + cp;                           // cp
   auto bL = [&](int q) { return Lb + (size_t)(q & 1) * m * PB; };
-  auto upk = [&](int a, int b) { return (size_t)b * mu - (size_t)b * (b - 1) / 2 + (a - b); };  // a >= b, packed
   // ---- the pivot columns from the condensed values (m x c, ld m), the update block zero
   for (int t0 = tid; t0 < m * cp; t0 += 4 * nt) {
     double v[4];
@@ -1286,7 +1289,11 @@ __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd,
     for (int u = 0; u < 4; ++u)
       if (t0 + u * nt < m * cp) Fl[t0 + u * nt] = v[u];
   }
-  for (int t = tid; t < mu * (mu + 1) / 2; t += nt) U0[t] = 0.0;
+  for (int t = tid; t < mu * (mu + 1) / 2; t += nt) {  // the update block's lower triangle, zero
+    const int b = tri_col(t, mu);
+    const int a = b + (t - (b * mu - b * (b - 1) / 2));
+    Up[a + (size_t)b * mu] = 0.0;
+  }
   for (int k = tid; k < cp; k += nt) thr[k] = (k < c) ? s.pivtol * fabs(kd[k]) : 0.0;
   // ---- children: wait for their completion, then add their update matrices,
   // entries of a pivot column to Fl and the others to the update block
@@ -1308,7 +1315,7 @@ __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd,
       const int ra = ch.rel[a], rb = ch.rel[b];  // ra >= rb
       const double v = __ldcg(ch.U + a + (size_t)b * mc);  // written by another block
       if (rb < c) Fl[ra + (size_t)rb * m] += v;
-      else U0[upk(ra - c, rb - c)] += v;
+      else Up[(ra - c) + (size_t)(rb - c) * mu] += v;  // this block's own matrix: plain accesses
     }
     __syncthreads();
   }
@@ -1316,7 +1323,7 @@ __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd,
   // (panel_factor; W of each panel in place in Fl, L in a panel buffer and
   // then in the factor), the panels' update of later pivot columns
   if (npan > 0)
-    panel_factor(ctl, Fl, invd, thr, bL(0), Fl, nullptr, nullptr, 0, m, 0, min(PB, c), 0, sB, s_pubv, s_to, limit,
+    panel_factor<NBULK_FLOW>(ctl, Fl, invd, thr, bL(0), Fl, nullptr, nullptr, 0, m, 0, min(PB, c), 0, sB, s_pubv, s_to, limit,
                  0, 0);
   for (int p = 0; p < npan; ++p) {
     const int jb = p * PB, w = min(PB, c - jb);
@@ -1341,8 +1348,8 @@ __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd,
       // lookahead: the next panel gets this panel's update and is factored,
       // while the bulk warps finish this panel (the chain does not wait for it)
       const int k0 = nx * PB;
-      panel_factor(ctl, Fl, invd + k0, thr + k0, bL(nx), Fl, Pl, Pw, w, m, k0, min(PB, c - k0), k0, sB, s_pubv,
-                   s_to, limit, k0, 0, [&](int bt) { finish(bt, NBULK); });
+      panel_factor<NBULK_FLOW>(ctl, Fl, invd + k0, thr + k0, bL(nx), Fl, Pl, Pw, w, m, k0, min(PB, c - k0), k0, sB,
+                               s_pubv, s_to, limit, k0, 0, [&](int bt) { finish(bt, NBULK_FLOW); });
     } else {
       finish(tid, nt);
       __syncthreads();
@@ -1350,10 +1357,10 @@ __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd,
   }
   // ---- phase 2: the update matrix U = (children's part) - L21 D L21^T for
   // the parent (schur_update)
-  schur_update(Fl, Lu, U0, invd, Up, m, c);
+  schur_update(Fl, Lu, invd, Up, m, c);
 }
 
-__global__ void __launch_bounds__(FCT, 2) k_factor_flow(Dev d, SnDev s, const FrontDesc* dl, int nf, int* flags) {
+__global__ void __launch_bounds__(FCT, 3) k_factor_flow(Dev d, SnDev s, const FrontDesc* dl, int nf, int* flags) {
   __shared__ FrontDesc fd;
   __shared__ int s_q, s_to, s_any_to;
   __shared__ double s_pubv[PB * PB];

@@ -106,12 +106,11 @@ constexpr int CLUSTER_THREADS = 256;  // per CTA of the cluster-cooperative fron
 constexpr int CLUSTER_PB = 8;         // column block of the cluster kernel (PB in factor_kernels.cu)
 constexpr int FLOW_SMEM_CAP_BYTES = 220 * 1024;  // dynamic shared memory of a k_factor_flow block
 // shared memory (doubles) of k_factor_flow for a front of m rows and c pivot
-// columns: the pivot columns rounded up to whole panels, the packed update
-// block, L of the update rows, two L panel buffers, thresholds and
-// reciprocal pivots
+// columns: the pivot columns rounded up to whole panels, two L panel buffers
+// or (later) L of the update rows, thresholds and reciprocal pivots
 long long flow_need(long long m, long long c) {
   const long long cp = (c + CLUSTER_PB - 1) / CLUSTER_PB * CLUSTER_PB, mu = m - c;
-  return m * cp + mu * (mu + 1) / 2 + mu * c + 2 * m * CLUSTER_PB + 2 * cp;
+  return m * cp + std::max(mu * c, 2 * m * CLUSTER_PB) + 2 * cp;
 }
 constexpr int SENS_REFINE = 6;        // refinement sweeps of the adjoint solve
 
