@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = [os.path.join(_HERE, f) for f in ("nmpc_oracle.c", "nmpc_oracle.h", "or_model.inc")]
+_SOURCES = [os.path.join(_HERE, f) for f in ("nmpc_oracle.c", "nmpc_oracle.h", "or_model.inc", "or_sparse.inc")]
 _lock = threading.Lock()
 _lib = None
 
@@ -55,7 +55,8 @@ class _Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("gamma", C.c_double), ("mu0_cold", C.c_double),
                 ("mu0_warm", C.c_double), ("push_cold", C.c_double), ("push_warm", C.c_double),
                 ("max_iter", C.c_int), ("pivtol", C.c_double), ("dw_max", C.c_double),
-                ("kkt", C.c_int), ("hy_gamma", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int)]
+                ("kkt", C.c_int), ("hy_gamma", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int),
+                ("linsolve", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -93,6 +94,9 @@ def lib():
                                          C.c_double, C.c_double, C.POINTER(_State)]
             L.or_band_cholesky.argtypes = [C.c_int, C.c_int, _D]
             L.or_symbolic.argtypes = [C.c_int, _I, _I, _I, _I, _I, C.c_int]
+            L.or_nd_order.argtypes = [C.c_int, _I, _I, C.c_int, _I]
+            L.or_sparse_cholesky.argtypes = [C.c_int, _I, _I, _D, C.c_int, C.c_double, _I, _D,
+                                             C.POINTER(C.c_long)]
             _lib = L
     return _lib
 
@@ -110,6 +114,9 @@ INF = float("inf")
 # Newton-system forms: Lifted-KKT (eq. liftedkkt-pd) and HyKKT (Sec. 3.2.2's
 # alternative: equalities kept, augmented-Lagrangian Cholesky plus CG).
 KKT_LIFTED, KKT_HYKKT = 0, 1
+# Factorization of the condensed matrix: band Cholesky in stage order, or the
+# sparse Cholesky after the oracle's own nested-dissection ordering.
+LINSOLVE_BAND, LINSOLVE_SPARSE = 0, 1
 HY_GAMMA, CG_TOL, CG_MAX_ITER = 1e4, 1e-12, 200
 
 
@@ -265,7 +272,7 @@ def steady_state(prob, u):
 def default_options(**kw):
     o = dict(tol=1e-8, gamma=1e-8, mu0_cold=0.1, mu0_warm=1e-8, push_cold=1e-2, push_warm=1e-9,
              max_iter=200, pivtol=1e-12, dw_max=1e40, kkt=KKT_LIFTED, hy_gamma=HY_GAMMA, cg_tol=CG_TOL,
-             cg_max_iter=CG_MAX_ITER)
+             cg_max_iter=CG_MAX_ITER, linsolve=LINSOLVE_BAND)
     o.update(kw)
     return o
 
@@ -370,3 +377,37 @@ def symbolic(n, colptr, rowidx):
     Li = np.empty(cap, dtype=np.int32)
     nnz = lib().or_symbolic(n, _ip(colptr), _ip(rowidx), _ip(parent), _ip(Lp), _ip(Li), cap)
     return parent, Lp, Li[:nnz]
+
+
+def nd_order(xadj, adj, leaf=64):
+    """Nested-dissection order of a symmetric graph (adjacency without self
+    loops): perm[k] = the vertex numbered k."""
+    xadj = np.ascontiguousarray(xadj, dtype=np.int32)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    n = len(xadj) - 1
+    perm = np.empty(n, dtype=np.int32)
+    lib().or_nd_order(n, _ip(xadj), _ip(adj), int(leaf), _ip(perm))
+    return perm
+
+
+def sparse_cholesky(K, use_nd=True, tol=0.0, b=None):
+    """Sparse Cholesky of the symmetric dense matrix K (its lower triangle's
+    nonzeros form the pattern), after nested dissection or in natural order.
+    Returns (rc, perm, x, nnzL): rc 0 on success or j+1 for the first failing
+    pivot j in the permuted order, x = K^-1 b when b is given and rc == 0."""
+    K = np.asarray(K, dtype=np.float64)
+    n = K.shape[0]
+    cols, rows, vals = [], [], []
+    colptr = np.zeros(n + 1, dtype=np.int32)
+    for j in range(n):
+        r = np.nonzero(K[j:, j])[0] + j
+        rows.append(r); vals.append(K[r, j])
+        colptr[j + 1] = colptr[j] + len(r)
+    rowidx = np.ascontiguousarray(np.concatenate(rows) if rows else np.zeros(0), dtype=np.int32)
+    v = np.ascontiguousarray(np.concatenate(vals) if vals else np.zeros(0), dtype=np.float64)
+    perm = np.empty(n, dtype=np.int32)
+    x = None if b is None else np.array(b, dtype=np.float64)
+    nnz = C.c_long()
+    rc = lib().or_sparse_cholesky(n, _ip(colptr), _ip(rowidx), _dp(v), int(bool(use_nd)), float(tol),
+                                   _ip(perm), None if x is None else _dp(x), C.byref(nnz))
+    return rc, perm, x, nnz.value

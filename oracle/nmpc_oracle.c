@@ -9,7 +9,10 @@
  * Linear algebra: the condensed Lifted-KKT matrix is assembled as a symmetric
  * band matrix in the natural stage order and factored by a textbook banded
  * Cholesky (no reordering, no supernodes).  Success of the Cholesky is the
- * inertia test of eq. (infiniteOCP-inertia).
+ * inertia test of eq. (infiniteOCP-inertia).  With options.linsolve = 1 the
+ * same matrix goes to a plain sparse Cholesky after a nested-dissection
+ * ordering of the oracle's own (or_sparse.inc), for plates whose band is too
+ * wide; the arithmetic per entry and the pivot test are the same.
  *
  * HyKKT form (options.kkt = 1), the alternative to Lifted-KKT that Sec. 3.2.2
  * names, after the hybrid direct-iterative method it cites (Regev et al.
@@ -434,52 +437,89 @@ static void band_solve(int n, int b, const double* band, double* x) {
 
 /* ------------------------------------------------------ SymCholesky */
 
+static int cmp_int(const void* a, const void* b) {
+  const int x = *(const int*)a, y = *(const int*)b;
+  return (x > y) - (x < y);
+}
+
 /* Symbolic factorization as described in Sec. 3.2.3: the parent of column j
  * in the elimination tree is the first off-diagonal row of column j of L, and
  * the structure of column j of L is the structure of column j of the (lower)
  * matrix united with the structures of its children, without the child's own
- * row.  Columns are processed in increasing order so children come first.
+ * row.  Columns are processed in increasing order so children come first; each
+ * column joins its parent's list of children once its structure is known.
  * Input: lower-triangular pattern in CSC (diagonal optional, rows sorted or
- * not).  Output: parent (-1 = root) and the pattern of L (CSC, rows sorted,
- * diagonal included).  Returns nnz(L), or -1 if cap is too small. */
-int or_symbolic(int n, const int* colptr, const int* rowidx, int* parent,
-                int* Lcolptr, int* Lrowidx, int cap) {
-  char* mark = calloc(n, 1);
-  int** cols = malloc(sizeof(int*) * n);
-  int* cnt = calloc(n, sizeof(int));
-  int total = 0, ok = 1;
-  for (int j = 0; j < n; ++j) {
-    memset(mark, 0, n);
-    mark[j] = 1;
-    for (int e = colptr[j]; e < colptr[j + 1]; ++e) if (rowidx[e] > j) mark[rowidx[e]] = 1;
-    for (int c = 0; c < j; ++c) {
-      if (parent[c] != j) continue;
-      for (int q = 0; q < cnt[c]; ++q) if (cols[c][q] > j) mark[cols[c][q]] = 1;
-    }
+ * not).  Output: parent (-1 = root) and the pattern of L as malloc'd CSC
+ * arrays (rows sorted, diagonal included).  Returns nnz(L), or -1 if out of
+ * memory or above the int range. */
+static long symbolic_alloc(int n, const int* colptr, const int* rowidx, int* parent,
+                           int** Lcolptr, int** Lrowidx) {
+  const int nn = n > 0 ? n : 1;
+  int* mark = malloc(sizeof(int) * nn);
+  int* child = malloc(sizeof(int) * nn);  /* first child of each column */
+  int* sib = malloc(sizeof(int) * nn);    /* next child of the same parent */
+  int** cols = calloc(nn, sizeof(int*));
+  int* cnt = calloc(nn, sizeof(int));
+  int* buf = malloc(sizeof(int) * nn);
+  long total = 0;
+  int ok = mark && child && sib && cols && cnt && buf;
+  for (int j = 0; ok && j < n; ++j) { mark[j] = -1; child[j] = -1; }
+  for (int j = 0; ok && j < n; ++j) {
     int k = 0;
-    for (int i = j; i < n; ++i) k += mark[i];
-    cols[j] = malloc(sizeof(int) * k);
-    cnt[j] = 0;
-    parent[j] = -1;
-    for (int i = j; i < n; ++i) if (mark[i]) {
-      cols[j][cnt[j]++] = i;
-      if (i > j && parent[j] < 0) parent[j] = i;
+    buf[k++] = j;
+    mark[j] = j;
+    for (int e = colptr[j]; e < colptr[j + 1]; ++e) {
+      const int i = rowidx[e];
+      if (i > j && mark[i] != j) { mark[i] = j; buf[k++] = i; }
     }
+    for (int c = child[j]; c >= 0; c = sib[c])
+      for (int q = 0; q < cnt[c]; ++q) {
+        const int i = cols[c][q];
+        if (i > j && mark[i] != j) { mark[i] = j; buf[k++] = i; }
+      }
+    qsort(buf, k, sizeof(int), cmp_int);
+    cols[j] = malloc(sizeof(int) * k);
+    if (!cols[j]) { ok = 0; break; }
+    memcpy(cols[j], buf, sizeof(int) * k);
+    cnt[j] = k;
+    parent[j] = k > 1 ? buf[1] : -1;
+    if (k > 1) { sib[j] = child[buf[1]]; child[buf[1]] = j; }
     total += k;
   }
-  if (total > cap) ok = 0;
+  if (total > 2147483647L) ok = 0;
+  if (ok) {
+    *Lcolptr = malloc(sizeof(int) * (nn + 1));
+    *Lrowidx = malloc(sizeof(int) * (total > 0 ? total : 1));
+    ok = *Lcolptr && *Lrowidx;
+  }
   if (ok) {
     int e = 0;
     for (int j = 0; j < n; ++j) {
-      Lcolptr[j] = e;
-      for (int q = 0; q < cnt[j]; ++q) Lrowidx[e++] = cols[j][q];
+      (*Lcolptr)[j] = e;
+      memcpy(*Lrowidx + e, cols[j], sizeof(int) * cnt[j]);
+      e += cnt[j];
     }
-    Lcolptr[n] = e;
+    (*Lcolptr)[n] = e;
   }
-  for (int j = 0; j < n; ++j) free(cols[j]);
-  free(cols); free(cnt); free(mark);
+  for (int j = 0; cols && j < n; ++j) free(cols[j]);
+  free(cols); free(cnt); free(mark); free(child); free(sib); free(buf);
   return ok ? total : -1;
 }
+
+/* or_symbolic: the same into caller arrays; returns nnz(L), or -1 if cap is
+ * too small. */
+int or_symbolic(int n, const int* colptr, const int* rowidx, int* parent,
+                int* Lcolptr, int* Lrowidx, int cap) {
+  int *Lp = NULL, *Li = NULL;
+  const long total = symbolic_alloc(n, colptr, rowidx, parent, &Lp, &Li);
+  if (total < 0 || total > cap) { free(Lp); free(Li); return -1; }
+  memcpy(Lcolptr, Lp, sizeof(int) * (n + 1));
+  memcpy(Lrowidx, Li, sizeof(int) * total);
+  free(Lp); free(Li);
+  return (int)total;
+}
+
+#include "or_sparse.inc"
 
 /* ------------------------------------------------------ interior point */
 
@@ -514,7 +554,62 @@ typedef struct {
   double *band, *rhs, *lam, *tmp;
   double *gv, *cg_r, *cg_p, *cg_q, *cg_x; /* HyKKT: right-hand side g (n), CG vectors (m) */
   int nL, nU;
+  int sparse;      /* options.linsolve = 1: K in the sparse factor below, band unused */
+  sp_factor spf;
 } work;
+
+static int cmp_long(const void* a, const void* b) {
+  const long x = *(const long*)a, y = *(const long*)b;
+  return (x > y) - (x < y);
+}
+
+/* Lower pattern of K = W + Sigma_y + delta_w I + H^T D H as CSC without
+ * duplicates: the Hessian triplets, the diagonal and every pair of columns
+ * of one Jacobian row.  Sets up the sparse factor on it. */
+static int sparse_init(work* w, int cnt) {
+  const int n = w->n, m = w->m;
+  long np = (long)cnt + n;
+  for (int r = 0; r < m; ++r) { const long k = w->rp[r + 1] - w->rp[r]; np += k * (k + 1) / 2; }
+  long* key = malloc(sizeof(long) * np);
+  if (!key) return -1;
+  long q = 0;
+  for (int t = 0; t < cnt; ++t) key[q++] = (long)w->tc[t] * n + w->tr[t];
+  for (int i = 0; i < n; ++i) key[q++] = (long)i * n + i;
+  for (int r = 0; r < m; ++r)
+    for (int a = w->rp[r]; a < w->rp[r + 1]; ++a)
+      for (int c = w->rp[r]; c <= a; ++c) key[q++] = (long)w->ci[c] * n + w->ci[a];
+  qsort(key, np, sizeof(long), cmp_long);
+  int* colptr = calloc(n + 1, sizeof(int));
+  int* rowidx = malloc(sizeof(int) * np);
+  long u = 0;
+  for (long e = 0; e < np; ++e) {
+    if (e > 0 && key[e] == key[e - 1]) continue;
+    ++colptr[key[e] / n + 1];
+    rowidx[u++] = (int)(key[e] % n);
+  }
+  for (int j = 0; j < n; ++j) colptr[j + 1] += colptr[j];
+  free(key);
+  const int rc = sp_setup(&w->spf, n, colptr, rowidx, 1);
+  free(colptr); free(rowidx);
+  return rc;
+}
+
+/* add v to K(i, j), i >= j */
+static inline void kadd(work* w, int i, int j, double v) {
+  if (w->sparse) sp_add(&w->spf, i, j, v);
+  else w->band[(size_t)j * (w->b + 1) + (i - j)] += v;
+}
+
+/* factor K in place with the inertia test's pivot tolerance; 0 on success */
+static int kfactor(work* w, double tol) {
+  return w->sparse ? sp_cholesky_tol(&w->spf, tol) : band_cholesky_tol(w->n, w->b, w->band, tol);
+}
+
+/* x <- K^-1 x with the factor of kfactor */
+static void ksolve(work* w, double* x) {
+  if (w->sparse) sp_solve(&w->spf, x);
+  else band_solve(w->n, w->b, w->band, x);
+}
 
 static int work_init(work* w, const or_problem* p, const or_options* o) {
   memset(w, 0, sizeof(*w));
@@ -544,19 +639,22 @@ static int work_init(work* w, const or_problem* p, const or_options* o) {
   for (int t = 0; t < cnt; ++t) if (w->tr[t] - w->tc[t] > b) b = w->tr[t] - w->tc[t];
   w->b = b;
   free(y0);
-  w->band = malloc(sizeof(double) * (size_t)(b + 1) * n);
+  w->sparse = o->linsolve == 1;
+  if (w->sparse) { if (sparse_init(w, cnt) != 0) return -1; }
+  else w->band = malloc(sizeof(double) * (size_t)(b + 1) * n);
   w->rhs = malloc(sizeof(double) * n);
   w->tmp = malloc(sizeof(double) * (n > m ? n : m));
   w->gv = malloc(sizeof(double) * n);
   w->cg_r = malloc(sizeof(double) * m); w->cg_p = malloc(sizeof(double) * m);
   w->cg_q = malloc(sizeof(double) * m); w->cg_x = malloc(sizeof(double) * m);
-  return (w->band && w->rhs && w->gv && w->cg_r && w->cg_p && w->cg_q && w->cg_x) ? 0 : -1;
+  return ((w->band || w->sparse) && w->rhs && w->gv && w->cg_r && w->cg_p && w->cg_q && w->cg_x) ? 0 : -1;
 }
 
 static void work_free(work* w) {
   free(w->yL); free(w->yU); free(w->grad); free(w->h); free(w->Hv); free(w->rp); free(w->ci);
   free(w->lam); free(w->tr); free(w->tc); free(w->tv); free(w->band); free(w->rhs); free(w->tmp);
   free(w->gv); free(w->cg_r); free(w->cg_p); free(w->cg_q); free(w->cg_x);
+  if (w->sparse) sp_free(&w->spf);
 }
 
 static void eval_all(work* w, const double* y) {
@@ -681,29 +779,30 @@ static void merit_of(work* w, const double* y, const double* sp, const double* s
   else merit(w, y, sp, sm, f, h, mu, phi, theta);
 }
 
-/* Assemble K_c = W + Sigma_y + delta_w I + H^T (Q+ + Q-) H into band storage
- * (eq. liftedkkt-pd), from w->grad/h/Hv evaluated at z->y.  In the HyKKT form
+/* Assemble K_c = W + Sigma_y + delta_w I + H^T (Q+ + Q-) H into band or
+ * sparse storage (eq. liftedkkt-pd), from w->grad/h/Hv evaluated at z->y.  In the HyKKT form
  * the same pattern holds K_gamma = W + Sigma_y + delta_w I + gamma H^T H, the
  * augmented-Lagrangian matrix, with W the Hessian at the multipliers lambda. */
 static void assemble(work* w, const or_state* z, double delta_w) {
-  const int n = w->n, m = w->m, bw = w->b + 1;
+  const int n = w->n, m = w->m;
   const int hy = w->o->kkt == 1;
-  memset(w->band, 0, sizeof(double) * (size_t)bw * n);
+  if (w->sparse) memset(w->spf.Lx, 0, sizeof(double) * (size_t)w->spf.Lp[n]);
+  else memset(w->band, 0, sizeof(double) * (size_t)(w->b + 1) * n);
   for (int r = 0; r < m; ++r) w->lam[r] = hy ? z->w_p[r] : z->w_p[r] - z->w_m[r];
   int cnt = or_hessian(w->p, z->y, w->lam, w->tr, w->tc, w->tv, w->ntrip_cap);
-  for (int t = 0; t < cnt; ++t) w->band[(size_t)w->tc[t] * bw + (w->tr[t] - w->tc[t])] += w->tv[t];
+  for (int t = 0; t < cnt; ++t) kadd(w, w->tr[t], w->tc[t], w->tv[t]);
   for (int i = 0; i < n; ++i) {
     double sig = delta_w;
     if (isfinite(w->yL[i])) sig += z->zL[i] / (z->y[i] - w->yL[i]);
     if (isfinite(w->yU[i])) sig += z->zU[i] / (w->yU[i] - z->y[i]);
-    w->band[(size_t)i * bw] += sig;
+    kadd(w, i, i, sig);
   }
   for (int r = 0; r < m; ++r) {
     const double D = hy ? w->o->hy_gamma : z->b_p[r] / z->s_p[r] + z->b_m[r] / z->s_m[r];
     for (int a = w->rp[r]; a < w->rp[r + 1]; ++a)
       for (int c = w->rp[r]; c <= a; ++c) {
         const int i = w->ci[a], j = w->ci[c]; /* columns ascending: i >= j */
-        w->band[(size_t)j * bw + (i - j)] += D * w->Hv[a] * w->Hv[c];
+        kadd(w, i, j, D * w->Hv[a] * w->Hv[c]);
       }
   }
 }
@@ -730,7 +829,7 @@ static void direction(work* w, const or_state* z, double mu, or_state* d) {
     w->rhs[i] = -r1;
   }
   memcpy(d->y, w->rhs, sizeof(double) * n);
-  band_solve(n, w->b, w->band, d->y);
+  ksolve(w, d->y);
   /* recover the eliminated directions */
   double* Hd = w->tmp;
   jac_mult(w, d->y, Hd);
@@ -785,7 +884,7 @@ static int direction_hy(work* w, const or_state* z, double mu, or_state* d) {
   }
   /* r_0 = H K^-1 g - c = H K^-1 g + h */
   memcpy(v, g, sizeof(double) * n);
-  band_solve(n, w->b, w->band, v);
+  ksolve(w, v);
   jac_mult(w, v, r);
   double rr = 0.0;
   for (int i = 0; i < m; ++i) { r[i] += w->h[i]; x[i] = 0.0; p[i] = r[i]; rr += r[i] * r[i]; }
@@ -794,7 +893,7 @@ static int direction_hy(work* w, const or_state* z, double mu, or_state* d) {
   while (rr > stop && it < w->o->cg_max_iter) {
     /* q = S p = H K^-1 H^T p */
     jac_t_mult(w, p, v);
-    band_solve(n, w->b, w->band, v);
+    ksolve(w, v);
     jac_mult(w, v, q);
     double pq = 0.0;
     for (int i = 0; i < m; ++i) pq += p[i] * q[i];
@@ -810,7 +909,7 @@ static int direction_hy(work* w, const or_state* z, double mu, or_state* d) {
   /* dy = K^-1 (g - H^T dlam) */
   jac_t_mult(w, x, v);
   for (int i = 0; i < n; ++i) d->y[i] = g[i] - v[i];
-  band_solve(n, w->b, w->band, d->y);
+  ksolve(w, d->y);
   memcpy(d->w_p, x, sizeof(double) * m);
   for (int i = 0; i < n; ++i) {
     d->zL[i] = d->zU[i] = 0.0;
@@ -833,12 +932,12 @@ static int direction_hy(work* w, const or_state* z, double mu, or_state* d) {
 static int factor_with_correction(work* w, const or_state* z, double* dw_last, double* dw, int* retries) {
   const double tol = w->o->pivtol;
   assemble(w, z, 0.0);
-  if (band_cholesky_tol(w->n, w->b, w->band, tol) == 0) { *dw = 0.0; return 0; }
+  if (kfactor(w, tol) == 0) { *dw = 0.0; return 0; }
   double d = (*dw_last == 0.0) ? DELTA_W0 : fmax(DELTA_WMIN, KAPPA_W_MINUS * *dw_last);
   for (;;) {
     ++*retries;
     assemble(w, z, d);
-    if (band_cholesky_tol(w->n, w->b, w->band, tol) == 0) { *dw = d; *dw_last = d; return 0; }
+    if (kfactor(w, tol) == 0) { *dw = d; *dw_last = d; return 0; }
     d = (*dw_last == 0.0) ? KAPPA_W_PLUS_BAR * d : KAPPA_W_PLUS * d;
     if (d > w->o->dw_max) return -1;
   }
@@ -1060,7 +1159,7 @@ int or_newton_step(const or_problem* p, const or_options* o, const or_state* z, 
   work_init(&w, p, o);
   eval_all(&w, z->y);
   assemble(&w, z, delta_w);
-  int rc = or_band_cholesky(w.n, w.b, w.band);
+  int rc = kfactor(&w, 0.0);
   if (rc == 0 && o->kkt == 1) direction_hy(&w, z, mu, d);
   else if (rc == 0) direction(&w, z, mu, d);
   work_free(&w);

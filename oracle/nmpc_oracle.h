@@ -10,6 +10,11 @@
  *   model residuals/derivatives  pinned (complex step, conservation laws,
  *                                steady state of Sec. 4.1, stencil exactness)
  *   banded Cholesky              pinned (numpy.linalg.cholesky, Laplacian)
+ *   sparse Cholesky, ND order    pinned (fill against numpy.linalg.cholesky of
+ *                                the permuted matrix, solves, the failing pivot
+ *                                against Schur-complement pivots, fill on grids
+ *                                below the natural order's, Newton step and
+ *                                IPM solutions equal to the band path's)
  *   SymCholesky                  pinned (Fig. cholesky-symExample, brute force)
  *   Newton step / condensation   pinned (uncondensed primal-dual Newton system)
  *   optimality error E_mu, E_0   pinned (lifted KKT residual from the dense
@@ -70,6 +75,8 @@ typedef struct {
   double hy_gamma;   /* HyKKT: augmented-Lagrangian weight of H^T H */
   double cg_tol;     /* HyKKT: CG stops when ||r||^2 <= cg_tol^2 ||r_0||^2 */
   int cg_max_iter;   /* HyKKT: CG iterations per Newton step at most */
+  int linsolve;      /* factorization of K: 0 band Cholesky in stage order, 1 sparse Cholesky
+                        after the oracle's nested-dissection ordering (or_sparse.inc) */
 } or_options;
 
 typedef struct {
@@ -111,6 +118,9 @@ int or_newton_step(const or_problem* p, const or_options* o, const or_state* z, 
 int or_band_cholesky(int n, int b, double* band);
 int or_symbolic(int n, const int* colptr, const int* rowidx, int* parent,
                 int* Lcolptr, int* Lrowidx, int cap);
+int or_nd_order(int n, const int* xadj, const int* adj, int leaf, int* perm);
+int or_sparse_cholesky(int n, const int* colptr, const int* rowidx, const double* vals,
+                       int use_nd, double tol, int* perm, double* b, long* nnzL);
 
 #ifdef __cplusplus
 }
