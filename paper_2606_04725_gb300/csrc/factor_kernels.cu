@@ -1111,19 +1111,23 @@ __device__ __forceinline__ void wait_done(const int* flag, long long limit, int*
 }
 
 template <bool FWD>
-__device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* dl, int nf, int smem_cap, int* flags) {
+__device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* dl, int nf, int smem_cap, int* flags,
+                                 const int* list, const int* count) {
   __shared__ unsigned long long bar;
   __shared__ int s_to, s_lost;
   __shared__ int s_q;
   __shared__ FrontDesc fd;
   const int tid = threadIdx.x;
+  // with a list, the claims run over its na fronts (level order) only
+  const int na = list ? *count : nf;
   if (tid == 0) s_to = s_lost = 0;
   for (;;) {
     if (tid == 0) s_q = atomicAdd(flags, 1);
     __syncthreads();
     const int k = s_q;
-    if (k >= nf) break;
-    const int q = FWD ? k : nf - 1 - k;  // backward: parents first
+    if (k >= na) break;
+    const int kk = FWD ? k : na - 1 - k;  // backward: parents first
+    const int q = list ? list[kk] : kk;
     load_desc(&fd, dl + q);
     __syncthreads();
     if (solve_on(d.ctl[fd.inst])) {  // uniform over the block
@@ -1158,8 +1162,14 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
   __shared__ int s_last;
   if (tid == 0) s_last = atomicAdd(flags + nf + 1, 1) == (int)gridDim.x - 1;
   __syncthreads();
-  if (s_last)
-    for (int i = tid; i < nf + 2; i += blockDim.x) flags[i] = 0;
+  if (s_last) {
+    if (list) {
+      for (int k = tid; k < na; k += blockDim.x) flags[1 + list[k]] = 0;
+      if (tid == 0) { flags[0] = 0; flags[nf + 1] = 0; }
+    } else {
+      for (int i = tid; i < nf + 2; i += blockDim.x) flags[i] = 0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1360,7 +1370,8 @@ __device__ void factor_front_flow(Ctl* ctl, const SnDev& s, const FrontDesc& fd,
   schur_update(Fl, Lu, invd, Up, m, c);
 }
 
-__global__ void __launch_bounds__(FCT, 3) k_factor_flow(Dev d, SnDev s, const FrontDesc* dl, int nf, int* flags) {
+__global__ void __launch_bounds__(FCT, 3) k_factor_flow(Dev d, SnDev s, const FrontDesc* dl, int nf, int* flags,
+                                                          const int* list, const int* count) {
   __shared__ FrontDesc fd;
   __shared__ int s_q, s_to, s_any_to;
   __shared__ double s_pubv[PB * PB];
@@ -1368,14 +1379,16 @@ __global__ void __launch_bounds__(FCT, 3) k_factor_flow(Dev d, SnDev s, const Fr
   const int tid = threadIdx.x;
   if (tid == 0) s_any_to = 0;
   const long long limit = s.spin_limit;
+  // with a list, the claims run over its na fronts (level order) only
+  const int na = list ? *count : nf;
   for (;;) {
     if (tid == 0) {
       s_q = atomicAdd(flags, 1);
       s_to = 0;
     }
     __syncthreads();
-    const int q = s_q;
-    if (q >= nf) break;
+    if (s_q >= na) break;
+    const int q = list ? list[s_q] : s_q;
     load_desc(&fd, dl + q);
     __syncthreads();
     Ctl* ctl = d.ctl + fd.inst;
@@ -1396,17 +1409,69 @@ __global__ void __launch_bounds__(FCT, 3) k_factor_flow(Dev d, SnDev s, const Fr
   __shared__ int s_last;
   if (tid == 0) s_last = atomicAdd(flags + nf + 1, 1) == (int)gridDim.x - 1;
   __syncthreads();
-  if (s_last)
-    for (int i = tid; i < nf + 2; i += blockDim.x) flags[i] = 0;
+  if (s_last) {
+    if (list) {
+      for (int k = tid; k < na; k += blockDim.x) flags[1 + list[k]] = 0;
+      if (tid == 0) { flags[0] = 0; flags[nf + 1] = 0; }
+    } else {
+      for (int i = tid; i < nf + 2; i += blockDim.x) flags[i] = 0;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(ST) k_fwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
-                                                    int* flags) {
-  solve_persistent<true>(d, s, dl, nf, smem_cap, flags);
+                                                    int* flags, const int* list, const int* count) {
+  solve_persistent<true>(d, s, dl, nf, smem_cap, flags, list, count);
 }
 __global__ void __launch_bounds__(ST) k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
-                                                    int* flags) {
-  solve_persistent<false>(d, s, dl, nf, smem_cap, flags);
+                                                    int* flags, const int* list, const int* count) {
+  solve_persistent<false>(d, s, dl, nf, smem_cap, flags, list, count);
+}
+
+// The fronts q in [0, nf) (level order) whose instance takes part in the
+// next persistent launch, in level order: list[0 .. *count).  Mode 0: the
+// instance needs a factorization; 1: it is being solved.  In the last
+// iterations of a batch most instances have stopped, and claiming their
+// fronts one at a time costs more than the work left.  One block: a byte per
+// instance in shared memory; thread t takes the contiguous fronts
+// [t per, (t+1) per), counts its active ones, one scan over the block gives
+// its offset, and it writes them in order, so the list keeps level order
+// (children before parents).
+__global__ void __launch_bounds__(FL_THREADS) k_front_list(Dev d, SnDev s, int nf, int mode, int* list, int* count) {
+  extern __shared__ unsigned char s_on[];
+  __shared__ int s_warp[FL_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < d.n_inst; i += FL_THREADS) {
+    const Ctl& c = d.ctl[i];
+    s_on[i] = (unsigned char)(mode == 0 ? c.need_factor != 0 : solve_on(c));
+  }
+  __syncthreads();
+  const int per = (nf + FL_THREADS - 1) / FL_THREADS;
+  const int q0 = min(nf, tid * per), q1 = min(nf, q0 + per);
+  int mine = 0;
+  for (int q = q0; q < q1; ++q) mine += s_on[s.front_inst[q]];
+  // inclusive scan of the counts over the block: lanes, then warps
+  int x = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {  // FL_THREADS / 32 = 32 warps
+    const int v = s_warp[lane];
+    int w = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w - v;  // exclusive over the warps
+  }
+  __syncthreads();
+  int at = s_warp[wid] + x - mine;
+  for (int q = q0; q < q1; ++q)
+    if (s_on[s.front_inst[q]]) list[at++] = q;
+  if (tid == FL_THREADS - 1) *count = at;
 }
 
 // ---------------------------------------------------------------------------

@@ -216,11 +216,12 @@ __global__ void k_red_eval(Dev d, int max_iter, CondArgs ca) {
     double v[11] = {0.0, 0.0, 0.0, DBL_MAX, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
     const int op[11] = {1, 1, 1, 2, 0, 0, 0, 3, 0, 0, 0};
     if (ch.kind == 0) {
-      for (int j = ch.begin + threadIdx.x; j < ch.end; j += RED_CHUNK) {
+      for (int t = ch.begin + threadIdx.x; t < ch.end; t += RED_CHUNK) {
+        const int j = d.red_var[t];  // longest H columns first: lanes of a warp loop alike
         double r = d.grad[j];
         for (int q = d.Hcsc_ptr[j]; q < d.Hcsc_ptr[j + 1]; ++q) {
-          const int s = d.Hcsc_slot[q], row = s / WH;
-          r += d.Hv[s] * (d.wp[row] - d.wm[row]);
+          const int s = d.Hcsc_slot[q];
+          r += d.Hv[s] * d.lam[s / WH];
         }
         const double yj = d.y[j], lo = d.yL[j], hi = d.yU[j];
         if (fin(lo)) {
@@ -354,6 +355,14 @@ __global__ void k_zero_L(Dev d, const long long* inst_Lbeg, const long long* ins
 // Per row: D_r = Q+ + Q- (the lifted pair's barrier weight) and
 // v_r = (w+ - w-) + (Q+ r4+ - r2+) - (Q- r4- - r2-), so that the condensed
 // right-hand side is -(grad f - mu/(y-yL) + mu/(yU-y) + H^T v).
+// H_rs D_r for the WH slots of row r: each H^T D H term of the assembly is
+// then one multiply-add, (H_ra D_r) H_rb, and the product H_ra D_r is formed
+// once per slot instead of once per term.
+__device__ __forceinline__ void row_hd(const Dev& d, int r, double D) {
+  const int WH = d.mc.WH;
+  for (int s = 0; s < WH; ++s) d.HD[(size_t)r * WH + s] = d.Hv[(size_t)r * WH + s] * D;
+}
+
 __device__ void rows_pre_at(const Dev& d, double* Drow, int r) {
   const Ctl& c = d.ctl[d.row_inst[r]];
   if (c.status != ST_RUNNING) return;
@@ -364,12 +373,14 @@ __device__ void rows_pre_at(const Dev& d, double* Drow, int r) {
     const double gh = d.mc.hy_gamma;
     Drow[r] = gh;
     d.rowv[r] = d.wp[r] + gh * d.h[r];
+    row_hd(d, r, gh);
     return;
   }
   const double mu = c.mu, gam = d.mc.gamma;
   const double sp = d.sp[r], sm = d.sm[r], isp = d.isp[r], ism = d.ism[r];
   const double Qp = d.bp[r] * isp, Qm = d.bm[r] * ism;
   Drow[r] = Qp + Qm;
+  row_hd(d, r, Qp + Qm);
   const double r4p = d.h[r] - gam + sp, r4m = -d.h[r] - gam + sm;
   const double r2p = d.wp[r] - mu * isp, r2m = d.wm[r] - mu * ism;
   d.rowv[r] = (d.wp[r] - d.wm[r]) + (Qp * r4p - r2p) - (Qm * r4m - r2m);
@@ -404,13 +415,9 @@ __global__ void k_assemble(Dev d, const int* tgt_inst, const double* Drow) {
   if (t >= d.n_tgt) return;
   const Ctl& c = d.ctl[tgt_inst[t]];
   if (!c.need_factor) return;
-  const int WH = d.mc.WH;
   double v = 0.0;
   for (int q = d.tw_ptr[t]; q < d.tw_ptr[t + 1]; ++q) v += d.Wv[d.tw_idx[q]];
-  for (int q = d.th_ptr[t]; q < d.th_ptr[t + 1]; ++q) {
-    const int a = d.th_a[q], b = d.th_b[q];
-    v += d.Hv[a] * Drow[a / WH] * d.Hv[b];
-  }
+  for (int q = d.th_ptr[t]; q < d.th_ptr[t + 1]; ++q) v += d.HD[d.th_a[q]] * d.Hv[d.th_b[q]];
   const int j = d.tgt_diag[t];
   if (j >= 0) {
     // Sigma_y = zL/(y - yL) + zU/(yU - y) (reciprocals are 0 where a bound is absent)
@@ -454,8 +461,9 @@ __global__ void k_ctl_factor(Dev d, CondArgs ca) {
 
 // right-hand side of eq. liftedkkt-pd, scattered into the factor ordering
 __global__ void k_rhs(Dev d) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= d.n) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.n) return;
+  const int v = d.red_var[t];  // longest H columns first: lanes of a warp loop alike
   const Ctl& c = d.ctl[d.var_inst[v]];
   if (c.status != ST_RUNNING) return;
   const int WH = d.mc.WH;

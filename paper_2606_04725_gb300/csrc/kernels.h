@@ -62,11 +62,19 @@ __global__ void k_hy_rhs(Dev d);
 // factor_kernels.cu
 __global__ void k_factor_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
 __global__ void k_factor_cluster(Dev d, SnDev s, const FrontDesc* dl);
-__global__ void k_factor_flow(Dev d, SnDev s, const FrontDesc* dl, int nf, int* flags);
+__global__ void k_factor_flow(Dev d, SnDev s, const FrontDesc* dl, int nf, int* flags, const int* list,
+                              const int* count);
 __global__ void k_fwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
 __global__ void k_bwd_level(Dev d, SnDev s, const FrontDesc* dl, int smem_cap);
-__global__ void k_fwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap, int* flags);
-__global__ void k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap, int* flags);
+__global__ void k_fwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap, int* flags, const int* list,
+                              const int* count);
+__global__ void k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap, int* flags, const int* list,
+                              const int* count);
+// level-ordered list of the fronts [0, nf) of the instances that take part in
+// a persistent launch (mode 0: need a factorization; 1: are being solved)
+constexpr int FL_THREADS = 1024;
+constexpr int FL_MAX_INST = 32768;  // one byte of shared memory per instance
+__global__ void k_front_list(Dev d, SnDev s, int nf, int mode, int* list, int* count);
 __global__ void k_diag_inv(Dev d, SnDev s, int i0);
 __global__ void k_panel_scale(Dev d, SnDev s, int u0);
 __global__ void k_big_zero(Dev d, SnDev s, const FrontDesc* dl);

@@ -272,6 +272,7 @@ __device__ void eval_row_at(const Dev& d, int r, int use_trial, int with_jac) {
   } else {
     if (c.status != ST_RUNNING) return;
     eval_row(d, d.y, r, d.h, with_jac ? d.Hv : nullptr);
+    if (with_jac) d.lam[r] = d.wp[r] - d.wm[r];  // the row's multiplier, for the H^T products
     if (with_jac && d.mc.kkt != 1) {  // reciprocals of the slacks and their duals, reused by every later kernel
       d.isp[r] = recip_nr(d.sp[r]);
       d.ism[r] = recip_nr(d.sm[r]);

@@ -69,6 +69,12 @@ struct nmpc_handle {
   // dataflow factorization (factor_mode 3) over the first flow_levels levels (fronts in level order)
   int flow_levels = 0, flow_fronts = 0, flow_blocks = 0, flow_smem = 0;
   int* d_flow_flags = nullptr;
+  // level-ordered lists of the fronts of the instances taking part in the
+  // next persistent factorization ([0, ns)) and solves ([ns, 2 ns)), and
+  // their lengths ([0], [1]); used for batches (front_lists)
+  int* d_front_list = nullptr;
+  int* d_front_cnt = nullptr;
+  bool front_lists = false;
   std::vector<int> lvl_maxm, lvl_maxc, lvl_maxmu, lvl_maxch, lvl_maxmc;
   std::vector<int> amap;                             // extend-add pairs (source, destination)
   std::vector<long long> amap_ptr;                   // ranges per (front, CTA, child)
@@ -216,6 +222,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   d.dy = cv.take<double>(n); d.dzL = cv.take<double>(n); d.dzU = cv.take<double>(n);
   d.dsp = cv.take<double>(m); d.dsm = cv.take<double>(m); d.dwp = cv.take<double>(m); d.dwm = cv.take<double>(m);
   d.dbp = cv.take<double>(m); d.dbm = cv.take<double>(m); d.rowv = cv.take<double>(m);
+  d.lam = cv.take<double>(m); d.HD = cv.take<double>((size_t)m * WH);
   d.cg_r = d.dsp; d.cg_p = d.dsm; d.cg_q = d.dbp;  // HyKKT only, where these are unused
   d.yt = cv.take<double>(n); d.spt = cv.take<double>(m); d.smt = cv.take<double>(m); d.ht = cv.take<double>(m);
   d.fvart = cv.take<double>(n);
@@ -223,6 +230,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   d.ctl = cv.take<Ctl>(ni);
   d.filt_th = cv.take<double>((size_t)ni * FILTER_CAP); d.filt_ph = cv.take<double>((size_t)ni * FILTER_CAP);
   d.chunks = cv.take<Chunk>(nch); d.inst_chunk_ptr = cv.take<int>(ni + 1); d.inst_chunk_list = cv.take<int>(nch);
+  d.red_var = cv.take<int>(n);
   d.red_eval = cv.take<RedEval>(nch); d.red_dir = cv.take<RedDir>(nch); d.red_trial = cv.take<RedTrial>(nch);
   d.red_cg = cv.take<double>(nch);
   d.tgt_L = cv.take<long long>(A.tgt_L.size()); d.tgt_diag = cv.take<int>(A.tgt_diag.size());
@@ -249,6 +257,10 @@ void carve(nmpc_handle* h, Carver& cv) {
   s.sn_uvptr = cv.take<long long>(ns + 1);
   s.desc = cv.take<FrontDesc>(ns);
   s.pos_of_sn = cv.take<int>(ns);
+  s.front_inst = cv.take<int>(ns);
+  h->d_front_list = cv.take<int>(2 * ns);
+  h->d_front_cnt = cv.take<int>(2);
+  h->front_lists = ni > 1 && ni <= FL_MAX_INST;
   h->d_solve_flags = cv.take<int>(2 * (ns + 2));  // forward and backward persistent solves
   h->d_flow_flags = cv.take<int>(h->flow_fronts + 2);
   s.amap = cv.take<IdxPair>(h->amap.size() / 2);
@@ -354,8 +366,15 @@ nmpc_status launch_factor(nmpc_handle* h) {
   bool forked = h->side_pending;
   const int L = h->flow_levels;
   if (L > 0) {
+    const int* list = nullptr;
+    if (h->front_lists) {  // only the fronts of the instances that need a factorization
+      k_front_list<<<1, FL_THREADS, h->A.n_inst, h->stream>>>(h->d, h->s, h->flow_fronts, 0, h->d_front_list,
+                                                               h->d_front_cnt);
+      ++h->launches;
+      list = h->d_front_list;
+    }
     k_factor_flow<<<h->flow_blocks, CLUSTER_THREADS, h->flow_smem, h->stream>>>(h->d, h->s, h->s.desc, h->flow_fronts,
-                                                                              h->d_flow_flags);
+                                                                              h->d_flow_flags, list, h->d_front_cnt);
     ++h->launches;
   }
   for (int l = (L > 0 ? L - 1 : 0); l < nl; ++l) {
@@ -428,9 +447,17 @@ nmpc_status launch_solve(nmpc_handle* h) {
   const int L = h->opt.solve_mode == 1 ? 0 : h->solve_prefix;  // levels covered by one persistent launch
   int* fwd_flags = h->d_solve_flags;                              // zero between launches
   int* bwd_flags = h->d_solve_flags + h->solve_prefix_fronts + 2;
+  const int* list = nullptr;
+  const int ns = (int)h->A.sn_first.size();
+  if (L > 0 && h->front_lists) {  // only the fronts of the instances being solved (both directions)
+    k_front_list<<<1, FL_THREADS, h->A.n_inst, h->stream>>>(h->d, h->s, h->solve_prefix_fronts, 1,
+                                                             h->d_front_list + ns, h->d_front_cnt + 1);
+    ++h->launches;
+    list = h->d_front_list + ns;
+  }
   if (L > 0) {
     k_fwd_persist<<<h->persist_blocks_fwd, 128, h->persist_smem_fwd, h->stream>>>(
-        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, fwd_flags);
+        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, fwd_flags, list, h->d_front_cnt + 1);
     ++h->launches;
   }
   for (int l = L; l < nl; ++l) {
@@ -457,7 +484,7 @@ nmpc_status launch_solve(nmpc_handle* h) {
   }
   if (L > 0) {
     k_bwd_persist<<<h->persist_blocks_bwd, 128, h->persist_smem_bwd, h->stream>>>(
-        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, bwd_flags);
+        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, bwd_flags, list, h->d_front_cnt + 1);
     ++h->launches;
   }
   return NMPC_OK;
@@ -478,7 +505,11 @@ long long seq_factor(nmpc_handle* h) {
   Dev& d = h->d;
   cudaStream_t st = h->stream;
   const int ni = h->A.n_inst;
-  const int zx = (int)std::max(1u, std::min(1024u, blocks_for(h->A.nnzL / std::max(1, ni) + 1, EW)));
+  // zeroing blocks per instance: enough to spread one instance's panels over
+  // the GPU, but at most about 8k blocks in all (the blocks of instances that
+  // need no factorization leave at once, yet each still has to be scheduled)
+  const int zx = (int)std::max(1u, std::min({1024u, blocks_for(h->A.nnzL / std::max(1, ni) + 1, EW),
+                                             (unsigned)std::max(1, 8192 / std::max(1, ni))}));
   const long long l0 = h->launches;
   k_zero_rows<<<(unsigned)((long long)zx * ni + blocks_for(d.m, EW)), EW, 0, st>>>(d, h->d_inst_Lbeg, h->d_inst_Lend,
                                                                                     h->d_Drow, zx);
@@ -1012,6 +1043,7 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   CUDA_TRY(h, up(d.Wadj_other, A.Wadj_other, st));
   CUDA_TRY(h, up(d.perm, A.perm, st)); CUDA_TRY(h, up(d.iperm, A.iperm, st));
   CUDA_TRY(h, up(d.chunks, ch, st)); CUDA_TRY(h, up(d.inst_chunk_ptr, A.inst_chunk_ptr, st));
+  CUDA_TRY(h, up(d.red_var, A.red_var, st));
   CUDA_TRY(h, up(d.inst_chunk_list, A.inst_chunk_list, st));
   CUDA_TRY(h, up(d.tgt_L, A.tgt_L, st)); CUDA_TRY(h, up(d.tgt_diag, A.tgt_diag, st));
   CUDA_TRY(h, up(d.tw_ptr, A.tw_ptr, st)); CUDA_TRY(h, up(d.tw_idx, A.tw_idx, st));
@@ -1048,6 +1080,10 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
     std::vector<int> pos_of(A.level_sn.size());
     for (size_t q = 0; q < A.level_sn.size(); ++q) pos_of[A.level_sn[q]] = (int)q;
     CUDA_TRY(h, up(s.pos_of_sn, pos_of, st));
+    std::vector<int> finst(A.level_sn.size());
+    for (size_t q = 0; q < A.level_sn.size(); ++q) finst[q] = A.sn_inst[A.level_sn[q]];
+    CUDA_TRY(h, up(s.front_inst, finst, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));  // finst goes out of scope
     for (size_t q = 0; q < A.level_sn.size(); ++q) {
       const int J = A.level_sn[q];
       FrontDesc& f = desc[q];

@@ -87,6 +87,8 @@ struct ModelConst {
 // One chunk is reduced by one block of RED_CHUNK threads (one element per
 // thread): small chunks spread the FP64 work of a reduction over many SMs.
 constexpr int RED_CHUNK = 128;
+// Blocks a reduction should give at least, when the problem allows (152 SMs x 8).
+constexpr int RED_TARGET_BLOCKS = 1216;
 struct Chunk {
   int inst, kind, begin, end;
 };
@@ -137,6 +139,8 @@ struct Dev {
   double *cg_r, *cg_p, *cg_q;
   double* red_cg;       // per reduction chunk: partial sum of a CG dot product
   double* rowv;         // per-row scratch (H^T v products)
+  double* lam;          // per row: w+ - w- at the current iterate (set with the Jacobian)
+  double* HD;           // per H slot: H_rs D_r, set with the rows' weights D_r before each assembly
   // trial
   double *yt, *spt, *smt, *ht, *fvart;
   // permutation / solve
@@ -149,6 +153,7 @@ struct Dev {
   // reductions
   const Chunk* chunks; int n_chunks;
   const int* inst_chunk_ptr; const int* inst_chunk_list;
+  const int* red_var;   // variables chunk by chunk, longest H column first (a permutation)
   RedEval* red_eval; RedDir* red_dir; RedTrial* red_trial;
   // assembly map
   int n_tgt;
@@ -233,6 +238,7 @@ struct SnDev {
   const int* level_ptr; const int* level_sn;    // supernodes by level (height)
   const FrontDesc* desc;      // descriptors in level_sn order
   const int* pos_of_sn;       // level-order position of each supernode
+  const int* front_inst;      // instance of each front, level order
   const IdxPair* amap;        // extend-add pairs (source in child U, destination in own columns)
   const long long* amap_ptr;  // per (front, CTA, child) ranges, from FrontDesc::abase
   const long long* sn_uvptr;  // offset of the (m_s-c_s) update vector (solves)

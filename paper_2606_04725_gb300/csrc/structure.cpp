@@ -809,8 +809,17 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
         A.th_ptr.push_back(A.th_ptr.back() + P.th_cnt[t]);
       }
     }
-    // reduction chunks (never crossing an instance)
-    const int CH = RED_CHUNK;
+    // Reduction chunks (never crossing an instance).  A block reduces one
+    // chunk, RED_CHUNK threads striding over it; a chunk holds RED_CHUNK x E
+    // elements with E chosen so that the whole problem still gives about
+    // RED_TARGET_BLOCKS blocks (E = 1 for a single small instance, whose
+    // reductions are latency-bound; up to 16 for wide batches, where the tree
+    // reduction of a 128-element chunk would cost more than its elements).
+    long long tot_el = 0;
+    for (int i = 0; i < ni; ++i) tot_el += (long long)A.inst_n[i] + A.inst_m[i];
+    const int E = (int)std::max(1LL, std::min(16LL, tot_el / ((long long)RED_TARGET_BLOCKS * RED_CHUNK)));
+    const int CH = RED_CHUNK * E;
+    A.red_chunk_elems = CH;
     A.chunks.clear();
     A.inst_chunk_ptr.assign(ni + 1, 0);
     for (int i = 0; i < ni; ++i) {
@@ -819,6 +828,17 @@ std::string analyze(const ProblemSpec& sp, Analysis& A) {
       for (int b = 0; b < A.inst_m[i]; b += CH)
         A.chunks.push_back({i, 1, A.inst_roff[i] + b, A.inst_roff[i] + std::min(A.inst_m[i], b + CH)});
       A.inst_chunk_ptr[i + 1] = (int)A.chunks.size();
+    }
+    // Within each variable chunk, variables by descending column length of H
+    // (stable): the H^T products loop over a column, and a warp runs as many
+    // FP64 iterations as its longest column, whatever the other lanes need.
+    A.red_var.resize(A.n);
+    std::iota(A.red_var.begin(), A.red_var.end(), 0);
+    for (const Chunk& c : A.chunks) {
+      if (c.kind != 0) continue;
+      std::stable_sort(A.red_var.begin() + c.begin, A.red_var.begin() + c.end, [&](int a, int b) {
+        return A.Hcsc_ptr[a + 1] - A.Hcsc_ptr[a] > A.Hcsc_ptr[b + 1] - A.Hcsc_ptr[b];
+      });
     }
     A.inst_chunk_list.resize(A.chunks.size());
     std::iota(A.inst_chunk_list.begin(), A.inst_chunk_list.end(), 0);

@@ -47,9 +47,12 @@ struct Analysis {
   // assembly map
   std::vector<long long> tgt_L;
   std::vector<int> tgt_diag, tw_ptr, tw_idx, th_ptr, th_a, th_b;
-  // reduction chunks
+  // reduction chunks, and the variables of each variable chunk ordered by
+  // their number of Jacobian entries (longest first)
   std::vector<Chunk> chunks;
   std::vector<int> inst_chunk_ptr, inst_chunk_list;
+  std::vector<int> red_var;
+  int red_chunk_elems = 0;
   // stats
   double factor_flops = 0, solve_flops = 0, analysis_ms = 0;
   long long nnzL_true = 0;
