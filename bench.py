@@ -389,6 +389,44 @@ def plate_factorization(P, dev, peak):
     return out
 
 
+def plate_closed_loop(P, dev, resolves):
+    """Heated plate at full size (g = 64, S = 8, T = 50; n = 209,296) in
+    closed loop: a cold solve from the zero field (target of seed 3), then
+    `resolves` warm re-solves, each from the previous solution's x_1 (the
+    state one interval later) with the same target.  Re-solves/s and ms per
+    interior-point iteration from CUDA events around each re-solve."""
+    import torch
+    import paper_2606_04725_gb300.inputs as I
+    g, S, T = 64, 8, 50
+    g2 = g * g
+    s = P.Solver(P.MODEL_PLATE, [T], g=g, S=S, device=dev)
+    target = I.plate_target(g, seed=3)
+    s.set_params(x0=np.zeros(g2), setpoint=target)
+    t0 = time.perf_counter()
+    cold = s.solve()[0]
+    torch.cuda.synchronize()
+    cold_s = time.perf_counter() - t0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, iters, ok = [], [], cold["status"] == 0
+    for _ in range(resolves):
+        y = s.get_solution(0)
+        s.set_params(x0=y[g2:2 * g2].copy(), setpoint=target)  # x_1: the first stage after x_0
+        ev0.record(torch.cuda.current_stream())
+        info = s.solve(warm=True)[0]
+        ev1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        iters.append(info["iters"])
+        ok = ok and info["status"] == 0
+    s.close()
+    tot = sum(ms)
+    return {"workload": "plate_g64_S8_T50_closed_loop", "resolves": resolves,
+            "resolves_per_s": resolves / (tot * 1e-3), "ms_per_resolve": tot / resolves,
+            "ms_per_ipm_iter": tot / max(1, sum(iters)), "ipm_iters_per_resolve": sum(iters) / resolves,
+            "cold_solve_s": cold_s, "cold_solve_iters": cold["iters"], "statuses_ok": ok,
+            "note": "x0 <- x_1 of the previous solution, target fixed; CUDA events around each warm re-solve"}
+
+
 def plate_g128_iteration(P, dev, peak):
     """The 128 x 128 plate with 16 actuators and 100 intervals (n = 1,656,384):
     analysis and binding, then one interior-point iteration from the cold
@@ -570,6 +608,8 @@ def main():
     ap.add_argument("--instances", type=int, default=0,
                     help="solve only the first K instances of the batch (smaller profiling cases)")
     ap.add_argument("--no-probe", action="store_true", help="skip the FP64 throughput probe")
+    ap.add_argument("--plate-closed-loop", type=int, default=0,
+                    help="also run the 64x64 plate's closed loop with this many warm re-solves")
     ap.add_argument("--plate-g128", action="store_true",
                     help="also time one interior-point iteration of the 128 x 128 plate (S = 16, T = 100)")
     ap.add_argument("--host-loop", action="store_true",
@@ -769,6 +809,8 @@ def main():
     del flush
     if args.plate_g128:
         line["plate_g128"] = plate_g128_iteration(P, dev, peak)
+    if args.plate_closed_loop > 0:
+        line["plate_closed_loop"] = plate_closed_loop(P, dev, args.plate_closed_loop)
     if not args.no_extras:
         line["single_column"] = single_column(P, dev, rank=rank)
         line["plate_full_size"] = plate_factorization(P, dev, peak)

@@ -1118,17 +1118,24 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
   __shared__ int s_q;
   __shared__ FrontDesc fd;
   const int tid = threadIdx.x;
-  // with a list, the claims run over its na fronts (level order) only
-  const int na = list ? *count : nf;
   if (tid == 0) s_to = s_lost = 0;
   for (;;) {
-    if (tid == 0) s_q = atomicAdd(flags, 1);
+    // thread 0 claims the next front (with a list, among its fronts only, in
+    // level order; backward: parents first) and resolves its position, so
+    // the other threads keep no claim state in registers
+    if (tid == 0) {
+      const int k = atomicAdd(flags, 1);
+      const int na = list ? *count : nf;
+      int q = -1;
+      if (k < na) {
+        const int kk = FWD ? k : na - 1 - k;
+        q = list ? list[kk] : kk;
+      }
+      s_q = q;
+    }
     __syncthreads();
-    const int k = s_q;
-    if (k >= na) break;
-    const int kk = FWD ? k : na - 1 - k;  // backward: parents first
-    const int q = list ? list[kk] : kk;
-    load_desc(&fd, dl + q);
+    if (s_q < 0) break;
+    load_desc(&fd, dl + s_q);
     __syncthreads();
     if (solve_on(d.ctl[fd.inst])) {  // uniform over the block
       // started before the wait: the panel copy and the front's own values
@@ -1152,7 +1159,7 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
     // the block barrier (release is cumulative), and a waiting block reads
     // them after its acquire load and its own barrier.
     __syncthreads();
-    if (tid == 0) st_release_gpu(flags + 1 + q, 1);
+    if (tid == 0) st_release_gpu(flags + 1 + fd.pos, 1);
     // a panel copy that did not land may still write this block's shared
     // memory: the block claims no further front (s_lost is uniform here)
     if (s_lost) break;
@@ -1164,6 +1171,7 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
   __syncthreads();
   if (s_last) {
     if (list) {
+      const int na = *count;
       for (int k = tid; k < na; k += blockDim.x) flags[1 + list[k]] = 0;
       if (tid == 0) { flags[0] = 0; flags[nf + 1] = 0; }
     } else {
@@ -1423,7 +1431,7 @@ __global__ void __launch_bounds__(ST) k_fwd_persist(Dev d, SnDev s, const FrontD
                                                     int* flags, const int* list, const int* count) {
   solve_persistent<true>(d, s, dl, nf, smem_cap, flags, list, count);
 }
-__global__ void __launch_bounds__(ST) k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
+__global__ void __launch_bounds__(ST, 16) k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
                                                     int* flags, const int* list, const int* count) {
   solve_persistent<false>(d, s, dl, nf, smem_cap, flags, list, count);
 }
@@ -1433,45 +1441,51 @@ __global__ void __launch_bounds__(ST) k_bwd_persist(Dev d, SnDev s, const FrontD
 // instance needs a factorization; 1: it is being solved.  In the last
 // iterations of a batch most instances have stopped, and claiming their
 // fronts one at a time costs more than the work left.  One block: a byte per
-// instance in shared memory; thread t takes the contiguous fronts
-// [t per, (t+1) per), counts its active ones, one scan over the block gives
-// its offset, and it writes them in order, so the list keeps level order
-// (children before parents).
+// instance in shared memory; warp w takes the contiguous fronts of segment w,
+// 32 at a time (coalesced loads, a ballot each); a scan over the warps'
+// counts gives each segment's offset, and a second pass writes the fronts in
+// order, so the list keeps level order (children before parents).
 __global__ void __launch_bounds__(FL_THREADS) k_front_list(Dev d, SnDev s, int nf, int mode, int* list, int* count) {
   extern __shared__ unsigned char s_on[];
   __shared__ int s_warp[FL_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr unsigned FULLM = 0xffffffffu;
   for (int i = tid; i < d.n_inst; i += FL_THREADS) {
     const Ctl& c = d.ctl[i];
     s_on[i] = (unsigned char)(mode == 0 ? c.need_factor != 0 : solve_on(c));
   }
   __syncthreads();
-  const int per = (nf + FL_THREADS - 1) / FL_THREADS;
-  const int q0 = min(nf, tid * per), q1 = min(nf, q0 + per);
-  int mine = 0;
-  for (int q = q0; q < q1; ++q) mine += s_on[s.front_inst[q]];
-  // inclusive scan of the counts over the block: lanes, then warps
-  int x = mine;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+  constexpr int NW = FL_THREADS / 32;
+  const int seg = (nf + NW * 32 - 1) / (NW * 32) * 32;  // fronts per warp, a multiple of 32
+  const int w0 = min(nf, wid * seg), w1 = min(nf, w0 + seg);
+  int cnt = 0;
+#pragma unroll 4
+  for (int b = w0; b < w1; b += 32) {
+    const int q = b + lane;
+    cnt += __popc(__ballot_sync(FULLM, q < w1 && s_on[s.front_inst[q]]));
   }
-  if (lane == 31) s_warp[wid] = x;
+  if (lane == 0) s_warp[wid] = cnt;
   __syncthreads();
-  if (wid == 0) {  // FL_THREADS / 32 = 32 warps
+  if (wid == 0) {  // exclusive scan of the NW = 32 warps' counts
     const int v = s_warp[lane];
-    int w = v;
+    int x = v;
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
+      const int y = __shfl_up_sync(FULLM, x, o);
+      if (lane >= o) x += y;
     }
-    s_warp[lane] = w - v;  // exclusive over the warps
+    s_warp[lane] = x - v;
+    if (lane == 31) *count = x;
   }
   __syncthreads();
-  int at = s_warp[wid] + x - mine;
-  for (int q = q0; q < q1; ++q)
-    if (s_on[s.front_inst[q]]) list[at++] = q;
-  if (tid == FL_THREADS - 1) *count = at;
+  int at = s_warp[wid];
+#pragma unroll 4
+  for (int b = w0; b < w1; b += 32) {
+    const int q = b + lane;
+    const bool on = q < w1 && s_on[s.front_inst[q]];
+    const unsigned bal = __ballot_sync(FULLM, on);
+    if (on) list[at + __popc(bal & ((1u << lane) - 1u))] = q;
+    at += __popc(bal);
+  }
 }
 
 // ---------------------------------------------------------------------------
