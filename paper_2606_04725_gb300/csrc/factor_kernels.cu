@@ -1118,24 +1118,33 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
   __shared__ int s_q;
   __shared__ FrontDesc fd;
   const int tid = threadIdx.x;
-  if (tid == 0) s_to = s_lost = 0;
+  // Claims (thread 0 only).  With a list they run over its na fronts, in
+  // level order (backward: parents first).  Fronts are claimed one ahead:
+  // the next front's counter increment is issued when a front starts and its
+  // list entry is read while the front waits for its dependencies, so
+  // neither round trip stalls the block between fronts.  Holding a claimed
+  // front not yet started forms no cycle of waits: the block first finishes
+  // its current front, which waits only on fronts claimed before it.
+  int na = nf, k_next = 0, q_next = -1;
+  bool have_next = false;
+  auto resolve = [&](int k) {
+    if (k >= na) return -1;
+    const int kk = FWD ? k : na - 1 - k;
+    return list ? list[kk] : kk;
+  };
+  if (tid == 0) {
+    s_to = s_lost = 0;
+    if (list) na = *count;
+    s_q = resolve(atomicAdd(flags, 1));
+  }
   for (;;) {
-    // thread 0 claims the next front (with a list, among its fronts only, in
-    // level order; backward: parents first) and resolves its position, so
-    // the other threads keep no claim state in registers
-    if (tid == 0) {
-      const int k = atomicAdd(flags, 1);
-      const int na = list ? *count : nf;
-      int q = -1;
-      if (k < na) {
-        const int kk = FWD ? k : na - 1 - k;
-        q = list ? list[kk] : kk;
-      }
-      s_q = q;
-    }
     __syncthreads();
     if (s_q < 0) break;
     load_desc(&fd, dl + s_q);
+    if (tid == 0) {
+      k_next = atomicAdd(flags, 1);  // used only once the front waits
+      have_next = false;
+    }
     __syncthreads();
     if (solve_on(d.ctl[fd.inst])) {  // uniform over the block
       // started before the wait: the panel copy and the front's own values
@@ -1149,6 +1158,8 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
           } else if (fd.par_pos >= 0 && fd.par_pos < nf) {
             wait_done(flags + 1 + fd.par_pos, s.spin_limit, &s_to);
           }
+          q_next = resolve(k_next);
+          have_next = true;
         }
         __syncthreads();
       };
@@ -1159,10 +1170,17 @@ __device__ void solve_persistent(const Dev& d, const SnDev& s, const FrontDesc* 
     // the block barrier (release is cumulative), and a waiting block reads
     // them after its acquire load and its own barrier.
     __syncthreads();
-    if (tid == 0) st_release_gpu(flags + 1 + fd.pos, 1);
-    // a panel copy that did not land may still write this block's shared
-    // memory: the block claims no further front (s_lost is uniform here)
-    if (s_lost) break;
+    if (tid == 0) {
+      st_release_gpu(flags + 1 + fd.pos, 1);
+      if (!have_next) q_next = resolve(k_next);
+      s_q = q_next;
+      // a panel copy that did not land may still write this block's shared
+      // memory: the block starts no further front, and the front it has
+      // claimed is released unsolved (the timeout flag reports the failure)
+      // so that no block waits for it
+      if (s_lost && q_next >= 0) st_release_gpu(flags + 1 + q_next, 1);
+    }
+    if (s_lost) break;  // uniform: set before the barrier above
   }
   if (tid == 0 && (s_to || s_lost)) atomicExch(s.timeout, 1);
   // no block touches the flags after it has arrived here
@@ -1385,19 +1403,26 @@ __global__ void __launch_bounds__(FCT, 3) k_factor_flow(Dev d, SnDev s, const Fr
   __shared__ double s_pubv[PB * PB];
   __shared__ double sB[PB];
   const int tid = threadIdx.x;
-  if (tid == 0) s_any_to = 0;
   const long long limit = s.spin_limit;
-  // with a list, the claims run over its na fronts (level order) only
-  const int na = list ? *count : nf;
+  // Claims (thread 0 only), with a list over its na fronts (level order).
+  // The next front's counter increment is issued when a front starts and
+  // resolved when it ends, so the round trip overlaps the factorization;
+  // holding a claimed front not yet started forms no cycle of waits (the
+  // block first finishes its current front, which waits only on fronts
+  // claimed before it).
+  int na = nf, k_next = 0;
+  auto resolve = [&](int k) { return k >= na ? -1 : (list ? list[k] : k); };
+  if (tid == 0) {
+    s_any_to = 0;
+    if (list) na = *count;
+    s_q = resolve(atomicAdd(flags, 1));
+  }
   for (;;) {
-    if (tid == 0) {
-      s_q = atomicAdd(flags, 1);
-      s_to = 0;
-    }
+    if (tid == 0) s_to = 0;
     __syncthreads();
-    if (s_q >= na) break;
-    const int q = list ? list[s_q] : s_q;
-    load_desc(&fd, dl + q);
+    if (s_q < 0) break;
+    load_desc(&fd, dl + s_q);
+    if (tid == 0) k_next = atomicAdd(flags, 1);  // used only when this front ends
     __syncthreads();
     Ctl* ctl = d.ctl + fd.inst;
     if (ctl->need_factor) factor_front_flow(ctl, s, fd, flags, nf, &s_to, s_pubv, sB, limit);  // uniform
@@ -1409,7 +1434,8 @@ __global__ void __launch_bounds__(FCT, 3) k_factor_flow(Dev d, SnDev s, const Fr
         flag_fail(ctl);
         s_any_to = 1;
       }
-      st_release_gpu(flags + 1 + q, 1);
+      st_release_gpu(flags + 1 + fd.pos, 1);
+      s_q = resolve(k_next);
     }
   }
   if (tid == 0 && s_any_to) atomicExch(s.timeout, 1);
@@ -1419,7 +1445,8 @@ __global__ void __launch_bounds__(FCT, 3) k_factor_flow(Dev d, SnDev s, const Fr
   __syncthreads();
   if (s_last) {
     if (list) {
-      for (int k = tid; k < na; k += blockDim.x) flags[1 + list[k]] = 0;
+      const int nl = *count;  // na is thread 0's
+      for (int k = tid; k < nl; k += blockDim.x) flags[1 + list[k]] = 0;
       if (tid == 0) { flags[0] = 0; flags[nf + 1] = 0; }
     } else {
       for (int i = tid; i < nf + 2; i += blockDim.x) flags[i] = 0;
@@ -1427,11 +1454,11 @@ __global__ void __launch_bounds__(FCT, 3) k_factor_flow(Dev d, SnDev s, const Fr
   }
 }
 
-__global__ void __launch_bounds__(ST) k_fwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
+__global__ void __launch_bounds__(ST, 10) k_fwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
                                                     int* flags, const int* list, const int* count) {
   solve_persistent<true>(d, s, dl, nf, smem_cap, flags, list, count);
 }
-__global__ void __launch_bounds__(ST, 16) k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
+__global__ void __launch_bounds__(ST, 12) k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int smem_cap,
                                                     int* flags, const int* list, const int* count) {
   solve_persistent<false>(d, s, dl, nf, smem_cap, flags, list, count);
 }
