@@ -138,6 +138,17 @@ __device__ __forceinline__ bool last_of_instance(const Dev& d, int inst) {
   __syncthreads();
   return s_last != 0;
 }
+// uniform over the block: this block runs instance inst's control step.  An
+// instance that took part stores a partial in every chunk, so its step runs
+// on the last of its chunk blocks to arrive; one that did not (stopped, or
+// not searching) has no partials: its first chunk block runs the step at
+// once and the others leave without touching a counter -- in the last
+// iterations of a batch most blocks are such, and each fence and atomic
+// costs.
+__device__ __forceinline__ bool runs_control(const Dev& d, int inst, bool active) {
+  if (active) return last_of_instance(d, inst);
+  return (int)blockIdx.x == d.inst_chunk_ptr[inst];  // chunks are numbered instance after instance
+}
 // uniform over the block: this block finished the last instance
 __device__ __forceinline__ bool last_instance(const Dev& d) {
   __shared__ int s_last;
@@ -209,7 +220,8 @@ __device__ void ctl_post(const Dev& d, int i, Ctl& c, bool write);
 __global__ void k_red_eval(Dev d, int max_iter, CondArgs ca) {
   const Chunk ch = d.chunks[blockIdx.x];
   const Ctl& c = d.ctl[ch.inst];
-  if (c.status == ST_RUNNING) {  // uniform over the block
+  const bool active = c.status == ST_RUNNING;  // uniform over the block
+  if (active) {
     const double gam = d.mc.gamma;
     const int WH = d.mc.WH;
     // dual, prim, cmax, cmin, sum_l, sum_z, f, log-mantissa, log-exponent, theta, nonfinite
@@ -275,7 +287,7 @@ __global__ void k_red_eval(Dev d, int max_iter, CondArgs ca) {
       d.red_eval[blockIdx.x] = e;
     }
   }
-  if (!last_of_instance(d, ch.inst)) return;
+  if (!runs_control(d, ch.inst, active)) return;
   if (threadIdx.x < 32) ctl_pre_warp(d, ch.inst, threadIdx.x, max_iter);
   if (ca.on && last_instance(d)) set_conditions(d, ca, END_EVAL);
 }
@@ -525,7 +537,8 @@ __device__ void ctl_dir_warp(const Dev& d, int i, int lane);
 __global__ void k_red_dir(Dev d, CondArgs ca) {
   const Chunk ch = d.chunks[blockIdx.x];
   const Ctl& c = d.ctl[ch.inst];
-  if (c.status == ST_RUNNING) {  // uniform over the block
+  const bool active = c.status == ST_RUNNING;  // uniform over the block
+  if (active) {
     const double mu = c.mu, tau = c.tau;
     double v[3] = {0.0, 0.0, 0.0};  // max primal ratio, max dual ratio, gphi
     const int op[3] = {1, 1, 0};
@@ -565,7 +578,7 @@ __global__ void k_red_dir(Dev d, CondArgs ca) {
       d.red_dir[blockIdx.x] = RedDir{ap, ad, v[2], 0.0};
     }
   }
-  if (!last_of_instance(d, ch.inst)) return;
+  if (!runs_control(d, ch.inst, active)) return;
   if (threadIdx.x < 32) ctl_dir_warp(d, ch.inst, threadIdx.x);
   if (ca.on && last_instance(d)) set_conditions(d, ca, END_DIR);
 }
@@ -629,7 +642,8 @@ __device__ void ctl_ls_warp(const Dev& d, int i, int lane);
 __global__ void k_red_trial(Dev d, CondArgs ca) {
   const Chunk ch = d.chunks[blockIdx.x];
   const Ctl& c = d.ctl[ch.inst];
-  if (c.ls_active) {  // uniform over the block
+  const bool active = c.ls_active != 0;  // uniform over the block
+  if (active) {
     const double gam = d.mc.gamma;
     double v[5] = {0.0, 1.0, 0.0, 0.0, 0.0};  // f, log-mantissa, log-exponent, theta, nonfinite
     const int op[5] = {0, 3, 0, 0, 0};
@@ -658,7 +672,7 @@ __global__ void k_red_trial(Dev d, CondArgs ca) {
     block_reduce<5>(v, op);
     if (threadIdx.x == 0) d.red_trial[blockIdx.x] = RedTrial{v[0], v[1], v[2], v[3], v[4]};
   }
-  if (!last_of_instance(d, ch.inst)) return;
+  if (!runs_control(d, ch.inst, active)) return;
   if (threadIdx.x < 32) ctl_ls_warp(d, ch.inst, threadIdx.x);
   if (ca.on && last_instance(d)) set_conditions(d, ca, END_TRIAL);
 }
