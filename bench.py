@@ -572,7 +572,7 @@ def paper_plate_resolves(P, dev, warmup=3, kkt=0):
 # DRAM bytes (read + write) of one k_factor_flow launch measured by ncu on the
 # first 64 instances of the batch (profiles/k_factor_flow_batch64_distillation_N34_T50_200.md),
 # with the flops of that case; the traffic grows with the instances as the flops do.
-FLOW64_DRAM_BYTES, FLOW64_FLOPS = 500.009728e6 + 368.840704e6, 1971262569.0
+FLOW64_DRAM_BYTES, FLOW64_FLOPS = 494.803712e6 + 368.445184e6, 1971262569.0
 
 
 def flow_traffic(opts, st):
