@@ -72,6 +72,11 @@ def hbm_rooflines(st, ph, latency_bound=False):
                      "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
         if latency_bound:
             out[name]["note"] = "working set L2-resident; latency-bound, not bandwidth-bound"
+    # the solves' FP64 work: one multiply-add per factor entry each way (4 nnz(L)
+    # flops); on this GPU their bound is FP64 issue and latency rather than HBM
+    tf = 4.0 * nnz / (ph["ms_solve"] * 1e-3) / 1e12
+    out["solves"]["fp64_tflops"] = tf
+    out["solves"]["fp64_frac_of_nominal"] = tf / fp64_nominal_tflops(_peaks().get("sm_max_mhz"))
     return out
 
 
