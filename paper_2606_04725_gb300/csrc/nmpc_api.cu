@@ -65,6 +65,7 @@ struct nmpc_handle {
   // persistent solves over the first solve_prefix levels (fronts in level order)
   int solve_prefix = 0, solve_prefix_fronts = 0, persist_blocks_fwd = 0, persist_blocks_bwd = 0;
   int persist_smem_fwd = 0, persist_smem_bwd = 0;
+  int persist_stage_cap = 0;  // doubles: panels staged by the persistent solves at most this large
   int* d_solve_flags = nullptr;
   // dataflow factorization (factor_mode 3) over the first flow_levels levels (fronts in level order)
   int flow_levels = 0, flow_fronts = 0, flow_blocks = 0, flow_smem = 0;
@@ -457,7 +458,7 @@ nmpc_status launch_solve(nmpc_handle* h) {
   }
   if (L > 0) {
     k_fwd_persist<<<h->persist_blocks_fwd, 128, h->persist_smem_fwd, h->stream>>>(
-        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, fwd_flags, list, h->d_front_cnt + 1);
+        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->persist_stage_cap, fwd_flags, list, h->d_front_cnt + 1);
     ++h->launches;
   }
   for (int l = L; l < nl; ++l) {
@@ -484,7 +485,7 @@ nmpc_status launch_solve(nmpc_handle* h) {
   }
   if (L > 0) {
     k_bwd_persist<<<h->persist_blocks_bwd, 128, h->persist_smem_bwd, h->stream>>>(
-        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->smem_cap_doubles, bwd_flags, list, h->d_front_cnt + 1);
+        h->d, h->s, h->s.desc, h->solve_prefix_fronts, h->persist_stage_cap, bwd_flags, list, h->d_front_cnt + 1);
     ++h->launches;
   }
   return NMPC_OK;
@@ -1129,6 +1130,21 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
     }
     h->solve_prefix = L;
     h->solve_prefix_fronts = nf;
+    // A batch's persistent solves stage only the panels of up to
+    // PERSIST_STAGE_CAP bytes (the rest read their panel from global memory):
+    // the launch's shared memory is its largest staged panel's, and one level
+    // of large fronts would otherwise hold every level to its occupancy.
+    h->persist_stage_cap = h->smem_cap_doubles;
+    if (h->front_lists) {
+      h->persist_stage_cap = PERSIST_STAGE_CAP / 8;
+      smf = smb = 8;
+      for (int q = 0; q < nf; ++q) {
+        const int sn = A.level_sn[q];
+        const long long mm = A.sn_nrow[sn], cc = A.sn_ncol[sn], lsz = (mm * cc + 1) & ~1LL;
+        const long long need = (lsz + mm + cc <= h->persist_stage_cap) ? lsz + mm + cc : mm + cc;
+        smf = smb = std::max<int>(smf, (int)(need * 8));
+      }
+    }
     h->persist_smem_fwd = smf;
     h->persist_smem_bwd = smb;
     if (smf > 48 * 1024) CUDA_TRY(h, cudaFuncSetAttribute(k_fwd_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, smf));
