@@ -807,10 +807,19 @@ __device__ bool fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   const double* Lg = s.L + fd.Lptr;
   const long long lsz = ((long long)m * c + 1) & ~1LL;
   const bool stage = lsz + m + c <= smem_cap;
-  double* fv = dsm + (stage ? lsz : 0);  // m: right-hand side, updated block by block
-  double* ys = fv + m;                   // c: y
+  // a panel too large to stage: column substitution still stages its c x c
+  // triangle (ld c) when that fits, and reads the rows below from global memory
+  const long long tsz = ((long long)c * c + 1) & ~1LL;
+  const bool tri = !stage && s.solve_form == 0 && c <= ST && tsz + m + c <= smem_cap;
+  double* fv = dsm + (stage ? lsz : (tri ? tsz : 0));  // m: right-hand side, updated block by block
+  double* ys = fv + m;                                 // c: y
   const double* Ls = stage ? dsm : Lg;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tri)
+    for (int t = tid; t < c * c; t += nt) {
+      const int j = t / c, i = t - j * c;
+      dsm[t] = Lg[i + (size_t)j * m];
+    }
   if (tid == 0 && stage) {
     // earlier generic accesses to this shared memory (a previous front of
     // this block) are ordered before the asynchronous copy
@@ -858,7 +867,8 @@ __device__ bool fwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   if (stage && tid == 0) mbar_inval(bar);
   double* uvJ = s.uv + fd.uvptr;  // u_i = f_i - sum_j L_ij y_j (rows c..m-1)
   if (s.solve_form == 0) {
-    subst_lower(fv, ys, Ls, m, c, stage, s, s_to);  // y in place of f_0..c-1
+    if (tri) subst_lower(fv, ys, dsm, c, c, true, s, s_to);  // y in place of f_0..c-1
+    else subst_lower(fv, ys, Ls, m, c, stage, s, s_to);
     block_dots(
         m - c, c, [&](int r, int j) { return Ls[(c + r) + (size_t)j * m]; }, [&](int j) { return fv[j]; },
         [&](int r, double a) { uvJ[r] = fv[c + r] - a; });
@@ -909,10 +919,17 @@ __device__ bool bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
   const int* rows_idx = s.sn_rows + fd.rowptr;
   const long long lsz = ((long long)m * c + 1) & ~1LL;
   const bool stage = lsz + m + c <= smem_cap;
-  double* xv = dsm + (stage ? lsz : 0);  // m: x (pivot rows solved block by block, ancestors' x below)
-  double* zs = xv + m;                   // c: z
+  const long long tsz = ((long long)c * c + 1) & ~1LL;  // staged triangle only (as in fwd_front)
+  const bool tri = !stage && s.solve_form == 0 && c <= ST && tsz + m + c <= smem_cap;
+  double* xv = dsm + (stage ? lsz : (tri ? tsz : 0));  // m: x (pivot rows solved block by block, ancestors' x below)
+  double* zs = xv + m;                                 // c: z
   const double* Ls = stage ? dsm : Lg;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tri)
+    for (int t = tid; t < c * c; t += nt) {
+      const int j = t / c, i = t - j * c;
+      dsm[t] = Lg[i + (size_t)j * m];
+    }
   if (tid == 0 && stage) {
     // earlier generic accesses to this shared memory (a previous front of
     // this block) are ordered before the asynchronous copy
@@ -935,7 +952,8 @@ __device__ bool bwd_front(const Dev& d, const SnDev& s, const FrontDesc& fd, int
     __syncthreads();
     for (int j = tid; j < c; j += nt) zs[j] = __longlong_as_double(SENTINEL);
     __syncthreads();
-    subst_upper(xv, zs, Ls, m, c, stage, s, s_to);
+    if (tri) subst_upper(xv, zs, dsm, c, c, true, s, s_to);
+    else subst_upper(xv, zs, Ls, m, c, stage, s, s_to);
     for (int j = tid; j < c; j += nt) d.b[first + j] = xv[j];
     return true;
   }

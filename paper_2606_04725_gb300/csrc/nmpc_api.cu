@@ -1141,7 +1141,10 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
       for (int q = 0; q < nf; ++q) {
         const int sn = A.level_sn[q];
         const long long mm = A.sn_nrow[sn], cc = A.sn_ncol[sn], lsz = (mm * cc + 1) & ~1LL;
-        const long long need = (lsz + mm + cc <= h->persist_stage_cap) ? lsz + mm + cc : mm + cc;
+        const long long tsz = (cc * cc + 1) & ~1LL;  // the triangle alone (column substitution)
+        const long long need = (lsz + mm + cc <= h->persist_stage_cap) ? lsz + mm + cc
+                               : (h->s_form == 0 && cc <= 128 && tsz + mm + cc <= h->persist_stage_cap) ? tsz + mm + cc
+                                                                                                          : mm + cc;
         smf = smb = std::max<int>(smf, (int)(need * 8));
       }
     }
