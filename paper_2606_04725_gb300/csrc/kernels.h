@@ -74,7 +74,7 @@ __global__ void k_bwd_persist(Dev d, SnDev s, const FrontDesc* dl, int nf, int s
 // a persistent launch (mode 0: need a factorization; 1: are being solved)
 constexpr int FL_THREADS = 1024;
 constexpr int FL_MAX_INST = 32768;  // one byte of shared memory per instance
-constexpr int PERSIST_STAGE_CAP = 32 * 1024;  // bytes: largest panel a batch's persistent solves stage
+constexpr int PERSIST_STAGE_CAP = 21 * 1024;  // bytes: largest panel a batch's persistent solves stage
 __global__ void k_front_list(Dev d, SnDev s, int nf, int mode, int* list, int* count);
 __global__ void k_diag_inv(Dev d, SnDev s, int i0);
 __global__ void k_panel_scale(Dev d, SnDev s, int u0);
