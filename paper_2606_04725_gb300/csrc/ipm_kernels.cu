@@ -513,8 +513,8 @@ __device__ void recover_row(const Dev& d, int r) {
   const double mu = c.mu, gam = d.mc.gamma;
   double Hd = 0.0;
   for (int s = 0; s < WH; ++s) {
-    const int col = d.Hcol[(size_t)r * WH + s];
-    if (col >= 0) Hd += d.Hv[(size_t)r * WH + s] * d.b[d.perm[col]];  // dy, read where the solve left it
+    const int pos = d.Hpos[(size_t)r * WH + s];
+    if (pos >= 0) Hd += d.Hv[(size_t)r * WH + s] * d.b[pos];  // dy, read where the solve left it
   }
   const double sp = d.sp[r], sm = d.sm[r], isp = d.isp[r], ism = d.ism[r];
   const double Qp = d.bp[r] * isp, Qm = d.bm[r] * ism;
@@ -814,8 +814,8 @@ __device__ __forceinline__ double row_times_b(const Dev& d, int r) {  // (H b)_r
   const int WH = d.mc.WH;
   double s = 0.0;
   for (int q = 0; q < WH; ++q) {
-    const int col = d.Hcol[(size_t)r * WH + q];
-    if (col >= 0) s += d.Hv[(size_t)r * WH + q] * d.b[d.perm[col]];
+    const int pos = d.Hpos[(size_t)r * WH + q];
+    if (pos >= 0) s += d.Hv[(size_t)r * WH + q] * d.b[pos];
   }
   return s;
 }

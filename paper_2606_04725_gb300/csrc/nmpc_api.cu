@@ -216,7 +216,7 @@ void carve(nmpc_handle* h, Carver& cv) {
   d.Wv = cv.take<double>(A.nW); d.fvar = cv.take<double>(n);
   d.igL = cv.take<double>(n); d.igU = cv.take<double>(n); d.izL = cv.take<double>(n); d.izU = cv.take<double>(n);
   d.isp = cv.take<double>(m); d.ism = cv.take<double>(m); d.ibp = cv.take<double>(m); d.ibm = cv.take<double>(m);
-  d.Hcol = cv.take<int>((size_t)m * WH);
+  d.Hcol = cv.take<int>((size_t)m * WH); d.Hpos = cv.take<int>((size_t)m * WH);
   d.Hcsc_ptr = cv.take<int>(n + 1); d.Hcsc_slot = cv.take<int>(A.Hcsc_slot.size());
   d.Wadj_ptr = cv.take<int>(n + 1); d.Wadj_slot = cv.take<int>(A.Wadj_slot.size());
   d.Wadj_other = cv.take<int>(A.Wadj_other.size());
@@ -1043,6 +1043,12 @@ nmpc_status upload_structure(nmpc_handle* h, void* ws) {
   CUDA_TRY(h, up(d.Wadj_ptr, A.Wadj_ptr, st)); CUDA_TRY(h, up(d.Wadj_slot, A.Wadj_slot, st));
   CUDA_TRY(h, up(d.Wadj_other, A.Wadj_other, st));
   CUDA_TRY(h, up(d.perm, A.perm, st)); CUDA_TRY(h, up(d.iperm, A.iperm, st));
+  {
+    std::vector<int> hpos(A.Hcol.size());
+    for (size_t q = 0; q < hpos.size(); ++q) hpos[q] = A.Hcol[q] >= 0 ? A.perm[A.Hcol[q]] : -1;
+    CUDA_TRY(h, up(d.Hpos, hpos, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));  // hpos goes out of scope
+  }
   CUDA_TRY(h, up(d.chunks, ch, st)); CUDA_TRY(h, up(d.inst_chunk_ptr, A.inst_chunk_ptr, st));
   CUDA_TRY(h, up(d.red_var, A.red_var, st));
   CUDA_TRY(h, up(d.inst_chunk_list, A.inst_chunk_list, st));

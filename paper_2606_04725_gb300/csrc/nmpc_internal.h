@@ -130,6 +130,7 @@ struct Dev {
   // reciprocals at the current iterate: bound gaps, bound duals (n); slacks, slack duals (m)
   double *igL, *igU, *izL, *izU, *isp, *ism, *ibp, *ibm;
   const int* Hcol;
+  const int* Hpos;      // per H slot: factor position of its column (perm[Hcol]), -1 for an empty slot
   const int* Hcsc_ptr; const int* Hcsc_slot;
   const int* Wadj_ptr; const int* Wadj_slot; const int* Wadj_other;
   // direction (HyKKT: dwp is lambda's step, the CG iterate)
