@@ -3,7 +3,8 @@
 n = 105,024).  The oracle's band Cholesky is out of reach here (4.5e11 flops
 per factorization), so the oracle runs its sparse Cholesky after its own
 nested-dissection ordering (linsolve = 1, 1.8e11 flops per factorization,
-about a minute and a half each); its results are stored once.
+about three minutes each on one host core: 3.5 hours for the cold solve, about
+an hour more for the six re-solves); its results are stored once.
 
 Calls only the oracle (and the seeded input recipes):
   * a cold solve at tol 1e-12 from the zero initial field, target field of

@@ -3,8 +3,8 @@ at the reduced grid g = 32 (S = 16, T = 100, n = 105,024), on the GPU under
 the library's defaults (nested dissection, large-front path) against the
 oracle's sparse Cholesky with its own nested dissection.
 
-The oracle needs about an hour and a half for its cold solve here, so its
-results were written once by tests/golden/make_plate_g32_S16_T100.py (oracle
+The oracle needs three and a half hours of one host core for its cold solve
+here, so its results were written once by tests/golden/make_plate_g32_S16_T100.py (oracle
 only) to tests/golden/plate_g32_S16_T100.json.  Pins:
   * the converged primal point at tol 1e-12 equals the oracle's at 4096 seeded
     positions within 1e-6 relative, with the same objective and tracking loss;
