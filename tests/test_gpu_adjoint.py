@@ -151,3 +151,24 @@ def test_autograd_function(P):
     s.sensitivity(0, gy, dx0, dsp)
     torch.testing.assert_close(gx, dx0, rtol=1e-12, atol=1e-14)
     torch.testing.assert_close(gs, dsp - 2 * (y.detach()[idx] - sp.detach()), rtol=1e-12, atol=1e-14)
+
+
+def test_envelope_theorem_in_a_batch(P, oracle):
+    """In a batch of three columns with uneven horizons (the batch's solves run
+    over front lists), the adjoint of each instance satisfies the envelope
+    theorem on its own initial-condition rows, as the single column does."""
+    hz = [14, 20, 26]
+    s = P.Solver(P.MODEL_DISTILLATION, hz, N=12, Nf=5, opts=P.options(tol=1e-10))
+    x0s = [I.distillation_x0(12, 5, seed=11 + i) for i in range(3)]
+    sps = [np.full(T, 0.78 + 0.02 * i) for i, T in enumerate(hz)]
+    for i in range(3):
+        s.set_params(x0=x0s[i], setpoint=sps[i], u_prev=np.array([I.U_REF]), instance=i)
+    assert all(info["status"] == 0 for info in s.solve())
+    for i, T in enumerate(hz):
+        y, du = s.get_solution(i, duals=True)
+        prob = oracle.distillation(12, 5, T, x0s[i], sps[i], I.U_REF)
+        _, grad_f, _, _ = oracle.evaluate(prob, y)
+        dx0 = np.zeros(12)
+        s.sensitivity(i, grad_f, dx0, np.zeros(T))
+        lam0 = du["w_p"][:12] - du["w_m"][:12]
+        np.testing.assert_allclose(dx0, -lam0, rtol=1e-5, atol=1e-7, err_msg=f"instance {i}")
