@@ -295,7 +295,12 @@ nmpc_status nmpc_instance_dims(const nmpc_handle* h, int instance, int* n, int* 
  *   5 supernode parent (-1 for roots)
  *   6 level pointer (n_levels + 1), 7 supernodes ordered by level
  *   8 condensed-matrix lower pattern as (row, col) pairs in factor order
- *     (2 int32 per entry; the returned length counts pairs) */
+ *     (2 int32 per entry; the returned length counts pairs)
+ *   9 reduction chunks as (instance, kind 0 variables / 1 rows, begin, end)
+ *     (4 int32 per chunk; the returned length counts chunks)
+ *   10 the variables in the order the reductions visit them (n_total): chunk
+ *      by chunk, longest column of the Jacobian first
+ *   11 entries of each variable's column of the Jacobian (n_total) */
 long long nmpc_structure_export(const nmpc_handle* h, int what, void* out, long long cap);
 
 /* Size of the library's static device workspace used by nmpc_solve_static. */

@@ -243,9 +243,10 @@ class Structure:
         cnt = L.nmpc_structure_export(self._h, what, None, 0)
         if cnt < 0:
             raise ValueError(what)
-        out = np.empty(cnt * (2 if what == 8 else 1), dtype=np.int32)
+        width = {8: 2, 9: 4}.get(what, 1)
+        out = np.empty(cnt * width, dtype=np.int32)
         L.nmpc_structure_export(self._h, what, out.ctypes.data, cnt)
-        return out.reshape(-1, 2) if what == 8 else out
+        return out.reshape(-1, width) if width > 1 else out
 
     def workspace_bytes(self):
         b = C.c_size_t()

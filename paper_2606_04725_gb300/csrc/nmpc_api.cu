@@ -1591,6 +1591,21 @@ long long nmpc_structure_export(const nmpc_handle* h, int what, void* out, long 
     case 5: return copy(A.sn_parent);
     case 6: return copy(A.level_ptr);
     case 7: return copy(A.level_sn);
+    case 9: {  // reduction chunks: (instance, kind, begin, end) each
+      const long long cnt = (long long)A.chunks.size();
+      int* o = static_cast<int*>(out);
+      for (long long c = 0; out && c < std::min(cap, cnt); ++c) {
+        const Chunk& ch = A.chunks[c];
+        o[4 * c] = ch.inst; o[4 * c + 1] = ch.kind; o[4 * c + 2] = ch.begin; o[4 * c + 3] = ch.end;
+      }
+      return cnt;
+    }
+    case 10: return copy(A.red_var);
+    case 11: {  // entries of each variable's column of H
+      std::vector<int> len(A.n);
+      for (int v = 0; v < A.n; ++v) len[v] = A.Hcsc_ptr[v + 1] - A.Hcsc_ptr[v];
+      return copy(len);
+    }
     case 8: {
       const long long cnt = (long long)A.tgt_L.size();
       int* o = static_cast<int*>(out);

@@ -253,3 +253,37 @@ def test_library_and_oracle_default_to_the_same_model_constants(P, oracle):
         gp, _ = P._lib.problem(model, [3])
         for f in fields:
             assert getattr(gp, f) == getattr(op._p, f), (model, f, getattr(gp, f), getattr(op._p, f))
+
+
+@pytest.mark.parametrize("hz", [[200], [50 + 37 * (i % 5) for i in range(40)], [60 + (i * 7) % 140 for i in range(256)]])
+def test_reduction_chunks_and_visiting_order(P, hz):
+    """Reduction chunks partition every instance's variables and rows without
+    crossing an instance, hold at most 128 E elements with E = clamp(total /
+    (1216 x 128), 1, 16), and the reductions visit each variable chunk's
+    variables longest Jacobian column first, ties in index order."""
+    S = P.Structure(P.MODEL_DISTILLATION, hz, N=34, Nf=17)
+    st = S.stats()
+    n, m = st["n_total"], st["m_total"]
+    E = max(1, min(16, (n + m) // (1216 * 128)))
+    # instance offsets: x_0 plus (x_k, u_k) per stage; the initial rows plus N per stage
+    voff = np.concatenate([[0], np.cumsum([34 + T * 35 for T in hz])])
+    roff = np.concatenate([[0], np.cumsum([34 + T * 34 for T in hz])])
+    assert voff[-1] == n and roff[-1] == m
+    ch = S.export(9)
+    order = S.export(10)
+    clen = S.export(11)
+    assert sorted(order.tolist()) == list(range(n))
+    seen_v = np.zeros(n, dtype=int)
+    seen_r = np.zeros(m, dtype=int)
+    for inst, kind, b, e in ch:
+        assert 0 < e - b <= 128 * E
+        (seen_v if kind == 0 else seen_r)[b:e] += 1
+        lo, hi = (voff[inst], voff[inst + 1]) if kind == 0 else (roff[inst], roff[inst + 1])
+        assert lo <= b and e <= hi  # inside its own instance
+        if kind == 0:
+            vs = order[b:e]
+            assert sorted(vs.tolist()) == list(range(b, e))  # the chunk's own variables
+            key = [(-clen[v], v) for v in vs]
+            assert key == sorted(key)
+    assert (seen_v == 1).all() and (seen_r == 1).all()
+    S.close()
